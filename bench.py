@@ -1,0 +1,327 @@
+"""Benchmark: particles/s of one full FMM velocity evaluation of 2^24 clustered
+Gaussian vortex blobs (8 Gaussian clusters, std 0.02; L = 10, p = 17,
+sigma = 0.002, FP32 storage) in mixed precision, checked against the FP64 GPU
+FMM at rel-L2 <= 1e-5.
+
+One step = one ``petfmm_evaluate`` (binning, sort, P2M, M2M, M2L, L2L, P2P +
+L2P) on inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+``--impl reference`` times the FP64 CPU oracle (the textbook FMM written from
+the paper) on the host cores, on a bounded sample of the same workload.
+Multi-GPU: the evaluation is not sharded; N ranks run independent replicas
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0905_2637_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particles/s per FMM eval, N=16M p=17, mixed vs FP64 at rel-L2≤1e-5; p99 latency"
+WORKLOAD = ("clustered-16M: N=16777216 Gaussian blobs from 8 isotropic clusters "
+            "(centres U(0.2,0.8)^2, std 0.02), gamma~N(0,1)/N, sigma=0.002, L=10, p=17, "
+            "fp32 storage, mixed precision")
+P2P_OPS_PER_PAIR = 14       # FP32 operations of one pair of Eq. 8/9, written out
+SMS, FP32_LANES = 152, 128  # GB300: SMs, FP32 lanes per SM
+PROFILE = os.path.join(ROOT, "profiles", "p2p_clustered16M.md")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()] if vis else []
+        self.gpu = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.file:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _p2p_traffic():
+    """DRAM bytes per P2P launch from the committed ncu summary, or None if
+    the kernel source changed since it was taken."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"p2p_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h:
+        return None
+    src = open(os.path.join(ROOT, "paper_0905_2637_gb300", "csrc", "p2p.cu"), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
+        return None
+    return float(m.group(1))
+
+
+def cpu_sample_workload():
+    # The same clustered recipe with 4^-3 of the blobs on a tree 3 levels
+    # shallower: equal expected blobs per leaf, so equal work per blob.
+    return W.clustered_scaled(shrink_levels=3)
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = cpu_sample_workload()
+    xd, yd, gd = w.as_f64()
+    threads = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle.fmm(xd, yd, gd, w.domain, w.L, w.p, w.sigma)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fmm(xd, yd, gd, w.domain, w.L, w.p, w.sigma)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = w.n * args.steps / total
+    sample = (f"oracle FMM (FP64, OpenMP) on {w.name}: N={w.n}, L={w.L}, p={w.p}, same cluster recipe "
+              f"and blobs per leaf as the full workload; one full evaluation per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline():
+    import oracle
+    oracle.build()
+    w = cpu_sample_workload()
+    xd, yd, gd = w.as_f64()
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.fmm(xd, yd, gd, w.domain, w.L, w.p, w.sigma)
+    dt = time.perf_counter() - t0
+    return {"value": w.n / dt, "unit": "particles/s", "cores": threads, "kind": "oracle",
+            "sample": f"oracle FMM (FP64, OpenMP {threads} threads) on {w.name}: N={w.n}, L={w.L}, "
+                      f"p={w.p}, same recipe and blobs per leaf; {dt:.1f} s wall"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0905_2637_gb300 import _lib
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = W.clustered()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        x, y, g = (torch.from_numpy(a).cuda() for a in (w.x, w.y, w.gamma))
+        u = torch.empty_like(x)
+        v = torch.empty_like(x)
+    torch.cuda.synchronize()
+    ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype="f32", stream=stream)
+    ctx.set_option(_lib.PETFMM_OPT_TIMING, 1)
+    for _ in range(args.warmup):
+        ctx.evaluate(x, y, g, u, v)
+    ctx.sync()
+    launches0 = ctx.stats()["kernel_launches"]
+
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.evaluate(x, y, g, u, v)
+    ev1.record(stream)
+    ctx.sync()
+    torch.cuda.synchronize()
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = ctx.stats()["kernel_launches"] - launches0
+    # P2P kernel duration per launch: the library's CUDA events around the
+    # launch, on the stream it launches on, one step at a time
+    p2p_ms = []
+    for _ in range(args.steps):
+        ctx.evaluate(x, y, g, u, v)
+        ctx.sync()
+        p2p_ms.append(ctx.stage_times()["p2p"])
+    clocks = sampler.stop()
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    stats = ctx.stats()
+    stages = ctx.stage_times()
+    value = w.n * args.steps * ws / elapsed
+
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    hx, hy, hg = (torch.from_numpy(a).pin_memory() for a in (w.x, w.y, w.gamma))
+    hu, hv = torch.empty_like(hx).pin_memory(), torch.empty_like(hx).pin_memory()
+    ctx.evaluate_host_ptrs(w.n, hx.data_ptr(), hy.data_ptr(), hg.data_ptr(), hu.data_ptr(), hv.data_ptr())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.evaluate_host_ptrs(w.n, hx.data_ptr(), hy.data_ptr(), hg.data_ptr(), hu.data_ptr(), hv.data_ptr())
+    e2e_t = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e = {"value": w.n * args.steps * ws / e2e_t, "unit": "particles/s",
+           "h2d_bytes_per_step": 3 * w.n * 4, "d2h_bytes_per_step": 2 * w.n * 4}
+
+    # accuracy gate and the FP64 GPU FMM on the same GPU
+    umx, vmx = u.clone(), v.clone()
+    fp64 = None
+    rel = None
+    if not args.no_fp64:
+        ctx64 = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="fp64", dtype="f32", stream=stream)
+        u64, v64 = torch.empty_like(x), torch.empty_like(x)
+        ctx64.evaluate(x, y, g, u64, v64)
+        ctx64.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx64.evaluate(x, y, g, u64, v64)
+        e1.record(stream)
+        ctx64.sync()
+        t64 = e0.elapsed_time(e1) / 1e3
+        ctx64.close()
+        d = (umx.double() - u64.double()) ** 2 + (vmx.double() - v64.double()) ** 2
+        ref = u64.double() ** 2 + v64.double() ** 2
+        rel = float(torch.sqrt(d.sum() / ref.sum()))
+        fp64 = {"value": w.n / t64, "unit": "particles/s", "ms_per_step": 1e3 * t64}
+
+    peaks, peak_kind = _peaks()
+    pairs = stats["p2p_pairs"]
+    p2p_t = statistics.mean(p2p_ms) / 1e3
+    achieved = pairs * P2P_OPS_PER_PAIR / p2p_t / 1e12
+    peak = SMS * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "k_p2p_mixed (P2P + L2P)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": _p2p_traffic(),
+                "note": (f"{P2P_OPS_PER_PAIR} FP32 ops per ordered pair x {pairs} pairs / mean P2P "
+                         f"launch {1e3 * p2p_t:.3f} ms (CUDA events on the launching stream); peak = "
+                         f"{SMS} SMs x {FP32_LANES} FP32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} "
+                         f"MHz ({peak_kind} max SM clock), one op per lane per cycle")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": w.n, "levels": w.L, "order": w.p,
+                           "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                           "l2": "inputs larger than L2 (x, y, gamma 201 MB; u, v 134 MB)"},
+                "rel_l2_vs_fp64": rel, "fp64_gpu": fp64,
+                "stages_ms": stages, "p2p_pairs": pairs, "m2l_pairs": stats["m2l_pairs"],
+                "p2p_load_balance": stats["p2p_load_balance"],
+                "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
+                "gpu": torch.cuda.get_device_name()}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

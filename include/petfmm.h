@@ -1,0 +1,257 @@
+/*
+ * petfmm.h -- C ABI of the GB300 (sm_103a) 2D vortex-blob fast multipole
+ * library.
+ *
+ * One call evaluates the velocity that N Gaussian vortex blobs induce on one
+ * another, the N-body sum of Eq. 1 with targets = sources, in the vortex-method
+ * form of Sec. 3:
+ *
+ *     u(x_i) = sum_{j != i} gamma_j K_sigma(x_i - x_j)                  (Eq. 9)
+ *     K_sigma(x) = (-x2, x1) (1 - exp(-|x|^2 / 2 sigma^2)) / (2 pi |x|^2) (Eq. 8)
+ *
+ * accelerated by the fast multipole method of Sec. 2 (Fig. 2): binning into a
+ * uniform quadtree with z-order numbering (Sec. 2.1, Sec. 5.1), P2M and M2M
+ * (upward sweep), M2L over each box's interaction list and L2L (downward
+ * sweep), then L2P plus the direct near-field P2P over the box and its 8
+ * neighbours (evaluation step).  The far field uses the expansions of the
+ * singular kernel 1/|x|^2 (kernel substitution, end of Sec. 3); the near field
+ * uses K_sigma exactly.  Expansions have p terms (k = 0..p-1).
+ *
+ * Conventions for every entry point:
+ *   - Status: 0 (PETFMM_OK) or a negative PETFMM_E* code; nothing else crosses
+ *     the ABI (no exceptions, no exit).  petfmm_strerror() names a code.
+ *   - Device pointers are CUDA global-memory pointers on the context's device;
+ *     host pointers are ordinary (preferably page-locked) host memory.
+ *   - x, y, gamma, u, v are dense 1-D arrays of n elements of the context's
+ *     storage type (PETFMM_F64: double, PETFMM_F32: float), owned by the caller.
+ *   - Kernels are enqueued on the context's CUDA stream; device-side errors
+ *     (a particle outside the domain, a bounded wait that ran out) are
+ *     recorded in a status word and returned by the next petfmm_sync().
+ *   - A context is bound to one stream and one device and is not thread-safe;
+ *     the server (petfmm_serve_*) is thread-safe.
+ */
+#ifndef PETFMM_H
+#define PETFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    PETFMM_OK = 0,
+    PETFMM_EINVAL = -1,    /* an argument is out of range (checked before any launch) */
+    PETFMM_ENOMEM = -2,    /* device or host allocation failed, or over a memory budget */
+    PETFMM_EDOMAIN = -3,   /* a particle lies outside the closed domain square, or is NaN */
+    PETFMM_ECUDA = -4,     /* a CUDA runtime call failed */
+    PETFMM_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+    PETFMM_EBUSY = -6,     /* the server has no free slot and the queue is full */
+    PETFMM_ENOTREADY = -7  /* a served request has not finished yet */
+};
+
+/* Precision mode of the arithmetic. */
+enum {
+    PETFMM_FP64 = 0,   /* every stage in FP64 */
+    PETFMM_MIXED = 1   /* binning/sort exact, P2P and expansions in FP32 with
+                          rescaled expansions, M2L on the tensor cores (3xTF32) */
+};
+
+/* Storage type of x, y, gamma, u, v. */
+enum { PETFMM_F64 = 0, PETFMM_F32 = 1 };
+
+/* Closed square domain [x0, x0 + width] x [y0, y0 + width] (Sec. 2.1). */
+typedef struct {
+    double x0, y0, width;
+} petfmm_domain;
+
+typedef struct petfmm_ctx petfmm_ctx;
+
+/*
+ * petfmm_create -- make an evaluation context (Sec. 6.1: the Evaluator over a
+ * Quadtree with one Kernel; here the regularised Biot-Savart kernel).
+ *   dom        domain square (width > 0, finite).
+ *   levels     depth L of the uniform quadtree, 1..15 (leaves = 4^L); the
+ *              interaction lists are empty at levels 0 and 1 (Sec. 2.2).
+ *   order      p, the number of expansion terms, 1..40 (Sec. 2, Table 1).
+ *   sigma      blob core size of Eq. 5 / Eq. 8, > 0.
+ *   precision  PETFMM_FP64 or PETFMM_MIXED.
+ *   dtype      PETFMM_F64 or PETFMM_F32 (storage type of the caller's arrays).
+ *   cuda_stream  a cudaStream_t of the current device, or NULL for the
+ *              legacy default stream.
+ *   out        receives the context; the library owns it and every buffer
+ *              in it until petfmm_destroy().
+ * Returns PETFMM_EINVAL for out-of-range arguments, PETFMM_ENOMEM, or
+ * PETFMM_ECUDA.
+ */
+int petfmm_create(const petfmm_domain *dom, int levels, int order, double sigma,
+                  int precision, int dtype, void *cuda_stream, petfmm_ctx **out);
+
+/*
+ * petfmm_evaluate -- one full FMM velocity evaluation (Sec. 2.2): Morton
+ * binning and sort, P2M, M2M, M2L, L2L, L2P + P2P, written back to u, v in
+ * the caller's particle order.
+ *   n          number of particles, 0 <= n < 2^31.
+ *   x, y, gamma  device arrays (positions and circulations gamma_j of Eq. 4).
+ *   u, v       device arrays receiving the velocity of Eq. 9 (including the
+ *              1/2pi factor); may not alias the inputs.
+ * Asynchronous on the context's stream: the arrays must stay valid until
+ * petfmm_sync() returns.  Library buffers grow on demand (PETFMM_ENOMEM if
+ * that fails).  A particle outside the domain makes the next petfmm_sync()
+ * return PETFMM_EDOMAIN; u, v are then unspecified.
+ */
+int petfmm_evaluate(petfmm_ctx *ctx, int64_t n, const void *x, const void *y,
+                    const void *gamma, void *u, void *v);
+
+/*
+ * petfmm_evaluate_host -- the same evaluation with HOST arrays: copies x, y,
+ * gamma to the device, evaluates, copies u, v back, and waits.  Pinned host
+ * memory gives the fastest copies.  Returns the evaluation's status.
+ */
+int petfmm_evaluate_host(petfmm_ctx *ctx, int64_t n, const void *x, const void *y,
+                         const void *gamma, void *u, void *v);
+
+/* petfmm_sync -- wait for the context's stream; returns the first deferred
+ * device status since the previous sync (and clears it). */
+int petfmm_sync(petfmm_ctx *ctx);
+
+/* petfmm_destroy -- wait for outstanding work and free the context. */
+int petfmm_destroy(petfmm_ctx *ctx);
+
+/*
+ * Batched evaluation: many independent FMM problems of uneven size in one
+ * pass of batched kernels (every stage launches once for all instances, or
+ * once per tree level).
+ *   levels <= 0 asks the library to choose L from the work model of Sec. 5.2
+ *   (Eq. 14), under the kernel-substitution guard exp(-r_L^2 / 2 sigma^2) <=
+ *   1e-8 for the leaf width r_L.
+ * The context supplies precision, storage type, stream and workspace; its own
+ * domain, L, p, sigma are not used.  Arrays are device pointers; the call is
+ * asynchronous like petfmm_evaluate().  Each instance's result is bit-for-bit
+ * the one it gets alone.
+ */
+typedef struct {
+    petfmm_domain domain;
+    int levels;          /* L, or <= 0 for automatic */
+    int order;           /* p, 1..40 */
+    double sigma;        /* > 0 */
+    int64_t n;           /* particles, >= 0 */
+    const void *x, *y, *gamma;
+    void *u, *v;
+} petfmm_instance;
+
+int petfmm_evaluate_batch(petfmm_ctx *ctx, int n_inst, const petfmm_instance *inst);
+
+/*
+ * petfmm_choose_levels -- the automatic L of petfmm_evaluate_batch for one
+ * problem: minimises the Sec. 5.2 work estimate (Eq. 13 for the upper levels,
+ * Eq. 14 for the leaves, uniform occupancy assumed) under the guard above.
+ * Returns L >= 1, or PETFMM_EINVAL.
+ */
+int petfmm_choose_levels(int64_t n, int order, double sigma, const petfmm_domain *dom);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: a thread-safe request loop with continuous batching.           */
+/* ---------------------------------------------------------------------- */
+typedef struct petfmm_server petfmm_server;
+
+/*
+ * One request = n_steps midpoint-RK2 steps (2 velocity evaluations each) of
+ * the Lagrangian vortex method of Sec. 3 (Eq. 6: blobs move with their
+ * velocity, gamma is carried unchanged).  x, y, gamma are HOST arrays copied
+ * at submit time; the domain is re-fitted on the device before every
+ * evaluation (a square around the current blobs), so blobs may leave the
+ * initial square.
+ */
+typedef struct {
+    int64_t n;
+    const double *x, *y, *gamma;  /* host, FP64, copied at submit */
+    int levels, order;            /* levels <= 0: automatic */
+    double sigma, dt;
+    int n_steps;                  /* RK2 steps (evaluations = 2 * n_steps) */
+    int precision;                /* PETFMM_FP64 or PETFMM_MIXED */
+} petfmm_request;
+
+typedef struct {
+    int status;            /* PETFMM_OK or the request's error */
+    double latency_ms;     /* submit -> completion */
+    double queue_ms;       /* submit -> admission */
+    int64_t n;
+    double *x, *y;         /* host arrays owned by the server: final positions
+                              (valid until petfmm_serve_release or destroy) */
+} petfmm_result;
+
+/* hbm_budget_bytes: device memory the server may hold for admitted requests;
+ * max_slots: most requests resident at once; max_queue: most waiting. */
+int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue,
+                        petfmm_server **out);
+/* Queue a request; PETFMM_EBUSY if the queue is full, PETFMM_EINVAL, or
+ * PETFMM_ENOMEM if the request alone exceeds the budget. */
+int petfmm_serve_submit(petfmm_server *s, const petfmm_request *req, uint64_t *ticket);
+/* PETFMM_ENOTREADY until the request is done; then fills *out. */
+int petfmm_serve_poll(petfmm_server *s, uint64_t ticket, petfmm_result *out);
+/* Free a finished request's result arrays. */
+int petfmm_serve_release(petfmm_server *s, uint64_t ticket);
+/* Stop the scheduler thread (finishing admitted work) and free everything. */
+int petfmm_serve_destroy(petfmm_server *s);
+/* Per-request device-memory estimate used for admission (Table 1 adapted). */
+size_t petfmm_serve_estimate_bytes(int64_t n, int levels, int order, int precision);
+
+/* ---------------------------------------------------------------------- */
+/* Inspection (the verification dump of Sec. 6.2) and instrumentation.    */
+/* ---------------------------------------------------------------------- */
+
+/* Tree of the last petfmm_evaluate (after petfmm_sync): host arrays
+ * keys[n] (Morton key of each particle, input order), perm[n] (input index
+ * of each sorted rank) and start[4^L + 1] (first rank of each leaf).
+ * Any pointer may be NULL. */
+int petfmm_debug_tree(petfmm_ctx *ctx, uint32_t *keys, uint32_t *perm, uint32_t *start);
+
+/* Expansions of level `level` (2..L) of the last evaluation, copied to the
+ * host as FP64 complex pairs out[(m * p + k) * 2 + {0,1}], m = Morton index.
+ * which = 0: multipole (ME), scaled a_k / r^k; which = 1: local (LE), scaled
+ * r^(k+1) b_k; r = box width at that level. */
+int petfmm_debug_expansions(petfmm_ctx *ctx, int level, int which, double *out);
+
+/* Interaction list of box (level, ix, iy) as the device kernels enumerate it:
+ * out[2 * i], out[2 * i + 1] = source box coordinates (at most 27 entries);
+ * returns the count, or PETFMM_EINVAL. */
+int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out);
+
+/* Options. */
+enum {
+    PETFMM_OPT_TIMING = 1,     /* 1: record per-stage CUDA events each evaluation */
+    PETFMM_OPT_SPIN_LIMIT = 2, /* iteration limit of device-side waits (0 = default) */
+    PETFMM_OPT_P2P_MODE = 3    /* P2P scheduler: 0 work-model partition, 1 dynamic queue */
+};
+int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
+
+/* Stages reported by petfmm_stage_times (milliseconds, last evaluation). */
+enum {
+    PETFMM_STAGE_MORTON = 0, PETFMM_STAGE_SORT, PETFMM_STAGE_GATHER, PETFMM_STAGE_P2M,
+    PETFMM_STAGE_M2M, PETFMM_STAGE_M2L, PETFMM_STAGE_L2L, PETFMM_STAGE_WORKLIST,
+    PETFMM_STAGE_P2P, PETFMM_STAGE_COUNT
+};
+int petfmm_stage_times(petfmm_ctx *ctx, float *ms, int cap);
+
+typedef struct {
+    uint64_t kernel_launches;  /* kernels this context has launched */
+    uint64_t evaluations;
+    int64_t p2p_pairs;         /* ordered near-field pairs of the last evaluation */
+    int64_t m2l_pairs;         /* (target, source) M2L translations of the last evaluation */
+    int64_t p2p_items;         /* P2P work items of the last evaluation */
+    float p2p_load_balance;    /* min / max CTA busy time of the last P2P (Eq. 20) */
+} petfmm_stats;
+/* Counters; p2p_pairs, m2l_pairs, p2p_items and p2p_load_balance need
+ * PETFMM_OPT_TIMING and a petfmm_sync() after the evaluation. */
+int petfmm_get_stats(petfmm_ctx *ctx, petfmm_stats *out);
+
+const char *petfmm_strerror(int code);
+int petfmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PETFMM_H */

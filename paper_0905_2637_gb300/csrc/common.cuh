@@ -1,0 +1,151 @@
+// common.cuh -- shared definitions of the GB300 vortex-blob FMM kernels.
+//
+// Data layout in HBM (one batch of instances; a single evaluation is a batch
+// of one):
+//   particles   keys/vals (uint32) ping-pong pairs for the radix sort, then
+//               the sorted particles: FP64 path SoA double x, y, gamma (global
+//               coordinates); mixed path float4 (xi, eta, gamma, 0) with
+//               (xi, eta) = (x - leaf centre) / leaf width, i.e. leaf-relative
+//               coordinates in leaf units (exact for FP32 inputs on a dyadic
+//               domain).
+//   start       per instance 4^L + 1 uint32 leaf starts (global sorted rank).
+//   ME, LE      per instance, per level l, 4^l boxes x p complex coefficients
+//               (double2 or float2).  Boxes of a level are stored "by child
+//               class": box (ix, iy) at level l >= 1 has class
+//               c = (ix & 1) | (iy & 1) << 1 and parent cell P = (ix >> 1,
+//               iy >> 1), and index c * 4^(l-1) + Py * 2^(l-1) + Px.  The four
+//               children of one parent sit at the same P in four planes, and a
+//               fixed (class, parent offset) pair of the interaction list is a
+//               constant shift of the parent grid.
+//   Expansions are rescaled so that the translation operators do not depend
+//   on the level and FP32 cannot overflow: a~_k = a_k / r^k (ME) and
+//   c^_m = r^(m+1) b_m (LE), r = box width.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace petfmm {
+
+constexpr int MAX_P = 40;
+constexpr int MAX_L = 15;
+constexpr int POLY_MAX = 14;
+
+// Device status codes (same values as the PETFMM_E* codes of the ABI).
+constexpr int ST_EDOMAIN = -3;
+constexpr int ST_ETIMEOUT = -5;
+
+// One FMM problem of a batch.
+struct InstDesc {
+    double x0, y0, width;   // domain square
+    double scale;           // 2^L / width (computed once on the host)
+    double wleaf;           // width / 2^L
+    double sigma;
+    int L, p;
+    int64_t n;              // particles
+    int64_t poff;           // first particle of this instance in batch arrays
+    int64_t soff;           // first entry of its leaf-start array
+    int64_t loff;           // first leaf of this instance in batch leaf arrays
+    int64_t eoff;           // first box of this instance in ME/LE (box units)
+    uint32_t key_hi;        // composite sort key = key_hi | Morton key
+    int pad0;
+    const void *x, *y, *g;  // caller's arrays (storage type of the context)
+    void *u, *v;
+    const void *t_m2m, *t_l2l, *t_m2l;  // operator tables for this p (path's real type)
+    // mixed-precision P2P constants (leaf units)
+    float kappa;            // w^2 / (2 sigma^2): q = kappa * rho^2
+    float cnear;            // w / (4 pi sigma^2)
+    float cfar;             // 1 / (2 pi w)
+    float qsplit_rho2;      // general path: polynomial below this rho^2
+    int deg;                // polynomial degree (in rho^2) of g(q) = (1 - e^-q) / q
+    int general;            // 1: some near pairs exceed the polynomial range
+    float poly[POLY_MAX + 1];
+    // FP64 constants
+    double inv2s2;          // 1 / (2 sigma^2)
+    double cnear64;         // 1 / (2 pi)
+    double cfar64;          // 1 / (2 pi w)
+};
+
+// A range of work units of one kind, for one instance (and level).
+struct Task {
+    int inst;
+    int level;
+    int64_t count;    // work units
+    int64_t block0;   // first block of the launch assigned to this task
+};
+
+__host__ __device__ __forceinline__ int64_t lvl_off(int l) {
+    return ((int64_t(1) << (2 * l)) - 1) / 3;
+}
+
+// index of box (ix, iy) within its level, class-split layout
+__host__ __device__ __forceinline__ int64_t box_index(int l, uint32_t ix, uint32_t iy) {
+    if (l == 0) return 0;
+    int64_t q = int64_t(1) << (2 * (l - 1));
+    int64_t c = (ix & 1u) | ((iy & 1u) << 1);
+    return c * q + int64_t(iy >> 1) * (int64_t(1) << (l - 1)) + int64_t(ix >> 1);
+}
+
+__host__ __device__ __forceinline__ uint32_t spread_bits(uint32_t v) {
+    v &= 0x0000ffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__host__ __device__ __forceinline__ uint32_t compact_bits(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0f0f0f0fu;
+    v = (v | (v >> 4)) & 0x00ff00ffu;
+    v = (v | (v >> 8)) & 0x0000ffffu;
+    return v;
+}
+
+// z-order key: x bit b -> key bit 2b, y bit b -> key bit 2b + 1
+__host__ __device__ __forceinline__ uint32_t morton_key(uint32_t ix, uint32_t iy) {
+    return spread_bits(ix) | (spread_bits(iy) << 1);
+}
+
+__device__ __forceinline__ int find_task(const Task *tasks, int ntasks, int64_t b) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].block0 <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void set_status(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+template <typename R> struct Cplx;
+template <> struct Cplx<double> { using T = double2; };
+template <> struct Cplx<float> { using T = float2; };
+
+template <typename T2> __host__ __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    T2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename T2> __host__ __device__ __forceinline__ T2 cfma(T2 a, T2 b, T2 c) {
+    // a * b + c
+    T2 r;
+    r.x = a.x * b.x - a.y * b.y + c.x;
+    r.y = a.x * b.y + a.y * b.x + c.y;
+    return r;
+}
+
+// Interaction-list table: for child class c, the 27 (dx, dy) offsets of the
+// sources relative to the target box and the index (0..39) of the M2L
+// operator for that offset.  Filled by the host (expansions.cu).
+struct IlEntry {
+    int8_t dx, dy;
+    int8_t op;
+    int8_t pad;
+};
+
+}  // namespace petfmm

@@ -1,0 +1,864 @@
+// engine.cu -- the evaluation context and the C ABI of include/petfmm.h.
+//
+// One evaluation (Sec. 2.2, Fig. 2) is this sequence of launches on the
+// context's stream, every one of them covering all instances of the batch:
+//   morton -> radix sort (ceil(bits / 8) passes) -> leaf starts -> gather
+//   -> P2M -> M2M (one launch per level, bottom-up) -> M2L (all levels in one
+//   launch) -> L2L (one launch per level, top-down) -> P2P work list
+//   -> P2P + L2P.
+// The host only plans (task tables, offsets) and launches; nothing is read
+// back until petfmm_sync().
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/petfmm.h"
+#include "kernels.cuh"
+
+using namespace petfmm;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+// Grows `b` to at least `bytes` (waits for the stream first: the old buffer
+// may still be in use).  Returns PETFMM_OK or PETFMM_ENOMEM / PETFMM_ECUDA.
+int ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return PETFMM_OK;
+    if (b.p) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return PETFMM_ECUDA;
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return PETFMM_ENOMEM;
+        }
+        want = bytes;
+    }
+    b.cap = want;
+    return PETFMM_OK;
+}
+
+struct TaskRange {
+    int first = 0;
+    int count = 0;
+    int64_t nblocks = 0;
+};
+
+struct Plan {
+    std::vector<InstDesc> inst;
+    std::vector<Task> tasks;
+    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l;
+    std::vector<TaskRange> m2m, l2l;  // in launch order
+    int64_t N = 0, nleaves = 0, nstart = 0, ncoef = 0, items_cap = 0;
+    int nbits = 0, pmax = 1, Lmax = 0;
+    int deg = 0, general = 0;          // mixed P2P variant (max over instances)
+};
+
+struct Problem {
+    petfmm_domain dom;
+    int L, p;
+    double sigma;
+    int64_t n;
+    const void *x, *y, *g;
+    void *u, *v;
+};
+
+}  // namespace
+
+struct petfmm_ctx {
+    petfmm_domain dom{};
+    int L = 0, p = 0;
+    double sigma = 0.0;
+    int precision = 0, dtype = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool timing = false;
+    int p2p_mode = 1;
+    int64_t spin_limit = 0;
+    uint64_t launches = 0, evaluations = 0;
+
+    DevBuf keysA, keysB, valsA, valsB, hist, scratch, start, xs, ys, gs, rec, me, le, cnt, off,
+        items, ctrl, plan_dev, busy;
+    DevBuf hx, hy, hg, hu, hv;  // device staging for petfmm_evaluate_host
+    std::map<int, OpTables> tables;
+
+    // plan upload
+    std::vector<unsigned char> last_upload;
+    void *pinned = nullptr;
+    size_t pinned_cap = 0;
+    cudaEvent_t upload_done = nullptr;
+    bool upload_pending = false;
+
+    // last evaluation (for inspection)
+    Plan plan;
+    bool sorted_in_first = true;
+    int p2p_grid = 0;
+    cudaEvent_t ev[PETFMM_STAGE_COUNT + 1] = {};
+    bool ev_recorded = false;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int check_problem(const petfmm_domain *dom, int L, int p, double sigma) {
+    if (!dom) return PETFMM_EINVAL;
+    if (!(dom->width > 0.0) || !std::isfinite(dom->width) || !std::isfinite(dom->x0) ||
+        !std::isfinite(dom->y0))
+        return PETFMM_EINVAL;
+    if (L < 1 || L > MAX_L) return PETFMM_EINVAL;
+    if (p < 1 || p > MAX_P) return PETFMM_EINVAL;
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return PETFMM_EINVAL;
+    return PETFMM_OK;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return PETFMM_OK;
+    if (e == cudaErrorMemoryAllocation) return PETFMM_ENOMEM;
+    return PETFMM_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Near-field polynomial: Chebyshev interpolation of g(q) = (1 - e^-q) / q on
+// [0, Q], converted to monomials in rho^2 (q = kappa rho^2).  The smallest
+// degree whose relative error on a fine grid stays below 3e-8 is taken.
+// ---------------------------------------------------------------------------
+double g_exact(double q) { return q == 0.0 ? 1.0 : -std::expm1(-q) / q; }
+
+bool solve_dense(std::vector<double> &A, std::vector<double> &b, int n) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return false;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) std::swap(A[c * n + k], A[piv * n + k]);
+            std::swap(b[c], b[piv]);
+        }
+        for (int r = c + 1; r < n; ++r) {
+            const double f = A[r * n + c] / A[c * n + c];
+            for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * b[k];
+        b[r] = s / A[r * n + r];
+    }
+    return true;
+}
+
+// Fits on q in [0, Q]; returns degree (0 on failure) and coefficients in rho^2.
+int fit_near_poly(double Q, double kappa, float *coef) {
+    for (int d = 4; d <= 12; ++d) {
+        const int n = d + 1;
+        std::vector<double> A(size_t(n) * n), b(n);
+        for (int j = 0; j < n; ++j) {
+            const double t = 0.5 * (1.0 - std::cos(M_PI * (j + 0.5) / n));  // in [0, 1]
+            double pw = 1.0;
+            for (int k = 0; k < n; ++k) {
+                A[size_t(j) * n + k] = pw;
+                pw *= t;
+            }
+            b[j] = g_exact(t * Q);
+        }
+        if (!solve_dense(A, b, n)) continue;
+        // coefficients in rho^2: a_k = b_k (kappa / Q)^k
+        double a[16];
+        const double r = kappa / Q;
+        double rp = 1.0;
+        for (int k = 0; k < n; ++k) {
+            a[k] = b[k] * rp;
+            rp *= r;
+        }
+        double err = 0.0;
+        const double smax = Q / kappa;
+        for (int i = 0; i <= 4000; ++i) {
+            const double s = smax * i / 4000.0;
+            double v = a[d];
+            for (int k = d - 1; k >= 0; --k) v = v * s + a[k];
+            err = std::max(err, std::fabs(v - g_exact(kappa * s)) / g_exact(kappa * s));
+        }
+        if (err < 3e-8) {
+            for (int k = 0; k <= POLY_MAX; ++k) coef[k] = k <= d ? float(a[k]) : 0.0f;
+            return d;
+        }
+    }
+    return 0;
+}
+
+// Largest q the polynomial alone may cover.
+constexpr double kPolyQMax = 2.0;
+
+void fill_p2p_constants(InstDesc &d) {
+    const double w = d.wleaf;
+    const double kappa = w * w / (2.0 * d.sigma * d.sigma);
+    d.kappa = float(kappa);
+    d.cnear = float(w / (4.0 * M_PI * d.sigma * d.sigma));
+    d.cfar = float(1.0 / (2.0 * M_PI * w));
+    d.inv2s2 = 1.0 / (2.0 * d.sigma * d.sigma);
+    d.cnear64 = 1.0 / (2.0 * M_PI);
+    d.cfar64 = 1.0 / (2.0 * M_PI * w);
+    // near pairs are at most 2 leaf widths apart per axis: rho^2 <= 8
+    const double rho2max = 8.0 * (1.0 + 1e-6);
+    const double qmax = kappa * rho2max;
+    if (qmax <= kPolyQMax) {
+        d.general = 0;
+        d.deg = fit_near_poly(qmax, kappa, d.poly);
+        d.qsplit_rho2 = float(rho2max);
+    } else {
+        d.general = 1;
+        d.deg = fit_near_poly(1.0, kappa, d.poly);
+        d.qsplit_rho2 = float(1.0 / kappa);
+    }
+}
+
+OpTables *get_tables(petfmm_ctx *c, int p, int *err) {
+    auto it = c->tables.find(p);
+    if (it != c->tables.end()) return &it->second;
+    OpTables t;
+    cudaError_t e = build_op_tables(p, &t);
+    if (e != cudaSuccess) {
+        free_op_tables(&t);
+        *err = cuda_status(e);
+        return nullptr;
+    }
+    return &(c->tables[p] = t);
+}
+
+void add_task(Plan &pl, TaskRange &r, int inst, int level, int64_t count, int64_t per_block) {
+    if (count <= 0) return;
+    if (r.count == 0) r.first = int(pl.tasks.size());
+    Task t;
+    t.inst = inst;
+    t.level = level;
+    t.count = count;
+    t.block0 = r.nblocks;
+    pl.tasks.push_back(t);
+    r.count++;
+    r.nblocks += (count + per_block - 1) / per_block;
+}
+
+int build_plan(petfmm_ctx *c, const std::vector<Problem> &probs, Plan &pl) {
+    pl = Plan();
+    const int ni = int(probs.size());
+    int inst_bits = 0;
+    while ((1 << inst_bits) < ni) ++inst_bits;
+    int Lmax = 0, pmax = 1;
+    for (const auto &pb : probs) {
+        Lmax = std::max(Lmax, pb.L);
+        pmax = std::max(pmax, pb.p);
+    }
+    pl.Lmax = Lmax;
+    pl.pmax = pmax;
+    pl.nbits = 2 * Lmax + inst_bits;
+    if (pl.nbits > 32) return PETFMM_EINVAL;
+    int64_t poff = 0, loff = 0, eoff = 0;
+    for (int i = 0; i < ni; ++i) {
+        const Problem &pb = probs[i];
+        InstDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.x0 = pb.dom.x0;
+        d.y0 = pb.dom.y0;
+        d.width = pb.dom.width;
+        d.scale = std::ldexp(1.0, pb.L) / pb.dom.width;
+        d.wleaf = pb.dom.width / std::ldexp(1.0, pb.L);
+        d.sigma = pb.sigma;
+        d.L = pb.L;
+        d.p = pb.p;
+        d.n = pb.n;
+        d.poff = poff;
+        d.loff = loff;
+        d.soff = loff + i;
+        d.eoff = eoff;
+        d.key_hi = inst_bits ? (uint32_t(i) << (2 * Lmax)) : 0u;
+        d.x = pb.x;
+        d.y = pb.y;
+        d.g = pb.g;
+        d.u = pb.u;
+        d.v = pb.v;
+        int err = PETFMM_OK;
+        OpTables *t = get_tables(c, pb.p, &err);
+        if (!t) return err;
+        if (c->precision == PETFMM_FP64) {
+            d.t_m2m = t->m2m64; d.t_l2l = t->l2l64; d.t_m2l = t->m2l64;
+        } else {
+            d.t_m2m = t->m2m32; d.t_l2l = t->l2l32; d.t_m2l = t->m2l32;
+        }
+        fill_p2p_constants(d);
+        if (c->precision == PETFMM_MIXED && d.deg == 0) return PETFMM_EINVAL;
+        pl.deg = std::max(pl.deg, d.deg);
+        pl.general |= d.general;
+        pl.inst.push_back(d);
+        const int64_t nleaf = int64_t(1) << (2 * pb.L);
+        poff += pb.n;
+        loff += nleaf;
+        eoff += lvl_off(pb.L + 1) * pb.p;
+    }
+    pl.N = poff;
+    pl.nleaves = loff;
+    pl.nstart = loff + ni;
+    pl.ncoef = eoff;
+    if (pl.N >= (int64_t(1) << 31)) return PETFMM_EINVAL;
+
+    const int tpi = c->precision == PETFMM_MIXED ? P2P_TPI_MIXED : P2P_TPI_F64;
+    int64_t items_cap = 0;
+    for (int i = 0; i < ni; ++i) {
+        const InstDesc &d = pl.inst[i];
+        const int64_t nleaf = int64_t(1) << (2 * d.L);
+        add_task(pl, pl.morton, i, d.L, d.n, 256);
+        add_task(pl, pl.start, i, d.L, nleaf + 1, 256);
+        add_task(pl, pl.particles, i, d.L, d.n, 256);
+        add_task(pl, pl.leaves_p2m, i, d.L, nleaf, P2M_WARPS);
+        add_task(pl, pl.leaves_wl, i, d.L, nleaf, 256);
+        for (int l = 2; l <= d.L; ++l)
+            add_task(pl, pl.m2l, i, l, int64_t(1) << (2 * l), M2L_WARPS);
+        items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
+    }
+    // M2M rounds: round r computes level L_i - 1 - r (>= 2) of every instance.
+    for (int r = 0; r + 3 <= Lmax; ++r) {
+        TaskRange tr;
+        for (int i = 0; i < ni; ++i) {
+            const int l = pl.inst[i].L - 1 - r;
+            if (l >= 2) add_task(pl, tr, i, l, (int64_t(1) << (2 * l)) * pl.inst[i].p, EXP_THREADS);
+        }
+        if (tr.count) pl.m2m.push_back(tr);
+    }
+    // L2L rounds: round r translates level 2 + r into level 3 + r.
+    for (int r = 0; r + 3 <= Lmax; ++r) {
+        TaskRange tr;
+        for (int i = 0; i < ni; ++i) {
+            const int l = 3 + r;
+            if (l <= pl.inst[i].L)
+                add_task(pl, tr, i, l, (int64_t(1) << (2 * l)) * pl.inst[i].p, EXP_THREADS);
+        }
+        if (tr.count) pl.l2l.push_back(tr);
+    }
+    pl.items_cap = items_cap;
+    return PETFMM_OK;
+}
+
+// Uploads InstDesc[] followed by Task[] to c->plan_dev (skipped when equal to
+// the previous upload).
+int upload_plan(petfmm_ctx *c, const Plan &pl) {
+    const size_t ib = pl.inst.size() * sizeof(InstDesc);
+    const size_t tb = pl.tasks.size() * sizeof(Task);
+    const size_t total = align_up(ib) + tb;
+    std::vector<unsigned char> blob(total, 0);
+    std::memcpy(blob.data(), pl.inst.data(), ib);
+    if (tb) std::memcpy(blob.data() + align_up(ib), pl.tasks.data(), tb);
+    if (blob == c->last_upload && c->plan_dev.p) return PETFMM_OK;
+    int rc = ensure(c->plan_dev, total, c->stream);
+    if (rc) return rc;
+    if (c->pinned_cap < total) {
+        if (c->pinned) {
+            cudaEventSynchronize(c->upload_done);
+            cudaFreeHost(c->pinned);
+            c->pinned = nullptr;
+        }
+        if (cudaMallocHost(&c->pinned, total) != cudaSuccess) {
+            cudaGetLastError();
+            c->pinned = nullptr;
+            c->pinned_cap = 0;
+            return PETFMM_ENOMEM;
+        }
+        c->pinned_cap = total;
+        c->upload_pending = false;
+    }
+    if (c->upload_pending) cudaEventSynchronize(c->upload_done);
+    std::memcpy(c->pinned, blob.data(), total);
+    cudaError_t e = cudaMemcpyAsync(c->plan_dev.p, c->pinned, total, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaEventRecord(c->upload_done, c->stream);
+    c->upload_pending = true;
+    c->last_upload.swap(blob);
+    return PETFMM_OK;
+}
+
+#define PF_TRY(expr)                         \
+    do {                                     \
+        int rc_ = (expr);                    \
+        if (rc_ != PETFMM_OK) return rc_;    \
+    } while (0)
+#define PF_CUDA(expr) PF_TRY(cuda_status(expr))
+
+void stage_mark(petfmm_ctx *c, int stage) {
+    if (c->timing) cudaEventRecord(c->ev[stage], c->stream);
+}
+
+int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
+    Plan &pl = c->plan;
+    PF_TRY(build_plan(c, probs, pl));
+    cudaStream_t st = c->stream;
+    const bool mixed = c->precision == PETFMM_MIXED;
+    const int64_t N = pl.N;
+    // buffers
+    PF_TRY(ensure(c->ctrl, CTRL_WORDS * sizeof(uint32_t), st));
+    if (c->evaluations == 0 && c->launches == 0) PF_CUDA(cudaMemsetAsync(c->ctrl.p, 0, CTRL_WORDS * 4, st));
+    PF_TRY(upload_plan(c, pl));
+    if (N == 0) {
+        c->evaluations++;
+        c->ev_recorded = false;
+        return PETFMM_OK;
+    }
+    PF_TRY(ensure(c->keysA, N * 4, st));
+    PF_TRY(ensure(c->keysB, N * 4, st));
+    PF_TRY(ensure(c->valsA, N * 4, st));
+    PF_TRY(ensure(c->valsB, N * 4, st));
+    const int64_t rb = radix_blocks(N);
+    PF_TRY(ensure(c->hist, size_t(256) * rb * 4, st));
+    const int64_t scan_n = std::max<int64_t>(256 * rb, pl.nleaves);
+    PF_TRY(ensure(c->scratch, size_t(scan_scratch_words(scan_n)) * 4, st));
+    PF_TRY(ensure(c->start, size_t(pl.nstart) * 4, st));
+    if (mixed) {
+        PF_TRY(ensure(c->rec, size_t(N) * sizeof(float4), st));
+        PF_TRY(ensure(c->me, size_t(pl.ncoef) * sizeof(float2), st));
+        PF_TRY(ensure(c->le, size_t(pl.ncoef) * sizeof(float2), st));
+    } else {
+        PF_TRY(ensure(c->xs, size_t(N) * 8, st));
+        PF_TRY(ensure(c->ys, size_t(N) * 8, st));
+        PF_TRY(ensure(c->gs, size_t(N) * 8, st));
+        PF_TRY(ensure(c->me, size_t(pl.ncoef) * sizeof(double2), st));
+        PF_TRY(ensure(c->le, size_t(pl.ncoef) * sizeof(double2), st));
+    }
+    PF_TRY(ensure(c->cnt, size_t(pl.nleaves) * 4, st));
+    PF_TRY(ensure(c->off, size_t(pl.nleaves) * 4, st));
+    PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
+    const int grid = p2p_grid(mixed, pl.deg, pl.general);
+    if (grid <= 0) return PETFMM_EINVAL;
+    c->p2p_grid = grid;
+    unsigned long long *busy = nullptr;
+    if (c->timing) {
+        PF_TRY(ensure(c->busy, size_t(grid) * 8 * 2 * sizeof(unsigned long long), st));
+        busy = static_cast<unsigned long long *>(c->busy.p);
+    }
+
+    const InstDesc *dinst = static_cast<const InstDesc *>(c->plan_dev.p);
+    const Task *dtask = reinterpret_cast<const Task *>(static_cast<unsigned char *>(c->plan_dev.p) +
+                                                       align_up(pl.inst.size() * sizeof(InstDesc)));
+    uint32_t *ctrl = static_cast<uint32_t *>(c->ctrl.p);
+    uint32_t *kA = static_cast<uint32_t *>(c->keysA.p), *kB = static_cast<uint32_t *>(c->keysB.p);
+    uint32_t *vA = static_cast<uint32_t *>(c->valsA.p), *vB = static_cast<uint32_t *>(c->valsB.p);
+    uint32_t *start = static_cast<uint32_t *>(c->start.p);
+    uint32_t *scratch = static_cast<uint32_t *>(c->scratch.p);
+    const int f32 = c->dtype == PETFMM_F32;
+    uint64_t *lc = &c->launches;
+
+    // per-evaluation control words (the status word survives until sync)
+    PF_CUDA(cudaMemsetAsync(ctrl + 1, 0, (CTRL_WORDS - 1) * 4, st));
+
+    stage_mark(c, PETFMM_STAGE_MORTON);
+    PF_CUDA(launch_morton(dtask + pl.morton.first, pl.morton.count, pl.morton.nblocks, dinst, f32, kA,
+                          reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
+    stage_mark(c, PETFMM_STAGE_SORT);
+    bool in_first = true;
+    PF_CUDA(radix_sort(kA, vA, kB, vB, N, pl.nbits, static_cast<uint32_t *>(c->hist.p), scratch,
+                       &in_first, st, lc));
+    c->sorted_in_first = in_first;
+    const uint32_t *skeys = in_first ? kA : kB;
+    const uint32_t *perm = in_first ? vA : vB;
+    PF_CUDA(launch_leaf_start(dtask + pl.start.first, pl.start.count, pl.start.nblocks, dinst, skeys,
+                              start, st, lc));
+    stage_mark(c, PETFMM_STAGE_GATHER);
+    if (mixed)
+        PF_CUDA(launch_gather_mixed(dtask + pl.particles.first, pl.particles.count,
+                                    pl.particles.nblocks, dinst, f32, perm, skeys,
+                                    static_cast<float4 *>(c->rec.p), st, lc));
+    else
+        PF_CUDA(launch_gather_f64(dtask + pl.particles.first, pl.particles.count,
+                                  pl.particles.nblocks, dinst, f32, perm,
+                                  static_cast<double *>(c->xs.p), static_cast<double *>(c->ys.p),
+                                  static_cast<double *>(c->gs.p), st, lc));
+    stage_mark(c, PETFMM_STAGE_P2M);
+    if (mixed)
+        PF_CUDA(launch_p2m<float>(dtask + pl.leaves_p2m.first, pl.leaves_p2m.count,
+                                  pl.leaves_p2m.nblocks, dinst, pl.pmax, start, nullptr, nullptr,
+                                  nullptr, static_cast<const float4 *>(c->rec.p),
+                                  static_cast<float2 *>(c->me.p), st, lc));
+    else
+        PF_CUDA(launch_p2m<double>(dtask + pl.leaves_p2m.first, pl.leaves_p2m.count,
+                                   pl.leaves_p2m.nblocks, dinst, pl.pmax, start,
+                                   static_cast<const double *>(c->xs.p),
+                                   static_cast<const double *>(c->ys.p),
+                                   static_cast<const double *>(c->gs.p), nullptr,
+                                   static_cast<double2 *>(c->me.p), st, lc));
+    stage_mark(c, PETFMM_STAGE_M2M);
+    for (const TaskRange &tr : pl.m2m) {
+        if (mixed)
+            PF_CUDA(launch_m2m<float>(dtask + tr.first, tr.count, tr.nblocks, dinst,
+                                      static_cast<float2 *>(c->me.p), st, lc));
+        else
+            PF_CUDA(launch_m2m<double>(dtask + tr.first, tr.count, tr.nblocks, dinst,
+                                       static_cast<double2 *>(c->me.p), st, lc));
+    }
+    stage_mark(c, PETFMM_STAGE_M2L);
+    if (pl.m2l.count) {
+        if (mixed)
+            PF_CUDA(launch_m2l<float>(dtask + pl.m2l.first, pl.m2l.count, pl.m2l.nblocks, dinst,
+                                      static_cast<const float2 *>(c->me.p),
+                                      static_cast<float2 *>(c->le.p), st, lc));
+        else
+            PF_CUDA(launch_m2l<double>(dtask + pl.m2l.first, pl.m2l.count, pl.m2l.nblocks, dinst,
+                                       static_cast<const double2 *>(c->me.p),
+                                       static_cast<double2 *>(c->le.p), st, lc));
+    }
+    stage_mark(c, PETFMM_STAGE_L2L);
+    for (const TaskRange &tr : pl.l2l) {
+        if (mixed)
+            PF_CUDA(launch_l2l<float>(dtask + tr.first, tr.count, tr.nblocks, dinst,
+                                      static_cast<float2 *>(c->le.p), st, lc));
+        else
+            PF_CUDA(launch_l2l<double>(dtask + tr.first, tr.count, tr.nblocks, dinst,
+                                       static_cast<double2 *>(c->le.p), st, lc));
+    }
+    stage_mark(c, PETFMM_STAGE_WORKLIST);
+    const int tpi = mixed ? P2P_TPI_MIXED : P2P_TPI_F64;
+    PF_CUDA(launch_p2p_worklist(dtask + pl.leaves_wl.first, pl.leaves_wl.count, pl.leaves_wl.nblocks,
+                                dinst, start, pl.nleaves, tpi, static_cast<uint32_t *>(c->cnt.p),
+                                static_cast<uint32_t *>(c->off.p), scratch,
+                                static_cast<uint4 *>(c->items.p), ctrl, st, lc));
+    stage_mark(c, PETFMM_STAGE_P2P);
+    if (mixed)
+        PF_CUDA(launch_p2p_mixed(grid, pl.deg, pl.general, static_cast<const uint4 *>(c->items.p),
+                                 ctrl, dinst, start, static_cast<const float4 *>(c->rec.p),
+                                 static_cast<const float2 *>(c->le.p), f32, busy, st, lc));
+    else
+        PF_CUDA(launch_p2p_f64(grid, static_cast<const uint4 *>(c->items.p), ctrl, dinst, start,
+                               static_cast<const double *>(c->xs.p),
+                               static_cast<const double *>(c->ys.p),
+                               static_cast<const double *>(c->gs.p), perm,
+                               static_cast<const double2 *>(c->le.p), f32, busy, st, lc));
+    stage_mark(c, PETFMM_STAGE_COUNT);
+    c->ev_recorded = c->timing;
+    c->evaluations++;
+    return PETFMM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int petfmm_version(void) { return 1; }
+
+const char *petfmm_strerror(int code) {
+    switch (code) {
+        case PETFMM_OK: return "ok";
+        case PETFMM_EINVAL: return "invalid argument";
+        case PETFMM_ENOMEM: return "out of memory";
+        case PETFMM_EDOMAIN: return "particle outside the domain";
+        case PETFMM_ECUDA: return "CUDA error";
+        case PETFMM_ETIMEOUT: return "device wait timed out";
+        case PETFMM_EBUSY: return "server busy";
+        case PETFMM_ENOTREADY: return "not ready";
+        default: return "unknown status";
+    }
+}
+
+int petfmm_create(const petfmm_domain *dom, int levels, int order, double sigma, int precision,
+                  int dtype, void *cuda_stream, petfmm_ctx **out) {
+    if (!out) return PETFMM_EINVAL;
+    *out = nullptr;
+    int rc = check_problem(dom, levels, order, sigma);
+    if (rc) return rc;
+    if (precision != PETFMM_FP64 && precision != PETFMM_MIXED) return PETFMM_EINVAL;
+    if (dtype != PETFMM_F64 && dtype != PETFMM_F32) return PETFMM_EINVAL;
+    petfmm_ctx *c = new (std::nothrow) petfmm_ctx();
+    if (!c) return PETFMM_ENOMEM;
+    c->dom = *dom;
+    c->L = levels;
+    c->p = order;
+    c->sigma = sigma;
+    c->precision = precision;
+    c->dtype = dtype;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return PETFMM_ECUDA;
+    }
+    if (cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return PETFMM_ECUDA;
+    }
+    for (auto &e : c->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            petfmm_destroy(c);
+            return PETFMM_ECUDA;
+        }
+    }
+    int err = PETFMM_OK;
+    if (!get_tables(c, order, &err)) {
+        petfmm_destroy(c);
+        return err;
+    }
+    *out = c;
+    return PETFMM_OK;
+}
+
+int petfmm_destroy(petfmm_ctx *c) {
+    if (!c) return PETFMM_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    DevBuf *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
+                      &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
+                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->hx, &c->hy,
+                      &c->hg, &c->hu, &c->hv};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    for (auto &kv : c->tables) free_op_tables(&kv.second);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->upload_done) cudaEventDestroy(c->upload_done);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete c;
+    return PETFMM_OK;
+}
+
+int petfmm_evaluate(petfmm_ctx *c, int64_t n, const void *x, const void *y, const void *gamma,
+                    void *u, void *v) {
+    if (!c || n < 0) return PETFMM_EINVAL;
+    if (n > 0 && (!x || !y || !gamma || !u || !v)) return PETFMM_EINVAL;
+    std::vector<Problem> probs(1);
+    probs[0] = Problem{c->dom, c->L, c->p, c->sigma, n, x, y, gamma, u, v};
+    return run(c, probs);
+}
+
+int petfmm_evaluate_host(petfmm_ctx *c, int64_t n, const void *x, const void *y, const void *gamma,
+                         void *u, void *v) {
+    if (!c || n < 0) return PETFMM_EINVAL;
+    if (n > 0 && (!x || !y || !gamma || !u || !v)) return PETFMM_EINVAL;
+    const size_t es = c->dtype == PETFMM_F32 ? 4 : 8;
+    const size_t bytes = size_t(n) * es;
+    cudaStream_t st = c->stream;
+    PF_TRY(ensure(c->hx, bytes, st));
+    PF_TRY(ensure(c->hy, bytes, st));
+    PF_TRY(ensure(c->hg, bytes, st));
+    PF_TRY(ensure(c->hu, bytes, st));
+    PF_TRY(ensure(c->hv, bytes, st));
+    if (n > 0) {
+        PF_CUDA(cudaMemcpyAsync(c->hx.p, x, bytes, cudaMemcpyHostToDevice, st));
+        PF_CUDA(cudaMemcpyAsync(c->hy.p, y, bytes, cudaMemcpyHostToDevice, st));
+        PF_CUDA(cudaMemcpyAsync(c->hg.p, gamma, bytes, cudaMemcpyHostToDevice, st));
+    }
+    int rc = petfmm_evaluate(c, n, c->hx.p, c->hy.p, c->hg.p, c->hu.p, c->hv.p);
+    if (rc) return rc;
+    if (n > 0) {
+        PF_CUDA(cudaMemcpyAsync(u, c->hu.p, bytes, cudaMemcpyDeviceToHost, st));
+        PF_CUDA(cudaMemcpyAsync(v, c->hv.p, bytes, cudaMemcpyDeviceToHost, st));
+    }
+    return petfmm_sync(c);
+}
+
+int petfmm_sync(petfmm_ctx *c) {
+    if (!c) return PETFMM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return PETFMM_ECUDA;
+    if (!c->ctrl.p) return PETFMM_OK;
+    int status = 0;
+    e = cudaMemcpy(&status, c->ctrl.p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return PETFMM_ECUDA;
+    if (status) {
+        e = cudaMemset(c->ctrl.p, 0, sizeof(int));
+        if (e != cudaSuccess) return PETFMM_ECUDA;
+    }
+    return status;
+}
+
+int petfmm_evaluate_batch(petfmm_ctx *c, int n_inst, const petfmm_instance *inst) {
+    if (!c || n_inst < 0 || (n_inst > 0 && !inst)) return PETFMM_EINVAL;
+    std::vector<Problem> probs(static_cast<size_t>(n_inst));
+    for (int i = 0; i < n_inst; ++i) {
+        const petfmm_instance &s = inst[i];
+        int L = s.levels;
+        if (L <= 0) {
+            L = petfmm_choose_levels(s.n, s.order, s.sigma, &s.domain);
+            if (L < 0) return L;
+        }
+        int rc = check_problem(&s.domain, L, s.order, s.sigma);
+        if (rc) return rc;
+        if (s.n < 0 || (s.n > 0 && (!s.x || !s.y || !s.gamma || !s.u || !s.v))) return PETFMM_EINVAL;
+        probs[i] = Problem{s.domain, L, s.order, s.sigma, s.n, s.x, s.y, s.gamma, s.u, s.v};
+    }
+    return run(c, probs);
+}
+
+int petfmm_choose_levels(int64_t n, int order, double sigma, const petfmm_domain *dom) {
+    if (n < 0 || order < 1 || order > MAX_P || !(sigma > 0.0) || !dom || !(dom->width > 0.0))
+        return PETFMM_EINVAL;
+    // Kernel-substitution guard: the far field starts one leaf away, so the
+    // leaf width must keep exp(-r^2 / 2 sigma^2) <= 1e-8.
+    const double rmin = sigma * std::sqrt(2.0 * std::log(1e8));
+    const double p = order, p2 = double(order) * order;
+    // Relative GPU costs of the units of Eq. 13 / 14 (one P2P pair, one
+    // complex multiply-add of an expansion translation, one P2M/L2P term).
+    const double c_pair = 1.0, c_mac = 0.35, c_term = 1.0;
+    int best = 1;
+    double best_cost = -1.0;
+    for (int L = 1; L <= 12; ++L) {
+        if (dom->width / std::ldexp(1.0, L) < rmin) break;
+        const double nleaf = std::ldexp(1.0, 2 * L);
+        const double s = double(n) / nleaf;
+        double cost = nleaf * (c_term * 2.0 * s * p + c_mac * p2 * 27.0 + c_pair * 9.0 * s * s);
+        for (int l = 2; l < L; ++l) cost += std::ldexp(1.0, 2 * l) * c_mac * p2 * (2.0 * 4.0 + 27.0);
+        if (best_cost < 0.0 || cost < best_cost) {
+            best_cost = cost;
+            best = L;
+        }
+    }
+    return best;
+}
+
+int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
+    if (!c) return PETFMM_EINVAL;
+    switch (option) {
+        case PETFMM_OPT_TIMING: c->timing = value != 0; return PETFMM_OK;
+        case PETFMM_OPT_SPIN_LIMIT: if (value < 0) return PETFMM_EINVAL; c->spin_limit = value; return PETFMM_OK;
+        case PETFMM_OPT_P2P_MODE: if (value < 0 || value > 1) return PETFMM_EINVAL; c->p2p_mode = int(value); return PETFMM_OK;
+        default: return PETFMM_EINVAL;
+    }
+}
+
+int petfmm_stage_times(petfmm_ctx *c, float *ms, int cap) {
+    if (!c || !ms || cap < 0) return PETFMM_EINVAL;
+    if (!c->ev_recorded) return PETFMM_ENOTREADY;
+    const int n = std::min(cap, int(PETFMM_STAGE_COUNT));
+    for (int s = 0; s < n; ++s) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->ev[s], c->ev[s + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return PETFMM_ECUDA;
+        }
+        ms[s] = t;
+    }
+    return n;
+}
+
+int petfmm_get_stats(petfmm_ctx *c, petfmm_stats *out) {
+    if (!c || !out) return PETFMM_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->kernel_launches = c->launches;
+    out->evaluations = c->evaluations;
+    for (const InstDesc &d : c->plan.inst) out->m2l_pairs += m2l_pair_count(d.L);
+    if (c->ctrl.p && c->evaluations) {
+        uint32_t w[CTRL_WORDS];
+        if (cudaMemcpy(w, c->ctrl.p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return PETFMM_ECUDA;
+        out->p2p_items = w[CTRL_NITEMS];
+        unsigned long long pairs;
+        std::memcpy(&pairs, w + CTRL_PAIRS_LO, sizeof(pairs));
+        out->p2p_pairs = int64_t(pairs);
+    }
+    if (c->timing && c->busy.p && c->p2p_grid > 0 && c->ev_recorded) {
+        const int warps = 8;
+        std::vector<unsigned long long> b(size_t(c->p2p_grid) * warps * 2);
+        if (cudaMemcpy(b.data(), c->busy.p, b.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return PETFMM_ECUDA;
+        double lo = 0, hi = 0;
+        bool first = true;
+        for (int blk = 0; blk < c->p2p_grid; ++blk) {
+            unsigned long long s = ~0ull, e = 0;
+            for (int w = 0; w < warps; ++w) {
+                s = std::min(s, b[(size_t(blk) * warps + w) * 2]);
+                e = std::max(e, b[(size_t(blk) * warps + w) * 2 + 1]);
+            }
+            const double span = double(e - s);
+            if (first) { lo = hi = span; first = false; }
+            lo = std::min(lo, span);
+            hi = std::max(hi, span);
+        }
+        out->p2p_load_balance = hi > 0 ? float(lo / hi) : 1.0f;
+    }
+    return PETFMM_OK;
+}
+
+int petfmm_debug_tree(petfmm_ctx *c, uint32_t *keys, uint32_t *perm, uint32_t *start) {
+    if (!c) return PETFMM_EINVAL;
+    if (c->plan.inst.size() != 1) return PETFMM_EINVAL;
+    const int64_t n = c->plan.N;
+    const InstDesc &d = c->plan.inst[0];
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PETFMM_ECUDA;
+    std::vector<uint32_t> sk(static_cast<size_t>(n)), pm(static_cast<size_t>(n));
+    if (n > 0) {
+        const void *skp = c->sorted_in_first ? c->keysA.p : c->keysB.p;
+        const void *pmp = c->sorted_in_first ? c->valsA.p : c->valsB.p;
+        if (cudaMemcpy(sk.data(), skp, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PETFMM_ECUDA;
+        if (cudaMemcpy(pm.data(), pmp, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PETFMM_ECUDA;
+    }
+    if (perm) std::memcpy(perm, pm.data(), size_t(n) * 4);
+    if (keys)
+        for (int64_t r = 0; r < n; ++r) keys[pm[r]] = sk[r];
+    if (start) {
+        const size_t ns = (size_t(1) << (2 * d.L)) + 1;
+        if (n > 0) {
+            if (cudaMemcpy(start, c->start.p, ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PETFMM_ECUDA;
+        } else {
+            std::memset(start, 0, ns * 4);
+        }
+    }
+    return PETFMM_OK;
+}
+
+int petfmm_debug_expansions(petfmm_ctx *c, int level, int which, double *out) {
+    if (!c || !out || (which != 0 && which != 1)) return PETFMM_EINVAL;
+    if (c->plan.inst.size() != 1 || c->plan.N == 0) return PETFMM_EINVAL;
+    const InstDesc &d = c->plan.inst[0];
+    if (level < 2 || level > d.L) return PETFMM_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PETFMM_ECUDA;
+    const int p = d.p;
+    const int64_t nb = int64_t(1) << (2 * level);
+    const DevBuf &src = which == 0 ? c->me : c->le;
+    const bool mixed = c->precision == PETFMM_MIXED;
+    const size_t es = mixed ? sizeof(float2) : sizeof(double2);
+    std::vector<unsigned char> h(size_t(nb) * p * es);
+    const unsigned char *base = static_cast<const unsigned char *>(src.p) + (d.eoff + lvl_off(level) * p) * es;
+    if (cudaMemcpy(h.data(), base, h.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return PETFMM_ECUDA;
+    for (int64_t m = 0; m < nb; ++m) {
+        const uint32_t ix = compact_bits(uint32_t(m)), iy = compact_bits(uint32_t(m) >> 1);
+        const int64_t b = box_index(level, ix, iy);
+        for (int k = 0; k < p; ++k) {
+            double re, im;
+            if (mixed) {
+                const float2 *f = reinterpret_cast<const float2 *>(h.data()) + b * p + k;
+                re = f->x; im = f->y;
+            } else {
+                const double2 *f = reinterpret_cast<const double2 *>(h.data()) + b * p + k;
+                re = f->x; im = f->y;
+            }
+            out[(m * p + k) * 2] = re;
+            out[(m * p + k) * 2 + 1] = im;
+        }
+    }
+    return PETFMM_OK;
+}
+
+int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out) {
+    if (!out) return PETFMM_EINVAL;
+    const int n = host_interaction_list(level, ix, iy, out);
+    return n < 0 ? PETFMM_EINVAL : n;
+}
+
+}  // extern "C"

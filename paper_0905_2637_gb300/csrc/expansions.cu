@@ -1,0 +1,466 @@
+// expansions.cu -- the upward and downward sweeps of Sec. 2.2 (Fig. 2):
+// P2M, M2M, M2L over the interaction list, L2L.  SIMT kernels, templated on
+// the real type (double for the FP64 path, float for the mixed path's
+// non-tensor stages).
+//
+// Series (Cauchy kernel; the paper leaves the mathematics to Greengard-
+// Rokhlin, Sec. 2.2).  With z = x + i y, the far field is
+// w(z) = sum_j gamma_j / (z - z_j) and (u, v) = (Im w, Re w) / 2pi.  Rescaled
+// coefficients, r = width of the box that owns the expansion:
+//   P2M  a~_k = sum_j gamma_j zeta_j^k,       zeta_j = (z_j - z_c) / r
+//   M2M  a~'_l = 2^-l sum_{k<=l} C(l,k) e^(l-k) a~_k,  e = (child - parent
+//        centre) / r_child in {+-1/2 +- i/2}
+//   M2L  c^_m = sum_k (-1)^(k+1) C(k+m,k) delta^-(k+m+1) a~_k,  delta = (source
+//        - target centre) / r, one of 40 fixed offsets
+//   L2L  c^'_n = sum_{m>=n} 2^-(m+1) C(m,n) e^(m-n) c^_m
+//   L2P  w(z) = r^-1 sum_m c^_m zeta^m
+// Costs (Sec. 5.2): P2M O(N_i p) per leaf, M2M and L2L O(p^2) per child,
+// M2L O(p^2 n_IL) per box with n_IL <= 27.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace petfmm {
+
+#define PF_LAUNCHED(n) do { if (launches) *launches += (n); } while (0)
+
+// ----------------------------------------------------------------------------
+// Interaction-list table.  For a target of child class c = (cx, cy) the
+// sources are the children of the parent's 3x3 neighbourhood that are not
+// within one box of the target: per axis dx in [-2, 3] if cx = 0 and [-3, 2]
+// if cx = 1 (same for y), minus the 3x3 block around the target -- 27
+// offsets.  Each offset maps to one of the 40 vectors of [-3, 3]^2 \ [-1, 1]^2.
+// ----------------------------------------------------------------------------
+__constant__ IlEntry c_il[4][27];
+
+static int offset_op_index(int dx, int dy) {
+    int idx = 0;
+    for (int y = -3; y <= 3; ++y)
+        for (int x = -3; x <= 3; ++x) {
+            if (x >= -1 && x <= 1 && y >= -1 && y <= 1) continue;
+            if (x == dx && y == dy) return idx;
+            ++idx;
+        }
+    return -1;
+}
+
+static void il_offsets(int c, IlEntry *out) {
+    const int cx = c & 1, cy = c >> 1;
+    const int x_lo = cx ? -3 : -2, y_lo = cy ? -3 : -2;
+    int n = 0;
+    for (int dy = y_lo; dy <= y_lo + 5; ++dy)
+        for (int dx = x_lo; dx <= x_lo + 5; ++dx) {
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+            out[n].dx = int8_t(dx);
+            out[n].dy = int8_t(dy);
+            out[n].op = int8_t(offset_op_index(dx, dy));
+            out[n].pad = 0;
+            ++n;
+        }
+}
+
+static bool g_il_uploaded = false;
+
+static cudaError_t upload_il() {
+    if (g_il_uploaded) return cudaSuccess;
+    IlEntry h[4][27];
+    for (int c = 0; c < 4; ++c) il_offsets(c, h[c]);
+    cudaError_t e = cudaMemcpyToSymbol(c_il, h, sizeof(h));
+    if (e == cudaSuccess) g_il_uploaded = true;
+    return e;
+}
+
+int host_interaction_list(int level, int ix, int iy, int32_t *out) {
+    if (level < 0 || level > MAX_L) return -1;
+    const int nside = 1 << level;
+    if (ix < 0 || iy < 0 || ix >= nside || iy >= nside) return -1;
+    if (level < 2) return 0;
+    IlEntry e[27];
+    il_offsets((ix & 1) | ((iy & 1) << 1), e);
+    int n = 0;
+    for (int i = 0; i < 27; ++i) {
+        const int sx = ix + e[i].dx, sy = iy + e[i].dy;
+        if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
+        out[2 * n] = sx;
+        out[2 * n + 1] = sy;
+        ++n;
+    }
+    return n;
+}
+
+int64_t m2l_pair_count(int L) {
+    int64_t tot = 0;
+    for (int l = 2; l <= L; ++l) {
+        const int64_t n = int64_t(1) << l;
+        tot += (6 * n - 8) * (6 * n - 8) - (3 * n - 2) * (3 * n - 2);
+    }
+    return tot;
+}
+
+// ----------------------------------------------------------------------------
+// Operator tables, built in FP64 on the host.
+// ----------------------------------------------------------------------------
+struct HC { double re, im; };
+static HC hmul(HC a, HC b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+static std::vector<double> binomials(int nmax) {
+    // Pascal's triangle, nmax + 1 rows
+    std::vector<double> c(size_t(nmax + 1) * (nmax + 1), 0.0);
+    for (int n = 0; n <= nmax; ++n) {
+        c[size_t(n) * (nmax + 1)] = 1.0;
+        for (int k = 1; k <= n; ++k)
+            c[size_t(n) * (nmax + 1) + k] =
+                c[size_t(n - 1) * (nmax + 1) + k - 1] + (k <= n - 1 ? c[size_t(n - 1) * (nmax + 1) + k] : 0.0);
+    }
+    return c;
+}
+
+void host_m2l_table(int p, double *out) {
+    const int nb = 2 * p;
+    std::vector<double> C = binomials(nb);
+    auto binom = [&](int n, int k) { return C[size_t(n) * (nb + 1) + k]; };
+    int op = 0;
+    for (int y = -3; y <= 3; ++y)
+        for (int x = -3; x <= 3; ++x) {
+            if (x >= -1 && x <= 1 && y >= -1 && y <= 1) continue;
+            // powers of 1/delta
+            const double den = double(x) * x + double(y) * y;
+            const HC inv = {double(x) / den, -double(y) / den};
+            std::vector<HC> ip(size_t(2 * p + 1));
+            ip[0] = {1.0, 0.0};
+            for (int i = 1; i <= 2 * p; ++i) ip[i] = hmul(ip[i - 1], inv);
+            for (int k = 0; k < p; ++k)
+                for (int m = 0; m < p; ++m) {
+                    const double s = ((k & 1) ? 1.0 : -1.0) * binom(k + m, k);
+                    const HC t = ip[k + m + 1];
+                    double *o = out + ((size_t(op) * p + k) * p + m) * 2;
+                    o[0] = s * t.re;
+                    o[1] = s * t.im;
+                }
+            ++op;
+        }
+}
+
+static void host_m2m_table(int p, double *out /* [c][l][k] */) {
+    std::vector<double> C = binomials(p);
+    for (int c = 0; c < 4; ++c) {
+        const HC e = {(c & 1) - 0.5, (c >> 1) - 0.5};
+        std::vector<HC> ep(size_t(p + 1));
+        ep[0] = {1.0, 0.0};
+        for (int i = 1; i <= p; ++i) ep[i] = hmul(ep[i - 1], e);
+        for (int l = 0; l < p; ++l)
+            for (int k = 0; k < p; ++k) {
+                double *o = out + ((size_t(c) * p + l) * p + k) * 2;
+                if (k > l) { o[0] = o[1] = 0.0; continue; }
+                const double s = std::ldexp(C[size_t(l) * (p + 1) + k], -l);
+                o[0] = s * ep[l - k].re;
+                o[1] = s * ep[l - k].im;
+            }
+    }
+}
+
+static void host_l2l_table(int p, double *out /* [c][n][m] */) {
+    std::vector<double> C = binomials(p);
+    for (int c = 0; c < 4; ++c) {
+        const HC e = {(c & 1) - 0.5, (c >> 1) - 0.5};
+        std::vector<HC> ep(size_t(p + 1));
+        ep[0] = {1.0, 0.0};
+        for (int i = 1; i <= p; ++i) ep[i] = hmul(ep[i - 1], e);
+        for (int n = 0; n < p; ++n)
+            for (int m = 0; m < p; ++m) {
+                double *o = out + ((size_t(c) * p + n) * p + m) * 2;
+                if (m < n) { o[0] = o[1] = 0.0; continue; }
+                const double s = std::ldexp(C[size_t(m) * (p + 1) + n], -(m + 1));
+                o[0] = s * ep[m - n].re;
+                o[1] = s * ep[m - n].im;
+            }
+    }
+}
+
+cudaError_t build_op_tables(int p, OpTables *t) {
+    cudaError_t e = upload_il();
+    if (e != cudaSuccess) return e;
+    t->p = p;
+    const size_t n_m2m = size_t(4) * p * p, n_m2l = size_t(40) * p * p;
+    std::vector<double> m2m(2 * n_m2m), l2l(2 * n_m2m), m2l(2 * n_m2l);
+    host_m2m_table(p, m2m.data());
+    host_l2l_table(p, l2l.data());
+    host_m2l_table(p, m2l.data());
+    std::vector<float> m2m32(m2m.begin(), m2m.end()), l2l32(l2l.begin(), l2l.end()),
+        m2l32(m2l.begin(), m2l.end());
+    auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+        cudaError_t r = cudaMalloc(dst, bytes);
+        if (r != cudaSuccess) return r;
+        return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    if ((e = up((void **)&t->m2m64, m2m.data(), m2m.size() * 8)) != cudaSuccess) return e;
+    if ((e = up((void **)&t->l2l64, l2l.data(), l2l.size() * 8)) != cudaSuccess) return e;
+    if ((e = up((void **)&t->m2l64, m2l.data(), m2l.size() * 8)) != cudaSuccess) return e;
+    if ((e = up((void **)&t->m2m32, m2m32.data(), m2m32.size() * 4)) != cudaSuccess) return e;
+    if ((e = up((void **)&t->l2l32, l2l32.data(), l2l32.size() * 4)) != cudaSuccess) return e;
+    if ((e = up((void **)&t->m2l32, m2l32.data(), m2l32.size() * 4)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+void free_op_tables(OpTables *t) {
+    cudaFree(t->m2m64); cudaFree(t->l2l64); cudaFree(t->m2l64);
+    cudaFree(t->m2m32); cudaFree(t->l2l32); cudaFree(t->m2l32);
+    *t = OpTables();
+}
+
+// ----------------------------------------------------------------------------
+// P2M: one warp per leaf.  Lanes take 32 particles at a time, write the
+// gamma * zeta^k powers to shared memory, and lane k sums column k in a fixed
+// order (deterministic).
+// ----------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ typename Cplx<R>::T mk2(R a, R b) {
+    typename Cplx<R>::T r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m(
+    const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts, int pmax,
+    const uint32_t *__restrict__ start, const double *__restrict__ xs,
+    const double *__restrict__ ys, const double *__restrict__ gs, const float4 *__restrict__ rec,
+    typename Cplx<R>::T *__restrict__ me) {
+    using C2 = typename Cplx<R>::T;
+    extern __shared__ unsigned char smem_raw[];
+    C2 *buf = reinterpret_cast<C2 *>(smem_raw) + size_t(threadIdx.x >> 5) * 32 * pmax;
+    const int lane = threadIdx.x & 31;
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t m = (int64_t(blockIdx.x) - t.block0) * P2M_WARPS + (threadIdx.x >> 5);
+    if (m >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int p = d.p, L = d.L;
+    const uint32_t ix = compact_bits(uint32_t(m)), iy = compact_bits(uint32_t(m) >> 1);
+    const uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+    const double cx = d.x0 + (double(ix) + 0.5) * d.wleaf;
+    const double cy = d.y0 + (double(iy) + 0.5) * d.wleaf;
+    C2 acc0 = mk2<R>(R(0), R(0)), acc1 = mk2<R>(R(0), R(0));
+    for (uint32_t c0 = s0; c0 < s1; c0 += 32) {
+        const uint32_t j = c0 + lane;
+        C2 z, w;
+        if (j < s1) {
+            if (rec) {
+                const float4 r = rec[j];
+                z = mk2<R>(R(r.x), R(r.y));
+                w = mk2<R>(R(r.z), R(0));
+            } else {
+                z = mk2<R>(R((xs[j] - cx) * d.scale), R((ys[j] - cy) * d.scale));
+                w = mk2<R>(R(gs[j]), R(0));
+            }
+        } else {
+            z = mk2<R>(R(0), R(0));
+            w = mk2<R>(R(0), R(0));
+        }
+        for (int k = 0; k < p; ++k) {
+            buf[lane * pmax + k] = w;
+            w = cmul(w, z);
+        }
+        __syncwarp();
+        if (lane < p) {
+            for (int q = 0; q < 32; ++q) {
+                const C2 b = buf[q * pmax + lane];
+                acc0.x += b.x;
+                acc0.y += b.y;
+            }
+        }
+        if (lane + 32 < p) {
+            for (int q = 0; q < 32; ++q) {
+                const C2 b = buf[q * pmax + lane + 32];
+                acc1.x += b.x;
+                acc1.y += b.y;
+            }
+        }
+        __syncwarp();
+    }
+    C2 *dst = me + d.eoff + (lvl_off(L) + box_index(L, ix, iy)) * p;
+    if (lane < p) dst[lane] = acc0;
+    if (lane + 32 < p) dst[lane + 32] = acc1;
+}
+
+template <typename R>
+cudaError_t launch_p2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       int pmax, const uint32_t *start, const double *xs, const double *ys,
+                       const double *gs, const float4 *rec, typename Cplx<R>::T *me,
+                       cudaStream_t st, uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    const size_t smem = size_t(P2M_WARPS) * 32 * pmax * sizeof(typename Cplx<R>::T);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k_p2m<R><<<unsigned(nblocks), P2M_WARPS * 32, smem, st>>>(tasks, ntasks, insts, pmax, start, xs,
+                                                             ys, gs, rec, me);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// M2M: one thread per (parent box, output coefficient).  Task = (instance,
+// parent level l); units = 4^l * p in row-major box order.
+// ----------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(EXP_THREADS) k_m2m(const Task *__restrict__ tasks, int ntasks,
+                                                     const InstDesc *__restrict__ insts,
+                                                     typename Cplx<R>::T *__restrict__ me) {
+    using C2 = typename Cplx<R>::T;
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t u = (int64_t(blockIdx.x) - t.block0) * EXP_THREADS + threadIdx.x;
+    if (u >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int p = d.p, l = t.level;
+    const int64_t box = u / p;
+    const int lp = int(u - box * p);
+    const uint32_t ix = uint32_t(box & ((int64_t(1) << l) - 1)), iy = uint32_t(box >> l);
+    const C2 *tab = static_cast<const C2 *>(d.t_m2m);
+    const int64_t quarter = int64_t(1) << (2 * l);
+    const C2 *child = me + d.eoff + (lvl_off(l + 1) + int64_t(iy) * (int64_t(1) << l) + ix) * p;
+    C2 s = mk2<R>(R(0), R(0));
+    for (int c = 0; c < 4; ++c) {
+        const C2 *a = child + c * quarter * p;
+        const C2 *row = tab + (size_t(c) * p + lp) * p;
+        for (int k = 0; k <= lp; ++k) s = cfma(row[k], a[k], s);
+    }
+    me[d.eoff + (lvl_off(l) + box_index(l, ix, iy)) * p + lp] = s;
+}
+
+template <typename R>
+cudaError_t launch_m2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       typename Cplx<R>::T *me, cudaStream_t st, uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_m2m<R><<<unsigned(nblocks), EXP_THREADS, 0, st>>>(tasks, ntasks, insts, me);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// L2L: one thread per (child box, output coefficient); adds the parent's
+// local expansion, translated, to the child's.  Task = (instance, child
+// level l); units = 4^l * p, row-major.
+// ----------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(EXP_THREADS) k_l2l(const Task *__restrict__ tasks, int ntasks,
+                                                     const InstDesc *__restrict__ insts,
+                                                     typename Cplx<R>::T *__restrict__ le) {
+    using C2 = typename Cplx<R>::T;
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t u = (int64_t(blockIdx.x) - t.block0) * EXP_THREADS + threadIdx.x;
+    if (u >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int p = d.p, l = t.level;
+    const int64_t box = u / p;
+    const int n = int(u - box * p);
+    const uint32_t ix = uint32_t(box & ((int64_t(1) << l) - 1)), iy = uint32_t(box >> l);
+    const int c = int((ix & 1u) | ((iy & 1u) << 1));
+    const C2 *tab = static_cast<const C2 *>(d.t_l2l) + (size_t(c) * p + n) * p;
+    const C2 *par = le + d.eoff + (lvl_off(l - 1) + box_index(l - 1, ix >> 1, iy >> 1)) * p;
+    C2 s = mk2<R>(R(0), R(0));
+    for (int m = n; m < p; ++m) s = cfma(tab[m], par[m], s);
+    C2 *dst = le + d.eoff + (lvl_off(l) + box_index(l, ix, iy)) * p + n;
+    C2 o = *dst;
+    o.x += s.x;
+    o.y += s.y;
+    *dst = o;
+}
+
+template <typename R>
+cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       typename Cplx<R>::T *le, cudaStream_t st, uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_l2l<R><<<unsigned(nblocks), EXP_THREADS, 0, st>>>(tasks, ntasks, insts, le);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// M2L (SIMT): one warp per target box; lane m owns output coefficient m (and
+// m + 32).  The source ME is staged in per-warp shared memory and read as a
+// broadcast; operator rows come through L1.  Task = (instance, level l),
+// units = 4^l target boxes, row-major.
+// ----------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__ tasks,
+                                                        int ntasks,
+                                                        const InstDesc *__restrict__ insts,
+                                                        const typename Cplx<R>::T *__restrict__ me,
+                                                        typename Cplx<R>::T *__restrict__ le) {
+    using C2 = typename Cplx<R>::T;
+    __shared__ C2 sa[M2L_WARPS][MAX_P];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t box = (int64_t(blockIdx.x) - t.block0) * M2L_WARPS + wid;
+    if (box >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int p = d.p, l = t.level;
+    const int nside = 1 << l;
+    const int ix = int(box & (nside - 1)), iy = int(box >> l);
+    const int c = (ix & 1) | ((iy & 1) << 1);
+    const C2 *tab = static_cast<const C2 *>(d.t_m2l);
+    const C2 *lev = me + d.eoff + lvl_off(l) * p;
+    C2 acc0 = mk2<R>(R(0), R(0)), acc1 = mk2<R>(R(0), R(0));
+    for (int e = 0; e < 27; ++e) {
+        const IlEntry en = c_il[c][e];
+        const int sx = ix + en.dx, sy = iy + en.dy;
+        if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
+        const C2 *src = lev + box_index(l, uint32_t(sx), uint32_t(sy)) * p;
+        if (lane < p) sa[wid][lane] = src[lane];
+        if (lane + 32 < p) sa[wid][lane + 32] = src[lane + 32];
+        __syncwarp();
+        const C2 *T = tab + size_t(en.op) * p * p;
+        if (lane < p) {
+            for (int k = 0; k < p; ++k) acc0 = cfma(T[k * p + lane], sa[wid][k], acc0);
+        }
+        if (lane + 32 < p) {
+            for (int k = 0; k < p; ++k) acc1 = cfma(T[k * p + lane + 32], sa[wid][k], acc1);
+        }
+        __syncwarp();
+    }
+    C2 *dst = le + d.eoff + (lvl_off(l) + box_index(l, uint32_t(ix), uint32_t(iy))) * p;
+    if (lane < p) dst[lane] = acc0;
+    if (lane + 32 < p) dst[lane + 32] = acc1;
+}
+
+template <typename R>
+cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       const typename Cplx<R>::T *me, typename Cplx<R>::T *le, cudaStream_t st,
+                       uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_m2l<R><<<unsigned(nblocks), M2L_WARPS * 32, 0, st>>>(tasks, ntasks, insts, me, le);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_p2m<double>(const Task *, int, int64_t, const InstDesc *, int,
+                                        const uint32_t *, const double *, const double *,
+                                        const double *, const float4 *, double2 *, cudaStream_t,
+                                        uint64_t *);
+template cudaError_t launch_p2m<float>(const Task *, int, int64_t, const InstDesc *, int,
+                                       const uint32_t *, const double *, const double *,
+                                       const double *, const float4 *, float2 *, cudaStream_t,
+                                       uint64_t *);
+template cudaError_t launch_m2m<double>(const Task *, int, int64_t, const InstDesc *, double2 *,
+                                        cudaStream_t, uint64_t *);
+template cudaError_t launch_m2m<float>(const Task *, int, int64_t, const InstDesc *, float2 *,
+                                       cudaStream_t, uint64_t *);
+template cudaError_t launch_l2l<double>(const Task *, int, int64_t, const InstDesc *, double2 *,
+                                        cudaStream_t, uint64_t *);
+template cudaError_t launch_l2l<float>(const Task *, int, int64_t, const InstDesc *, float2 *,
+                                       cudaStream_t, uint64_t *);
+template cudaError_t launch_m2l<double>(const Task *, int, int64_t, const InstDesc *,
+                                        const double2 *, double2 *, cudaStream_t, uint64_t *);
+template cudaError_t launch_m2l<float>(const Task *, int, int64_t, const InstDesc *,
+                                       const float2 *, float2 *, cudaStream_t, uint64_t *);
+
+}  // namespace petfmm

@@ -1,0 +1,102 @@
+// kernels.cuh -- host-side launchers of the FMM kernels (internal).
+#pragma once
+#include "common.cuh"
+
+namespace petfmm {
+
+// Every launcher returns cudaGetLastError() after the launch and adds the
+// number of kernels it launched to *launches.
+
+// ---- tree.cu ---------------------------------------------------------------
+// Sec. 2.1 binning + z-order key of every particle (composite key for batches).
+cudaError_t launch_morton(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                          int dtype_f32, uint32_t *keys, int *status, cudaStream_t st,
+                          uint64_t *launches);
+
+// Scratch (uint32 words) needed by exclusive_scan for n elements.
+int64_t scan_scratch_words(int64_t n);
+// out[i] = sum_{j < i} in[j]; in may equal out.  If total != nullptr the sum
+// of all elements is written there (device).
+cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch,
+                           uint32_t *total, cudaStream_t st, uint64_t *launches);
+
+// Stable LSD radix sort of (key, value) over the low nbits bits; the initial
+// values are the element indices.  Result ends up in (k0, v0) or (k1, v1):
+// *result_in_first tells which.  hist must hold 256 * radix_blocks(n) words.
+int64_t radix_blocks(int64_t n);
+cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n,
+                       int nbits, uint32_t *hist, uint32_t *scan_scratch, bool *result_in_first,
+                       cudaStream_t st, uint64_t *launches);
+
+// start[soff + b] = first sorted rank of leaf b (b = 0..4^L).
+cudaError_t launch_leaf_start(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                              const uint32_t *skeys, uint32_t *start, cudaStream_t st,
+                              uint64_t *launches);
+
+// Sorted particle arrays.
+cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                              int dtype_f32, const uint32_t *perm, double *xs, double *ys,
+                              double *gs, cudaStream_t st, uint64_t *launches);
+cudaError_t launch_gather_mixed(const Task *tasks, int ntasks, int64_t nblocks,
+                                const InstDesc *insts, int dtype_f32, const uint32_t *perm,
+                                const uint32_t *skeys, float4 *rec, cudaStream_t st,
+                                uint64_t *launches);
+
+// ---- expansions.cu ---------------------------------------------------------
+// Operator tables for p (FP64 build, also rounded to FP32), device-resident.
+struct OpTables {
+    int p = 0;
+    double2 *m2m64 = nullptr, *l2l64 = nullptr, *m2l64 = nullptr;
+    float2 *m2m32 = nullptr, *l2l32 = nullptr, *m2l32 = nullptr;
+};
+cudaError_t build_op_tables(int p, OpTables *out);
+void free_op_tables(OpTables *t);
+void host_m2l_table(int p, double *out_re_im /* 40 * p * p * 2, [op][k][m] */);
+// Interaction list exactly as the kernels enumerate it; returns the count.
+int host_interaction_list(int level, int ix, int iy, int32_t *out);
+// Number of (target, source) M2L translations of levels 2..L.
+int64_t m2l_pair_count(int L);
+
+template <typename R>
+cudaError_t launch_p2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       int pmax, const uint32_t *start, const double *xs, const double *ys,
+                       const double *gs, const float4 *rec, typename Cplx<R>::T *me,
+                       cudaStream_t st, uint64_t *launches);
+template <typename R>
+cudaError_t launch_m2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       typename Cplx<R>::T *me, cudaStream_t st, uint64_t *launches);
+template <typename R>
+cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       const typename Cplx<R>::T *me, typename Cplx<R>::T *le, cudaStream_t st,
+                       uint64_t *launches);
+template <typename R>
+cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       typename Cplx<R>::T *le, cudaStream_t st, uint64_t *launches);
+
+// units of work per block of each expansion kernel (the host plans with them)
+constexpr int P2M_WARPS = 4;      // leaves per block
+constexpr int M2L_WARPS = 4;      // target boxes per block
+constexpr int EXP_THREADS = 256;  // (box, coefficient) pairs per block for M2M / L2L
+
+// ---- p2p.cu ----------------------------------------------------------------
+// Work list: items (inst, leaf, first target rank, target count) for every
+// occupied leaf, tpi targets per item.  ctrl[CTRL_NITEMS] receives the count.
+enum { CTRL_STATUS = 0, CTRL_NITEMS = 1, CTRL_QUEUE = 2, CTRL_PAIRS_LO = 4, CTRL_WORDS = 16 };
+cudaError_t launch_p2p_worklist(const Task *tasks, int ntasks, int64_t nblocks,
+                                const InstDesc *insts, const uint32_t *start, int64_t nleaves,
+                                int tpi, uint32_t *cnt, uint32_t *off, uint32_t *scan_scratch,
+                                uint4 *items, uint32_t *ctrl, cudaStream_t st, uint64_t *launches);
+cudaError_t launch_p2p_f64(int grid, const uint4 *items, uint32_t *ctrl, const InstDesc *insts,
+                           const uint32_t *start, const double *xs, const double *ys,
+                           const double *gs, const uint32_t *perm, const double2 *le,
+                           int dtype_f32, unsigned long long *busy, cudaStream_t st,
+                           uint64_t *launches);
+cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
+                             const InstDesc *insts, const uint32_t *start, const float4 *rec,
+                             const float2 *le, int dtype_f32, unsigned long long *busy,
+                             cudaStream_t st, uint64_t *launches);
+int p2p_grid(int precision_mixed, int deg, int general);
+constexpr int P2P_TPI_F64 = 32;
+constexpr int P2P_TPI_MIXED = 64;
+
+}  // namespace petfmm

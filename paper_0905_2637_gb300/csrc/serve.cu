@@ -1,0 +1,451 @@
+// serve.cu -- request loop with continuous batching.
+//
+// A request is a short run of the vortex method of Sec. 3: blobs move with
+// their own velocity (Eq. 6) and keep their circulation, here with n_steps
+// midpoint-RK2 steps, i.e. 2 * n_steps velocity evaluations (Eq. 9 by the
+// FMM).  The scheduler thread works in rounds.  Every round it admits queued
+// requests while slots and the HBM budget allow (the per-request estimate
+// adapts the memory model of Table 1), runs ONE evaluation for every resident
+// request in a single batched pass (petfmm_evaluate_batch: all stages launch
+// once for the whole mix), applies each request's RK2 stage on the device,
+// and retires requests whose last step is done.  Requests that arrive while
+// others are on the GPU join at the next round; their state (positions,
+// circulations, RK2 copy) stays resident on the device until retirement.
+// An instance's arithmetic does not depend on the rest of the batch, so a
+// request's result is the same alone and in the mix.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/petfmm.h"
+#include "common.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// RK2 stage update: stage 0 saves x_n and moves to the midpoint, stage 1
+// completes the step from x_n with the midpoint velocity.
+__global__ void k_rk2(int64_t n, int stage, double dt, double *x, double *y, double *xn,
+                      double *yn, const double *u, const double *v) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (stage == 0) {
+        const double x0 = x[i], y0 = y[i];
+        xn[i] = x0;
+        yn[i] = y0;
+        x[i] = x0 + 0.5 * dt * u[i];
+        y[i] = y0 + 0.5 * dt * v[i];
+    } else {
+        x[i] = xn[i] + dt * u[i];
+        y[i] = yn[i] + dt * v[i];
+    }
+}
+
+// Bounding box of the positions (min x, min y, max x, max y), one block.
+__global__ void k_bbox(int64_t n, const double *x, const double *y, double *out) {
+    __shared__ double s[4][256];
+    double a = INFINITY, b = INFINITY, c = -INFINITY, d = -INFINITY;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        a = fmin(a, x[i]);
+        b = fmin(b, y[i]);
+        c = fmax(c, x[i]);
+        d = fmax(d, y[i]);
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    s[2][threadIdx.x] = c;
+    s[3][threadIdx.x] = d;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            s[0][threadIdx.x] = fmin(s[0][threadIdx.x], s[0][threadIdx.x + o]);
+            s[1][threadIdx.x] = fmin(s[1][threadIdx.x], s[1][threadIdx.x + o]);
+            s[2][threadIdx.x] = fmax(s[2][threadIdx.x], s[2][threadIdx.x + o]);
+            s[3][threadIdx.x] = fmax(s[3][threadIdx.x], s[3][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = s[threadIdx.x][0];
+}
+
+struct Req {
+    uint64_t ticket = 0;
+    petfmm_request spec{};
+    std::vector<double> hx, hy, hg;  // host copies (initial state, then result)
+    Clock::time_point t_submit, t_admit, t_done;
+    int status = PETFMM_OK;
+    bool done = false;
+    // resident state
+    double *x = nullptr, *y = nullptr, *g = nullptr, *u = nullptr, *v = nullptr, *xn = nullptr,
+           *yn = nullptr;
+    int levels = 1;
+    petfmm_domain dom{};
+    int evals_done = 0;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct petfmm_server {
+    size_t budget = 0;
+    int max_slots = 0, max_queue = 0;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Req *> queue;
+    std::vector<Req *> active;
+    std::map<uint64_t, Req *> all;
+    uint64_t next_ticket = 1;
+    size_t used = 0;
+    bool stop = false;
+    std::thread worker;
+    cudaStream_t stream = nullptr;
+    petfmm_ctx *ctx64 = nullptr, *ctxmx = nullptr;
+    double *dbox = nullptr, *hbox = nullptr;
+    int box_cap = 0;
+};
+
+namespace {
+
+size_t estimate(int64_t n, int L, int p, int precision) {
+    const double lam = (std::ldexp(1.0, 2 * (L + 1)) - 1.0) / 3.0;
+    const double leaves = std::ldexp(1.0, 2 * L);
+    const size_t per_particle = 56 /* resident x, y, g, u, v, RK2 copy */ + 16 /* sort keys/vals */ +
+                                (precision == PETFMM_FP64 ? 24 : 16) /* sorted particles */ + 8;
+    const size_t coef = precision == PETFMM_FP64 ? 16 : 8;
+    return size_t(n) * per_particle + size_t(2.0 * lam * p * coef) + size_t(leaves * 12.0) +
+           size_t((n / 32 + leaves) * 16.0) + (1u << 20);
+}
+
+void free_state(Req *r) {
+    double *bufs[] = {r->x, r->y, r->g, r->u, r->v, r->xn, r->yn};
+    for (double *b : bufs)
+        if (b) cudaFree(b);
+    r->x = r->y = r->g = r->u = r->v = r->xn = r->yn = nullptr;
+}
+
+// Square domain around the bounding box, with a margin so that blobs can move.
+petfmm_domain fit_domain(double x0, double y0, double x1, double y1) {
+    double w = std::max(x1 - x0, y1 - y0);
+    if (!(w > 0.0)) w = 1.0;
+    w *= 1.25;
+    petfmm_domain d;
+    d.x0 = 0.5 * (x0 + x1) - 0.5 * w;
+    d.y0 = 0.5 * (y0 + y1) - 0.5 * w;
+    d.width = w;
+    return d;
+}
+
+bool inside(const petfmm_domain &d, const double *b) {
+    return b[0] >= d.x0 && b[1] >= d.y0 && b[2] <= d.x0 + d.width && b[3] <= d.y0 + d.width;
+}
+
+int admit(petfmm_server *s, Req *r) {
+    const int64_t n = r->spec.n;
+    const size_t bytes = size_t(n > 0 ? n : 1) * sizeof(double);
+    double **bufs[] = {&r->x, &r->y, &r->g, &r->u, &r->v, &r->xn, &r->yn};
+    for (double **b : bufs) {
+        if (cudaMalloc(b, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_state(r);
+            return PETFMM_ENOMEM;
+        }
+    }
+    if (n > 0) {
+        if (cudaMemcpyAsync(r->x, r->hx.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(r->y, r->hy.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(r->g, r->hg.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+            free_state(r);
+            return PETFMM_ECUDA;
+        }
+        // host copies stay valid until the stream is synchronised below
+        if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+            free_state(r);
+            return PETFMM_ECUDA;
+        }
+        double bx0 = r->hx[0], by0 = r->hy[0], bx1 = bx0, by1 = by0;
+        for (int64_t i = 1; i < n; ++i) {
+            bx0 = std::min(bx0, r->hx[i]); bx1 = std::max(bx1, r->hx[i]);
+            by0 = std::min(by0, r->hy[i]); by1 = std::max(by1, r->hy[i]);
+        }
+        r->dom = fit_domain(bx0, by0, bx1, by1);
+    } else {
+        r->dom = petfmm_domain{0.0, 0.0, 1.0};
+    }
+    r->levels = r->spec.levels > 0 ? r->spec.levels
+                                   : petfmm_choose_levels(n, r->spec.order, r->spec.sigma, &r->dom);
+    if (r->levels < 1) {
+        free_state(r);
+        return PETFMM_EINVAL;
+    }
+    return PETFMM_OK;
+}
+
+void finish(petfmm_server *s, Req *r, int status) {
+    const int64_t n = r->spec.n;
+    if (status == PETFMM_OK && n > 0) {
+        if (cudaMemcpy(r->hx.data(), r->x, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(r->hy.data(), r->y, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            status = PETFMM_ECUDA;
+    }
+    free_state(r);
+    r->hg.clear();
+    r->hg.shrink_to_fit();
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->status = status;
+    r->t_done = Clock::now();
+    r->done = true;
+    s->used -= r->bytes;
+}
+
+// One round: one evaluation for every resident request, then its RK2 stage.
+void run_round(petfmm_server *s, std::vector<Req *> &act) {
+    std::vector<petfmm_instance> in64, inmx;
+    std::vector<Req *> r64, rmx;
+    for (Req *r : act) {
+        petfmm_instance it;
+        it.domain = r->dom;
+        it.levels = r->levels;
+        it.order = r->spec.order;
+        it.sigma = r->spec.sigma;
+        it.n = r->spec.n;
+        it.x = r->x; it.y = r->y; it.gamma = r->g; it.u = r->u; it.v = r->v;
+        if (r->spec.precision == PETFMM_FP64) { in64.push_back(it); r64.push_back(r); }
+        else { inmx.push_back(it); rmx.push_back(r); }
+    }
+    int rc64 = in64.empty() ? 0 : petfmm_evaluate_batch(s->ctx64, int(in64.size()), in64.data());
+    int rcmx = inmx.empty() ? 0 : petfmm_evaluate_batch(s->ctxmx, int(inmx.size()), inmx.data());
+    if ((int)act.size() > s->box_cap) {
+        cudaFree(s->dbox);
+        cudaFreeHost(s->hbox);
+        s->box_cap = std::max<int>(int(act.size()), 2 * s->box_cap);
+        cudaMalloc(&s->dbox, size_t(s->box_cap) * 4 * sizeof(double));
+        cudaMallocHost(&s->hbox, size_t(s->box_cap) * 4 * sizeof(double));
+    }
+    for (size_t i = 0; i < act.size(); ++i) {
+        Req *r = act[i];
+        const int64_t n = r->spec.n;
+        if (n > 0) {
+            const int stage = r->evals_done & 1;
+            k_rk2<<<unsigned((n + 255) / 256), 256, 0, s->stream>>>(n, stage, r->spec.dt, r->x, r->y,
+                                                                    r->xn, r->yn, r->u, r->v);
+            k_bbox<<<1, 256, 0, s->stream>>>(n, r->x, r->y, s->dbox + 4 * i);
+        }
+    }
+    cudaMemcpyAsync(s->hbox, s->dbox, act.size() * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    int st64 = in64.empty() ? 0 : petfmm_sync(s->ctx64);
+    int stmx = inmx.empty() ? 0 : petfmm_sync(s->ctxmx);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    for (size_t i = 0; i < act.size(); ++i) {
+        Req *r = act[i];
+        const bool is64 = r->spec.precision == PETFMM_FP64;
+        int st = is64 ? (rc64 ? rc64 : st64) : (rcmx ? rcmx : stmx);
+        if (e != cudaSuccess) st = PETFMM_ECUDA;
+        r->evals_done++;
+        if (st != PETFMM_OK) {
+            finish(s, r, st);
+            continue;
+        }
+        if (r->spec.n > 0 && !inside(r->dom, s->hbox + 4 * i)) {
+            const double *b = s->hbox + 4 * i;
+            if (!(std::isfinite(b[0]) && std::isfinite(b[1]) && std::isfinite(b[2]) && std::isfinite(b[3]))) {
+                finish(s, r, PETFMM_EDOMAIN);
+                continue;
+            }
+            r->dom = fit_domain(b[0], b[1], b[2], b[3]);
+        }
+        if (r->evals_done >= 2 * r->spec.n_steps) finish(s, r, PETFMM_OK);
+    }
+    act.erase(std::remove_if(act.begin(), act.end(), [](Req *r) { return r->done; }), act.end());
+}
+
+void worker_main(petfmm_server *s) {
+    cudaSetDevice(s->device);
+    std::vector<Req *> act;
+    for (;;) {
+        std::vector<Req *> newly;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            while (!s->stop && act.empty() && s->queue.empty()) s->cv.wait(lk);
+            if (s->stop) {
+                for (Req *r : s->queue) {
+                    r->status = PETFMM_EBUSY;
+                    r->done = true;
+                    r->t_done = Clock::now();
+                }
+                s->queue.clear();
+                if (act.empty()) break;
+            }
+            while (!s->queue.empty() && int(act.size() + newly.size()) < s->max_slots &&
+                   s->used + s->queue.front()->bytes <= s->budget) {
+                Req *r = s->queue.front();
+                s->queue.pop_front();
+                s->used += r->bytes;
+                newly.push_back(r);
+            }
+        }
+        for (Req *r : newly) {
+            int rc = admit(s, r);
+            r->t_admit = Clock::now();
+            if (rc != PETFMM_OK) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                r->status = rc;
+                r->done = true;
+                r->t_done = Clock::now();
+                s->used -= r->bytes;
+                continue;
+            }
+            if (r->spec.n == 0 || r->spec.n_steps == 0) {
+                finish(s, r, PETFMM_OK);
+                continue;
+            }
+            act.push_back(r);
+        }
+        if (!act.empty()) run_round(s, act);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t petfmm_serve_estimate_bytes(int64_t n, int levels, int order, int precision) {
+    if (n < 0 || levels < 1 || levels > petfmm::MAX_L || order < 1 || order > petfmm::MAX_P) return 0;
+    return estimate(n, levels, order, precision);
+}
+
+int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, petfmm_server **out) {
+    if (!out || max_slots < 1 || max_queue < 1 || hbm_budget_bytes == 0) return PETFMM_EINVAL;
+    *out = nullptr;
+    petfmm_server *s = new (std::nothrow) petfmm_server();
+    if (!s) return PETFMM_ENOMEM;
+    s->budget = hbm_budget_bytes;
+    s->max_slots = max_slots;
+    s->max_queue = max_queue;
+    if (cudaGetDevice(&s->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return PETFMM_ECUDA;
+    }
+    const petfmm_domain unit{0.0, 0.0, 1.0};
+    int rc = petfmm_create(&unit, 2, 8, 0.01, PETFMM_FP64, PETFMM_F64, s->stream, &s->ctx64);
+    if (rc == PETFMM_OK)
+        rc = petfmm_create(&unit, 2, 8, 0.01, PETFMM_MIXED, PETFMM_F64, s->stream, &s->ctxmx);
+    if (rc != PETFMM_OK) {
+        if (s->ctx64) petfmm_destroy(s->ctx64);
+        cudaStreamDestroy(s->stream);
+        delete s;
+        return rc;
+    }
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return PETFMM_OK;
+}
+
+int petfmm_serve_submit(petfmm_server *s, const petfmm_request *req, uint64_t *ticket) {
+    if (!s || !req || !ticket) return PETFMM_EINVAL;
+    const petfmm_request &q = *req;
+    if (q.n < 0 || (q.n > 0 && (!q.x || !q.y || !q.gamma)) || q.order < 1 || q.order > petfmm::MAX_P ||
+        !(q.sigma > 0.0) || !std::isfinite(q.dt) || q.n_steps < 0 || q.levels > petfmm::MAX_L ||
+        (q.precision != PETFMM_FP64 && q.precision != PETFMM_MIXED))
+        return PETFMM_EINVAL;
+    Req *r = new (std::nothrow) Req();
+    if (!r) return PETFMM_ENOMEM;
+    r->spec = q;
+    r->spec.x = r->spec.y = r->spec.gamma = nullptr;
+    try {
+        r->hx.assign(q.x, q.x + q.n);
+        r->hy.assign(q.y, q.y + q.n);
+        r->hg.assign(q.gamma, q.gamma + q.n);
+    } catch (...) {
+        delete r;
+        return PETFMM_ENOMEM;
+    }
+    // admission estimate with the level the request will use (worst case 10)
+    int L = q.levels > 0 ? q.levels : 10;
+    if (q.levels <= 0 && q.n > 0) {
+        L = std::min(12, std::max(1, int(std::ceil(std::log(double(q.n) / 8.0) / std::log(4.0)))));
+    }
+    r->bytes = estimate(q.n, L, q.order, q.precision);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (r->bytes > s->budget) {
+            delete r;
+            return PETFMM_ENOMEM;
+        }
+        if (int(s->queue.size()) >= s->max_queue || s->stop) {
+            delete r;
+            return PETFMM_EBUSY;
+        }
+        r->ticket = s->next_ticket++;
+        s->queue.push_back(r);
+        s->all[r->ticket] = r;
+        *ticket = r->ticket;
+    }
+    s->cv.notify_one();
+    return PETFMM_OK;
+}
+
+int petfmm_serve_poll(petfmm_server *s, uint64_t ticket, petfmm_result *out) {
+    if (!s || !out) return PETFMM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return PETFMM_EINVAL;
+    Req *r = it->second;
+    if (!r->done) return PETFMM_ENOTREADY;
+    out->status = r->status;
+    out->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    const auto adm = r->t_admit.time_since_epoch().count() ? r->t_admit : r->t_done;
+    out->queue_ms = std::chrono::duration<double, std::milli>(adm - r->t_submit).count();
+    out->n = r->status == PETFMM_OK ? r->spec.n : 0;
+    out->x = r->status == PETFMM_OK ? r->hx.data() : nullptr;
+    out->y = r->status == PETFMM_OK ? r->hy.data() : nullptr;
+    return PETFMM_OK;
+}
+
+int petfmm_serve_release(petfmm_server *s, uint64_t ticket) {
+    if (!s) return PETFMM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return PETFMM_EINVAL;
+    if (!it->second->done) return PETFMM_ENOTREADY;
+    delete it->second;
+    s->all.erase(it);
+    return PETFMM_OK;
+}
+
+int petfmm_serve_destroy(petfmm_server *s) {
+    if (!s) return PETFMM_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (auto &kv : s->all) {
+        free_state(kv.second);
+        delete kv.second;
+    }
+    if (s->ctx64) petfmm_destroy(s->ctx64);
+    if (s->ctxmx) petfmm_destroy(s->ctxmx);
+    if (s->dbox) cudaFree(s->dbox);
+    if (s->hbox) cudaFreeHost(s->hbox);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    cudaGetLastError();
+    delete s;
+    return PETFMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,389 @@
+// tree.cu -- the uniform quadtree of Sec. 2.1 on the device: binning with
+// z-order keys (Sec. 5.1), a stable LSD radix sort of the keys, the leaf
+// ranges, and the gather of the particles into sorted order.
+//
+// All of it is bandwidth-bound.  Per particle the algorithmic traffic is one
+// read of x, y and one key write (binning), then per radix pass one read of
+// (key, value) for the histogram, one more read and one write for the
+// scatter, and finally a gather of x, y, gamma into sorted order.
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace petfmm {
+
+#define PF_LAUNCHED(n) do { if (launches) *launches += (n); } while (0)
+
+// ----------------------------------------------------------------------------
+// Binning: t = x - x0; s = t * (2^L / W); ix = floor(s) clamped to [0, 2^L-1].
+// The FP64 operations are spelled as round-to-nearest intrinsics so that no
+// contraction can change a bit; the host computes 2^L / W once.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t bin_coord(double x, double x0, double scale, uint32_t nb) {
+    double t = __dsub_rn(x, x0);
+    double s = __dmul_rn(t, scale);
+    double f = floor(s);
+    if (!(f >= 0.0)) return 0u;  // also NaN (reported separately)
+    if (f > double(nb - 1)) return nb - 1;
+    return uint32_t(f);
+}
+
+template <typename TIn>
+__global__ void __launch_bounds__(256) k_morton(const Task *__restrict__ tasks, int ntasks,
+                                                const InstDesc *__restrict__ insts,
+                                                uint32_t *__restrict__ keys, int *status) {
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    if (j >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const double x = double(static_cast<const TIn *>(d.x)[j]);
+    const double y = double(static_cast<const TIn *>(d.y)[j]);
+    const double x1 = __dadd_rn(d.x0, d.width), y1 = __dadd_rn(d.y0, d.width);
+    if (!(x >= d.x0 && x <= x1 && y >= d.y0 && y <= y1)) set_status(status, ST_EDOMAIN);
+    const uint32_t nb = 1u << d.L;
+    const uint32_t ix = bin_coord(x, d.x0, d.scale, nb);
+    const uint32_t iy = bin_coord(y, d.y0, d.scale, nb);
+    keys[d.poff + j] = d.key_hi | morton_key(ix, iy);
+}
+
+cudaError_t launch_morton(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                          int dtype_f32, uint32_t *keys, int *status, cudaStream_t st,
+                          uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (dtype_f32)
+        k_morton<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, keys, status);
+    else
+        k_morton<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, keys, status);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Exclusive scan (reduce-then-scan, recursive over tiles of 2048).
+// ----------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t n = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += n;
+        }
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t before = warp ? warp_sums[warp - 1] : 0u;
+    *total = warp_sums[SCAN_THREADS / 32 - 1];
+    __syncthreads();
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile_sums(const uint32_t *__restrict__ in,
+                                                                 int64_t n,
+                                                                 uint32_t *__restrict__ sums) {
+    const int64_t base = int64_t(blockIdx.x) * SCAN_TILE;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        int64_t i = base + int64_t(k) * SCAN_THREADS + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    uint32_t total;
+    block_exclusive_sum(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t *in, uint32_t *out,
+                                                             int64_t n,
+                                                             const uint32_t *__restrict__ prefix,
+                                                             uint32_t *total_out) {
+    const int64_t base = int64_t(blockIdx.x) * SCAN_TILE + int64_t(threadIdx.x) * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_sum(s, &total);
+    const uint32_t p0 = prefix ? prefix[blockIdx.x] : 0u;
+    run += p0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total_out = p0 + total;
+}
+
+int64_t scan_scratch_words(int64_t n) {
+    int64_t w = 0;
+    while (n > SCAN_TILE) {
+        n = (n + SCAN_TILE - 1) / SCAN_TILE;
+        w += n;
+    }
+    return w + 1;
+}
+
+cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch,
+                           uint32_t *total, cudaStream_t st, uint64_t *launches) {
+    if (n <= 0) {
+        if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+        return cudaSuccess;
+    }
+    if (n <= SCAN_TILE) {
+        k_scan_tiles<<<1, SCAN_THREADS, 0, st>>>(in, out, n, nullptr, total);
+        PF_LAUNCHED(1);
+        return cudaGetLastError();
+    }
+    const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+    uint32_t *sums = scratch;
+    k_scan_tile_sums<<<unsigned(nt), SCAN_THREADS, 0, st>>>(in, n, sums);
+    PF_LAUNCHED(1);
+    cudaError_t e = exclusive_scan(sums, sums, nt, scratch + nt, nullptr, st, launches);
+    if (e != cudaSuccess) return e;
+    k_scan_tiles<<<unsigned(nt), SCAN_THREADS, 0, st>>>(in, out, n, sums, total);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Stable LSD radix sort, 8-bit digits, reduce-then-scan.  A block owns a tile
+// of RS_ITEMS * 256 consecutive elements; element (round k, thread t) of the
+// tile is tile + k * 256 + t, so ranking rounds in order, warps in order and
+// lanes in order keeps equal digits in input order (stability).
+// ----------------------------------------------------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+int64_t radix_blocks(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__restrict__ keys,
+                                                           int64_t n, int shift, uint32_t mask,
+                                                           uint32_t *__restrict__ hist,
+                                                           int64_t nblocks) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
+#pragma unroll 4
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        int64_t i = tile + int64_t(k) * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    hist[int64_t(threadIdx.x) * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t n, int shift, uint32_t mask,
+    const uint32_t *__restrict__ offs, int64_t nblocks) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wpos[RS_THREADS / 32][256];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    base[tid] = offs[int64_t(tid) * nblocks + blockIdx.x];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
+    for (int k = 0; k < RS_ITEMS; ++k) {
+#pragma unroll
+        for (int w = 0; w < RS_THREADS / 32; ++w) wpos[w][tid] = 0;
+        __syncthreads();
+        const int64_t i = tile + int64_t(k) * RS_THREADS + tid;
+        const bool valid = i < n;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t val = valid ? (vin ? vin[i] : uint32_t(i)) : 0u;
+        const uint32_t dg = valid ? ((key >> shift) & mask) : 0x100u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t below = peers & lt_mask;
+        if (valid && below == 0) wpos[warp][dg] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t s = base[tid];
+#pragma unroll
+            for (int w = 0; w < RS_THREADS / 32; ++w) {
+                const uint32_t c = wpos[w][tid];
+                wpos[w][tid] = s;
+                s += c;
+            }
+            base[tid] = s;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = wpos[warp][dg] + __popc(below);
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n,
+                       int nbits, uint32_t *hist, uint32_t *scan_scratch, bool *result_in_first,
+                       cudaStream_t st, uint64_t *launches) {
+    *result_in_first = true;
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = radix_blocks(n);
+    uint32_t *kin = k0, *vin = nullptr, *kout = k1, *vout = v1;
+    bool in_first = true;
+    const int passes = (nbits + 7) / 8;
+    if (passes == 0) {
+        // nothing to sort: values are the identity
+        return cudaErrorInvalidValue;
+    }
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        const int bits = nbits - shift < 8 ? nbits - shift : 8;
+        const uint32_t mask = (1u << bits) - 1u;
+        k_radix_hist<<<unsigned(nb), RS_THREADS, 0, st>>>(kin, n, shift, mask, hist, nb);
+        PF_LAUNCHED(1);
+        cudaError_t e = exclusive_scan(hist, hist, 256 * nb, scan_scratch, nullptr, st, launches);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<unsigned(nb), RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, mask,
+                                                               hist, nb);
+        PF_LAUNCHED(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        in_first = !in_first;
+        if (in_first) {
+            kin = k0; vin = v0; kout = k1; vout = v1;
+        } else {
+            kin = k1; vin = v1; kout = k0; vout = v0;
+        }
+    }
+    *result_in_first = in_first;
+    return cudaSuccess;
+}
+
+// ----------------------------------------------------------------------------
+// Leaf ranges: start[b] = lower_bound(sorted keys of the instance, key_hi | b).
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_leaf_start(const Task *__restrict__ tasks, int ntasks,
+                                                    const InstDesc *__restrict__ insts,
+                                                    const uint32_t *__restrict__ skeys,
+                                                    uint32_t *__restrict__ start) {
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t b = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    if (b >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int64_t nleaf = int64_t(1) << (2 * d.L);
+    uint32_t r;
+    if (b >= nleaf) {
+        r = uint32_t(d.poff + d.n);
+    } else {
+        const uint32_t want = d.key_hi | uint32_t(b);
+        int64_t lo = d.poff, hi = d.poff + d.n;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (skeys[mid] < want) lo = mid + 1; else hi = mid;
+        }
+        r = uint32_t(lo);
+    }
+    start[d.soff + b] = r;
+}
+
+cudaError_t launch_leaf_start(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                              const uint32_t *skeys, uint32_t *start, cudaStream_t st,
+                              uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_leaf_start<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, skeys, start);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Gather into sorted order.  Task units are sorted ranks of one instance.
+// ----------------------------------------------------------------------------
+template <typename TIn>
+__global__ void __launch_bounds__(256) k_gather_f64(const Task *__restrict__ tasks, int ntasks,
+                                                    const InstDesc *__restrict__ insts,
+                                                    const uint32_t *__restrict__ perm,
+                                                    double *__restrict__ xs, double *__restrict__ ys,
+                                                    double *__restrict__ gs) {
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    if (j >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int64_t r = d.poff + j;
+    const int64_t q = int64_t(perm[r]) - d.poff;
+    xs[r] = double(static_cast<const TIn *>(d.x)[q]);
+    ys[r] = double(static_cast<const TIn *>(d.y)[q]);
+    gs[r] = double(static_cast<const TIn *>(d.g)[q]);
+}
+
+// Mixed path: leaf-relative coordinates in leaf units, computed in FP64 and
+// rounded once; .w carries the batch index of the particle (for the output).
+template <typename TIn>
+__global__ void __launch_bounds__(256) k_gather_mixed(const Task *__restrict__ tasks, int ntasks,
+                                                      const InstDesc *__restrict__ insts,
+                                                      const uint32_t *__restrict__ perm,
+                                                      const uint32_t *__restrict__ skeys,
+                                                      float4 *__restrict__ rec) {
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    if (j >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int64_t r = d.poff + j;
+    const uint32_t qb = perm[r];
+    const int64_t q = int64_t(qb) - d.poff;
+    const uint32_t m = skeys[r] & ((d.L >= 16) ? 0xffffffffu : ((1u << (2 * d.L)) - 1u));
+    const uint32_t ix = compact_bits(m), iy = compact_bits(m >> 1);
+    const double cx = d.x0 + (double(ix) + 0.5) * d.wleaf;
+    const double cy = d.y0 + (double(iy) + 0.5) * d.wleaf;
+    const double x = double(static_cast<const TIn *>(d.x)[q]);
+    const double y = double(static_cast<const TIn *>(d.y)[q]);
+    const double g = double(static_cast<const TIn *>(d.g)[q]);
+    float4 o;
+    o.x = float((x - cx) * d.scale);
+    o.y = float((y - cy) * d.scale);
+    o.z = float(g);
+    o.w = __uint_as_float(qb);
+    rec[r] = o;
+}
+
+cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                              int dtype_f32, const uint32_t *perm, double *xs, double *ys,
+                              double *gs, cudaStream_t st, uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (dtype_f32)
+        k_gather_f64<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, xs, ys, gs);
+    else
+        k_gather_f64<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, xs, ys, gs);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_mixed(const Task *tasks, int ntasks, int64_t nblocks,
+                                const InstDesc *insts, int dtype_f32, const uint32_t *perm,
+                                const uint32_t *skeys, float4 *rec, cudaStream_t st,
+                                uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (dtype_f32)
+        k_gather_mixed<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys, rec);
+    else
+        k_gather_mixed<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys, rec);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+}  // namespace petfmm

@@ -1,0 +1,65 @@
+"""Instrumentation: per-stage timings (the per-stage breakdown of Fig. 6),
+pair counts against the oracle's tree, the load-balance metric of Eq. 20,
+launch counting, and the host-array entry point."""
+import numpy as np
+import pytest
+
+import gpu_util as G
+from paper_0905_2637_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_stage_times_and_counters(orc):
+    _lib = G.lib()
+    w = W.tiny(50_000, 3, L=6, p=12, clustered_frac=0.4)
+    keep = []
+    G.run(w, "mixed", timing=True, ctx_out=keep)
+    ctx = keep[0]
+    t = ctx.stage_times()
+    assert set(t) == set(_lib.STAGES) and all(v >= 0 for v in t.values())
+    st = ctx.stats()
+    # ordered near-field pairs, counted from the oracle's own tree
+    _, _, key = orc.bin(w.x, w.y, w.domain, w.L)
+    _, start = orc.sort(key, w.L)
+    cnt = np.diff(start.astype(np.int64))
+    n = 1 << w.L
+    grid = np.zeros((n, n), np.int64)
+    for m in np.nonzero(cnt)[0]:
+        ix = iy = 0
+        for b in range(w.L):
+            ix |= ((int(m) >> (2 * b)) & 1) << b
+            iy |= ((int(m) >> (2 * b + 1)) & 1) << b
+        grid[iy, ix] = cnt[m]
+    pad = np.pad(grid, 1)
+    near = sum(pad[1 + dy:1 + dy + n, 1 + dx:1 + dx + n] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    assert st["p2p_pairs"] == int(np.sum(grid * (near - 1) * (grid > 0)))
+    assert st["m2l_pairs"] == sum((6 * (1 << l) - 8) ** 2 - (3 * (1 << l) - 2) ** 2 for l in range(2, w.L + 1))
+    assert 0.0 < st["p2p_load_balance"] <= 1.0
+    assert st["kernel_launches"] > 10 and st["evaluations"] == 1
+    ctx.close()
+
+
+def test_evaluate_host_matches_device_path():
+    _lib = G.lib()
+    w = W.tiny(20_000, 4, L=5, p=12, dtype="f32")
+    ud, vd = G.run(w, "mixed")
+    ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype="f32")
+    uh, vh = ctx.evaluate_host(w.x, w.y, w.gamma)
+    ctx.close()
+    assert np.array_equal(uh.astype(np.float64), ud) and np.array_equal(vh.astype(np.float64), vd)
+
+
+def test_repeated_evaluations_are_deterministic():
+    _lib = G.lib()
+    w = W.tiny(100_000, 5, L=7, p=17, clustered_frac=0.5, dtype="f32")
+    ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype="f32")
+    x, y, g = G.to_dev((w.x, w.y, w.gamma))
+    outs = []
+    for _ in range(3):
+        u, v = ctx.evaluate(x, y, g)
+        ctx.sync()
+        outs.append((u.cpu().numpy(), v.cpu().numpy()))
+    ctx.close()
+    for u, v in outs[1:]:
+        assert np.array_equal(u, outs[0][0]) and np.array_equal(v, outs[0][1])
