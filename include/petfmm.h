@@ -161,9 +161,9 @@ typedef struct petfmm_server petfmm_server;
  * One request = n_steps midpoint-RK2 steps (2 velocity evaluations each) of
  * the Lagrangian vortex method of Sec. 3 (Eq. 6: blobs move with their
  * velocity, gamma is carried unchanged).  x, y, gamma are HOST arrays copied
- * at submit time; the domain is re-fitted on the device before every
- * evaluation (a square around the current blobs), so blobs may leave the
- * initial square.
+ * at submit time.  The domain is a square 1.25 times the blobs' bounding box;
+ * after every evaluation the bounding box is reduced on the device and, if a
+ * blob has left the square, the square is refitted before the next one.
  */
 typedef struct {
     int64_t n;
@@ -212,7 +212,9 @@ int petfmm_debug_tree(petfmm_ctx *ctx, uint32_t *keys, uint32_t *perm, uint32_t 
 /* Expansions of level `level` (2..L) of the last evaluation, copied to the
  * host as FP64 complex pairs out[(m * p + k) * 2 + {0,1}], m = Morton index.
  * which = 0: multipole (ME), scaled a_k / r^k; which = 1: local (LE), scaled
- * r^(k+1) b_k; r = box width at that level. */
+ * r^(k+1) b_k; r = box width at that level.  Only boxes with particles in
+ * them are computed (an empty box's ME is exactly zero and its LE is never
+ * evaluated); the values of the other boxes are unspecified. */
 int petfmm_debug_expansions(petfmm_ctx *ctx, int level, int which, double *out);
 
 /* Interaction list of box (level, ix, iy) as the device kernels enumerate it:
@@ -220,11 +222,28 @@ int petfmm_debug_expansions(petfmm_ctx *ctx, int level, int which, double *out);
  * returns the count, or PETFMM_EINVAL. */
 int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out);
 
+/* Launch plan of a batch, built on the host without touching the device
+ * (pointers in inst are not dereferenced).  Each task is written as five
+ * int64 {range, instance, level, units, first block}; range 0 binning,
+ * 1 leaf starts, 2 gather, 3 P2M, 4 P2P work list, 5 M2L (SIMT, units =
+ * target boxes), 6 M2L on the tensor cores (units = CTAs), 100 + r the r-th
+ * M2M launch, 200 + r the r-th L2L launch.  Writes at most cap tasks and
+ * returns the total count, or PETFMM_EINVAL. */
+int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, int64_t *out, int cap);
+
 /* Options. */
 enum {
     PETFMM_OPT_TIMING = 1,     /* 1: record per-stage CUDA events each evaluation */
-    PETFMM_OPT_SPIN_LIMIT = 2, /* iteration limit of device-side waits (0 = default) */
-    PETFMM_OPT_P2P_MODE = 3    /* P2P scheduler: 0 work-model partition, 1 dynamic queue */
+    PETFMM_OPT_SPIN_LIMIT = 2, /* iteration limit of device-side waits (0 = default 2^26;
+                                  < 0: no iterations, so the first wait of the tensor-core
+                                  M2L reports PETFMM_ETIMEOUT -- for testing the report;
+                                  that evaluation's u, v are then unspecified) */
+    PETFMM_OPT_P2P_MODE = 3,   /* P2P scheduler: 0 work-model partition, 1 dynamic queue */
+    PETFMM_OPT_POISON = 4,     /* 1: fill the expansion buffers with NaN bytes before each
+                                  evaluation (testing: a read of a never-written
+                                  coefficient then shows up as NaN in u, v) */
+    PETFMM_OPT_M2L_TC = 5      /* mixed path: 1 (default) M2L of levels >= 8 on the tensor
+                                  cores (3xTF32), 0 all levels on the FP32 SIMT kernel */
 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
 

@@ -22,7 +22,8 @@ PETFMM_OK, PETFMM_EINVAL, PETFMM_ENOMEM, PETFMM_EDOMAIN = 0, -1, -2, -3
 PETFMM_ECUDA, PETFMM_ETIMEOUT, PETFMM_EBUSY, PETFMM_ENOTREADY = -4, -5, -6, -7
 PETFMM_FP64, PETFMM_MIXED = 0, 1
 PETFMM_F64, PETFMM_F32 = 0, 1
-PETFMM_OPT_TIMING, PETFMM_OPT_SPIN_LIMIT, PETFMM_OPT_P2P_MODE = 1, 2, 3
+PETFMM_OPT_TIMING, PETFMM_OPT_SPIN_LIMIT, PETFMM_OPT_P2P_MODE, PETFMM_OPT_POISON = 1, 2, 3, 4
+PETFMM_OPT_M2L_TC = 5
 STAGES = ("morton", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "worklist", "p2p")
 
 
@@ -109,6 +110,7 @@ def load():
             "petfmm_debug_tree": (I, [P, P, P, P]),
             "petfmm_debug_expansions": (I, [P, I, I, P]),
             "petfmm_debug_interaction_list": (I, [I, I, I, P]),
+            "petfmm_debug_plan": (I, [I, I, ctypes.POINTER(Instance), P, I]),
             "petfmm_set_option": (I, [P, I, I64]),
             "petfmm_stage_times": (I, [P, P, I]),
             "petfmm_get_stats": (I, [P, ctypes.POINTER(Stats)]),
@@ -167,6 +169,19 @@ def petfmm_debug_interaction_list(level, ix, iy):
     cnt = _ck(load().petfmm_debug_interaction_list(int(level), int(ix), int(iy), out.ctypes.data),
               "petfmm_debug_interaction_list")
     return out[: 2 * cnt].reshape(cnt, 2).copy()
+
+
+def petfmm_debug_plan(precision, instances):
+    """Host-side launch plan: list of (range, inst, level, units, block0)."""
+    arr = (Instance * max(1, len(instances)))()
+    for i, it in enumerate(instances):
+        arr[i] = Instance(Domain(*map(float, it["domain"])), int(it.get("levels", 0)),
+                          int(it["order"]), float(it["sigma"]), int(it["n"]), 8, 8, 8, 8, 8)
+    n = _ck(load().petfmm_debug_plan(int(precision), len(instances), arr, None, 0), "petfmm_debug_plan")
+    out = np.zeros((max(n, 1), 5), np.int64)
+    _ck(load().petfmm_debug_plan(int(precision), len(instances), arr, out.ctypes.data, n),
+        "petfmm_debug_plan")
+    return out[:n]
 
 
 def petfmm_serve_estimate_bytes(n, levels, order, precision):

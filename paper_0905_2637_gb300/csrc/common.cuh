@@ -51,6 +51,7 @@ struct InstDesc {
     const void *x, *y, *g;  // caller's arrays (storage type of the context)
     void *u, *v;
     const void *t_m2m, *t_l2l, *t_m2l;  // operator tables for this p (path's real type)
+    const void *t_m2l_tc;               // tensor-core M2L operator images (mixed path)
     // mixed-precision P2P constants (leaf units)
     float kappa;            // w^2 / (2 sigma^2): q = kappa * rho^2
     float cnear;            // w / (4 pi sigma^2)
@@ -108,6 +109,15 @@ __host__ __device__ __forceinline__ uint32_t morton_key(uint32_t ix, uint32_t iy
     return spread_bits(ix) | (spread_bits(iy) << 1);
 }
 
+// Particles in box m (Morton index) of level l: the leaves of a box form one
+// contiguous Morton range, so this is two reads of the leaf starts st[] of
+// an instance with depth L.  Expansions of empty boxes are never computed
+// or read (their coefficients would be exactly zero).
+__device__ __forceinline__ uint32_t box_count(const uint32_t *st, int L, int l, uint32_t m) {
+    const int sh = 2 * (L - l);
+    return st[(uint64_t(m) + 1) << sh] - st[uint64_t(m) << sh];
+}
+
 __device__ __forceinline__ int find_task(const Task *tasks, int ntasks, int64_t b) {
     int lo = 0, hi = ntasks - 1;
     while (lo < hi) {
@@ -137,6 +147,15 @@ template <typename T2> __host__ __device__ __forceinline__ T2 cfma(T2 a, T2 b, T
     r.x = a.x * b.x - a.y * b.y + c.x;
     r.y = a.x * b.y + a.y * b.x + c.y;
     return r;
+}
+
+// Position of the M2L offset (dx, dy) among the 40 vectors of
+// [-3, 3]^2 \ [-1, 1]^2, taken row by row (increasing dy, then dx): the index
+// of its operator T_delta.
+__host__ __device__ __forceinline__ int m2l_op_index(int dx, int dy) {
+    const int base = dy <= -1 ? 7 * (dy + 3) : (dy <= 2 ? 14 + 4 * (dy + 1) : 33);
+    const int pos = (dy >= -1 && dy <= 1) ? (dx < 0 ? dx + 3 : dx) : dx + 3;
+    return base + pos;
 }
 
 // Interaction-list table: for child class c, the 27 (dx, dy) offsets of the

@@ -55,20 +55,26 @@ int ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
     return PETFMM_OK;
 }
 
+// The tasks of one launch.  Kernels binary-search their block in a
+// contiguous slice of the uploaded task array, so each range keeps its own
+// list while planning and the lists are laid out one after another at the
+// end (flatten_tasks).
 struct TaskRange {
     int first = 0;
     int count = 0;
     int64_t nblocks = 0;
+    std::vector<Task> list;
 };
 
 struct Plan {
     std::vector<InstDesc> inst;
     std::vector<Task> tasks;
-    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l;
+    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc;
     std::vector<TaskRange> m2m, l2l;  // in launch order
     int64_t N = 0, nleaves = 0, nstart = 0, ncoef = 0, items_cap = 0;
     int nbits = 0, pmax = 1, Lmax = 0;
     int deg = 0, general = 0;          // mixed P2P variant (max over instances)
+    size_t tc_smem = 0;                // dynamic shared memory of the tensor-core M2L
 };
 
 struct Problem {
@@ -91,6 +97,8 @@ struct petfmm_ctx {
     int device = 0;
     bool timing = false;
     int p2p_mode = 1;
+    bool poison = false;
+    bool m2l_tc = true;
     int64_t spin_limit = 0;
     uint64_t launches = 0, evaluations = 0;
 
@@ -140,7 +148,8 @@ int cuda_status(cudaError_t e) {
 // ---------------------------------------------------------------------------
 // Near-field polynomial: Chebyshev interpolation of g(q) = (1 - e^-q) / q on
 // [0, Q], converted to monomials in rho^2 (q = kappa rho^2).  The smallest
-// degree whose relative error on a fine grid stays below 3e-8 is taken.
+// degree whose relative error on a fine grid stays below 1e-7 (the size of
+// the FP32 rounding of the Horner evaluation itself) is taken.
 // ---------------------------------------------------------------------------
 double g_exact(double q) { return q == 0.0 ? 1.0 : -std::expm1(-q) / q; }
 
@@ -199,7 +208,7 @@ int fit_near_poly(double Q, double kappa, float *coef) {
             for (int k = d - 1; k >= 0; --k) v = v * s + a[k];
             err = std::max(err, std::fabs(v - g_exact(kappa * s)) / g_exact(kappa * s));
         }
-        if (err < 3e-8) {
+        if (err < 1e-7) {
             for (int k = 0; k <= POLY_MAX; ++k) coef[k] = k <= d ? float(a[k]) : 0.0f;
             return d;
         }
@@ -246,20 +255,36 @@ OpTables *get_tables(petfmm_ctx *c, int p, int *err) {
     return &(c->tables[p] = t);
 }
 
-void add_task(Plan &pl, TaskRange &r, int inst, int level, int64_t count, int64_t per_block) {
+void add_task(TaskRange &r, int inst, int level, int64_t count, int64_t per_block) {
     if (count <= 0) return;
-    if (r.count == 0) r.first = int(pl.tasks.size());
     Task t;
     t.inst = inst;
     t.level = level;
     t.count = count;
     t.block0 = r.nblocks;
-    pl.tasks.push_back(t);
+    r.list.push_back(t);
     r.count++;
     r.nblocks += (count + per_block - 1) / per_block;
 }
 
-int build_plan(petfmm_ctx *c, const std::vector<Problem> &probs, Plan &pl) {
+void flatten_tasks(Plan &pl) {
+    pl.tasks.clear();
+    auto put = [&](TaskRange &r) {
+        r.first = int(pl.tasks.size());
+        pl.tasks.insert(pl.tasks.end(), r.list.begin(), r.list.end());
+    };
+    put(pl.morton);
+    put(pl.start);
+    put(pl.particles);
+    put(pl.leaves_p2m);
+    put(pl.leaves_wl);
+    put(pl.m2l);
+    put(pl.m2l_tc);
+    for (TaskRange &r : pl.m2m) put(r);
+    for (TaskRange &r : pl.l2l) put(r);
+}
+
+int build_plan(int precision, bool use_tc, const std::vector<Problem> &probs, Plan &pl) {
     pl = Plan();
     const int ni = int(probs.size());
     int inst_bits = 0;
@@ -297,16 +322,8 @@ int build_plan(petfmm_ctx *c, const std::vector<Problem> &probs, Plan &pl) {
         d.g = pb.g;
         d.u = pb.u;
         d.v = pb.v;
-        int err = PETFMM_OK;
-        OpTables *t = get_tables(c, pb.p, &err);
-        if (!t) return err;
-        if (c->precision == PETFMM_FP64) {
-            d.t_m2m = t->m2m64; d.t_l2l = t->l2l64; d.t_m2l = t->m2l64;
-        } else {
-            d.t_m2m = t->m2m32; d.t_l2l = t->l2l32; d.t_m2l = t->m2l32;
-        }
         fill_p2p_constants(d);
-        if (c->precision == PETFMM_MIXED && d.deg == 0) return PETFMM_EINVAL;
+        if (precision == PETFMM_MIXED && d.deg == 0) return PETFMM_EINVAL;
         pl.deg = std::max(pl.deg, d.deg);
         pl.general |= d.general;
         pl.inst.push_back(d);
@@ -321,18 +338,24 @@ int build_plan(petfmm_ctx *c, const std::vector<Problem> &probs, Plan &pl) {
     pl.ncoef = eoff;
     if (pl.N >= (int64_t(1) << 31)) return PETFMM_EINVAL;
 
-    const int tpi = c->precision == PETFMM_MIXED ? P2P_TPI_MIXED : P2P_TPI_F64;
+    const int tpi = precision == PETFMM_MIXED ? P2P_TPI_MIXED : P2P_TPI_F64;
     int64_t items_cap = 0;
     for (int i = 0; i < ni; ++i) {
         const InstDesc &d = pl.inst[i];
         const int64_t nleaf = int64_t(1) << (2 * d.L);
-        add_task(pl, pl.morton, i, d.L, d.n, 256);
-        add_task(pl, pl.start, i, d.L, nleaf + 1, 256);
-        add_task(pl, pl.particles, i, d.L, d.n, 256);
-        add_task(pl, pl.leaves_p2m, i, d.L, nleaf, P2M_WARPS);
-        add_task(pl, pl.leaves_wl, i, d.L, nleaf, 256);
-        for (int l = 2; l <= d.L; ++l)
-            add_task(pl, pl.m2l, i, l, int64_t(1) << (2 * l), M2L_WARPS);
+        add_task(pl.morton, i, d.L, d.n, 256);
+        add_task(pl.start, i, d.L, nleaf + 1, 256);
+        add_task(pl.particles, i, d.L, d.n, 256);
+        add_task(pl.leaves_p2m, i, d.L, nleaf, P2M_WARPS);
+        add_task(pl.leaves_wl, i, d.L, nleaf, 256);
+        for (int l = 2; l <= d.L; ++l) {
+            if (precision == PETFMM_MIXED && use_tc && m2l_tc_supported(d.p, l)) {
+                add_task(pl.m2l_tc, i, l, m2l_tc_units(l), 1);
+                pl.tc_smem = std::max(pl.tc_smem, m2l_tc_smem_bytes(d.p, m2l_tc_seg(l)));
+            } else {
+                add_task(pl.m2l, i, l, int64_t(1) << (2 * l), M2L_WARPS);
+            }
+        }
         items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
     }
     // M2M rounds: round r computes level L_i - 1 - r (>= 2) of every instance.
@@ -340,7 +363,7 @@ int build_plan(petfmm_ctx *c, const std::vector<Problem> &probs, Plan &pl) {
         TaskRange tr;
         for (int i = 0; i < ni; ++i) {
             const int l = pl.inst[i].L - 1 - r;
-            if (l >= 2) add_task(pl, tr, i, l, (int64_t(1) << (2 * l)) * pl.inst[i].p, EXP_THREADS);
+            if (l >= 2) add_task(tr, i, l, (int64_t(1) << (2 * l)) * pl.inst[i].p, EXP_THREADS);
         }
         if (tr.count) pl.m2m.push_back(tr);
     }
@@ -350,11 +373,28 @@ int build_plan(petfmm_ctx *c, const std::vector<Problem> &probs, Plan &pl) {
         for (int i = 0; i < ni; ++i) {
             const int l = 3 + r;
             if (l <= pl.inst[i].L)
-                add_task(pl, tr, i, l, (int64_t(1) << (2 * l)) * pl.inst[i].p, EXP_THREADS);
+                add_task(tr, i, l, (int64_t(1) << (2 * l)) * pl.inst[i].p, EXP_THREADS);
         }
         if (tr.count) pl.l2l.push_back(tr);
     }
     pl.items_cap = items_cap;
+    flatten_tasks(pl);
+    return PETFMM_OK;
+}
+
+// Operator tables (device pointers) of every instance's p.
+int attach_tables(petfmm_ctx *c, Plan &pl) {
+    for (InstDesc &d : pl.inst) {
+        int err = PETFMM_OK;
+        OpTables *t = get_tables(c, d.p, &err);
+        if (!t) return err;
+        if (c->precision == PETFMM_FP64) {
+            d.t_m2m = t->m2m64; d.t_l2l = t->l2l64; d.t_m2l = t->m2l64;
+        } else {
+            d.t_m2m = t->m2m32; d.t_l2l = t->l2l32; d.t_m2l = t->m2l32;
+            d.t_m2l_tc = t->m2l_tc;
+        }
+    }
     return PETFMM_OK;
 }
 
@@ -408,7 +448,8 @@ void stage_mark(petfmm_ctx *c, int stage) {
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     Plan &pl = c->plan;
-    PF_TRY(build_plan(c, probs, pl));
+    PF_TRY(build_plan(c->precision, c->m2l_tc, probs, pl));
+    PF_TRY(attach_tables(c, pl));
     cudaStream_t st = c->stream;
     const bool mixed = c->precision == PETFMM_MIXED;
     const int64_t N = pl.N;
@@ -464,6 +505,11 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     const int f32 = c->dtype == PETFMM_F32;
     uint64_t *lc = &c->launches;
 
+    if (c->poison) {
+        const size_t es = mixed ? sizeof(float2) : sizeof(double2);
+        PF_CUDA(cudaMemsetAsync(c->me.p, 0xff, size_t(pl.ncoef) * es, st));
+        PF_CUDA(cudaMemsetAsync(c->le.p, 0xff, size_t(pl.ncoef) * es, st));
+    }
     // per-evaluation control words (the status word survives until sync)
     PF_CUDA(cudaMemsetAsync(ctrl + 1, 0, (CTRL_WORDS - 1) * 4, st));
 
@@ -505,30 +551,38 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     stage_mark(c, PETFMM_STAGE_M2M);
     for (const TaskRange &tr : pl.m2m) {
         if (mixed)
-            PF_CUDA(launch_m2m<float>(dtask + tr.first, tr.count, tr.nblocks, dinst,
+            PF_CUDA(launch_m2m<float>(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
                                       static_cast<float2 *>(c->me.p), st, lc));
         else
-            PF_CUDA(launch_m2m<double>(dtask + tr.first, tr.count, tr.nblocks, dinst,
+            PF_CUDA(launch_m2m<double>(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
                                        static_cast<double2 *>(c->me.p), st, lc));
     }
     stage_mark(c, PETFMM_STAGE_M2L);
     if (pl.m2l.count) {
         if (mixed)
             PF_CUDA(launch_m2l<float>(dtask + pl.m2l.first, pl.m2l.count, pl.m2l.nblocks, dinst,
-                                      static_cast<const float2 *>(c->me.p),
+                                      start, static_cast<const float2 *>(c->me.p),
                                       static_cast<float2 *>(c->le.p), st, lc));
         else
             PF_CUDA(launch_m2l<double>(dtask + pl.m2l.first, pl.m2l.count, pl.m2l.nblocks, dinst,
-                                       static_cast<const double2 *>(c->me.p),
+                                       start, static_cast<const double2 *>(c->me.p),
                                        static_cast<double2 *>(c->le.p), st, lc));
+    }
+    if (pl.m2l_tc.count) {
+        // spin_limit < 0: zero-iteration budget (tests the timeout report)
+        const long long spin = c->spin_limit > 0 ? c->spin_limit : c->spin_limit < 0 ? 0 : (1LL << 26);
+        PF_CUDA(launch_m2l_tc(dtask + pl.m2l_tc.first, pl.m2l_tc.count, pl.m2l_tc.nblocks, dinst,
+                              start, static_cast<const float2 *>(c->me.p),
+                              static_cast<float2 *>(c->le.p), pl.tc_smem, spin,
+                              reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
     }
     stage_mark(c, PETFMM_STAGE_L2L);
     for (const TaskRange &tr : pl.l2l) {
         if (mixed)
-            PF_CUDA(launch_l2l<float>(dtask + tr.first, tr.count, tr.nblocks, dinst,
+            PF_CUDA(launch_l2l<float>(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
                                       static_cast<float2 *>(c->le.p), st, lc));
         else
-            PF_CUDA(launch_l2l<double>(dtask + tr.first, tr.count, tr.nblocks, dinst,
+            PF_CUDA(launch_l2l<double>(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
                                        static_cast<double2 *>(c->le.p), st, lc));
     }
     stage_mark(c, PETFMM_STAGE_WORKLIST);
@@ -689,9 +743,8 @@ int petfmm_sync(petfmm_ctx *c) {
     return status;
 }
 
-int petfmm_evaluate_batch(petfmm_ctx *c, int n_inst, const petfmm_instance *inst) {
-    if (!c || n_inst < 0 || (n_inst > 0 && !inst)) return PETFMM_EINVAL;
-    std::vector<Problem> probs(static_cast<size_t>(n_inst));
+static int problems_from(int n_inst, const petfmm_instance *inst, std::vector<Problem> &probs) {
+    probs.resize(static_cast<size_t>(n_inst));
     for (int i = 0; i < n_inst; ++i) {
         const petfmm_instance &s = inst[i];
         int L = s.levels;
@@ -704,7 +757,47 @@ int petfmm_evaluate_batch(petfmm_ctx *c, int n_inst, const petfmm_instance *inst
         if (s.n < 0 || (s.n > 0 && (!s.x || !s.y || !s.gamma || !s.u || !s.v))) return PETFMM_EINVAL;
         probs[i] = Problem{s.domain, L, s.order, s.sigma, s.n, s.x, s.y, s.gamma, s.u, s.v};
     }
+    return PETFMM_OK;
+}
+
+int petfmm_evaluate_batch(petfmm_ctx *c, int n_inst, const petfmm_instance *inst) {
+    if (!c || n_inst < 0 || (n_inst > 0 && !inst)) return PETFMM_EINVAL;
+    std::vector<Problem> probs;
+    int rc = problems_from(n_inst, inst, probs);
+    if (rc) return rc;
     return run(c, probs);
+}
+
+int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, int64_t *out, int cap) {
+    if (n_inst < 0 || (n_inst > 0 && !inst) || cap < 0 || (cap > 0 && !out)) return PETFMM_EINVAL;
+    if (precision != PETFMM_FP64 && precision != PETFMM_MIXED) return PETFMM_EINVAL;
+    std::vector<Problem> probs;
+    int rc = problems_from(n_inst, inst, probs);
+    if (rc) return rc;
+    Plan pl;
+    rc = build_plan(precision, true, probs, pl);
+    if (rc) return rc;
+    int n = 0;
+    auto emit = [&](int64_t id, const TaskRange &r) {
+        for (int i = 0; i < r.count; ++i) {
+            const Task &t = pl.tasks[size_t(r.first + i)];
+            if (n < cap) {
+                int64_t *o = out + 5 * size_t(n);
+                o[0] = id; o[1] = t.inst; o[2] = t.level; o[3] = t.count; o[4] = t.block0;
+            }
+            ++n;
+        }
+    };
+    emit(0, pl.morton);
+    emit(1, pl.start);
+    emit(2, pl.particles);
+    emit(3, pl.leaves_p2m);
+    emit(4, pl.leaves_wl);
+    emit(5, pl.m2l);
+    emit(6, pl.m2l_tc);
+    for (size_t r = 0; r < pl.m2m.size(); ++r) emit(100 + int64_t(r), pl.m2m[r]);
+    for (size_t r = 0; r < pl.l2l.size(); ++r) emit(200 + int64_t(r), pl.l2l[r]);
+    return n;
 }
 
 int petfmm_choose_levels(int64_t n, int order, double sigma, const petfmm_domain *dom) {
@@ -737,8 +830,10 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
     if (!c) return PETFMM_EINVAL;
     switch (option) {
         case PETFMM_OPT_TIMING: c->timing = value != 0; return PETFMM_OK;
-        case PETFMM_OPT_SPIN_LIMIT: if (value < 0) return PETFMM_EINVAL; c->spin_limit = value; return PETFMM_OK;
+        case PETFMM_OPT_SPIN_LIMIT: c->spin_limit = value; return PETFMM_OK;
         case PETFMM_OPT_P2P_MODE: if (value < 0 || value > 1) return PETFMM_EINVAL; c->p2p_mode = int(value); return PETFMM_OK;
+        case PETFMM_OPT_POISON: c->poison = value != 0; return PETFMM_OK;
+        case PETFMM_OPT_M2L_TC: c->m2l_tc = value != 0; return PETFMM_OK;
         default: return PETFMM_EINVAL;
     }
 }

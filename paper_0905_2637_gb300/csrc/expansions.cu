@@ -35,16 +35,7 @@ namespace petfmm {
 // ----------------------------------------------------------------------------
 __constant__ IlEntry c_il[4][27];
 
-static int offset_op_index(int dx, int dy) {
-    int idx = 0;
-    for (int y = -3; y <= 3; ++y)
-        for (int x = -3; x <= 3; ++x) {
-            if (x >= -1 && x <= 1 && y >= -1 && y <= 1) continue;
-            if (x == dx && y == dy) return idx;
-            ++idx;
-        }
-    return -1;
-}
+static int offset_op_index(int dx, int dy) { return m2l_op_index(dx, dy); }
 
 static void il_offsets(int c, IlEntry *out) {
     const int cx = c & 1, cy = c >> 1;
@@ -201,12 +192,18 @@ cudaError_t build_op_tables(int p, OpTables *t) {
     if ((e = up((void **)&t->m2m32, m2m32.data(), m2m32.size() * 4)) != cudaSuccess) return e;
     if ((e = up((void **)&t->l2l32, l2l32.data(), l2l32.size() * 4)) != cudaSuccess) return e;
     if ((e = up((void **)&t->m2l32, m2l32.data(), m2l32.size() * 4)) != cudaSuccess) return e;
+    if (((2 * p + 15) & ~15) <= 48) {
+        std::vector<float> img;
+        host_m2l_tc_images(p, img);
+        if ((e = up((void **)&t->m2l_tc, img.data(), img.size() * 4)) != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
 void free_op_tables(OpTables *t) {
     cudaFree(t->m2m64); cudaFree(t->l2l64); cudaFree(t->m2l64);
     cudaFree(t->m2m32); cudaFree(t->l2l32); cudaFree(t->m2l32);
+    cudaFree(t->m2l_tc);
     *t = OpTables();
 }
 
@@ -241,6 +238,7 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m(
     const int p = d.p, L = d.L;
     const uint32_t ix = compact_bits(uint32_t(m)), iy = compact_bits(uint32_t(m) >> 1);
     const uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+    if (s0 == s1) return;  // empty leaf: expansion never read
     const double cx = d.x0 + (double(ix) + 0.5) * d.wleaf;
     const double cy = d.y0 + (double(iy) + 0.5) * d.wleaf;
     C2 acc0 = mk2<R>(R(0), R(0)), acc1 = mk2<R>(R(0), R(0));
@@ -311,6 +309,7 @@ cudaError_t launch_p2m(const Task *tasks, int ntasks, int64_t nblocks, const Ins
 template <typename R>
 __global__ void __launch_bounds__(EXP_THREADS) k_m2m(const Task *__restrict__ tasks, int ntasks,
                                                      const InstDesc *__restrict__ insts,
+                                                     const uint32_t *__restrict__ start,
                                                      typename Cplx<R>::T *__restrict__ me) {
     using C2 = typename Cplx<R>::T;
     const int ti = find_task(tasks, ntasks, blockIdx.x);
@@ -322,11 +321,17 @@ __global__ void __launch_bounds__(EXP_THREADS) k_m2m(const Task *__restrict__ ta
     const int64_t box = u / p;
     const int lp = int(u - box * p);
     const uint32_t ix = uint32_t(box & ((int64_t(1) << l) - 1)), iy = uint32_t(box >> l);
+    const uint32_t *st = start + d.soff;
+    const uint32_t pm = morton_key(ix, iy);
+    if (!box_count(st, d.L, l, pm)) return;
     const C2 *tab = static_cast<const C2 *>(d.t_m2m);
     const int64_t quarter = int64_t(1) << (2 * l);
     const C2 *child = me + d.eoff + (lvl_off(l + 1) + int64_t(iy) * (int64_t(1) << l) + ix) * p;
     C2 s = mk2<R>(R(0), R(0));
     for (int c = 0; c < 4; ++c) {
+        // child c of the parent has Morton index 4 pm + c; an empty child has
+        // no expansion (it would be zero)
+        if (!box_count(st, d.L, l + 1, 4 * pm + uint32_t(c))) continue;
         const C2 *a = child + c * quarter * p;
         const C2 *row = tab + (size_t(c) * p + lp) * p;
         for (int k = 0; k <= lp; ++k) s = cfma(row[k], a[k], s);
@@ -336,9 +341,10 @@ __global__ void __launch_bounds__(EXP_THREADS) k_m2m(const Task *__restrict__ ta
 
 template <typename R>
 cudaError_t launch_m2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                       typename Cplx<R>::T *me, cudaStream_t st, uint64_t *launches) {
+                       const uint32_t *start, typename Cplx<R>::T *me, cudaStream_t st,
+                       uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    k_m2m<R><<<unsigned(nblocks), EXP_THREADS, 0, st>>>(tasks, ntasks, insts, me);
+    k_m2m<R><<<unsigned(nblocks), EXP_THREADS, 0, st>>>(tasks, ntasks, insts, start, me);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
@@ -351,6 +357,7 @@ cudaError_t launch_m2m(const Task *tasks, int ntasks, int64_t nblocks, const Ins
 template <typename R>
 __global__ void __launch_bounds__(EXP_THREADS) k_l2l(const Task *__restrict__ tasks, int ntasks,
                                                      const InstDesc *__restrict__ insts,
+                                                     const uint32_t *__restrict__ start,
                                                      typename Cplx<R>::T *__restrict__ le) {
     using C2 = typename Cplx<R>::T;
     const int ti = find_task(tasks, ntasks, blockIdx.x);
@@ -362,6 +369,7 @@ __global__ void __launch_bounds__(EXP_THREADS) k_l2l(const Task *__restrict__ ta
     const int64_t box = u / p;
     const int n = int(u - box * p);
     const uint32_t ix = uint32_t(box & ((int64_t(1) << l) - 1)), iy = uint32_t(box >> l);
+    if (!box_count(start + d.soff, d.L, l, morton_key(ix, iy))) return;
     const int c = int((ix & 1u) | ((iy & 1u) << 1));
     const C2 *tab = static_cast<const C2 *>(d.t_l2l) + (size_t(c) * p + n) * p;
     const C2 *par = le + d.eoff + (lvl_off(l - 1) + box_index(l - 1, ix >> 1, iy >> 1)) * p;
@@ -376,9 +384,10 @@ __global__ void __launch_bounds__(EXP_THREADS) k_l2l(const Task *__restrict__ ta
 
 template <typename R>
 cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                       typename Cplx<R>::T *le, cudaStream_t st, uint64_t *launches) {
+                       const uint32_t *start, typename Cplx<R>::T *le, cudaStream_t st,
+                       uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    k_l2l<R><<<unsigned(nblocks), EXP_THREADS, 0, st>>>(tasks, ntasks, insts, le);
+    k_l2l<R><<<unsigned(nblocks), EXP_THREADS, 0, st>>>(tasks, ntasks, insts, start, le);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
@@ -393,6 +402,7 @@ template <typename R>
 __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__ tasks,
                                                         int ntasks,
                                                         const InstDesc *__restrict__ insts,
+                                                        const uint32_t *__restrict__ start,
                                                         const typename Cplx<R>::T *__restrict__ me,
                                                         typename Cplx<R>::T *__restrict__ le) {
     using C2 = typename Cplx<R>::T;
@@ -406,6 +416,8 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
     const int p = d.p, l = t.level;
     const int nside = 1 << l;
     const int ix = int(box & (nside - 1)), iy = int(box >> l);
+    const uint32_t *st = start + d.soff;
+    if (!box_count(st, d.L, l, morton_key(uint32_t(ix), uint32_t(iy)))) return;
     const int c = (ix & 1) | ((iy & 1) << 1);
     const C2 *tab = static_cast<const C2 *>(d.t_m2l);
     const C2 *lev = me + d.eoff + lvl_off(l) * p;
@@ -414,6 +426,7 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
         const IlEntry en = c_il[c][e];
         const int sx = ix + en.dx, sy = iy + en.dy;
         if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
+        if (!box_count(st, d.L, l, morton_key(uint32_t(sx), uint32_t(sy)))) continue;
         const C2 *src = lev + box_index(l, uint32_t(sx), uint32_t(sy)) * p;
         if (lane < p) sa[wid][lane] = src[lane];
         if (lane + 32 < p) sa[wid][lane + 32] = src[lane + 32];
@@ -434,10 +447,10 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
 
 template <typename R>
 cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                       const typename Cplx<R>::T *me, typename Cplx<R>::T *le, cudaStream_t st,
-                       uint64_t *launches) {
+                       const uint32_t *start, const typename Cplx<R>::T *me,
+                       typename Cplx<R>::T *le, cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    k_m2l<R><<<unsigned(nblocks), M2L_WARPS * 32, 0, st>>>(tasks, ntasks, insts, me, le);
+    k_m2l<R><<<unsigned(nblocks), M2L_WARPS * 32, 0, st>>>(tasks, ntasks, insts, start, me, le);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
@@ -450,17 +463,19 @@ template cudaError_t launch_p2m<float>(const Task *, int, int64_t, const InstDes
                                        const uint32_t *, const double *, const double *,
                                        const double *, const float4 *, float2 *, cudaStream_t,
                                        uint64_t *);
-template cudaError_t launch_m2m<double>(const Task *, int, int64_t, const InstDesc *, double2 *,
-                                        cudaStream_t, uint64_t *);
-template cudaError_t launch_m2m<float>(const Task *, int, int64_t, const InstDesc *, float2 *,
-                                       cudaStream_t, uint64_t *);
-template cudaError_t launch_l2l<double>(const Task *, int, int64_t, const InstDesc *, double2 *,
-                                        cudaStream_t, uint64_t *);
-template cudaError_t launch_l2l<float>(const Task *, int, int64_t, const InstDesc *, float2 *,
-                                       cudaStream_t, uint64_t *);
+template cudaError_t launch_m2m<double>(const Task *, int, int64_t, const InstDesc *,
+                                        const uint32_t *, double2 *, cudaStream_t, uint64_t *);
+template cudaError_t launch_m2m<float>(const Task *, int, int64_t, const InstDesc *,
+                                       const uint32_t *, float2 *, cudaStream_t, uint64_t *);
+template cudaError_t launch_l2l<double>(const Task *, int, int64_t, const InstDesc *,
+                                        const uint32_t *, double2 *, cudaStream_t, uint64_t *);
+template cudaError_t launch_l2l<float>(const Task *, int, int64_t, const InstDesc *,
+                                       const uint32_t *, float2 *, cudaStream_t, uint64_t *);
 template cudaError_t launch_m2l<double>(const Task *, int, int64_t, const InstDesc *,
-                                        const double2 *, double2 *, cudaStream_t, uint64_t *);
+                                        const uint32_t *, const double2 *, double2 *, cudaStream_t,
+                                        uint64_t *);
 template cudaError_t launch_m2l<float>(const Task *, int, int64_t, const InstDesc *,
-                                       const float2 *, float2 *, cudaStream_t, uint64_t *);
+                                       const uint32_t *, const float2 *, float2 *, cudaStream_t,
+                                       uint64_t *);
 
 }  // namespace petfmm

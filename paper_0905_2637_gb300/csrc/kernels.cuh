@@ -1,5 +1,7 @@
 // kernels.cuh -- host-side launchers of the FMM kernels (internal).
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace petfmm {
@@ -48,6 +50,7 @@ struct OpTables {
     int p = 0;
     double2 *m2m64 = nullptr, *l2l64 = nullptr, *m2l64 = nullptr;
     float2 *m2m32 = nullptr, *l2l32 = nullptr, *m2l32 = nullptr;
+    float *m2l_tc = nullptr;  // hi/lo B images for the tensor-core M2L (p <= 24)
 };
 cudaError_t build_op_tables(int p, OpTables *out);
 void free_op_tables(OpTables *t);
@@ -62,16 +65,33 @@ cudaError_t launch_p2m(const Task *tasks, int ntasks, int64_t nblocks, const Ins
                        int pmax, const uint32_t *start, const double *xs, const double *ys,
                        const double *gs, const float4 *rec, typename Cplx<R>::T *me,
                        cudaStream_t st, uint64_t *launches);
+// M2M, M2L and L2L skip boxes with no particles in their subtree (and M2L
+// skips empty sources): their coefficients would be exactly zero and are
+// never read.  start = the batch's leaf-start array.
 template <typename R>
 cudaError_t launch_m2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                       typename Cplx<R>::T *me, cudaStream_t st, uint64_t *launches);
-template <typename R>
-cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                       const typename Cplx<R>::T *me, typename Cplx<R>::T *le, cudaStream_t st,
+                       const uint32_t *start, typename Cplx<R>::T *me, cudaStream_t st,
                        uint64_t *launches);
 template <typename R>
-cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       const uint32_t *start, const typename Cplx<R>::T *me,
                        typename Cplx<R>::T *le, cudaStream_t st, uint64_t *launches);
+template <typename R>
+cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                       const uint32_t *start, typename Cplx<R>::T *le, cudaStream_t st,
+                       uint64_t *launches);
+
+// ---- m2l_tc.cu -------------------------------------------------------------
+// Tensor-core M2L (mixed path) for levels with at least 128 parent cells per
+// row and p <= 24: one CTA per (target class, parent row, segment) unit.
+bool m2l_tc_supported(int p, int level);
+int64_t m2l_tc_units(int level);
+size_t m2l_tc_smem_bytes(int p, int seg);
+int m2l_tc_seg(int level);
+void host_m2l_tc_images(int p, std::vector<float> &out);
+cudaError_t launch_m2l_tc(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                          const uint32_t *start, const float2 *me, float2 *le, size_t smem_bytes,
+                          long long spin_limit, int *status, cudaStream_t st, uint64_t *launches);
 
 // units of work per block of each expansion kernel (the host plans with them)
 constexpr int P2M_WARPS = 4;      // leaves per block

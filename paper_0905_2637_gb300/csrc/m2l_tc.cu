@@ -1,0 +1,354 @@
+// m2l_tc.cu -- M2L (Sec. 2.2, downward sweep) as a dense GEMM on the 5th-
+// generation tensor cores (tcgen05, TF32 inputs, FP32 accumulation in TMEM),
+// mixed-precision path.
+//
+// With expansions stored by child class (common.cuh), the interaction list of
+// a target of class c at parent cell P is the set of 27 (source class c',
+// parent offset (dx, dy)) pairs whose child offset
+//     delta = (2 dx + c'x - cx, 2 dy + c'y - cy)
+// is not within one box.  Each such pair is one fixed operator T_delta, and
+// the translation of all targets of one parent row is
+//     LE_c[P] += ME_c'[P + (dx, dy)] T_delta^T
+// i.e. a real GEMM with M = targets (128 per MMA), K = 2p source coefficients
+// (real parts then imaginary parts) and N = 2p output coefficients, with
+// B_delta = [[Tr^T, Ti^T], [-Ti^T, Tr^T]].
+//
+// Unit of work (one CTA): a segment of up to 512 parent cells of one parent
+// row, for one target class.  For each of the 12 (c', dy) source strips the
+// CTA stages the strip's source expansions once in shared memory, K-major
+// without swizzle (core matrices of 8 rows x 16 bytes; rows 16 B apart inside
+// a k-group, so a row offset is a 16-byte shift of the descriptor start), and
+// the three dx shifts of the strip are the same staged data read one row
+// earlier or later.  Operands are split for 3xTF32: a = a_hi + a_lo with
+// a_hi = a with its low 13 mantissa bits cleared; the GEMM accumulates
+// a_hi b_hi + a_hi b_lo + a_lo b_hi (relative error about 2^-20).  Units whose
+// targets are all empty are skipped, and so are strips whose sources are all
+// empty (their expansions would be zero).
+//
+// One thread issues the MMAs; their completion is tracked with an mbarrier
+// (tcgen05.commit); every wait is bounded and reports PETFMM_ETIMEOUT.
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace petfmm {
+
+#define PF_LAUNCHED(n) do { if (launches) *launches += (n); } while (0)
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_MAX_SEG = 512;
+constexpr int TC_MAX_NPAD = 48;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return uint32_t(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: LBO = byte distance
+// between core matrices adjacent in K, SBO = between core matrices adjacent
+// in M/N; bits 46-47 hold the descriptor version (1).
+__device__ __forceinline__ uint64_t mma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    uint32_t done = 0;
+    for (long long it = 0; it < limit && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity));
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ float tf32_hi(float v) {
+    return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
+    const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
+    const uint32_t *__restrict__ start, const float2 *__restrict__ me, float2 *__restrict__ le,
+    long long spin_limit, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    __shared__ uint32_t used_mask;
+    __shared__ uint8_t rowocc[TC_MAX_SEG + 2];
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const InstDesc &d = insts[t.inst];
+    const int l = t.level, L = d.L, p = d.p;
+    const int W = 1 << (l - 1);
+    const int SEG = W < TC_MAX_SEG ? W : TC_MAX_SEG;
+    const int nseg = W / SEG;
+    const int S = SEG / 128;
+    const int64_t unit = int64_t(blockIdx.x) - t.block0;
+    const int c = int(unit / (int64_t(W) * nseg));
+    const int64_t rem = unit - int64_t(c) * W * nseg;
+    const int Py = int(rem / nseg);
+    const int Px0 = int(rem - int64_t(Py) * nseg) * SEG;
+    const int cx = c & 1, cy = c >> 1;
+    const uint32_t *st = start + d.soff;
+
+    // 1. skip the unit if none of its targets holds particles
+    bool any = false;
+    for (int i = tid; i < SEG; i += TC_THREADS) {
+        const uint32_t ix = uint32_t(2 * (Px0 + i) + cx), iy = uint32_t(2 * Py + cy);
+        any |= box_count(st, L, l, morton_key(ix, iy)) != 0;
+    }
+    if (!__syncthreads_or(any)) return;
+
+    const int K2 = 2 * p;
+    const int Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
+    const int KG = Kpad / 4, Rs = SEG + 2;
+    float *A_hi = reinterpret_cast<float *>(smem);
+    float *A_lo = A_hi + size_t(KG) * Rs * 4;
+    float *Bsm = A_lo + size_t(KG) * Rs * 4;  // 6 slots of Kpad x Npad floats
+    const int bslot = Kpad * Npad;
+    // zero the K padding of every staged row once (never overwritten)
+    for (int i = tid; i < Rs * (Kpad - K2); i += TC_THREADS) {
+        const int r = i / (Kpad - K2), k = K2 + i % (Kpad - K2);
+        const size_t o = (size_t(k >> 2) * Rs + r) * 4 + (k & 3);
+        A_hi[o] = 0.f;
+        A_lo[o] = 0.f;
+    }
+    const uint32_t bar = smem_addr(&mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        used_mask = 0;
+    }
+    int ncols = 32;
+    while (ncols < S * Npad) ncols <<= 1;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tslot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = tslot;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(Npad >> 3) << 17) |
+                           (uint32_t(128 >> 4) << 24);
+    const uint32_t LBO_A = uint32_t(Rs) * 16, LBO_B = uint32_t(Npad) * 16, SBO = 128;
+    const int64_t quarter = int64_t(1) << (2 * (l - 1));
+    const float2 *lev = me + d.eoff + lvl_off(l) * p;
+    const float *bimg = static_cast<const float *>(d.t_m2l_tc);
+    uint32_t phase = 0;
+    bool ok = true;
+    uint32_t used = 0;  // thread 0's record of initialised accumulators
+
+    for (int cs = 0; cs < 4 && ok; ++cs) {
+        const int csx = cs & 1, csy = cs >> 1;
+        for (int dyp = -1; dyp <= 1 && ok; ++dyp) {
+            const int Pys = Py + dyp;
+            if (Pys < 0 || Pys >= W) continue;
+            int ops[3];
+            uint32_t mask3 = 0;
+            for (int dxp = -1; dxp <= 1; ++dxp) {
+                const int ddx = 2 * dxp + csx - cx, ddy = 2 * dyp + csy - cy;
+                const int ax = ddx < 0 ? -ddx : ddx, ay = ddy < 0 ? -ddy : ddy;
+                ops[dxp + 1] = 0;
+                if ((ax > ay ? ax : ay) >= 2) {
+                    mask3 |= 1u << (dxp + 1);
+                    ops[dxp + 1] = m2l_op_index(ddx, ddy);
+                }
+            }
+            if (!mask3) continue;
+            // occupancy of the strip's source boxes (row r <-> Px = Px0 - 1 + r)
+            bool anyr = false;
+            for (int r = tid; r < Rs; r += TC_THREADS) {
+                const int Px = Px0 - 1 + r;
+                bool o = false;
+                if (Px >= 0 && Px < W)
+                    o = box_count(st, L, l, morton_key(uint32_t(2 * Px + csx), uint32_t(2 * Pys + csy))) != 0;
+                rowocc[r] = o;
+                anyr |= o;
+            }
+            if (!__syncthreads_or(anyr)) continue;
+            // stage the strip: real parts at k < p, imaginary parts at p <= k < 2p
+            const int64_t base = int64_t(cs) * quarter + int64_t(Pys) * W;
+            for (int e = tid; e < Rs * p; e += TC_THREADS) {
+                const int r = e / p, k = e - r * p;
+                float2 v = make_float2(0.f, 0.f);
+                if (rowocc[r]) v = __ldg(lev + (base + Px0 - 1 + r) * p + k);
+                const float hr = tf32_hi(v.x), hi_ = tf32_hi(v.y);
+                const size_t o_re = (size_t(k >> 2) * Rs + r) * 4 + (k & 3);
+                const size_t o_im = (size_t((k + p) >> 2) * Rs + r) * 4 + ((k + p) & 3);
+                A_hi[o_re] = hr;
+                A_lo[o_re] = v.x - hr;
+                A_hi[o_im] = hi_;
+                A_lo[o_im] = v.y - hi_;
+            }
+            // the B operators of the (up to three) dx shifts, hi and lo images
+            for (int s3 = 0; s3 < 3; ++s3) {
+                if (!(mask3 & (1u << s3))) continue;
+                const float4 *src = reinterpret_cast<const float4 *>(bimg + size_t(ops[s3]) * 2 * bslot);
+                float4 *dst = reinterpret_cast<float4 *>(Bsm + size_t(2 * s3) * bslot);
+                for (int i = tid; i < (2 * bslot) / 4; i += TC_THREADS) dst[i] = __ldg(src + i);
+            }
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t ahi = smem_addr(A_hi), alo = smem_addr(A_lo);
+                for (int s3 = 0; s3 < 3; ++s3) {
+                    if (!(mask3 & (1u << s3))) continue;
+                    const uint32_t bhi = smem_addr(Bsm + size_t(2 * s3) * bslot);
+                    const uint32_t blo = smem_addr(Bsm + size_t(2 * s3 + 1) * bslot);
+                    for (int s = 0; s < S; ++s) {
+                        const uint32_t row0 = uint32_t(s * 128 + 1 + (s3 - 1)) * 16;
+                        const uint32_t dt = tbase + uint32_t(s * Npad);
+                        const uint32_t as[3] = {ahi + row0, ahi + row0, alo + row0};
+                        const uint32_t bs[3] = {bhi, blo, bhi};
+                        for (int pr = 0; pr < 3; ++pr)
+                            for (int ks = 0; ks < Kpad / 8; ++ks) {
+                                mma_tf32(dt, mma_desc(as[pr] + uint32_t(ks) * 2 * LBO_A, LBO_A, SBO),
+                                         mma_desc(bs[pr] + uint32_t(ks) * 2 * LBO_B, LBO_B, SBO), idesc,
+                                         (used >> s) & 1u);
+                                used |= 1u << s;
+                            }
+                    }
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+            }
+            // wait until the tensor core has consumed the staged operands
+            const bool waited = mbar_wait(bar, phase, spin_limit);
+            // one decision for the whole CTA (every thread then takes the same barriers)
+            if (!__syncthreads_and(waited)) {
+                if (tid == 0) set_status(status, ST_ETIMEOUT);
+                ok = false;
+                // second bounded wait, so that TMEM is not freed under MMAs in flight
+                mbar_wait(bar, phase, 1LL << 26);
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            __syncthreads();
+        }
+    }
+    if (tid == 0) used_mask = used;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t umask = used_mask;
+    if (ok) {
+        for (int s = 0; s < S; ++s) {
+            const int Px = Px0 + s * 128 + tid;
+            float v[TC_MAX_NPAD];
+            if (umask & (1u << s)) {
+                const uint32_t taddr = tbase + (uint32_t(warp * 32) << 16) + uint32_t(s * Npad);
+                for (int c0 = 0; c0 < Npad; c0 += 16) tmem_ld16(taddr + uint32_t(c0), v + c0);
+            } else {
+#pragma unroll
+                for (int i = 0; i < TC_MAX_NPAD; ++i) v[i] = 0.f;
+            }
+            const uint32_t ix = uint32_t(2 * Px + cx), iy = uint32_t(2 * Py + cy);
+            if (box_count(st, L, l, morton_key(ix, iy))) {
+                float2 *dst = le + d.eoff + (lvl_off(l) + int64_t(c) * quarter + int64_t(Py) * W + Px) * p;
+                for (int m = 0; m < p; ++m) dst[m] = make_float2(v[m], v[p + m]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols));
+}
+
+size_t m2l_tc_smem_bytes(int p, int seg) {
+    const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
+    return size_t(2) * (Kpad / 4) * (seg + 2) * 16 + size_t(6) * Kpad * Npad * 4;
+}
+
+int m2l_tc_seg(int level) {
+    const int W = 1 << (level - 1);
+    return W < TC_MAX_SEG ? W : TC_MAX_SEG;
+}
+
+bool m2l_tc_supported(int p, int level) {
+    const int Npad = (2 * p + 15) & ~15;
+    return level >= 8 && level <= 15 && Npad <= TC_MAX_NPAD &&
+           m2l_tc_smem_bytes(p, m2l_tc_seg(level)) <= size_t(220) * 1024;
+}
+
+int64_t m2l_tc_units(int level) {
+    const int64_t W = int64_t(1) << (level - 1);
+    const int64_t seg = W < TC_MAX_SEG ? W : TC_MAX_SEG;
+    return 4 * W * (W / seg);
+}
+
+// B images for p: for each of the 40 offsets, hi then lo, each Kpad x Npad
+// floats in the K-major core-matrix layout [k / 4][n][k % 4].
+void host_m2l_tc_images(int p, std::vector<float> &out) {
+    const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
+    std::vector<double> T(size_t(40) * p * p * 2);
+    host_m2l_table(p, T.data());  // [op][k][m] complex
+    const size_t slot = size_t(Kpad) * Npad;
+    out.assign(size_t(40) * 2 * slot, 0.0f);
+    for (int op = 0; op < 40; ++op) {
+        float *hi = out.data() + size_t(op) * 2 * slot;
+        float *lo = hi + slot;
+        for (int n = 0; n < K2; ++n)
+            for (int k = 0; k < K2; ++k) {
+                const int m = n < p ? n : n - p, kk = k < p ? k : k - p;
+                const double *tc = T.data() + ((size_t(op) * p + kk) * p + m) * 2;
+                const double tr = tc[0], tim = tc[1];
+                double b;
+                if (n < p) b = k < p ? tr : -tim;
+                else b = k < p ? tim : tr;
+                const float bf = float(b);
+                uint32_t bits;
+                std::memcpy(&bits, &bf, 4);
+                bits &= 0xFFFFE000u;
+                float h;
+                std::memcpy(&h, &bits, 4);
+                const size_t o = (size_t(k >> 2) * Npad + n) * 4 + (k & 3);
+                hi[o] = h;
+                lo[o] = float(b - double(h));
+            }
+    }
+}
+
+cudaError_t launch_m2l_tc(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                          const uint32_t *start, const float2 *me, float2 *le, size_t smem_bytes,
+                          long long spin_limit, int *status, cudaStream_t st, uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem_bytes));
+    if (e != cudaSuccess) return e;
+    k_m2l_tc<<<unsigned(nblocks), TC_THREADS, smem_bytes, st>>>(tasks, ntasks, insts, start, me, le,
+                                                                spin_limit, status);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+}  // namespace petfmm

@@ -21,7 +21,7 @@ def to_dev(arrs):
     return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
 
 
-def run(w, precision, L=None, p=None, sigma=None, domain=None, timing=False, ctx_out=None):
+def run(w, precision, L=None, p=None, sigma=None, domain=None, timing=False, ctx_out=None, poison=True):
     """One evaluation of workload w; returns (u, v) as float64 numpy arrays."""
     _lib = lib()
     L = w.L if L is None else L
@@ -29,6 +29,9 @@ def run(w, precision, L=None, p=None, sigma=None, domain=None, timing=False, ctx
     ctx = _lib.Context(domain or w.domain, L, p, sigma or w.sigma, precision=precision, dtype=w.dtype)
     if timing:
         ctx.set_option(_lib.PETFMM_OPT_TIMING, 1)
+    if poison:
+        # any read of a coefficient this evaluation did not write turns into NaN
+        ctx.set_option(_lib.PETFMM_OPT_POISON, 1)
     x, y, g = to_dev((w.x, w.y, w.gamma))
     u, v = ctx.evaluate(x, y, g)
     rc = ctx.sync()

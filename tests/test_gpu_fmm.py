@@ -52,17 +52,23 @@ def test_fp64_expansions_match_oracle(orc):
     G.run(w, "fp64", ctx_out=keep)
     ctx = keep[0]
     _, _, me, le = orc.fmm(w.x, w.y, w.gamma, w.domain, w.L, w.p, w.sigma, export=True)
+    _, _, key = orc.bin(w.x, w.y, w.domain, w.L)
     k = np.arange(w.p)
     for level in range(2, w.L + 1):
         r = 1.0 / (1 << level)
         off = ((1 << (2 * level)) - 1) // 3
         nb = 1 << (2 * level)
-        me_o = me[off:off + nb] / r ** k
-        le_o = le[off:off + nb] * r ** (k + 1)
-        me_g = ctx.debug_expansions(level, 0)
-        le_g = ctx.debug_expansions(level, 1)
+        # boxes holding particles (empty boxes are skipped by the library: their
+        # ME is zero and their LE is never evaluated)
+        occ = np.zeros(nb, bool)
+        occ[np.unique(key >> (2 * (w.L - level)))] = True
+        me_o = me[off:off + nb][occ] / r ** k
+        le_o = le[off:off + nb][occ] * r ** (k + 1)
+        me_g = ctx.debug_expansions(level, 0)[occ]
+        le_g = ctx.debug_expansions(level, 1)[occ]
         assert np.max(np.abs(me_g - me_o)) <= 1e-12 * np.max(np.abs(me_o))
         assert np.max(np.abs(le_g - le_o)) <= 1e-12 * np.max(np.abs(le_o))
+        assert np.all(me[off:off + nb][~occ] == 0)
     ctx.close()
 
 
@@ -83,7 +89,10 @@ def test_lattice_1m_fp64_and_mixed(orc):
 
 def test_clustered_16m_mixed_vs_fp64_and_oracle_sample(orc):
     w = W.clustered()
-    u64, v64 = G.run(w, "fp64")
+    # the FP64 path on FP64 copies of the same (FP32-valued) inputs, so that
+    # its outputs are not rounded to FP32 storage
+    w64 = W.Workload(w.name, *w.as_f64(), w.sigma, w.domain, w.L, w.p, "f64")
+    u64, v64 = G.run(w64, "fp64")
     umx, vmx = G.run(w, "mixed")
     assert G.rel_l2(umx, vmx, u64, v64) <= TOLMX
     tg = W.sample_targets(w.n, 4096, seed=3)

@@ -1,0 +1,65 @@
+"""The tensor-core M2L (tcgen05, 3xTF32, mixed path, levels >= 8) against
+the FP32 SIMT M2L and the FP64 FMM, for each padded operand shape, plus the
+bounded-wait timeout report."""
+import numpy as np
+import pytest
+
+import gpu_util as G
+from paper_0905_2637_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(w, tc, L=None, p=None):
+    _lib = G.lib()
+    ctx = _lib.Context(w.domain, L or w.L, p or w.p, w.sigma, precision="mixed", dtype=w.dtype)
+    ctx.set_option(_lib.PETFMM_OPT_M2L_TC, 1 if tc else 0)
+    ctx.set_option(_lib.PETFMM_OPT_POISON, 1)
+    x, y, g = G.to_dev((w.x, w.y, w.gamma))
+    u, v = ctx.evaluate(x, y, g)
+    assert ctx.sync() == 0
+    out = u.cpu().numpy().astype(np.float64), v.cpu().numpy().astype(np.float64)
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("p", [8, 12, 17, 24])   # Kpad/Npad = 16/16, 24/32, 40/48, 48/48
+@pytest.mark.parametrize("L,n,frac", [(8, 300_000, 0.0), (9, 400_000, 0.6)])
+def test_tensor_core_m2l_matches_simt_and_fp64(L, n, frac, p):
+    w = W.tiny(n, 31 + L + p, L=L, p=p, clustered_frac=frac)
+    u_tc, v_tc = _run(w, tc=True)
+    u_si, v_si = _run(w, tc=False)
+    u64, v64 = G.run(w, "fp64")
+    assert G.rel_l2(u_tc, v_tc, u64, v64) <= 1e-5
+    assert G.rel_l2(u_tc, v_tc, u_si, v_si) <= 1e-5
+    assert np.all(np.isfinite(u_tc)) and np.all(np.isfinite(v_tc))
+
+
+def test_tensor_core_m2l_far_field_alone(orc):
+    # isolate the far field: subtract the P2P part by comparing two
+    # evaluations whose near fields agree exactly (same particles, same L)
+    # -- here simply check the full result against the oracle FMM at L = 10
+    w = W.tiny(120_000, 77, L=10, p=17, clustered_frac=0.5)
+    u_tc, v_tc = _run(w, tc=True)
+    tg = W.sample_targets(w.n, 2000, seed=5)
+    ur, vr = orc.fmm(w.x, w.y, w.gamma, w.domain, w.L, w.p, w.sigma, targets=tg)
+    assert G.rel_l2(u_tc[tg], v_tc[tg], ur, vr) <= 1e-5
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers():
+    _lib = G.lib()
+    w = W.tiny(200_000, 5, L=8, p=17)
+    ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype="f64")
+    x, y, g = G.to_dev((w.x, w.y, w.gamma))
+    ctx.set_option(_lib.PETFMM_OPT_SPIN_LIMIT, -1)  # first waits get no iterations
+    ctx.evaluate(x, y, g)
+    with pytest.raises(_lib.PetfmmError) as e:
+        ctx.sync()
+    assert e.value.code == _lib.PETFMM_ETIMEOUT
+    ctx.set_option(_lib.PETFMM_OPT_SPIN_LIMIT, 0)
+    u, v = ctx.evaluate(x, y, g)
+    assert ctx.sync() == 0
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    ctx.close()
+    uf, vf = _run(w, tc=True)
+    assert np.array_equal(u, uf) and np.array_equal(v, vf)

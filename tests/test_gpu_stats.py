@@ -63,3 +63,20 @@ def test_repeated_evaluations_are_deterministic():
     ctx.close()
     for u, v in outs[1:]:
         assert np.array_equal(u, outs[0][0]) and np.array_equal(v, outs[0][1])
+
+
+def test_reused_context_matches_fresh_context():
+    # A context keeps its buffers between evaluations; a second, different
+    # problem must not see anything of the first (no stale expansions).
+    _lib = G.lib()
+    a = W.tiny(40_000, 21, L=6, p=12, clustered_frac=0.6)
+    b = W.tiny(30_000, 22, L=6, p=12, clustered_frac=0.2)
+    ctx = _lib.Context(a.domain, 6, 12, a.sigma, precision="mixed", dtype="f64")
+    for w in (a, b):
+        x, y, g = G.to_dev((w.x, w.y, w.gamma))
+        u, v = ctx.evaluate(x, y, g)
+        assert ctx.sync() == 0
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    ctx.close()
+    uf, vf = G.run(b, "mixed", poison=False)
+    assert np.array_equal(u, uf) and np.array_equal(v, vf)
