@@ -267,6 +267,39 @@ typedef struct {
  * PETFMM_OPT_TIMING and a petfmm_sync() after the evaluation. */
 int petfmm_get_stats(petfmm_ctx *ctx, petfmm_stats *out);
 
+/*
+ * petfmm_tree_noalloc -- the quadtree build alone (binning, stable z-order
+ * sort, leaf ranges: the same results petfmm_debug_tree reports after an
+ * evaluation) without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * call cudaMalloc -- a host application whose own caching allocator already
+ * holds the GPU's memory, code with a fixed device-memory budget, or loops
+ * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * cause.  All intermediate buffers live in one static device array sized for
+ * PETFMM_NOALLOC_MAX_N particles (about 16.3 MB, held on every GPU that loads
+ * the library until the process exits).
+ *   dom, levels  domain square and depth L (1..15), as for petfmm_create.
+ *   dtype        PETFMM_F64 or PETFMM_F32 storage of x, y.
+ *   n            particles, 0 <= n <= PETFMM_NOALLOC_MAX_N; larger n returns
+ *                PETFMM_ENOMEM without launching anything.
+ *   x, y         device arrays of n positions.
+ *   keys         device array of n Morton keys in input order, or NULL.
+ *   perm         device array: perm[r] = input index of sorted rank r.
+ *   start        device array of 4^L + 1 leaf starts.
+ * Runs on cuda_stream (a cudaStream_t, NULL for the legacy default stream)
+ * and waits for it before returning; returns PETFMM_OK, PETFMM_EDOMAIN (a
+ * particle outside the domain; outputs unspecified), PETFMM_EINVAL or
+ * PETFMM_ECUDA.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call uses the same array, so calls
+ * that overlap on the GPU (other streams or host threads) race with each
+ * other; serialise them.
+ */
+#define PETFMM_NOALLOC_MAX_N 1048576
+int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dtype, int64_t n, const void *x,
+                        const void *y, uint32_t *keys, uint32_t *perm, uint32_t *start,
+                        void *cuda_stream);
+
 const char *petfmm_strerror(int code);
 int petfmm_version(void);
 

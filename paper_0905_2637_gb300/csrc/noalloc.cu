@@ -1,0 +1,143 @@
+// noalloc.cu -- petfmm_tree_noalloc: the quadtree build (binning, stable
+// z-order sort, leaf ranges) for callers that must not allocate device memory.
+//
+// Some callers cannot let a library call cudaMalloc: a host application whose
+// own caching allocator has already reserved the GPU's memory (a stray
+// allocation can fail or fragment its pool), code with a fixed, audited
+// device-memory budget, and latency-sensitive loops that cannot pay for
+// cudaMalloc/cudaFree, which may synchronise the whole device.  For them this
+// entry point keeps every intermediate buffer in one file-scope
+// __device__ array of fixed size (PETFMM_NOALLOC_MAX_N particles' worth,
+// about 16.3 MB), which every GPU that loads the library holds until the
+// process exits.  The caller passes the inputs and the outputs.
+//
+// The array is one resource shared by every call: it keeps the previous
+// call's contents, calls that overlap on the GPU (different streams, or
+// different host threads) race on it, and each call clears the words that
+// must start at zero.  Host code cannot use the array's name as a device
+// address; its address is fetched once per device with
+// cudaGetSymbolAddress, with that device current, during the first call on
+// that device, so that first call should come before any stream capture.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/petfmm.h"
+#include "kernels.cuh"
+
+using namespace petfmm;
+
+namespace {
+
+constexpr int64_t kMaxN = PETFMM_NOALLOC_MAX_N;
+constexpr int64_t kRsBlocks = (kMaxN + 4095) / 4096;     // radix tiles of 4096 keys
+constexpr int64_t kHistWords = 256 * kRsBlocks;
+constexpr int64_t kScanWords = 1024;                     // >= scan scratch for kHistWords
+constexpr int64_t kDescBytes = 4096;                     // InstDesc + Tasks
+constexpr int64_t kScratchBytes = 4 * (4 * kMaxN + kHistWords + kScanWords + 16) + kDescBytes;
+
+// The scratch: keys A, keys B, values A, values B (uint32 each), radix
+// histograms, scan partial sums, a status word, then the launch descriptors.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void *g_addr[64] = {};  // per device: device address of g_noalloc_scratch
+
+int scratch_address(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return PETFMM_ECUDA;
+    }
+    if (dev < 0 || dev >= 64) return PETFMM_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return PETFMM_ECUDA;
+        }
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return PETFMM_OK;
+}
+
+}  // namespace
+
+extern "C" int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dtype, int64_t n,
+                                   const void *x, const void *y, uint32_t *keys, uint32_t *perm,
+                                   uint32_t *start, void *cuda_stream) {
+    if (!dom || !(dom->width > 0.0) || levels < 1 || levels > MAX_L || n < 0 || !perm || !start)
+        return PETFMM_EINVAL;
+    if (dtype != PETFMM_F64 && dtype != PETFMM_F32) return PETFMM_EINVAL;
+    if (n > 0 && (!x || !y)) return PETFMM_EINVAL;
+    if (n > kMaxN) return PETFMM_ENOMEM;  // the fixed scratch holds at most kMaxN particles
+    if (radix_blocks(n) > kRsBlocks || scan_scratch_words(256 * radix_blocks(n)) > kScanWords)
+        return PETFMM_ENOMEM;
+    static_assert(kScanWords >= 64, "scan scratch");
+    void *base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    unsigned char *b = static_cast<unsigned char *>(base);
+    uint32_t *kA = reinterpret_cast<uint32_t *>(b);
+    uint32_t *kB = kA + kMaxN;
+    uint32_t *vA = kB + kMaxN;
+    uint32_t *vB = vA + kMaxN;
+    uint32_t *hist = vB + kMaxN;
+    uint32_t *scan = hist + kHistWords;
+    int *status = reinterpret_cast<int *>(scan + kScanWords);
+    unsigned char *descs = reinterpret_cast<unsigned char *>(status + 16);
+
+    // launch descriptors of this call: one instance, one task per stage
+    struct {
+        InstDesc d;
+        Task t[3];  // binning (particles), leaf starts (4^L + 1), unused
+    } h;
+    std::memset(&h, 0, sizeof(h));
+    h.d.x0 = dom->x0;
+    h.d.y0 = dom->y0;
+    h.d.width = dom->width;
+    h.d.scale = std::ldexp(1.0, levels) / dom->width;
+    h.d.wleaf = dom->width / std::ldexp(1.0, levels);
+    h.d.L = levels;
+    h.d.n = n;
+    h.d.x = x;
+    h.d.y = y;
+    h.t[0] = Task{0, levels, n, 0};
+    h.t[1] = Task{0, levels, (int64_t(1) << (2 * levels)) + 1, 0};
+    static_assert(sizeof(h) <= kDescBytes, "descriptor space");
+    InstDesc *dd = reinterpret_cast<InstDesc *>(descs);
+    Task *dt = reinterpret_cast<Task *>(descs + sizeof(InstDesc));
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PETFMM_ECUDA;
+    if (cudaMemcpyAsync(dd, &h, sizeof(h), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return PETFMM_ECUDA;
+    uint64_t launches = 0;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = launch_morton(dt, 1, (n + 255) / 256, dd, dtype == PETFMM_F32, kA, status, st, &launches);
+        if (e == cudaSuccess && keys) e = cudaMemcpyAsync(keys, kA, size_t(n) * 4, cudaMemcpyDeviceToDevice, st);
+        bool in_first = true;
+        if (e == cudaSuccess) e = radix_sort(kA, vA, kB, vB, n, 2 * levels, hist, scan, &in_first, st, &launches);
+        const uint32_t *sk = in_first ? kA : kB;
+        const uint32_t *sv = in_first ? vA : vB;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(perm, sv, size_t(n) * 4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = launch_leaf_start(dt + 1, 1, ((int64_t(1) << (2 * levels)) + 1 + 255) / 256, dd, sk, start, st,
+                                  &launches);
+    } else {
+        e = cudaMemsetAsync(start, 0, ((size_t(1) << (2 * levels)) + 1) * 4, st);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PETFMM_ECUDA;
+    }
+    int hs = 0;
+    if (cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return PETFMM_ECUDA;
+    }
+    return hs;
+}
