@@ -176,6 +176,91 @@ def cpu_baseline():
                       f"p={w.p}, same recipe and blobs per leaf; {dt:.1f} s wall"}
 
 
+def serving_leg(_lib, n_req=48, seed=5):
+    """Poisson arrivals (mean 200/s) of requests of 5 midpoint-RK2 steps
+    (10 evaluations) each, N log-uniform in [4e3, 4e6], Gaussian-patch
+    lattice or clustered layout, p in {8, 17}, mixed precision, admitted under
+    a 150 GB HBM budget.  Returns latency percentiles and throughput."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n_req):
+        n = int(np.exp(rng.uniform(np.log(4e3), np.log(4e6))))
+        p = int(rng.choice([8, 17]))
+        if rng.uniform() < 0.5:
+            side = max(8, int(round(np.sqrt(n))))
+            w = W.lattice(side=side, seed=seed * 1000 + i, p=p)
+            dt = 0.05
+        else:
+            w = W.clustered(n=n, seed=seed * 1000 + i, p=p, dtype="f64")
+            dt = 0.02
+        x, y, g = w.as_f64()
+        # the configured tree depth: about 16 blobs per leaf, as at the
+        # lattice and clustered configurations
+        levels = int(min(12, max(2, round(np.log(max(n, 16) / 16.0) / np.log(4.0)))))
+        reqs.append((x, y, g, w.sigma, p, dt, levels))
+    gaps = rng.exponential(1.0 / 200.0, n_req)
+    srv = _lib.Server(150 * (1 << 30), max_slots=64, max_queue=4096)
+    t0 = time.perf_counter()
+    tickets = []
+    due = 0.0
+    for (x, y, g, s, p, dt, levels), gap in zip(reqs, gaps):
+        due += gap
+        now = time.perf_counter() - t0
+        if due > now:
+            time.sleep(due - now)
+        tickets.append(srv.submit(x, y, g, s, p, dt, 5, levels=levels, precision="mixed"))
+    done = {}
+    while len(done) < len(tickets):
+        for t in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([done[t]["latency_ms"] for t in tickets])
+    ok = sum(done[t]["status"] == 0 for t in tickets)
+    evals = sum(r[0].size for r in reqs) * 10
+    return {"requests": n_req, "ok": int(ok), "arrival_rate_per_s": 200.0,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "makespan_s": makespan,
+            "particles_per_s": evals / makespan,
+            "offered_particle_evals_per_s": evals / max(float(np.sum(gaps)), 1e-9),
+            "layout": "Gaussian-patch lattice or 8-cluster, N log-uniform [4e3, 4e6], p in {8, 17}, "
+                      "L = round(log4(N / 16)), "
+                      "5 midpoint-RK2 steps, 150 GB budget"}
+
+
+def batch_leg(_lib, torch, stream, steps=5):
+    """512 independent instances (N log-uniform in [1e3, 2^18], uniform, sigma =
+    0.5/sqrt(N), p in {8, 12, 17}) in one batched evaluation; L chosen by the
+    work model."""
+    ws = W.batch(n_inst=512, seed=1, dtype="f32")
+    ctx = _lib.Context((0, 0, 1), 2, 8, 0.01, precision="mixed", dtype="f32", stream=stream)
+    insts = []
+    with torch.cuda.stream(stream):
+        for w in ws:
+            x, y, g = (torch.from_numpy(a).cuda() for a in (w.x, w.y, w.gamma))
+            insts.append(dict(domain=w.domain, levels=0, order=w.p, sigma=w.sigma, x=x, y=y, gamma=g,
+                              u=torch.empty_like(x), v=torch.empty_like(x)))
+    torch.cuda.synchronize()
+    for _ in range(2):
+        ctx.evaluate_batch(insts)
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.evaluate_batch(insts)
+    e1.record(stream)
+    ctx.sync()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    ctx.close()
+    n = sum(w.n for w in ws)
+    return {"instances": 512, "particles": n, "ms_per_batch": 1e3 * t, "instances_per_s": 512 / t,
+            "particles_per_s": n / t}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,6 +269,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--workload", default="clustered-16M",
+                    choices=["clustered-16M", "clustered-4M", "lattice-1M"],
+                    help="clustered-4M (2^22 blobs, L = 9, same blobs per leaf) and lattice-1M "
+                         "(every leaf occupied) are the small cases used for ncu captures")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -204,7 +295,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    w = W.clustered()
+    if args.workload == "clustered-16M":
+        w = W.clustered()
+    elif args.workload == "clustered-4M":
+        w = W.clustered(n=1 << 22, L=9, name="clustered-4M")
+    else:
+        w = W.lattice(dtype="f32")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         x, y, g = (torch.from_numpy(a).cuda() for a in (w.x, w.y, w.gamma))
@@ -314,6 +410,12 @@ def main():
                 "p2p_load_balance": stats["p2p_load_balance"],
                 "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
                 "gpu": torch.cuda.get_device_name()}
+        if args.workload != "clustered-16M":
+            line["config"]["workload"] = w.name + " (profiling case)"
+        if not args.no_batch:
+            line["batch"] = batch_leg(_lib, torch, stream)
+        if not args.no_serve:
+            line["serving"] = serving_leg(_lib)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -242,8 +242,15 @@ enum {
     PETFMM_OPT_POISON = 4,     /* 1: fill the expansion buffers with NaN bytes before each
                                   evaluation (testing: a read of a never-written
                                   coefficient then shows up as NaN in u, v) */
-    PETFMM_OPT_M2L_TC = 5      /* mixed path: 1 (default) M2L of levels >= 8 on the tensor
+    PETFMM_OPT_M2L_TC = 5,     /* mixed path: 1 (default) M2L of levels >= 8 on the tensor
                                   cores (3xTF32), 0 all levels on the FP32 SIMT kernel */
+    PETFMM_OPT_TC_DENSE = 6,   /* percent (0..100, default 25) of a tensor-core unit's
+                                  targets that must hold particles for the unit to run
+                                  on the tensor cores; sparser units use the SIMT kernel */
+    PETFMM_OPT_P2P_PACKED = 7, /* mixed path: 1 P2P with the two targets of a lane in
+                                  packed FP32x2 instructions, 0 (default) the scalar kernel */
+    PETFMM_OPT_TC_SEG = 8      /* widest tensor-core M2L unit in parent cells: 128
+                                  (default), 256 or 512 */
 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
 

@@ -52,6 +52,10 @@ struct InstDesc {
     void *u, *v;
     const void *t_m2m, *t_l2l, *t_m2l;  // operator tables for this p (path's real type)
     const void *t_m2l_tc;               // tensor-core M2L operator images (mixed path)
+    int64_t tc_unit0[MAX_L + 1];        // per level: first unit of this (instance, level)
+                                        // in the tensor-core M2L launch, or -1
+    int tc_segmax;                      // widest tensor-core unit (parent cells)
+    int tc_pad;
     // mixed-precision P2P constants (leaf units)
     float kappa;            // w^2 / (2 sigma^2): q = kappa * rho^2
     float cnear;            // w / (4 pi sigma^2)
@@ -156,6 +160,40 @@ __host__ __device__ __forceinline__ int m2l_op_index(int dx, int dy) {
     const int base = dy <= -1 ? 7 * (dy + 3) : (dy <= 2 ? 14 + 4 * (dy + 1) : 33);
     const int pos = (dy >= -1 && dy <= 1) ? (dx < 0 ? dx + 3 : dx) : dx + 3;
     return base + pos;
+}
+
+// Tensor-core M2L units: at level l (parent grid W = 2^(l-1) per side) a unit
+// is a segment of SEG = min(W, segmax) parent cells of one parent row, for one
+// target child class c; units are numbered ((c W) + Py) (W / SEG) + segment.
+// segmax is 128, 256 or 512 (InstDesc::tc_segmax).
+constexpr int TC_MAX_SEG = 512;
+
+__host__ __device__ __forceinline__ int tc_seg(int l, int segmax) {
+    const int W = 1 << (l - 1);
+    return W < segmax ? W : segmax;
+}
+
+__host__ __device__ __forceinline__ void tc_unit_decode(int l, int segmax, int64_t unit, int *c,
+                                                        int *Py, int *Px0, int *seg) {
+    const int W = 1 << (l - 1);
+    const int s = tc_seg(l, segmax), nseg = W / s;
+    *seg = s;
+    *c = int(unit / (int64_t(W) * nseg));
+    const int64_t rem = unit - int64_t(*c) * W * nseg;
+    *Py = int(rem / nseg);
+    *Px0 = int(rem - int64_t(*Py) * nseg) * s;
+}
+
+__host__ __device__ __forceinline__ int64_t tc_unit_of(int l, int segmax, int c, int Py, int Px) {
+    const int W = 1 << (l - 1);
+    const int s = tc_seg(l, segmax), nseg = W / s;
+    return (int64_t(c) * W + Py) * nseg + Px / s;
+}
+
+// A unit goes to the tensor cores when at least dense_pct percent of its
+// targets hold particles; the SIMT kernel takes the boxes of the others.
+__host__ __device__ __forceinline__ bool tc_unit_dense(uint32_t count, int seg, int dense_pct) {
+    return count > 0 && 100u * count >= uint32_t(dense_pct) * uint32_t(seg);
 }
 
 // Interaction-list table: for child class c, the 27 (dx, dy) offsets of the

@@ -99,11 +99,17 @@ struct petfmm_ctx {
     int p2p_mode = 1;
     bool poison = false;
     bool m2l_tc = true;
+    // measured on GB300 (clustered 16M and lattice 1M blobs): 128-cell units
+    // with a 25% occupancy threshold gave the fastest M2L on both; the packed
+    // FP32x2 P2P was 15% slower than the scalar kernel, so it is off
+    int tc_dense_pct = 25;
+    int tc_segmax = 128;
+    bool p2p_packed = false;
     int64_t spin_limit = 0;
     uint64_t launches = 0, evaluations = 0;
 
     DevBuf keysA, keysB, valsA, valsB, hist, scratch, start, xs, ys, gs, rec, me, le, cnt, off,
-        items, ctrl, plan_dev, busy;
+        items, ctrl, plan_dev, busy, ucount, src2, gam2;
     DevBuf hx, hy, hg, hu, hv;  // device staging for petfmm_evaluate_host
     std::map<int, OpTables> tables;
 
@@ -228,6 +234,26 @@ void fill_p2p_constants(InstDesc &d) {
     d.inv2s2 = 1.0 / (2.0 * d.sigma * d.sigma);
     d.cnear64 = 1.0 / (2.0 * M_PI);
     d.cfar64 = 1.0 / (2.0 * M_PI * w);
+    // The fit depends on kappa alone; evaluations of the same problem shape
+    // (a served request's every round, a repeated batch) reuse it.
+    struct Fit {
+        int general, deg;
+        float split;
+        float poly[POLY_MAX + 1];
+    };
+    static std::mutex mu;
+    static std::map<double, Fit> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(kappa);
+        if (it != cache.end()) {
+            d.general = it->second.general;
+            d.deg = it->second.deg;
+            d.qsplit_rho2 = it->second.split;
+            std::memcpy(d.poly, it->second.poly, sizeof(d.poly));
+            return;
+        }
+    }
     // near pairs are at most 2 leaf widths apart per axis: rho^2 <= 8
     const double rho2max = 8.0 * (1.0 + 1e-6);
     const double qmax = kappa * rho2max;
@@ -240,6 +266,14 @@ void fill_p2p_constants(InstDesc &d) {
         d.deg = fit_near_poly(1.0, kappa, d.poly);
         d.qsplit_rho2 = float(1.0 / kappa);
     }
+    Fit f;
+    f.general = d.general;
+    f.deg = d.deg;
+    f.split = d.qsplit_rho2;
+    std::memcpy(f.poly, d.poly, sizeof(f.poly));
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() > 4096) cache.clear();
+    cache[kappa] = f;
 }
 
 OpTables *get_tables(petfmm_ctx *c, int p, int *err) {
@@ -284,7 +318,8 @@ void flatten_tasks(Plan &pl) {
     for (TaskRange &r : pl.l2l) put(r);
 }
 
-int build_plan(int precision, bool use_tc, const std::vector<Problem> &probs, Plan &pl) {
+int build_plan(int precision, bool use_tc, int tc_segmax, const std::vector<Problem> &probs,
+               Plan &pl) {
     pl = Plan();
     const int ni = int(probs.size());
     int inst_bits = 0;
@@ -341,20 +376,25 @@ int build_plan(int precision, bool use_tc, const std::vector<Problem> &probs, Pl
     const int tpi = precision == PETFMM_MIXED ? P2P_TPI_MIXED : P2P_TPI_F64;
     int64_t items_cap = 0;
     for (int i = 0; i < ni; ++i) {
-        const InstDesc &d = pl.inst[i];
+        InstDesc &d = pl.inst[i];
         const int64_t nleaf = int64_t(1) << (2 * d.L);
+        for (int l = 0; l <= MAX_L; ++l) d.tc_unit0[l] = -1;
+        d.tc_segmax = tc_segmax;
         add_task(pl.morton, i, d.L, d.n, 256);
         add_task(pl.start, i, d.L, nleaf + 1, 256);
         add_task(pl.particles, i, d.L, d.n, 256);
         add_task(pl.leaves_p2m, i, d.L, nleaf, P2M_WARPS);
         add_task(pl.leaves_wl, i, d.L, nleaf, 256);
         for (int l = 2; l <= d.L; ++l) {
-            if (precision == PETFMM_MIXED && use_tc && m2l_tc_supported(d.p, l)) {
-                add_task(pl.m2l_tc, i, l, m2l_tc_units(l), 1);
-                pl.tc_smem = std::max(pl.tc_smem, m2l_tc_smem_bytes(d.p, m2l_tc_seg(l)));
-            } else {
-                add_task(pl.m2l, i, l, int64_t(1) << (2 * l), M2L_WARPS);
+            // levels the tensor cores can take get both launches: the tensor
+            // cores translate the dense units, the SIMT kernel the boxes of the
+            // sparse ones (a data-dependent split made on the device)
+            if (precision == PETFMM_MIXED && use_tc && m2l_tc_supported(d.p, l, tc_segmax)) {
+                d.tc_unit0[l] = pl.m2l_tc.nblocks;  // one unit per block
+                add_task(pl.m2l_tc, i, l, m2l_tc_units(l, tc_segmax), 1);
+                pl.tc_smem = std::max(pl.tc_smem, m2l_tc_smem_bytes(d.p, m2l_tc_seg(l, tc_segmax)));
             }
+            add_task(pl.m2l, i, l, int64_t(1) << (2 * l), M2L_WARPS);
         }
         items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
     }
@@ -448,7 +488,7 @@ void stage_mark(petfmm_ctx *c, int stage) {
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     Plan &pl = c->plan;
-    PF_TRY(build_plan(c->precision, c->m2l_tc, probs, pl));
+    PF_TRY(build_plan(c->precision, c->m2l_tc, c->tc_segmax, probs, pl));
     PF_TRY(attach_tables(c, pl));
     cudaStream_t st = c->stream;
     const bool mixed = c->precision == PETFMM_MIXED;
@@ -473,6 +513,10 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->start, size_t(pl.nstart) * 4, st));
     if (mixed) {
         PF_TRY(ensure(c->rec, size_t(N) * sizeof(float4), st));
+        if (c->p2p_packed) {
+            PF_TRY(ensure(c->src2, size_t(N) * sizeof(float4), st));
+            PF_TRY(ensure(c->gam2, size_t(N) * sizeof(float2), st));
+        }
         PF_TRY(ensure(c->me, size_t(pl.ncoef) * sizeof(float2), st));
         PF_TRY(ensure(c->le, size_t(pl.ncoef) * sizeof(float2), st));
     } else {
@@ -485,7 +529,9 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->cnt, size_t(pl.nleaves) * 4, st));
     PF_TRY(ensure(c->off, size_t(pl.nleaves) * 4, st));
     PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
-    const int grid = p2p_grid(mixed, pl.deg, pl.general);
+    PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks) * sizeof(uint32_t), st));
+    const bool packed = mixed && c->p2p_packed;
+    const int grid = p2p_grid(mixed, pl.deg, pl.general, packed);
     if (grid <= 0) return PETFMM_EINVAL;
     c->p2p_grid = grid;
     unsigned long long *busy = nullptr;
@@ -529,7 +575,9 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     if (mixed)
         PF_CUDA(launch_gather_mixed(dtask + pl.particles.first, pl.particles.count,
                                     pl.particles.nblocks, dinst, f32, perm, skeys,
-                                    static_cast<float4 *>(c->rec.p), st, lc));
+                                    static_cast<float4 *>(c->rec.p),
+                                    packed ? static_cast<float4 *>(c->src2.p) : nullptr,
+                                    packed ? static_cast<float2 *>(c->gam2.p) : nullptr, st, lc));
     else
         PF_CUDA(launch_gather_f64(dtask + pl.particles.first, pl.particles.count,
                                   pl.particles.nblocks, dinst, f32, perm,
@@ -558,23 +606,31 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                                        static_cast<double2 *>(c->me.p), st, lc));
     }
     stage_mark(c, PETFMM_STAGE_M2L);
+    uint32_t *ucount = nullptr;
+    if (pl.m2l_tc.count) {
+        ucount = static_cast<uint32_t *>(c->ucount.p);
+        PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc.first, pl.m2l_tc.count, pl.m2l_tc.nblocks,
+                                     dinst, start, ucount, st, lc));
+    }
     if (pl.m2l.count) {
         if (mixed)
             PF_CUDA(launch_m2l<float>(dtask + pl.m2l.first, pl.m2l.count, pl.m2l.nblocks, dinst,
                                       start, static_cast<const float2 *>(c->me.p),
-                                      static_cast<float2 *>(c->le.p), st, lc));
+                                      static_cast<float2 *>(c->le.p), ucount, c->tc_dense_pct,
+                                      st, lc));
         else
             PF_CUDA(launch_m2l<double>(dtask + pl.m2l.first, pl.m2l.count, pl.m2l.nblocks, dinst,
                                        start, static_cast<const double2 *>(c->me.p),
-                                       static_cast<double2 *>(c->le.p), st, lc));
+                                       static_cast<double2 *>(c->le.p), nullptr, 0, st, lc));
     }
     if (pl.m2l_tc.count) {
         // spin_limit < 0: zero-iteration budget (tests the timeout report)
         const long long spin = c->spin_limit > 0 ? c->spin_limit : c->spin_limit < 0 ? 0 : (1LL << 26);
         PF_CUDA(launch_m2l_tc(dtask + pl.m2l_tc.first, pl.m2l_tc.count, pl.m2l_tc.nblocks, dinst,
                               start, static_cast<const float2 *>(c->me.p),
-                              static_cast<float2 *>(c->le.p), pl.tc_smem, spin,
-                              reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
+                              static_cast<float2 *>(c->le.p), ucount, c->tc_dense_pct,
+                              pl.tc_smem, spin, reinterpret_cast<int *>(ctrl + CTRL_STATUS), st,
+                              lc));
     }
     stage_mark(c, PETFMM_STAGE_L2L);
     for (const TaskRange &tr : pl.l2l) {
@@ -595,6 +651,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     if (mixed)
         PF_CUDA(launch_p2p_mixed(grid, pl.deg, pl.general, static_cast<const uint4 *>(c->items.p),
                                  ctrl, dinst, start, static_cast<const float4 *>(c->rec.p),
+                                 packed ? static_cast<const float4 *>(c->src2.p) : nullptr,
+                                 packed ? static_cast<const float2 *>(c->gam2.p) : nullptr,
                                  static_cast<const float2 *>(c->le.p), f32, busy, st, lc));
     else
         PF_CUDA(launch_p2p_f64(grid, static_cast<const uint4 *>(c->items.p), ctrl, dinst, start,
@@ -679,7 +737,7 @@ int petfmm_destroy(petfmm_ctx *c) {
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                       &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
-                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->hx, &c->hy,
+                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->src2, &c->gam2, &c->hx, &c->hy,
                       &c->hg, &c->hu, &c->hv};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -775,7 +833,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     int rc = problems_from(n_inst, inst, probs);
     if (rc) return rc;
     Plan pl;
-    rc = build_plan(precision, true, probs, pl);
+    rc = build_plan(precision, true, TC_MAX_SEG, probs, pl);
     if (rc) return rc;
     int n = 0;
     auto emit = [&](int64_t id, const TaskRange &r) {
@@ -834,6 +892,12 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
         case PETFMM_OPT_P2P_MODE: if (value < 0 || value > 1) return PETFMM_EINVAL; c->p2p_mode = int(value); return PETFMM_OK;
         case PETFMM_OPT_POISON: c->poison = value != 0; return PETFMM_OK;
         case PETFMM_OPT_M2L_TC: c->m2l_tc = value != 0; return PETFMM_OK;
+        case PETFMM_OPT_P2P_PACKED: c->p2p_packed = value != 0; return PETFMM_OK;
+        case PETFMM_OPT_TC_SEG:
+            if (value != 128 && value != 256 && value != 512) return PETFMM_EINVAL;
+            c->tc_segmax = int(value);
+            return PETFMM_OK;
+        case PETFMM_OPT_TC_DENSE: if (value < 0 || value > 100) return PETFMM_EINVAL; c->tc_dense_pct = int(value); return PETFMM_OK;
         default: return PETFMM_EINVAL;
     }
 }

@@ -404,7 +404,9 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
                                                         const InstDesc *__restrict__ insts,
                                                         const uint32_t *__restrict__ start,
                                                         const typename Cplx<R>::T *__restrict__ me,
-                                                        typename Cplx<R>::T *__restrict__ le) {
+                                                        typename Cplx<R>::T *__restrict__ le,
+                                                        const uint32_t *__restrict__ ucount,
+                                                        int dense_pct) {
     using C2 = typename Cplx<R>::T;
     __shared__ C2 sa[M2L_WARPS][MAX_P];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -419,6 +421,11 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
     const uint32_t *st = start + d.soff;
     if (!box_count(st, d.L, l, morton_key(uint32_t(ix), uint32_t(iy)))) return;
     const int c = (ix & 1) | ((iy & 1) << 1);
+    if (d.tc_unit0[l] >= 0) {
+        // this level also runs on the tensor cores: leave the dense units to them
+        const int64_t u = d.tc_unit0[l] + tc_unit_of(l, d.tc_segmax, c, iy >> 1, ix >> 1);
+        if (tc_unit_dense(ucount[u], tc_seg(l, d.tc_segmax), dense_pct)) return;
+    }
     const C2 *tab = static_cast<const C2 *>(d.t_m2l);
     const C2 *lev = me + d.eoff + lvl_off(l) * p;
     C2 acc0 = mk2<R>(R(0), R(0)), acc1 = mk2<R>(R(0), R(0));
@@ -448,9 +455,11 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
 template <typename R>
 cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                        const uint32_t *start, const typename Cplx<R>::T *me,
-                       typename Cplx<R>::T *le, cudaStream_t st, uint64_t *launches) {
+                       typename Cplx<R>::T *le, const uint32_t *ucount, int dense_pct,
+                       cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    k_m2l<R><<<unsigned(nblocks), M2L_WARPS * 32, 0, st>>>(tasks, ntasks, insts, start, me, le);
+    k_m2l<R><<<unsigned(nblocks), M2L_WARPS * 32, 0, st>>>(tasks, ntasks, insts, start, me, le,
+                                                          ucount, dense_pct);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
@@ -472,10 +481,10 @@ template cudaError_t launch_l2l<double>(const Task *, int, int64_t, const InstDe
 template cudaError_t launch_l2l<float>(const Task *, int, int64_t, const InstDesc *,
                                        const uint32_t *, float2 *, cudaStream_t, uint64_t *);
 template cudaError_t launch_m2l<double>(const Task *, int, int64_t, const InstDesc *,
-                                        const uint32_t *, const double2 *, double2 *, cudaStream_t,
-                                        uint64_t *);
+                                        const uint32_t *, const double2 *, double2 *,
+                                        const uint32_t *, int, cudaStream_t, uint64_t *);
 template cudaError_t launch_m2l<float>(const Task *, int, int64_t, const InstDesc *,
-                                       const uint32_t *, const float2 *, float2 *, cudaStream_t,
-                                       uint64_t *);
+                                       const uint32_t *, const float2 *, float2 *,
+                                       const uint32_t *, int, cudaStream_t, uint64_t *);
 
 }  // namespace petfmm

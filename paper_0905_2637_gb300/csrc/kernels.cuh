@@ -39,10 +39,12 @@ cudaError_t launch_leaf_start(const Task *tasks, int ntasks, int64_t nblocks, co
 cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                               int dtype_f32, const uint32_t *perm, double *xs, double *ys,
                               double *gs, cudaStream_t st, uint64_t *launches);
+// rec = (xi, eta, gamma, caller index); if src2/gam2 are non-null also the
+// pre-broadcast source copies (-xi, -xi, eta, eta) and (gamma, gamma).
 cudaError_t launch_gather_mixed(const Task *tasks, int ntasks, int64_t nblocks,
                                 const InstDesc *insts, int dtype_f32, const uint32_t *perm,
-                                const uint32_t *skeys, float4 *rec, cudaStream_t st,
-                                uint64_t *launches);
+                                const uint32_t *skeys, float4 *rec, float4 *src2, float2 *gam2,
+                                cudaStream_t st, uint64_t *launches);
 
 // ---- expansions.cu ---------------------------------------------------------
 // Operator tables for p (FP64 build, also rounded to FP32), device-resident.
@@ -72,10 +74,13 @@ template <typename R>
 cudaError_t launch_m2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                        const uint32_t *start, typename Cplx<R>::T *me, cudaStream_t st,
                        uint64_t *launches);
+// For levels that also have tensor-core units (InstDesc::tc_unit0 >= 0) the
+// SIMT M2L skips the boxes of dense units (ucount, dense_pct).
 template <typename R>
 cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                        const uint32_t *start, const typename Cplx<R>::T *me,
-                       typename Cplx<R>::T *le, cudaStream_t st, uint64_t *launches);
+                       typename Cplx<R>::T *le, const uint32_t *ucount, int dense_pct,
+                       cudaStream_t st, uint64_t *launches);
 template <typename R>
 cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                        const uint32_t *start, typename Cplx<R>::T *le, cudaStream_t st,
@@ -84,13 +89,20 @@ cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const Ins
 // ---- m2l_tc.cu -------------------------------------------------------------
 // Tensor-core M2L (mixed path) for levels with at least 128 parent cells per
 // row and p <= 24: one CTA per (target class, parent row, segment) unit.
-bool m2l_tc_supported(int p, int level);
-int64_t m2l_tc_units(int level);
+bool m2l_tc_supported(int p, int level, int segmax);
+int64_t m2l_tc_units(int level, int segmax);
 size_t m2l_tc_smem_bytes(int p, int seg);
-int m2l_tc_seg(int level);
+int m2l_tc_seg(int level, int segmax);
 void host_m2l_tc_images(int p, std::vector<float> &out);
+// ucount[u] = targets holding particles in unit u of the tensor-core launch.
+cudaError_t launch_tc_unit_count(const Task *tasks, int ntasks, int64_t nunits,
+                                 const InstDesc *insts, const uint32_t *start, uint32_t *ucount,
+                                 cudaStream_t st, uint64_t *launches);
+// Dense units (tc_unit_dense) on the tensor cores; the SIMT launch covers the
+// boxes of the other units of the same levels.
 cudaError_t launch_m2l_tc(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                          const uint32_t *start, const float2 *me, float2 *le, size_t smem_bytes,
+                          const uint32_t *start, const float2 *me, float2 *le,
+                          const uint32_t *ucount, int dense_pct, size_t smem_bytes,
                           long long spin_limit, int *status, cudaStream_t st, uint64_t *launches);
 
 // units of work per block of each expansion kernel (the host plans with them)
@@ -111,11 +123,14 @@ cudaError_t launch_p2p_f64(int grid, const uint4 *items, uint32_t *ctrl, const I
                            const double *gs, const uint32_t *perm, const double2 *le,
                            int dtype_f32, unsigned long long *busy, cudaStream_t st,
                            uint64_t *launches);
+// src2/gam2 non-null: the FP32x2-packed variant (sources pre-broadcast by the
+// gather); null: the scalar variant.
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
                              const InstDesc *insts, const uint32_t *start, const float4 *rec,
-                             const float2 *le, int dtype_f32, unsigned long long *busy,
-                             cudaStream_t st, uint64_t *launches);
-int p2p_grid(int precision_mixed, int deg, int general);
+                             const float4 *src2, const float2 *gam2, const float2 *le,
+                             int dtype_f32, unsigned long long *busy, cudaStream_t st,
+                             uint64_t *launches);
+int p2p_grid(int precision_mixed, int deg, int general, int packed);
 constexpr int P2P_TPI_F64 = 32;
 constexpr int P2P_TPI_MIXED = 64;
 

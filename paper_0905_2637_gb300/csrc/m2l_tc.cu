@@ -37,7 +37,6 @@ namespace petfmm {
 #define PF_LAUNCHED(n) do { if (launches) *launches += (n); } while (0)
 
 constexpr int TC_THREADS = 128;
-constexpr int TC_MAX_SEG = 512;
 constexpr int TC_MAX_NPAD = 48;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -90,10 +89,37 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Counts, for every unit of the tensor-core launch (index = the launch's block
+// index), how many of its targets hold particles; one warp per unit.  The
+// tensor cores take the dense units, the SIMT kernel the boxes of the others.
+__global__ void __launch_bounds__(256) k_tc_unit_count(const Task *__restrict__ tasks, int ntasks,
+                                                       const InstDesc *__restrict__ insts,
+                                                       const uint32_t *__restrict__ start,
+                                                       uint32_t *__restrict__ ucount,
+                                                       int64_t nunits) {
+    const int64_t u = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= nunits) return;
+    const Task t = tasks[find_task(tasks, ntasks, u)];
+    const InstDesc &d = insts[t.inst];
+    const int l = t.level;
+    int c, Py, Px0, SEG;
+    tc_unit_decode(l, d.tc_segmax, u - t.block0, &c, &Py, &Px0, &SEG);
+    const uint32_t *st = start + d.soff;
+    uint32_t cnt = 0;
+    for (int i = lane; i < SEG; i += 32) {
+        const uint32_t ix = uint32_t(2 * (Px0 + i) + (c & 1)), iy = uint32_t(2 * Py + (c >> 1));
+        cnt += box_count(st, d.L, l, morton_key(ix, iy)) != 0;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if (lane == 0) ucount[u] = cnt;
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
     const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const float2 *__restrict__ me, float2 *__restrict__ le,
-    long long spin_limit, int *status) {
+    const uint32_t *__restrict__ ucount, int dense_pct, long long spin_limit, int *status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
@@ -106,24 +132,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
     const InstDesc &d = insts[t.inst];
     const int l = t.level, L = d.L, p = d.p;
     const int W = 1 << (l - 1);
-    const int SEG = W < TC_MAX_SEG ? W : TC_MAX_SEG;
-    const int nseg = W / SEG;
+    int c, Py, Px0, SEG;
+    tc_unit_decode(l, d.tc_segmax, int64_t(blockIdx.x) - t.block0, &c, &Py, &Px0, &SEG);
     const int S = SEG / 128;
-    const int64_t unit = int64_t(blockIdx.x) - t.block0;
-    const int c = int(unit / (int64_t(W) * nseg));
-    const int64_t rem = unit - int64_t(c) * W * nseg;
-    const int Py = int(rem / nseg);
-    const int Px0 = int(rem - int64_t(Py) * nseg) * SEG;
     const int cx = c & 1, cy = c >> 1;
     const uint32_t *st = start + d.soff;
 
-    // 1. skip the unit if none of its targets holds particles
-    bool any = false;
-    for (int i = tid; i < SEG; i += TC_THREADS) {
+    // 1. sparse units are left to the SIMT kernel (same test there)
+    if (!tc_unit_dense(ucount[blockIdx.x], SEG, dense_pct)) return;
+    // which 128-target sub-tiles hold particles (empty ones issue no MMA)
+    uint32_t sub_mask = 0;
+    for (int s = 0; s < S; ++s) {
+        const int i = s * 128 + tid;
         const uint32_t ix = uint32_t(2 * (Px0 + i) + cx), iy = uint32_t(2 * Py + cy);
-        any |= box_count(st, L, l, morton_key(ix, iy)) != 0;
+        if (__syncthreads_or(box_count(st, L, l, morton_key(ix, iy)) != 0)) sub_mask |= 1u << s;
     }
-    if (!__syncthreads_or(any)) return;
 
     const int K2 = 2 * p;
     const int Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
@@ -195,19 +218,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
                 anyr |= o;
             }
             if (!__syncthreads_or(anyr)) continue;
-            // stage the strip: real parts at k < p, imaginary parts at p <= k < 2p
-            const int64_t base = int64_t(cs) * quarter + int64_t(Pys) * W;
-            for (int e = tid; e < Rs * p; e += TC_THREADS) {
-                const int r = e / p, k = e - r * p;
-                float2 v = make_float2(0.f, 0.f);
-                if (rowocc[r]) v = __ldg(lev + (base + Px0 - 1 + r) * p + k);
-                const float hr = tf32_hi(v.x), hi_ = tf32_hi(v.y);
-                const size_t o_re = (size_t(k >> 2) * Rs + r) * 4 + (k & 3);
-                const size_t o_im = (size_t((k + p) >> 2) * Rs + r) * 4 + ((k + p) & 3);
-                A_hi[o_re] = hr;
-                A_lo[o_re] = v.x - hr;
-                A_hi[o_im] = hi_;
-                A_lo[o_im] = v.y - hi_;
+            // stage the strip: real parts at k < p, imaginary parts at p <= k < 2p.
+            // Element e of the strip is coefficient k of row r, e = r p + k; the
+            // row is e * inv_p >> 20 (exact for e < 2^14, p <= 24).  Four loads
+            // are issued before their stores so that they overlap.
+            const float2 *src = lev + (int64_t(cs) * quarter + int64_t(Pys) * W + Px0 - 1) * p;
+            const int total = Rs * p;
+            const uint32_t inv_p = ((1u << 20) + uint32_t(p) - 1) / uint32_t(p);
+            for (int e0 = tid; e0 < total; e0 += 4 * TC_THREADS) {
+                float2 v[4];
+                int rr[4], kk[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * TC_THREADS;
+                    rr[u] = int((uint32_t(e) * inv_p) >> 20);
+                    kk[u] = e - rr[u] * p;
+                    v[u] = make_float2(0.f, 0.f);
+                    if (e < total && rowocc[rr[u]]) v[u] = __ldg(src + e);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (e0 + u * TC_THREADS >= total) break;
+                    const int r = rr[u], k = kk[u];
+                    const float hr = tf32_hi(v[u].x), hi_ = tf32_hi(v[u].y);
+                    const size_t o_re = (size_t(k >> 2) * Rs + r) * 4 + (k & 3);
+                    const size_t o_im = (size_t((k + p) >> 2) * Rs + r) * 4 + ((k + p) & 3);
+                    A_hi[o_re] = hr;
+                    A_lo[o_re] = v[u].x - hr;
+                    A_hi[o_im] = hi_;
+                    A_lo[o_im] = v[u].y - hi_;
+                }
             }
             // the B operators of the (up to three) dx shifts, hi and lo images
             for (int s3 = 0; s3 < 3; ++s3) {
@@ -226,6 +266,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
                     const uint32_t bhi = smem_addr(Bsm + size_t(2 * s3) * bslot);
                     const uint32_t blo = smem_addr(Bsm + size_t(2 * s3 + 1) * bslot);
                     for (int s = 0; s < S; ++s) {
+                        if (!(sub_mask & (1u << s))) continue;  // no target there
                         const uint32_t row0 = uint32_t(s * 128 + 1 + (s3 - 1)) * 16;
                         const uint32_t dt = tbase + uint32_t(s * Npad);
                         const uint32_t as[3] = {ahi + row0, ahi + row0, alo + row0};
@@ -262,6 +303,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
     const uint32_t umask = used_mask;
     if (ok) {
         for (int s = 0; s < S; ++s) {
+            if (!(sub_mask & (1u << s))) continue;
             const int Px = Px0 + s * 128 + tid;
             float v[TC_MAX_NPAD];
             if (umask & (1u << s)) {
@@ -289,21 +331,17 @@ size_t m2l_tc_smem_bytes(int p, int seg) {
     return size_t(2) * (Kpad / 4) * (seg + 2) * 16 + size_t(6) * Kpad * Npad * 4;
 }
 
-int m2l_tc_seg(int level) {
-    const int W = 1 << (level - 1);
-    return W < TC_MAX_SEG ? W : TC_MAX_SEG;
-}
+int m2l_tc_seg(int level, int segmax) { return tc_seg(level, segmax); }
 
-bool m2l_tc_supported(int p, int level) {
+bool m2l_tc_supported(int p, int level, int segmax) {
     const int Npad = (2 * p + 15) & ~15;
     return level >= 8 && level <= 15 && Npad <= TC_MAX_NPAD &&
-           m2l_tc_smem_bytes(p, m2l_tc_seg(level)) <= size_t(220) * 1024;
+           m2l_tc_smem_bytes(p, m2l_tc_seg(level, segmax)) <= size_t(220) * 1024;
 }
 
-int64_t m2l_tc_units(int level) {
+int64_t m2l_tc_units(int level, int segmax) {
     const int64_t W = int64_t(1) << (level - 1);
-    const int64_t seg = W < TC_MAX_SEG ? W : TC_MAX_SEG;
-    return 4 * W * (W / seg);
+    return 4 * W * (W / tc_seg(level, segmax));
 }
 
 // B images for p: for each of the 40 offsets, hi then lo, each Kpad x Npad
@@ -338,15 +376,26 @@ void host_m2l_tc_images(int p, std::vector<float> &out) {
     }
 }
 
+cudaError_t launch_tc_unit_count(const Task *tasks, int ntasks, int64_t nunits,
+                                 const InstDesc *insts, const uint32_t *start, uint32_t *ucount,
+                                 cudaStream_t st, uint64_t *launches) {
+    if (nunits <= 0) return cudaSuccess;
+    const int64_t blocks = (nunits * 32 + 255) / 256;
+    k_tc_unit_count<<<unsigned(blocks), 256, 0, st>>>(tasks, ntasks, insts, start, ucount, nunits);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_m2l_tc(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                          const uint32_t *start, const float2 *me, float2 *le, size_t smem_bytes,
+                          const uint32_t *start, const float2 *me, float2 *le,
+                          const uint32_t *ucount, int dense_pct, size_t smem_bytes,
                           long long spin_limit, int *status, cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem_bytes));
     if (e != cudaSuccess) return e;
     k_m2l_tc<<<unsigned(nblocks), TC_THREADS, smem_bytes, st>>>(tasks, ntasks, insts, start, me, le,
-                                                                spin_limit, status);
+                                                                ucount, dense_pct, spin_limit, status);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }

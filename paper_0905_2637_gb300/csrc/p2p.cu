@@ -329,14 +329,168 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
 }
 
 // ----------------------------------------------------------------------------
+// Mixed-precision P2P + L2P, the two targets of a lane packed in FP32x2.
+//
+// Same arithmetic and source order as k_p2p_mixed, but every FP32 operation of
+// the pair loop acts on (target a, target b) at once with the packed FP32x2
+// instructions, which halves the issued instructions per pair.  To avoid
+// building broadcast operands in registers, the gather stores each source
+// already duplicated: src2[j] = (-xi, -xi, eta, eta), gam2[j] = (gamma, gamma).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+
+template <int DEG>
+__device__ __forceinline__ float2 poly2_eval(const float2 (&a)[DEG + 1], float2 s) {
+    float2 g = a[DEG];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; --k) g = __ffma2_rn(g, s, a[k]);
+    return g;
+}
+
+template <int DEG, bool GENERAL>
+__global__ void __launch_bounds__(P2P_THREADS) k_p2p_packed(
+    const uint4 *__restrict__ items, uint32_t *ctrl, const InstDesc *__restrict__ insts,
+    const uint32_t *__restrict__ start, const float4 *__restrict__ rec,
+    const float4 *__restrict__ src2, const float2 *__restrict__ gam2,
+    const float2 *__restrict__ le, int dtype_f32, unsigned long long *busy) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nitems = *reinterpret_cast<volatile uint32_t *>(ctrl + CTRL_NITEMS);
+    const uint64_t t_begin = busy ? global_ns() : 0;
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(ctrl + CTRL_QUEUE, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nitems) break;
+        const uint4 item = items[it];
+        const InstDesc &d = insts[item.x];
+        const int L = d.L;
+        float2 a[DEG + 1];
+#pragma unroll
+        for (int k = 0; k <= DEG; ++k) a[k] = pk(d.poly[k], d.poly[k]);
+        const float kappa = d.kappa, split = d.qsplit_rho2;
+        const uint32_t m = item.y;
+        const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
+        const uint32_t ta = item.z + lane, tb = item.z + lane + 32;
+        const bool has_a = uint32_t(lane) < item.w, has_b = uint32_t(lane + 32) < item.w;
+        const float4 ra = has_a ? rec[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 rb = has_b ? rec[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 u2 = pk(0.f, 0.f), v2 = pk(0.f, 0.f);
+        const uint32_t *st = start + d.soff;
+        const int nside = 1 << L;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int sy = iy + dy;
+            if (sy < 0 || sy >= nside) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int sx = ix + dx;
+                if (sx < 0 || sx >= nside) continue;
+                const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
+                const uint32_t j0 = st[nm], j1 = st[nm + 1];
+                // targets in the source leaf's frame: x_t - dx, and -(y_t - dy)
+                const float2 tx = pk(ra.x - float(dx), rb.x - float(dx));
+                const float2 tyn = pk(float(dy) - ra.y, float(dy) - rb.y);
+#pragma unroll 4
+                for (uint32_t j = j0; j < j1; ++j) {
+                    const float4 s = __ldg(src2 + j);
+                    const float2 gj = __ldg(gam2 + j);
+                    const float2 dxv = __fadd2_rn(tx, pk(s.x, s.y));   // x_t - x_s
+                    const float2 dyn = __fadd2_rn(pk(s.z, s.w), tyn);  // y_s - y_t
+                    const float2 r2 = __ffma2_rn(dxv, dxv, __fmul2_rn(dyn, dyn));
+                    float2 g = poly2_eval<DEG>(a, r2);
+                    if (GENERAL) {
+                        const float qx = kappa * r2.x, qy = kappa * r2.y;
+                        const float ex = __fdividef(1.0f - __expf(-qx), qx);
+                        const float ey = __fdividef(1.0f - __expf(-qy), qy);
+                        g.x = r2.x < split ? g.x : ex;
+                        g.y = r2.y < split ? g.y : ey;
+                    }
+                    const float2 f = __fmul2_rn(gj, g);
+                    u2 = __ffma2_rn(dyn, f, u2);
+                    v2 = __ffma2_rn(dxv, f, v2);
+                }
+            }
+        }
+        // far field: L2P of the leaf's local expansion, w = (1/r) sum c_m zeta^m
+        float fua = 0.f, fva = 0.f, fub = 0.f, fvb = 0.f;
+        if (L >= 2) {
+            const int p = d.p;
+            const float2 *c = le + d.eoff + (lvl_off(L) + box_index(L, uint32_t(ix), uint32_t(iy))) * p;
+            float2 wa = __ldg(c + p - 1), wb = wa;
+            for (int k = p - 2; k >= 0; --k) {
+                const float2 ck = __ldg(c + k);
+                const float wax = fmaf(wa.x, ra.x, fmaf(-wa.y, ra.y, ck.x));
+                const float way = fmaf(wa.x, ra.y, fmaf(wa.y, ra.x, ck.y));
+                const float wbx = fmaf(wb.x, rb.x, fmaf(-wb.y, rb.y, ck.x));
+                const float wby = fmaf(wb.x, rb.y, fmaf(wb.y, rb.x, ck.y));
+                wa = make_float2(wax, way);
+                wb = make_float2(wbx, wby);
+            }
+            fua = d.cfar * wa.y; fva = d.cfar * wa.x;
+            fub = d.cfar * wb.y; fvb = d.cfar * wb.x;
+        }
+        const float cn = d.cnear;
+        if (has_a) {
+            const int64_t q = int64_t(__float_as_uint(ra.w)) - d.poff;
+            const float uo = fmaf(cn, u2.x, fua), vo = fmaf(cn, v2.x, fva);
+            if (dtype_f32) {
+                static_cast<float *>(d.u)[q] = uo;
+                static_cast<float *>(d.v)[q] = vo;
+            } else {
+                static_cast<double *>(d.u)[q] = double(uo);
+                static_cast<double *>(d.v)[q] = double(vo);
+            }
+        }
+        if (has_b) {
+            const int64_t q = int64_t(__float_as_uint(rb.w)) - d.poff;
+            const float uo = fmaf(cn, u2.y, fub), vo = fmaf(cn, v2.y, fvb);
+            if (dtype_f32) {
+                static_cast<float *>(d.u)[q] = uo;
+                static_cast<float *>(d.v)[q] = vo;
+            } else {
+                static_cast<double *>(d.u)[q] = double(uo);
+                static_cast<double *>(d.v)[q] = double(vo);
+            }
+        }
+    }
+    if (busy && lane == 0) {
+        const uint64_t t_end = global_ns();
+        const size_t gw = size_t(blockIdx.x) * (P2P_THREADS / 32) + (threadIdx.x >> 5);
+        busy[2 * gw] = t_begin;
+        busy[2 * gw + 1] = t_end;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Launch helpers
 // ----------------------------------------------------------------------------
 typedef void (*MixedKernel)(const uint4 *, uint32_t *, const InstDesc *, const uint32_t *,
                             const float4 *, const float2 *, int, unsigned long long *);
+typedef void (*PackedKernel)(const uint4 *, uint32_t *, const InstDesc *, const uint32_t *,
+                             const float4 *, const float4 *, const float2 *, const float2 *, int,
+                             unsigned long long *);
 
 template <int D>
 static MixedKernel pick2(int general) {
     return general ? k_p2p_mixed<D, true> : k_p2p_mixed<D, false>;
+}
+
+template <int D>
+static PackedKernel pickp(int general) {
+    return general ? k_p2p_packed<D, true> : k_p2p_packed<D, false>;
+}
+
+static PackedKernel pick_packed(int deg, int general) {
+    switch (deg) {
+        case 4: return pickp<4>(general);
+        case 5: return pickp<5>(general);
+        case 6: return pickp<6>(general);
+        case 7: return pickp<7>(general);
+        case 8: return pickp<8>(general);
+        case 9: return pickp<9>(general);
+        case 10: return pickp<10>(general);
+        case 11: return pickp<11>(general);
+        case 12: return pickp<12>(general);
+        default: return nullptr;
+    }
 }
 
 static MixedKernel pick_mixed(int deg, int general) {
@@ -366,9 +520,13 @@ static int sm_count() {
     return g_sms;
 }
 
-int p2p_grid(int precision_mixed, int deg, int general) {
+int p2p_grid(int precision_mixed, int deg, int general, int packed) {
     int per_sm = 1;
-    if (precision_mixed) {
+    if (precision_mixed && packed) {
+        PackedKernel k = pick_packed(deg, general);
+        if (!k) return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, P2P_THREADS, 0);
+    } else if (precision_mixed) {
         MixedKernel k = pick_mixed(deg, general);
         if (!k) return 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, P2P_THREADS, 0);
@@ -381,11 +539,19 @@ int p2p_grid(int precision_mixed, int deg, int general) {
 
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
                              const InstDesc *insts, const uint32_t *start, const float4 *rec,
-                             const float2 *le, int dtype_f32, unsigned long long *busy,
-                             cudaStream_t st, uint64_t *launches) {
-    MixedKernel k = pick_mixed(deg, general);
-    if (!k) return cudaErrorInvalidValue;
-    k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, le, dtype_f32, busy);
+                             const float4 *src2, const float2 *gam2, const float2 *le,
+                             int dtype_f32, unsigned long long *busy, cudaStream_t st,
+                             uint64_t *launches) {
+    if (src2 && gam2) {
+        PackedKernel k = pick_packed(deg, general);
+        if (!k) return cudaErrorInvalidValue;
+        k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, src2, gam2, le, dtype_f32,
+                                        busy);
+    } else {
+        MixedKernel k = pick_mixed(deg, general);
+        if (!k) return cudaErrorInvalidValue;
+        k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, le, dtype_f32, busy);
+    }
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }

@@ -51,11 +51,15 @@ __global__ void k_rk2(int64_t n, int stage, double dt, double *x, double *y, dou
     }
 }
 
-// Bounding box of the positions (min x, min y, max x, max y), one block.
+constexpr int BBOX_BLOCKS = 64;
+
+// Bounding box of the positions (min x, min y, max x, max y): each block
+// reduces a grid-stride share into out[4 * blockIdx.x + 0..3].
 __global__ void k_bbox(int64_t n, const double *x, const double *y, double *out) {
     __shared__ double s[4][256];
     double a = INFINITY, b = INFINITY, c = -INFINITY, d = -INFINITY;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
         a = fmin(a, x[i]);
         b = fmin(b, y[i]);
         c = fmax(c, x[i]);
@@ -75,7 +79,24 @@ __global__ void k_bbox(int64_t n, const double *x, const double *y, double *out)
         }
         __syncthreads();
     }
-    if (threadIdx.x < 4) out[threadIdx.x] = s[threadIdx.x][0];
+    if (threadIdx.x < 4) out[4 * blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Combines the BBOX_BLOCKS partial boxes of request blockIdx.x.
+__global__ void k_bbox_final(const double *part, double *out) {
+    if (threadIdx.x != 0) return;
+    const double *p = part + size_t(blockIdx.x) * 4 * BBOX_BLOCKS;
+    double a = p[0], b = p[1], c = p[2], d = p[3];
+    for (int k = 1; k < BBOX_BLOCKS; ++k) {
+        a = fmin(a, p[4 * k]);
+        b = fmin(b, p[4 * k + 1]);
+        c = fmax(c, p[4 * k + 2]);
+        d = fmax(d, p[4 * k + 3]);
+    }
+    out[4 * blockIdx.x] = a;
+    out[4 * blockIdx.x + 1] = b;
+    out[4 * blockIdx.x + 2] = c;
+    out[4 * blockIdx.x + 3] = d;
 }
 
 struct Req {
@@ -229,9 +250,11 @@ void run_round(petfmm_server *s, std::vector<Req *> &act) {
         cudaFree(s->dbox);
         cudaFreeHost(s->hbox);
         s->box_cap = std::max<int>(int(act.size()), 2 * s->box_cap);
-        cudaMalloc(&s->dbox, size_t(s->box_cap) * 4 * sizeof(double));
+        // final boxes, then BBOX_BLOCKS partial boxes per request
+        cudaMalloc(&s->dbox, size_t(s->box_cap) * 4 * (BBOX_BLOCKS + 1) * sizeof(double));
         cudaMallocHost(&s->hbox, size_t(s->box_cap) * 4 * sizeof(double));
     }
+    double *dpart = s->dbox + size_t(s->box_cap) * 4;
     for (size_t i = 0; i < act.size(); ++i) {
         Req *r = act[i];
         const int64_t n = r->spec.n;
@@ -239,9 +262,11 @@ void run_round(petfmm_server *s, std::vector<Req *> &act) {
             const int stage = r->evals_done & 1;
             k_rk2<<<unsigned((n + 255) / 256), 256, 0, s->stream>>>(n, stage, r->spec.dt, r->x, r->y,
                                                                     r->xn, r->yn, r->u, r->v);
-            k_bbox<<<1, 256, 0, s->stream>>>(n, r->x, r->y, s->dbox + 4 * i);
+            k_bbox<<<BBOX_BLOCKS, 256, 0, s->stream>>>(n, r->x, r->y, dpart + i * 4 * BBOX_BLOCKS);
         }
     }
+    if (!act.empty())
+        k_bbox_final<<<unsigned(act.size()), 32, 0, s->stream>>>(dpart, s->dbox);
     cudaMemcpyAsync(s->hbox, s->dbox, act.size() * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     int st64 = in64.empty() ? 0 : petfmm_sync(s->ctx64);
     int stmx = inmx.empty() ? 0 : petfmm_sync(s->ctxmx);

@@ -337,7 +337,9 @@ __global__ void __launch_bounds__(256) k_gather_mixed(const Task *__restrict__ t
                                                       const InstDesc *__restrict__ insts,
                                                       const uint32_t *__restrict__ perm,
                                                       const uint32_t *__restrict__ skeys,
-                                                      float4 *__restrict__ rec) {
+                                                      float4 *__restrict__ rec,
+                                                      float4 *__restrict__ src2,
+                                                      float2 *__restrict__ gam2) {
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
     const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
@@ -359,6 +361,10 @@ __global__ void __launch_bounds__(256) k_gather_mixed(const Task *__restrict__ t
     o.z = float(g);
     o.w = __uint_as_float(qb);
     rec[r] = o;
+    if (src2) {
+        src2[r] = make_float4(-o.x, -o.x, o.y, o.y);
+        gam2[r] = make_float2(o.z, o.z);
+    }
 }
 
 cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
@@ -375,13 +381,15 @@ cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, co
 
 cudaError_t launch_gather_mixed(const Task *tasks, int ntasks, int64_t nblocks,
                                 const InstDesc *insts, int dtype_f32, const uint32_t *perm,
-                                const uint32_t *skeys, float4 *rec, cudaStream_t st,
-                                uint64_t *launches) {
+                                const uint32_t *skeys, float4 *rec, float4 *src2, float2 *gam2,
+                                cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
     if (dtype_f32)
-        k_gather_mixed<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys, rec);
+        k_gather_mixed<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys, rec,
+                                                                 src2, gam2);
     else
-        k_gather_mixed<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys, rec);
+        k_gather_mixed<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys, rec,
+                                                                  src2, gam2);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }

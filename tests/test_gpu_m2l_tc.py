@@ -10,10 +10,12 @@ from paper_0905_2637_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, tc, L=None, p=None):
+def _run(w, tc, L=None, p=None, dense_pct=None):
     _lib = G.lib()
     ctx = _lib.Context(w.domain, L or w.L, p or w.p, w.sigma, precision="mixed", dtype=w.dtype)
     ctx.set_option(_lib.PETFMM_OPT_M2L_TC, 1 if tc else 0)
+    if dense_pct is not None:
+        ctx.set_option(_lib.PETFMM_OPT_TC_DENSE, dense_pct)
     ctx.set_option(_lib.PETFMM_OPT_POISON, 1)
     x, y, g = G.to_dev((w.x, w.y, w.gamma))
     u, v = ctx.evaluate(x, y, g)
@@ -33,6 +35,17 @@ def test_tensor_core_m2l_matches_simt_and_fp64(L, n, frac, p):
     assert G.rel_l2(u_tc, v_tc, u64, v64) <= 1e-5
     assert G.rel_l2(u_tc, v_tc, u_si, v_si) <= 1e-5
     assert np.all(np.isfinite(u_tc)) and np.all(np.isfinite(v_tc))
+
+
+@pytest.mark.parametrize("dense_pct", [0, 10, 50, 100])
+def test_dense_sparse_split_covers_every_box(dense_pct):
+    # whichever units the tensor cores take, the two kernels together must
+    # translate every target exactly once (poisoned buffers would show NaN)
+    w = W.tiny(300_000, 91, L=9, p=17, clustered_frac=0.7)
+    u_mx, v_mx = _run(w, tc=True, dense_pct=dense_pct)
+    u_si, v_si = _run(w, tc=False)
+    assert np.all(np.isfinite(u_mx)) and np.all(np.isfinite(v_mx))
+    assert G.rel_l2(u_mx, v_mx, u_si, v_si) <= 1e-5
 
 
 def test_tensor_core_m2l_far_field_alone(orc):

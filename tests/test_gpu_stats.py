@@ -80,3 +80,22 @@ def test_reused_context_matches_fresh_context():
     ctx.close()
     uf, vf = G.run(b, "mixed", poison=False)
     assert np.array_equal(u, uf) and np.array_equal(v, vf)
+
+
+def test_packed_and_scalar_p2p_agree_bitwise():
+    # the FP32x2 kernel performs the scalar kernel's operations, in the same
+    # order, two targets at a time
+    _lib = G.lib()
+    outs = []
+    for packed in (1, 0):
+        for w in (W.tiny(60_000, 17, L=6, p=12, clustered_frac=0.5, dtype="f32"),
+                  W.tiny(20_000, 18, L=4, p=12, sigma=0.003)):  # second one: exp branch
+            ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype=w.dtype)
+            ctx.set_option(_lib.PETFMM_OPT_P2P_PACKED, packed)
+            x, y, g = G.to_dev((w.x, w.y, w.gamma))
+            u, v = ctx.evaluate(x, y, g)
+            assert ctx.sync() == 0
+            outs.append((u.cpu().numpy(), v.cpu().numpy()))
+            ctx.close()
+    for (ua, va), (ub, vb) in zip(outs[:2], outs[2:]):
+        assert np.array_equal(ua, ub) and np.array_equal(va, vb)

@@ -59,9 +59,10 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
             assert len(rows) == 1 and rows[0][3] == units
         simt = sorted(int(r[2]) for r in ranges.get(5, []) if r[1] == i)
         tc = sorted(int(r[2]) for r in ranges.get(6, []) if r[1] == i)
-        assert sorted(simt + tc) == list(range(2, L + 1))
-        # the tensor-core M2L takes the levels with >= 128 parent cells per row
-        # (mixed path, p <= 24); one CTA per (class, parent row, 512-cell segment)
+        # every level has a SIMT launch; the levels with >= 128 parent cells per
+        # row (mixed path, p <= 24) also get the tensor-core launch, one CTA per
+        # (class, parent row, 512-cell segment), which takes the dense units
+        assert simt == list(range(2, L + 1))
         assert tc == ([l for l in range(8, L + 1)] if precision == 1 and p <= 24 else [])
         for r in ranges.get(6, []):
             if r[1] == i:
