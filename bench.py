@@ -298,7 +298,9 @@ def main():
     if args.workload == "clustered-16M":
         w = W.clustered()
     elif args.workload == "clustered-4M":
-        w = W.clustered(n=1 << 22, L=9, name="clustered-4M")
+        # a quarter of the blobs, one level shallower, sigma scaled with the
+        # leaf: the same blobs per leaf and the same near-field kernel variant
+        w = W.clustered(n=1 << 22, L=9, sigma=0.004, name="clustered-4M")
     else:
         w = W.lattice(dtype="f32")
     stream = torch.cuda.Stream()

@@ -238,7 +238,10 @@ enum {
                                   < 0: no iterations, so the first wait of the tensor-core
                                   M2L reports PETFMM_ETIMEOUT -- for testing the report;
                                   that evaluation's u, v are then unspecified) */
-    PETFMM_OPT_P2P_MODE = 3,   /* P2P scheduler: 0 work-model partition, 1 dynamic queue */
+    PETFMM_OPT_P2P_MODE = 3,   /* order in which the persistent P2P warps take the work
+                                  items from their queue: 0 (default) heaviest first by
+                                  the targets x sources cost of Eq. 14, 1 leaf (Morton)
+                                  order; the results are identical */
     PETFMM_OPT_POISON = 4,     /* 1: fill the expansion buffers with NaN bytes before each
                                   evaluation (testing: a read of a never-written
                                   coefficient then shows up as NaN in u, v) */
@@ -247,8 +250,6 @@ enum {
     PETFMM_OPT_TC_DENSE = 6,   /* percent (0..100, default 25) of a tensor-core unit's
                                   targets that must hold particles for the unit to run
                                   on the tensor cores; sparser units use the SIMT kernel */
-    PETFMM_OPT_P2P_PACKED = 7, /* mixed path: 1 P2P with the two targets of a lane in
-                                  packed FP32x2 instructions, 0 (default) the scalar kernel */
     PETFMM_OPT_TC_SEG = 8      /* widest tensor-core M2L unit in parent cells: 128
                                   (default), 256 or 512 */
 };

@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace petfmm {
 
 constexpr int MAX_P = 40;
@@ -68,7 +70,25 @@ struct InstDesc {
     double inv2s2;          // 1 / (2 sigma^2)
     double cnear64;         // 1 / (2 pi)
     double cfar64;          // 1 / (2 pi w)
+    // float-float copies of the domain: x0 = x0h + x0l, y0 = y0h + y0l,
+    // scale = sh + sl (binning shortcut and leaf-relative coordinates in FP32)
+    float x0h, x0l, y0h, y0l, sh, sl;
 };
+
+// Sets the domain square and the quantities derived from it.
+inline void inst_set_domain(InstDesc &d, double x0, double y0, double width, int L) {
+    d.x0 = x0;
+    d.y0 = y0;
+    d.width = width;
+    d.scale = std::ldexp(1.0, L) / width;
+    d.wleaf = width / std::ldexp(1.0, L);
+    d.x0h = float(x0);
+    d.x0l = float(x0 - double(d.x0h));
+    d.y0h = float(y0);
+    d.y0l = float(y0 - double(d.y0h));
+    d.sh = float(d.scale);
+    d.sl = float(d.scale - double(d.sh));
+}
 
 // A range of work units of one kind, for one instance (and level).
 struct Task {

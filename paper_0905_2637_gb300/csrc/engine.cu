@@ -96,20 +96,18 @@ struct petfmm_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     bool timing = false;
-    int p2p_mode = 1;
+    int p2p_mode = 0;  // 0: work items heaviest first (Eq. 14 weights), 1: Morton order
     bool poison = false;
     bool m2l_tc = true;
     // measured on GB300 (clustered 16M and lattice 1M blobs): 128-cell units
-    // with a 25% occupancy threshold gave the fastest M2L on both; the packed
-    // FP32x2 P2P was 15% slower than the scalar kernel, so it is off
+    // with a 25% occupancy threshold gave the fastest M2L on both
     int tc_dense_pct = 25;
     int tc_segmax = 128;
-    bool p2p_packed = false;
     int64_t spin_limit = 0;
     uint64_t launches = 0, evaluations = 0;
 
     DevBuf keysA, keysB, valsA, valsB, hist, scratch, start, xs, ys, gs, rec, me, le, cnt, off,
-        items, ctrl, plan_dev, busy, ucount, src2, gam2;
+        items, ctrl, plan_dev, busy, ucount, items_u, ikA, ikB, ivA, ivB, ihist;
     DevBuf hx, hy, hg, hu, hv;  // device staging for petfmm_evaluate_host
     std::map<int, OpTables> tables;
 
@@ -338,11 +336,7 @@ int build_plan(int precision, bool use_tc, int tc_segmax, const std::vector<Prob
         const Problem &pb = probs[i];
         InstDesc d;
         std::memset(&d, 0, sizeof(d));
-        d.x0 = pb.dom.x0;
-        d.y0 = pb.dom.y0;
-        d.width = pb.dom.width;
-        d.scale = std::ldexp(1.0, pb.L) / pb.dom.width;
-        d.wleaf = pb.dom.width / std::ldexp(1.0, pb.L);
+        inst_set_domain(d, pb.dom.x0, pb.dom.y0, pb.dom.width, pb.L);
         d.sigma = pb.sigma;
         d.L = pb.L;
         d.p = pb.p;
@@ -508,15 +502,12 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->valsB, N * 4, st));
     const int64_t rb = radix_blocks(N);
     PF_TRY(ensure(c->hist, size_t(256) * rb * 4, st));
-    const int64_t scan_n = std::max<int64_t>(256 * rb, pl.nleaves);
+    const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(256 * rb, pl.nleaves),
+                                             256 * radix_blocks(pl.items_cap));
     PF_TRY(ensure(c->scratch, size_t(scan_scratch_words(scan_n)) * 4, st));
     PF_TRY(ensure(c->start, size_t(pl.nstart) * 4, st));
     if (mixed) {
         PF_TRY(ensure(c->rec, size_t(N) * sizeof(float4), st));
-        if (c->p2p_packed) {
-            PF_TRY(ensure(c->src2, size_t(N) * sizeof(float4), st));
-            PF_TRY(ensure(c->gam2, size_t(N) * sizeof(float2), st));
-        }
         PF_TRY(ensure(c->me, size_t(pl.ncoef) * sizeof(float2), st));
         PF_TRY(ensure(c->le, size_t(pl.ncoef) * sizeof(float2), st));
     } else {
@@ -530,8 +521,24 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->off, size_t(pl.nleaves) * 4, st));
     PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
     PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks) * sizeof(uint32_t), st));
-    const bool packed = mixed && c->p2p_packed;
-    const int grid = p2p_grid(mixed, pl.deg, pl.general, packed);
+    P2POrder order{};
+    if (c->p2p_mode == 0) {
+        const size_t cap = size_t(pl.items_cap);
+        PF_TRY(ensure(c->items_u, cap * sizeof(uint4), st));
+        PF_TRY(ensure(c->ikA, cap * 4, st));
+        PF_TRY(ensure(c->ikB, cap * 4, st));
+        PF_TRY(ensure(c->ivA, cap * 4, st));
+        PF_TRY(ensure(c->ivB, cap * 4, st));
+        PF_TRY(ensure(c->ihist, size_t(256) * radix_blocks(pl.items_cap) * 4, st));
+        order.cap = pl.items_cap;
+        order.items_unsorted = static_cast<uint4 *>(c->items_u.p);
+        order.kA = static_cast<uint32_t *>(c->ikA.p);
+        order.kB = static_cast<uint32_t *>(c->ikB.p);
+        order.vA = static_cast<uint32_t *>(c->ivA.p);
+        order.vB = static_cast<uint32_t *>(c->ivB.p);
+        order.hist = static_cast<uint32_t *>(c->ihist.p);
+    }
+    const int grid = p2p_grid(mixed, pl.deg, pl.general);
     if (grid <= 0) return PETFMM_EINVAL;
     c->p2p_grid = grid;
     unsigned long long *busy = nullptr;
@@ -575,9 +582,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     if (mixed)
         PF_CUDA(launch_gather_mixed(dtask + pl.particles.first, pl.particles.count,
                                     pl.particles.nblocks, dinst, f32, perm, skeys,
-                                    static_cast<float4 *>(c->rec.p),
-                                    packed ? static_cast<float4 *>(c->src2.p) : nullptr,
-                                    packed ? static_cast<float2 *>(c->gam2.p) : nullptr, st, lc));
+                                    static_cast<float4 *>(c->rec.p), st, lc));
     else
         PF_CUDA(launch_gather_f64(dtask + pl.particles.first, pl.particles.count,
                                   pl.particles.nblocks, dinst, f32, perm,
@@ -646,13 +651,12 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_CUDA(launch_p2p_worklist(dtask + pl.leaves_wl.first, pl.leaves_wl.count, pl.leaves_wl.nblocks,
                                 dinst, start, pl.nleaves, tpi, static_cast<uint32_t *>(c->cnt.p),
                                 static_cast<uint32_t *>(c->off.p), scratch,
-                                static_cast<uint4 *>(c->items.p), ctrl, st, lc));
+                                static_cast<uint4 *>(c->items.p), ctrl,
+                                c->p2p_mode == 0 ? &order : nullptr, st, lc));
     stage_mark(c, PETFMM_STAGE_P2P);
     if (mixed)
         PF_CUDA(launch_p2p_mixed(grid, pl.deg, pl.general, static_cast<const uint4 *>(c->items.p),
                                  ctrl, dinst, start, static_cast<const float4 *>(c->rec.p),
-                                 packed ? static_cast<const float4 *>(c->src2.p) : nullptr,
-                                 packed ? static_cast<const float2 *>(c->gam2.p) : nullptr,
                                  static_cast<const float2 *>(c->le.p), f32, busy, st, lc));
     else
         PF_CUDA(launch_p2p_f64(grid, static_cast<const uint4 *>(c->items.p), ctrl, dinst, start,
@@ -737,7 +741,7 @@ int petfmm_destroy(petfmm_ctx *c) {
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                       &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
-                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->src2, &c->gam2, &c->hx, &c->hy,
+                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB, &c->ihist, &c->hx, &c->hy,
                       &c->hg, &c->hu, &c->hv};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -892,7 +896,6 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
         case PETFMM_OPT_P2P_MODE: if (value < 0 || value > 1) return PETFMM_EINVAL; c->p2p_mode = int(value); return PETFMM_OK;
         case PETFMM_OPT_POISON: c->poison = value != 0; return PETFMM_OK;
         case PETFMM_OPT_M2L_TC: c->m2l_tc = value != 0; return PETFMM_OK;
-        case PETFMM_OPT_P2P_PACKED: c->p2p_packed = value != 0; return PETFMM_OK;
         case PETFMM_OPT_TC_SEG:
             if (value != 128 && value != 256 && value != 512) return PETFMM_EINVAL;
             c->tc_segmax = int(value);

@@ -39,12 +39,11 @@ cudaError_t launch_leaf_start(const Task *tasks, int ntasks, int64_t nblocks, co
 cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                               int dtype_f32, const uint32_t *perm, double *xs, double *ys,
                               double *gs, cudaStream_t st, uint64_t *launches);
-// rec = (xi, eta, gamma, caller index); if src2/gam2 are non-null also the
-// pre-broadcast source copies (-xi, -xi, eta, eta) and (gamma, gamma).
+// rec = (xi, eta, gamma, caller index): leaf-relative coordinates in leaf units.
 cudaError_t launch_gather_mixed(const Task *tasks, int ntasks, int64_t nblocks,
                                 const InstDesc *insts, int dtype_f32, const uint32_t *perm,
-                                const uint32_t *skeys, float4 *rec, float4 *src2, float2 *gam2,
-                                cudaStream_t st, uint64_t *launches);
+                                const uint32_t *skeys, float4 *rec, cudaStream_t st,
+                                uint64_t *launches);
 
 // ---- expansions.cu ---------------------------------------------------------
 // Operator tables for p (FP64 build, also rounded to FP32), device-resident.
@@ -114,23 +113,29 @@ constexpr int EXP_THREADS = 256;  // (box, coefficient) pairs per block for M2M 
 // Work list: items (inst, leaf, first target rank, target count) for every
 // occupied leaf, tpi targets per item.  ctrl[CTRL_NITEMS] receives the count.
 enum { CTRL_STATUS = 0, CTRL_NITEMS = 1, CTRL_QUEUE = 2, CTRL_PAIRS_LO = 4, CTRL_WORDS = 16 };
+// Buffers for dispatching the items heaviest first (order != nullptr): the
+// items are emitted to items_unsorted, sorted by work class (one stable radix
+// pass over cap entries) and permuted into the item array.
+struct P2POrder {
+    int64_t cap;
+    uint4 *items_unsorted;
+    uint32_t *kA, *kB, *vA, *vB, *hist;  // hist: 256 * radix_blocks(cap) words
+};
 cudaError_t launch_p2p_worklist(const Task *tasks, int ntasks, int64_t nblocks,
                                 const InstDesc *insts, const uint32_t *start, int64_t nleaves,
                                 int tpi, uint32_t *cnt, uint32_t *off, uint32_t *scan_scratch,
-                                uint4 *items, uint32_t *ctrl, cudaStream_t st, uint64_t *launches);
+                                uint4 *items, uint32_t *ctrl, const P2POrder *order,
+                                cudaStream_t st, uint64_t *launches);
 cudaError_t launch_p2p_f64(int grid, const uint4 *items, uint32_t *ctrl, const InstDesc *insts,
                            const uint32_t *start, const double *xs, const double *ys,
                            const double *gs, const uint32_t *perm, const double2 *le,
                            int dtype_f32, unsigned long long *busy, cudaStream_t st,
                            uint64_t *launches);
-// src2/gam2 non-null: the FP32x2-packed variant (sources pre-broadcast by the
-// gather); null: the scalar variant.
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
                              const InstDesc *insts, const uint32_t *start, const float4 *rec,
-                             const float4 *src2, const float2 *gam2, const float2 *le,
-                             int dtype_f32, unsigned long long *busy, cudaStream_t st,
-                             uint64_t *launches);
-int p2p_grid(int precision_mixed, int deg, int general, int packed);
+                             const float2 *le, int dtype_f32, unsigned long long *busy,
+                             cudaStream_t st, uint64_t *launches);
+int p2p_grid(int precision_mixed, int deg, int general);
 constexpr int P2P_TPI_F64 = 32;
 constexpr int P2P_TPI_MIXED = 64;
 

@@ -96,11 +96,7 @@ extern "C" int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dty
         Task t[3];  // binning (particles), leaf starts (4^L + 1), unused
     } h;
     std::memset(&h, 0, sizeof(h));
-    h.d.x0 = dom->x0;
-    h.d.y0 = dom->y0;
-    h.d.width = dom->width;
-    h.d.scale = std::ldexp(1.0, levels) / dom->width;
-    h.d.wleaf = dom->width / std::ldexp(1.0, levels);
+    inst_set_domain(h.d, dom->x0, dom->y0, dom->width, levels);
     h.d.L = levels;
     h.d.n = n;
     h.d.x = x;

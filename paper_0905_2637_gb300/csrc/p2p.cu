@@ -7,8 +7,12 @@
 // leaves), the n_nd N_i^2 term of the work estimate of Eq. 14.  Warps of a
 // persistent grid take items from a queue, so equal-cost items of one leaf
 // spread across SMs and the heavy leaves of clustered inputs do not pin one
-// SM.  Each target's sum runs in one lane in a fixed source order: results
-// do not depend on which warp ran the item.
+// SM.  An item with few targets (small leaves: a uniform layout holds about
+// 16 blobs per leaf) would leave most lanes idle, so its warp splits into S
+// groups of lanes: each group holds all the item's targets and takes every
+// S-th source, and the S partial sums of a target are added by a fixed
+// butterfly of warp shuffles.  The order of every sum depends only on the
+// item's target count: results do not depend on which warp ran the item.
 //
 // Mixed path (FP32).  Coordinates are leaf-relative in leaf units; with
 // rho^2 = |dx|^2 in leaf units and q = kappa rho^2, kappa = w^2 / 2 sigma^2,
@@ -37,6 +41,16 @@ __device__ __forceinline__ uint64_t global_ns() {
 // ----------------------------------------------------------------------------
 // Work list
 // ----------------------------------------------------------------------------
+// log2 of the lanes that hold the targets of an item with nt targets, r per
+// lane: the smallest power of two >= ceil(nt / r), at most 32.  The other
+// 32 / 2^lw lane groups split the item's sources.
+__host__ __device__ __forceinline__ int p2p_group_log2(uint32_t nt, int r) {
+    const uint32_t h = (nt + uint32_t(r) - 1) / uint32_t(r);
+    int lw = 0;
+    while (lw < 5 && (1u << lw) < h) ++lw;
+    return lw;
+}
+
 __global__ void __launch_bounds__(256) k_p2p_count(const Task *__restrict__ tasks, int ntasks,
                                                    const InstDesc *__restrict__ insts,
                                                    const uint32_t *__restrict__ start, int tpi,
@@ -82,7 +96,8 @@ __global__ void __launch_bounds__(256) k_p2p_emit(const Task *__restrict__ tasks
                                                   const uint32_t *__restrict__ start, int tpi,
                                                   const uint32_t *__restrict__ cnt,
                                                   const uint32_t *__restrict__ off,
-                                                  uint4 *__restrict__ items) {
+                                                  uint4 *__restrict__ items,
+                                                  uint32_t *__restrict__ wclass) {
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
     const int64_t m = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
@@ -90,19 +105,61 @@ __global__ void __launch_bounds__(256) k_p2p_emit(const Task *__restrict__ tasks
     const InstDesc &d = insts[t.inst];
     const uint32_t c = cnt[d.loff + m];
     if (!c) return;
-    const uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+    const uint32_t *st = start + d.soff;
+    const uint32_t s0 = st[m], s1 = st[m + 1];
     const uint32_t o = off[d.loff + m];
+    // sources of the item: the blobs of the leaf and its neighbours
+    uint32_t src = 0;
+    if (wclass) {
+        const int nside = 1 << d.L;
+        const int ix = int(compact_bits(uint32_t(m))), iy = int(compact_bits(uint32_t(m) >> 1));
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int sx = ix + dx, sy = iy + dy;
+                if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
+                const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
+                src += st[nm + 1] - st[nm];
+            }
+    }
     for (uint32_t i = 0; i < c; ++i) {
         const uint32_t f = s0 + i * uint32_t(tpi);
         const uint32_t nt = (s1 - f) < uint32_t(tpi) ? (s1 - f) : uint32_t(tpi);
         items[o + i] = make_uint4(uint32_t(t.inst), uint32_t(m), f, nt);
+        // work class of the item (Eq. 14, n_nd N_i^2 term: targets x sources).
+        // Every lane of the warp runs the source loop of its group, target
+        // slot filled or not, so the cost is the sources per lane group,
+        // ceil(src / S) with S groups.  Class = log2(cost) in quarter steps,
+        // stored as 127 - class so that an ascending sort is heaviest first.
+        if (wclass) {
+            const int ns = 5 - p2p_group_log2(nt, tpi / 32);  // log2 S
+            const uint32_t cost = (src + (1u << ns) - 1) >> ns;
+            const int e = 31 - __clz(int(cost));  // cost >= 1: the leaf's own blobs
+            const uint32_t frac = e >= 2 ? (cost >> (e - 2)) & 3u : (cost << (2 - e)) & 3u;
+            wclass[o + i] = 127u - (uint32_t(e) * 4u + frac);
+        }
     }
+}
+
+// Invalid tail of the item array (beyond the device-side count) sorts last.
+__global__ void __launch_bounds__(256) k_item_tail(uint32_t *__restrict__ wclass, int64_t cap,
+                                                   const uint32_t *ctrl) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < cap && i >= int64_t(ctrl[CTRL_NITEMS])) wclass[i] = 255u;
+}
+
+__global__ void __launch_bounds__(256) k_item_permute(const uint4 *__restrict__ in,
+                                                      const uint32_t *__restrict__ perm,
+                                                      uint4 *__restrict__ out, int64_t cap,
+                                                      const uint32_t *ctrl) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r < cap && r < int64_t(ctrl[CTRL_NITEMS])) out[r] = in[perm[r]];
 }
 
 cudaError_t launch_p2p_worklist(const Task *tasks, int ntasks, int64_t nblocks,
                                 const InstDesc *insts, const uint32_t *start, int64_t nleaves,
                                 int tpi, uint32_t *cnt, uint32_t *off, uint32_t *scan_scratch,
-                                uint4 *items, uint32_t *ctrl, cudaStream_t st, uint64_t *launches) {
+                                uint4 *items, uint32_t *ctrl, const P2POrder *order,
+                                cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
     k_p2p_count<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, tpi, cnt, ctrl);
     PF_LAUNCHED(1);
@@ -110,7 +167,21 @@ cudaError_t launch_p2p_worklist(const Task *tasks, int ntasks, int64_t nblocks,
     if (e != cudaSuccess) return e;
     e = exclusive_scan(cnt, off, nleaves, scan_scratch, ctrl + CTRL_NITEMS, st, launches);
     if (e != cudaSuccess) return e;
-    k_p2p_emit<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, tpi, cnt, off, items);
+    uint4 *emit_to = order ? order->items_unsorted : items;
+    k_p2p_emit<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, tpi, cnt, off, emit_to,
+                                                  order ? order->kA : nullptr);
+    PF_LAUNCHED(1);
+    if ((e = cudaGetLastError()) != cudaSuccess || !order) return e;
+    // heaviest items first: one stable 8-bit radix pass over the work classes
+    const int64_t cap = order->cap;
+    const unsigned g = unsigned((cap + 255) / 256);
+    k_item_tail<<<g, 256, 0, st>>>(order->kA, cap, ctrl);
+    PF_LAUNCHED(1);
+    bool in_first = true;
+    e = radix_sort(order->kA, order->vA, order->kB, order->vB, cap, 8, order->hist, scan_scratch,
+                   &in_first, st, launches);
+    if (e != cudaSuccess) return e;
+    k_item_permute<<<g, 256, 0, st>>>(emit_to, in_first ? order->vA : order->vB, items, cap, ctrl);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
@@ -139,6 +210,24 @@ __device__ __forceinline__ float g_of(const float (&a)[DEG + 1], float r2, float
     return g;
 }
 
+// One source against the lane's two targets (a, b), both in the source
+// leaf's frame.
+template <int DEG, bool GENERAL>
+__device__ __forceinline__ void pair2(const float4 s, float xa, float ya, float xb, float yb,
+                                      const float (&a)[DEG + 1], float kappa, float split,
+                                      float &ua, float &va, float &ub, float &vb) {
+    const float dxa = xa - s.x, dya = ya - s.y;
+    const float dxb = xb - s.x, dyb = yb - s.y;
+    const float r2a = fmaf(dxa, dxa, dya * dya);
+    const float r2b = fmaf(dxb, dxb, dyb * dyb);
+    const float fa = s.z * g_of<DEG, GENERAL>(a, r2a, kappa, split);
+    const float fb = s.z * g_of<DEG, GENERAL>(a, r2b, kappa, split);
+    ua = fmaf(-dya, fa, ua);
+    va = fmaf(dxa, fa, va);
+    ub = fmaf(-dyb, fb, ub);
+    vb = fmaf(dxb, fb, vb);
+}
+
 template <int DEG, bool GENERAL>
 __global__ void __launch_bounds__(P2P_THREADS) k_p2p_mixed(
     const uint4 *__restrict__ items, uint32_t *ctrl, const InstDesc *__restrict__ insts,
@@ -161,8 +250,12 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_mixed(
         const float kappa = d.kappa, split = d.qsplit_rho2;
         const uint32_t m = item.y;
         const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
-        const uint32_t ta = item.z + lane, tb = item.z + lane + 32;
-        const bool has_a = uint32_t(lane) < item.w, has_b = uint32_t(lane + 32) < item.w;
+        // lane = (source group grp, target slot k); targets k and k + W
+        const int lw = p2p_group_log2(item.w, 2);
+        const uint32_t W = 1u << lw, S = 32u >> lw;
+        const uint32_t grp = uint32_t(lane) >> lw, k = uint32_t(lane) & (W - 1u);
+        const uint32_t ta = item.z + k, tb = item.z + k + W;
+        const bool has_a = k < item.w, has_b = k + W < item.w;
         const float4 ra = has_a ? rec[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 rb = has_b ? rec[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
         float ua = 0.f, va = 0.f, ub = 0.f, vb = 0.f;
@@ -178,21 +271,26 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_mixed(
                 const uint32_t j0 = st[nm], j1 = st[nm + 1];
                 const float xa = ra.x - float(dx), ya = ra.y - float(dy);
                 const float xb = rb.x - float(dx), yb = rb.y - float(dy);
+                // the stride-1 loop keeps constant load offsets after unrolling
+                if (S == 1) {
 #pragma unroll 4
-                for (uint32_t j = j0; j < j1; ++j) {
-                    const float4 s = __ldg(rec + j);
-                    const float dxa = xa - s.x, dya = ya - s.y;
-                    const float dxb = xb - s.x, dyb = yb - s.y;
-                    const float r2a = fmaf(dxa, dxa, dya * dya);
-                    const float r2b = fmaf(dxb, dxb, dyb * dyb);
-                    const float fa = s.z * g_of<DEG, GENERAL>(a, r2a, kappa, split);
-                    const float fb = s.z * g_of<DEG, GENERAL>(a, r2b, kappa, split);
-                    ua = fmaf(-dya, fa, ua);
-                    va = fmaf(dxa, fa, va);
-                    ub = fmaf(-dyb, fb, ub);
-                    vb = fmaf(dxb, fb, vb);
+                    for (uint32_t j = j0; j < j1; ++j)
+                        pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
+                                            va, ub, vb);
+                } else {
+#pragma unroll 4
+                    for (uint32_t j = j0 + grp; j < j1; j += S)
+                        pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
+                                            va, ub, vb);
                 }
             }
+        }
+        // add the partial sums of the source groups (fixed butterfly)
+        for (uint32_t o = W; o < 32u; o <<= 1) {
+            ua += __shfl_xor_sync(0xffffffffu, ua, int(o));
+            va += __shfl_xor_sync(0xffffffffu, va, int(o));
+            ub += __shfl_xor_sync(0xffffffffu, ub, int(o));
+            vb += __shfl_xor_sync(0xffffffffu, vb, int(o));
         }
         // far field: L2P of the leaf's local expansion, w = (1/r) sum c_m zeta^m
         float fua = 0.f, fva = 0.f, fub = 0.f, fvb = 0.f;
@@ -213,7 +311,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_mixed(
             fub = d.cfar * wb.y; fvb = d.cfar * wb.x;
         }
         const float cn = d.cnear;
-        if (has_a) {
+        if (has_a && grp == 0) {
             const int64_t q = int64_t(__float_as_uint(ra.w)) - d.poff;
             const float uo = fmaf(cn, ua, fua), vo = fmaf(cn, va, fva);
             if (dtype_f32) {
@@ -224,7 +322,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_mixed(
                 static_cast<double *>(d.v)[q] = double(vo);
             }
         }
-        if (has_b) {
+        if (has_b && grp == 0) {
             const int64_t q = int64_t(__float_as_uint(rb.w)) - d.poff;
             const float uo = fmaf(cn, ub, fub), vo = fmaf(cn, vb, fvb);
             if (dtype_f32) {
@@ -265,8 +363,11 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
         const int L = d.L;
         const uint32_t m = item.y;
         const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
-        const bool has = uint32_t(lane) < item.w;
-        const uint32_t ti = item.z + (has ? lane : 0);
+        const int lw = p2p_group_log2(item.w, 1);
+        const uint32_t W = 1u << lw, S = 32u >> lw;
+        const uint32_t grp = uint32_t(lane) >> lw, k = uint32_t(lane) & (W - 1u);
+        const bool has = k < item.w;
+        const uint32_t ti = item.z + (has ? k : 0u);
         const double x = xs[ti], y = ys[ti];
         const double inv2s2 = d.inv2s2;
         double su = 0.0, sv = 0.0;
@@ -280,7 +381,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
                 if (sx < 0 || sx >= nside) continue;
                 const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
                 const uint32_t j0 = st[nm], j1 = st[nm + 1];
-                for (uint32_t j = j0; j < j1; ++j) {
+                for (uint32_t j = j0 + grp; j < j1; j += S) {
                     const double ddx = x - __ldg(xs + j), ddy = y - __ldg(ys + j);
                     const double r2 = ddx * ddx + ddy * ddy;
                     if (r2 > 0.0) {
@@ -290,6 +391,10 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
                     }
                 }
             }
+        }
+        for (uint32_t o = W; o < 32u; o <<= 1) {
+            su += __shfl_xor_sync(0xffffffffu, su, int(o));
+            sv += __shfl_xor_sync(0xffffffffu, sv, int(o));
         }
         double fu = 0.0, fv = 0.0;
         if (L >= 2) {
@@ -308,7 +413,7 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
             fu = d.cfar64 * w.y;
             fv = d.cfar64 * w.x;
         }
-        if (has) {
+        if (has && grp == 0) {
             const int64_t q = int64_t(perm[ti]) - d.poff;
             const double uo = su * d.cnear64 + fu, vo = sv * d.cnear64 + fv;
             if (dtype_f32) {
@@ -329,168 +434,13 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
 }
 
 // ----------------------------------------------------------------------------
-// Mixed-precision P2P + L2P, the two targets of a lane packed in FP32x2.
-//
-// Same arithmetic and source order as k_p2p_mixed, but every FP32 operation of
-// the pair loop acts on (target a, target b) at once with the packed FP32x2
-// instructions, which halves the issued instructions per pair.  To avoid
-// building broadcast operands in registers, the gather stores each source
-// already duplicated: src2[j] = (-xi, -xi, eta, eta), gam2[j] = (gamma, gamma).
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
-
-template <int DEG>
-__device__ __forceinline__ float2 poly2_eval(const float2 (&a)[DEG + 1], float2 s) {
-    float2 g = a[DEG];
-#pragma unroll
-    for (int k = DEG - 1; k >= 0; --k) g = __ffma2_rn(g, s, a[k]);
-    return g;
-}
-
-template <int DEG, bool GENERAL>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p_packed(
-    const uint4 *__restrict__ items, uint32_t *ctrl, const InstDesc *__restrict__ insts,
-    const uint32_t *__restrict__ start, const float4 *__restrict__ rec,
-    const float4 *__restrict__ src2, const float2 *__restrict__ gam2,
-    const float2 *__restrict__ le, int dtype_f32, unsigned long long *busy) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t nitems = *reinterpret_cast<volatile uint32_t *>(ctrl + CTRL_NITEMS);
-    const uint64_t t_begin = busy ? global_ns() : 0;
-    for (;;) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(ctrl + CTRL_QUEUE, 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= nitems) break;
-        const uint4 item = items[it];
-        const InstDesc &d = insts[item.x];
-        const int L = d.L;
-        float2 a[DEG + 1];
-#pragma unroll
-        for (int k = 0; k <= DEG; ++k) a[k] = pk(d.poly[k], d.poly[k]);
-        const float kappa = d.kappa, split = d.qsplit_rho2;
-        const uint32_t m = item.y;
-        const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
-        const uint32_t ta = item.z + lane, tb = item.z + lane + 32;
-        const bool has_a = uint32_t(lane) < item.w, has_b = uint32_t(lane + 32) < item.w;
-        const float4 ra = has_a ? rec[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 rb = has_b ? rec[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 u2 = pk(0.f, 0.f), v2 = pk(0.f, 0.f);
-        const uint32_t *st = start + d.soff;
-        const int nside = 1 << L;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int sy = iy + dy;
-            if (sy < 0 || sy >= nside) continue;
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int sx = ix + dx;
-                if (sx < 0 || sx >= nside) continue;
-                const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
-                const uint32_t j0 = st[nm], j1 = st[nm + 1];
-                // targets in the source leaf's frame: x_t - dx, and -(y_t - dy)
-                const float2 tx = pk(ra.x - float(dx), rb.x - float(dx));
-                const float2 tyn = pk(float(dy) - ra.y, float(dy) - rb.y);
-#pragma unroll 4
-                for (uint32_t j = j0; j < j1; ++j) {
-                    const float4 s = __ldg(src2 + j);
-                    const float2 gj = __ldg(gam2 + j);
-                    const float2 dxv = __fadd2_rn(tx, pk(s.x, s.y));   // x_t - x_s
-                    const float2 dyn = __fadd2_rn(pk(s.z, s.w), tyn);  // y_s - y_t
-                    const float2 r2 = __ffma2_rn(dxv, dxv, __fmul2_rn(dyn, dyn));
-                    float2 g = poly2_eval<DEG>(a, r2);
-                    if (GENERAL) {
-                        const float qx = kappa * r2.x, qy = kappa * r2.y;
-                        const float ex = __fdividef(1.0f - __expf(-qx), qx);
-                        const float ey = __fdividef(1.0f - __expf(-qy), qy);
-                        g.x = r2.x < split ? g.x : ex;
-                        g.y = r2.y < split ? g.y : ey;
-                    }
-                    const float2 f = __fmul2_rn(gj, g);
-                    u2 = __ffma2_rn(dyn, f, u2);
-                    v2 = __ffma2_rn(dxv, f, v2);
-                }
-            }
-        }
-        // far field: L2P of the leaf's local expansion, w = (1/r) sum c_m zeta^m
-        float fua = 0.f, fva = 0.f, fub = 0.f, fvb = 0.f;
-        if (L >= 2) {
-            const int p = d.p;
-            const float2 *c = le + d.eoff + (lvl_off(L) + box_index(L, uint32_t(ix), uint32_t(iy))) * p;
-            float2 wa = __ldg(c + p - 1), wb = wa;
-            for (int k = p - 2; k >= 0; --k) {
-                const float2 ck = __ldg(c + k);
-                const float wax = fmaf(wa.x, ra.x, fmaf(-wa.y, ra.y, ck.x));
-                const float way = fmaf(wa.x, ra.y, fmaf(wa.y, ra.x, ck.y));
-                const float wbx = fmaf(wb.x, rb.x, fmaf(-wb.y, rb.y, ck.x));
-                const float wby = fmaf(wb.x, rb.y, fmaf(wb.y, rb.x, ck.y));
-                wa = make_float2(wax, way);
-                wb = make_float2(wbx, wby);
-            }
-            fua = d.cfar * wa.y; fva = d.cfar * wa.x;
-            fub = d.cfar * wb.y; fvb = d.cfar * wb.x;
-        }
-        const float cn = d.cnear;
-        if (has_a) {
-            const int64_t q = int64_t(__float_as_uint(ra.w)) - d.poff;
-            const float uo = fmaf(cn, u2.x, fua), vo = fmaf(cn, v2.x, fva);
-            if (dtype_f32) {
-                static_cast<float *>(d.u)[q] = uo;
-                static_cast<float *>(d.v)[q] = vo;
-            } else {
-                static_cast<double *>(d.u)[q] = double(uo);
-                static_cast<double *>(d.v)[q] = double(vo);
-            }
-        }
-        if (has_b) {
-            const int64_t q = int64_t(__float_as_uint(rb.w)) - d.poff;
-            const float uo = fmaf(cn, u2.y, fub), vo = fmaf(cn, v2.y, fvb);
-            if (dtype_f32) {
-                static_cast<float *>(d.u)[q] = uo;
-                static_cast<float *>(d.v)[q] = vo;
-            } else {
-                static_cast<double *>(d.u)[q] = double(uo);
-                static_cast<double *>(d.v)[q] = double(vo);
-            }
-        }
-    }
-    if (busy && lane == 0) {
-        const uint64_t t_end = global_ns();
-        const size_t gw = size_t(blockIdx.x) * (P2P_THREADS / 32) + (threadIdx.x >> 5);
-        busy[2 * gw] = t_begin;
-        busy[2 * gw + 1] = t_end;
-    }
-}
-
-// ----------------------------------------------------------------------------
 // Launch helpers
 // ----------------------------------------------------------------------------
 typedef void (*MixedKernel)(const uint4 *, uint32_t *, const InstDesc *, const uint32_t *,
                             const float4 *, const float2 *, int, unsigned long long *);
-typedef void (*PackedKernel)(const uint4 *, uint32_t *, const InstDesc *, const uint32_t *,
-                             const float4 *, const float4 *, const float2 *, const float2 *, int,
-                             unsigned long long *);
-
 template <int D>
 static MixedKernel pick2(int general) {
     return general ? k_p2p_mixed<D, true> : k_p2p_mixed<D, false>;
-}
-
-template <int D>
-static PackedKernel pickp(int general) {
-    return general ? k_p2p_packed<D, true> : k_p2p_packed<D, false>;
-}
-
-static PackedKernel pick_packed(int deg, int general) {
-    switch (deg) {
-        case 4: return pickp<4>(general);
-        case 5: return pickp<5>(general);
-        case 6: return pickp<6>(general);
-        case 7: return pickp<7>(general);
-        case 8: return pickp<8>(general);
-        case 9: return pickp<9>(general);
-        case 10: return pickp<10>(general);
-        case 11: return pickp<11>(general);
-        case 12: return pickp<12>(general);
-        default: return nullptr;
-    }
 }
 
 static MixedKernel pick_mixed(int deg, int general) {
@@ -520,13 +470,9 @@ static int sm_count() {
     return g_sms;
 }
 
-int p2p_grid(int precision_mixed, int deg, int general, int packed) {
+int p2p_grid(int precision_mixed, int deg, int general) {
     int per_sm = 1;
-    if (precision_mixed && packed) {
-        PackedKernel k = pick_packed(deg, general);
-        if (!k) return 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, P2P_THREADS, 0);
-    } else if (precision_mixed) {
+    if (precision_mixed) {
         MixedKernel k = pick_mixed(deg, general);
         if (!k) return 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, P2P_THREADS, 0);
@@ -539,19 +485,11 @@ int p2p_grid(int precision_mixed, int deg, int general, int packed) {
 
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
                              const InstDesc *insts, const uint32_t *start, const float4 *rec,
-                             const float4 *src2, const float2 *gam2, const float2 *le,
-                             int dtype_f32, unsigned long long *busy, cudaStream_t st,
-                             uint64_t *launches) {
-    if (src2 && gam2) {
-        PackedKernel k = pick_packed(deg, general);
-        if (!k) return cudaErrorInvalidValue;
-        k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, src2, gam2, le, dtype_f32,
-                                        busy);
-    } else {
-        MixedKernel k = pick_mixed(deg, general);
-        if (!k) return cudaErrorInvalidValue;
-        k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, le, dtype_f32, busy);
-    }
+                             const float2 *le, int dtype_f32, unsigned long long *busy,
+                             cudaStream_t st, uint64_t *launches) {
+    MixedKernel k = pick_mixed(deg, general);
+    if (!k) return cudaErrorInvalidValue;
+    k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, le, dtype_f32, busy);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }

@@ -28,6 +28,28 @@ __device__ __forceinline__ uint32_t bin_coord(double x, double x0, double scale,
     return uint32_t(f);
 }
 
+// FP32 shortcut (FP64 arithmetic is slow on this GPU).  With xf, x0f and
+// scalef the FP32 roundings of x, x0 and scale, s32 = fl(fl(xf - x0f) scalef)
+// differs from the FP64 s above by at most 4 u scale (|x| + |x0|) plus terms
+// of order u^2 (u = 2^-24: one rounding each of xf, x0f, scalef, the
+// difference and the product); the margin m = 8 u scale (|x| + |x0|) also
+// covers the roundings of s32 -/+ m.  If both ends of [s32 - m, s32 + m] fall
+// in the same bin and inside (0.5, nb - 0.5), the FP64 value is in that bin
+// too, and strictly inside the domain (no clamping, no out-of-domain report).
+// Otherwise (near a bin edge or the domain boundary, NaN, Inf) returns false
+// and the caller takes the FP64 path.  The result is therefore bit-identical.
+__device__ __forceinline__ bool bin_coord_fast(float xf, float x0f, float scalef, uint32_t nb,
+                                               uint32_t *bin) {
+    const float s = __fmul_rn(__fsub_rn(xf, x0f), scalef);
+    const float m = __fmul_rn(__fmul_rn(__fadd_rn(fabsf(xf), fabsf(x0f)), scalef), 0x1p-21f);
+    const float lo = __fsub_rn(s, m), hi = __fadd_rn(s, m);
+    if (!(lo > 0.5f && hi < float(nb) - 0.5f)) return false;
+    const float f = floorf(lo);
+    if (f != floorf(hi)) return false;
+    *bin = uint32_t(f);
+    return true;
+}
+
 template <typename TIn>
 __global__ void __launch_bounds__(256) k_morton(const Task *__restrict__ tasks, int ntasks,
                                                 const InstDesc *__restrict__ insts,
@@ -37,13 +59,18 @@ __global__ void __launch_bounds__(256) k_morton(const Task *__restrict__ tasks, 
     const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
     if (j >= t.count) return;
     const InstDesc &d = insts[t.inst];
-    const double x = double(static_cast<const TIn *>(d.x)[j]);
-    const double y = double(static_cast<const TIn *>(d.y)[j]);
-    const double x1 = __dadd_rn(d.x0, d.width), y1 = __dadd_rn(d.y0, d.width);
-    if (!(x >= d.x0 && x <= x1 && y >= d.y0 && y <= y1)) set_status(status, ST_EDOMAIN);
+    const TIn xin = static_cast<const TIn *>(d.x)[j];
+    const TIn yin = static_cast<const TIn *>(d.y)[j];
     const uint32_t nb = 1u << d.L;
-    const uint32_t ix = bin_coord(x, d.x0, d.scale, nb);
-    const uint32_t iy = bin_coord(y, d.y0, d.scale, nb);
+    uint32_t ix, iy;
+    if (!(bin_coord_fast(float(xin), d.x0h, d.sh, nb, &ix) &&
+          bin_coord_fast(float(yin), d.y0h, d.sh, nb, &iy))) {
+        const double x = double(xin), y = double(yin);
+        const double x1 = __dadd_rn(d.x0, d.width), y1 = __dadd_rn(d.y0, d.width);
+        if (!(x >= d.x0 && x <= x1 && y >= d.y0 && y <= y1)) set_status(status, ST_EDOMAIN);
+        ix = bin_coord(x, d.x0, d.scale, nb);
+        iy = bin_coord(y, d.y0, d.scale, nb);
+    }
     keys[d.poff + j] = d.key_hi | morton_key(ix, iy);
 }
 
@@ -332,14 +359,40 @@ __global__ void __launch_bounds__(256) k_gather_f64(const Task *__restrict__ tas
 
 // Mixed path: leaf-relative coordinates in leaf units, computed in FP64 and
 // rounded once; .w carries the batch index of the particle (for the output).
+//
+// Leaf-relative coordinate (x - c) scale, c = x0 + (i + 1/2) w, computed as
+// (x - x0) scale - (i + 1/2) in float-float arithmetic (x0 = x0h + x0l,
+// scale = sh + sl; two-sum for the difference, an FMA for the product's
+// error): the result before its final rounding to FP32 is within about 2^-44
+// of the exact value, relative to (x - x0) scale.
+__device__ __forceinline__ void split_ff(float x, float *h, float *l) { *h = x; *l = 0.0f; }
+__device__ __forceinline__ void split_ff(double x, float *h, float *l) {
+    *h = float(x);
+    *l = float(x - double(*h));
+}
+template <typename TIn>
+__device__ __forceinline__ float leaf_coord(TIn xin, float x0h, float x0l, float sh, float sl,
+                                            uint32_t i) {
+    float xh, xl;
+    split_ff(xin, &xh, &xl);
+    // t = x - x0 = th + tl
+    const float th = __fsub_rn(xh, x0h);
+    const float bb = __fsub_rn(th, xh);
+    float tl = __fadd_rn(__fsub_rn(xh, __fsub_rn(th, bb)), __fsub_rn(-x0h, bb));
+    tl = __fadd_rn(tl, __fsub_rn(xl, x0l));
+    // s = t scale = p + e
+    const float p = __fmul_rn(th, sh);
+    float e = __fmaf_rn(th, sh, -p);
+    e = __fmaf_rn(th, sl, __fmaf_rn(tl, sh, e));
+    return __fadd_rn(__fsub_rn(p, __fadd_rn(float(i), 0.5f)), e);
+}
+
 template <typename TIn>
 __global__ void __launch_bounds__(256) k_gather_mixed(const Task *__restrict__ tasks, int ntasks,
                                                       const InstDesc *__restrict__ insts,
                                                       const uint32_t *__restrict__ perm,
                                                       const uint32_t *__restrict__ skeys,
-                                                      float4 *__restrict__ rec,
-                                                      float4 *__restrict__ src2,
-                                                      float2 *__restrict__ gam2) {
+                                                      float4 *__restrict__ rec) {
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
     const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
@@ -350,21 +403,15 @@ __global__ void __launch_bounds__(256) k_gather_mixed(const Task *__restrict__ t
     const int64_t q = int64_t(qb) - d.poff;
     const uint32_t m = skeys[r] & ((d.L >= 16) ? 0xffffffffu : ((1u << (2 * d.L)) - 1u));
     const uint32_t ix = compact_bits(m), iy = compact_bits(m >> 1);
-    const double cx = d.x0 + (double(ix) + 0.5) * d.wleaf;
-    const double cy = d.y0 + (double(iy) + 0.5) * d.wleaf;
-    const double x = double(static_cast<const TIn *>(d.x)[q]);
-    const double y = double(static_cast<const TIn *>(d.y)[q]);
-    const double g = double(static_cast<const TIn *>(d.g)[q]);
+    const TIn x = static_cast<const TIn *>(d.x)[q];
+    const TIn y = static_cast<const TIn *>(d.y)[q];
+    const TIn g = static_cast<const TIn *>(d.g)[q];
     float4 o;
-    o.x = float((x - cx) * d.scale);
-    o.y = float((y - cy) * d.scale);
+    o.x = leaf_coord(x, d.x0h, d.x0l, d.sh, d.sl, ix);
+    o.y = leaf_coord(y, d.y0h, d.y0l, d.sh, d.sl, iy);
     o.z = float(g);
     o.w = __uint_as_float(qb);
     rec[r] = o;
-    if (src2) {
-        src2[r] = make_float4(-o.x, -o.x, o.y, o.y);
-        gam2[r] = make_float2(o.z, o.z);
-    }
 }
 
 cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
@@ -381,15 +428,15 @@ cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, co
 
 cudaError_t launch_gather_mixed(const Task *tasks, int ntasks, int64_t nblocks,
                                 const InstDesc *insts, int dtype_f32, const uint32_t *perm,
-                                const uint32_t *skeys, float4 *rec, float4 *src2, float2 *gam2,
-                                cudaStream_t st, uint64_t *launches) {
+                                const uint32_t *skeys, float4 *rec, cudaStream_t st,
+                                uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
     if (dtype_f32)
-        k_gather_mixed<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys, rec,
-                                                                 src2, gam2);
+        k_gather_mixed<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys,
+                                                                 rec);
     else
-        k_gather_mixed<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys, rec,
-                                                                  src2, gam2);
+        k_gather_mixed<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys,
+                                                                  rec);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }

@@ -82,20 +82,24 @@ def test_reused_context_matches_fresh_context():
     assert np.array_equal(u, uf) and np.array_equal(v, vf)
 
 
-def test_packed_and_scalar_p2p_agree_bitwise():
-    # the FP32x2 kernel performs the scalar kernel's operations, in the same
-    # order, two targets at a time
+def test_p2p_dispatch_order_does_not_change_results():
+    # each target's sum runs in one lane in a fixed source order, so taking
+    # the work items heaviest first (mode 0) or in leaf order (mode 1) gives
+    # the same bits, in both precisions
     _lib = G.lib()
-    outs = []
-    for packed in (1, 0):
-        for w in (W.tiny(60_000, 17, L=6, p=12, clustered_frac=0.5, dtype="f32"),
-                  W.tiny(20_000, 18, L=4, p=12, sigma=0.003)):  # second one: exp branch
-            ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype=w.dtype)
-            ctx.set_option(_lib.PETFMM_OPT_P2P_PACKED, packed)
+    cases = [(W.tiny(60_000, 21, L=6, p=12, clustered_frac=0.7, dtype="f32"), "mixed"),
+             (W.tiny(30_000, 22, L=5, p=14, clustered_frac=0.7), "fp64"),
+             (W.tiny(1, 23, L=3, p=8), "mixed")]
+    for w, prec in cases:
+        outs = []
+        for mode in (0, 1):
+            ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision=prec, dtype=w.dtype)
+            ctx.set_option(_lib.PETFMM_OPT_P2P_MODE, mode)
+            ctx.set_option(_lib.PETFMM_OPT_POISON, 1)
             x, y, g = G.to_dev((w.x, w.y, w.gamma))
             u, v = ctx.evaluate(x, y, g)
             assert ctx.sync() == 0
             outs.append((u.cpu().numpy(), v.cpu().numpy()))
             ctx.close()
-    for (ua, va), (ub, vb) in zip(outs[:2], outs[2:]):
-        assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+        assert np.all(np.isfinite(outs[0][0])) and np.all(np.isfinite(outs[0][1]))
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])

@@ -100,3 +100,32 @@ def test_outside_particle_reports_edomain_then_recovers():
         ctx.sync()
     assert e.value.code == _lib.PETFMM_EDOMAIN
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("dom", [(0.1234567891, -0.3718281828, 0.7071067811865476),
+                                 (1.0e5 + 0.3, -2.5e4, 3.0)])
+def test_binning_near_bin_edges(orc, dtype, dom):
+    # The kernel bins in FP32 where that provably gives the FP64 bin and falls
+    # back to FP64 otherwise: points on and a few ulps around every bin edge
+    # of one row, in an awkward domain (x0 and the scale not representable in
+    # FP32; the second one so far from the origin that FP32 never decides)
+    L = 10
+    nb = 1 << L
+    x0, y0, wd = dom
+    ft = np.float32 if dtype == "f32" else np.float64
+    e = (x0 + np.arange(nb + 1) * (wd / nb)).astype(ft)
+    x = [e]
+    for direction in (np.inf, -np.inf):
+        v = e
+        for _ in range(3):
+            v = np.nextafter(v, ft(direction))
+            x.append(v)
+    x = np.concatenate(x)
+    xd = x.astype(np.float64)
+    x = x[(xd >= x0) & (xd <= x0 + wd)]
+    rng = np.random.default_rng(11)
+    y = (y0 + rng.uniform(0.01 * wd, 0.99 * wd, x.size)).astype(ft)
+    g = rng.uniform(-1, 1, x.size).astype(ft)
+    w = W.Workload("bin-edges", x, y, g, 0.01, dom, L, 8, dtype)
+    _check(orc, w)
