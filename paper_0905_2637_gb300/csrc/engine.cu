@@ -107,7 +107,7 @@ struct petfmm_ctx {
     uint64_t launches = 0, evaluations = 0;
 
     DevBuf keysA, keysB, valsA, valsB, hist, scratch, start, xs, ys, gs, rec, me, le, cnt, off,
-        items, ctrl, plan_dev, busy, ucount, items_u, ikA, ikB, ivA, ivB, ihist;
+        items, ctrl, plan_dev, busy, ucount, recu, occ, items_u, ikA, ikB, ivA, ivB, ihist;
     DevBuf hx, hy, hg, hu, hv;  // device staging for petfmm_evaluate_host
     std::map<int, OpTables> tables;
 
@@ -377,7 +377,7 @@ int build_plan(int precision, bool use_tc, int tc_segmax, const std::vector<Prob
         add_task(pl.morton, i, d.L, d.n, 256);
         add_task(pl.start, i, d.L, nleaf + 1, 256);
         add_task(pl.particles, i, d.L, d.n, 256);
-        add_task(pl.leaves_p2m, i, d.L, nleaf, P2M_WARPS);
+        add_task(pl.leaves_p2m, i, d.L, nleaf, 256);
         add_task(pl.leaves_wl, i, d.L, nleaf, 256);
         for (int l = 2; l <= d.L; ++l) {
             // levels the tensor cores can take get both launches: the tensor
@@ -388,7 +388,7 @@ int build_plan(int precision, bool use_tc, int tc_segmax, const std::vector<Prob
                 add_task(pl.m2l_tc, i, l, m2l_tc_units(l, tc_segmax), 1);
                 pl.tc_smem = std::max(pl.tc_smem, m2l_tc_smem_bytes(d.p, m2l_tc_seg(l, tc_segmax)));
             }
-            add_task(pl.m2l, i, l, int64_t(1) << (2 * l), M2L_WARPS);
+            add_task(pl.m2l, i, l, int64_t(1) << (2 * l), M2L_BOXES);
         }
         items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
     }
@@ -508,6 +508,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->start, size_t(pl.nstart) * 4, st));
     if (mixed) {
         PF_TRY(ensure(c->rec, size_t(N) * sizeof(float4), st));
+        PF_TRY(ensure(c->recu, size_t(N) * sizeof(float4), st));
         PF_TRY(ensure(c->me, size_t(pl.ncoef) * sizeof(float2), st));
         PF_TRY(ensure(c->le, size_t(pl.ncoef) * sizeof(float2), st));
     } else {
@@ -518,6 +519,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         PF_TRY(ensure(c->le, size_t(pl.ncoef) * sizeof(double2), st));
     }
     PF_TRY(ensure(c->cnt, size_t(pl.nleaves) * 4, st));
+    PF_TRY(ensure(c->occ, size_t(pl.nleaves) * sizeof(uint2), st));
     PF_TRY(ensure(c->off, size_t(pl.nleaves) * 4, st));
     PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
     PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks) * sizeof(uint32_t), st));
@@ -568,6 +570,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
 
     stage_mark(c, PETFMM_STAGE_MORTON);
     PF_CUDA(launch_morton(dtask + pl.morton.first, pl.morton.count, pl.morton.nblocks, dinst, f32, kA,
+                          mixed ? static_cast<float4 *>(c->recu.p) : nullptr,
                           reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
     stage_mark(c, PETFMM_STAGE_SORT);
     bool in_first = true;
@@ -580,23 +583,23 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                               start, st, lc));
     stage_mark(c, PETFMM_STAGE_GATHER);
     if (mixed)
-        PF_CUDA(launch_gather_mixed(dtask + pl.particles.first, pl.particles.count,
-                                    pl.particles.nblocks, dinst, f32, perm, skeys,
-                                    static_cast<float4 *>(c->rec.p), st, lc));
+        PF_CUDA(launch_gather_mixed(static_cast<const float4 *>(c->recu.p), perm,
+                                    static_cast<float4 *>(c->rec.p), N, st, lc));
     else
         PF_CUDA(launch_gather_f64(dtask + pl.particles.first, pl.particles.count,
                                   pl.particles.nblocks, dinst, f32, perm,
                                   static_cast<double *>(c->xs.p), static_cast<double *>(c->ys.p),
                                   static_cast<double *>(c->gs.p), st, lc));
     stage_mark(c, PETFMM_STAGE_P2M);
+    uint2 *occ = static_cast<uint2 *>(c->occ.p);
+    PF_CUDA(launch_occ_list(dtask + pl.leaves_p2m.first, pl.leaves_p2m.count, pl.leaves_p2m.nblocks,
+                            dinst, start, occ, ctrl, st, lc));
     if (mixed)
-        PF_CUDA(launch_p2m<float>(dtask + pl.leaves_p2m.first, pl.leaves_p2m.count,
-                                  pl.leaves_p2m.nblocks, dinst, pl.pmax, start, nullptr, nullptr,
+        PF_CUDA(launch_p2m<float>(occ, ctrl, pl.nleaves, dinst, pl.pmax, start, nullptr, nullptr,
                                   nullptr, static_cast<const float4 *>(c->rec.p),
                                   static_cast<float2 *>(c->me.p), st, lc));
     else
-        PF_CUDA(launch_p2m<double>(dtask + pl.leaves_p2m.first, pl.leaves_p2m.count,
-                                   pl.leaves_p2m.nblocks, dinst, pl.pmax, start,
+        PF_CUDA(launch_p2m<double>(occ, ctrl, pl.nleaves, dinst, pl.pmax, start,
                                    static_cast<const double *>(c->xs.p),
                                    static_cast<const double *>(c->ys.p),
                                    static_cast<const double *>(c->gs.p), nullptr,
@@ -741,7 +744,7 @@ int petfmm_destroy(petfmm_ctx *c) {
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                       &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
-                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB, &c->ihist, &c->hx, &c->hy,
+                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->recu, &c->occ, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB, &c->ihist, &c->hx, &c->hy,
                       &c->hg, &c->hu, &c->hv};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);

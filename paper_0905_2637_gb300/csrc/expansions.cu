@@ -16,8 +16,10 @@
 //   L2P  w(z) = r^-1 sum_m c^_m zeta^m
 // Costs (Sec. 5.2): P2M O(N_i p) per leaf, M2M and L2L O(p^2) per child,
 // M2L O(p^2 n_IL) per box with n_IL <= 27.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -208,10 +210,43 @@ void free_op_tables(OpTables *t) {
 }
 
 // ----------------------------------------------------------------------------
-// P2M: one warp per leaf.  Lanes take 32 particles at a time, write the
-// gamma * zeta^k powers to shared memory, and lane k sums column k in a fixed
-// order (deterministic).
+// P2M: one warp per occupied leaf.  k_occ_list collects the occupied leaves
+// (in no particular order); a persistent grid of warps strides over that
+// list, so no block is spent on an empty leaf and the dense leaves of a
+// cluster spread over all SMs.  Per leaf, lanes take 32 particles at a time,
+// write the gamma * zeta^k powers to shared memory, and lane k sums column k
+// in a fixed order: each leaf's expansion does not depend on which warp or
+// in which order the leaves were processed.
 // ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_occ_list(const Task *__restrict__ tasks, int ntasks,
+                                                  const InstDesc *__restrict__ insts,
+                                                  const uint32_t *__restrict__ start,
+                                                  uint2 *__restrict__ occ, uint32_t *ctrl) {
+    const int lane = threadIdx.x & 31;
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t m = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    bool o = false;
+    if (m < t.count) {
+        const uint32_t *st = start + insts[t.inst].soff;
+        o = st[m + 1] > st[m];
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, o);
+    uint32_t base = 0;
+    if (lane == 0 && b) base = atomicAdd(ctrl + CTRL_NOCC, uint32_t(__popc(b)));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (o) occ[base + __popc(b & ((1u << lane) - 1u))] = make_uint2(uint32_t(t.inst), uint32_t(m));
+}
+
+cudaError_t launch_occ_list(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                            const uint32_t *start, uint2 *occ, uint32_t *ctrl, cudaStream_t st,
+                            uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_occ_list<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, occ, ctrl);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
 template <typename R>
 __device__ __forceinline__ typename Cplx<R>::T mk2(R a, R b) {
     typename Cplx<R>::T r;
@@ -222,82 +257,178 @@ __device__ __forceinline__ typename Cplx<R>::T mk2(R a, R b) {
 
 template <typename R>
 __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m(
-    const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts, int pmax,
-    const uint32_t *__restrict__ start, const double *__restrict__ xs,
+    const uint2 *__restrict__ occ, const uint32_t *ctrl, const InstDesc *__restrict__ insts,
+    int pmax, const uint32_t *__restrict__ start, const double *__restrict__ xs,
     const double *__restrict__ ys, const double *__restrict__ gs, const float4 *__restrict__ rec,
     typename Cplx<R>::T *__restrict__ me) {
     using C2 = typename Cplx<R>::T;
     extern __shared__ unsigned char smem_raw[];
     C2 *buf = reinterpret_cast<C2 *>(smem_raw) + size_t(threadIdx.x >> 5) * 32 * pmax;
     const int lane = threadIdx.x & 31;
-    const int ti = find_task(tasks, ntasks, blockIdx.x);
-    const Task t = tasks[ti];
-    const int64_t m = (int64_t(blockIdx.x) - t.block0) * P2M_WARPS + (threadIdx.x >> 5);
-    if (m >= t.count) return;
-    const InstDesc &d = insts[t.inst];
-    const int p = d.p, L = d.L;
-    const uint32_t ix = compact_bits(uint32_t(m)), iy = compact_bits(uint32_t(m) >> 1);
-    const uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
-    if (s0 == s1) return;  // empty leaf: expansion never read
-    const double cx = d.x0 + (double(ix) + 0.5) * d.wleaf;
-    const double cy = d.y0 + (double(iy) + 0.5) * d.wleaf;
-    C2 acc0 = mk2<R>(R(0), R(0)), acc1 = mk2<R>(R(0), R(0));
-    for (uint32_t c0 = s0; c0 < s1; c0 += 32) {
-        const uint32_t j = c0 + lane;
-        C2 z, w;
-        if (j < s1) {
-            if (rec) {
-                const float4 r = rec[j];
-                z = mk2<R>(R(r.x), R(r.y));
-                w = mk2<R>(R(r.z), R(0));
+    const uint32_t nocc = ctrl[CTRL_NOCC];
+    const uint32_t nwarps = gridDim.x * P2M_WARPS;
+    for (uint32_t i = blockIdx.x * P2M_WARPS + (threadIdx.x >> 5); i < nocc; i += nwarps) {
+        const uint2 e = occ[i];
+        const InstDesc &d = insts[e.x];
+        const int p = d.p, L = d.L;
+        const uint32_t m = e.y;
+        const uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+        const uint32_t ix = compact_bits(m), iy = compact_bits(m >> 1);
+        const double cx = d.x0 + (double(ix) + 0.5) * d.wleaf;
+        const double cy = d.y0 + (double(iy) + 0.5) * d.wleaf;
+        C2 acc0 = mk2<R>(R(0), R(0)), acc1 = mk2<R>(R(0), R(0));
+        for (uint32_t c0 = s0; c0 < s1; c0 += 32) {
+            const uint32_t j = c0 + lane;
+            C2 z, w;
+            if (j < s1) {
+                if (rec) {
+                    const float4 r = rec[j];
+                    z = mk2<R>(R(r.x), R(r.y));
+                    w = mk2<R>(R(r.z), R(0));
+                } else {
+                    z = mk2<R>(R((xs[j] - cx) * d.scale), R((ys[j] - cy) * d.scale));
+                    w = mk2<R>(R(gs[j]), R(0));
+                }
             } else {
-                z = mk2<R>(R((xs[j] - cx) * d.scale), R((ys[j] - cy) * d.scale));
-                w = mk2<R>(R(gs[j]), R(0));
+                z = mk2<R>(R(0), R(0));
+                w = mk2<R>(R(0), R(0));
             }
-        } else {
-            z = mk2<R>(R(0), R(0));
-            w = mk2<R>(R(0), R(0));
+            for (int k = 0; k < p; ++k) {
+                buf[lane * pmax + k] = w;
+                w = cmul(w, z);
+            }
+            __syncwarp();
+            if (lane < p) {
+                for (int q = 0; q < 32; ++q) {
+                    const C2 b = buf[q * pmax + lane];
+                    acc0.x += b.x;
+                    acc0.y += b.y;
+                }
+            }
+            if (lane + 32 < p) {
+                for (int q = 0; q < 32; ++q) {
+                    const C2 b = buf[q * pmax + lane + 32];
+                    acc1.x += b.x;
+                    acc1.y += b.y;
+                }
+            }
+            __syncwarp();
         }
-        for (int k = 0; k < p; ++k) {
-            buf[lane * pmax + k] = w;
-            w = cmul(w, z);
+        C2 *dst = me + d.eoff + (lvl_off(L) + box_index(L, ix, iy)) * p;
+        if (lane < p) dst[lane] = acc0;
+        if (lane + 32 < p) dst[lane + 32] = acc1;
+    }
+}
+
+// Mixed path, p <= PM: each lane keeps the running sums of its particles'
+// gamma zeta^k in registers over all chunks of the leaf, and the warp adds
+// the 32 lanes' sums once per leaf (transposed through shared memory, lane k
+// adding column k: even rows and odd rows separately, then the two).  About a
+// third of the instructions of the per-chunk transpose above.
+template <int PM>
+__global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m_reg(
+    const uint2 *__restrict__ occ, const uint32_t *ctrl, const InstDesc *__restrict__ insts,
+    const uint32_t *__restrict__ start, const float4 *__restrict__ rec, float2 *__restrict__ me) {
+    constexpr int SP = PM | 1;  // odd row stride: conflict-free 8-byte accesses
+    __shared__ float2 buf[P2M_WARPS][32 * SP];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t nocc = ctrl[CTRL_NOCC];
+    const uint32_t nwarps = gridDim.x * P2M_WARPS;
+    for (uint32_t i = blockIdx.x * P2M_WARPS + wid; i < nocc; i += nwarps) {
+        const uint2 e = occ[i];
+        const InstDesc &d = insts[e.x];
+        const int p = d.p, L = d.L;
+        const uint32_t m = e.y;
+        const uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+        float2 acc[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k) acc[k] = make_float2(0.f, 0.f);
+        for (uint32_t c0 = s0; c0 < s1; c0 += 32) {
+            const uint32_t j = c0 + lane;
+            const float4 r = j < s1 ? rec[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 w = make_float2(r.z, 0.f);
+            const float2 z = make_float2(r.x, r.y);
+#pragma unroll
+            for (int k = 0; k < PM; ++k) {
+                if (k < p) {
+                    acc[k].x += w.x;
+                    acc[k].y += w.y;
+                    w = cmul(w, z);
+                }
+            }
         }
+        float2 *row = buf[wid] + lane * SP;
+#pragma unroll
+        for (int k = 0; k < PM; ++k)
+            if (k < p) row[k] = acc[k];
         __syncwarp();
         if (lane < p) {
-            for (int q = 0; q < 32; ++q) {
-                const C2 b = buf[q * pmax + lane];
-                acc0.x += b.x;
-                acc0.y += b.y;
+            float2 se = make_float2(0.f, 0.f), so = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int q = 0; q < 32; q += 2) {
+                const float2 a = buf[wid][q * SP + lane], b = buf[wid][(q + 1) * SP + lane];
+                se.x += a.x;
+                se.y += a.y;
+                so.x += b.x;
+                so.y += b.y;
             }
-        }
-        if (lane + 32 < p) {
-            for (int q = 0; q < 32; ++q) {
-                const C2 b = buf[q * pmax + lane + 32];
-                acc1.x += b.x;
-                acc1.y += b.y;
-            }
+            const uint32_t ix = compact_bits(m), iy = compact_bits(m >> 1);
+            me[d.eoff + (lvl_off(L) + box_index(L, ix, iy)) * p + lane] =
+                make_float2(se.x + so.x, se.y + so.y);
         }
         __syncwarp();
     }
-    C2 *dst = me + d.eoff + (lvl_off(L) + box_index(L, ix, iy)) * p;
-    if (lane < p) dst[lane] = acc0;
-    if (lane + 32 < p) dst[lane + 32] = acc1;
+}
+
+template <int PM, typename C2>
+cudaError_t launch_p2m_reg(const uint2 *occ, const uint32_t *ctrl, int64_t max_occ,
+                           const InstDesc *insts, const uint32_t *start, const float4 *rec,
+                           C2 *me, cudaStream_t st) {
+    if constexpr (std::is_same<C2, float2>::value) {
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2m_reg<PM>, P2M_WARPS * 32, 0);
+        if (per_sm < 1) per_sm = 1;
+        const int64_t grid = std::min<int64_t>((max_occ + P2M_WARPS - 1) / P2M_WARPS,
+                                               int64_t(per_sm) * device_sm_count());
+        k_p2m_reg<PM><<<unsigned(grid), P2M_WARPS * 32, 0, st>>>(occ, ctrl, insts, start, rec, me);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
 }
 
 template <typename R>
-cudaError_t launch_p2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                       int pmax, const uint32_t *start, const double *xs, const double *ys,
-                       const double *gs, const float4 *rec, typename Cplx<R>::T *me,
-                       cudaStream_t st, uint64_t *launches) {
-    if (nblocks <= 0) return cudaSuccess;
+cudaError_t launch_p2m(const uint2 *occ, const uint32_t *ctrl, int64_t max_occ,
+                       const InstDesc *insts, int pmax, const uint32_t *start, const double *xs,
+                       const double *ys, const double *gs, const float4 *rec,
+                       typename Cplx<R>::T *me, cudaStream_t st, uint64_t *launches) {
+    if (max_occ <= 0) return cudaSuccess;
     const size_t smem = size_t(P2M_WARPS) * 32 * pmax * sizeof(typename Cplx<R>::T);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
         if (e != cudaSuccess) return e;
     }
-    k_p2m<R><<<unsigned(nblocks), P2M_WARPS * 32, smem, st>>>(tasks, ntasks, insts, pmax, start, xs,
-                                                             ys, gs, rec, me);
+    if (rec) {
+        // mixed path: the register-accumulating kernel for the smallest
+        // compiled bound on p
+        cudaError_t e = cudaErrorNotSupported;
+        if (pmax <= 8) e = launch_p2m_reg<8>(occ, ctrl, max_occ, insts, start, rec, me, st);
+        else if (pmax <= 12) e = launch_p2m_reg<12>(occ, ctrl, max_occ, insts, start, rec, me, st);
+        else if (pmax <= 17) e = launch_p2m_reg<17>(occ, ctrl, max_occ, insts, start, rec, me, st);
+        else if (pmax <= 24) e = launch_p2m_reg<24>(occ, ctrl, max_occ, insts, start, rec, me, st);
+        if (e != cudaErrorNotSupported) {
+            PF_LAUNCHED(1);
+            return e;
+        }
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2m<R>, P2M_WARPS * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = std::min<int64_t>((max_occ + P2M_WARPS - 1) / P2M_WARPS,
+                                           int64_t(per_sm) * device_sm_count());
+    k_p2m<R><<<unsigned(grid), P2M_WARPS * 32, smem, st>>>(occ, ctrl, insts, pmax, start, xs, ys,
+                                                          gs, rec, me);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
@@ -412,44 +543,56 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
-    const int64_t box = (int64_t(blockIdx.x) - t.block0) * M2L_WARPS + wid;
-    if (box >= t.count) return;
+    const int64_t box0 = ((int64_t(blockIdx.x) - t.block0) * M2L_WARPS + wid) * BOX_RUN;
+    if (box0 >= t.count) return;
     const InstDesc &d = insts[t.inst];
     const int p = d.p, l = t.level;
     const int nside = 1 << l;
-    const int ix = int(box & (nside - 1)), iy = int(box >> l);
     const uint32_t *st = start + d.soff;
-    if (!box_count(st, d.L, l, morton_key(uint32_t(ix), uint32_t(iy)))) return;
-    const int c = (ix & 1) | ((iy & 1) << 1);
-    if (d.tc_unit0[l] >= 0) {
-        // this level also runs on the tensor cores: leave the dense units to them
-        const int64_t u = d.tc_unit0[l] + tc_unit_of(l, d.tc_segmax, c, iy >> 1, ix >> 1);
-        if (tc_unit_dense(ucount[u], tc_seg(l, d.tc_segmax), dense_pct)) return;
-    }
-    const C2 *tab = static_cast<const C2 *>(d.t_m2l);
-    const C2 *lev = me + d.eoff + lvl_off(l) * p;
-    C2 acc0 = mk2<R>(R(0), R(0)), acc1 = mk2<R>(R(0), R(0));
-    for (int e = 0; e < 27; ++e) {
-        const IlEntry en = c_il[c][e];
-        const int sx = ix + en.dx, sy = iy + en.dy;
-        if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
-        if (!box_count(st, d.L, l, morton_key(uint32_t(sx), uint32_t(sy)))) continue;
-        const C2 *src = lev + box_index(l, uint32_t(sx), uint32_t(sy)) * p;
-        if (lane < p) sa[wid][lane] = src[lane];
-        if (lane + 32 < p) sa[wid][lane + 32] = src[lane + 32];
-        __syncwarp();
-        const C2 *T = tab + size_t(en.op) * p * p;
-        if (lane < p) {
-            for (int k = 0; k < p; ++k) acc0 = cfma(T[k * p + lane], sa[wid][k], acc0);
+    // the run's target boxes that hold particles and are not left to the
+    // tensor cores (levels that also run there leave the dense units to them)
+    bool mine = false;
+    if (lane < BOX_RUN && box0 + lane < t.count) {
+        const int64_t bx = box0 + lane;
+        const int jx = int(bx & (nside - 1)), jy = int(bx >> l);
+        mine = box_count(st, d.L, l, morton_key(uint32_t(jx), uint32_t(jy))) != 0;
+        if (mine && d.tc_unit0[l] >= 0) {
+            const int jc = (jx & 1) | ((jy & 1) << 1);
+            const int64_t u = d.tc_unit0[l] + tc_unit_of(l, d.tc_segmax, jc, jy >> 1, jx >> 1);
+            mine = !tc_unit_dense(ucount[u], tc_seg(l, d.tc_segmax), dense_pct);
         }
-        if (lane + 32 < p) {
-            for (int k = 0; k < p; ++k) acc1 = cfma(T[k * p + lane + 32], sa[wid][k], acc1);
-        }
-        __syncwarp();
     }
-    C2 *dst = le + d.eoff + (lvl_off(l) + box_index(l, uint32_t(ix), uint32_t(iy))) * p;
-    if (lane < p) dst[lane] = acc0;
-    if (lane + 32 < p) dst[lane + 32] = acc1;
+    uint32_t todo = __ballot_sync(0xffffffffu, mine);
+    while (todo) {
+        const int64_t box = box0 + (__ffs(todo) - 1);
+        todo &= todo - 1;
+        const int ix = int(box & (nside - 1)), iy = int(box >> l);
+        const int c = (ix & 1) | ((iy & 1) << 1);
+        const C2 *tab = static_cast<const C2 *>(d.t_m2l);
+        const C2 *lev = me + d.eoff + lvl_off(l) * p;
+        C2 acc0 = mk2<R>(R(0), R(0)), acc1 = mk2<R>(R(0), R(0));
+        for (int e = 0; e < 27; ++e) {
+            const IlEntry en = c_il[c][e];
+            const int sx = ix + en.dx, sy = iy + en.dy;
+            if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
+            if (!box_count(st, d.L, l, morton_key(uint32_t(sx), uint32_t(sy)))) continue;
+            const C2 *src = lev + box_index(l, uint32_t(sx), uint32_t(sy)) * p;
+            if (lane < p) sa[wid][lane] = src[lane];
+            if (lane + 32 < p) sa[wid][lane + 32] = src[lane + 32];
+            __syncwarp();
+            const C2 *T = tab + size_t(en.op) * p * p;
+            if (lane < p) {
+                for (int k = 0; k < p; ++k) acc0 = cfma(T[k * p + lane], sa[wid][k], acc0);
+            }
+            if (lane + 32 < p) {
+                for (int k = 0; k < p; ++k) acc1 = cfma(T[k * p + lane + 32], sa[wid][k], acc1);
+            }
+            __syncwarp();
+        }
+        C2 *dst = le + d.eoff + (lvl_off(l) + box_index(l, uint32_t(ix), uint32_t(iy))) * p;
+        if (lane < p) dst[lane] = acc0;
+        if (lane + 32 < p) dst[lane + 32] = acc1;
+    }
 }
 
 template <typename R>
@@ -464,12 +607,12 @@ cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const Ins
     return cudaGetLastError();
 }
 
-template cudaError_t launch_p2m<double>(const Task *, int, int64_t, const InstDesc *, int,
-                                        const uint32_t *, const double *, const double *,
-                                        const double *, const float4 *, double2 *, cudaStream_t,
-                                        uint64_t *);
-template cudaError_t launch_p2m<float>(const Task *, int, int64_t, const InstDesc *, int,
-                                       const uint32_t *, const double *, const double *,
+template cudaError_t launch_p2m<double>(const uint2 *, const uint32_t *, int64_t,
+                                        const InstDesc *, int, const uint32_t *, const double *,
+                                        const double *, const double *, const float4 *, double2 *,
+                                        cudaStream_t, uint64_t *);
+template cudaError_t launch_p2m<float>(const uint2 *, const uint32_t *, int64_t, const InstDesc *,
+                                       int, const uint32_t *, const double *, const double *,
                                        const double *, const float4 *, float2 *, cudaStream_t,
                                        uint64_t *);
 template cudaError_t launch_m2m<double>(const Task *, int, int64_t, const InstDesc *,

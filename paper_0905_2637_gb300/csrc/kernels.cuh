@@ -10,10 +10,12 @@ namespace petfmm {
 // number of kernels it launched to *launches.
 
 // ---- tree.cu ---------------------------------------------------------------
-// Sec. 2.1 binning + z-order key of every particle (composite key for batches).
+// Sec. 2.1 binning + z-order key of every particle (composite key for batches);
+// if recu != nullptr also its mixed-path record (see launch_gather_mixed) in
+// input order.
 cudaError_t launch_morton(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                          int dtype_f32, uint32_t *keys, int *status, cudaStream_t st,
-                          uint64_t *launches);
+                          int dtype_f32, uint32_t *keys, float4 *recu, int *status,
+                          cudaStream_t st, uint64_t *launches);
 
 // Scratch (uint32 words) needed by exclusive_scan for n elements.
 int64_t scan_scratch_words(int64_t n);
@@ -39,11 +41,10 @@ cudaError_t launch_leaf_start(const Task *tasks, int ntasks, int64_t nblocks, co
 cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                               int dtype_f32, const uint32_t *perm, double *xs, double *ys,
                               double *gs, cudaStream_t st, uint64_t *launches);
-// rec = (xi, eta, gamma, caller index): leaf-relative coordinates in leaf units.
-cudaError_t launch_gather_mixed(const Task *tasks, int ntasks, int64_t nblocks,
-                                const InstDesc *insts, int dtype_f32, const uint32_t *perm,
-                                const uint32_t *skeys, float4 *rec, cudaStream_t st,
-                                uint64_t *launches);
+// rec[r] = recu[perm[r]]: (xi, eta, gamma, batch index) in sorted order, with
+// (xi, eta) the offset from the leaf centre in leaf widths.
+cudaError_t launch_gather_mixed(const float4 *recu, const uint32_t *perm, float4 *rec, int64_t n,
+                                cudaStream_t st, uint64_t *launches);
 
 // ---- expansions.cu ---------------------------------------------------------
 // Operator tables for p (FP64 build, also rounded to FP32), device-resident.
@@ -61,11 +62,17 @@ int host_interaction_list(int level, int ix, int iy, int32_t *out);
 // Number of (target, source) M2L translations of levels 2..L.
 int64_t m2l_pair_count(int L);
 
+// occ[0 .. ctrl[CTRL_NOCC]) = (instance, leaf) of every occupied leaf, in no
+// particular order (one thread per leaf of the tasks).
+cudaError_t launch_occ_list(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                            const uint32_t *start, uint2 *occ, uint32_t *ctrl, cudaStream_t st,
+                            uint64_t *launches);
+// P2M of the listed leaves by a persistent grid (max_occ bounds the list).
 template <typename R>
-cudaError_t launch_p2m(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                       int pmax, const uint32_t *start, const double *xs, const double *ys,
-                       const double *gs, const float4 *rec, typename Cplx<R>::T *me,
-                       cudaStream_t st, uint64_t *launches);
+cudaError_t launch_p2m(const uint2 *occ, const uint32_t *ctrl, int64_t max_occ,
+                       const InstDesc *insts, int pmax, const uint32_t *start, const double *xs,
+                       const double *ys, const double *gs, const float4 *rec,
+                       typename Cplx<R>::T *me, cudaStream_t st, uint64_t *launches);
 // M2M, M2L and L2L skip boxes with no particles in their subtree (and M2L
 // skips empty sources): their coefficients would be exactly zero and are
 // never read.  start = the batch's leaf-start array.
@@ -105,14 +112,21 @@ cudaError_t launch_m2l_tc(const Task *tasks, int ntasks, int64_t nblocks, const 
                           long long spin_limit, int *status, cudaStream_t st, uint64_t *launches);
 
 // units of work per block of each expansion kernel (the host plans with them)
-constexpr int P2M_WARPS = 4;      // leaves per block
-constexpr int M2L_WARPS = 4;      // target boxes per block
+constexpr int P2M_WARPS = 4;      // warps per block
+constexpr int M2L_WARPS = 4;      // warps per block
+// Each warp of the SIMT M2L owns a run of consecutive boxes and skips the
+// empty ones after one ballot: at the clustered workload 87% of the leaves
+// are empty, and a block per few boxes made the kernel bound by block
+// scheduling.
+constexpr int BOX_RUN = 8;
+constexpr int M2L_BOXES = M2L_WARPS * BOX_RUN;   // target boxes per block
 constexpr int EXP_THREADS = 256;  // (box, coefficient) pairs per block for M2M / L2L
 
 // ---- p2p.cu ----------------------------------------------------------------
 // Work list: items (inst, leaf, first target rank, target count) for every
 // occupied leaf, tpi targets per item.  ctrl[CTRL_NITEMS] receives the count.
-enum { CTRL_STATUS = 0, CTRL_NITEMS = 1, CTRL_QUEUE = 2, CTRL_PAIRS_LO = 4, CTRL_WORDS = 16 };
+enum { CTRL_STATUS = 0, CTRL_NITEMS = 1, CTRL_QUEUE = 2, CTRL_PAIRS_LO = 4, CTRL_NOCC = 6,
+       CTRL_WORDS = 16 };
 // Buffers for dispatching the items heaviest first (order != nullptr): the
 // items are emitted to items_unsorted, sorted by work class (one stable radix
 // pass over cap entries) and permuted into the item array.
@@ -136,6 +150,7 @@ cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items,
                              const float2 *le, int dtype_f32, unsigned long long *busy,
                              cudaStream_t st, uint64_t *launches);
 int p2p_grid(int precision_mixed, int deg, int general);
+int device_sm_count();
 constexpr int P2P_TPI_F64 = 32;
 constexpr int P2P_TPI_MIXED = 64;
 

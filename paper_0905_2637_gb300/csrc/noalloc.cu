@@ -112,7 +112,8 @@ extern "C" int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dty
     uint64_t launches = 0;
     cudaError_t e = cudaSuccess;
     if (n > 0) {
-        e = launch_morton(dt, 1, (n + 255) / 256, dd, dtype == PETFMM_F32, kA, status, st, &launches);
+        e = launch_morton(dt, 1, (n + 255) / 256, dd, dtype == PETFMM_F32, kA, nullptr, status, st,
+                          &launches);
         if (e == cudaSuccess && keys) e = cudaMemcpyAsync(keys, kA, size_t(n) * 4, cudaMemcpyDeviceToDevice, st);
         bool in_first = true;
         if (e == cudaSuccess) e = radix_sort(kA, vA, kB, vB, n, 2 * levels, hist, scan, &in_first, st, &launches);

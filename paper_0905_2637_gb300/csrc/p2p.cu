@@ -460,7 +460,7 @@ static MixedKernel pick_mixed(int deg, int general) {
 
 static int g_sms = 0;
 
-static int sm_count() {
+int device_sm_count() {
     if (!g_sms) {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -480,7 +480,7 @@ int p2p_grid(int precision_mixed, int deg, int general) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p_f64, P2P_THREADS, 0);
     }
     if (per_sm < 1) per_sm = 1;
-    return per_sm * sm_count();
+    return per_sm * device_sm_count();
 }
 
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,

@@ -28,6 +28,33 @@ __device__ __forceinline__ uint32_t bin_coord(double x, double x0, double scale,
     return uint32_t(f);
 }
 
+// Leaf-relative coordinate (x - c) scale, c = x0 + (i + 1/2) w, computed as
+// (x - x0) scale - (i + 1/2) in float-float arithmetic (x0 = x0h + x0l,
+// scale = sh + sl; two-sum for the difference, an FMA for the product's
+// error): the result before its final rounding to FP32 is within about 2^-44
+// of the exact value, relative to (x - x0) scale.
+__device__ __forceinline__ void split_ff(float x, float *h, float *l) { *h = x; *l = 0.0f; }
+__device__ __forceinline__ void split_ff(double x, float *h, float *l) {
+    *h = float(x);
+    *l = float(x - double(*h));
+}
+template <typename TIn>
+__device__ __forceinline__ float leaf_coord(TIn xin, float x0h, float x0l, float sh, float sl,
+                                            uint32_t i) {
+    float xh, xl;
+    split_ff(xin, &xh, &xl);
+    // t = x - x0 = th + tl
+    const float th = __fsub_rn(xh, x0h);
+    const float bb = __fsub_rn(th, xh);
+    float tl = __fadd_rn(__fsub_rn(xh, __fsub_rn(th, bb)), __fsub_rn(-x0h, bb));
+    tl = __fadd_rn(tl, __fsub_rn(xl, x0l));
+    // s = t scale = p + e
+    const float p = __fmul_rn(th, sh);
+    float e = __fmaf_rn(th, sh, -p);
+    e = __fmaf_rn(th, sl, __fmaf_rn(tl, sh, e));
+    return __fadd_rn(__fsub_rn(p, __fadd_rn(float(i), 0.5f)), e);
+}
+
 // FP32 shortcut (FP64 arithmetic is slow on this GPU).  With xf, x0f and
 // scalef the FP32 roundings of x, x0 and scale, s32 = fl(fl(xf - x0f) scalef)
 // differs from the FP64 s above by at most 4 u scale (|x| + |x0|) plus terms
@@ -50,10 +77,14 @@ __device__ __forceinline__ bool bin_coord_fast(float xf, float x0f, float scalef
     return true;
 }
 
+// recu != nullptr (mixed path): also the blob's record in input order,
+// (xi, eta, gamma, batch index) with (xi, eta) its offset from its leaf's
+// centre in leaf widths.
 template <typename TIn>
 __global__ void __launch_bounds__(256) k_morton(const Task *__restrict__ tasks, int ntasks,
                                                 const InstDesc *__restrict__ insts,
-                                                uint32_t *__restrict__ keys, int *status) {
+                                                uint32_t *__restrict__ keys,
+                                                float4 *__restrict__ recu, int *status) {
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
     const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
@@ -72,16 +103,25 @@ __global__ void __launch_bounds__(256) k_morton(const Task *__restrict__ tasks, 
         iy = bin_coord(y, d.y0, d.scale, nb);
     }
     keys[d.poff + j] = d.key_hi | morton_key(ix, iy);
+    if (recu) {
+        float4 o;
+        o.x = leaf_coord(xin, d.x0h, d.x0l, d.sh, d.sl, ix);
+        o.y = leaf_coord(yin, d.y0h, d.y0l, d.sh, d.sl, iy);
+        o.z = float(static_cast<const TIn *>(d.g)[j]);
+        o.w = __uint_as_float(uint32_t(d.poff + j));
+        recu[d.poff + j] = o;
+    }
 }
 
 cudaError_t launch_morton(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
-                          int dtype_f32, uint32_t *keys, int *status, cudaStream_t st,
-                          uint64_t *launches) {
+                          int dtype_f32, uint32_t *keys, float4 *recu, int *status,
+                          cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
     if (dtype_f32)
-        k_morton<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, keys, status);
+        k_morton<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, keys, recu, status);
     else
-        k_morton<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, keys, status);
+        k_morton<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, keys, recu,
+                                                            status);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
@@ -192,12 +232,18 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 
 // ----------------------------------------------------------------------------
 // Stable LSD radix sort, 8-bit digits, reduce-then-scan.  A block owns a tile
-// of RS_ITEMS * 256 consecutive elements; element (round k, thread t) of the
-// tile is tile + k * 256 + t, so ranking rounds in order, warps in order and
-// lanes in order keeps equal digits in input order (stability).
+// of RS_TILE consecutive elements; warp w owns the consecutive chunk
+// [w * RS_WCHUNK, (w + 1) * RS_WCHUNK) of the tile and reads it in rounds of
+// 32 (lane order), so (warp, round, lane) is the input order.  The scatter
+// ranks every element within its warp (match_any per round), turns the ranks
+// into positions of the tile sorted by digit, sorts the tile in shared memory
+// and writes each digit's run to its place in the output: consecutive
+// threads write consecutive addresses.
 // ----------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 16;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_WCHUNK = RS_ITEMS * 32;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
 int64_t radix_blocks(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
@@ -209,11 +255,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__res
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
 #pragma unroll 4
     for (int k = 0; k < RS_ITEMS; ++k) {
-        int64_t i = tile + int64_t(k) * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1u);
+        const int64_t i = tile + int64_t(k) * RS_THREADS + threadIdx.x;
+        const uint32_t dg = i < n ? (keys[i] >> shift) & mask : 0x100u;
+        // one shared atomic per distinct digit of the warp (clustered keys
+        // share few digits)
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        if (dg < 0x100u && (peers & ((1u << lane) - 1u)) == 0)
+            atomicAdd(&cnt[dg], uint32_t(__popc(peers)));
     }
     __syncthreads();
     hist[int64_t(threadIdx.x) * nblocks + blockIdx.x] = cnt[threadIdx.x];
@@ -223,42 +275,68 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, int shift, uint32_t mask,
     const uint32_t *__restrict__ offs, int64_t nblocks) {
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wpos[RS_THREADS / 32][256];
+    __shared__ uint32_t wcnt[RS_WARPS][256];  // per-warp digit counts, then warp offsets
+    __shared__ uint32_t lstart[256];          // start of each digit's run in the sorted tile
+    __shared__ uint32_t gbase[256];           // its start in the output
+    __shared__ uint32_t skey[RS_TILE], sval[RS_TILE];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    base[tid] = offs[int64_t(tid) * nblocks + blockIdx.x];
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
-    for (int k = 0; k < RS_ITEMS; ++k) {
+    const int64_t tile_n = n - tile < RS_TILE ? n - tile : RS_TILE;
 #pragma unroll
-        for (int w = 0; w < RS_THREADS / 32; ++w) wpos[w][tid] = 0;
-        __syncthreads();
-        const int64_t i = tile + int64_t(k) * RS_THREADS + tid;
+    for (int w = 0; w < RS_WARPS; ++w) wcnt[w][tid] = 0;
+    gbase[tid] = offs[int64_t(tid) * nblocks + blockIdx.x];
+    __syncthreads();
+    // 1. rank within the warp, in input order
+    uint32_t key[RS_ITEMS], val[RS_ITEMS], rk[RS_ITEMS];
+    const int64_t wbase = tile + int64_t(warp) * RS_WCHUNK;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
         const bool valid = i < n;
-        const uint32_t key = valid ? kin[i] : 0u;
-        const uint32_t val = valid ? (vin ? vin[i] : uint32_t(i)) : 0u;
-        const uint32_t dg = valid ? ((key >> shift) & mask) : 0x100u;
+        key[r] = valid ? kin[i] : 0u;
+        val[r] = valid ? (vin ? vin[i] : uint32_t(i)) : 0u;
+        const uint32_t dg = valid ? (key[r] >> shift) & mask : 0x100u;
         const uint32_t peers = __match_any_sync(0xffffffffu, dg);
         const uint32_t below = peers & lt_mask;
-        if (valid && below == 0) wpos[warp][dg] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t s = base[tid];
+        rk[r] = valid ? wcnt[warp][dg & 0xffu] + __popc(below) : 0u;
+        __syncwarp();
+        if (valid && below == 0) wcnt[warp][dg] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // 2. per digit (thread tid = digit): offsets of the warps, then the runs
+    {
+        uint32_t s = 0;
 #pragma unroll
-            for (int w = 0; w < RS_THREADS / 32; ++w) {
-                const uint32_t c = wpos[w][tid];
-                wpos[w][tid] = s;
-                s += c;
-            }
-            base[tid] = s;
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = s;
+            s += c;
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t pos = wpos[warp][dg] + __popc(below);
-            kout[pos] = key;
-            vout[pos] = val;
+        uint32_t total;
+        lstart[tid] = block_exclusive_sum(s, &total);
+    }
+    __syncthreads();
+    // 3. sort the tile in shared memory
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = wbase + r * 32 + lane;
+        if (i < n) {
+            const uint32_t dg = (key[r] >> shift) & mask;
+            const uint32_t pos = lstart[dg] + wcnt[warp][dg] + rk[r];
+            skey[pos] = key[r];
+            sval[pos] = val[r];
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    // 4. write the runs
+    for (int q = tid; q < tile_n; q += RS_THREADS) {
+        const uint32_t k = skey[q];
+        const uint32_t dg = (k >> shift) & mask;
+        const uint32_t pos = gbase[dg] + (uint32_t(q) - lstart[dg]);
+        kout[pos] = k;
+        vout[pos] = sval[q];
     }
 }
 
@@ -357,61 +435,14 @@ __global__ void __launch_bounds__(256) k_gather_f64(const Task *__restrict__ tas
     gs[r] = double(static_cast<const TIn *>(d.g)[q]);
 }
 
-// Mixed path: leaf-relative coordinates in leaf units, computed in FP64 and
-// rounded once; .w carries the batch index of the particle (for the output).
-//
-// Leaf-relative coordinate (x - c) scale, c = x0 + (i + 1/2) w, computed as
-// (x - x0) scale - (i + 1/2) in float-float arithmetic (x0 = x0h + x0l,
-// scale = sh + sl; two-sum for the difference, an FMA for the product's
-// error): the result before its final rounding to FP32 is within about 2^-44
-// of the exact value, relative to (x - x0) scale.
-__device__ __forceinline__ void split_ff(float x, float *h, float *l) { *h = x; *l = 0.0f; }
-__device__ __forceinline__ void split_ff(double x, float *h, float *l) {
-    *h = float(x);
-    *l = float(x - double(*h));
-}
-template <typename TIn>
-__device__ __forceinline__ float leaf_coord(TIn xin, float x0h, float x0l, float sh, float sl,
-                                            uint32_t i) {
-    float xh, xl;
-    split_ff(xin, &xh, &xl);
-    // t = x - x0 = th + tl
-    const float th = __fsub_rn(xh, x0h);
-    const float bb = __fsub_rn(th, xh);
-    float tl = __fadd_rn(__fsub_rn(xh, __fsub_rn(th, bb)), __fsub_rn(-x0h, bb));
-    tl = __fadd_rn(tl, __fsub_rn(xl, x0l));
-    // s = t scale = p + e
-    const float p = __fmul_rn(th, sh);
-    float e = __fmaf_rn(th, sh, -p);
-    e = __fmaf_rn(th, sl, __fmaf_rn(tl, sh, e));
-    return __fadd_rn(__fsub_rn(p, __fadd_rn(float(i), 0.5f)), e);
-}
-
-template <typename TIn>
-__global__ void __launch_bounds__(256) k_gather_mixed(const Task *__restrict__ tasks, int ntasks,
-                                                      const InstDesc *__restrict__ insts,
+// Mixed path: the records were built by the binning kernel in input order;
+// the gather is one 16-byte permutation (a random read of one sector per
+// blob, where reading x, y, gamma separately would touch three).
+__global__ void __launch_bounds__(256) k_gather_mixed(const float4 *__restrict__ recu,
                                                       const uint32_t *__restrict__ perm,
-                                                      const uint32_t *__restrict__ skeys,
-                                                      float4 *__restrict__ rec) {
-    const int ti = find_task(tasks, ntasks, blockIdx.x);
-    const Task t = tasks[ti];
-    const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
-    if (j >= t.count) return;
-    const InstDesc &d = insts[t.inst];
-    const int64_t r = d.poff + j;
-    const uint32_t qb = perm[r];
-    const int64_t q = int64_t(qb) - d.poff;
-    const uint32_t m = skeys[r] & ((d.L >= 16) ? 0xffffffffu : ((1u << (2 * d.L)) - 1u));
-    const uint32_t ix = compact_bits(m), iy = compact_bits(m >> 1);
-    const TIn x = static_cast<const TIn *>(d.x)[q];
-    const TIn y = static_cast<const TIn *>(d.y)[q];
-    const TIn g = static_cast<const TIn *>(d.g)[q];
-    float4 o;
-    o.x = leaf_coord(x, d.x0h, d.x0l, d.sh, d.sl, ix);
-    o.y = leaf_coord(y, d.y0h, d.y0l, d.sh, d.sl, iy);
-    o.z = float(g);
-    o.w = __uint_as_float(qb);
-    rec[r] = o;
+                                                      float4 *__restrict__ rec, int64_t n) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r < n) rec[r] = recu[perm[r]];
 }
 
 cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
@@ -426,17 +457,10 @@ cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_mixed(const Task *tasks, int ntasks, int64_t nblocks,
-                                const InstDesc *insts, int dtype_f32, const uint32_t *perm,
-                                const uint32_t *skeys, float4 *rec, cudaStream_t st,
-                                uint64_t *launches) {
-    if (nblocks <= 0) return cudaSuccess;
-    if (dtype_f32)
-        k_gather_mixed<float><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys,
-                                                                 rec);
-    else
-        k_gather_mixed<double><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm, skeys,
-                                                                  rec);
+cudaError_t launch_gather_mixed(const float4 *recu, const uint32_t *perm, float4 *rec, int64_t n,
+                                cudaStream_t st, uint64_t *launches) {
+    if (n <= 0) return cudaSuccess;
+    k_gather_mixed<<<unsigned((n + 255) / 256), 256, 0, st>>>(recu, perm, rec, n);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }

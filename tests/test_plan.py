@@ -17,7 +17,7 @@ def lib():
     return _lib
 
 
-UNITS_PER_BLOCK = {0: 256, 1: 256, 2: 256, 3: 4, 4: 256, 5: 4, 6: 1}
+UNITS_PER_BLOCK = {0: 256, 1: 256, 2: 256, 3: 256, 4: 256, 5: 32, 6: 1}
 
 
 def _instances(seed, k):
