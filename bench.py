@@ -334,11 +334,20 @@ def main():
     launches = ctx.stats()["kernel_launches"] - launches0
     # P2P kernel duration per launch: the library's CUDA events around the
     # launch, on the stream it launches on, one step at a time
-    p2p_ms = []
+    # (and the whole evaluation's duration, one step at a time, for its
+    # median and p99)
+    p2p_ms, m2l_ms, step_ms = [], [], []
     for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         ctx.evaluate(x, y, g, u, v)
+        e1.record(stream)
         ctx.sync()
-        p2p_ms.append(ctx.stage_times()["p2p"])
+        st_ = ctx.stage_times()
+        p2p_ms.append(st_["p2p"])
+        m2l_ms.append(st_["m2l"])
+        step_ms.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
     if dist is not None:
         t = torch.tensor([elapsed], device="cuda")
@@ -387,6 +396,7 @@ def main():
         fp64 = {"value": w.n / t64, "unit": "particles/s", "ms_per_step": 1e3 * t64}
 
     peaks, peak_kind = _peaks()
+    pipes = _lib.petfmm_measure_peaks()
     pairs = stats["p2p_pairs"]
     p2p_t = statistics.mean(p2p_ms) / 1e3
     achieved = pairs * P2P_OPS_PER_PAIR / p2p_t / 1e12
@@ -397,7 +407,31 @@ def main():
                 "note": (f"{P2P_OPS_PER_PAIR} FP32 ops per ordered pair x {pairs} pairs / mean P2P "
                          f"launch {1e3 * p2p_t:.3f} ms (CUDA events on the launching stream); peak = "
                          f"{SMS} SMs x {FP32_LANES} FP32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} "
-                         f"MHz ({peak_kind} max SM clock), one op per lane per cycle")}
+                         f"MHz ({peak_kind} max SM clock), one op per lane per cycle"),
+                "peak_measured": pipes["fp32_ops"] / 1e12,
+                "frac_of_measured": achieved / (pipes["fp32_ops"] / 1e12)}
+    # M2L (tensor-core units + SIMT remainder, the whole stage) against the
+    # measured dense TF32 rate: 8 p^2 real flops per (target, source) pair
+    m2l_t = statistics.mean(m2l_ms) / 1e3
+    m2l_ach = 8.0 * w.p * w.p * stats["m2l_pairs"] / m2l_t / 1e12
+    m2l = {"bound": "tensor", "stage": "M2L (k_m2l_tc + k_m2l)", "achieved": m2l_ach,
+           "peak_measured": pipes["tf32_flops"] / 1e12, "unit": "TFLOP/s",
+           "frac_of_measured": m2l_ach / (pipes["tf32_flops"] / 1e12),
+           "note": (f"8 p^2 flops x {stats['m2l_pairs']} translations / mean M2L stage "
+                    f"{1e3 * m2l_t:.3f} ms; peak = tcgen05 kind::tf32 microbenchmark "
+                    "(petfmm_measure_peaks); 3xTF32 executes 3x the algorithmic flops")}
+    pipes_out = {"fp32_tops": pipes["fp32_ops"] / 1e12, "fp64_tops": pipes["fp64_ops"] / 1e12,
+                 "mufu_rcp_tops": pipes["mufu_rcp_ops"] / 1e12,
+                 "mufu_ex2_tops": pipes["mufu_ex2_ops"] / 1e12,
+                 "tf32_tflops": pipes["tf32_flops"] / 1e12,
+                 "note": "petfmm_measure_peaks microbenchmarks on this GPU, after the timed region"}
+    step_sorted = sorted(step_ms)
+    step_dist = {"median": statistics.median(step_ms),
+                 "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))],
+                 "n": len(step_ms),
+                 "note": "one evaluation at a time (CUDA events around it, synchronised)"}
+    in_mb = 3 * w.n * w.x.itemsize / 1e6
+    out_mb = 2 * w.n * w.x.itemsize / 1e6
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
@@ -406,11 +440,15 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": w.n, "levels": w.L, "order": w.p,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                           "l2": "inputs larger than L2 (x, y, gamma 201 MB; u, v 134 MB)"},
+                           "l2": (f"inputs larger than L2 (x, y, gamma {in_mb:.0f} MB; u, v "
+                                  f"{out_mb:.0f} MB)" if in_mb > 129 else
+                                  f"inputs {in_mb:.0f} MB, outputs {out_mb:.0f} MB: smaller than L2 "
+                                  "(profiling case, not a bench line)")},
                 "rel_l2_vs_fp64": rel, "fp64_gpu": fp64,
                 "stages_ms": stages, "p2p_pairs": pairs, "m2l_pairs": stats["m2l_pairs"],
                 "p2p_load_balance": stats["p2p_load_balance"],
-                "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": launches, "roofline": roofline, "m2l_roofline": m2l,
+                "pipes_measured": pipes_out, "step_ms": step_dist, "clocks": clocks, "e2e": e2e,
                 "gpu": torch.cuda.get_device_name()}
         if args.workload != "clustered-16M":
             line["config"]["workload"] = w.name + " (profiling case)"

@@ -308,6 +308,26 @@ int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dtype, int64_t
                         const void *y, uint32_t *keys, uint32_t *perm, uint32_t *start,
                         void *cuda_stream);
 
+/* Measured pipe rates of the current device, for quoting roofline fractions
+ * (Sec. 5.2 costs the steps by operation counts; the paper has no
+ * counterpart of the measurement itself).  Runs microbenchmarks on every SM
+ * for tens of milliseconds on a private stream and waits for them:
+ *   fp32_ops      FP32 FFMA instructions per second x 32 lanes (one op each)
+ *   fp64_ops      FP64 DFMA, counted the same way
+ *   mufu_rcp_ops  special-function unit, rcp.approx
+ *   mufu_ex2_ops  special-function unit, ex2.approx
+ *   tf32_flops    dense TF32 MMA on the tensor cores (tcgen05 kind::tf32,
+ *                 M = 128, N = 256, K = 8 from shared memory), 2 flops per MAC
+ *   sms           streaming multiprocessors used
+ * Returns PETFMM_OK, PETFMM_EINVAL (out NULL), PETFMM_ENOMEM, PETFMM_ECUDA or
+ * PETFMM_ETIMEOUT (the tensor-core wait gave up; tf32_flops then
+ * unspecified).  Allocates and frees a few MB of device memory. */
+typedef struct {
+    double fp32_ops, fp64_ops, mufu_rcp_ops, mufu_ex2_ops, tf32_flops;
+    int sms;
+} petfmm_peaks;
+int petfmm_measure_peaks(petfmm_peaks *out);
+
 const char *petfmm_strerror(int code);
 int petfmm_version(void);
 

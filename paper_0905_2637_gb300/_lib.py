@@ -116,6 +116,7 @@ def load():
             "petfmm_get_stats": (I, [P, ctypes.POINTER(Stats)]),
             "petfmm_strerror": (ctypes.c_char_p, [I]),
             "petfmm_version": (I, []),
+            "petfmm_measure_peaks": (I, [ctypes.POINTER(Peaks)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -194,6 +195,19 @@ def petfmm_strerror(code):
 
 def petfmm_version():
     return int(load().petfmm_version())
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_ops", ctypes.c_double), ("fp64_ops", ctypes.c_double),
+                ("mufu_rcp_ops", ctypes.c_double), ("mufu_ex2_ops", ctypes.c_double),
+                ("tf32_flops", ctypes.c_double), ("sms", ctypes.c_int)]
+
+
+def petfmm_measure_peaks():
+    """Measured pipe rates of the current device (petfmm_measure_peaks)."""
+    pk = Peaks()
+    _ck(load().petfmm_measure_peaks(ctypes.byref(pk)), "petfmm_measure_peaks")
+    return {f: getattr(pk, f) for f, _ in Peaks._fields_}
 
 
 # --------------------------------------------------------------------------- torch wrappers

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace petfmm {
 
@@ -38,56 +39,6 @@ namespace petfmm {
 
 constexpr int TC_THREADS = 128;
 constexpr int TC_MAX_NPAD = 48;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return uint32_t(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor, K-major, no swizzle: LBO = byte distance
-// between core matrices adjacent in K, SBO = between core matrices adjacent
-// in M/N; bits 46-47 hold the descriptor version (1).
-__device__ __forceinline__ uint64_t mma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
-           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
-    uint32_t done = 0;
-    for (long long it = 0; it < limit && !done; ++it) {
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity));
-    }
-    return done != 0;
-}
-
-__device__ __forceinline__ float tf32_hi(float v) {
-    return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Counts, for every unit of the tensor-core launch (index = the launch's block
 // index), how many of its targets hold particles; one warp per unit.  The
