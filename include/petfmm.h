@@ -250,8 +250,14 @@ enum {
     PETFMM_OPT_TC_DENSE = 6,   /* percent (0..100, default 25) of a tensor-core unit's
                                   targets that must hold particles for the unit to run
                                   on the tensor cores; sparser units use the SIMT kernel */
-    PETFMM_OPT_TC_SEG = 8      /* widest tensor-core M2L unit in parent cells: 128
+    PETFMM_OPT_TC_SEG = 8,     /* widest tensor-core M2L unit in parent cells: 128
                                   (default), 256 or 512 */
+    PETFMM_OPT_NEAR_TOL = 9    /* mixed path: relative tolerance of the polynomial that
+                                  evaluates Eq. 8's factor (1 - e^-q)/q, in units of
+                                  1e-9 (1 .. 1000000; default 2500 = 2.5e-6, a quarter
+                                  of the 1e-5 budget against FP64; 100 = 1e-7 is the
+                                  FP32 rounding level).  Applies from the next
+                                  evaluation. */
 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
 

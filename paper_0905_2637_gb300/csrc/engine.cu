@@ -88,6 +88,11 @@ struct Problem {
 
 }  // namespace
 
+namespace {
+// default relative tolerance of the near-field polynomial (PETFMM_OPT_NEAR_TOL)
+constexpr double kNearTolDefault = 2.5e-6;
+}  // namespace
+
 struct petfmm_ctx {
     petfmm_domain dom{};
     int L = 0, p = 0;
@@ -103,6 +108,7 @@ struct petfmm_ctx {
     // with a 25% occupancy threshold gave the fastest M2L on both
     int tc_dense_pct = 25;
     int tc_segmax = 128;
+    double near_tol = kNearTolDefault;
     int64_t spin_limit = 0;
     uint64_t launches = 0, evaluations = 0;
 
@@ -152,8 +158,11 @@ int cuda_status(cudaError_t e) {
 // ---------------------------------------------------------------------------
 // Near-field polynomial: Chebyshev interpolation of g(q) = (1 - e^-q) / q on
 // [0, Q], converted to monomials in rho^2 (q = kappa rho^2).  The smallest
-// degree whose relative error on a fine grid stays below 1e-7 (the size of
-// the FP32 rounding of the Horner evaluation itself) is taken.
+// degree (at least 4) whose relative error on a fine grid stays below the
+// context's tolerance is taken: by default 2.5e-6, a quarter of the 1e-5
+// budget of the mixed path against FP64 (each pair's factor g is then within
+// 2.5e-6 of exact, before FP32 rounding); 1e-7 reaches the FP32 rounding of
+// the Horner evaluation itself.
 // ---------------------------------------------------------------------------
 double g_exact(double q) { return q == 0.0 ? 1.0 : -std::expm1(-q) / q; }
 
@@ -182,7 +191,7 @@ bool solve_dense(std::vector<double> &A, std::vector<double> &b, int n) {
 }
 
 // Fits on q in [0, Q]; returns degree (0 on failure) and coefficients in rho^2.
-int fit_near_poly(double Q, double kappa, float *coef) {
+int fit_near_poly(double Q, double kappa, double tol, float *coef) {
     for (int d = 4; d <= 12; ++d) {
         const int n = d + 1;
         std::vector<double> A(size_t(n) * n), b(n);
@@ -212,7 +221,7 @@ int fit_near_poly(double Q, double kappa, float *coef) {
             for (int k = d - 1; k >= 0; --k) v = v * s + a[k];
             err = std::max(err, std::fabs(v - g_exact(kappa * s)) / g_exact(kappa * s));
         }
-        if (err < 1e-7) {
+        if (err < tol) {
             for (int k = 0; k <= POLY_MAX; ++k) coef[k] = k <= d ? float(a[k]) : 0.0f;
             return d;
         }
@@ -223,7 +232,7 @@ int fit_near_poly(double Q, double kappa, float *coef) {
 // Largest q the polynomial alone may cover.
 constexpr double kPolyQMax = 2.0;
 
-void fill_p2p_constants(InstDesc &d) {
+void fill_p2p_constants(InstDesc &d, double tol) {
     const double w = d.wleaf;
     const double kappa = w * w / (2.0 * d.sigma * d.sigma);
     d.kappa = float(kappa);
@@ -240,10 +249,11 @@ void fill_p2p_constants(InstDesc &d) {
         float poly[POLY_MAX + 1];
     };
     static std::mutex mu;
-    static std::map<double, Fit> cache;
+    static std::map<std::pair<double, double>, Fit> cache;
+    const std::pair<double, double> key(kappa, tol);
     {
         std::lock_guard<std::mutex> lk(mu);
-        auto it = cache.find(kappa);
+        auto it = cache.find(key);
         if (it != cache.end()) {
             d.general = it->second.general;
             d.deg = it->second.deg;
@@ -257,11 +267,11 @@ void fill_p2p_constants(InstDesc &d) {
     const double qmax = kappa * rho2max;
     if (qmax <= kPolyQMax) {
         d.general = 0;
-        d.deg = fit_near_poly(qmax, kappa, d.poly);
+        d.deg = fit_near_poly(qmax, kappa, tol, d.poly);
         d.qsplit_rho2 = float(rho2max);
     } else {
         d.general = 1;
-        d.deg = fit_near_poly(1.0, kappa, d.poly);
+        d.deg = fit_near_poly(1.0, kappa, tol, d.poly);
         d.qsplit_rho2 = float(1.0 / kappa);
     }
     Fit f;
@@ -271,7 +281,7 @@ void fill_p2p_constants(InstDesc &d) {
     std::memcpy(f.poly, d.poly, sizeof(f.poly));
     std::lock_guard<std::mutex> lk(mu);
     if (cache.size() > 4096) cache.clear();
-    cache[kappa] = f;
+    cache[key] = f;
 }
 
 OpTables *get_tables(petfmm_ctx *c, int p, int *err) {
@@ -316,8 +326,8 @@ void flatten_tasks(Plan &pl) {
     for (TaskRange &r : pl.l2l) put(r);
 }
 
-int build_plan(int precision, bool use_tc, int tc_segmax, const std::vector<Problem> &probs,
-               Plan &pl) {
+int build_plan(int precision, bool use_tc, int tc_segmax, double near_tol,
+               const std::vector<Problem> &probs, Plan &pl) {
     pl = Plan();
     const int ni = int(probs.size());
     int inst_bits = 0;
@@ -351,7 +361,7 @@ int build_plan(int precision, bool use_tc, int tc_segmax, const std::vector<Prob
         d.g = pb.g;
         d.u = pb.u;
         d.v = pb.v;
-        fill_p2p_constants(d);
+        fill_p2p_constants(d, near_tol);
         if (precision == PETFMM_MIXED && d.deg == 0) return PETFMM_EINVAL;
         pl.deg = std::max(pl.deg, d.deg);
         pl.general |= d.general;
@@ -482,7 +492,7 @@ void stage_mark(petfmm_ctx *c, int stage) {
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     Plan &pl = c->plan;
-    PF_TRY(build_plan(c->precision, c->m2l_tc, c->tc_segmax, probs, pl));
+    PF_TRY(build_plan(c->precision, c->m2l_tc, c->tc_segmax, c->near_tol, probs, pl));
     PF_TRY(attach_tables(c, pl));
     cudaStream_t st = c->stream;
     const bool mixed = c->precision == PETFMM_MIXED;
@@ -840,7 +850,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     int rc = problems_from(n_inst, inst, probs);
     if (rc) return rc;
     Plan pl;
-    rc = build_plan(precision, true, TC_MAX_SEG, probs, pl);
+    rc = build_plan(precision, true, TC_MAX_SEG, kNearTolDefault, probs, pl);
     if (rc) return rc;
     int n = 0;
     auto emit = [&](int64_t id, const TaskRange &r) {
@@ -902,6 +912,10 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
         case PETFMM_OPT_TC_SEG:
             if (value != 128 && value != 256 && value != 512) return PETFMM_EINVAL;
             c->tc_segmax = int(value);
+            return PETFMM_OK;
+        case PETFMM_OPT_NEAR_TOL:
+            if (value < 1 || value > 1000000) return PETFMM_EINVAL;
+            c->near_tol = double(value) * 1e-9;
             return PETFMM_OK;
         case PETFMM_OPT_TC_DENSE: if (value < 0 || value > 100) return PETFMM_EINVAL; c->tc_dense_pct = int(value); return PETFMM_OK;
         default: return PETFMM_EINVAL;

@@ -229,7 +229,7 @@ __device__ __forceinline__ void pair2(const float4 s, float xa, float ya, float 
 }
 
 template <int DEG, bool GENERAL>
-__global__ void __launch_bounds__(P2P_THREADS) k_p2p_mixed(
+__global__ void __launch_bounds__(P2P_THREADS, 5) k_p2p_mixed(
     const uint4 *__restrict__ items, uint32_t *ctrl, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const float4 *__restrict__ rec,
     const float2 *__restrict__ le, int dtype_f32, unsigned long long *busy) {

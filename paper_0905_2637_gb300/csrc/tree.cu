@@ -235,11 +235,25 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 // of RS_TILE consecutive elements; warp w owns the consecutive chunk
 // [w * RS_WCHUNK, (w + 1) * RS_WCHUNK) of the tile and reads it in rounds of
 // 32 (lane order), so (warp, round, lane) is the input order.  The scatter
-// ranks every element within its warp (match_any per round), turns the ranks
+// ranks every element within its warp (digit_peers per round), turns the ranks
 // into positions of the tile sorted by digit, sorts the tile in shared memory
 // and writes each digit's run to its place in the output: consecutive
 // threads write consecutive addresses.
 // ----------------------------------------------------------------------------
+// Lanes of the warp holding the same digit as this lane (bit d of the
+// 9-bit value 0..256, 256 = no element): 9 ballots, which run on the ALU
+// pipe, where __match_any_sync stalls on a long-latency unit.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t dg) {
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const bool bit = (dg >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_WARPS = RS_THREADS / 32;
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__res
         const uint32_t dg = i < n ? (keys[i] >> shift) & mask : 0x100u;
         // one shared atomic per distinct digit of the warp (clustered keys
         // share few digits)
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t peers = digit_peers(dg);
         if (dg < 0x100u && (peers & ((1u << lane) - 1u)) == 0)
             atomicAdd(&cnt[dg], uint32_t(__popc(peers)));
     }
@@ -297,7 +311,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
         key[r] = valid ? kin[i] : 0u;
         val[r] = valid ? (vin ? vin[i] : uint32_t(i)) : 0u;
         const uint32_t dg = valid ? (key[r] >> shift) & mask : 0x100u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t peers = digit_peers(dg);
         const uint32_t below = peers & lt_mask;
         rk[r] = valid ? wcnt[warp][dg & 0xffu] + __popc(below) : 0u;
         __syncwarp();

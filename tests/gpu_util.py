@@ -21,7 +21,8 @@ def to_dev(arrs):
     return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
 
 
-def run(w, precision, L=None, p=None, sigma=None, domain=None, timing=False, ctx_out=None, poison=True):
+def run(w, precision, L=None, p=None, sigma=None, domain=None, timing=False, ctx_out=None, poison=True,
+        options=None):
     """One evaluation of workload w; returns (u, v) as float64 numpy arrays."""
     _lib = lib()
     L = w.L if L is None else L
@@ -32,6 +33,8 @@ def run(w, precision, L=None, p=None, sigma=None, domain=None, timing=False, ctx
     if poison:
         # any read of a coefficient this evaluation did not write turns into NaN
         ctx.set_option(_lib.PETFMM_OPT_POISON, 1)
+    for opt, val in (options or {}).items():
+        ctx.set_option(opt, val)
     x, y, g = to_dev((w.x, w.y, w.gamma))
     u, v = ctx.evaluate(x, y, g)
     rc = ctx.sync()

@@ -149,3 +149,25 @@ def test_coincident_particles_and_self_are_zero(orc):
     assert G.rel_l2(u, v, ur, vr) <= TOL64
     umx, vmx = G.run(w, "mixed")
     assert np.all(np.isfinite(umx)) and G.rel_l2(umx, vmx, u, v) <= TOLMX
+
+
+def test_near_field_tolerance_option():
+    # The near-field factor's polynomial is fitted to the context's tolerance
+    # (default 2.5e-6): both it and the FP32-rounding-level fit (1e-7) keep
+    # the mixed path within the 1e-5 bar; out-of-range values are rejected.
+    _lib = G.lib()
+    w = W.tiny(40_000, 12, L=6, p=17, clustered_frac=0.6, dtype="f32")
+    u64, v64 = G.run(w, "fp64")
+    errs = {}
+    for tol in (None, 100, 2500, 20000):
+        opts = {} if tol is None else {_lib.PETFMM_OPT_NEAR_TOL: tol}
+        umx, vmx = G.run(w, "mixed", options=opts)
+        errs[tol] = G.rel_l2(umx, vmx, u64, v64)
+    assert errs[None] == errs[2500]              # the default is 2.5e-6
+    assert errs[100] <= TOLMX and errs[2500] <= TOLMX
+    assert errs[20000] < 5e-5                   # a loose fit: loose, bounded result
+    ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype=w.dtype)
+    for bad in (0, -5, 1_000_001):
+        with pytest.raises(_lib.PetfmmError):
+            ctx.set_option(_lib.PETFMM_OPT_NEAR_TOL, bad)
+    ctx.close()
