@@ -57,7 +57,9 @@ struct InstDesc {
     int64_t tc_unit0[MAX_L + 1];        // per level: first unit of this (instance, level)
                                         // in the tensor-core M2L launch, or -1
     int tc_segmax;                      // widest tensor-core unit (parent cells)
-    int tc_pad;
+    uint32_t tc_levels;                 // bit l: level l's dense units run on the tensor
+                                        // cores (else, if tc_unit0[l] >= 0, on the
+                                        // tiled SIMT kernel)
     // mixed-precision P2P constants (leaf units)
     float kappa;            // w^2 / (2 sigma^2): q = kappa * rho^2
     float cnear;            // w / (4 pi sigma^2)
@@ -210,8 +212,17 @@ __host__ __device__ __forceinline__ int64_t tc_unit_of(int l, int segmax, int c,
     return (int64_t(c) * W + Py) * nseg + Px / s;
 }
 
-// A unit goes to the tensor cores when at least dense_pct percent of its
-// targets hold particles; the SIMT kernel takes the boxes of the others.
+// Units of the tiled SIMT M2L hold up to this many parent cells.
+constexpr int M2L_TILE_SEG = 128;
+
+// Widest unit of level l of an instance (tensor-core or tiled SIMT units).
+__host__ __device__ __forceinline__ int unit_segmax(const InstDesc &d, int l) {
+    return ((d.tc_levels >> l) & 1u) ? d.tc_segmax : M2L_TILE_SEG;
+}
+
+// A unit goes to the tensor cores (or the tiled SIMT kernel) when at least
+// dense_pct percent of its targets hold particles; the per-box SIMT kernel
+// takes the boxes of the others.
 __host__ __device__ __forceinline__ bool tc_unit_dense(uint32_t count, int seg, int dense_pct) {
     return count > 0 && 100u * count >= uint32_t(dense_pct) * uint32_t(seg);
 }

@@ -69,10 +69,10 @@ struct TaskRange {
 struct Plan {
     std::vector<InstDesc> inst;
     std::vector<Task> tasks;
-    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc;
+    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tile;
     std::vector<TaskRange> m2m, l2l;  // in launch order
     int64_t N = 0, nleaves = 0, nstart = 0, ncoef = 0, items_cap = 0;
-    int nbits = 0, pmax = 1, Lmax = 0;
+    int nbits = 0, pmax = 1, Lmax = 0, tile_pmax = 1;
     int deg = 0, general = 0;          // mixed P2P variant (max over instances)
     size_t tc_smem = 0;                // dynamic shared memory of the tensor-core M2L
 };
@@ -322,6 +322,7 @@ void flatten_tasks(Plan &pl) {
     put(pl.leaves_wl);
     put(pl.m2l);
     put(pl.m2l_tc);
+    put(pl.m2l_tile);
     for (TaskRange &r : pl.m2m) put(r);
     for (TaskRange &r : pl.l2l) put(r);
 }
@@ -384,6 +385,7 @@ int build_plan(int precision, bool use_tc, int tc_segmax, double near_tol,
         const int64_t nleaf = int64_t(1) << (2 * d.L);
         for (int l = 0; l <= MAX_L; ++l) d.tc_unit0[l] = -1;
         d.tc_segmax = tc_segmax;
+        d.tc_levels = 0;
         add_task(pl.morton, i, d.L, d.n, 256);
         add_task(pl.start, i, d.L, nleaf + 1, 256);
         add_task(pl.particles, i, d.L, d.n, 256);
@@ -395,12 +397,27 @@ int build_plan(int precision, bool use_tc, int tc_segmax, double near_tol,
             // sparse ones (a data-dependent split made on the device)
             if (precision == PETFMM_MIXED && use_tc && m2l_tc_supported(d.p, l, tc_segmax)) {
                 d.tc_unit0[l] = pl.m2l_tc.nblocks;  // one unit per block
+                d.tc_levels |= 1u << l;
                 add_task(pl.m2l_tc, i, l, m2l_tc_units(l, tc_segmax), 1);
                 pl.tc_smem = std::max(pl.tc_smem, m2l_tc_smem_bytes(d.p, m2l_tc_seg(l, tc_segmax)));
             }
             add_task(pl.m2l, i, l, int64_t(1) << (2 * l), M2L_BOXES);
         }
         items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
+    }
+    // the other levels of the mixed path: dense units on the tiled SIMT kernel
+    // (their units follow the tensor-core units in the unit-count array)
+    if (precision == PETFMM_MIXED) {
+        for (int i = 0; i < ni; ++i) {
+            InstDesc &d = pl.inst[i];
+            if (!m2l_tile_supported(d.p)) continue;
+            for (int l = 2; l <= d.L; ++l) {
+                if ((d.tc_levels >> l) & 1u) continue;
+                d.tc_unit0[l] = pl.m2l_tc.nblocks + pl.m2l_tile.nblocks;
+                add_task(pl.m2l_tile, i, l, m2l_tile_units(l), 1);
+                pl.tile_pmax = std::max(pl.tile_pmax, d.p);
+            }
+        }
     }
     // M2M rounds: round r computes level L_i - 1 - r (>= 2) of every instance.
     for (int r = 0; r + 3 <= Lmax; ++r) {
@@ -532,7 +549,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->occ, size_t(pl.nleaves) * sizeof(uint2), st));
     PF_TRY(ensure(c->off, size_t(pl.nleaves) * 4, st));
     PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
-    PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks) * sizeof(uint32_t), st));
+    PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks + pl.m2l_tile.nblocks) * sizeof(uint32_t),
+                  st));
     P2POrder order{};
     if (c->p2p_mode == 0) {
         const size_t cap = size_t(pl.items_cap);
@@ -625,10 +643,15 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     }
     stage_mark(c, PETFMM_STAGE_M2L);
     uint32_t *ucount = nullptr;
-    if (pl.m2l_tc.count) {
+    if (pl.m2l_tc.count || pl.m2l_tile.count) {
         ucount = static_cast<uint32_t *>(c->ucount.p);
-        PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc.first, pl.m2l_tc.count, pl.m2l_tc.nblocks,
-                                     dinst, start, ucount, st, lc));
+        if (pl.m2l_tc.count)
+            PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc.first, pl.m2l_tc.count,
+                                         pl.m2l_tc.nblocks, dinst, start, ucount, st, lc));
+        if (pl.m2l_tile.count)
+            PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tile.first, pl.m2l_tile.count,
+                                         pl.m2l_tile.nblocks, dinst, start,
+                                         ucount + pl.m2l_tc.nblocks, st, lc));
     }
     if (pl.m2l.count) {
         if (mixed)
@@ -650,6 +673,12 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                               pl.tc_smem, spin, reinterpret_cast<int *>(ctrl + CTRL_STATUS), st,
                               lc));
     }
+    if (pl.m2l_tile.count)
+        PF_CUDA(launch_m2l_tile(dtask + pl.m2l_tile.first, pl.m2l_tile.count, pl.m2l_tile.nblocks,
+                                pl.tile_pmax, dinst, start,
+                                static_cast<const float2 *>(c->me.p),
+                                static_cast<float2 *>(c->le.p), ucount + pl.m2l_tc.nblocks,
+                                c->tc_dense_pct, st, lc));
     stage_mark(c, PETFMM_STAGE_L2L);
     for (const TaskRange &tr : pl.l2l) {
         if (mixed)
@@ -870,6 +899,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     emit(4, pl.leaves_wl);
     emit(5, pl.m2l);
     emit(6, pl.m2l_tc);
+    emit(7, pl.m2l_tile);
     for (size_t r = 0; r < pl.m2m.size(); ++r) emit(100 + int64_t(r), pl.m2m[r]);
     for (size_t r = 0; r < pl.l2l.size(); ++r) emit(200 + int64_t(r), pl.l2l[r]);
     return n;

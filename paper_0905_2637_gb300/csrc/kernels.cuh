@@ -100,7 +100,8 @@ int64_t m2l_tc_units(int level, int segmax);
 size_t m2l_tc_smem_bytes(int p, int seg);
 int m2l_tc_seg(int level, int segmax);
 void host_m2l_tc_images(int p, std::vector<float> &out);
-// ucount[u] = targets holding particles in unit u of the tensor-core launch.
+// ucount[u] = targets holding particles in unit u of the launch (tensor-core
+// or tiled SIMT units; block index = unit).
 cudaError_t launch_tc_unit_count(const Task *tasks, int ntasks, int64_t nunits,
                                  const InstDesc *insts, const uint32_t *start, uint32_t *ucount,
                                  cudaStream_t st, uint64_t *launches);
@@ -110,6 +111,17 @@ cudaError_t launch_m2l_tc(const Task *tasks, int ntasks, int64_t nblocks, const 
                           const uint32_t *start, const float2 *me, float2 *le,
                           const uint32_t *ucount, int dense_pct, size_t smem_bytes,
                           long long spin_limit, int *status, cudaStream_t st, uint64_t *launches);
+
+// ---- m2l_tile.cu -----------------------------------------------------------
+// Tiled SIMT M2L (mixed path, p <= 24) for the dense units of the levels the
+// tensor cores do not take; units as above with M2L_TILE_SEG parent cells.
+bool m2l_tile_supported(int p);
+int64_t m2l_tile_units(int level);
+size_t m2l_tile_smem_bytes(int p, int level);
+cudaError_t launch_m2l_tile(const Task *tasks, int ntasks, int64_t nblocks, int pmax,
+                            const InstDesc *insts, const uint32_t *start, const float2 *me,
+                            float2 *le, const uint32_t *ucount, int dense_pct, cudaStream_t st,
+                            uint64_t *launches);
 
 // units of work per block of each expansion kernel (the host plans with them)
 constexpr int P2M_WARPS = 4;      // warps per block

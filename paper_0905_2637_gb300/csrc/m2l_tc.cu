@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) k_tc_unit_count(const Task *__restrict__ 
     const InstDesc &d = insts[t.inst];
     const int l = t.level;
     int c, Py, Px0, SEG;
-    tc_unit_decode(l, d.tc_segmax, u - t.block0, &c, &Py, &Px0, &SEG);
+    tc_unit_decode(l, unit_segmax(d, l), u - t.block0, &c, &Py, &Px0, &SEG);
     const uint32_t *st = start + d.soff;
     uint32_t cnt = 0;
     for (int i = lane; i < SEG; i += 32) {
