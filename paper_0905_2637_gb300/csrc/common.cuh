@@ -212,12 +212,51 @@ __host__ __device__ __forceinline__ int64_t tc_unit_of(int l, int segmax, int c,
     return (int64_t(c) * W + Py) * nseg + Px / s;
 }
 
-// Units of the tiled SIMT M2L hold up to this many parent cells.
+// Units of the tiled SIMT M2L: a segment of M2L_TILE_SEG parent cells of one
+// parent row, or, where rows are shorter, R whole rows of together at most
+// M2L_TILE_ROWS_BOXES target boxes (half a full unit: a shallow level has few
+// boxes, and smaller units keep more CTAs in flight).
 constexpr int M2L_TILE_SEG = 128;
+constexpr int M2L_TILE_ROWS_BOXES = 64;
 
-// Widest unit of level l of an instance (tensor-core or tiled SIMT units).
-__host__ __device__ __forceinline__ int unit_segmax(const InstDesc &d, int l) {
-    return ((d.tc_levels >> l) & 1u) ? d.tc_segmax : M2L_TILE_SEG;
+__host__ __device__ __forceinline__ void tile_geom(int l, int *R, int *seg) {
+    const int W = 1 << (l - 1);
+    *seg = W < M2L_TILE_SEG ? W : M2L_TILE_SEG;
+    const int r = W < M2L_TILE_SEG ? M2L_TILE_ROWS_BOXES / *seg : 1;
+    *R = r < 1 ? 1 : r < W ? r : W;
+}
+
+__host__ __device__ __forceinline__ int64_t tile_units(int l) {
+    const int W = 1 << (l - 1);
+    int R, s;
+    tile_geom(l, &R, &s);
+    return int64_t(4) * (W / R) * (W / s);
+}
+
+__host__ __device__ __forceinline__ void tile_unit_decode(int l, int64_t unit, int *c, int *Py0,
+                                                          int *R, int *Px0, int *seg) {
+    const int W = 1 << (l - 1);
+    tile_geom(l, R, seg);
+    const int nseg = W / *seg, nrow = W / *R;
+    *c = int(unit / (int64_t(nrow) * nseg));
+    const int64_t rem = unit - int64_t(*c) * nrow * nseg;
+    *Py0 = int(rem / nseg) * *R;
+    *Px0 = int(rem - (rem / nseg) * nseg) * *seg;
+}
+
+// Unit of box (c, Py, Px) of level l (tensor-core or tiled units) and the
+// number of its targets.
+__host__ __device__ __forceinline__ int64_t unit_of(const InstDesc &d, int l, int c, int Py,
+                                                    int Px, int *nbox) {
+    if ((d.tc_levels >> l) & 1u) {
+        *nbox = tc_seg(l, d.tc_segmax);
+        return tc_unit_of(l, d.tc_segmax, c, Py, Px);
+    }
+    const int W = 1 << (l - 1);
+    int R, s;
+    tile_geom(l, &R, &s);
+    *nbox = R * s;
+    return (int64_t(c) * (W / R) + Py / R) * (W / s) + Px / s;
 }
 
 // A unit goes to the tensor cores (or the tiled SIMT kernel) when at least

@@ -558,9 +558,9 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
         mine = box_count(st, d.L, l, morton_key(uint32_t(jx), uint32_t(jy))) != 0;
         if (mine && d.tc_unit0[l] >= 0) {
             const int jc = (jx & 1) | ((jy & 1) << 1);
-            const int sm = unit_segmax(d, l);
-            const int64_t u = d.tc_unit0[l] + tc_unit_of(l, sm, jc, jy >> 1, jx >> 1);
-            mine = !tc_unit_dense(ucount[u], tc_seg(l, sm), dense_pct);
+            int nbox;
+            const int64_t u = d.tc_unit0[l] + unit_of(d, l, jc, jy >> 1, jx >> 1, &nbox);
+            mine = !tc_unit_dense(ucount[u], nbox, dense_pct);
         }
     }
     uint32_t todo = __ballot_sync(0xffffffffu, mine);

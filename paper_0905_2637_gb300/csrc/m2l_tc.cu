@@ -54,12 +54,16 @@ __global__ void __launch_bounds__(256) k_tc_unit_count(const Task *__restrict__ 
     const Task t = tasks[find_task(tasks, ntasks, u)];
     const InstDesc &d = insts[t.inst];
     const int l = t.level;
-    int c, Py, Px0, SEG;
-    tc_unit_decode(l, unit_segmax(d, l), u - t.block0, &c, &Py, &Px0, &SEG);
+    int c, Py0, R = 1, Px0, SEG;
+    if ((d.tc_levels >> l) & 1u)
+        tc_unit_decode(l, d.tc_segmax, u - t.block0, &c, &Py0, &Px0, &SEG);
+    else
+        tile_unit_decode(l, u - t.block0, &c, &Py0, &R, &Px0, &SEG);
     const uint32_t *st = start + d.soff;
     uint32_t cnt = 0;
-    for (int i = lane; i < SEG; i += 32) {
-        const uint32_t ix = uint32_t(2 * (Px0 + i) + (c & 1)), iy = uint32_t(2 * Py + (c >> 1));
+    for (int i = lane; i < R * SEG; i += 32) {
+        const int r = i / SEG, x = i - r * SEG;
+        const uint32_t ix = uint32_t(2 * (Px0 + x) + (c & 1)), iy = uint32_t(2 * (Py0 + r) + (c >> 1));
         cnt += box_count(st, d.L, l, morton_key(ix, iy)) != 0;
     }
 #pragma unroll

@@ -2,15 +2,17 @@
 // mixed path, on the levels the tensor cores do not take (parent rows of
 // fewer than 128 cells) and for every level when they are switched off.
 //
-// The unit of work is the tensor-core kernel's (m2l_tc.cu): one CTA per
-// (target child class c, parent row, segment of up to 128 parent cells), and
-// it takes the unit only if at least dense_pct percent of its targets hold
-// particles (the per-box SIMT kernel takes the boxes of the others).  For
-// each of the 12 (source class c', parent row offset dy) strips the CTA
-// stages the strip's source expansions once in shared memory -- the segment
-// plus one cell on each side, empty or out-of-domain boxes as zeros -- and
-// the up to three operators T_delta of the strip's dx shifts; the dx shifts
-// read the same strip one row earlier or later.  Thread t holds target boxes
+// The unit of work follows the tensor-core kernel's (m2l_tc.cu): one CTA per
+// (target child class c, target boxes) -- a segment of 128 parent cells of
+// one parent row, or R whole rows of together at most 64 cells where rows
+// are shorter -- and it takes
+// the unit only if at least dense_pct percent of its targets hold particles
+// (the per-box SIMT kernel takes the boxes of the others).  For each of the
+// 12 (source class c', parent row offset dy) strips the CTA stages, for each
+// of its rows, the source expansions of the segment plus one cell on each
+// side once in shared memory (empty or out-of-domain boxes as zeros), and the
+// up to three operators T_delta of the strip's dx shifts; the dx shifts read
+// the same staged rows one row earlier or later.  Thread t holds target boxes
 // t mod 64 and t mod 64 + 64 and one half of the p output coefficients, so a
 // step of the k loop is two shared loads of source coefficients, one
 // broadcast load of an operator entry per output coefficient and eight FFMA
@@ -28,7 +30,8 @@ namespace petfmm {
 #define PF_LAUNCHED(n) do { if (launches) *launches += (n); } while (0)
 
 constexpr int MT_THREADS = 128;
-constexpr int MT_SEG = M2L_TILE_SEG;  // parent cells per unit (all of a shorter row)
+constexpr int MT_BOXES = M2L_TILE_SEG;  // target boxes per unit
+constexpr int MT_MAX_ROWS = 160;        // staged rows: R (SEG + 2) <= 144
 constexpr int MT_MAX_P = 24;
 
 // shared-memory row stride of the staged strip: odd, so that the 8-byte reads
@@ -41,7 +44,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
     const uint32_t *__restrict__ start, const float2 *__restrict__ me, float2 *__restrict__ le,
     const uint32_t *__restrict__ ucount, int dense_pct) {
     extern __shared__ float2 mt_smem[];
-    __shared__ uint8_t rowocc[MT_SEG + 2];
+    __shared__ uint8_t rowocc[MT_MAX_ROWS];
 
     const int tid = threadIdx.x;
     const int ti = find_task(tasks, ntasks, blockIdx.x);
@@ -49,24 +52,30 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
     const InstDesc &d = insts[t.inst];
     const int l = t.level, L = d.L, p = d.p;
     const int W = 1 << (l - 1);
-    int c, Py, Px0, SEG;
-    tc_unit_decode(l, MT_SEG, int64_t(blockIdx.x) - t.block0, &c, &Py, &Px0, &SEG);
-    if (!tc_unit_dense(ucount[blockIdx.x], SEG, dense_pct)) return;  // sparse: per-box kernel
+    // the unit: parent rows Py0 .. Py0 + R - 1, cells Px0 .. Px0 + SEG - 1
+    int c, Py0, R, Px0, SEG;
+    tile_unit_decode(l, int64_t(blockIdx.x) - t.block0, &c, &Py0, &R, &Px0, &SEG);
+    if (!tc_unit_dense(ucount[blockIdx.x], R * SEG, dense_pct)) return;  // sparse: per-box kernel
     const int cx = c & 1, cy = c >> 1;
     const uint32_t *st = start + d.soff;
 
     const int SP = mt_stride(p);
-    const int Rs = SEG + 2;
-    float2 *strip = mt_smem;                     // Rs rows x SP
-    float2 *tsm = mt_smem + size_t(Rs) * SP;     // 3 operators, [k][m]
+    const int Rs = SEG + 2;          // staged rows per parent row
+    const int nrows = R * Rs;
+    float2 *strip = mt_smem;                      // nrows x SP
+    float2 *tsm = mt_smem + size_t(nrows) * SP;   // 3 operators, [k][m]
     const int psq = p * p;
 
-    // this thread: boxes b0, b1 of the segment, coefficients m0 .. m0 + mc - 1
+    // this thread: boxes b0, b1 of the unit, coefficients m0 .. m0 + mc - 1;
+    // box b is cell b % SEG of row b / SEG, staged at row (b / SEG) Rs + b % SEG + 1
     const int half = (p + 1) >> 1;
     const int b0 = tid & 63, b1 = b0 + 64;
     const int m0 = (tid >> 6) * half;
     const int mc = (tid >> 6) ? p - half : half;
-    const bool act0 = b0 < SEG, act1 = b1 < SEG;
+    const int nb = R * SEG;
+    const bool act0 = b0 < nb, act1 = b1 < nb;
+    const int r0 = b0 / SEG, r1 = b1 / SEG;
+    const int s0 = r0 * Rs + (b0 - r0 * SEG) + 1, s1 = r1 * Rs + (b1 - r1 * SEG) + 1;
 
     float2 acc0[PH], acc1[PH];
 #pragma unroll
@@ -77,12 +86,11 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
     const int64_t quarter = int64_t(1) << (2 * (l - 1));
     const float2 *lev = me + d.eoff + lvl_off(l) * p;
     const float2 *tab = static_cast<const float2 *>(d.t_m2l);
+    const uint32_t inv_p = ((1u << 20) + uint32_t(p) - 1) / uint32_t(p);
 
     for (int cs = 0; cs < 4; ++cs) {
         const int csx = cs & 1, csy = cs >> 1;
         for (int dyp = -1; dyp <= 1; ++dyp) {
-            const int Pys = Py + dyp;
-            if (Pys < 0 || Pys >= W) continue;
             int ops[3];
             uint32_t mask3 = 0;
             for (int dxp = -1; dxp <= 1; ++dxp) {
@@ -95,27 +103,36 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
                 }
             }
             if (!mask3) continue;
-            // occupancy of the strip's source boxes (row r <-> Px = Px0 - 1 + r);
-            // never-written expansions of empty boxes are staged as zeros
+            // occupancy of the staged source boxes: staged row q is cell
+            // Px0 - 1 + q % Rs of parent row Py0 + q / Rs + dyp; empty and
+            // out-of-domain boxes (never-written expansions) are staged as zeros
             bool anyr = false;
-            for (int r = tid; r < Rs; r += MT_THREADS) {
-                const int Px = Px0 - 1 + r;
+            for (int q = tid; q < nrows; q += MT_THREADS) {
+                const int rr = q / Rs;
+                const int Px = Px0 - 1 + (q - rr * Rs), Pys = Py0 + rr + dyp;
                 bool o = false;
-                if (Px >= 0 && Px < W)
+                if (Px >= 0 && Px < W && Pys >= 0 && Pys < W)
                     o = box_count(st, L, l,
                                   morton_key(uint32_t(2 * Px + csx), uint32_t(2 * Pys + csy))) != 0;
-                rowocc[r] = o;
+                rowocc[q] = o;
                 anyr |= o;
             }
             if (!__syncthreads_or(anyr)) continue;
-            // stage the strip (contiguous in the class-split layout) ...
-            const float2 *src = lev + (int64_t(cs) * quarter + int64_t(Pys) * W + Px0 - 1) * p;
-            const int total = Rs * p;
+            // stage the strips (each row's cells are contiguous in the
+            // class-split layout); element e = q p + k, q = e / p exactly for
+            // e < 2^14 by the multiply-shift (p <= 24, nrows <= MT_MAX_ROWS)
+            const int total = nrows * p;
             for (int e = tid; e < total; e += MT_THREADS) {
-                const int r = e / p, k = e - r * p;
-                strip[r * SP + k] = rowocc[r] ? __ldg(src + e) : make_float2(0.f, 0.f);
+                const int q = int((uint32_t(e) * inv_p) >> 20), k = e - q * p;
+                float2 v = make_float2(0.f, 0.f);
+                if (rowocc[q]) {
+                    const int rr = q / Rs;
+                    const int Px = Px0 - 1 + (q - rr * Rs), Pys = Py0 + rr + dyp;
+                    v = __ldg(lev + (int64_t(cs) * quarter + int64_t(Pys) * W + Px) * p + k);
+                }
+                strip[q * SP + k] = v;
             }
-            // ... and the operators of its dx shifts
+            // ... and the operators of the dx shifts
             for (int s3 = 0; s3 < 3; ++s3) {
                 if (!(mask3 & (1u << s3))) continue;
                 const float2 *T = tab + size_t(ops[s3]) * psq;
@@ -125,8 +142,8 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
             for (int s3 = 0; s3 < 3; ++s3) {
                 if (!(mask3 & (1u << s3))) continue;
                 const float2 *T = tsm + s3 * psq + m0;
-                const float2 *a0p = strip + (b0 + s3) * SP;  // row b + 1 + (s3 - 1)
-                const float2 *a1p = strip + (b1 + s3) * SP;
+                const float2 *a0p = strip + (s0 + s3 - 1) * SP;
+                const float2 *a1p = strip + (s1 + s3 - 1) * SP;
                 if (act1) {
                     for (int k = 0; k < p; ++k) {
                         const float2 a0 = a0p[k], a1 = a1p[k];
@@ -153,9 +170,9 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
     }
     // write the targets that hold particles (the others' LE is never read)
     for (int j = 0; j < 2; ++j) {
-        const int b = j ? b1 : b0;
         if (!(j ? act1 : act0)) continue;
-        const int Px = Px0 + b;
+        const int b = j ? b1 : b0, rr = j ? r1 : r0;
+        const int Px = Px0 + b - rr * SEG, Py = Py0 + rr;
         if (!box_count(st, L, l, morton_key(uint32_t(2 * Px + cx), uint32_t(2 * Py + cy))))
             continue;
         float2 *dst = le + d.eoff + (lvl_off(l) + int64_t(c) * quarter + int64_t(Py) * W + Px) * p;
@@ -167,11 +184,12 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
 
 bool m2l_tile_supported(int p) { return p >= 1 && p <= MT_MAX_P; }
 
-int64_t m2l_tile_units(int level) { return m2l_tc_units(level, MT_SEG); }
+int64_t m2l_tile_units(int level) { return tile_units(level); }
 
 size_t m2l_tile_smem_bytes(int p, int level) {
-    const int seg = tc_seg(level, MT_SEG);
-    return (size_t(seg + 2) * mt_stride(p) + size_t(3) * p * p) * sizeof(float2);
+    int R, seg;
+    tile_geom(level, &R, &seg);
+    return (size_t(R) * (seg + 2) * mt_stride(p) + size_t(3) * p * p) * sizeof(float2);
 }
 
 cudaError_t launch_m2l_tile(const Task *tasks, int ntasks, int64_t nblocks, int pmax,
@@ -179,7 +197,7 @@ cudaError_t launch_m2l_tile(const Task *tasks, int ntasks, int64_t nblocks, int 
                             float2 *le, const uint32_t *ucount, int dense_pct, cudaStream_t st,
                             uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    const size_t smem = (size_t(MT_SEG + 2) * mt_stride(pmax) + size_t(3) * pmax * pmax) *
+    const size_t smem = (size_t(MT_MAX_ROWS) * mt_stride(pmax) + size_t(3) * pmax * pmax) *
                         sizeof(float2);
     const int ph = (pmax + 1) / 2;
     void (*k)(const Task *, int, const InstDesc *, const uint32_t *, const float2 *, float2 *,

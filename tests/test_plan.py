@@ -69,14 +69,17 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
                 w = 2 ** (int(r[2]) - 1)
                 assert r[3] == 4 * w * (w // min(w, 512))
         # the other levels of the mixed path (p <= 24) get the tiled SIMT
-        # launch, one CTA per (class, parent row, 128-cell segment)
+        # launch, one CTA per (class, 128 target boxes: a 128-cell segment of
+        # a parent row, or several whole rows where rows are shorter)
         tile = sorted(int(r[2]) for r in ranges.get(7, []) if r[1] == i)
         assert tile == ([l for l in range(2, L + 1) if l not in tc]
                         if precision == 1 and p <= 24 else [])
         for r in ranges.get(7, []):
             if r[1] == i:
                 w = 2 ** (int(r[2]) - 1)
-                assert r[3] == 4 * w * (w // min(w, 128))
+                seg = min(w, 128)
+                rows = max(1, min(64 // seg, w)) if w < 128 else 1
+                assert r[3] == 4 * (w // rows) * (w // seg)
         m2m = [(rid, int(r[2])) for rid, rs in ranges.items() if 100 <= rid < 200 for r in rs if r[1] == i]
         assert sorted(l for _, l in m2m) == list(range(2, L))
         # bottom-up: round r holds level L - 1 - r
