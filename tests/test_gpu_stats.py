@@ -88,6 +88,9 @@ def test_p2p_dispatch_order_does_not_change_results():
     # the same bits, in both precisions
     _lib = G.lib()
     cases = [(W.tiny(60_000, 21, L=6, p=12, clustered_frac=0.7, dtype="f32"), "mixed"),
+             # sigma small against the leaf: the exp-branch kernel, whose
+             # tiers are chosen by warp votes
+             (W.tiny(40_000, 24, L=5, p=12, sigma=0.002, clustered_frac=0.3), "mixed"),
              (W.tiny(30_000, 22, L=5, p=14, clustered_frac=0.7), "fp64"),
              (W.tiny(1, 23, L=3, p=8), "mixed")]
     for w, prec in cases:
