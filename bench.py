@@ -272,9 +272,11 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--workload", default="clustered-16M",
-                    choices=["clustered-16M", "clustered-4M", "lattice-1M"],
+                    choices=["clustered-16M", "clustered-4M", "lattice-1M", "lamb-oseen-765k"],
                     help="clustered-4M (2^22 blobs, L = 9, same blobs per leaf) and lattice-1M "
-                         "(every leaf occupied) are the small cases used for ncu captures")
+                         "(every leaf occupied) are the small cases used for ncu captures; "
+                         "lamb-oseen-765k is the paper's Sec. 7.1 test case (875^2 lattice, "
+                         "L = 10, p = 17)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
@@ -301,6 +303,8 @@ def main():
         # a quarter of the blobs, one level shallower, sigma scaled with the
         # leaf: the same blobs per leaf and the same near-field kernel variant
         w = W.clustered(n=1 << 22, L=9, sigma=0.004, name="clustered-4M")
+    elif args.workload == "lamb-oseen-765k":
+        w = W.lamb_oseen_paper(dtype="f32")
     else:
         w = W.lattice(dtype="f32")
     stream = torch.cuda.Stream()

@@ -227,8 +227,9 @@ int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out);
  * int64 {range, instance, level, units, first block}; range 0 binning,
  * 1 leaf starts, 2 gather, 3 P2M, 4 P2P work list, 5 M2L (SIMT, units =
  * target boxes), 6 M2L on the tensor cores (units = CTAs), 7 tiled SIMT M2L
- * (units = CTAs), 100 + r the r-th M2M launch, 200 + r the r-th L2L launch.  Writes at most cap tasks and
- * returns the total count, or PETFMM_EINVAL. */
+ * (units = CTAs), 100 + r the r-th M2M launch, 200 + r the r-th L2L launch,
+ * as a context with default options would launch them.  Writes at most cap
+ * tasks and returns the total count, or PETFMM_EINVAL. */
 int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, int64_t *out, int cap);
 
 /* Options. */

@@ -91,6 +91,8 @@ struct Problem {
 namespace {
 // default relative tolerance of the near-field polynomial (PETFMM_OPT_NEAR_TOL)
 constexpr double kNearTolDefault = 2.5e-6;
+// default widest tensor-core M2L unit (PETFMM_OPT_TC_SEG)
+constexpr int kTcSegDefault = 128;
 }  // namespace
 
 struct petfmm_ctx {
@@ -107,7 +109,7 @@ struct petfmm_ctx {
     // measured on GB300 (clustered 16M and lattice 1M blobs): 128-cell units
     // with a 25% occupancy threshold gave the fastest M2L on both
     int tc_dense_pct = 25;
-    int tc_segmax = 128;
+    int tc_segmax = kTcSegDefault;
     double near_tol = kNearTolDefault;
     int64_t spin_limit = 0;
     uint64_t launches = 0, evaluations = 0;
@@ -879,7 +881,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     int rc = problems_from(n_inst, inst, probs);
     if (rc) return rc;
     Plan pl;
-    rc = build_plan(precision, true, TC_MAX_SEG, kNearTolDefault, probs, pl);
+    rc = build_plan(precision, true, kTcSegDefault, kNearTolDefault, probs, pl);
     if (rc) return rc;
     int n = 0;
     auto emit = [&](int64_t id, const TaskRange &r) {

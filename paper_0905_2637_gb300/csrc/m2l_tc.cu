@@ -37,8 +37,29 @@ namespace petfmm {
 
 #define PF_LAUNCHED(n) do { if (launches) *launches += (n); } while (0)
 
-constexpr int TC_THREADS = 128;
+// 256 threads: the first 128 own the TMEM lanes (targets) in the epilogue,
+// all of them stage operands (twice the loads in flight of 128 threads)
+constexpr int TC_THREADS = 256;
 constexpr int TC_MAX_NPAD = 48;
+
+// Operators of the strip (source class cs, parent row offset dyp) for a
+// target of class c: bit s of the result is set if the dx shift dxp = s - 1
+// is in the interaction list (child offset not within one box), ops[s] its
+// operator index.
+__device__ __forceinline__ uint32_t tc_strip_ops(int c, int cs, int dyp, int *ops) {
+    const int cx = c & 1, cy = c >> 1, csx = cs & 1, csy = cs >> 1;
+    uint32_t mask3 = 0;
+    for (int dxp = -1; dxp <= 1; ++dxp) {
+        const int ddx = 2 * dxp + csx - cx, ddy = 2 * dyp + csy - cy;
+        const int ax = ddx < 0 ? -ddx : ddx, ay = ddy < 0 ? -ddy : ddy;
+        ops[dxp + 1] = 0;
+        if ((ax > ay ? ax : ay) >= 2) {
+            mask3 |= 1u << (dxp + 1);
+            ops[dxp + 1] = m2l_op_index(ddx, ddy);
+        }
+    }
+    return mask3;
+}
 
 // Counts, for every unit of the tensor-core launch (index = the launch's block
 // index), how many of its targets hold particles; one warp per unit.  The
@@ -79,7 +100,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     __shared__ uint32_t used_mask;
-    __shared__ uint8_t rowocc[TC_MAX_SEG + 2];
+    // source-box occupancy of every strip of the unit: [strip][row]
+    __shared__ uint8_t socc[12][TC_MAX_SEG + 2];
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int ti = find_task(tasks, ntasks, blockIdx.x);
@@ -98,9 +120,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
     // which 128-target sub-tiles hold particles (empty ones issue no MMA)
     uint32_t sub_mask = 0;
     for (int s = 0; s < S; ++s) {
-        const int i = s * 128 + tid;
-        const uint32_t ix = uint32_t(2 * (Px0 + i) + cx), iy = uint32_t(2 * Py + cy);
-        if (__syncthreads_or(box_count(st, L, l, morton_key(ix, iy)) != 0)) sub_mask |= 1u << s;
+        bool o = false;
+        if (tid < 128) {
+            const int i = s * 128 + tid;
+            const uint32_t ix = uint32_t(2 * (Px0 + i) + cx), iy = uint32_t(2 * Py + cy);
+            o = box_count(st, L, l, morton_key(ix, iy)) != 0;
+        }
+        if (__syncthreads_or(o)) sub_mask |= 1u << s;
     }
 
     const int K2 = 2 * p;
@@ -145,118 +171,149 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
     bool ok = true;
     uint32_t used = 0;  // thread 0's record of initialised accumulators
 
-    for (int cs = 0; cs < 4 && ok; ++cs) {
-        const int csx = cs & 1, csy = cs >> 1;
-        for (int dyp = -1; dyp <= 1 && ok; ++dyp) {
+    // The strips: (source class cs, parent row offset dyp) pairs with at
+    // least one interaction-list operator, in a fixed order.  Strip j + 1's
+    // source expansions are copied asynchronously (cp.async, empty boxes
+    // zero-filled) into a raw buffer while strip j is split into the TF32
+    // operand layout and multiplied; its operator images follow as soon as
+    // strip j's MMAs have released the B buffer.
+    int ncand = 0;
+    uint8_t cand[12];
+    for (int cs = 0; cs < 4; ++cs)
+        for (int dyp = -1; dyp <= 1; ++dyp) {
             const int Pys = Py + dyp;
             if (Pys < 0 || Pys >= W) continue;
             int ops[3];
-            uint32_t mask3 = 0;
-            for (int dxp = -1; dxp <= 1; ++dxp) {
-                const int ddx = 2 * dxp + csx - cx, ddy = 2 * dyp + csy - cy;
-                const int ax = ddx < 0 ? -ddx : ddx, ay = ddy < 0 ? -ddy : ddy;
-                ops[dxp + 1] = 0;
-                if ((ax > ay ? ax : ay) >= 2) {
-                    mask3 |= 1u << (dxp + 1);
-                    ops[dxp + 1] = m2l_op_index(ddx, ddy);
-                }
-            }
-            if (!mask3) continue;
-            // occupancy of the strip's source boxes (row r <-> Px = Px0 - 1 + r)
-            bool anyr = false;
-            for (int r = tid; r < Rs; r += TC_THREADS) {
-                const int Px = Px0 - 1 + r;
-                bool o = false;
-                if (Px >= 0 && Px < W)
-                    o = box_count(st, L, l, morton_key(uint32_t(2 * Px + csx), uint32_t(2 * Pys + csy))) != 0;
-                rowocc[r] = o;
-                anyr |= o;
-            }
-            if (!__syncthreads_or(anyr)) continue;
-            // stage the strip: real parts at k < p, imaginary parts at p <= k < 2p.
-            // Element e of the strip is coefficient k of row r, e = r p + k; the
-            // row is e * inv_p >> 20 (exact for e < 2^14, p <= 24).  Four loads
-            // are issued before their stores so that they overlap.
+            if (tc_strip_ops(c, cs, dyp, ops)) cand[ncand++] = uint8_t(cs * 3 + dyp + 1);
+        }
+    const int total = Rs * p;
+    const uint32_t inv_p = ((1u << 20) + uint32_t(p) - 1) / uint32_t(p);
+    float2 *raw = reinterpret_cast<float2 *>(Bsm + size_t(6) * bslot);
+    // occupancy of all strips' source boxes at once (one round of lookups)
+    __shared__ uint32_t sany;
+    if (tid == 0) sany = 0;
+    __syncthreads();
+    for (int i = tid; i < ncand * Rs; i += TC_THREADS) {
+        const int jj = i / Rs, r = i - jj * Rs;
+        const int cs = cand[jj] / 3, dyp = cand[jj] % 3 - 1;
+        const int Px = Px0 - 1 + r, Pys = Py + dyp;
+        bool o = false;
+        if (Px >= 0 && Px < W)
+            o = box_count(st, L, l, morton_key(uint32_t(2 * Px + (cs & 1)),
+                                               uint32_t(2 * Pys + (cs >> 1)))) != 0;
+        socc[jj][r] = o;
+        if (o) atomicOr(&sany, 1u << jj);
+    }
+    __syncthreads();
+    const uint32_t strip_any = sany;
+    // first candidate >= j0 with an occupied source box: its raw copy is
+    // requested (one commit group); returns ncand if there is none
+    auto prepare = [&](int j0) -> int {
+        for (int jj = j0; jj < ncand; ++jj) {
+            if (!((strip_any >> jj) & 1u)) continue;
+            const int cs = cand[jj] / 3, dyp = cand[jj] % 3 - 1, Pys = Py + dyp;
             const float2 *src = lev + (int64_t(cs) * quarter + int64_t(Pys) * W + Px0 - 1) * p;
-            const int total = Rs * p;
-            const uint32_t inv_p = ((1u << 20) + uint32_t(p) - 1) / uint32_t(p);
-            for (int e0 = tid; e0 < total; e0 += 4 * TC_THREADS) {
-                float2 v[4];
-                int rr[4], kk[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * TC_THREADS;
-                    rr[u] = int((uint32_t(e) * inv_p) >> 20);
-                    kk[u] = e - rr[u] * p;
-                    v[u] = make_float2(0.f, 0.f);
-                    if (e < total && rowocc[rr[u]]) v[u] = __ldg(src + e);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (e0 + u * TC_THREADS >= total) break;
-                    const int r = rr[u], k = kk[u];
-                    const float hr = tf32_hi(v[u].x), hi_ = tf32_hi(v[u].y);
-                    const size_t o_re = (size_t(k >> 2) * Rs + r) * 4 + (k & 3);
-                    const size_t o_im = (size_t((k + p) >> 2) * Rs + r) * 4 + ((k + p) & 3);
-                    A_hi[o_re] = hr;
-                    A_lo[o_re] = v[u].x - hr;
-                    A_hi[o_im] = hi_;
-                    A_lo[o_im] = v[u].y - hi_;
-                }
+            for (int e = tid; e < total; e += TC_THREADS) {
+                const int r = int((uint32_t(e) * inv_p) >> 20);
+                cp_async8(smem_addr(raw + e), src + e, socc[jj][r] ? 8u : 0u);
             }
-            // the B operators of the (up to three) dx shifts, hi and lo images
+            cp_async_commit();
+            return jj;
+        }
+        return ncand;
+    };
+    // the B operators of strip jj's (up to three) dx shifts, hi and lo images
+    auto request_b = [&](int jj) {
+        int ops[3];
+        const uint32_t mask3 = tc_strip_ops(c, cand[jj] / 3, cand[jj] % 3 - 1, ops);
+        const int n4 = (2 * bslot) / 4;
+        for (int s3 = 0; s3 < 3; ++s3) {
+            if (!(mask3 & (1u << s3))) continue;
+            const float4 *src = reinterpret_cast<const float4 *>(bimg + size_t(ops[s3]) * 2 * bslot);
+            const uint32_t dst = smem_addr(Bsm + size_t(2 * s3) * bslot);
+            for (int i = tid; i < n4; i += TC_THREADS) cp_async16(dst + uint32_t(i) * 16, src + i);
+        }
+        cp_async_commit();
+    };
+
+    int j = prepare(0);
+    if (j < ncand) request_b(j);
+    while (j < ncand && ok) {
+        cp_async_wait_all();
+        __syncthreads();
+        // split the strip: real parts at k < p, imaginary parts at p <= k < 2p;
+        // element e of the raw strip is coefficient k of row r, e = r p + k,
+        // with r = e * inv_p >> 20 (exact for e < 2^14, p <= 24)
+        for (int e = tid; e < total; e += TC_THREADS) {
+            const int r = int((uint32_t(e) * inv_p) >> 20), k = e - r * p;
+            const float2 v = raw[e];
+            const float hr = tf32_hi(v.x), hi_ = tf32_hi(v.y);
+            const size_t o_re = (size_t(k >> 2) * Rs + r) * 4 + (k & 3);
+            const size_t o_im = (size_t((k + p) >> 2) * Rs + r) * 4 + ((k + p) & 3);
+            A_hi[o_re] = hr;
+            A_lo[o_re] = v.x - hr;
+            A_hi[o_im] = hi_;
+            A_lo[o_im] = v.y - hi_;
+        }
+        __syncthreads();
+        int ops[3];
+        const uint32_t mask3 = tc_strip_ops(c, cand[j] / 3, cand[j] % 3 - 1, ops);
+        const int jn = prepare(j + 1);  // its copy overlaps this strip's MMAs
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ahi = smem_addr(A_hi), alo = smem_addr(A_lo);
             for (int s3 = 0; s3 < 3; ++s3) {
                 if (!(mask3 & (1u << s3))) continue;
-                const float4 *src = reinterpret_cast<const float4 *>(bimg + size_t(ops[s3]) * 2 * bslot);
-                float4 *dst = reinterpret_cast<float4 *>(Bsm + size_t(2 * s3) * bslot);
-                for (int i = tid; i < (2 * bslot) / 4; i += TC_THREADS) dst[i] = __ldg(src + i);
-            }
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t ahi = smem_addr(A_hi), alo = smem_addr(A_lo);
-                for (int s3 = 0; s3 < 3; ++s3) {
-                    if (!(mask3 & (1u << s3))) continue;
-                    const uint32_t bhi = smem_addr(Bsm + size_t(2 * s3) * bslot);
-                    const uint32_t blo = smem_addr(Bsm + size_t(2 * s3 + 1) * bslot);
-                    for (int s = 0; s < S; ++s) {
-                        if (!(sub_mask & (1u << s))) continue;  // no target there
-                        const uint32_t row0 = uint32_t(s * 128 + 1 + (s3 - 1)) * 16;
-                        const uint32_t dt = tbase + uint32_t(s * Npad);
-                        const uint32_t as[3] = {ahi + row0, ahi + row0, alo + row0};
-                        const uint32_t bs[3] = {bhi, blo, bhi};
-                        for (int pr = 0; pr < 3; ++pr)
-                            for (int ks = 0; ks < Kpad / 8; ++ks) {
-                                mma_tf32(dt, mma_desc(as[pr] + uint32_t(ks) * 2 * LBO_A, LBO_A, SBO),
-                                         mma_desc(bs[pr] + uint32_t(ks) * 2 * LBO_B, LBO_B, SBO), idesc,
-                                         (used >> s) & 1u);
-                                used |= 1u << s;
-                            }
+                const uint32_t bhi = smem_addr(Bsm + size_t(2 * s3) * bslot);
+                const uint32_t blo = smem_addr(Bsm + size_t(2 * s3 + 1) * bslot);
+                // descriptors step by adding to their start-address field
+                // (address / 16 in the low bits; shared addresses stay below
+                // 256 KB, so the sum never carries out of the field)
+                const uint64_t sa = (2 * LBO_A) >> 4, sb = (2 * LBO_B) >> 4;
+                const uint64_t dbh = mma_desc(bhi, LBO_B, SBO), dbl = mma_desc(blo, LBO_B, SBO);
+                for (int s = 0; s < S; ++s) {
+                    if (!(sub_mask & (1u << s))) continue;  // no target there
+                    const uint32_t row0 = uint32_t(s * 128 + 1 + (s3 - 1)) * 16;
+                    const uint32_t dt = tbase + uint32_t(s * Npad);
+                    const uint64_t dah = mma_desc(ahi + row0, LBO_A, SBO);
+                    const uint64_t dal = mma_desc(alo + row0, LBO_A, SBO);
+                    for (int ks = 0; ks < Kpad / 8; ++ks) {
+                        const uint32_t acc = (used >> s) & 1u;
+                        mma_tf32(dt, dah + ks * sa, dbh + ks * sb, idesc, acc);
+                        mma_tf32(dt, dah + ks * sa, dbl + ks * sb, idesc, 1u);
+                        mma_tf32(dt, dal + ks * sa, dbh + ks * sb, idesc, 1u);
+                        used |= 1u << s;
                     }
                 }
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
             }
-            // wait until the tensor core has consumed the staged operands
-            const bool waited = mbar_wait(bar, phase, spin_limit);
-            // one decision for the whole CTA (every thread then takes the same barriers)
-            if (!__syncthreads_and(waited)) {
-                if (tid == 0) set_status(status, ST_ETIMEOUT);
-                ok = false;
-                // second bounded wait, so that TMEM is not freed under MMAs in flight
-                mbar_wait(bar, phase, 1LL << 26);
-            }
-            phase ^= 1u;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            __syncthreads();
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
         }
+        // wait until the tensor core has consumed the staged operands
+        const bool waited = mbar_wait(bar, phase, spin_limit);
+        // one decision for the whole CTA (every thread then takes the same barriers)
+        if (!__syncthreads_and(waited)) {
+            if (tid == 0) set_status(status, ST_ETIMEOUT);
+            ok = false;
+            // second bounded wait, so that TMEM is not freed under MMAs in flight
+            mbar_wait(bar, phase, 1LL << 26);
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (ok && jn < ncand) request_b(jn);
+        j = jn;
     }
+    // no asynchronous copy may still be writing shared memory past this point
+    cp_async_wait_all();
+    __syncthreads();
     if (tid == 0) used_mask = used;
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t umask = used_mask;
-    if (ok) {
+    if (ok && tid < 128) {
         for (int s = 0; s < S; ++s) {
             if (!(sub_mask & (1u << s))) continue;
             const int Px = Px0 + s * 128 + tid;
@@ -283,7 +340,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
 
 size_t m2l_tc_smem_bytes(int p, int seg) {
     const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
-    return size_t(2) * (Kpad / 4) * (seg + 2) * 16 + size_t(6) * Kpad * Npad * 4;
+    // A hi and lo, six B images, the raw strip (seg + 2 rows of p complex)
+    return size_t(2) * (Kpad / 4) * (seg + 2) * 16 + size_t(6) * Kpad * Npad * 4 +
+           size_t(seg + 2) * p * 8;
 }
 
 int m2l_tc_seg(int level, int segmax) { return tc_seg(level, segmax); }

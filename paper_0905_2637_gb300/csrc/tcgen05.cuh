@@ -1,6 +1,6 @@
 // tcgen05.cuh -- inline-PTX helpers for the 5th-generation tensor cores
 // (internal): shared-memory matrix descriptors, TF32 MMA issue, bounded
-// mbarrier waits, TF32 operand split and TMEM loads.
+// mbarrier waits, TF32 operand split, TMEM loads and asynchronous copies.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -55,6 +55,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Asynchronous global -> shared copies (cp.async): 8 bytes, of which
+// src_bytes (0 or 8) are read and the rest zero-filled; 16 bytes (L2 only).
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 }  // namespace petfmm

@@ -117,6 +117,16 @@ def lamb_oseen(sigma=0.02, half_width=0.5, core=0.1, gamma0=1.0, L=4, p=17, dtyp
     return Workload("lamb-oseen", x, y, g, sigma, dom, L, p, dtype)
 
 
+def lamb_oseen_paper(dtype="f32"):
+    """The Sec. 7.1 test case at the paper's size: an 875 x 875 lattice
+    (765,625 blobs) with sigma = 0.02 and h = 0.8 sigma, L = 10, p = 17; the
+    paper leaves Gamma_0, nu and t open, taken here as Gamma_0 = 1 and
+    4 nu t = 1."""
+    w = lamb_oseen(sigma=0.02, half_width=7.0, core=1.0, gamma0=1.0, L=10, p=17, dtype=dtype)
+    w.name = "lamb-oseen-765k"
+    return w
+
+
 def batch(n_inst=512, seed=1, dtype="f64", n_min=1_000, n_max=262_144):
     """Independent uniform instances of uneven size (log-uniform N)."""
     rng = np.random.default_rng(seed)

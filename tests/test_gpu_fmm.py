@@ -171,3 +171,17 @@ def test_near_field_tolerance_option():
         with pytest.raises(_lib.PetfmmError):
             ctx.set_option(_lib.PETFMM_OPT_NEAR_TOL, bad)
     ctx.close()
+
+
+def test_lamb_oseen_paper_case(orc):
+    # Sec. 7.1 at the paper's size: 875^2 lattice blobs, sigma = 0.02,
+    # h = 0.8 sigma, L = 10, p = 17 (leaves narrower than the lattice
+    # spacing: about one blob per occupied leaf, M2L-dominated)
+    w = W.lamb_oseen_paper(dtype="f64")  # FP64 outputs for the 1e-12 comparison
+    assert w.n == 875 * 875
+    u64, v64 = G.run(w, "fp64")
+    umx, vmx = G.run(w, "mixed")
+    assert G.rel_l2(umx, vmx, u64, v64) <= TOLMX
+    tg = W.sample_targets(w.n, 512, seed=11)
+    ur, vr = orc.fmm(w.x, w.y, w.gamma, w.domain, w.L, w.p, w.sigma, targets=tg)
+    assert G.rel_l2(u64[tg], v64[tg], ur, vr) <= TOL64

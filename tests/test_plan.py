@@ -61,13 +61,13 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
         tc = sorted(int(r[2]) for r in ranges.get(6, []) if r[1] == i)
         # every level has a SIMT launch; the levels with >= 128 parent cells per
         # row (mixed path, p <= 24) also get the tensor-core launch, one CTA per
-        # (class, parent row, 512-cell segment), which takes the dense units
+        # (class, parent row, 128-cell segment), which takes the dense units
         assert simt == list(range(2, L + 1))
         assert tc == ([l for l in range(8, L + 1)] if precision == 1 and p <= 24 else [])
         for r in ranges.get(6, []):
             if r[1] == i:
                 w = 2 ** (int(r[2]) - 1)
-                assert r[3] == 4 * w * (w // min(w, 512))
+                assert r[3] == 4 * w * (w // min(w, 128))
         # the other levels of the mixed path (p <= 24) get the tiled SIMT
         # launch, one CTA per (class, 128 target boxes: a 128-cell segment of
         # a parent row, or several whole rows where rows are shorter)
