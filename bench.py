@@ -57,6 +57,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (the slowest replica's time); x itself
+    without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, ws, seconds):
+    """Whole-job rate: every replica processed units_per_rank per step."""
+    return units_per_rank * steps * ws / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -353,13 +369,10 @@ def main():
         m2l_ms.append(st_["m2l"])
         step_ms.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
     stats = ctx.stats()
     stages = ctx.stage_times()
-    value = w.n * args.steps * ws / elapsed
+    value = job_throughput(w.n, args.steps, ws, elapsed)
 
     # end to end through the C ABI with pinned host buffers (copies inside)
     hx, hy, hg = (torch.from_numpy(a).pin_memory() for a in (w.x, w.y, w.gamma))
@@ -370,11 +383,8 @@ def main():
     for _ in range(args.steps):
         ctx.evaluate_host_ptrs(w.n, hx.data_ptr(), hy.data_ptr(), hg.data_ptr(), hu.data_ptr(), hv.data_ptr())
     e2e_t = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_t], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e = {"value": w.n * args.steps * ws / e2e_t, "unit": "particles/s",
+    e2e_t = max_over_ranks(e2e_t, dist, "cuda")
+    e2e = {"value": job_throughput(w.n, args.steps, ws, e2e_t), "unit": "particles/s",
            "h2d_bytes_per_step": 3 * w.n * 4, "d2h_bytes_per_step": 2 * w.n * 4}
 
     # accuracy gate and the FP64 GPU FMM on the same GPU
