@@ -254,6 +254,7 @@ def batch_leg(_lib, torch, stream, steps=5):
     work model."""
     ws = W.batch(n_inst=512, seed=1, dtype="f32")
     ctx = _lib.Context((0, 0, 1), 2, 8, 0.01, precision="mixed", dtype="f32", stream=stream)
+    ctx.set_option(_lib.PETFMM_OPT_GRAPH, 1)  # one graph launch per batch after the first
     insts = []
     with torch.cuda.stream(stream):
         for w in ws:
@@ -331,6 +332,7 @@ def main():
     torch.cuda.synchronize()
     ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype="f32", stream=stream)
     ctx.set_option(_lib.PETFMM_OPT_TIMING, 1)
+    ctx.set_option(_lib.PETFMM_OPT_GRAPH, 1)  # replay the launch sequence as a CUDA graph
     for _ in range(args.warmup):
         ctx.evaluate(x, y, g, u, v)
     ctx.sync()
@@ -454,6 +456,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": w.n, "levels": w.L, "order": w.p,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                           "launch": "CUDA graph replay of each evaluation (PETFMM_OPT_GRAPH)",
                            "l2": (f"inputs larger than L2 (x, y, gamma {in_mb:.0f} MB; u, v "
                                   f"{out_mb:.0f} MB)" if in_mb > 129 else
                                   f"inputs {in_mb:.0f} MB, outputs {out_mb:.0f} MB: smaller than L2 "

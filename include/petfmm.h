@@ -253,12 +253,18 @@ enum {
                                   on the tensor cores; sparser units use the SIMT kernel */
     PETFMM_OPT_TC_SEG = 8,     /* widest tensor-core M2L unit in parent cells: 128
                                   (default), 256 or 512 */
-    PETFMM_OPT_NEAR_TOL = 9    /* mixed path: relative tolerance of the polynomial that
+    PETFMM_OPT_NEAR_TOL = 9,   /* mixed path: relative tolerance of the polynomial that
                                   evaluates Eq. 8's factor (1 - e^-q)/q, in units of
                                   1e-9 (1 .. 1000000; default 2500 = 2.5e-6, a quarter
                                   of the 1e-5 budget against FP64; 100 = 1e-7 is the
                                   FP32 rounding level).  Applies from the next
                                   evaluation. */
+    PETFMM_OPT_GRAPH = 10      /* 1: run an evaluation's launch sequence as a CUDA graph,
+                                  captured on the first evaluation of a launch shape
+                                  (sizes, tree depths, orders, options; the caller's
+                                  arrays may change) and replayed while it repeats;
+                                  0 (default) plain launches.  Results are identical.
+                                  The context's stream must not be capturing. */
 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
 

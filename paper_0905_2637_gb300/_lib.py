@@ -24,6 +24,7 @@ PETFMM_FP64, PETFMM_MIXED = 0, 1
 PETFMM_F64, PETFMM_F32 = 0, 1
 PETFMM_OPT_TIMING, PETFMM_OPT_SPIN_LIMIT, PETFMM_OPT_P2P_MODE, PETFMM_OPT_POISON = 1, 2, 3, 4
 PETFMM_OPT_M2L_TC, PETFMM_OPT_TC_DENSE, PETFMM_OPT_TC_SEG, PETFMM_OPT_NEAR_TOL = 5, 6, 8, 9
+PETFMM_OPT_GRAPH = 10
 STAGES = ("morton", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "worklist", "p2p")
 
 

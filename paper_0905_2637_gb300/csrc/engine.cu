@@ -130,6 +130,12 @@ struct petfmm_ctx {
     Plan plan;
     bool sorted_in_first = true;
     int p2p_grid = 0;
+    // CUDA-graph replay of the launch sequence (PETFMM_OPT_GRAPH)
+    bool use_graph = false;
+    bool capturing = false;
+    cudaStream_t cap_stream = nullptr;  // captures run here (the legacy stream cannot)
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey = 0, glaunches = 0;
     cudaEvent_t ev[PETFMM_STAGE_COUNT + 1] = {};
     bool ev_recorded = false;
 };
@@ -505,15 +511,54 @@ int upload_plan(petfmm_ctx *c, const Plan &pl) {
     } while (0)
 #define PF_CUDA(expr) PF_TRY(cuda_status(expr))
 
+// FNV-1a over everything a kernel argument of the launch sequence depends on.
+struct KeyHash {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+    template <typename T> void put(const T &v) { add(&v, sizeof(v)); }
+};
+
+uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
+    KeyHash k;
+    if (!pl.tasks.empty()) k.add(pl.tasks.data(), pl.tasks.size() * sizeof(Task));
+    auto range = [&](const TaskRange &r) { k.put(r.first); k.put(r.count); k.put(r.nblocks); };
+    for (const TaskRange *r : {&pl.morton, &pl.start, &pl.particles, &pl.leaves_p2m, &pl.leaves_wl,
+                               &pl.m2l, &pl.m2l_tc, &pl.m2l_tile})
+        range(*r);
+    for (const TaskRange &r : pl.m2m) range(r);
+    for (const TaskRange &r : pl.l2l) range(r);
+    k.put(pl.m2m.size()); k.put(pl.l2l.size());
+    k.put(pl.N); k.put(pl.nleaves); k.put(pl.nstart); k.put(pl.ncoef); k.put(pl.items_cap);
+    k.put(pl.nbits); k.put(pl.pmax); k.put(pl.tile_pmax); k.put(pl.deg); k.put(pl.general);
+    k.put(pl.tc_smem); k.put(grid);
+    k.put(c->precision); k.put(c->dtype); k.put(c->timing); k.put(c->p2p_mode); k.put(c->poison);
+    k.put(c->tc_dense_pct); k.put(c->spin_limit);
+    for (const DevBuf *b : {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
+                            &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
+                            &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount,
+                            &c->recu, &c->occ, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB,
+                            &c->ihist})
+        k.put(b->p);
+    return k.h;
+}
+
 void stage_mark(petfmm_ctx *c, int stage) {
-    if (c->timing) cudaEventRecord(c->ev[stage], c->stream);
+    if (!c->timing) return;
+    // inside a capture the record must become an event node of the graph
+    if (c->capturing)
+        cudaEventRecordWithFlags(c->ev[stage], c->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(c->ev[stage], c->stream);
 }
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     Plan &pl = c->plan;
     PF_TRY(build_plan(c->precision, c->m2l_tc, c->tc_segmax, c->near_tol, probs, pl));
     PF_TRY(attach_tables(c, pl));
-    cudaStream_t st = c->stream;
+    cudaStream_t st = c->stream;  // the launch sequence's stream (a capture swaps it)
     const bool mixed = c->precision == PETFMM_MIXED;
     const int64_t N = pl.N;
     // buffers
@@ -590,6 +635,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     const int f32 = c->dtype == PETFMM_F32;
     uint64_t *lc = &c->launches;
 
+    // the launch sequence (the only part of an evaluation a graph replays)
+    auto launch_all = [&]() -> int {
     if (c->poison) {
         const size_t es = mixed ? sizeof(float2) : sizeof(double2);
         PF_CUDA(cudaMemsetAsync(c->me.p, 0xff, size_t(pl.ncoef) * es, st));
@@ -709,6 +756,58 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                                static_cast<const double *>(c->gs.p), perm,
                                static_cast<const double2 *>(c->le.p), f32, busy, st, lc));
     stage_mark(c, PETFMM_STAGE_COUNT);
+    return PETFMM_OK;
+    };
+
+    if (!c->use_graph) {
+        PF_TRY(launch_all());
+    } else {
+        // Every kernel argument is a function of the launch shape, the
+        // library's buffers and the options (the plan itself, including the
+        // caller's arrays, is read from device memory): replay the captured
+        // graph while they are unchanged, capture a new one otherwise.
+        const uint64_t key = graph_key(c, pl, grid);
+        if (!(c->gexec && c->gkey == key)) {
+            if (c->gexec) {
+                cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+            }
+            if (!c->cap_stream &&
+                cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                c->cap_stream = nullptr;
+                return PETFMM_ECUDA;
+            }
+            const cudaStream_t user = c->stream;
+            PF_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            c->stream = st = c->cap_stream;
+            c->capturing = true;
+            const uint64_t l0 = c->launches;
+            const int rc = launch_all();
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+            c->capturing = false;
+            c->stream = st = user;
+            if (rc != PETFMM_OK || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                c->launches = l0;
+                return rc != PETFMM_OK ? rc : PETFMM_ECUDA;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                cudaGetLastError();
+                c->gexec = nullptr;
+                c->launches = l0;
+                return PETFMM_ECUDA;
+            }
+            c->gkey = key;
+            c->glaunches = c->launches - l0;
+            c->launches = l0;
+        }
+        PF_CUDA(cudaGraphLaunch(c->gexec, st));
+        c->launches += c->glaunches;
+    }
     c->ev_recorded = c->timing;
     c->evaluations++;
     return PETFMM_OK;
@@ -790,6 +889,8 @@ int petfmm_destroy(petfmm_ctx *c) {
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto &kv : c->tables) free_op_tables(&kv.second);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->upload_done) cudaEventDestroy(c->upload_done);
     for (auto &e : c->ev)
@@ -945,6 +1046,7 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
             if (value != 128 && value != 256 && value != 512) return PETFMM_EINVAL;
             c->tc_segmax = int(value);
             return PETFMM_OK;
+        case PETFMM_OPT_GRAPH: c->use_graph = value != 0; return PETFMM_OK;
         case PETFMM_OPT_NEAR_TOL:
             if (value < 1 || value > 1000000) return PETFMM_EINVAL;
             c->near_tol = double(value) * 1e-9;

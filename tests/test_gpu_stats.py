@@ -106,3 +106,37 @@ def test_p2p_dispatch_order_does_not_change_results():
             ctx.close()
         assert np.all(np.isfinite(outs[0][0])) and np.all(np.isfinite(outs[0][1]))
         assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_graph_replay_matches_plain_launches():
+    # PETFMM_OPT_GRAPH: the launch sequence is captured once per launch shape
+    # and replayed; new caller arrays of the same shape reuse the graph (the
+    # plan is read from device memory), a new size captures again.  Results
+    # are bitwise those of plain launches.
+    _lib = G.lib()
+    torch = G.torch_cuda()
+    w1 = W.tiny(50_000, 31, L=6, p=12, clustered_frac=0.5, dtype="f32")
+    w2 = W.tiny(50_000, 32, L=6, p=12, clustered_frac=0.5, dtype="f32")
+    w3 = W.tiny(20_000, 33, L=6, p=12, clustered_frac=0.5, dtype="f32")
+    ref = {}
+    plain = _lib.Context(w1.domain, w1.L, w1.p, w1.sigma, precision="mixed", dtype="f32")
+    for w in (w1, w2, w3):
+        x, y, g = G.to_dev((w.x, w.y, w.gamma))
+        u, v = plain.evaluate(x, y, g)
+        assert plain.sync() == 0
+        ref[w.name + str(w.n) + str(w.x[0])] = (u.cpu().numpy(), v.cpu().numpy())
+    plain.close()
+    ctx = _lib.Context(w1.domain, w1.L, w1.p, w1.sigma, precision="mixed", dtype="f32")
+    ctx.set_option(_lib.PETFMM_OPT_GRAPH, 1)
+    ctx.set_option(_lib.PETFMM_OPT_TIMING, 1)
+    for w in (w1, w1, w2, w3, w1):
+        x, y, g = G.to_dev((w.x, w.y, w.gamma))
+        u, v = ctx.evaluate(x, y, g)
+        assert ctx.sync() == 0
+        ur, vr = ref[w.name + str(w.n) + str(w.x[0])]
+        assert np.array_equal(u.cpu().numpy(), ur) and np.array_equal(v.cpu().numpy(), vr)
+        st = ctx.stage_times()
+        assert st["p2p"] > 0 and all(t >= 0 for t in st.values())
+    assert ctx.stats()["kernel_launches"] > 0
+    ctx.close()
+    torch.cuda.synchronize()
