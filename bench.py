@@ -37,9 +37,9 @@ METRIC = "particles/s per FMM eval, N=16M p=17, mixed vs FP64 at rel-L2≤1e-5; 
 WORKLOAD = ("clustered-16M: N=16777216 Gaussian blobs from 8 isotropic clusters "
             "(centres U(0.2,0.8)^2, std 0.02), gamma~N(0,1)/N, sigma=0.002, L=10, p=17, "
             "fp32 storage, mixed precision")
-P2P_OPS_PER_PAIR = 14       # FP32 operations of one pair of Eq. 8/9, written out
+P2P_OPS_PER_PAIR = 14       # FP32 operations of one pair interaction of Eq. 8/9, written out
 SMS, FP32_LANES = 152, 128  # GB300: SMs, FP32 lanes per SM
-PROFILE = os.path.join(ROOT, "profiles", "p2p_clustered16M.md")
+PROFILE = os.path.join(ROOT, "profiles", "p2p_pairs_clustered16M.md")
 
 
 def _peaks():
@@ -123,16 +123,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _p2p_traffic():
-    """DRAM bytes per P2P launch from the committed ncu summary, or None if
-    the kernel source changed since it was taken."""
+def _p2p_traffic(kernel):
+    """DRAM bytes per launch of the near-field kernel from the committed ncu
+    summary, or None if it covers another kernel or the kernel source changed
+    since it was taken."""
     try:
         text = open(PROFILE).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     h = re.search(r"p2p_source_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h:
+    k = re.search(r"kernel:\s*(\w+)", text)
+    if not m or not h or not k or k.group(1) != kernel:
         return None
     src = open(os.path.join(ROOT, "paper_0905_2637_gb300", "csrc", "p2p.cu"), "rb").read()
     if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
@@ -358,7 +360,7 @@ def main():
     # launch, on the stream it launches on, one step at a time
     # (and the whole evaluation's duration, one step at a time, for its
     # median and p99)
-    p2p_ms, m2l_ms, step_ms = [], [], []
+    p2p_ms, pairs_ms, m2l_ms, step_ms = [], [], [], []
     for _ in range(args.steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -368,6 +370,7 @@ def main():
         ctx.sync()
         st_ = ctx.stage_times()
         p2p_ms.append(st_["p2p"])
+        pairs_ms.append(st_["pairs"])
         m2l_ms.append(st_["m2l"])
         step_ms.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
@@ -413,17 +416,31 @@ def main():
 
     peaks, peak_kind = _peaks()
     pipes = _lib.petfmm_measure_peaks()
-    pairs = stats["p2p_pairs"]
+    pairs, sym = stats["p2p_pairs"], stats["p2p_sym_pairs"]
     p2p_t = statistics.mean(p2p_ms) / 1e3
-    achieved = pairs * P2P_OPS_PER_PAIR / p2p_t / 1e12
+    pairs_t = statistics.mean(pairs_ms) / 1e3
     peak = SMS * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "k_p2p_mixed (P2P + L2P)", "achieved": achieved,
+    peak_note = (f"peak = {SMS} SMs x {FP32_LANES} FP32 lanes x "
+                 f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_kind} max SM clock), one op "
+                 "per lane per cycle")
+    if sym > 0 and pairs_t >= p2p_t:
+        # the pair kernel dominates: one interaction per unordered blob pair,
+        # its kernel value serving both blobs
+        kernel = "k_p2p_pairs"
+        achieved = sym * P2P_OPS_PER_PAIR / pairs_t / 1e12
+        note = (f"{P2P_OPS_PER_PAIR} FP32 ops per pair interaction (one unordered blob pair, "
+                f"both blobs served) x {sym} pairs / mean pair-kernel launch "
+                f"{1e3 * pairs_t:.3f} ms (CUDA events on the launching stream); {peak_note}. "
+                f"The directed kernel + final pass take {1e3 * p2p_t:.3f} ms more")
+    else:
+        kernel = "k_p2p_mixed"
+        achieved = pairs * P2P_OPS_PER_PAIR / p2p_t / 1e12
+        note = (f"{P2P_OPS_PER_PAIR} FP32 ops per ordered pair x {pairs} pairs / mean P2P "
+                f"stage {1e3 * p2p_t:.3f} ms (CUDA events on the launching stream); {peak_note}")
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": _p2p_traffic(),
-                "note": (f"{P2P_OPS_PER_PAIR} FP32 ops per ordered pair x {pairs} pairs / mean P2P "
-                         f"launch {1e3 * p2p_t:.3f} ms (CUDA events on the launching stream); peak = "
-                         f"{SMS} SMs x {FP32_LANES} FP32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} "
-                         f"MHz ({peak_kind} max SM clock), one op per lane per cycle"),
+                "traffic": _p2p_traffic(kernel), "note": note,
+                "ordered_pairs_per_s": pairs / (pairs_t + p2p_t),
                 "peak_measured": pipes["fp32_ops"] / 1e12,
                 "frac_of_measured": achieved / (pipes["fp32_ops"] / 1e12)}
     # M2L (tensor-core units + SIMT remainder, the whole stage) against the
@@ -463,7 +480,8 @@ def main():
                                   "(profiling case, not a bench line)")},
                 "rel_l2_vs_fp64": rel, "fp64_gpu": fp64,
                 "stages_ms": stages, "p2p_pairs": pairs, "m2l_pairs": stats["m2l_pairs"],
-                "p2p_load_balance": stats["p2p_load_balance"],
+                "p2p_sym_pairs": sym, "p2p_load_balance": stats["p2p_load_balance"],
+                "pairs_load_balance": stats["pairs_load_balance"],
                 "gpu_launches": launches, "roofline": roofline, "m2l_roofline": m2l,
                 "pipes_measured": pipes_out, "step_ms": step_dist, "clocks": clocks, "e2e": e2e,
                 "gpu": torch.cuda.get_device_name()}

@@ -259,20 +259,31 @@ enum {
                                   of the 1e-5 budget against FP64; 100 = 1e-7 is the
                                   FP32 rounding level).  Applies from the next
                                   evaluation. */
-    PETFMM_OPT_GRAPH = 10      /* 1: run an evaluation's launch sequence as a CUDA graph,
+    PETFMM_OPT_GRAPH = 10,     /* 1: run an evaluation's launch sequence as a CUDA graph,
                                   captured on the first evaluation of a launch shape
                                   (sizes, tree depths, orders, options; the caller's
                                   arrays may change) and replayed while it repeats;
                                   0 (default) plain launches.  Results are identical.
                                   The context's stream must not be capturing. */
+    PETFMM_OPT_P2P_PAIRS = 11  /* mixed path: 1 (default) each pair of neighbouring leaves
+                                  that both hold >= 32 blobs is evaluated once, its
+                                  kernel values serving both sides (K of Eq. 8 is odd);
+                                  heavy pairs are cut into pieces for load balance.
+                                  0: every leaf sums its 9 leaves directly.  Both
+                                  deterministic; they differ by FP32 rounding of the
+                                  sums.  Extra device memory in mode 1: 80 bytes per
+                                  blob and 24 per leaf. */
 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
 
-/* Stages reported by petfmm_stage_times (milliseconds, last evaluation). */
+/* Stages reported by petfmm_stage_times (milliseconds, last evaluation).
+ * PAIRS: the pairwise near-field kernel (mixed path, PETFMM_OPT_P2P_PAIRS = 1;
+ * about zero otherwise); P2P: the directed near field and the final pass
+ * (far field, sums, output). */
 enum {
     PETFMM_STAGE_MORTON = 0, PETFMM_STAGE_SORT, PETFMM_STAGE_GATHER, PETFMM_STAGE_P2M,
     PETFMM_STAGE_M2M, PETFMM_STAGE_M2L, PETFMM_STAGE_L2L, PETFMM_STAGE_WORKLIST,
-    PETFMM_STAGE_P2P, PETFMM_STAGE_COUNT
+    PETFMM_STAGE_PAIRS, PETFMM_STAGE_P2P, PETFMM_STAGE_COUNT
 };
 int petfmm_stage_times(petfmm_ctx *ctx, float *ms, int cap);
 
@@ -283,8 +294,14 @@ typedef struct {
     int64_t m2l_pairs;         /* (target, source) M2L translations of the last evaluation */
     int64_t p2p_items;         /* P2P work items of the last evaluation */
     float p2p_load_balance;    /* min / max CTA busy time of the last P2P (Eq. 20) */
+    int64_t p2p_pair_items;    /* pairwise mode: (leaf pair, piece) items of the last evaluation */
+    int64_t p2p_split_entries; /* pairwise mode: scratch entries the split pairs wanted (pairs
+                                  are split only when these fit in one entry per blob) */
+    int64_t p2p_sym_pairs;     /* pairwise mode: unordered blob pairs the pair kernel
+                                  evaluated (each serves two of the ordered p2p_pairs) */
+    float pairs_load_balance;  /* pairwise mode: min / max CTA busy time of the pair kernel */
 } petfmm_stats;
-/* Counters; p2p_pairs, m2l_pairs, p2p_items and p2p_load_balance need
+/* Counters; p2p_pairs, m2l_pairs, p2p_items and the load balances need
  * PETFMM_OPT_TIMING and a petfmm_sync() after the evaluation. */
 int petfmm_get_stats(petfmm_ctx *ctx, petfmm_stats *out);
 

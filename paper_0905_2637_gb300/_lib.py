@@ -24,8 +24,8 @@ PETFMM_FP64, PETFMM_MIXED = 0, 1
 PETFMM_F64, PETFMM_F32 = 0, 1
 PETFMM_OPT_TIMING, PETFMM_OPT_SPIN_LIMIT, PETFMM_OPT_P2P_MODE, PETFMM_OPT_POISON = 1, 2, 3, 4
 PETFMM_OPT_M2L_TC, PETFMM_OPT_TC_DENSE, PETFMM_OPT_TC_SEG, PETFMM_OPT_NEAR_TOL = 5, 6, 8, 9
-PETFMM_OPT_GRAPH = 10
-STAGES = ("morton", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "worklist", "p2p")
+PETFMM_OPT_GRAPH, PETFMM_OPT_P2P_PAIRS = 10, 11
+STAGES = ("morton", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "worklist", "pairs", "p2p")
 
 
 class Domain(ctypes.Structure):
@@ -55,7 +55,9 @@ class Result(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("evaluations", ctypes.c_uint64),
                 ("p2p_pairs", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64),
-                ("p2p_items", ctypes.c_int64), ("p2p_load_balance", ctypes.c_float)]
+                ("p2p_items", ctypes.c_int64), ("p2p_load_balance", ctypes.c_float),
+                ("p2p_pair_items", ctypes.c_int64), ("p2p_split_entries", ctypes.c_int64),
+                ("p2p_sym_pairs", ctypes.c_int64), ("pairs_load_balance", ctypes.c_float)]
 
 
 class PetfmmError(RuntimeError):

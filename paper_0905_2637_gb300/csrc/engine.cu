@@ -104,6 +104,7 @@ struct petfmm_ctx {
     int device = 0;
     bool timing = false;
     int p2p_mode = 0;  // 0: work items heaviest first (Eq. 14 weights), 1: Morton order
+    bool p2p_pairs = true;  // mixed path: neighbouring leaves pairwise (PETFMM_OPT_P2P_PAIRS)
     bool poison = false;
     bool m2l_tc = true;
     // measured on GB300 (clustered 16M and lattice 1M blobs): 128-cell units
@@ -115,7 +116,8 @@ struct petfmm_ctx {
     uint64_t launches = 0, evaluations = 0;
 
     DevBuf keysA, keysB, valsA, valsB, hist, scratch, start, xs, ys, gs, rec, me, le, cnt, off,
-        items, ctrl, plan_dev, busy, ucount, recu, occ, items_u, ikA, ikB, ivA, ivB, ihist;
+        items, ctrl, plan_dev, busy, ucount, recu, occ, items_u, ikA, ikB, ivA, ivB, ihist, own,
+        part, pitems, pxtra, pxs;
     DevBuf hx, hy, hg, hu, hv;  // device staging for petfmm_evaluate_host
     std::map<int, OpTables> tables;
 
@@ -129,7 +131,7 @@ struct petfmm_ctx {
     // last evaluation (for inspection)
     Plan plan;
     bool sorted_in_first = true;
-    int p2p_grid = 0;
+    int p2p_grid = 0, pairs_grid = 0;  // CTAs of the persistent near-field launches
     // CUDA-graph replay of the launch sequence (PETFMM_OPT_GRAPH)
     bool use_graph = false;
     bool capturing = false;
@@ -535,12 +537,12 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     k.put(pl.nbits); k.put(pl.pmax); k.put(pl.tile_pmax); k.put(pl.deg); k.put(pl.general);
     k.put(pl.tc_smem); k.put(grid);
     k.put(c->precision); k.put(c->dtype); k.put(c->timing); k.put(c->p2p_mode); k.put(c->poison);
-    k.put(c->tc_dense_pct); k.put(c->spin_limit);
+    k.put(c->tc_dense_pct); k.put(c->spin_limit); k.put(c->p2p_pairs);
     for (const DevBuf *b : {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                             &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
                             &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount,
                             &c->recu, &c->occ, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB,
-                            &c->ihist})
+                            &c->ihist, &c->own, &c->part, &c->pitems, &c->pxtra, &c->pxs})
         k.put(b->p);
     return k.h;
 }
@@ -576,8 +578,14 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->valsB, N * 4, st));
     const int64_t rb = radix_blocks(N);
     PF_TRY(ensure(c->hist, size_t(256) * rb * 4, st));
+    // pairwise near field (mixed path): at most 4 forward neighbours per leaf,
+    // a pair cut into at most ceil(na / 128) pieces
+    const bool pairs = mixed && c->p2p_pairs;
+    const int64_t pair_cap =
+        pairs ? 4 * (std::min<int64_t>(pl.nleaves, N) + N / 128) + 1 : 0;
+    const int64_t order_cap = std::max<int64_t>(pl.items_cap, pair_cap);
     const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(256 * rb, pl.nleaves),
-                                             256 * radix_blocks(pl.items_cap));
+                                             256 * radix_blocks(order_cap));
     PF_TRY(ensure(c->scratch, size_t(scan_scratch_words(scan_n)) * 4, st));
     PF_TRY(ensure(c->start, size_t(pl.nstart) * 4, st));
     if (mixed) {
@@ -598,15 +606,33 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
     PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks + pl.m2l_tile.nblocks) * sizeof(uint32_t),
                   st));
-    P2POrder order{};
+    if (mixed) PF_TRY(ensure(c->own, size_t(N) * sizeof(float2), st));
+    if (pairs) {
+        PF_TRY(ensure(c->part, size_t(8) * N * sizeof(float2), st));
+        PF_TRY(ensure(c->pitems, size_t(pair_cap) * sizeof(uint4), st));
+        PF_TRY(ensure(c->pxtra, size_t(6) * pl.nleaves * sizeof(uint32_t), st));
+        PF_TRY(ensure(c->pxs, size_t(N) * sizeof(float2), st));
+    }
+    PairBufs pb{};
+    if (mixed) pb.own = static_cast<float2 *>(c->own.p);
+    if (pairs) {
+        pb.part = static_cast<float2 *>(c->part.p);
+        pb.nslot = N;
+        pb.xcnt = static_cast<uint32_t *>(c->pxtra.p);
+        pb.xoff = pb.xcnt + pl.nleaves;
+        pb.xtab = pb.xoff + pl.nleaves;
+        pb.xs = static_cast<float2 *>(c->pxs.p);
+        pb.xcap = N;  // scratch of split pairs; more wanted: no pair is split
+    }
+    P2POrder order{}, porder{};
     if (c->p2p_mode == 0) {
-        const size_t cap = size_t(pl.items_cap);
+        const size_t cap = size_t(order_cap);
         PF_TRY(ensure(c->items_u, cap * sizeof(uint4), st));
         PF_TRY(ensure(c->ikA, cap * 4, st));
         PF_TRY(ensure(c->ikB, cap * 4, st));
         PF_TRY(ensure(c->ivA, cap * 4, st));
         PF_TRY(ensure(c->ivB, cap * 4, st));
-        PF_TRY(ensure(c->ihist, size_t(256) * radix_blocks(pl.items_cap) * 4, st));
+        PF_TRY(ensure(c->ihist, size_t(256) * radix_blocks(order_cap) * 4, st));
         order.cap = pl.items_cap;
         order.items_unsorted = static_cast<uint4 *>(c->items_u.p);
         order.kA = static_cast<uint32_t *>(c->ikA.p);
@@ -614,14 +640,21 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         order.vA = static_cast<uint32_t *>(c->ivA.p);
         order.vB = static_cast<uint32_t *>(c->ivB.p);
         order.hist = static_cast<uint32_t *>(c->ihist.p);
+        porder = order;
+        porder.cap = pair_cap;
     }
     const int grid = p2p_grid(mixed, pl.deg, pl.general);
     if (grid <= 0) return PETFMM_EINVAL;
+    const int pgrid = pairs ? p2p_pairs_grid(pl.deg, pl.general) : 0;
+    if (pairs && pgrid <= 0) return PETFMM_EINVAL;
+    // busy times: the directed kernel's CTAs, then the pair kernel's
     c->p2p_grid = grid;
-    unsigned long long *busy = nullptr;
+    c->pairs_grid = pgrid;
+    unsigned long long *busy = nullptr, *pbusy = nullptr;
     if (c->timing) {
-        PF_TRY(ensure(c->busy, size_t(grid) * 8 * 2 * sizeof(unsigned long long), st));
+        PF_TRY(ensure(c->busy, size_t(grid + pgrid) * 8 * 2 * sizeof(unsigned long long), st));
         busy = static_cast<unsigned long long *>(c->busy.p);
+        if (pairs) pbusy = busy + size_t(grid) * 8 * 2;
     }
 
     const InstDesc *dinst = static_cast<const InstDesc *>(c->plan_dev.p);
@@ -744,12 +777,31 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                                 static_cast<uint32_t *>(c->off.p), scratch,
                                 static_cast<uint4 *>(c->items.p), ctrl,
                                 c->p2p_mode == 0 ? &order : nullptr, st, lc));
+    if (pairs)
+        PF_CUDA(launch_pair_worklist(dtask + pl.leaves_wl.first, pl.leaves_wl.count,
+                                     pl.leaves_wl.nblocks, dinst, start, pl.nleaves,
+                                     static_cast<uint32_t *>(c->cnt.p),
+                                     static_cast<uint32_t *>(c->off.p), scratch,
+                                     static_cast<uint4 *>(c->pitems.p), ctrl,
+                                     c->p2p_mode == 0 ? &porder : nullptr, pb, st, lc));
+    stage_mark(c, PETFMM_STAGE_PAIRS);
+    // pairwise mode: the neighbouring leaves pairwise
+    if (pairs)
+        PF_CUDA(launch_p2p_pairs(pgrid, pl.deg, pl.general, static_cast<const uint4 *>(c->pitems.p),
+                                 ctrl, dinst, start, static_cast<const float4 *>(c->rec.p), pb,
+                                 pbusy, st, lc));
     stage_mark(c, PETFMM_STAGE_P2P);
-    if (mixed)
+    if (mixed) {
+        // near sums of the own leaf and the directed neighbours, then far
+        // field and the sum
         PF_CUDA(launch_p2p_mixed(grid, pl.deg, pl.general, static_cast<const uint4 *>(c->items.p),
-                                 ctrl, dinst, start, static_cast<const float4 *>(c->rec.p),
-                                 static_cast<const float2 *>(c->le.p), f32, busy, st, lc));
-    else
+                                 ctrl, dinst, start, static_cast<const float4 *>(c->rec.p), pb.own,
+                                 pairs, busy, st, lc));
+        PF_CUDA(launch_p2p_final(dtask + pl.particles.first, pl.particles.count,
+                                 pl.particles.nblocks, dinst, start, skeys,
+                                 static_cast<const float4 *>(c->rec.p),
+                                 static_cast<const float2 *>(c->le.p), pb, f32, st, lc));
+    } else
         PF_CUDA(launch_p2p_f64(grid, static_cast<const uint4 *>(c->items.p), ctrl, dinst, start,
                                static_cast<const double *>(c->xs.p),
                                static_cast<const double *>(c->ys.p),
@@ -884,7 +936,7 @@ int petfmm_destroy(petfmm_ctx *c) {
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                       &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
-                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->recu, &c->occ, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB, &c->ihist, &c->hx, &c->hy,
+                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->recu, &c->occ, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB, &c->ihist, &c->own, &c->part, &c->pitems, &c->pxtra, &c->pxs, &c->hx, &c->hy,
                       &c->hg, &c->hu, &c->hv};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
@@ -1047,6 +1099,7 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
             c->tc_segmax = int(value);
             return PETFMM_OK;
         case PETFMM_OPT_GRAPH: c->use_graph = value != 0; return PETFMM_OK;
+        case PETFMM_OPT_P2P_PAIRS: c->p2p_pairs = value != 0; return PETFMM_OK;
         case PETFMM_OPT_NEAR_TOL:
             if (value < 1 || value > 1000000) return PETFMM_EINVAL;
             c->near_tol = double(value) * 1e-9;
@@ -1084,26 +1137,39 @@ int petfmm_get_stats(petfmm_ctx *c, petfmm_stats *out) {
         unsigned long long pairs;
         std::memcpy(&pairs, w + CTRL_PAIRS_LO, sizeof(pairs));
         out->p2p_pairs = int64_t(pairs);
+        if (c->p2p_pairs && c->precision != PETFMM_FP64) {
+            out->p2p_pair_items = w[CTRL_NPAIRS];
+            out->p2p_split_entries = w[CTRL_NXTRA];
+            unsigned long long sym;
+            std::memcpy(&sym, w + CTRL_SYM_LO, sizeof(sym));
+            out->p2p_sym_pairs = int64_t(sym);
+        }
     }
     if (c->timing && c->busy.p && c->p2p_grid > 0 && c->ev_recorded) {
         const int warps = 8;
-        std::vector<unsigned long long> b(size_t(c->p2p_grid) * warps * 2);
+        const bool pairs = c->p2p_pairs && c->precision != PETFMM_FP64 && c->pairs_grid > 0;
+        const size_t nblk = size_t(c->p2p_grid) + (pairs ? size_t(c->pairs_grid) : 0);
+        std::vector<unsigned long long> b(nblk * warps * 2);
         if (cudaMemcpy(b.data(), c->busy.p, b.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
             return PETFMM_ECUDA;
-        double lo = 0, hi = 0;
-        bool first = true;
-        for (int blk = 0; blk < c->p2p_grid; ++blk) {
-            unsigned long long s = ~0ull, e = 0;
-            for (int w = 0; w < warps; ++w) {
-                s = std::min(s, b[(size_t(blk) * warps + w) * 2]);
-                e = std::max(e, b[(size_t(blk) * warps + w) * 2 + 1]);
+        // Eq. 20 over the CTAs of one persistent launch: min / max busy span
+        auto lb = [&](size_t b0, size_t nb) {
+            double lo = 0, hi = 0;
+            for (size_t blk = b0; blk < b0 + nb; ++blk) {
+                unsigned long long s = ~0ull, e = 0;
+                for (int w = 0; w < warps; ++w) {
+                    s = std::min(s, b[(blk * warps + w) * 2]);
+                    e = std::max(e, b[(blk * warps + w) * 2 + 1]);
+                }
+                const double span = double(e - s);
+                if (blk == b0) lo = hi = span;
+                lo = std::min(lo, span);
+                hi = std::max(hi, span);
             }
-            const double span = double(e - s);
-            if (first) { lo = hi = span; first = false; }
-            lo = std::min(lo, span);
-            hi = std::max(hi, span);
-        }
-        out->p2p_load_balance = hi > 0 ? float(lo / hi) : 1.0f;
+            return hi > 0 ? float(lo / hi) : 1.0f;
+        };
+        out->p2p_load_balance = lb(0, size_t(c->p2p_grid));
+        if (pairs) out->pairs_load_balance = lb(size_t(c->p2p_grid), size_t(c->pairs_grid));
     }
     return PETFMM_OK;
 }

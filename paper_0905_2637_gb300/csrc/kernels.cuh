@@ -27,10 +27,12 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 // Stable LSD radix sort of (key, value) over the low nbits bits; the initial
 // values are the element indices.  Result ends up in (k0, v0) or (k1, v1):
 // *result_in_first tells which.  hist must hold 256 * radix_blocks(n) words.
+// n_live (device, optional): sort only the first min(n, *n_live) elements
+// (the grid stays sized for n; tiles past the live ones return at once).
 int64_t radix_blocks(int64_t n);
 cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n,
                        int nbits, uint32_t *hist, uint32_t *scan_scratch, bool *result_in_first,
-                       cudaStream_t st, uint64_t *launches);
+                       cudaStream_t st, uint64_t *launches, const uint32_t *n_live = nullptr);
 
 // start[soff + b] = first sorted rank of leaf b (b = 0..4^L).
 cudaError_t launch_leaf_start(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
@@ -138,7 +140,7 @@ constexpr int EXP_THREADS = 256;  // (box, coefficient) pairs per block for M2M 
 // Work list: items (inst, leaf, first target rank, target count) for every
 // occupied leaf, tpi targets per item.  ctrl[CTRL_NITEMS] receives the count.
 enum { CTRL_STATUS = 0, CTRL_NITEMS = 1, CTRL_QUEUE = 2, CTRL_PAIRS_LO = 4, CTRL_NOCC = 6,
-       CTRL_WORDS = 16 };
+       CTRL_NPAIRS = 7, CTRL_QUEUE2 = 8, CTRL_NXTRA = 9, CTRL_SYM_LO = 10, CTRL_WORDS = 16 };
 // Buffers for dispatching the items heaviest first (order != nullptr): the
 // items are emitted to items_unsorted, sorted by work class (one stable radix
 // pass over cap entries) and permuted into the item array.
@@ -157,10 +159,49 @@ cudaError_t launch_p2p_f64(int grid, const uint4 *items, uint32_t *ctrl, const I
                            const double *gs, const uint32_t *perm, const double2 *le,
                            int dtype_f32, unsigned long long *busy, cudaStream_t st,
                            uint64_t *launches);
+// Mixed near field, every leaf against all 9 leaves (pairs: not the
+// neighbours the pair kernel covers): own[r] = the near sum of sorted blob r
+// (launch_p2p_final then adds the far field).
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
                              const InstDesc *insts, const uint32_t *start, const float4 *rec,
-                             const float2 *le, int dtype_f32, unsigned long long *busy,
-                             cudaStream_t st, uint64_t *launches);
+                             float2 *own, int pairs, unsigned long long *busy, cudaStream_t st,
+                             uint64_t *launches);
+// Pairwise near field between neighbouring leaves (mixed path).  Buffers:
+// own[N]: each blob's directly summed part (sorted order; the only one used
+// by the directed mode, part == nullptr there); part: 8 slots of
+// nslot float2 (slot d: A's blobs from forward neighbour d, slot 4 + d: B's
+// blobs from A); xcnt, xoff: per leaf, the scratch entries of its split pairs
+// and their exclusive scan; xtab[4 nleaves]: per (leaf, direction) of a split
+// pair its scratch base (all ones: not split); xs[xcap]: the scratch runs of
+// pieces 1 .. of split pairs.
+struct PairBufs {
+    float2 *own, *part;
+    int64_t nslot;
+    uint32_t *xcnt, *xoff, *xtab;
+    float2 *xs;
+    int64_t xcap;
+};
+// ... the item list (inst, leaf A, direction | piece << 2, scratch base),
+// ctrl[CTRL_NPAIRS] its count, ctrl[CTRL_NXTRA] the scratch entries wanted ...
+cudaError_t launch_pair_worklist(const Task *tasks, int ntasks, int64_t nblocks,
+                                 const InstDesc *insts, const uint32_t *start, int64_t nleaves,
+                                 uint32_t *cnt, uint32_t *off, uint32_t *scan_scratch,
+                                 uint4 *items, uint32_t *ctrl, const P2POrder *order,
+                                 const PairBufs &pb, cudaStream_t st, uint64_t *launches);
+// ... the pair items, one persistent launch (the directed items follow in
+// launch_p2p_mixed with pairs = 1) ...
+int p2p_pairs_grid(int deg, int general);
+cudaError_t launch_p2p_pairs(int grid, int deg, int general, const uint4 *pitems, uint32_t *ctrl,
+                             const InstDesc *insts, const uint32_t *start, const float4 *rec,
+                             const PairBufs &pb, unsigned long long *busy, cudaStream_t st,
+                             uint64_t *launches);
+// Either mode's final pass: far field (L2P) + own + pair slots per blob,
+// written at the caller's index (tasks over blobs).
+cudaError_t launch_p2p_final(const Task *tasks, int ntasks, int64_t nblocks,
+                                const InstDesc *insts, const uint32_t *start,
+                                const uint32_t *skeys, const float4 *rec, const float2 *le,
+                                const PairBufs &pb, int dtype_f32, cudaStream_t st,
+                                uint64_t *launches);
 int p2p_grid(int precision_mixed, int deg, int general);
 int device_sm_count();
 constexpr int P2P_TPI_F64 = 32;

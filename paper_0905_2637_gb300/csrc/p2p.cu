@@ -141,18 +141,28 @@ __global__ void __launch_bounds__(256) k_p2p_emit(const Task *__restrict__ tasks
 }
 
 // Invalid tail of the item array (beyond the device-side count) sorts last.
-__global__ void __launch_bounds__(256) k_item_tail(uint32_t *__restrict__ wclass, int64_t cap,
-                                                   const uint32_t *ctrl) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < cap && i >= int64_t(ctrl[CTRL_NITEMS])) wclass[i] = 255u;
-}
-
 __global__ void __launch_bounds__(256) k_item_permute(const uint4 *__restrict__ in,
                                                       const uint32_t *__restrict__ perm,
                                                       uint4 *__restrict__ out, int64_t cap,
-                                                      const uint32_t *ctrl) {
+                                                      const uint32_t *count) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r < cap && r < int64_t(ctrl[CTRL_NITEMS])) out[r] = in[perm[r]];
+    if (r < cap && r < int64_t(*count)) out[r] = in[perm[r]];
+}
+
+// heaviest items first: one stable 8-bit radix pass over the work classes in
+// order->kA, then the items permuted from order->items_unsorted to items
+static cudaError_t order_items(const P2POrder *order, uint4 *items, const uint32_t *count,
+                               uint32_t *scan_scratch, cudaStream_t st, uint64_t *launches) {
+    const int64_t cap = order->cap;
+    const unsigned g = unsigned((cap + 255) / 256);
+    bool in_first = true;
+    cudaError_t e = radix_sort(order->kA, order->vA, order->kB, order->vB, cap, 8, order->hist,
+                               scan_scratch, &in_first, st, launches, count);
+    if (e != cudaSuccess) return e;
+    k_item_permute<<<g, 256, 0, st>>>(order->items_unsorted, in_first ? order->vA : order->vB,
+                                      items, cap, count);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_p2p_worklist(const Task *tasks, int ntasks, int64_t nblocks,
@@ -172,19 +182,9 @@ cudaError_t launch_p2p_worklist(const Task *tasks, int ntasks, int64_t nblocks,
                                                   order ? order->kA : nullptr);
     PF_LAUNCHED(1);
     if ((e = cudaGetLastError()) != cudaSuccess || !order) return e;
-    // heaviest items first: one stable 8-bit radix pass over the work classes
-    const int64_t cap = order->cap;
-    const unsigned g = unsigned((cap + 255) / 256);
-    k_item_tail<<<g, 256, 0, st>>>(order->kA, cap, ctrl);
-    PF_LAUNCHED(1);
-    bool in_first = true;
-    e = radix_sort(order->kA, order->vA, order->kB, order->vB, cap, 8, order->hist, scan_scratch,
-                   &in_first, st, launches);
-    if (e != cudaSuccess) return e;
-    k_item_permute<<<g, 256, 0, st>>>(emit_to, in_first ? order->vA : order->vB, items, cap, ctrl);
-    PF_LAUNCHED(1);
-    return cudaGetLastError();
+    return order_items(order, items, ctrl + CTRL_NITEMS, scan_scratch, st, launches);
 }
+
 
 // ----------------------------------------------------------------------------
 // Mixed-precision P2P + L2P
@@ -210,6 +210,43 @@ __device__ __forceinline__ float g_of(const float (&a)[DEG + 1], float r2, float
     return g;
 }
 
+// Forward neighbours of a leaf in the pairwise near field (see below).
+__constant__ int8_t c_fwd[4][2] = {{1, 0}, {-1, 1}, {0, 1}, {1, 1}};
+
+// A pair of neighbouring leaves is evaluated pairwise when both hold at least
+// a warp's worth of blobs; with fewer, most lanes of the 64 x 32 tile would
+// idle, and the leaves' own warps sum that neighbour directly instead.  Both
+// leaves of a pair decide from the same two counts.
+constexpr uint32_t P2P_PAIR_MIN = 32;
+constexpr uint32_t P2P_PAIR_TPL4 = 96;  // leaves this full use 4 targets per lane
+__host__ __device__ __forceinline__ bool pairwise(uint32_t na, uint32_t nb) {
+    return na >= P2P_PAIR_MIN && nb >= P2P_PAIR_MIN;
+}
+
+// A heavy pair is cut into pieces along A, each piece a run of whole
+// 128-target chunks holding at most P2P_PAIR_CAPU tiles of 128 targets x 32
+// sources, so that no single warp's item outlasts the average share of the
+// launch.  Piece 0 writes B's reaction to the pair's slot, piece i >= 1 to a
+// scratch run of nb entries; the final pass adds them in piece order.
+// Returns the number of pieces; *pc = targets per piece (a multiple of 128).
+constexpr uint64_t P2P_PAIR_CAPU = 256;
+__host__ __device__ __forceinline__ uint32_t pair_pieces(uint32_t na, uint32_t nb, uint32_t *pc) {
+    const uint32_t ca = (na + 127) / 128, cb = (nb + 31) / 32;
+    uint64_t np = (uint64_t(ca) * cb + P2P_PAIR_CAPU - 1) / P2P_PAIR_CAPU;
+    if (np > ca) np = ca;
+    if (np < 1) np = 1;
+    const uint32_t per = uint32_t((ca + np - 1) / np);
+    *pc = per * 128;
+    return (ca + per - 1) / per;
+}
+
+// count of the leaf (x, y), 0 outside the domain
+__device__ __forceinline__ uint32_t leaf_count(const uint32_t *st, int nside, int x, int y) {
+    if (x < 0 || y < 0 || x >= nside || y >= nside) return 0;
+    const uint32_t m = morton_key(uint32_t(x), uint32_t(y));
+    return st[m + 1] - st[m];
+}
+
 // One source against the lane's two targets (a, b), both in the source
 // leaf's frame.
 template <int DEG, bool GENERAL>
@@ -228,11 +265,78 @@ __device__ __forceinline__ void pair2(const float4 s, float xa, float ya, float 
     vb = fmaf(dxb, fb, vb);
 }
 
-template <int DEG, bool GENERAL>
+// One work item of the directed near field: up to 64 targets of a leaf
+// against the leaf and its neighbours (PAIRS: not the neighbours the pair
+// kernel covers); the near sum goes to own[] in sorted order, the final pass
+// adds the far field.  No L2P here: with few targets per item the lanes of
+// all source groups would repeat it.
+template <int DEG, bool GENERAL, bool PAIRS>
+__device__ __forceinline__ void directed_item(const uint4 item, const InstDesc *__restrict__ insts,
+                                              const uint32_t *__restrict__ start,
+                                              const float4 *__restrict__ rec,
+                                              float2 *__restrict__ own, int lane) {
+    const InstDesc &d = insts[item.x];
+    const int L = d.L;
+    float a[DEG + 1];
+#pragma unroll
+    for (int k = 0; k <= DEG; ++k) a[k] = d.poly[k];
+    const float kappa = d.kappa, split = d.qsplit_rho2;
+    const uint32_t m = item.y;
+    const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
+    // lane = (source group grp, target slot k); targets k and k + W
+    const int lw = p2p_group_log2(item.w, 2);
+    const uint32_t W = 1u << lw, S = 32u >> lw;
+    const uint32_t grp = uint32_t(lane) >> lw, k = uint32_t(lane) & (W - 1u);
+    const uint32_t ta = item.z + k, tb = item.z + k + W;
+    const bool has_a = k < item.w, has_b = k + W < item.w;
+    const float4 ra = has_a ? rec[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 rb = has_b ? rec[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float ua = 0.f, va = 0.f, ub = 0.f, vb = 0.f;
+    const uint32_t *st = start + d.soff;
+    const int nside = 1 << L;
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int sy = iy + dy;
+        if (sy < 0 || sy >= nside) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int sx = ix + dx;
+            if (sx < 0 || sx >= nside) continue;
+            const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
+            const uint32_t j0 = st[nm], j1 = st[nm + 1];
+            // pairwise mode: neighbours that the pair kernel covers are skipped
+            if (PAIRS && (dx | dy) && pairwise(st[m + 1] - st[m], j1 - j0)) continue;
+            const float xa = ra.x - float(dx), ya = ra.y - float(dy);
+            const float xb = rb.x - float(dx), yb = rb.y - float(dy);
+            // the stride-1 loop keeps constant load offsets after unrolling
+            if (S == 1) {
+#pragma unroll 4
+                for (uint32_t j = j0; j < j1; ++j)
+                    pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
+                                        va, ub, vb);
+            } else {
+#pragma unroll 4
+                for (uint32_t j = j0 + grp; j < j1; j += S)
+                    pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
+                                        va, ub, vb);
+            }
+        }
+    }
+    // add the partial sums of the source groups (fixed butterfly)
+    for (uint32_t o = W; o < 32u; o <<= 1) {
+        ua += __shfl_xor_sync(0xffffffffu, ua, int(o));
+        va += __shfl_xor_sync(0xffffffffu, va, int(o));
+        ub += __shfl_xor_sync(0xffffffffu, ub, int(o));
+        vb += __shfl_xor_sync(0xffffffffu, vb, int(o));
+    }
+    const float cn = d.cnear;
+    if (has_a && grp == 0) own[ta] = make_float2(cn * ua, cn * va);
+    if (has_b && grp == 0) own[tb] = make_float2(cn * ub, cn * vb);
+}
+
+template <int DEG, bool GENERAL, bool PAIRS>
 __global__ void __launch_bounds__(P2P_THREADS, 5) k_p2p_mixed(
     const uint4 *__restrict__ items, uint32_t *ctrl, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const float4 *__restrict__ rec,
-    const float2 *__restrict__ le, int dtype_f32, unsigned long long *busy) {
+    float2 *__restrict__ own, unsigned long long *busy) {
     const int lane = threadIdx.x & 31;
     const uint32_t nitems = *reinterpret_cast<volatile uint32_t *>(ctrl + CTRL_NITEMS);
     const uint64_t t_begin = busy ? global_ns() : 0;
@@ -241,98 +345,7 @@ __global__ void __launch_bounds__(P2P_THREADS, 5) k_p2p_mixed(
         if (lane == 0) it = atomicAdd(ctrl + CTRL_QUEUE, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= nitems) break;
-        const uint4 item = items[it];
-        const InstDesc &d = insts[item.x];
-        const int L = d.L;
-        float a[DEG + 1];
-#pragma unroll
-        for (int k = 0; k <= DEG; ++k) a[k] = d.poly[k];
-        const float kappa = d.kappa, split = d.qsplit_rho2;
-        const uint32_t m = item.y;
-        const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
-        // lane = (source group grp, target slot k); targets k and k + W
-        const int lw = p2p_group_log2(item.w, 2);
-        const uint32_t W = 1u << lw, S = 32u >> lw;
-        const uint32_t grp = uint32_t(lane) >> lw, k = uint32_t(lane) & (W - 1u);
-        const uint32_t ta = item.z + k, tb = item.z + k + W;
-        const bool has_a = k < item.w, has_b = k + W < item.w;
-        const float4 ra = has_a ? rec[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 rb = has_b ? rec[tb] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float ua = 0.f, va = 0.f, ub = 0.f, vb = 0.f;
-        const uint32_t *st = start + d.soff;
-        const int nside = 1 << L;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int sy = iy + dy;
-            if (sy < 0 || sy >= nside) continue;
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int sx = ix + dx;
-                if (sx < 0 || sx >= nside) continue;
-                const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
-                const uint32_t j0 = st[nm], j1 = st[nm + 1];
-                const float xa = ra.x - float(dx), ya = ra.y - float(dy);
-                const float xb = rb.x - float(dx), yb = rb.y - float(dy);
-                // the stride-1 loop keeps constant load offsets after unrolling
-                if (S == 1) {
-#pragma unroll 4
-                    for (uint32_t j = j0; j < j1; ++j)
-                        pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
-                                            va, ub, vb);
-                } else {
-#pragma unroll 4
-                    for (uint32_t j = j0 + grp; j < j1; j += S)
-                        pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
-                                            va, ub, vb);
-                }
-            }
-        }
-        // add the partial sums of the source groups (fixed butterfly)
-        for (uint32_t o = W; o < 32u; o <<= 1) {
-            ua += __shfl_xor_sync(0xffffffffu, ua, int(o));
-            va += __shfl_xor_sync(0xffffffffu, va, int(o));
-            ub += __shfl_xor_sync(0xffffffffu, ub, int(o));
-            vb += __shfl_xor_sync(0xffffffffu, vb, int(o));
-        }
-        // far field: L2P of the leaf's local expansion, w = (1/r) sum c_m zeta^m
-        float fua = 0.f, fva = 0.f, fub = 0.f, fvb = 0.f;
-        if (L >= 2) {
-            const int p = d.p;
-            const float2 *c = le + d.eoff + (lvl_off(L) + box_index(L, uint32_t(ix), uint32_t(iy))) * p;
-            float2 wa = __ldg(c + p - 1), wb = wa;
-            for (int k = p - 2; k >= 0; --k) {
-                const float2 ck = __ldg(c + k);
-                const float wax = fmaf(wa.x, ra.x, fmaf(-wa.y, ra.y, ck.x));
-                const float way = fmaf(wa.x, ra.y, fmaf(wa.y, ra.x, ck.y));
-                const float wbx = fmaf(wb.x, rb.x, fmaf(-wb.y, rb.y, ck.x));
-                const float wby = fmaf(wb.x, rb.y, fmaf(wb.y, rb.x, ck.y));
-                wa = make_float2(wax, way);
-                wb = make_float2(wbx, wby);
-            }
-            fua = d.cfar * wa.y; fva = d.cfar * wa.x;
-            fub = d.cfar * wb.y; fvb = d.cfar * wb.x;
-        }
-        const float cn = d.cnear;
-        if (has_a && grp == 0) {
-            const int64_t q = int64_t(__float_as_uint(ra.w)) - d.poff;
-            const float uo = fmaf(cn, ua, fua), vo = fmaf(cn, va, fva);
-            if (dtype_f32) {
-                static_cast<float *>(d.u)[q] = uo;
-                static_cast<float *>(d.v)[q] = vo;
-            } else {
-                static_cast<double *>(d.u)[q] = double(uo);
-                static_cast<double *>(d.v)[q] = double(vo);
-            }
-        }
-        if (has_b && grp == 0) {
-            const int64_t q = int64_t(__float_as_uint(rb.w)) - d.poff;
-            const float uo = fmaf(cn, ub, fub), vo = fmaf(cn, vb, fvb);
-            if (dtype_f32) {
-                static_cast<float *>(d.u)[q] = uo;
-                static_cast<float *>(d.v)[q] = vo;
-            } else {
-                static_cast<double *>(d.u)[q] = double(uo);
-                static_cast<double *>(d.v)[q] = double(vo);
-            }
-        }
+        directed_item<DEG, GENERAL, PAIRS>(items[it], insts, start, rec, own, lane);
     }
     if (busy && lane == 0) {
         const uint64_t t_end = global_ns();
@@ -434,26 +447,392 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
 }
 
 // ----------------------------------------------------------------------------
+// Pairwise near field between neighbouring leaves (mixed path).
+//
+// Each unordered pair {A, B} of neighbouring occupied leaves is evaluated
+// once, by the item (A, d) with B = A + off[d] one of A's four forward
+// neighbours.  One warp holds up to 64 targets of A (two per lane) and 32
+// sources of B (one per lane); in 32 steps the sources travel once around
+// the warp (shuffles), and for every (target, source) pair the kernel factor
+// K(x_a - x_s) is computed once and used twice: gamma_s K for the target and
+// -gamma_a K for the source (K is odd, Eq. 8), the latter summed in a register
+// that travels with the source.  The sums go to single-owner slots of the
+// receiving particle: part[d][a] (from the forward neighbour d) and
+// part[4 + d][b] (from the backward neighbour); the 64-target chunks of A
+// add to a source's slot one after another in the same warp.  A final pass
+// adds, per particle, its own leaf's sum and far field and the slots of its
+// occupied neighbours in a fixed order: the result does not depend on which
+// warp ran which item.
+// ----------------------------------------------------------------------------
+
+// cnt[leaf] = forward neighbours of an occupied leaf that hold particles
+__global__ void __launch_bounds__(256) k_pair_count(const Task *__restrict__ tasks, int ntasks,
+                                                    const InstDesc *__restrict__ insts,
+                                                    const uint32_t *__restrict__ start,
+                                                    uint32_t *__restrict__ cnt,
+                                                    uint32_t *__restrict__ xcnt,
+                                                    uint32_t *ctrl) {
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t m = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    unsigned long long sym = 0;
+    if (m < t.count) {
+        const InstDesc &d = insts[t.inst];
+        const uint32_t *st = start + d.soff;
+        uint32_t c = 0, x = 0;
+        const uint32_t na = st[m + 1] - st[m];
+        if (na >= P2P_PAIR_MIN) {
+            const int nside = 1 << d.L;
+            const int ix = int(compact_bits(uint32_t(m))), iy = int(compact_bits(uint32_t(m) >> 1));
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t nb = leaf_count(st, nside, ix + c_fwd[k][0], iy + c_fwd[k][1]);
+                if (!pairwise(na, nb)) continue;
+                uint32_t pc;
+                const uint32_t np = pair_pieces(na, nb, &pc);
+                c += np;
+                x += (np - 1) * nb;
+                sym += (unsigned long long)na * nb;
+            }
+        }
+        cnt[d.loff + m] = c;
+        xcnt[d.loff + m] = x;
+    }
+    // block reduction of the unordered pair count (for the statistics)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sym += __shfl_down_sync(0xffffffffu, sym, o);
+    __shared__ unsigned long long ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sym;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < 8; ++w) s += ws[w];
+        if (s) atomicAdd(reinterpret_cast<unsigned long long *>(ctrl + CTRL_SYM_LO), s);
+    }
+}
+
+// items (inst, leaf A, direction d, 0) and their work class (targets x
+// sources, log2 in quarter steps, stored as 127 - class: heaviest first)
+__global__ void __launch_bounds__(256) k_pair_emit(const Task *__restrict__ tasks, int ntasks,
+                                                   const InstDesc *__restrict__ insts,
+                                                   const uint32_t *__restrict__ start,
+                                                   const uint32_t *__restrict__ off,
+                                                   const uint32_t *__restrict__ xoff,
+                                                   const uint32_t *__restrict__ ctrl,
+                                                   int64_t xcap, uint32_t *__restrict__ xtab,
+                                                   uint4 *__restrict__ items,
+                                                   uint32_t *__restrict__ wclass) {
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t m = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    if (m >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const uint32_t *st = start + d.soff;
+    const uint32_t na = st[m + 1] - st[m];
+    if (na < P2P_PAIR_MIN) return;
+    const int nside = 1 << d.L;
+    const int ix = int(compact_bits(uint32_t(m))), iy = int(compact_bits(uint32_t(m) >> 1));
+    uint32_t o = off[d.loff + m], xb = xoff[d.loff + m];
+    // the pieces' scratch runs exist only if all of them fit; else every pair
+    // is one piece (decided alike for all pairs, so the result does not depend
+    // on which fit)
+    const bool split = int64_t(ctrl[CTRL_NXTRA]) <= xcap;
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t nb = leaf_count(st, nside, ix + c_fwd[k][0], iy + c_fwd[k][1]);
+        if (!pairwise(na, nb)) continue;
+        uint32_t pc;
+        const uint32_t np = pair_pieces(na, nb, &pc);
+        const uint32_t base = split ? xb : 0xffffffffu;
+        if (np > 1) xtab[(d.loff + m) * 4 + k] = base;
+        for (uint32_t i = 0; i < np; ++i) {
+            items[o] = make_uint4(uint32_t(t.inst), uint32_t(m), uint32_t(k) | (i << 2), base);
+            if (wclass) {
+                // a warp spends 32 steps per (64-target chunk, 32-source chunk)
+                const uint32_t nt = split ? min(pc, na - i * pc) : (i ? 0u : na);
+                uint32_t cost = ((nt + 63) / 64) * ((nb + 31) / 32);
+                if (cost < 1) cost = 1;
+                const int e = 31 - __clz(int(cost));
+                const uint32_t frac = e >= 2 ? (cost >> (e - 2)) & 3u : (cost << (2 - e)) & 3u;
+                wclass[o] = 127u - (uint32_t(e) * 4u + frac);
+            }
+            ++o;
+        }
+        xb += (np - 1) * nb;
+    }
+}
+
+// One target (in A's frame) against the travelling source (already in A's
+// frame): the target gains gs K, the source -ga K.
+template <int DEG, bool GENERAL>
+__device__ __forceinline__ void pair_sym(float xa, float ya, float ga, float xs, float ys, float gs,
+                                         const float (&a)[DEG + 1], float kappa, float split,
+                                         float &ua, float &va, float &bu, float &bv) {
+    const float dx = xa - xs, dy = ya - ys;
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float g = g_of<DEG, GENERAL>(a, r2, kappa, split);
+    const float kx = -dy * g, ky = dx * g;
+    ua = fmaf(gs, kx, ua);
+    va = fmaf(gs, ky, va);
+    bu = fmaf(-ga, kx, bu);
+    bv = fmaf(-ga, ky, bv);
+}
+
+// The pairs of blobs abeg .. aend - 1 of leaf A (from a0) with leaf B (nb
+// from b0, centre at (ox, oy) leaves from A's): A in chunks of 32 TPL targets
+// (TPL per lane), B in chunks of 32 sources travelling around the warp.
+// fwd[i]: A's blob i from B; bwd[j]: B's blob j from the A range.
+template <int DEG, bool GENERAL, int TPL>
+__device__ __forceinline__ void pair_leaves(const float4 *__restrict__ rec, uint32_t a0,
+                                            uint32_t abeg, uint32_t aend, uint32_t b0, uint32_t nb,
+                                            int ox, int oy, const float (&a)[DEG + 1],
+                                            float kappa, float split, float cn,
+                                            float2 *__restrict__ fwd, float2 *__restrict__ bwd,
+                                            int lane) {
+    // placeholders of missing targets / sources: far apart (finite kernel
+    // values), zero strength (they add nothing and their sums are dropped)
+    constexpr float kFar = 64.f;
+    const int next = (lane + 1) & 31;
+    for (uint32_t ac = abeg; ac < aend; ac += 32 * TPL) {
+        float tx[TPL], ty[TPL], tg[TPL], u[TPL], v[TPL];
+#pragma unroll
+        for (int t = 0; t < TPL; ++t) {
+            const bool h = ac + lane + 32 * t < aend;
+            const float4 r = h ? rec[a0 + ac + lane + 32 * t] : make_float4(kFar, kFar, 0.f, 0.f);
+            tx[t] = r.x;
+            ty[t] = r.y;
+            tg[t] = r.z;
+            u[t] = v[t] = 0.f;
+        }
+        for (uint32_t bc = 0; bc < nb; bc += 32) {
+            const bool hs = bc + lane < nb;
+            const uint32_t sb = bc + lane;
+            const float4 s = hs ? rec[b0 + sb] : make_float4(-kFar, -kFar, 0.f, 0.f);
+            // the source in A's frame (B's centre is A's plus (ox, oy) leaves)
+            float xs = s.x + float(ox), ys = s.y + float(oy), gs = s.z;
+            float bu = 0.f, bv = 0.f;
+#pragma unroll 2
+            for (int k = 0; k < 32; ++k) {
+#pragma unroll
+                for (int t = 0; t < TPL; ++t)
+                    pair_sym<DEG, GENERAL>(tx[t], ty[t], tg[t], xs, ys, gs, a, kappa, split, u[t],
+                                           v[t], bu, bv);
+                xs = __shfl_sync(0xffffffffu, xs, next);
+                ys = __shfl_sync(0xffffffffu, ys, next);
+                gs = __shfl_sync(0xffffffffu, gs, next);
+                bu = __shfl_sync(0xffffffffu, bu, next);
+                bv = __shfl_sync(0xffffffffu, bv, next);
+            }
+            // after 32 steps every travelling sum is back at its source's lane
+            if (hs) {
+                float2 w = make_float2(cn * bu, cn * bv);
+                if (ac != abeg) {
+                    const float2 o = bwd[sb];
+                    w = make_float2(o.x + w.x, o.y + w.y);
+                }
+                bwd[sb] = w;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+            if (ac + lane + 32 * t < aend)
+                fwd[ac + lane + 32 * t] = make_float2(cn * u[t], cn * v[t]);
+    }
+}
+
+// One item of the pairwise near field: piece item.z >> 2 of leaf A (item.y)
+// with its forward neighbour item.z & 3; item.w = the pair's scratch base
+// (all ones: the pair is not split, piece 0 takes all of it).
+template <int DEG, bool GENERAL>
+__device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__restrict__ insts,
+                                          const uint32_t *__restrict__ start,
+                                          const float4 *__restrict__ rec,
+                                          float2 *__restrict__ part, int64_t nslot,
+                                          float2 *__restrict__ xs, int lane) {
+    const InstDesc &d = insts[item.x];
+    float a[DEG + 1];
+#pragma unroll
+    for (int k = 0; k <= DEG; ++k) a[k] = d.poly[k];
+    const float kappa = d.kappa, split = d.qsplit_rho2, cn = d.cnear;
+    const uint32_t m = item.y;
+    const int dir = int(item.z & 3u);
+    const uint32_t piece = item.z >> 2;
+    const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
+    const int ox = c_fwd[dir][0], oy = c_fwd[dir][1];
+    const uint32_t mb = morton_key(uint32_t(ix + ox), uint32_t(iy + oy));
+    const uint32_t *st = start + d.soff;
+    const uint32_t a0 = st[m], na = st[m + 1] - a0;
+    const uint32_t b0 = st[mb], nb = st[mb + 1] - b0;
+    uint32_t abeg = 0, aend = na;
+    float2 *fwd = part + int64_t(dir) * nslot + a0;      // A's particles, from B
+    float2 *bwd = part + int64_t(4 + dir) * nslot + b0;  // B's particles, from A
+    if (item.w != 0xffffffffu) {
+        uint32_t pc;
+        pair_pieces(na, nb, &pc);
+        abeg = piece * pc;
+        aend = min(na, abeg + pc);
+        if (piece) bwd = xs + item.w + int64_t(piece - 1) * nb;
+    } else if (piece) {
+        return;
+    }
+    // four targets per lane (half the shuffles per pair) where A fills them
+    if (na >= P2P_PAIR_TPL4)
+        pair_leaves<DEG, GENERAL, 4>(rec, a0, abeg, aend, b0, nb, ox, oy, a, kappa, split, cn,
+                                     fwd, bwd, lane);
+    else
+        pair_leaves<DEG, GENERAL, 2>(rec, a0, abeg, aend, b0, nb, ox, oy, a, kappa, split, cn,
+                                     fwd, bwd, lane);
+}
+
+// The pair items of the pairwise mode, heaviest first, in one persistent
+// launch (64 registers for the four targets per lane: 4 CTAs per SM); the
+// directed items of the leaves' own and not-pairwise neighbours follow in
+// k_p2p_mixed<.., PAIRS = true> at its higher occupancy.  Measured on GB300,
+// one queue over both kinds of item (the directed ones filling the pairs'
+// tail) was slower: the directed items ran at this kernel's occupancy.
+template <int DEG, bool GENERAL>
+__global__ void __launch_bounds__(P2P_THREADS, 4) k_p2p_pairs(
+    const uint4 *__restrict__ pitems, uint32_t *ctrl, const InstDesc *__restrict__ insts,
+    const uint32_t *__restrict__ start, const float4 *__restrict__ rec, const PairBufs pb,
+    unsigned long long *busy) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t npairs = *reinterpret_cast<volatile uint32_t *>(ctrl + CTRL_NPAIRS);
+    const uint64_t t_begin = busy ? global_ns() : 0;
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(ctrl + CTRL_QUEUE2, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= npairs) break;
+        pair_item<DEG, GENERAL>(pitems[it], insts, start, rec, pb.part, pb.nslot, pb.xs, lane);
+    }
+    if (busy && lane == 0) {
+        const size_t gw = size_t(blockIdx.x) * (P2P_THREADS / 32) + (threadIdx.x >> 5);
+        busy[2 * gw] = t_begin;
+        busy[2 * gw + 1] = global_ns();
+    }
+}
+
+// The final pass of the mixed near field, one thread per blob: u, v = its
+// leaf's far field (L2P of the local expansion, Sec. 2.2), plus its directly
+// summed near part, plus (pairwise mode, pb.part != nullptr) the slots of its
+// pairwise neighbours, a split pair's scratch runs after its slot in piece
+// order; a fixed order throughout, written at the caller's index.
+__global__ void __launch_bounds__(256) k_p2p_final(
+    const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
+    const uint32_t *__restrict__ start, const uint32_t *__restrict__ skeys,
+    const float4 *__restrict__ rec, const float2 *__restrict__ le, const PairBufs pb,
+    int dtype_f32) {
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    if (j >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int64_t r = d.poff + j;
+    const uint32_t *st = start + d.soff;
+    const int nside = 1 << d.L;
+    const uint32_t m = skeys[r] & ((d.L >= 16) ? 0xffffffffu : ((1u << (2 * d.L)) - 1u));
+    const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
+    const float4 rr = rec[r];
+    float2 w = make_float2(0.f, 0.f);
+    if (d.L >= 2) {
+        // w = (1/r) sum c_m zeta^m, zeta the offset from the leaf centre
+        const int p = d.p;
+        const float2 *c =
+            le + d.eoff + (lvl_off(d.L) + box_index(d.L, uint32_t(ix), uint32_t(iy))) * p;
+        float2 z = __ldg(c + p - 1);
+        for (int k = p - 2; k >= 0; --k) {
+            const float2 ck = __ldg(c + k);
+            z = make_float2(fmaf(z.x, rr.x, fmaf(-z.y, rr.y, ck.x)),
+                            fmaf(z.x, rr.y, fmaf(z.y, rr.x, ck.y)));
+        }
+        w = make_float2(d.cfar * z.y, d.cfar * z.x);
+    }
+    const float2 o = pb.own[r];
+    w.x += o.x;
+    w.y += o.y;
+    const uint32_t nme = st[m + 1] - st[m];
+    if (pb.part && nme >= P2P_PAIR_MIN) {
+        const uint32_t jme = uint32_t(r) - st[m];
+        for (int k = 0; k < 4; ++k) {
+            if (pairwise(nme, leaf_count(st, nside, ix + c_fwd[k][0], iy + c_fwd[k][1]))) {
+                const float2 p = pb.part[int64_t(k) * pb.nslot + r];
+                w.x += p.x;
+                w.y += p.y;
+            }
+            const int ax = ix - c_fwd[k][0], ay = iy - c_fwd[k][1];
+            const uint32_t na = leaf_count(st, nside, ax, ay);
+            if (!pairwise(na, nme)) continue;
+            const float2 p = pb.part[int64_t(4 + k) * pb.nslot + r];
+            w.x += p.x;
+            w.y += p.y;
+            uint32_t pc;
+            const uint32_t np = pair_pieces(na, nme, &pc);
+            if (np > 1) {
+                const uint32_t ma = morton_key(uint32_t(ax), uint32_t(ay));
+                const uint32_t base = pb.xtab[(d.loff + int64_t(ma)) * 4 + k];
+                if (base != 0xffffffffu)
+                    for (uint32_t i = 1; i < np; ++i) {
+                        const float2 x = pb.xs[base + int64_t(i - 1) * nme + jme];
+                        w.x += x.x;
+                        w.y += x.y;
+                    }
+            }
+        }
+    }
+    const int64_t q = int64_t(__float_as_uint(rr.w)) - d.poff;
+    if (dtype_f32) {
+        static_cast<float *>(d.u)[q] = w.x;
+        static_cast<float *>(d.v)[q] = w.y;
+    } else {
+        static_cast<double *>(d.u)[q] = double(w.x);
+        static_cast<double *>(d.v)[q] = double(w.y);
+    }
+}
+
+cudaError_t launch_pair_worklist(const Task *tasks, int ntasks, int64_t nblocks,
+                                 const InstDesc *insts, const uint32_t *start, int64_t nleaves,
+                                 uint32_t *cnt, uint32_t *off, uint32_t *scan_scratch,
+                                 uint4 *items, uint32_t *ctrl, const P2POrder *order,
+                                 const PairBufs &pb, cudaStream_t st, uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_pair_count<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, cnt, pb.xcnt,
+                                                    ctrl);
+    PF_LAUNCHED(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(cnt, off, nleaves, scan_scratch, ctrl + CTRL_NPAIRS, st, launches);
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(pb.xcnt, pb.xoff, nleaves, scan_scratch, ctrl + CTRL_NXTRA, st, launches);
+    if (e != cudaSuccess) return e;
+    uint4 *emit_to = order ? order->items_unsorted : items;
+    k_pair_emit<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, off, pb.xoff, ctrl,
+                                                   pb.xcap, pb.xtab, emit_to,
+                                                   order ? order->kA : nullptr);
+    PF_LAUNCHED(1);
+    if ((e = cudaGetLastError()) != cudaSuccess || !order) return e;
+    return order_items(order, items, ctrl + CTRL_NPAIRS, scan_scratch, st, launches);
+}
+
+// ----------------------------------------------------------------------------
 // Launch helpers
 // ----------------------------------------------------------------------------
 typedef void (*MixedKernel)(const uint4 *, uint32_t *, const InstDesc *, const uint32_t *,
-                            const float4 *, const float2 *, int, unsigned long long *);
+                            const float4 *, float2 *, unsigned long long *);
 template <int D>
-static MixedKernel pick2(int general) {
-    return general ? k_p2p_mixed<D, true> : k_p2p_mixed<D, false>;
+static MixedKernel pick2(int general, bool pairs) {
+    if (pairs) return general ? k_p2p_mixed<D, true, true> : k_p2p_mixed<D, false, true>;
+    return general ? k_p2p_mixed<D, true, false> : k_p2p_mixed<D, false, false>;
 }
 
-static MixedKernel pick_mixed(int deg, int general) {
+static MixedKernel pick_mixed(int deg, int general, bool pairs = false) {
     switch (deg) {
-        case 4: return pick2<4>(general);
-        case 5: return pick2<5>(general);
-        case 6: return pick2<6>(general);
-        case 7: return pick2<7>(general);
-        case 8: return pick2<8>(general);
-        case 9: return pick2<9>(general);
-        case 10: return pick2<10>(general);
-        case 11: return pick2<11>(general);
-        case 12: return pick2<12>(general);
+        case 4: return pick2<4>(general, pairs);
+        case 5: return pick2<5>(general, pairs);
+        case 6: return pick2<6>(general, pairs);
+        case 7: return pick2<7>(general, pairs);
+        case 8: return pick2<8>(general, pairs);
+        case 9: return pick2<9>(general, pairs);
+        case 10: return pick2<10>(general, pairs);
+        case 11: return pick2<11>(general, pairs);
+        case 12: return pick2<12>(general, pairs);
         default: return nullptr;
     }
 }
@@ -485,11 +864,66 @@ int p2p_grid(int precision_mixed, int deg, int general) {
 
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
                              const InstDesc *insts, const uint32_t *start, const float4 *rec,
-                             const float2 *le, int dtype_f32, unsigned long long *busy,
-                             cudaStream_t st, uint64_t *launches) {
-    MixedKernel k = pick_mixed(deg, general);
+                             float2 *own, int pairs, unsigned long long *busy, cudaStream_t st,
+                             uint64_t *launches) {
+    MixedKernel k = pick_mixed(deg, general, pairs != 0);
     if (!k) return cudaErrorInvalidValue;
-    k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, le, dtype_f32, busy);
+    k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, own, busy);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+typedef void (*PairsKernel)(const uint4 *, uint32_t *, const InstDesc *, const uint32_t *,
+                            const float4 *, const PairBufs, unsigned long long *);
+
+template <int D>
+static PairsKernel pick_pairs2(int general) {
+    return general ? k_p2p_pairs<D, true> : k_p2p_pairs<D, false>;
+}
+
+static PairsKernel pick_pairs(int deg, int general) {
+    switch (deg) {
+        case 4: return pick_pairs2<4>(general);
+        case 5: return pick_pairs2<5>(general);
+        case 6: return pick_pairs2<6>(general);
+        case 7: return pick_pairs2<7>(general);
+        case 8: return pick_pairs2<8>(general);
+        case 9: return pick_pairs2<9>(general);
+        case 10: return pick_pairs2<10>(general);
+        case 11: return pick_pairs2<11>(general);
+        case 12: return pick_pairs2<12>(general);
+        default: return nullptr;
+    }
+}
+
+int p2p_pairs_grid(int deg, int general) {
+    PairsKernel k = pick_pairs(deg, general);
+    if (!k) return 0;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, P2P_THREADS, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * device_sm_count();
+}
+
+cudaError_t launch_p2p_pairs(int grid, int deg, int general, const uint4 *pitems, uint32_t *ctrl,
+                             const InstDesc *insts, const uint32_t *start, const float4 *rec,
+                             const PairBufs &pb, unsigned long long *busy, cudaStream_t st,
+                             uint64_t *launches) {
+    PairsKernel k = pick_pairs(deg, general);
+    if (!k) return cudaErrorInvalidValue;
+    k<<<grid, P2P_THREADS, 0, st>>>(pitems, ctrl, insts, start, rec, pb, busy);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2p_final(const Task *tasks, int ntasks, int64_t nblocks,
+                                const InstDesc *insts, const uint32_t *start,
+                                const uint32_t *skeys, const float4 *rec, const float2 *le,
+                                const PairBufs &pb, int dtype_f32, cudaStream_t st,
+                                uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_p2p_final<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, skeys, rec, le, pb,
+                                                   dtype_f32);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }

@@ -271,6 +271,11 @@ void run_round(petfmm_server *s, std::vector<Req *> &act) {
     int st64 = in64.empty() ? 0 : petfmm_sync(s->ctx64);
     int stmx = inmx.empty() ? 0 : petfmm_sync(s->ctxmx);
     cudaError_t e = cudaStreamSynchronize(s->stream);
+    // A finished request belongs to the caller from the moment finish() marks
+    // it done (a poll may release it at once), so it is dropped from the
+    // active list here and never touched again.
+    std::vector<Req *> keep;
+    keep.reserve(act.size());
     for (size_t i = 0; i < act.size(); ++i) {
         Req *r = act[i];
         const bool is64 = r->spec.precision == PETFMM_FP64;
@@ -289,9 +294,13 @@ void run_round(petfmm_server *s, std::vector<Req *> &act) {
             }
             r->dom = fit_domain(b[0], b[1], b[2], b[3]);
         }
-        if (r->evals_done >= 2 * r->spec.n_steps) finish(s, r, PETFMM_OK);
+        if (r->evals_done >= 2 * r->spec.n_steps) {
+            finish(s, r, PETFMM_OK);
+            continue;
+        }
+        keep.push_back(r);
     }
-    act.erase(std::remove_if(act.begin(), act.end(), [](Req *r) { return r->done; }), act.end());
+    act.swap(keep);
 }
 
 void worker_main(petfmm_server *s) {

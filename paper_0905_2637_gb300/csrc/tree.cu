@@ -262,15 +262,29 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 
 int64_t radix_blocks(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
 
+// n_live (device, may be null): only the first *n_live of the n elements
+// take part; tiles past them count nothing and move nothing.
+__device__ __forceinline__ int64_t live_count(int64_t n, const uint32_t *n_live) {
+    if (!n_live) return n;
+    const int64_t m = int64_t(*n_live);
+    return m < n ? m : n;
+}
+
 __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__restrict__ keys,
-                                                           int64_t n, int shift, uint32_t mask,
+                                                           int64_t n, const uint32_t *n_live,
+                                                           int shift, uint32_t mask,
                                                            uint32_t *__restrict__ hist,
                                                            int64_t nblocks) {
     __shared__ uint32_t cnt[256];
+    const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
+    n = live_count(n, n_live);
+    if (tile >= n) {
+        hist[int64_t(threadIdx.x) * nblocks + blockIdx.x] = 0;
+        return;
+    }
     cnt[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
 #pragma unroll 4
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t i = tile + int64_t(k) * RS_THREADS + threadIdx.x;
@@ -287,7 +301,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__res
 
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, int64_t n, int shift, uint32_t mask,
+    uint32_t *__restrict__ vout, int64_t n, const uint32_t *n_live, int shift, uint32_t mask,
     const uint32_t *__restrict__ offs, int64_t nblocks) {
     __shared__ uint32_t wcnt[RS_WARPS][256];  // per-warp digit counts, then warp offsets
     __shared__ uint32_t lstart[256];          // start of each digit's run in the sorted tile
@@ -296,6 +310,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
+    n = live_count(n, n_live);
+    if (tile >= n) return;
     const int64_t tile_n = n - tile < RS_TILE ? n - tile : RS_TILE;
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) wcnt[w][tid] = 0;
@@ -356,7 +372,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
 
 cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n,
                        int nbits, uint32_t *hist, uint32_t *scan_scratch, bool *result_in_first,
-                       cudaStream_t st, uint64_t *launches) {
+                       cudaStream_t st, uint64_t *launches, const uint32_t *n_live) {
     *result_in_first = true;
     if (n <= 0) return cudaSuccess;
     const int64_t nb = radix_blocks(n);
@@ -371,12 +387,12 @@ cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, i
         const int shift = 8 * pass;
         const int bits = nbits - shift < 8 ? nbits - shift : 8;
         const uint32_t mask = (1u << bits) - 1u;
-        k_radix_hist<<<unsigned(nb), RS_THREADS, 0, st>>>(kin, n, shift, mask, hist, nb);
+        k_radix_hist<<<unsigned(nb), RS_THREADS, 0, st>>>(kin, n, n_live, shift, mask, hist, nb);
         PF_LAUNCHED(1);
         cudaError_t e = exclusive_scan(hist, hist, 256 * nb, scan_scratch, nullptr, st, launches);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<unsigned(nb), RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, shift, mask,
-                                                               hist, nb);
+        k_radix_scatter<<<unsigned(nb), RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, n_live, shift,
+                                                               mask, hist, nb);
         PF_LAUNCHED(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -97,3 +97,24 @@ def test_admission_limits():
     srv.close()
     assert all(r["status"] == 0 for r in res)
     assert got_busy or len(ts) == 9
+
+
+def test_release_while_worker_runs():
+    # a finished request belongs to the caller: polling (which releases it)
+    # as fast as possible while new requests arrive and the worker keeps
+    # running rounds must never let the worker touch a released request
+    _lib = G.lib()
+    srv = _lib.Server(8 << 30, max_slots=16, max_queue=4096)
+    rng = np.random.default_rng(3)
+    pending, results = [], []
+    for i in range(300):
+        x, y, g, s = _patch(int(rng.integers(4, 24)), i)
+        pending.append(srv.submit(x, y, g, s, 8, 0.05, int(rng.integers(1, 3))))
+        for t in list(pending):
+            r = srv.poll(t)
+            if r is not None:
+                results.append(r)
+                pending.remove(t)
+    results += _wait(srv, pending)
+    srv.close()
+    assert len(results) == 300 and all(r["status"] == 0 for r in results)
