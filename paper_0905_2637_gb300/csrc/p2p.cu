@@ -218,7 +218,6 @@ __constant__ int8_t c_fwd[4][2] = {{1, 0}, {-1, 1}, {0, 1}, {1, 1}};
 // idle, and the leaves' own warps sum that neighbour directly instead.  Both
 // leaves of a pair decide from the same two counts.
 constexpr uint32_t P2P_PAIR_MIN = 32;
-constexpr uint32_t P2P_PAIR_TPL4 = 96;  // leaves this full use 4 targets per lane
 __host__ __device__ __forceinline__ bool pairwise(uint32_t na, uint32_t nb) {
     return na >= P2P_PAIR_MIN && nb >= P2P_PAIR_MIN;
 }
@@ -576,65 +575,181 @@ __device__ __forceinline__ void pair_sym(float xa, float ya, float ga, float xs,
     bv = fmaf(-ga, ky, bv);
 }
 
-// The pairs of blobs abeg .. aend - 1 of leaf A (from a0) with leaf B (nb
-// from b0, centre at (ox, oy) leaves from A's): A in chunks of 32 TPL targets
-// (TPL per lane), B in chunks of 32 sources travelling around the warp.
-// fwd[i]: A's blob i from B; bwd[j]: B's blob j from the A range.
+// placeholders of missing targets / sources: far apart (finite kernel
+// values), zero strength (they add nothing and their sums are dropped)
+constexpr float kPairFar = 64.f;
+
+// One chunk of a leaf pair: targets ac .. min(ac + 32 TPL, aend) - 1 of leaf A
+// (TPL per lane: lane + 32 t) against all nb sources of leaf B, B in chunks
+// of 32 sources travelling around the warp with their reaction sums.
+// fwd[i]: A's blob i from B; bwd[j]: B's blob j from A (first: the chunk
+// writes bwd, else adds to it).
 template <int DEG, bool GENERAL, int TPL>
+__device__ __forceinline__ void pair_chunk(const float4 *__restrict__ rec, uint32_t a0,
+                                           uint32_t ac, uint32_t aend, uint32_t b0, uint32_t nb,
+                                           int ox, int oy, const float (&a)[DEG + 1],
+                                           float kappa, float split, float cn,
+                                           float2 *__restrict__ fwd, float2 *__restrict__ bwd,
+                                           bool first, int lane) {
+    const int next = (lane + 1) & 31;
+    float tx[TPL], ty[TPL], tg[TPL], u[TPL], v[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; ++t) {
+        const bool h = ac + lane + 32 * t < aend;
+        const float4 r =
+            h ? rec[a0 + ac + lane + 32 * t] : make_float4(kPairFar, kPairFar, 0.f, 0.f);
+        tx[t] = r.x;
+        ty[t] = r.y;
+        tg[t] = r.z;
+        u[t] = v[t] = 0.f;
+    }
+    for (uint32_t bc = 0; bc < nb; bc += 32) {
+        const bool hs = bc + lane < nb;
+        const uint32_t sb = bc + lane;
+        const float4 s = hs ? rec[b0 + sb] : make_float4(-kPairFar, -kPairFar, 0.f, 0.f);
+        // the source in A's frame (B's centre is A's plus (ox, oy) leaves)
+        float xs = s.x + float(ox), ys = s.y + float(oy), gs = s.z;
+        float bu = 0.f, bv = 0.f;
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+#pragma unroll
+            for (int t = 0; t < TPL; ++t)
+                pair_sym<DEG, GENERAL>(tx[t], ty[t], tg[t], xs, ys, gs, a, kappa, split, u[t], v[t],
+                                       bu, bv);
+            xs = __shfl_sync(0xffffffffu, xs, next);
+            ys = __shfl_sync(0xffffffffu, ys, next);
+            gs = __shfl_sync(0xffffffffu, gs, next);
+            bu = __shfl_sync(0xffffffffu, bu, next);
+            bv = __shfl_sync(0xffffffffu, bv, next);
+        }
+        // after 32 steps every travelling sum is back at its source's lane
+        if (hs) {
+            float2 w = make_float2(cn * bu, cn * bv);
+            if (!first) {
+                const float2 o = bwd[sb];
+                w = make_float2(o.x + w.x, o.y + w.y);
+            }
+            bwd[sb] = w;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPL; ++t)
+        if (ac + lane + 32 * t < aend) fwd[ac + lane + 32 * t] = make_float2(cn * u[t], cn * v[t]);
+}
+
+// The same chunk with 2 H targets per lane held as H pairs (targets lane +
+// 64 h and lane + 64 h + 32) and evaluated with packed FP32x2 instructions
+// (polynomial near-field factor only): the same products per pair as
+// pair_chunk, each packed instruction doing two of them, so half the issue
+// slots.  The reaction sums of a step run in the two halves of a pair and
+// are added before the source moves on.
+template <int DEG, int H>
+__device__ __forceinline__ void pair_chunk_x2(const float4 *__restrict__ rec, uint32_t a0,
+                                              uint32_t ac, uint32_t aend, uint32_t b0,
+                                              uint32_t nb, int ox, int oy,
+                                              const float (&a)[DEG + 1], float cn,
+                                              float2 *__restrict__ fwd, float2 *__restrict__ bwd,
+                                              bool first, int lane) {
+    const int next = (lane + 1) & 31;
+    float2 tx[H], ty[H], tg[H], ntg[H], u[H], v[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const uint32_t i0 = ac + lane + 64 * h, i1 = i0 + 32;
+        const float4 r0 = i0 < aend ? rec[a0 + i0] : make_float4(kPairFar, kPairFar, 0.f, 0.f);
+        const float4 r1 = i1 < aend ? rec[a0 + i1] : make_float4(kPairFar, kPairFar, 0.f, 0.f);
+        tx[h] = make_float2(r0.x, r1.x);
+        ty[h] = make_float2(r0.y, r1.y);
+        tg[h] = make_float2(r0.z, r1.z);
+        ntg[h] = make_float2(-r0.z, -r1.z);
+        u[h] = v[h] = make_float2(0.f, 0.f);
+    }
+    float2 a2[DEG + 1];
+#pragma unroll
+    for (int k = 0; k <= DEG; ++k) a2[k] = make_float2(a[k], a[k]);
+    for (uint32_t bc = 0; bc < nb; bc += 32) {
+        const bool hs = bc + lane < nb;
+        const uint32_t sb = bc + lane;
+        const float4 s = hs ? rec[b0 + sb] : make_float4(-kPairFar, -kPairFar, 0.f, 0.f);
+        float xs = s.x + float(ox), ys = s.y + float(oy), gs = s.z;
+        float bu = 0.f, bv = 0.f;
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+            // with K = (-dy, dx) g: u_a += g_s K, reaction u_b -= g_a K
+            const float2 nx = make_float2(-xs, -xs), ny = make_float2(-ys, -ys);
+            const float2 g2 = make_float2(gs, gs), ng2 = make_float2(-gs, -gs);
+            float2 bu2 = make_float2(bu, 0.f), bv2 = make_float2(bv, 0.f);
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const float2 dx = __fadd2_rn(tx[h], nx), dy = __fadd2_rn(ty[h], ny);
+                const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+                float2 g = a2[DEG];
+#pragma unroll
+                for (int q = DEG - 1; q >= 0; --q) g = __ffma2_rn(g, r2, a2[q]);
+                const float2 py = __fmul2_rn(dy, g), px = __fmul2_rn(dx, g);
+                u[h] = __ffma2_rn(ng2, py, u[h]);
+                v[h] = __ffma2_rn(g2, px, v[h]);
+                bu2 = __ffma2_rn(tg[h], py, bu2);
+                bv2 = __ffma2_rn(ntg[h], px, bv2);
+            }
+            bu = bu2.x + bu2.y;
+            bv = bv2.x + bv2.y;
+            xs = __shfl_sync(0xffffffffu, xs, next);
+            ys = __shfl_sync(0xffffffffu, ys, next);
+            gs = __shfl_sync(0xffffffffu, gs, next);
+            bu = __shfl_sync(0xffffffffu, bu, next);
+            bv = __shfl_sync(0xffffffffu, bv, next);
+        }
+        if (hs) {
+            float2 w = make_float2(cn * bu, cn * bv);
+            if (!first) {
+                const float2 o = bwd[sb];
+                w = make_float2(o.x + w.x, o.y + w.y);
+            }
+            bwd[sb] = w;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const uint32_t i0 = ac + lane + 64 * h, i1 = i0 + 32;
+        if (i0 < aend) fwd[i0] = make_float2(cn * u[h].x, cn * v[h].x);
+        if (i1 < aend) fwd[i1] = make_float2(cn * u[h].y, cn * v[h].y);
+    }
+}
+
+// The pairs of blobs abeg .. aend - 1 of leaf A (from a0) with leaf B (nb
+// from b0): A in chunks of 256, 128, 64 or 32 targets, the largest that the
+// remaining targets fill at least three quarters of (less padding than one
+// fixed size; more targets per lane, fewer shuffles per pair).
+template <int DEG, bool GENERAL>
 __device__ __forceinline__ void pair_leaves(const float4 *__restrict__ rec, uint32_t a0,
                                             uint32_t abeg, uint32_t aend, uint32_t b0, uint32_t nb,
                                             int ox, int oy, const float (&a)[DEG + 1],
                                             float kappa, float split, float cn,
                                             float2 *__restrict__ fwd, float2 *__restrict__ bwd,
                                             int lane) {
-    // placeholders of missing targets / sources: far apart (finite kernel
-    // values), zero strength (they add nothing and their sums are dropped)
-    constexpr float kFar = 64.f;
-    const int next = (lane + 1) & 31;
-    for (uint32_t ac = abeg; ac < aend; ac += 32 * TPL) {
-        float tx[TPL], ty[TPL], tg[TPL], u[TPL], v[TPL];
-#pragma unroll
-        for (int t = 0; t < TPL; ++t) {
-            const bool h = ac + lane + 32 * t < aend;
-            const float4 r = h ? rec[a0 + ac + lane + 32 * t] : make_float4(kFar, kFar, 0.f, 0.f);
-            tx[t] = r.x;
-            ty[t] = r.y;
-            tg[t] = r.z;
-            u[t] = v[t] = 0.f;
+    bool first = true;
+    for (uint32_t ac = abeg; ac < aend; first = false) {
+        const uint32_t rem = aend - ac;
+        if (!GENERAL && rem >= 192) {
+            pair_chunk_x2<DEG, 4>(rec, a0, ac, aend, b0, nb, ox, oy, a, cn, fwd, bwd, first, lane);
+            ac += 256;
+        } else if (rem >= 96) {
+            if (GENERAL)
+                pair_chunk<DEG, GENERAL, 4>(rec, a0, ac, aend, b0, nb, ox, oy, a, kappa, split, cn,
+                                            fwd, bwd, first, lane);
+            else
+                pair_chunk_x2<DEG, 2>(rec, a0, ac, aend, b0, nb, ox, oy, a, cn, fwd, bwd, first,
+                                      lane);
+            ac += 128;
+        } else if (rem > 32) {
+            pair_chunk<DEG, GENERAL, 2>(rec, a0, ac, aend, b0, nb, ox, oy, a, kappa, split, cn,
+                                        fwd, bwd, first, lane);
+            ac += 64;
+        } else {
+            pair_chunk<DEG, GENERAL, 1>(rec, a0, ac, aend, b0, nb, ox, oy, a, kappa, split, cn,
+                                        fwd, bwd, first, lane);
+            ac += 32;
         }
-        for (uint32_t bc = 0; bc < nb; bc += 32) {
-            const bool hs = bc + lane < nb;
-            const uint32_t sb = bc + lane;
-            const float4 s = hs ? rec[b0 + sb] : make_float4(-kFar, -kFar, 0.f, 0.f);
-            // the source in A's frame (B's centre is A's plus (ox, oy) leaves)
-            float xs = s.x + float(ox), ys = s.y + float(oy), gs = s.z;
-            float bu = 0.f, bv = 0.f;
-#pragma unroll 2
-            for (int k = 0; k < 32; ++k) {
-#pragma unroll
-                for (int t = 0; t < TPL; ++t)
-                    pair_sym<DEG, GENERAL>(tx[t], ty[t], tg[t], xs, ys, gs, a, kappa, split, u[t],
-                                           v[t], bu, bv);
-                xs = __shfl_sync(0xffffffffu, xs, next);
-                ys = __shfl_sync(0xffffffffu, ys, next);
-                gs = __shfl_sync(0xffffffffu, gs, next);
-                bu = __shfl_sync(0xffffffffu, bu, next);
-                bv = __shfl_sync(0xffffffffu, bv, next);
-            }
-            // after 32 steps every travelling sum is back at its source's lane
-            if (hs) {
-                float2 w = make_float2(cn * bu, cn * bv);
-                if (ac != abeg) {
-                    const float2 o = bwd[sb];
-                    w = make_float2(o.x + w.x, o.y + w.y);
-                }
-                bwd[sb] = w;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < TPL; ++t)
-            if (ac + lane + 32 * t < aend)
-                fwd[ac + lane + 32 * t] = make_float2(cn * u[t], cn * v[t]);
     }
 }
 
@@ -673,13 +788,8 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
     } else if (piece) {
         return;
     }
-    // four targets per lane (half the shuffles per pair) where A fills them
-    if (na >= P2P_PAIR_TPL4)
-        pair_leaves<DEG, GENERAL, 4>(rec, a0, abeg, aend, b0, nb, ox, oy, a, kappa, split, cn,
-                                     fwd, bwd, lane);
-    else
-        pair_leaves<DEG, GENERAL, 2>(rec, a0, abeg, aend, b0, nb, ox, oy, a, kappa, split, cn,
-                                     fwd, bwd, lane);
+    pair_leaves<DEG, GENERAL>(rec, a0, abeg, aend, b0, nb, ox, oy, a, kappa, split, cn, fwd, bwd,
+                              lane);
 }
 
 // The pair items of the pairwise mode, heaviest first, in one persistent
@@ -689,7 +799,7 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
 // one queue over both kinds of item (the directed ones filling the pairs'
 // tail) was slower: the directed items ran at this kernel's occupancy.
 template <int DEG, bool GENERAL>
-__global__ void __launch_bounds__(P2P_THREADS, 4) k_p2p_pairs(
+__global__ void __launch_bounds__(P2P_THREADS, 3) k_p2p_pairs(
     const uint4 *__restrict__ pitems, uint32_t *ctrl, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const float4 *__restrict__ rec, const PairBufs pb,
     unsigned long long *busy) {
