@@ -265,13 +265,14 @@ enum {
                                   arrays may change) and replayed while it repeats;
                                   0 (default) plain launches.  Results are identical.
                                   The context's stream must not be capturing. */
-    PETFMM_OPT_P2P_PAIRS = 11  /* mixed path: 1 (default) each pair of neighbouring leaves
-                                  that both hold >= 32 blobs is evaluated once, its
-                                  kernel values serving both sides (K of Eq. 8 is odd);
+    PETFMM_OPT_P2P_PAIRS = 11  /* mixed path: 1 (default) each pair of blobs in the same
+                                  or neighbouring leaves that both hold >= 32 blobs is
+                                  evaluated once, its kernel value serving both blobs
+                                  (K of Eq. 8 is odd);
                                   heavy pairs are cut into pieces for load balance.
                                   0: every leaf sums its 9 leaves directly.  Both
                                   deterministic; they differ by FP32 rounding of the
-                                  sums.  Extra device memory in mode 1: 80 bytes per
+                                  sums.  Extra device memory in mode 1: 88 bytes per
                                   blob and 24 per leaf. */
 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);

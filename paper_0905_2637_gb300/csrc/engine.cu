@@ -579,10 +579,10 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     const int64_t rb = radix_blocks(N);
     PF_TRY(ensure(c->hist, size_t(256) * rb * 4, st));
     // pairwise near field (mixed path): at most 4 forward neighbours per leaf,
-    // a pair cut into at most ceil(na / 128) pieces
+    // a pair cut into at most ceil(na / 128) pieces, and the leaf's own pairs
     const bool pairs = mixed && c->p2p_pairs;
     const int64_t pair_cap =
-        pairs ? 4 * (std::min<int64_t>(pl.nleaves, N) + N / 128) + 1 : 0;
+        pairs ? 5 * std::min<int64_t>(pl.nleaves, N) + 4 * (N / 128) + 1 : 0;
     const int64_t order_cap = std::max<int64_t>(pl.items_cap, pair_cap);
     const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(256 * rb, pl.nleaves),
                                              256 * radix_blocks(order_cap));
@@ -608,7 +608,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                   st));
     if (mixed) PF_TRY(ensure(c->own, size_t(N) * sizeof(float2), st));
     if (pairs) {
-        PF_TRY(ensure(c->part, size_t(8) * N * sizeof(float2), st));
+        PF_TRY(ensure(c->part, size_t(9) * N * sizeof(float2), st));
         PF_TRY(ensure(c->pitems, size_t(pair_cap) * sizeof(uint4), st));
         PF_TRY(ensure(c->pxtra, size_t(6) * pl.nleaves * sizeof(uint32_t), st));
         PF_TRY(ensure(c->pxs, size_t(N) * sizeof(float2), st));

@@ -168,9 +168,9 @@ cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items,
                              uint64_t *launches);
 // Pairwise near field between neighbouring leaves (mixed path).  Buffers:
 // own[N]: each blob's directly summed part (sorted order; the only one used
-// by the directed mode, part == nullptr there); part: 8 slots of
+// by the directed mode, part == nullptr there); part: 9 slots of
 // nslot float2 (slot d: A's blobs from forward neighbour d, slot 4 + d: B's
-// blobs from A); xcnt, xoff: per leaf, the scratch entries of its split pairs
+// blobs from A, slot 8: each blob from the other blobs of its leaf); xcnt, xoff: per leaf, the scratch entries of its split pairs
 // and their exclusive scan; xtab[4 nleaves]: per (leaf, direction) of a split
 // pair its scratch base (all ones: not split); xs[xcap]: the scratch runs of
 // pieces 1 .. of split pairs.
@@ -181,7 +181,8 @@ struct PairBufs {
     float2 *xs;
     int64_t xcap;
 };
-// ... the item list (inst, leaf A, direction | piece << 2, scratch base),
+// ... the item list (inst, leaf A, direction | piece << 3, scratch base;
+// direction 4: the leaf's own pairs),
 // ctrl[CTRL_NPAIRS] its count, ctrl[CTRL_NXTRA] the scratch entries wanted ...
 cudaError_t launch_pair_worklist(const Task *tasks, int ntasks, int64_t nblocks,
                                  const InstDesc *insts, const uint32_t *start, int64_t nleaves,

@@ -301,8 +301,9 @@ __device__ __forceinline__ void directed_item(const uint4 item, const InstDesc *
             if (sx < 0 || sx >= nside) continue;
             const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
             const uint32_t j0 = st[nm], j1 = st[nm + 1];
-            // pairwise mode: neighbours that the pair kernel covers are skipped
-            if (PAIRS && (dx | dy) && pairwise(st[m + 1] - st[m], j1 - j0)) continue;
+            // pairwise mode: the leaves the pair kernel covers (the leaf itself
+            // included) are skipped
+            if (PAIRS && pairwise(st[m + 1] - st[m], j1 - j0)) continue;
             const float xa = ra.x - float(dx), ya = ra.y - float(dy);
             const float xb = rb.x - float(dx), yb = rb.y - float(dy);
             // the stride-1 loop keeps constant load offsets after unrolling
@@ -492,6 +493,9 @@ __global__ void __launch_bounds__(256) k_pair_count(const Task *__restrict__ tas
                 x += (np - 1) * nb;
                 sym += (unsigned long long)na * nb;
             }
+            // the leaf's own pairs: one item
+            c += 1;
+            sym += (unsigned long long)na * (na - 1) / 2;
         }
         cnt[d.loff + m] = c;
         xcnt[d.loff + m] = x;
@@ -511,6 +515,15 @@ __global__ void __launch_bounds__(256) k_pair_count(const Task *__restrict__ tas
 
 // items (inst, leaf A, direction d, 0) and their work class (targets x
 // sources, log2 in quarter steps, stored as 127 - class: heaviest first)
+// work class of an item of `cost` (64-target chunk, 32-source chunk) tiles:
+// heaviest first = smallest class, quarter steps of log2
+__device__ __forceinline__ uint32_t pair_wclass(uint32_t cost) {
+    if (cost < 1) cost = 1;
+    const int e = 31 - __clz(int(cost));
+    const uint32_t frac = e >= 2 ? (cost >> (e - 2)) & 3u : (cost << (2 - e)) & 3u;
+    return 127u - (uint32_t(e) * 4u + frac);
+}
+
 __global__ void __launch_bounds__(256) k_pair_emit(const Task *__restrict__ tasks, int ntasks,
                                                    const InstDesc *__restrict__ insts,
                                                    const uint32_t *__restrict__ start,
@@ -543,20 +556,19 @@ __global__ void __launch_bounds__(256) k_pair_emit(const Task *__restrict__ task
         const uint32_t base = split ? xb : 0xffffffffu;
         if (np > 1) xtab[(d.loff + m) * 4 + k] = base;
         for (uint32_t i = 0; i < np; ++i) {
-            items[o] = make_uint4(uint32_t(t.inst), uint32_t(m), uint32_t(k) | (i << 2), base);
+            items[o] = make_uint4(uint32_t(t.inst), uint32_t(m), uint32_t(k) | (i << 3), base);
             if (wclass) {
                 // a warp spends 32 steps per (64-target chunk, 32-source chunk)
                 const uint32_t nt = split ? min(pc, na - i * pc) : (i ? 0u : na);
-                uint32_t cost = ((nt + 63) / 64) * ((nb + 31) / 32);
-                if (cost < 1) cost = 1;
-                const int e = 31 - __clz(int(cost));
-                const uint32_t frac = e >= 2 ? (cost >> (e - 2)) & 3u : (cost << (2 - e)) & 3u;
-                wclass[o] = 127u - (uint32_t(e) * 4u + frac);
+                wclass[o] = pair_wclass(((nt + 63) / 64) * ((nb + 31) / 32));
             }
             ++o;
         }
         xb += (np - 1) * nb;
     }
+    // the leaf's own pairs (direction 4): half the tiles of the leaf with itself
+    items[o] = make_uint4(uint32_t(t.inst), uint32_t(m), 4u, 0u);
+    if (wclass) wclass[o] = pair_wclass(((na + 63) / 64) * ((na + 31) / 32) / 2);
 }
 
 // One target (in A's frame) against the travelling source (already in A's
@@ -579,18 +591,26 @@ __device__ __forceinline__ void pair_sym(float xa, float ya, float ga, float xs,
 // values), zero strength (they add nothing and their sums are dropped)
 constexpr float kPairFar = 64.f;
 
+// p[0] = w, or p[0] += w
+__device__ __forceinline__ void put2(float2 *p, float2 w, bool add) {
+    if (add) {
+        const float2 o = *p;
+        w = make_float2(o.x + w.x, o.y + w.y);
+    }
+    *p = w;
+}
+
 // One chunk of a leaf pair: targets ac .. min(ac + 32 TPL, aend) - 1 of leaf A
 // (TPL per lane: lane + 32 t) against all nb sources of leaf B, B in chunks
 // of 32 sources travelling around the warp with their reaction sums.
-// fwd[i]: A's blob i from B; bwd[j]: B's blob j from A (first: the chunk
-// writes bwd, else adds to it).
+// fwd[i]: A's blob i from B; bwd[j]: B's blob j from A (bwd_add / fwd_add:
+// the chunk adds to them, else writes).
 template <int DEG, bool GENERAL, int TPL>
-__device__ __forceinline__ void pair_chunk(const float4 *__restrict__ rec, uint32_t a0,
+__device__ __noinline__ void pair_chunk(const float4 *__restrict__ rec, uint32_t a0,
                                            uint32_t ac, uint32_t aend, uint32_t b0, uint32_t nb,
                                            int ox, int oy, const float (&a)[DEG + 1],
-                                           float kappa, float split, float cn,
-                                           float2 *__restrict__ fwd, float2 *__restrict__ bwd,
-                                           bool first, int lane) {
+                                           float kappa, float split, float cn, float2 *fwd,
+                                           float2 *bwd, bool bwd_add, bool fwd_add, int lane) {
     const int next = (lane + 1) & 31;
     float tx[TPL], ty[TPL], tg[TPL], u[TPL], v[TPL];
 #pragma unroll
@@ -623,18 +643,12 @@ __device__ __forceinline__ void pair_chunk(const float4 *__restrict__ rec, uint3
             bv = __shfl_sync(0xffffffffu, bv, next);
         }
         // after 32 steps every travelling sum is back at its source's lane
-        if (hs) {
-            float2 w = make_float2(cn * bu, cn * bv);
-            if (!first) {
-                const float2 o = bwd[sb];
-                w = make_float2(o.x + w.x, o.y + w.y);
-            }
-            bwd[sb] = w;
-        }
+        if (hs) put2(bwd + sb, make_float2(cn * bu, cn * bv), bwd_add);
     }
 #pragma unroll
     for (int t = 0; t < TPL; ++t)
-        if (ac + lane + 32 * t < aend) fwd[ac + lane + 32 * t] = make_float2(cn * u[t], cn * v[t]);
+        if (ac + lane + 32 * t < aend)
+            put2(fwd + ac + lane + 32 * t, make_float2(cn * u[t], cn * v[t]), fwd_add);
 }
 
 // The same chunk with 2 H targets per lane held as H pairs (targets lane +
@@ -644,12 +658,11 @@ __device__ __forceinline__ void pair_chunk(const float4 *__restrict__ rec, uint3
 // slots.  The reaction sums of a step run in the two halves of a pair and
 // are added before the source moves on.
 template <int DEG, int H>
-__device__ __forceinline__ void pair_chunk_x2(const float4 *__restrict__ rec, uint32_t a0,
+__device__ __noinline__ void pair_chunk_x2(const float4 *__restrict__ rec, uint32_t a0,
                                               uint32_t ac, uint32_t aend, uint32_t b0,
                                               uint32_t nb, int ox, int oy,
-                                              const float (&a)[DEG + 1], float cn,
-                                              float2 *__restrict__ fwd, float2 *__restrict__ bwd,
-                                              bool first, int lane) {
+                                              const float (&a)[DEG + 1], float cn, float2 *fwd,
+                                              float2 *bwd, bool bwd_add, bool fwd_add, int lane) {
     const int next = (lane + 1) & 31;
     float2 tx[H], ty[H], tg[H], ntg[H], u[H], v[H];
 #pragma unroll
@@ -699,63 +712,101 @@ __device__ __forceinline__ void pair_chunk_x2(const float4 *__restrict__ rec, ui
             bu = __shfl_sync(0xffffffffu, bu, next);
             bv = __shfl_sync(0xffffffffu, bv, next);
         }
-        if (hs) {
-            float2 w = make_float2(cn * bu, cn * bv);
-            if (!first) {
-                const float2 o = bwd[sb];
-                w = make_float2(o.x + w.x, o.y + w.y);
-            }
-            bwd[sb] = w;
-        }
+        if (hs) put2(bwd + sb, make_float2(cn * bu, cn * bv), bwd_add);
     }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
         const uint32_t i0 = ac + lane + 64 * h, i1 = i0 + 32;
-        if (i0 < aend) fwd[i0] = make_float2(cn * u[h].x, cn * v[h].x);
-        if (i1 < aend) fwd[i1] = make_float2(cn * u[h].y, cn * v[h].y);
+        if (i0 < aend) put2(fwd + i0, make_float2(cn * u[h].x, cn * v[h].x), fwd_add);
+        if (i1 < aend) put2(fwd + i1, make_float2(cn * u[h].y, cn * v[h].y), fwd_add);
     }
 }
 
-// The pairs of blobs abeg .. aend - 1 of leaf A (from a0) with leaf B (nb
-// from b0): A in chunks of 256, 128, 64 or 32 targets, the largest that the
-// remaining targets fill at least three quarters of (less padding than one
-// fixed size; more targets per lane, fewer shuffles per pair).
+// The pairs of blobs abeg .. aend - 1 of leaf A (from a0) with the nb blobs
+// of leaf B (from b0): A in chunks of 256, 128, 64 or 32 targets.  Leaf
+// pairs take the largest chunk that the remaining targets fill to at least
+// three quarters (less padding than one fixed size; more targets per lane,
+// fewer shuffles per pair); a range of whole 32-blob chunks (exact) is cut
+// without padding.  The first chunk writes bwd (unless bwd_add), later ones
+// add to it; fwd_add: the chunks add to fwd.
 template <int DEG, bool GENERAL>
 __device__ __forceinline__ void pair_leaves(const float4 *__restrict__ rec, uint32_t a0,
                                             uint32_t abeg, uint32_t aend, uint32_t b0, uint32_t nb,
                                             int ox, int oy, const float (&a)[DEG + 1],
-                                            float kappa, float split, float cn,
-                                            float2 *__restrict__ fwd, float2 *__restrict__ bwd,
+                                            float kappa, float split, float cn, float2 *fwd,
+                                            float2 *bwd, bool bwd_add, bool fwd_add, bool exact,
                                             int lane) {
-    bool first = true;
-    for (uint32_t ac = abeg; ac < aend; first = false) {
+    const uint32_t t8 = exact ? 256 : 192, t4 = exact ? 128 : 96, t2 = exact ? 64 : 33;
+    for (uint32_t ac = abeg; ac < aend; bwd_add = true) {
         const uint32_t rem = aend - ac;
-        if (!GENERAL && rem >= 192) {
-            pair_chunk_x2<DEG, 4>(rec, a0, ac, aend, b0, nb, ox, oy, a, cn, fwd, bwd, first, lane);
+        if (!GENERAL && rem >= t8) {
+            pair_chunk_x2<DEG, 4>(rec, a0, ac, aend, b0, nb, ox, oy, a, cn, fwd, bwd, bwd_add,
+                                  fwd_add, lane);
             ac += 256;
-        } else if (rem >= 96) {
+        } else if (rem >= t4) {
             if (GENERAL)
                 pair_chunk<DEG, GENERAL, 4>(rec, a0, ac, aend, b0, nb, ox, oy, a, kappa, split, cn,
-                                            fwd, bwd, first, lane);
+                                            fwd, bwd, bwd_add, fwd_add, lane);
             else
-                pair_chunk_x2<DEG, 2>(rec, a0, ac, aend, b0, nb, ox, oy, a, cn, fwd, bwd, first,
-                                      lane);
+                pair_chunk_x2<DEG, 2>(rec, a0, ac, aend, b0, nb, ox, oy, a, cn, fwd, bwd, bwd_add,
+                                      fwd_add, lane);
             ac += 128;
-        } else if (rem > 32) {
+        } else if (rem >= t2) {
             pair_chunk<DEG, GENERAL, 2>(rec, a0, ac, aend, b0, nb, ox, oy, a, kappa, split, cn,
-                                        fwd, bwd, first, lane);
+                                        fwd, bwd, bwd_add, fwd_add, lane);
             ac += 64;
         } else {
             pair_chunk<DEG, GENERAL, 1>(rec, a0, ac, aend, b0, nb, ox, oy, a, kappa, split, cn,
-                                        fwd, bwd, first, lane);
+                                        fwd, bwd, bwd_add, fwd_add, lane);
             ac += 32;
         }
     }
 }
 
-// One item of the pairwise near field: piece item.z >> 2 of leaf A (item.y)
-// with its forward neighbour item.z & 3; item.w = the pair's scratch base
-// (all ones: the pair is not split, piece 0 takes all of it).
+// The pairs within one leaf (n >= 32 blobs from a0), each once, summed into
+// slf[0 .. n) by one warp in a fixed order.  For each 32-blob sub-chunk j:
+// the pairs inside it -- the blobs rotate around the warp for 16 steps, so
+// that every lane meets every other lane's blob once (at step 16 the two
+// halves of the warp meet each other, so only lanes 0..15 count it), and a
+// final shuffle brings each travelling reaction back to its blob -- then its
+// pairs with all blobs before it, as a pair range (targets 0 .. 32 j,
+// sources the sub-chunk).
+template <int DEG, bool GENERAL>
+__device__ __forceinline__ void self_leaf(const float4 *__restrict__ rec, uint32_t a0,
+                                          uint32_t n, const float (&a)[DEG + 1], float kappa,
+                                          float split, float cn, float2 *slf, int lane) {
+    const int next = (lane + 1) & 31;
+    for (uint32_t s0 = 0; s0 < n; s0 += 32) {
+        const uint32_t ns = min(32u, n - s0);
+        const bool h = uint32_t(lane) < ns;
+        const float4 r = h ? rec[a0 + s0 + lane] : make_float4(kPairFar, kPairFar, 0.f, 0.f);
+        float xs = r.x, ys = r.y, gs = r.z, bu = 0.f, bv = 0.f, u = 0.f, v = 0.f;
+        for (int k = 1; k <= 16; ++k) {
+            xs = __shfl_sync(0xffffffffu, xs, next);
+            ys = __shfl_sync(0xffffffffu, ys, next);
+            gs = __shfl_sync(0xffffffffu, gs, next);
+            bu = __shfl_sync(0xffffffffu, bu, next);
+            bv = __shfl_sync(0xffffffffu, bv, next);
+            const bool on = k < 16 || lane < 16;
+            pair_sym<DEG, GENERAL>(r.x, r.y, on ? r.z : 0.f, xs, ys, on ? gs : 0.f, a, kappa,
+                                   split, u, v, bu, bv);
+        }
+        // lane l holds the reaction of the blob of lane l + 16
+        bu = __shfl_sync(0xffffffffu, bu, (lane + 16) & 31);
+        bv = __shfl_sync(0xffffffffu, bv, (lane + 16) & 31);
+        if (h) slf[s0 + lane] = make_float2(cn * (u + bu), cn * (v + bv));
+        __syncwarp();
+        if (s0)
+            pair_leaves<DEG, GENERAL>(rec, a0, 0, s0, a0 + s0, ns, 0, 0, a, kappa, split, cn, slf,
+                                      slf + s0, true, true, true, lane);
+        __syncwarp();
+    }
+}
+
+// One item of the pairwise near field: piece item.z >> 3 of leaf A (item.y)
+// with its forward neighbour item.z & 7 (4: the leaf's own pairs, to slot
+// 8); item.w = the pair's scratch base (all ones: the pair is not split,
+// piece 0 takes all of it).
 template <int DEG, bool GENERAL>
 __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__restrict__ insts,
                                           const uint32_t *__restrict__ start,
@@ -768,13 +819,17 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
     for (int k = 0; k <= DEG; ++k) a[k] = d.poly[k];
     const float kappa = d.kappa, split = d.qsplit_rho2, cn = d.cnear;
     const uint32_t m = item.y;
-    const int dir = int(item.z & 3u);
-    const uint32_t piece = item.z >> 2;
+    const int dir = int(item.z & 7u);
+    const uint32_t piece = item.z >> 3;
+    const uint32_t *st = start + d.soff;
+    const uint32_t a0 = st[m], na = st[m + 1] - a0;
+    if (dir == 4) {
+        self_leaf<DEG, GENERAL>(rec, a0, na, a, kappa, split, cn, part + 8 * nslot + a0, lane);
+        return;
+    }
     const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
     const int ox = c_fwd[dir][0], oy = c_fwd[dir][1];
     const uint32_t mb = morton_key(uint32_t(ix + ox), uint32_t(iy + oy));
-    const uint32_t *st = start + d.soff;
-    const uint32_t a0 = st[m], na = st[m + 1] - a0;
     const uint32_t b0 = st[mb], nb = st[mb + 1] - b0;
     uint32_t abeg = 0, aend = na;
     float2 *fwd = part + int64_t(dir) * nslot + a0;      // A's particles, from B
@@ -789,7 +844,7 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
         return;
     }
     pair_leaves<DEG, GENERAL>(rec, a0, abeg, aend, b0, nb, ox, oy, a, kappa, split, cn, fwd, bwd,
-                              lane);
+                              false, false, false, lane);
 }
 
 // The pair items of the pairwise mode, heaviest first, in one persistent
@@ -861,6 +916,9 @@ __global__ void __launch_bounds__(256) k_p2p_final(
     const uint32_t nme = st[m + 1] - st[m];
     if (pb.part && nme >= P2P_PAIR_MIN) {
         const uint32_t jme = uint32_t(r) - st[m];
+        const float2 sp = pb.part[8 * pb.nslot + r];  // the leaf's own pairs
+        w.x += sp.x;
+        w.y += sp.y;
         for (int k = 0; k < 4; ++k) {
             if (pairwise(nme, leaf_count(st, nside, ix + c_fwd[k][0], iy + c_fwd[k][1]))) {
                 const float2 p = pb.part[int64_t(k) * pb.nslot + r];

@@ -1,9 +1,10 @@
 """The pairwise near field of the mixed path.
 
-Every pair of neighbouring leaves that both hold at least 32 blobs is summed
-once: the kernel of Eq. 8 is odd in the offset, so the velocity a blob b
-induces on a and the one a induces on b share K(x_a - x_b) (Sec. 2.1, Eq. 9),
-and the reaction on the source leaf travels with the source.  Heavy pairs are
+Every pair of blobs in the same leaf or in neighbouring leaves that both
+hold at least 32 blobs is summed once: the kernel of Eq. 8 is odd in the
+offset, so the velocity a blob b induces on a and the one a induces on b
+share K(x_a - x_b) (Sec. 2.1, Eq. 9), and the reaction on the source travels
+with it.  Heavy pairs are
 cut into pieces along the target leaf (whole 128-target chunks, at most 256
 tiles of 128 x 32 per piece), the source leaf's partial sums of pieces 1 ..
 kept apart and added in piece order; when those partial sums would need more
@@ -55,6 +56,8 @@ def expected_pieces(grid):
             na = int(grid[iy, ix])
             if na < 32:
                 continue
+            items += 1                      # the leaf's own pairs
+            sym += na * (na - 1) // 2
             for dx, dy in FWD:
                 bx, by = ix + dx, iy + dy
                 if not (0 <= bx < n and 0 <= by < n):
