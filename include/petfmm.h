@@ -273,7 +273,7 @@ enum {
                                   0: every leaf sums its 9 leaves directly.  Both
                                   deterministic; they differ by FP32 rounding of the
                                   sums.  Extra device memory in mode 1: 88 bytes per
-                                  blob and 24 per leaf. */
+                                  blob and 28 per leaf. */
 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
 

@@ -610,7 +610,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     if (pairs) {
         PF_TRY(ensure(c->part, size_t(9) * N * sizeof(float2), st));
         PF_TRY(ensure(c->pitems, size_t(pair_cap) * sizeof(uint4), st));
-        PF_TRY(ensure(c->pxtra, size_t(6) * pl.nleaves * sizeof(uint32_t), st));
+        PF_TRY(ensure(c->pxtra, size_t(7) * pl.nleaves * sizeof(uint32_t), st));
         PF_TRY(ensure(c->pxs, size_t(N) * sizeof(float2), st));
     }
     PairBufs pb{};
@@ -621,6 +621,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         pb.xcnt = static_cast<uint32_t *>(c->pxtra.p);
         pb.xoff = pb.xcnt + pl.nleaves;
         pb.xtab = pb.xoff + pl.nleaves;
+        pb.lflags = pb.xtab + 4 * pl.nleaves;
         pb.xs = static_cast<float2 *>(c->pxs.p);
         pb.xcap = N;  // scratch of split pairs; more wanted: no pair is split
     }
@@ -773,7 +774,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     stage_mark(c, PETFMM_STAGE_WORKLIST);
     const int tpi = mixed ? P2P_TPI_MIXED : P2P_TPI_F64;
     PF_CUDA(launch_p2p_worklist(dtask + pl.leaves_wl.first, pl.leaves_wl.count, pl.leaves_wl.nblocks,
-                                dinst, start, pl.nleaves, tpi, static_cast<uint32_t *>(c->cnt.p),
+                                dinst, start, pl.nleaves, tpi, pairs ? 1 : 0,
+                                static_cast<uint32_t *>(c->cnt.p),
                                 static_cast<uint32_t *>(c->off.p), scratch,
                                 static_cast<uint4 *>(c->items.p), ctrl,
                                 c->p2p_mode == 0 ? &order : nullptr, st, lc));

@@ -149,11 +149,13 @@ struct P2POrder {
     uint4 *items_unsorted;
     uint32_t *kA, *kB, *vA, *vB, *hist;  // hist: 256 * radix_blocks(cap) words
 };
+// pairs_mode: only the leaves with directed work (leaves under 32 blobs, or
+// with a neighbour the pair kernel does not cover) get items.
 cudaError_t launch_p2p_worklist(const Task *tasks, int ntasks, int64_t nblocks,
                                 const InstDesc *insts, const uint32_t *start, int64_t nleaves,
-                                int tpi, uint32_t *cnt, uint32_t *off, uint32_t *scan_scratch,
-                                uint4 *items, uint32_t *ctrl, const P2POrder *order,
-                                cudaStream_t st, uint64_t *launches);
+                                int tpi, int pairs_mode, uint32_t *cnt, uint32_t *off,
+                                uint32_t *scan_scratch, uint4 *items, uint32_t *ctrl,
+                                const P2POrder *order, cudaStream_t st, uint64_t *launches);
 cudaError_t launch_p2p_f64(int grid, const uint4 *items, uint32_t *ctrl, const InstDesc *insts,
                            const uint32_t *start, const double *xs, const double *ys,
                            const double *gs, const uint32_t *perm, const double2 *le,
@@ -172,12 +174,13 @@ cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items,
 // nslot float2 (slot d: A's blobs from forward neighbour d, slot 4 + d: B's
 // blobs from A, slot 8: each blob from the other blobs of its leaf); xcnt, xoff: per leaf, the scratch entries of its split pairs
 // and their exclusive scan; xtab[4 nleaves]: per (leaf, direction) of a split
-// pair its scratch base (all ones: not split); xs[xcap]: the scratch runs of
-// pieces 1 .. of split pairs.
+// pair its scratch base (all ones: not split); lflags[nleaves]: per leaf,
+// which of these hold its blobs' sums; xs[xcap]: the scratch runs of pieces
+// 1 .. of split pairs.
 struct PairBufs {
     float2 *own, *part;
     int64_t nslot;
-    uint32_t *xcnt, *xoff, *xtab;
+    uint32_t *xcnt, *xoff, *xtab, *lflags;
     float2 *xs;
     int64_t xcap;
 };

@@ -51,10 +51,71 @@ __host__ __device__ __forceinline__ int p2p_group_log2(uint32_t nt, int r) {
     return lw;
 }
 
+// Forward neighbours of a leaf in the pairwise near field (see below).
+__constant__ int8_t c_fwd[4][2] = {{1, 0}, {-1, 1}, {0, 1}, {1, 1}};
+
+// A pair of neighbouring leaves is evaluated pairwise when both hold at least
+// a warp's worth of blobs; with fewer, most lanes of the 64 x 32 tile would
+// idle, and the leaves' own warps sum that neighbour directly instead.  Both
+// leaves of a pair decide from the same two counts.
+constexpr uint32_t P2P_PAIR_MIN = 32;
+__host__ __device__ __forceinline__ bool pairwise(uint32_t na, uint32_t nb) {
+    return na >= P2P_PAIR_MIN && nb >= P2P_PAIR_MIN;
+}
+
+// A heavy pair is cut into pieces along A, each piece a run of whole
+// 128-target chunks holding at most P2P_PAIR_CAPU tiles of 128 targets x 32
+// sources, so that no single warp's item outlasts the average share of the
+// launch.  Piece 0 writes B's reaction to the pair's slot, piece i >= 1 to a
+// scratch run of nb entries; the final pass adds them in piece order.
+// Returns the number of pieces; *pc = targets per piece (a multiple of 128).
+constexpr uint64_t P2P_PAIR_CAPU = 256;
+__host__ __device__ __forceinline__ uint32_t pair_pieces(uint32_t na, uint32_t nb, uint32_t *pc) {
+    const uint32_t ca = (na + 127) / 128, cb = (nb + 31) / 32;
+    uint64_t np = (uint64_t(ca) * cb + P2P_PAIR_CAPU - 1) / P2P_PAIR_CAPU;
+    if (np > ca) np = ca;
+    if (np < 1) np = 1;
+    const uint32_t per = uint32_t((ca + np - 1) / np);
+    *pc = per * 128;
+    return (ca + per - 1) / per;
+}
+
+// count of the leaf (x, y), 0 outside the domain
+__device__ __forceinline__ uint32_t leaf_count(const uint32_t *st, int nside, int x, int y) {
+    if (x < 0 || y < 0 || x >= nside || y >= nside) return 0;
+    const uint32_t m = morton_key(uint32_t(x), uint32_t(y));
+    return st[m + 1] - st[m];
+}
+
+// Whether a leaf (n blobs, at ix, iy) has directed near-field work in the
+// pairwise mode: its own blobs when it is too small for the pair kernel, or
+// an occupied neighbour the pair kernel does not cover.
+__device__ __forceinline__ bool directed_work(const uint32_t *st, int nside, int ix, int iy,
+                                              uint32_t n) {
+    if (!pairwise(n, n)) return n > 0;
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const uint32_t nb = leaf_count(st, nside, ix + dx, iy + dy);
+            if (nb && !pairwise(n, nb)) return true;
+        }
+    return false;
+}
+
+// Per-leaf flags of the pairwise mode, read by the final pass: which result
+// slots hold this leaf's blobs' sums.
+enum : uint32_t {
+    LF_FWD = 1u,        // << k: pairs with forward neighbour k (slot k)
+    LF_BWD = 16u,       // << k: pairs with backward neighbour k (slot 4 + k)
+    LF_SPLIT = 256u,    // << k: ... cut into pieces, partial sums in the scratch
+    LF_SELF = 4096u,    // the leaf's own pairs (slot 8)
+    LF_DIRECTED = 8192u // directed items (own[])
+};
+
 __global__ void __launch_bounds__(256) k_p2p_count(const Task *__restrict__ tasks, int ntasks,
                                                    const InstDesc *__restrict__ insts,
                                                    const uint32_t *__restrict__ start, int tpi,
-                                                   uint32_t *__restrict__ cnt, uint32_t *ctrl) {
+                                                   int pairs_mode, uint32_t *__restrict__ cnt,
+                                                   uint32_t *ctrl) {
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
     const int64_t m = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
@@ -63,10 +124,12 @@ __global__ void __launch_bounds__(256) k_p2p_count(const Task *__restrict__ task
         const InstDesc &d = insts[t.inst];
         const uint32_t *st = start + d.soff;
         const uint32_t n = st[m + 1] - st[m];
-        cnt[d.loff + m] = (n + tpi - 1) / tpi;
+        const int nside = 1 << d.L;
+        const int ix = int(compact_bits(uint32_t(m))), iy = int(compact_bits(uint32_t(m) >> 1));
+        // pairwise mode: items only for the leaves with directed work
+        const bool work = pairs_mode ? directed_work(st, nside, ix, iy, n) : n > 0;
+        cnt[d.loff + m] = work ? (n + tpi - 1) / tpi : 0u;
         if (n) {
-            const int nside = 1 << d.L;
-            const int ix = int(compact_bits(uint32_t(m))), iy = int(compact_bits(uint32_t(m) >> 1));
             uint32_t src = 0;
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
@@ -167,11 +230,12 @@ static cudaError_t order_items(const P2POrder *order, uint4 *items, const uint32
 
 cudaError_t launch_p2p_worklist(const Task *tasks, int ntasks, int64_t nblocks,
                                 const InstDesc *insts, const uint32_t *start, int64_t nleaves,
-                                int tpi, uint32_t *cnt, uint32_t *off, uint32_t *scan_scratch,
-                                uint4 *items, uint32_t *ctrl, const P2POrder *order,
-                                cudaStream_t st, uint64_t *launches) {
+                                int tpi, int pairs_mode, uint32_t *cnt, uint32_t *off,
+                                uint32_t *scan_scratch, uint4 *items, uint32_t *ctrl,
+                                const P2POrder *order, cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    k_p2p_count<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, tpi, cnt, ctrl);
+    k_p2p_count<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, tpi, pairs_mode,
+                                                   cnt, ctrl);
     PF_LAUNCHED(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -208,42 +272,6 @@ __device__ __forceinline__ float g_of(const float (&a)[DEG + 1], float r2, float
         g = r2 < split ? g : ge;
     }
     return g;
-}
-
-// Forward neighbours of a leaf in the pairwise near field (see below).
-__constant__ int8_t c_fwd[4][2] = {{1, 0}, {-1, 1}, {0, 1}, {1, 1}};
-
-// A pair of neighbouring leaves is evaluated pairwise when both hold at least
-// a warp's worth of blobs; with fewer, most lanes of the 64 x 32 tile would
-// idle, and the leaves' own warps sum that neighbour directly instead.  Both
-// leaves of a pair decide from the same two counts.
-constexpr uint32_t P2P_PAIR_MIN = 32;
-__host__ __device__ __forceinline__ bool pairwise(uint32_t na, uint32_t nb) {
-    return na >= P2P_PAIR_MIN && nb >= P2P_PAIR_MIN;
-}
-
-// A heavy pair is cut into pieces along A, each piece a run of whole
-// 128-target chunks holding at most P2P_PAIR_CAPU tiles of 128 targets x 32
-// sources, so that no single warp's item outlasts the average share of the
-// launch.  Piece 0 writes B's reaction to the pair's slot, piece i >= 1 to a
-// scratch run of nb entries; the final pass adds them in piece order.
-// Returns the number of pieces; *pc = targets per piece (a multiple of 128).
-constexpr uint64_t P2P_PAIR_CAPU = 256;
-__host__ __device__ __forceinline__ uint32_t pair_pieces(uint32_t na, uint32_t nb, uint32_t *pc) {
-    const uint32_t ca = (na + 127) / 128, cb = (nb + 31) / 32;
-    uint64_t np = (uint64_t(ca) * cb + P2P_PAIR_CAPU - 1) / P2P_PAIR_CAPU;
-    if (np > ca) np = ca;
-    if (np < 1) np = 1;
-    const uint32_t per = uint32_t((ca + np - 1) / np);
-    *pc = per * 128;
-    return (ca + per - 1) / per;
-}
-
-// count of the leaf (x, y), 0 outside the domain
-__device__ __forceinline__ uint32_t leaf_count(const uint32_t *st, int nside, int x, int y) {
-    if (x < 0 || y < 0 || x >= nside || y >= nside) return 0;
-    const uint32_t m = morton_key(uint32_t(x), uint32_t(y));
-    return st[m + 1] - st[m];
 }
 
 // One source against the lane's two targets (a, b), both in the source
@@ -531,6 +559,7 @@ __global__ void __launch_bounds__(256) k_pair_emit(const Task *__restrict__ task
                                                    const uint32_t *__restrict__ xoff,
                                                    const uint32_t *__restrict__ ctrl,
                                                    int64_t xcap, uint32_t *__restrict__ xtab,
+                                                   uint32_t *__restrict__ lflags,
                                                    uint4 *__restrict__ items,
                                                    uint32_t *__restrict__ wclass) {
     const int ti = find_task(tasks, ntasks, blockIdx.x);
@@ -540,14 +569,30 @@ __global__ void __launch_bounds__(256) k_pair_emit(const Task *__restrict__ task
     const InstDesc &d = insts[t.inst];
     const uint32_t *st = start + d.soff;
     const uint32_t na = st[m + 1] - st[m];
-    if (na < P2P_PAIR_MIN) return;
     const int nside = 1 << d.L;
     const int ix = int(compact_bits(uint32_t(m))), iy = int(compact_bits(uint32_t(m) >> 1));
-    uint32_t o = off[d.loff + m], xb = xoff[d.loff + m];
     // the pieces' scratch runs exist only if all of them fit; else every pair
     // is one piece (decided alike for all pairs, so the result does not depend
     // on which fit)
     const bool split = int64_t(ctrl[CTRL_NXTRA]) <= xcap;
+    // this leaf's flags for the final pass
+    uint32_t fl = directed_work(st, nside, ix, iy, na) ? LF_DIRECTED : 0u;
+    if (na >= P2P_PAIR_MIN) {
+        fl |= LF_SELF;
+        for (int k = 0; k < 4; ++k) {
+            if (pairwise(na, leaf_count(st, nside, ix + c_fwd[k][0], iy + c_fwd[k][1])))
+                fl |= LF_FWD << k;
+            const uint32_t nbk = leaf_count(st, nside, ix - c_fwd[k][0], iy - c_fwd[k][1]);
+            if (pairwise(nbk, na)) {
+                fl |= LF_BWD << k;
+                uint32_t pc;
+                if (split && pair_pieces(nbk, na, &pc) > 1) fl |= LF_SPLIT << k;
+            }
+        }
+    }
+    lflags[d.loff + m] = fl;
+    if (na < P2P_PAIR_MIN) return;
+    uint32_t o = off[d.loff + m], xb = xoff[d.loff + m];
     for (int k = 0; k < 4; ++k) {
         const uint32_t nb = leaf_count(st, nside, ix + c_fwd[k][0], iy + c_fwd[k][1]);
         if (!pairwise(na, nb)) continue;
@@ -910,38 +955,41 @@ __global__ void __launch_bounds__(256) k_p2p_final(
         }
         w = make_float2(d.cfar * z.y, d.cfar * z.x);
     }
-    const float2 o = pb.own[r];
-    w.x += o.x;
-    w.y += o.y;
-    const uint32_t nme = st[m + 1] - st[m];
-    if (pb.part && nme >= P2P_PAIR_MIN) {
-        const uint32_t jme = uint32_t(r) - st[m];
-        const float2 sp = pb.part[8 * pb.nslot + r];  // the leaf's own pairs
+    // then the near-field parts this leaf has, in a fixed order
+    const uint32_t fl = pb.part ? pb.lflags[d.loff + m] : LF_DIRECTED;
+    if (fl & LF_DIRECTED) {
+        const float2 o = pb.own[r];
+        w.x += o.x;
+        w.y += o.y;
+    }
+    if (fl & LF_SELF) {
+        const float2 sp = pb.part[8 * pb.nslot + r];
         w.x += sp.x;
         w.y += sp.y;
-        for (int k = 0; k < 4; ++k) {
-            if (pairwise(nme, leaf_count(st, nside, ix + c_fwd[k][0], iy + c_fwd[k][1]))) {
-                const float2 p = pb.part[int64_t(k) * pb.nslot + r];
-                w.x += p.x;
-                w.y += p.y;
-            }
-            const int ax = ix - c_fwd[k][0], ay = iy - c_fwd[k][1];
-            const uint32_t na = leaf_count(st, nside, ax, ay);
-            if (!pairwise(na, nme)) continue;
-            const float2 p = pb.part[int64_t(4 + k) * pb.nslot + r];
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (fl & (LF_FWD << k)) {
+            const float2 p = pb.part[int64_t(k) * pb.nslot + r];
             w.x += p.x;
             w.y += p.y;
+        }
+        if (!(fl & (LF_BWD << k))) continue;
+        const float2 p = pb.part[int64_t(4 + k) * pb.nslot + r];
+        w.x += p.x;
+        w.y += p.y;
+        if (fl & (LF_SPLIT << k)) {
+            // pieces 1 .. of the pair (A = the backward neighbour, B = this leaf)
+            const int ax = ix - c_fwd[k][0], ay = iy - c_fwd[k][1];
+            const uint32_t na = leaf_count(st, nside, ax, ay), nme = st[m + 1] - st[m];
+            const uint32_t jme = uint32_t(r) - st[m];
             uint32_t pc;
             const uint32_t np = pair_pieces(na, nme, &pc);
-            if (np > 1) {
-                const uint32_t ma = morton_key(uint32_t(ax), uint32_t(ay));
-                const uint32_t base = pb.xtab[(d.loff + int64_t(ma)) * 4 + k];
-                if (base != 0xffffffffu)
-                    for (uint32_t i = 1; i < np; ++i) {
-                        const float2 x = pb.xs[base + int64_t(i - 1) * nme + jme];
-                        w.x += x.x;
-                        w.y += x.y;
-                    }
+            const uint32_t ma = morton_key(uint32_t(ax), uint32_t(ay));
+            const uint32_t base = pb.xtab[(d.loff + int64_t(ma)) * 4 + k];
+            for (uint32_t i = 1; i < np; ++i) {
+                const float2 x = pb.xs[base + int64_t(i - 1) * nme + jme];
+                w.x += x.x;
+                w.y += x.y;
             }
         }
     }
@@ -972,7 +1020,7 @@ cudaError_t launch_pair_worklist(const Task *tasks, int ntasks, int64_t nblocks,
     if (e != cudaSuccess) return e;
     uint4 *emit_to = order ? order->items_unsorted : items;
     k_pair_emit<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, off, pb.xoff, ctrl,
-                                                   pb.xcap, pb.xtab, emit_to,
+                                                   pb.xcap, pb.xtab, pb.lflags, emit_to,
                                                    order ? order->kA : nullptr);
     PF_LAUNCHED(1);
     if ((e = cudaGetLastError()) != cudaSuccess || !order) return e;
