@@ -184,8 +184,8 @@ struct PairBufs {
     float2 *xs;
     int64_t xcap;
 };
-// ... the item list (inst, leaf A, direction | piece << 3, scratch base;
-// direction 4: the leaf's own pairs),
+// ... the item list (inst, leaf A, direction | swap << 3 | piece << 4,
+// scratch base; direction 4: the leaf's own pairs),
 // ctrl[CTRL_NPAIRS] its count, ctrl[CTRL_NXTRA] the scratch entries wanted ...
 cudaError_t launch_pair_worklist(const Task *tasks, int ntasks, int64_t nblocks,
                                  const InstDesc *insts, const uint32_t *start, int64_t nleaves,

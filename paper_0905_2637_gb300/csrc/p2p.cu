@@ -543,6 +543,23 @@ __global__ void __launch_bounds__(256) k_pair_count(const Task *__restrict__ tas
 
 // items (inst, leaf A, direction d, 0) and their work class (targets x
 // sources, log2 in quarter steps, stored as 127 - class: heaviest first)
+// Estimated time of nt targets against ns sources in the pair kernel: the
+// target chunks it cuts (256/128/64/32, see pair_leaves) weighted by their
+// measured time per source step (8 packed, 4 packed, 2 and 1 targets per
+// lane: 10.3, 5.6, 3.4 and 2.5 relative units), times the source steps (32
+// per chunk of 32, 16 for a last chunk of at most 16).
+__device__ __forceinline__ uint32_t pair_cost(uint32_t nt, uint32_t ns) {
+    uint32_t c = 0;
+    for (uint32_t r = nt; r > 0;) {
+        if (r >= 192) { c += 103; r = r > 256 ? r - 256 : 0; }
+        else if (r >= 96) { c += 56; r = r > 128 ? r - 128 : 0; }
+        else if (r >= 33) { c += 34; r = r > 64 ? r - 64 : 0; }
+        else { c += 25; r = r > 32 ? r - 32 : 0; }
+    }
+    const uint32_t tail = ns & 31u;
+    return c * ((ns & ~31u) + (tail == 0 ? 0u : tail <= 16 ? 16u : 32u));
+}
+
 // work class of an item of `cost` (64-target chunk, 32-source chunk) tiles:
 // heaviest first = smallest class, quarter steps of log2
 __device__ __forceinline__ uint32_t pair_wclass(uint32_t cost) {
@@ -600,8 +617,11 @@ __global__ void __launch_bounds__(256) k_pair_emit(const Task *__restrict__ task
         const uint32_t np = pair_pieces(na, nb, &pc);
         const uint32_t base = split ? xb : 0xffffffffu;
         if (np > 1) xtab[(d.loff + m) * 4 + k] = base;
+        // a pair in one piece runs with the leaf that pads less as targets
+        const uint32_t swap = np == 1 && pair_cost(nb, na) < pair_cost(na, nb) ? 1u : 0u;
         for (uint32_t i = 0; i < np; ++i) {
-            items[o] = make_uint4(uint32_t(t.inst), uint32_t(m), uint32_t(k) | (i << 3), base);
+            items[o] = make_uint4(uint32_t(t.inst), uint32_t(m),
+                                  uint32_t(k) | (swap << 3) | (i << 4), base);
             if (wclass) {
                 // a warp spends 32 steps per (64-target chunk, 32-source chunk)
                 const uint32_t nt = split ? min(pc, na - i * pc) : (i ? 0u : na);
@@ -645,18 +665,121 @@ __device__ __forceinline__ void put2(float2 *p, float2 w, bool add) {
     *p = w;
 }
 
+// One pass of a source chunk around the warp: W = 32 sources, one per lane,
+// or W = 16 (a tail of at most 16 sources held by both half-warps, each half
+// rotating its own copy).  Each step every lane evaluates its TPL targets
+// against the source it holds, the source's reaction sum travelling with it;
+// after W steps every sum is back at its source's lane (for W = 16 the two
+// halves' sums are then added).
+template <int DEG, bool GENERAL, int TPL, int W>
+__device__ __forceinline__ void source_pass(const float (&tx)[TPL], const float (&ty)[TPL],
+                                            const float (&tg)[TPL], float (&u)[TPL],
+                                            float (&v)[TPL], const float (&a)[DEG + 1],
+                                            float kappa, float split, float xs, float ys,
+                                            float gs, float &bu, float &bv, int lane) {
+    const int next = (lane & ~(W - 1)) | ((lane + 1) & (W - 1));
+    bu = 0.f;
+    bv = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < W; ++k) {
+#pragma unroll
+        for (int t = 0; t < TPL; ++t)
+            pair_sym<DEG, GENERAL>(tx[t], ty[t], tg[t], xs, ys, gs, a, kappa, split, u[t], v[t], bu,
+                                   bv);
+        xs = __shfl_sync(0xffffffffu, xs, next);
+        ys = __shfl_sync(0xffffffffu, ys, next);
+        gs = __shfl_sync(0xffffffffu, gs, next);
+        bu = __shfl_sync(0xffffffffu, bu, next);
+        bv = __shfl_sync(0xffffffffu, bv, next);
+    }
+    if (W < 32) {
+        bu += __shfl_xor_sync(0xffffffffu, bu, 16);
+        bv += __shfl_xor_sync(0xffffffffu, bv, 16);
+    }
+}
+
+// The same pass with 2 H targets per lane held as H pairs and evaluated with
+// packed FP32x2 instructions (polynomial near-field factor only): the same
+// products per pair as source_pass, each packed instruction doing two of
+// them, so half the issue slots.  The reaction sums of a step run in the two
+// halves of a pair and are added before the source moves on.
+template <int DEG, int H, int W>
+__device__ __forceinline__ void source_pass_x2(const float2 (&tx)[H], const float2 (&ty)[H],
+                                               const float2 (&tg)[H], const float2 (&ntg)[H],
+                                               float2 (&u)[H], float2 (&v)[H],
+                                               const float2 (&a2)[DEG + 1], float xs, float ys,
+                                               float gs, float &bu, float &bv, int lane) {
+    const int next = (lane & ~(W - 1)) | ((lane + 1) & (W - 1));
+    bu = 0.f;
+    bv = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < W; ++k) {
+        // with K = (-dy, dx) g: u_a += g_s K, reaction u_b -= g_a K
+        const float2 nx = make_float2(-xs, -xs), ny = make_float2(-ys, -ys);
+        const float2 g2 = make_float2(gs, gs), ng2 = make_float2(-gs, -gs);
+        float2 bu2 = make_float2(bu, 0.f), bv2 = make_float2(bv, 0.f);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const float2 dx = __fadd2_rn(tx[h], nx), dy = __fadd2_rn(ty[h], ny);
+            const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+            float2 g = a2[DEG];
+#pragma unroll
+            for (int q = DEG - 1; q >= 0; --q) g = __ffma2_rn(g, r2, a2[q]);
+            const float2 py = __fmul2_rn(dy, g), px = __fmul2_rn(dx, g);
+            u[h] = __ffma2_rn(ng2, py, u[h]);
+            v[h] = __ffma2_rn(g2, px, v[h]);
+            bu2 = __ffma2_rn(tg[h], py, bu2);
+            bv2 = __ffma2_rn(ntg[h], px, bv2);
+        }
+        bu = bu2.x + bu2.y;
+        bv = bv2.x + bv2.y;
+        xs = __shfl_sync(0xffffffffu, xs, next);
+        ys = __shfl_sync(0xffffffffu, ys, next);
+        gs = __shfl_sync(0xffffffffu, gs, next);
+        bu = __shfl_sync(0xffffffffu, bu, next);
+        bv = __shfl_sync(0xffffffffu, bv, next);
+    }
+    if (W < 32) {
+        bu += __shfl_xor_sync(0xffffffffu, bu, 16);
+        bv += __shfl_xor_sync(0xffffffffu, bv, 16);
+    }
+}
+
+// Source chunk bc of B as seen by this lane: the source it starts with (in
+// A's frame; placeholders past the end) and whether the chunk is a tail of
+// at most 16 (half-warp pass).
+struct SourceSlot {
+    float xs, ys, gs;
+    uint32_t sb;
+    bool hs, half;
+};
+__device__ __forceinline__ SourceSlot source_slot(const float4 *__restrict__ rec, uint32_t b0,
+                                                  uint32_t bc, uint32_t nb, int ox, int oy,
+                                                  int lane) {
+    SourceSlot o;
+    o.half = nb - bc <= 16;
+    o.sb = bc + uint32_t(o.half ? (lane & 15) : lane);
+    o.hs = o.sb < nb;
+    const float4 s = o.hs ? rec[b0 + o.sb] : make_float4(-kPairFar, -kPairFar, 0.f, 0.f);
+    // B's centre is A's plus (ox, oy) leaves
+    o.xs = s.x + float(ox);
+    o.ys = s.y + float(oy);
+    o.gs = s.z;
+    return o;
+}
+
 // One chunk of a leaf pair: targets ac .. min(ac + 32 TPL, aend) - 1 of leaf A
 // (TPL per lane: lane + 32 t) against all nb sources of leaf B, B in chunks
-// of 32 sources travelling around the warp with their reaction sums.
-// fwd[i]: A's blob i from B; bwd[j]: B's blob j from A (bwd_add / fwd_add:
-// the chunk adds to them, else writes).
+// of 32 sources travelling around the warp with their reaction sums (a last
+// chunk of at most 16 in a half-warp pass).  fwd[i]: A's blob i from B;
+// bwd[j]: B's blob j from A (bwd_add / fwd_add: the chunk adds to them, else
+// writes).
 template <int DEG, bool GENERAL, int TPL>
 __device__ __noinline__ void pair_chunk(const float4 *__restrict__ rec, uint32_t a0,
-                                           uint32_t ac, uint32_t aend, uint32_t b0, uint32_t nb,
-                                           int ox, int oy, const float (&a)[DEG + 1],
-                                           float kappa, float split, float cn, float2 *fwd,
-                                           float2 *bwd, bool bwd_add, bool fwd_add, int lane) {
-    const int next = (lane + 1) & 31;
+                                        uint32_t ac, uint32_t aend, uint32_t b0, uint32_t nb,
+                                        int ox, int oy, const float (&a)[DEG + 1], float kappa,
+                                        float split, float cn, float2 *fwd, float2 *bwd,
+                                        bool bwd_add, bool fwd_add, int lane) {
     float tx[TPL], ty[TPL], tg[TPL], u[TPL], v[TPL];
 #pragma unroll
     for (int t = 0; t < TPL; ++t) {
@@ -669,26 +792,16 @@ __device__ __noinline__ void pair_chunk(const float4 *__restrict__ rec, uint32_t
         u[t] = v[t] = 0.f;
     }
     for (uint32_t bc = 0; bc < nb; bc += 32) {
-        const bool hs = bc + lane < nb;
-        const uint32_t sb = bc + lane;
-        const float4 s = hs ? rec[b0 + sb] : make_float4(-kPairFar, -kPairFar, 0.f, 0.f);
-        // the source in A's frame (B's centre is A's plus (ox, oy) leaves)
-        float xs = s.x + float(ox), ys = s.y + float(oy), gs = s.z;
-        float bu = 0.f, bv = 0.f;
-#pragma unroll 2
-        for (int k = 0; k < 32; ++k) {
-#pragma unroll
-            for (int t = 0; t < TPL; ++t)
-                pair_sym<DEG, GENERAL>(tx[t], ty[t], tg[t], xs, ys, gs, a, kappa, split, u[t], v[t],
-                                       bu, bv);
-            xs = __shfl_sync(0xffffffffu, xs, next);
-            ys = __shfl_sync(0xffffffffu, ys, next);
-            gs = __shfl_sync(0xffffffffu, gs, next);
-            bu = __shfl_sync(0xffffffffu, bu, next);
-            bv = __shfl_sync(0xffffffffu, bv, next);
-        }
-        // after 32 steps every travelling sum is back at its source's lane
-        if (hs) put2(bwd + sb, make_float2(cn * bu, cn * bv), bwd_add);
+        const SourceSlot ss = source_slot(rec, b0, bc, nb, ox, oy, lane);
+        float bu, bv;
+        if (ss.half)
+            source_pass<DEG, GENERAL, TPL, 16>(tx, ty, tg, u, v, a, kappa, split, ss.xs, ss.ys,
+                                               ss.gs, bu, bv, lane);
+        else
+            source_pass<DEG, GENERAL, TPL, 32>(tx, ty, tg, u, v, a, kappa, split, ss.xs, ss.ys,
+                                               ss.gs, bu, bv, lane);
+        if (ss.hs && (!ss.half || lane < 16))
+            put2(bwd + ss.sb, make_float2(cn * bu, cn * bv), bwd_add);
     }
 #pragma unroll
     for (int t = 0; t < TPL; ++t)
@@ -697,18 +810,13 @@ __device__ __noinline__ void pair_chunk(const float4 *__restrict__ rec, uint32_t
 }
 
 // The same chunk with 2 H targets per lane held as H pairs (targets lane +
-// 64 h and lane + 64 h + 32) and evaluated with packed FP32x2 instructions
-// (polynomial near-field factor only): the same products per pair as
-// pair_chunk, each packed instruction doing two of them, so half the issue
-// slots.  The reaction sums of a step run in the two halves of a pair and
-// are added before the source moves on.
+// 64 h and lane + 64 h + 32), evaluated by source_pass_x2.
 template <int DEG, int H>
 __device__ __noinline__ void pair_chunk_x2(const float4 *__restrict__ rec, uint32_t a0,
-                                              uint32_t ac, uint32_t aend, uint32_t b0,
-                                              uint32_t nb, int ox, int oy,
-                                              const float (&a)[DEG + 1], float cn, float2 *fwd,
-                                              float2 *bwd, bool bwd_add, bool fwd_add, int lane) {
-    const int next = (lane + 1) & 31;
+                                           uint32_t ac, uint32_t aend, uint32_t b0, uint32_t nb,
+                                           int ox, int oy, const float (&a)[DEG + 1], float cn,
+                                           float2 *fwd, float2 *bwd, bool bwd_add, bool fwd_add,
+                                           int lane) {
     float2 tx[H], ty[H], tg[H], ntg[H], u[H], v[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) {
@@ -725,39 +833,16 @@ __device__ __noinline__ void pair_chunk_x2(const float4 *__restrict__ rec, uint3
 #pragma unroll
     for (int k = 0; k <= DEG; ++k) a2[k] = make_float2(a[k], a[k]);
     for (uint32_t bc = 0; bc < nb; bc += 32) {
-        const bool hs = bc + lane < nb;
-        const uint32_t sb = bc + lane;
-        const float4 s = hs ? rec[b0 + sb] : make_float4(-kPairFar, -kPairFar, 0.f, 0.f);
-        float xs = s.x + float(ox), ys = s.y + float(oy), gs = s.z;
-        float bu = 0.f, bv = 0.f;
-#pragma unroll 2
-        for (int k = 0; k < 32; ++k) {
-            // with K = (-dy, dx) g: u_a += g_s K, reaction u_b -= g_a K
-            const float2 nx = make_float2(-xs, -xs), ny = make_float2(-ys, -ys);
-            const float2 g2 = make_float2(gs, gs), ng2 = make_float2(-gs, -gs);
-            float2 bu2 = make_float2(bu, 0.f), bv2 = make_float2(bv, 0.f);
-#pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const float2 dx = __fadd2_rn(tx[h], nx), dy = __fadd2_rn(ty[h], ny);
-                const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-                float2 g = a2[DEG];
-#pragma unroll
-                for (int q = DEG - 1; q >= 0; --q) g = __ffma2_rn(g, r2, a2[q]);
-                const float2 py = __fmul2_rn(dy, g), px = __fmul2_rn(dx, g);
-                u[h] = __ffma2_rn(ng2, py, u[h]);
-                v[h] = __ffma2_rn(g2, px, v[h]);
-                bu2 = __ffma2_rn(tg[h], py, bu2);
-                bv2 = __ffma2_rn(ntg[h], px, bv2);
-            }
-            bu = bu2.x + bu2.y;
-            bv = bv2.x + bv2.y;
-            xs = __shfl_sync(0xffffffffu, xs, next);
-            ys = __shfl_sync(0xffffffffu, ys, next);
-            gs = __shfl_sync(0xffffffffu, gs, next);
-            bu = __shfl_sync(0xffffffffu, bu, next);
-            bv = __shfl_sync(0xffffffffu, bv, next);
-        }
-        if (hs) put2(bwd + sb, make_float2(cn * bu, cn * bv), bwd_add);
+        const SourceSlot ss = source_slot(rec, b0, bc, nb, ox, oy, lane);
+        float bu, bv;
+        if (ss.half)
+            source_pass_x2<DEG, H, 16>(tx, ty, tg, ntg, u, v, a2, ss.xs, ss.ys, ss.gs, bu, bv,
+                                       lane);
+        else
+            source_pass_x2<DEG, H, 32>(tx, ty, tg, ntg, u, v, a2, ss.xs, ss.ys, ss.gs, bu, bv,
+                                       lane);
+        if (ss.hs && (!ss.half || lane < 16))
+            put2(bwd + ss.sb, make_float2(cn * bu, cn * bv), bwd_add);
     }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
@@ -848,10 +933,11 @@ __device__ __forceinline__ void self_leaf(const float4 *__restrict__ rec, uint32
     }
 }
 
-// One item of the pairwise near field: piece item.z >> 3 of leaf A (item.y)
-// with its forward neighbour item.z & 7 (4: the leaf's own pairs, to slot
-// 8); item.w = the pair's scratch base (all ones: the pair is not split,
-// piece 0 takes all of it).
+// One item of the pairwise near field: piece item.z >> 4 of leaf A (item.y)
+// with its forward neighbour B, direction item.z & 7 (4: the leaf's own
+// pairs, to slot 8); bit 3: B's blobs are the targets (a pair in one piece);
+// item.w = the pair's scratch base (all ones: the pair is not split, piece 0
+// takes all of it).
 template <int DEG, bool GENERAL>
 __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__restrict__ insts,
                                           const uint32_t *__restrict__ start,
@@ -865,7 +951,8 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
     const float kappa = d.kappa, split = d.qsplit_rho2, cn = d.cnear;
     const uint32_t m = item.y;
     const int dir = int(item.z & 7u);
-    const uint32_t piece = item.z >> 3;
+    const bool swap = (item.z >> 3) & 1u;
+    const uint32_t piece = item.z >> 4;
     const uint32_t *st = start + d.soff;
     const uint32_t a0 = st[m], na = st[m + 1] - a0;
     if (dir == 4) {
@@ -876,9 +963,14 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
     const int ox = c_fwd[dir][0], oy = c_fwd[dir][1];
     const uint32_t mb = morton_key(uint32_t(ix + ox), uint32_t(iy + oy));
     const uint32_t b0 = st[mb], nb = st[mb + 1] - b0;
-    uint32_t abeg = 0, aend = na;
     float2 *fwd = part + int64_t(dir) * nslot + a0;      // A's particles, from B
     float2 *bwd = part + int64_t(4 + dir) * nslot + b0;  // B's particles, from A
+    if (swap) {
+        pair_leaves<DEG, GENERAL>(rec, b0, 0, nb, a0, na, -ox, -oy, a, kappa, split, cn, bwd, fwd,
+                                  false, false, false, lane);
+        return;
+    }
+    uint32_t abeg = 0, aend = na;
     if (item.w != 0xffffffffu) {
         uint32_t pc;
         pair_pieces(na, nb, &pc);
