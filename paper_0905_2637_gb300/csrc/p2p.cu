@@ -756,6 +756,9 @@ struct SourceSlot {
 __device__ __forceinline__ SourceSlot source_slot(const float4 *__restrict__ rec, uint32_t b0,
                                                   uint32_t bc, uint32_t nb, int ox, int oy,
                                                   int lane) {
+    // the next chunk's records into L1 while this one is evaluated
+    if (bc + 32 + uint32_t(lane) < nb)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + b0 + bc + 32 + lane));
     SourceSlot o;
     o.half = nb - bc <= 16;
     o.sb = bc + uint32_t(o.half ? (lane & 15) : lane);
