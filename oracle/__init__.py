@@ -16,6 +16,11 @@ Every function cites the passage of the PetFMM paper it follows:
 * ``bin`` / ``sort`` / ``interaction_list`` -- the tree of Sec. 2.1 with the
                       z-order numbering of Sec. 5.1 and the interaction list
                       of Sec. 2.2 (at most 27 members, Table 1).
+* ``laplace_direct`` / ``laplace_fmm`` -- the second kernel (the Evaluator of
+                      Sec. 6.1 takes the kernel as a parameter): the 2D
+                      logarithmic potential sum_{j != i} q_j log|x_i - x_j|,
+                      directly and by the FMM of Sec. 2.2 with the series of
+                      the complex logarithm.
 """
 from __future__ import annotations
 
@@ -75,10 +80,18 @@ def _load():
         lib.orc_kernel_sigma.restype = None
         lib.orc_p2m.argtypes = [i64, P, P, P, f64, f64, i32, P]
         lib.orc_p2m.restype = None
-        for name in ("orc_m2m", "orc_m2l", "orc_l2l", "orc_l2p", "orc_me_eval"):
+        for name in ("orc_m2m", "orc_m2l", "orc_l2l", "orc_l2p", "orc_me_eval",
+                     "orc_lap_m2m", "orc_lap_m2l", "orc_lap_me_eval"):
             fn = getattr(lib, name)
             fn.argtypes = [i32, P, f64, f64, f64, f64, P]
             fn.restype = None
+        lib.orc_lap_p2m.argtypes = [i64, P, P, P, f64, f64, i32, P]
+        lib.orc_lap_p2m.restype = None
+        lib.orc_laplace_direct.argtypes = [i64, P, P, P, i64, P, P, i32]
+        lib.orc_laplace_direct.restype = None
+        lib.orc_laplace_fmm.argtypes = [i64, P, P, P, f64, f64, f64, i32, i32, i64, P, P, P, P,
+                                        i32]
+        lib.orc_laplace_fmm.restype = i32
         lib.orc_max_threads.argtypes = []
         lib.orc_max_threads.restype = i32
         _lib = lib
@@ -257,4 +270,69 @@ def me_eval(a, zc, z):
     w = np.zeros(2)
     lib.orc_me_eval(len(a), _ptr(a), complex(zc).real, complex(zc).imag, complex(z).real,
                     complex(z).imag, _ptr(w))
+    return complex(w[0], w[1])
+
+
+# --- second kernel: the 2D logarithmic potential -------------------------------------------
+
+def laplace_direct(x, y, q, targets=None, nthreads=0):
+    """L1: phi_i = sum_{j != i} q_j log|x_i - x_j| (coincident pairs excluded)."""
+    lib = _load()
+    x, y, q = _f64(x), _f64(y), _f64(q)
+    n = x.size
+    t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if t is None else t.size
+    phi = np.zeros(nt)
+    lib.orc_laplace_direct(n, _ptr(x), _ptr(y), _ptr(q), nt, _ptr(t), _ptr(phi), nthreads)
+    return phi
+
+
+def laplace_fmm(x, y, q, domain, L, p, targets=None, export=False, nthreads=0):
+    """L3: the potential by the FMM of Sec. 2.2 with logarithmic series (p
+    terms, the log counted as one).  ``export`` as for ``fmm``."""
+    lib = _load()
+    x, y, q = _f64(x), _f64(y), _f64(q)
+    n = x.size
+    t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if t is None else t.size
+    phi = np.zeros(nt)
+    me = le = None
+    if export:
+        if t is not None:
+            raise ValueError("export needs every particle as a target")
+        nbox = ((1 << (2 * (L + 1))) - 1) // 3
+        me = np.zeros((nbox, p), np.complex128)
+        le = np.zeros((nbox, p), np.complex128)
+    x0, y0, W = domain
+    rc = lib.orc_laplace_fmm(n, _ptr(x), _ptr(y), _ptr(q), x0, y0, W, L, p, nt, _ptr(t),
+                             _ptr(phi), _ptr(me), _ptr(le), nthreads)
+    _check(rc, "laplace_fmm")
+    if export:
+        return phi, me, le
+    return phi
+
+
+def lap_p2m(x, y, q, zc, p):
+    lib = _load()
+    x, y, q = _f64(x), _f64(y), _f64(q)
+    a = np.zeros(p, np.complex128)
+    lib.orc_lap_p2m(x.size, _ptr(x), _ptr(y), _ptr(q), complex(zc).real, complex(zc).imag, p,
+                    _ptr(a))
+    return a
+
+
+def lap_m2m(a, zc, zp):
+    return _op("orc_lap_m2m", len(a), a, complex(zc), complex(zp))
+
+
+def lap_m2l(a, zs, zt):
+    return _op("orc_lap_m2l", len(a), a, complex(zs), complex(zt))
+
+
+def lap_me_eval(a, zc, z):
+    lib = _load()
+    a = _c(a)
+    w = np.zeros(2)
+    lib.orc_lap_me_eval(len(a), _ptr(a), complex(zc).real, complex(zc).imag, complex(z).real,
+                        complex(z).imag, _ptr(w))
     return complex(w[0], w[1])

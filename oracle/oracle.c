@@ -564,3 +564,266 @@ done:
     free(me); free(le); free(need);
     return rc;
 }
+
+/* ================================================================== */
+/* Second kernel: the 2D logarithmic (Laplace) potential.              */
+/*                                                                     */
+/* The paper's Evaluator is templated over a Kernel object that        */
+/* supplies the expansions and translation operators (Sec. 6.1), and   */
+/* names other kernels as the first extensions (Sec. 8).  This is the  */
+/* classic one for the same tree, interaction lists and sweeps:        */
+/*                                                                     */
+/*   phi(x_i) = sum_{j != i} q_j log |x_i - x_j|                        */
+/*            = Re sum_{j != i} q_j log(z_i - z_j),   z = x + i y.      */
+/*                                                                     */
+/* Readings:                                                           */
+/*   - p terms per expansion, the logarithm counted as one of them:    */
+/*       ME about zc: Phi(z) = a_0 log(z - zc) + sum_{k=1}^{p-1} a_k / (z - zc)^k */
+/*       LE about zl: Phi(z) = sum_{m=0}^{p-1} b_m (z - zl)^m           */
+/*     The series are those of the complex logarithm, written out from */
+/*     log(z - zj) = log(z - zc) + log(1 - (zj - zc)/(z - zc)).         */
+/*   - The potential is Re Phi; the imaginary part (a branch-dependent */
+/*     harmonic conjugate) is never used.                               */
+/*   - Self pairs and coincident pairs contribute 0 (log 0 excluded),  */
+/*     like the coincident pairs of the vortex kernel.                 */
+/*   - No regularisation: the near field is the same sum evaluated     */
+/*     directly.                                                        */
+/* ================================================================== */
+
+/* L1: direct sum. */
+void orc_laplace_direct(int64_t n, const double *x, const double *y, const double *q,
+                        int64_t nt, const int64_t *targets, double *phi, int nthreads) {
+    set_threads(nthreads);
+    if (targets == NULL) nt = n;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets ? targets[t] : t;
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = x[i] - x[j], dy = y[i] - y[j];
+            double r2 = dx * dx + dy * dy;
+            if (r2 == 0.0) continue;
+            s += q[j] * 0.5 * log(r2);
+        }
+        phi[t] = s;
+    }
+}
+
+/* P2M: a_0 = sum_j q_j, a_k = -sum_j q_j (z_j - zc)^k / k (k >= 1). */
+static void lap_p2m(int64_t n, const double *x, const double *y, const double *q,
+                    const uint32_t *idx, cplx zc, int p, cplx *a) {
+    for (int k = 0; k < p; ++k) a[k] = 0.0;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t j = idx ? idx[t] : t;
+        cplx d = (x[j] + I * y[j]) - zc;
+        a[0] += q[j];
+        cplx pw = q[j];
+        for (int k = 1; k < p; ++k) {
+            pw *= d;
+            a[k] -= pw / (double)k;
+        }
+    }
+}
+
+/* M2M: ME about zc -> ME about zp, d = zc - zp:
+ *   out_0 = a_0,
+ *   out_l = -a_0 d^l / l + sum_{k=1}^{l} C(l-1, k-1) a_k d^(l-k)   (l >= 1). */
+static void lap_m2m(int p, const cplx *a, cplx zc, cplx zp, cplx *out) {
+    cplx d = zc - zp;
+    cplx dpow[81];
+    dpow[0] = 1.0;
+    for (int i = 1; i < p; ++i) dpow[i] = dpow[i - 1] * d;
+    out[0] = a[0];
+    for (int l = 1; l < p; ++l) {
+        cplx s = -a[0] * dpow[l] / (double)l;
+        for (int k = 1; k <= l; ++k) s += binom(l - 1, k - 1) * a[k] * dpow[l - k];
+        out[l] = s;
+    }
+}
+
+/* M2L: ME about zs -> LE about zt, d = zs - zt:
+ *   b_0 = a_0 log(-d) + sum_{k>=1} (-1)^k a_k d^-k,
+ *   b_m = -a_0 / (m d^m) + sum_{k>=1} (-1)^k C(m+k-1, k-1) a_k d^-(k+m)   (m >= 1). */
+static void lap_m2l(int p, const cplx *a, cplx zs, cplx zt, cplx *b) {
+    cplx d = zs - zt;
+    cplx inv = 1.0 / d;
+    cplx ipow[81];
+    ipow[0] = 1.0;
+    for (int i = 1; i <= 2 * p; ++i) ipow[i] = ipow[i - 1] * inv;
+    cplx s0 = a[0] * clog(-d);
+    for (int k = 1; k < p; ++k) s0 += ((k % 2) ? -1.0 : 1.0) * a[k] * ipow[k];
+    b[0] = s0;
+    for (int m = 1; m < p; ++m) {
+        cplx s = -a[0] * ipow[m] / (double)m;
+        for (int k = 1; k < p; ++k)
+            s += ((k % 2) ? -1.0 : 1.0) * binom(m + k - 1, k - 1) * a[k] * ipow[k + m];
+        b[m] = s;
+    }
+}
+
+/* Direct evaluation of a Laplace multipole expansion (for pins). */
+static cplx lap_me_eval(int p, const cplx *a, cplx zc, cplx z) {
+    cplx inv = 1.0 / (z - zc), pw = inv, w = a[0] * clog(z - zc);
+    for (int k = 1; k < p; ++k) {
+        w += a[k] * pw;
+        pw *= inv;
+    }
+    return w;
+}
+
+/* Exposed single operators (interleaved re/im arrays of p complex values;
+ * the local-expansion shift and evaluation are the orc_l2l / orc_l2p above). */
+void orc_lap_p2m(int64_t n, const double *x, const double *y, const double *q,
+                 double zc_re, double zc_im, int p, double *a_out) {
+    lap_p2m(n, x, y, q, NULL, zc_re + I * zc_im, p, (cplx *)a_out);
+}
+void orc_lap_m2m(int p, const double *a, double zc_re, double zc_im, double zp_re,
+                 double zp_im, double *out) {
+    lap_m2m(p, (const cplx *)a, zc_re + I * zc_im, zp_re + I * zp_im, (cplx *)out);
+}
+void orc_lap_m2l(int p, const double *a, double zs_re, double zs_im, double zt_re,
+                 double zt_im, double *b_out) {
+    lap_m2l(p, (const cplx *)a, zs_re + I * zs_im, zt_re + I * zt_im, (cplx *)b_out);
+}
+void orc_lap_me_eval(int p, const double *a, double zc_re, double zc_im, double z_re,
+                     double z_im, double *w_out) {
+    cplx w = lap_me_eval(p, (const cplx *)a, zc_re + I * zc_im, z_re + I * z_im);
+    w_out[0] = creal(w);
+    w_out[1] = cimag(w);
+}
+
+/* L3: FMM of the potential, same binning, sort, interaction lists and sweeps
+ * as O3 (Sec. 2.2), with the operators above; targets / exports as in
+ * orc_fmm. */
+int orc_laplace_fmm(int64_t n, const double *x, const double *y, const double *q,
+                    double x0, double y0, double W, int L, int p, int64_t nt,
+                    const int64_t *targets, double *phi, double *me_out, double *le_out,
+                    int nthreads) {
+    if (L < 0 || L > 13 || p < 1 || p > 40 || !(W > 0.0) || n < 0) return ORC_EINVAL;
+    set_threads(nthreads);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    const int64_t nleaf = (int64_t)1 << (2 * L);
+    const int64_t nbox = level_offset(L + 1);
+    uint32_t *ix = (uint32_t *)malloc(sizeof(uint32_t) * nn);
+    uint32_t *iy = (uint32_t *)malloc(sizeof(uint32_t) * nn);
+    uint32_t *key = (uint32_t *)malloc(sizeof(uint32_t) * nn);
+    uint32_t *perm = (uint32_t *)malloc(sizeof(uint32_t) * nn);
+    uint32_t *start = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nleaf + 1));
+    cplx *me = (cplx *)calloc((size_t)nbox * (size_t)p, sizeof(cplx));
+    cplx *le = (cplx *)calloc((size_t)nbox * (size_t)p, sizeof(cplx));
+    unsigned char *need = (unsigned char *)calloc((size_t)nbox, 1);
+    int rc = ORC_OK;
+    if (!ix || !iy || !key || !perm || !start || !me || !le || !need) { rc = ORC_ENOMEM; goto done; }
+
+    rc = orc_bin(n, x, y, x0, y0, W, L, ix, iy, key);
+    if (rc != ORC_OK) goto done;
+    rc = orc_sort(n, key, L, perm, start);
+    if (rc != ORC_OK) goto done;
+
+    if (targets == NULL) {
+        memset(need, 1, (size_t)nbox);
+    } else {
+        for (int64_t t = 0; t < nt; ++t) {
+            uint32_t m = key[targets[t]];
+            for (int l = L; l >= 0; --l) need[level_offset(l) + (m >> (2 * (L - l)))] = 1;
+        }
+    }
+
+    /* upward sweep: P2M at the leaves, M2M to the root */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t m = 0; m < nleaf; ++m) {
+        uint32_t bx, by;
+        deinterleave((uint32_t)m, L, &bx, &by);
+        cplx zc = box_centre(L, bx, by, x0, y0, W);
+        lap_p2m((int64_t)(start[m + 1] - start[m]), x, y, q, perm + start[m], zc, p,
+                me + (level_offset(L) + m) * p);
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        int64_t nl = (int64_t)1 << (2 * l);
+#pragma omp parallel for schedule(static)
+        for (int64_t m = 0; m < nl; ++m) {
+            uint32_t bx, by;
+            deinterleave((uint32_t)m, l, &bx, &by);
+            cplx zp = box_centre(l, bx, by, x0, y0, W);
+            cplx *dst = me + (level_offset(l) + m) * p;
+            cplx tmp[40];
+            for (int c = 0; c < 4; ++c) {
+                int64_t child = 4 * m + c;
+                uint32_t cx, cy;
+                deinterleave((uint32_t)child, l + 1, &cx, &cy);
+                cplx zc = box_centre(l + 1, cx, cy, x0, y0, W);
+                lap_m2m(p, me + (level_offset(l + 1) + child) * p, zc, zp, tmp);
+                for (int k = 0; k < p; ++k) dst[k] += tmp[k];
+            }
+        }
+    }
+
+    /* downward sweep, levels 2..L: M2L over the interaction list, L2L */
+    for (int l = 2; l <= L; ++l) {
+        int64_t nl = (int64_t)1 << (2 * l);
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t m = 0; m < nl; ++m) {
+            if (!need[level_offset(l) + m]) continue;
+            uint32_t bx, by;
+            deinterleave((uint32_t)m, l, &bx, &by);
+            cplx zt = box_centre(l, bx, by, x0, y0, W);
+            cplx *dst = le + (level_offset(l) + m) * p;
+            int32_t il[2 * 27];
+            int cnt = orc_interaction_list(l, (int)bx, (int)by, il);
+            cplx tmp[40];
+            for (int s = 0; s < cnt; ++s) {
+                uint32_t sx = (uint32_t)il[2 * s], sy = (uint32_t)il[2 * s + 1];
+                uint32_t sm = interleave(sx, sy, l);
+                cplx zs = box_centre(l, sx, sy, x0, y0, W);
+                lap_m2l(p, me + (level_offset(l) + sm) * p, zs, zt, tmp);
+                for (int k = 0; k < p; ++k) dst[k] += tmp[k];
+            }
+            if (l >= 3) {
+                uint32_t pm = (uint32_t)m >> 2, pbx, pby;
+                deinterleave(pm, l - 1, &pbx, &pby);
+                cplx zp = box_centre(l - 1, pbx, pby, x0, y0, W);
+                l2l(p, le + (level_offset(l - 1) + pm) * p, zp, zt, tmp);
+                for (int k = 0; k < p; ++k) dst[k] += tmp[k];
+            }
+        }
+    }
+
+    /* evaluation: Re of the leaf's LE plus the near-field direct sum */
+    {
+        int64_t ntt = targets ? nt : n;
+        uint32_t nside = 1u << L;
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t t = 0; t < ntt; ++t) {
+            int64_t i = targets ? targets[t] : t;
+            uint32_t m = key[i];
+            cplx zl = box_centre(L, ix[i], iy[i], x0, y0, W);
+            double s = creal(l2p(p, le + (level_offset(L) + m) * p, zl, x[i] + I * y[i]));
+            double nf = 0.0;
+            for (int dy = -1; dy <= 1; ++dy) {
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t sx = (int64_t)ix[i] + dx, sy = (int64_t)iy[i] + dy;
+                    if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
+                    uint32_t sm = interleave((uint32_t)sx, (uint32_t)sy, L);
+                    for (uint32_t r = start[sm]; r < start[sm + 1]; ++r) {
+                        uint32_t j = perm[r];
+                        if ((int64_t)j == i) continue;
+                        double ddx = x[i] - x[j], ddy = y[i] - y[j];
+                        double r2 = ddx * ddx + ddy * ddy;
+                        if (r2 == 0.0) continue;
+                        nf += q[j] * 0.5 * log(r2);
+                    }
+                }
+            }
+            phi[t] = s + nf;
+        }
+    }
+
+    if (me_out) memcpy(me_out, me, sizeof(cplx) * (size_t)nbox * (size_t)p);
+    if (le_out) memcpy(le_out, le, sizeof(cplx) * (size_t)nbox * (size_t)p);
+
+done:
+    free(ix); free(iy); free(key); free(perm); free(start);
+    free(me); free(le); free(need);
+    return rc;
+}
