@@ -28,7 +28,8 @@ MUTANTS = {
     "p2m_power_off_by_one": ("            a[k] += pw;\n            pw *= d;", "            pw *= d;\n            a[k] += pw;"),
     "il_keeps_neighbours": ("if (abs(sx - ix) <= 1 && abs(sy - iy) <= 1) continue;",
                             "if (abs(sx - ix) <= 0 && abs(sy - iy) <= 0) continue;"),
-    "l2l_missing_level": ("            if (l >= 3) {", "            if (l >= 4) {"),
+    "l2l_missing_level": ("                m2l(p, me + (level_offset(l) + sm) * p, zs, zt, tmp);\n                for (int k = 0; k < p; ++k) dst[k] += tmp[k];\n            }\n            if (l >= 3) {",
+                          "                m2l(p, me + (level_offset(l) + sm) * p, zs, zt, tmp);\n                for (int k = 0; k < p; ++k) dst[k] += tmp[k];\n            }\n            if (l >= 4) {"),
     "l2p_re_im_swapped": ("double su = cimag(w) / (2.0 * ORC_PI);\n            double sv = creal(w) / (2.0 * ORC_PI);",
                           "double su = creal(w) / (2.0 * ORC_PI);\n            double sv = cimag(w) / (2.0 * ORC_PI);"),
     "near_column_dropped": ("                for (int dx = -1; dx <= 1; ++dx) {\n                    int64_t sx",
