@@ -32,8 +32,8 @@ MUTANTS = {
                           "                m2l(p, me + (level_offset(l) + sm) * p, zs, zt, tmp);\n                for (int k = 0; k < p; ++k) dst[k] += tmp[k];\n            }\n            if (l >= 4) {"),
     "l2p_re_im_swapped": ("double su = cimag(w) / (2.0 * ORC_PI);\n            double sv = creal(w) / (2.0 * ORC_PI);",
                           "double su = creal(w) / (2.0 * ORC_PI);\n            double sv = cimag(w) / (2.0 * ORC_PI);"),
-    "near_column_dropped": ("                for (int dx = -1; dx <= 1; ++dx) {\n                    int64_t sx",
-                            "                for (int dx = -1; dx <= 0; ++dx) {\n                    int64_t sx"),
+    "near_column_dropped": ("            double nu = 0.0, nv = 0.0;\n            for (int dy = -1; dy <= 1; ++dy) {\n                for (int dx = -1; dx <= 1; ++dx) {",
+                            "            double nu = 0.0, nv = 0.0;\n            for (int dy = -1; dy <= 1; ++dy) {\n                for (int dx = -1; dx <= 0; ++dx) {"),
     "kernel_width": ("-expm1(-r2 / (2.0 * sigma * sigma))", "-expm1(-r2 / (sigma * sigma))"),
     "kernel_sign": ("    *ku = -dy * f;\n    *kv = dx * f;\n}\n\n/* Singular", "    *ku = dy * f;\n    *kv = -dx * f;\n}\n\n/* Singular"),
     "binning_ceil": ("    double f = floor(s);", "    double f = ceil(s) - 1.0;"),
