@@ -265,7 +265,7 @@ enum {
                                   arrays may change) and replayed while it repeats;
                                   0 (default) plain launches.  Results are identical.
                                   The context's stream must not be capturing. */
-    PETFMM_OPT_P2P_PAIRS = 11  /* mixed path: 1 (default) each pair of blobs in the same
+    PETFMM_OPT_P2P_PAIRS = 11, /* mixed path: 1 (default) each pair of blobs in the same
                                   or neighbouring leaves that both hold >= 32 blobs is
                                   evaluated once, its kernel value serving both blobs
                                   (K of Eq. 8 is odd);
@@ -274,7 +274,18 @@ enum {
                                   deterministic; they differ by FP32 rounding of the
                                   sums.  Extra device memory in mode 1: 88 bytes per
                                   blob and 28 per leaf. */
+    PETFMM_OPT_KERNEL = 12     /* the sum the context evaluates (the kernel parameter of
+                                  the paper's Evaluator, Sec. 6.1):
+                                  PETFMM_KERNEL_VORTEX (default) the blob velocity of
+                                  Eq. 8/9; PETFMM_KERNEL_LAPLACE the 2D logarithmic
+                                  potential u_i = sum_{j != i} g_j log|x_i - x_j|
+                                  (coincident pairs excluded; sigma unused), v = 0,
+                                  by the same FMM with the series of the complex
+                                  logarithm (p terms, the log counted as one).  The
+                                  Laplace kernel needs PETFMM_FP64 (an evaluation of
+                                  a mixed context returns PETFMM_EINVAL). */
 };
+enum { PETFMM_KERNEL_VORTEX = 0, PETFMM_KERNEL_LAPLACE = 1 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
 
 /* Stages reported by petfmm_stage_times (milliseconds, last evaluation).

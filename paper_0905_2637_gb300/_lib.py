@@ -24,7 +24,8 @@ PETFMM_FP64, PETFMM_MIXED = 0, 1
 PETFMM_F64, PETFMM_F32 = 0, 1
 PETFMM_OPT_TIMING, PETFMM_OPT_SPIN_LIMIT, PETFMM_OPT_P2P_MODE, PETFMM_OPT_POISON = 1, 2, 3, 4
 PETFMM_OPT_M2L_TC, PETFMM_OPT_TC_DENSE, PETFMM_OPT_TC_SEG, PETFMM_OPT_NEAR_TOL = 5, 6, 8, 9
-PETFMM_OPT_GRAPH, PETFMM_OPT_P2P_PAIRS = 10, 11
+PETFMM_OPT_GRAPH, PETFMM_OPT_P2P_PAIRS, PETFMM_OPT_KERNEL = 10, 11, 12
+PETFMM_KERNEL_VORTEX, PETFMM_KERNEL_LAPLACE = 0, 1
 STAGES = ("morton", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "worklist", "pairs", "p2p")
 
 
@@ -232,7 +233,8 @@ def _dev_ptr(t, dtype, n, name):
 class Context:
     """One FMM configuration bound to a CUDA stream (``petfmm_create``)."""
 
-    def __init__(self, domain, levels, order, sigma, precision="mixed", dtype="f32", stream=None):
+    def __init__(self, domain, levels, order, sigma, precision="mixed", dtype="f32", stream=None,
+                 kernel="vortex"):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -243,6 +245,9 @@ class Context:
         self.domain, self.levels, self.order, self.sigma = tuple(domain), levels, order, sigma
         self.handle = petfmm_create(domain, levels, order, sigma, self.precision, self.dtype_code,
                                     ctypes.c_void_p(self.stream.cuda_stream))
+        if kernel != "vortex":
+            self.set_option(PETFMM_OPT_KERNEL,
+                            {"laplace": PETFMM_KERNEL_LAPLACE}[kernel])
 
     def close(self):
         if self.handle is not None:

@@ -37,6 +37,12 @@ constexpr int ST_EDOMAIN = -3;
 constexpr int ST_ETIMEOUT = -5;
 
 // One FMM problem of a batch.
+// The kernels an evaluation can sum (the Evaluator of Sec. 6.1 is
+// parameterised by its kernel): the Gaussian-regularised Biot-Savart
+// velocity of Eq. 8/9, and the 2D logarithmic potential
+// phi_i = sum_{j != i} q_j log|x_i - x_j|.
+enum { KERNEL_VORTEX = 0, KERNEL_LAPLACE = 1 };
+
 struct InstDesc {
     double x0, y0, width;   // domain square
     double scale;           // 2^L / width (computed once on the host)
@@ -49,7 +55,7 @@ struct InstDesc {
     int64_t loff;           // first leaf of this instance in batch leaf arrays
     int64_t eoff;           // first box of this instance in ME/LE (box units)
     uint32_t key_hi;        // composite sort key = key_hi | Morton key
-    int pad0;
+    int kernel;             // KERNEL_VORTEX or KERNEL_LAPLACE
     const void *x, *y, *g;  // caller's arrays (storage type of the context)
     void *u, *v;
     const void *t_m2m, *t_l2l, *t_m2l;  // operator tables for this p (path's real type)
@@ -72,6 +78,8 @@ struct InstDesc {
     double inv2s2;          // 1 / (2 sigma^2)
     double cnear64;         // 1 / (2 pi)
     double cfar64;          // 1 / (2 pi w)
+    double logw0;           // Laplace kernel: log(domain width); level l boxes are
+                            // log(width) - l log 2 wide in log scale
     // float-float copies of the domain: x0 = x0h + x0l, y0 = y0h + y0l,
     // scale = sh + sl (binning shortcut and leaf-relative coordinates in FP32)
     float x0h, x0l, y0h, y0l, sh, sl;
@@ -90,6 +98,7 @@ inline void inst_set_domain(InstDesc &d, double x0, double y0, double width, int
     d.y0l = float(y0 - double(d.y0h));
     d.sh = float(d.scale);
     d.sl = float(d.scale - double(d.sh));
+    d.logw0 = std::log(width);
 }
 
 // A range of work units of one kind, for one instance (and level).

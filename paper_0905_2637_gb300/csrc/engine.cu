@@ -105,6 +105,7 @@ struct petfmm_ctx {
     bool timing = false;
     int p2p_mode = 0;  // 0: work items heaviest first (Eq. 14 weights), 1: Morton order
     bool p2p_pairs = true;  // mixed path: neighbouring leaves pairwise (PETFMM_OPT_P2P_PAIRS)
+    int kernel = KERNEL_VORTEX;  // PETFMM_OPT_KERNEL
     bool poison = false;
     bool m2l_tc = true;
     // measured on GB300 (clustered 16M and lattice 1M blobs): 128-cell units
@@ -294,17 +295,18 @@ void fill_p2p_constants(InstDesc &d, double tol) {
     cache[key] = f;
 }
 
-OpTables *get_tables(petfmm_ctx *c, int p, int *err) {
-    auto it = c->tables.find(p);
+OpTables *get_tables(petfmm_ctx *c, int p, int kernel, int *err) {
+    const int key = p | (kernel << 16);
+    auto it = c->tables.find(key);
     if (it != c->tables.end()) return &it->second;
     OpTables t;
-    cudaError_t e = build_op_tables(p, &t);
+    cudaError_t e = build_op_tables(p, kernel, &t);
     if (e != cudaSuccess) {
         free_op_tables(&t);
         *err = cuda_status(e);
         return nullptr;
     }
-    return &(c->tables[p] = t);
+    return &(c->tables[key] = t);
 }
 
 void add_task(TaskRange &r, int inst, int level, int64_t count, int64_t per_block) {
@@ -457,7 +459,7 @@ int build_plan(int precision, bool use_tc, int tc_segmax, double near_tol,
 int attach_tables(petfmm_ctx *c, Plan &pl) {
     for (InstDesc &d : pl.inst) {
         int err = PETFMM_OK;
-        OpTables *t = get_tables(c, d.p, &err);
+        OpTables *t = get_tables(c, d.p, c->kernel, &err);
         if (!t) return err;
         if (c->precision == PETFMM_FP64) {
             d.t_m2m = t->m2m64; d.t_l2l = t->l2l64; d.t_m2l = t->m2l64;
@@ -537,7 +539,7 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     k.put(pl.nbits); k.put(pl.pmax); k.put(pl.tile_pmax); k.put(pl.deg); k.put(pl.general);
     k.put(pl.tc_smem); k.put(grid);
     k.put(c->precision); k.put(c->dtype); k.put(c->timing); k.put(c->p2p_mode); k.put(c->poison);
-    k.put(c->tc_dense_pct); k.put(c->spin_limit); k.put(c->p2p_pairs);
+    k.put(c->tc_dense_pct); k.put(c->spin_limit); k.put(c->p2p_pairs); k.put(c->kernel);
     for (const DevBuf *b : {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                             &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
                             &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount,
@@ -558,7 +560,10 @@ void stage_mark(petfmm_ctx *c, int stage) {
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     Plan &pl = c->plan;
+    // the Laplace kernel has the FP64 path only
+    if (c->kernel == KERNEL_LAPLACE && c->precision != PETFMM_FP64) return PETFMM_EINVAL;
     PF_TRY(build_plan(c->precision, c->m2l_tc, c->tc_segmax, c->near_tol, probs, pl));
+    for (InstDesc &d : pl.inst) d.kernel = c->kernel;
     PF_TRY(attach_tables(c, pl));
     cudaStream_t st = c->stream;  // the launch sequence's stream (a capture swaps it)
     const bool mixed = c->precision == PETFMM_MIXED;
@@ -925,7 +930,7 @@ int petfmm_create(const petfmm_domain *dom, int levels, int order, double sigma,
         }
     }
     int err = PETFMM_OK;
-    if (!get_tables(c, order, &err)) {
+    if (!get_tables(c, order, KERNEL_VORTEX, &err)) {
         petfmm_destroy(c);
         return err;
     }
@@ -1102,6 +1107,11 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
             return PETFMM_OK;
         case PETFMM_OPT_GRAPH: c->use_graph = value != 0; return PETFMM_OK;
         case PETFMM_OPT_P2P_PAIRS: c->p2p_pairs = value != 0; return PETFMM_OK;
+        case PETFMM_OPT_KERNEL:
+            if (value != PETFMM_KERNEL_VORTEX && value != PETFMM_KERNEL_LAPLACE)
+                return PETFMM_EINVAL;
+            c->kernel = int(value);
+            return PETFMM_OK;
         case PETFMM_OPT_NEAR_TOL:
             if (value < 1 || value > 1000000) return PETFMM_EINVAL;
             c->near_tol = double(value) * 1e-9;

@@ -172,15 +172,111 @@ static void host_l2l_table(int p, double *out /* [c][n][m] */) {
     }
 }
 
-cudaError_t build_op_tables(int p, OpTables *t) {
+// Laplace kernel (log potential), rescaled like the Cauchy series: ME
+// a~_0 = a_0, a~_k = a_k / w^k; LE b^_m = b_m w^m (w the box width).  With
+// e the child centre's offset from the parent's in child widths and delta the
+// source centre's offset from the target's in box widths, the translations
+// do not depend on the level, except the constant of M2L, whose a_0 log w
+// term the M2L kernel adds.
+//   M2M  [c][l][k]: l = 0: a~_0; l >= 1: -a~_0 e^l / (l 2^l)
+//                   + sum_{1<=k<=l} C(l-1, k-1) e^(l-k) 2^-l a~_k
+//   L2L  [c][n][m]: C(m, n) e^(m-n) 2^-m, m >= n
+//   M2L  [op][k][m]: k = 0: m = 0 log(-delta), m >= 1 -1 / (m delta^m);
+//                   k >= 1: (-1)^k C(m+k-1, k-1) / delta^(k+m)
+static void host_lap_m2m_table(int p, double *out /* [c][l][k] */) {
+    std::vector<double> C = binomials(p);
+    for (int c = 0; c < 4; ++c) {
+        const HC e = {(c & 1) - 0.5, (c >> 1) - 0.5};
+        std::vector<HC> ep(size_t(p + 1));
+        ep[0] = {1.0, 0.0};
+        for (int i = 1; i <= p; ++i) ep[i] = hmul(ep[i - 1], e);
+        for (int l = 0; l < p; ++l)
+            for (int k = 0; k < p; ++k) {
+                double *o = out + ((size_t(c) * p + l) * p + k) * 2;
+                o[0] = o[1] = 0.0;
+                if (k > l) continue;
+                if (l == 0) {
+                    o[0] = 1.0;
+                } else if (k == 0) {
+                    const double s = -std::ldexp(1.0, -l) / double(l);
+                    o[0] = s * ep[l].re;
+                    o[1] = s * ep[l].im;
+                } else {
+                    const double s = std::ldexp(C[size_t(l - 1) * (p + 1) + k - 1], -l);
+                    o[0] = s * ep[l - k].re;
+                    o[1] = s * ep[l - k].im;
+                }
+            }
+    }
+}
+
+static void host_lap_l2l_table(int p, double *out /* [c][n][m] */) {
+    std::vector<double> C = binomials(p);
+    for (int c = 0; c < 4; ++c) {
+        const HC e = {(c & 1) - 0.5, (c >> 1) - 0.5};
+        std::vector<HC> ep(size_t(p + 1));
+        ep[0] = {1.0, 0.0};
+        for (int i = 1; i <= p; ++i) ep[i] = hmul(ep[i - 1], e);
+        for (int n = 0; n < p; ++n)
+            for (int m = 0; m < p; ++m) {
+                double *o = out + ((size_t(c) * p + n) * p + m) * 2;
+                if (m < n) { o[0] = o[1] = 0.0; continue; }
+                const double s = std::ldexp(C[size_t(m) * (p + 1) + n], -m);
+                o[0] = s * ep[m - n].re;
+                o[1] = s * ep[m - n].im;
+            }
+    }
+}
+
+static void host_lap_m2l_table(int p, double *out /* [op][k][m] */) {
+    const int nb = 2 * p;
+    std::vector<double> C = binomials(nb);
+    auto binom = [&](int n, int k) { return C[size_t(n) * (nb + 1) + k]; };
+    int op = 0;
+    for (int y = -3; y <= 3; ++y)
+        for (int x = -3; x <= 3; ++x) {
+            if (x >= -1 && x <= 1 && y >= -1 && y <= 1) continue;
+            const double den = double(x) * x + double(y) * y;
+            const HC inv = {double(x) / den, -double(y) / den};
+            std::vector<HC> ip(size_t(2 * p + 1));
+            ip[0] = {1.0, 0.0};
+            for (int i = 1; i <= 2 * p; ++i) ip[i] = hmul(ip[i - 1], inv);
+            for (int k = 0; k < p; ++k)
+                for (int m = 0; m < p; ++m) {
+                    double *o = out + ((size_t(op) * p + k) * p + m) * 2;
+                    HC t;
+                    if (k == 0 && m == 0) {
+                        // log(-delta), principal branch (only Re enters the result)
+                        t = {0.5 * std::log(den), std::atan2(-double(y), -double(x))};
+                    } else if (k == 0) {
+                        const double s = -1.0 / double(m);
+                        t = {s * ip[m].re, s * ip[m].im};
+                    } else {
+                        const double s = ((k & 1) ? -1.0 : 1.0) * binom(m + k - 1, k - 1);
+                        t = {s * ip[k + m].re, s * ip[k + m].im};
+                    }
+                    o[0] = t.re;
+                    o[1] = t.im;
+                }
+            ++op;
+        }
+}
+
+cudaError_t build_op_tables(int p, int kernel, OpTables *t) {
     cudaError_t e = upload_il();
     if (e != cudaSuccess) return e;
     t->p = p;
     const size_t n_m2m = size_t(4) * p * p, n_m2l = size_t(40) * p * p;
     std::vector<double> m2m(2 * n_m2m), l2l(2 * n_m2m), m2l(2 * n_m2l);
-    host_m2m_table(p, m2m.data());
-    host_l2l_table(p, l2l.data());
-    host_m2l_table(p, m2l.data());
+    if (kernel == KERNEL_LAPLACE) {
+        host_lap_m2m_table(p, m2m.data());
+        host_lap_l2l_table(p, l2l.data());
+        host_lap_m2l_table(p, m2l.data());
+    } else {
+        host_m2m_table(p, m2m.data());
+        host_l2l_table(p, l2l.data());
+        host_m2l_table(p, m2l.data());
+    }
     std::vector<float> m2m32(m2m.begin(), m2m.end()), l2l32(l2l.begin(), l2l.end()),
         m2l32(m2l.begin(), m2l.end());
     auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
@@ -194,7 +290,7 @@ cudaError_t build_op_tables(int p, OpTables *t) {
     if ((e = up((void **)&t->m2m32, m2m32.data(), m2m32.size() * 4)) != cudaSuccess) return e;
     if ((e = up((void **)&t->l2l32, l2l32.data(), l2l32.size() * 4)) != cudaSuccess) return e;
     if ((e = up((void **)&t->m2l32, m2l32.data(), m2l32.size() * 4)) != cudaSuccess) return e;
-    if (((2 * p + 15) & ~15) <= 48) {
+    if (kernel == KERNEL_VORTEX && ((2 * p + 15) & ~15) <= 48) {
         std::vector<float> img;
         host_m2l_tc_images(p, img);
         if ((e = up((void **)&t->m2l_tc, img.data(), img.size() * 4)) != cudaSuccess) return e;
@@ -293,8 +389,15 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m(
                 z = mk2<R>(R(0), R(0));
                 w = mk2<R>(R(0), R(0));
             }
+            // vortex: gamma zeta^k; Laplace: q, then -q zeta^k / k
+            const bool lap = d.kernel == KERNEL_LAPLACE;
             for (int k = 0; k < p; ++k) {
-                buf[lane * pmax + k] = w;
+                C2 wk = w;
+                if (lap && k) {
+                    const R s = R(-1) / R(k);
+                    wk = mk2<R>(w.x * s, w.y * s);
+                }
+                buf[lane * pmax + k] = wk;
                 w = cmul(w, z);
             }
             __syncwarp();
@@ -564,6 +667,9 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
         }
     }
     uint32_t todo = __ballot_sync(0xffffffffu, mine);
+    // Laplace kernel: b^_0 also gets a~_0 log w_l from every source
+    const bool lap = d.kernel == KERNEL_LAPLACE;
+    const R logw = R(d.logw0 - double(l) * 0.69314718055994530942);
     while (todo) {
         const int64_t box = box0 + (__ffs(todo) - 1);
         todo &= todo - 1;
@@ -584,6 +690,10 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
             const C2 *T = tab + size_t(en.op) * p * p;
             if (lane < p) {
                 for (int k = 0; k < p; ++k) acc0 = cfma(T[k * p + lane], sa[wid][k], acc0);
+                if (lap && lane == 0) {
+                    acc0.x += logw * sa[wid][0].x;
+                    acc0.y += logw * sa[wid][0].y;
+                }
             }
             if (lane + 32 < p) {
                 for (int k = 0; k < p; ++k) acc1 = cfma(T[k * p + lane + 32], sa[wid][k], acc1);

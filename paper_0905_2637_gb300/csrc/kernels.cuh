@@ -56,7 +56,7 @@ struct OpTables {
     float2 *m2m32 = nullptr, *l2l32 = nullptr, *m2l32 = nullptr;
     float *m2l_tc = nullptr;  // hi/lo B images for the tensor-core M2L (p <= 24)
 };
-cudaError_t build_op_tables(int p, OpTables *out);
+cudaError_t build_op_tables(int p, int kernel, OpTables *out);
 void free_op_tables(OpTables *t);
 void host_m2l_table(int p, double *out_re_im /* 40 * p * p * 2, [op][k][m] */);
 // Interaction list exactly as the kernels enumerate it; returns the count.

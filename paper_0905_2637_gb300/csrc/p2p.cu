@@ -411,6 +411,8 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
         const uint32_t ti = item.z + (has ? k : 0u);
         const double x = xs[ti], y = ys[ti];
         const double inv2s2 = d.inv2s2;
+        // Laplace kernel: su = sum q_j log|x - x_j| (coincident pairs excluded)
+        const bool lap = d.kernel == KERNEL_LAPLACE;
         double su = 0.0, sv = 0.0;
         const uint32_t *st = start + d.soff;
         const int nside = 1 << L;
@@ -426,9 +428,13 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
                     const double ddx = x - __ldg(xs + j), ddy = y - __ldg(ys + j);
                     const double r2 = ddx * ddx + ddy * ddy;
                     if (r2 > 0.0) {
-                        const double f = __ldg(gs + j) * (-expm1(-r2 * inv2s2) / r2);
-                        su += -ddy * f;
-                        sv += ddx * f;
+                        if (lap) {
+                            su += __ldg(gs + j) * (0.5 * log(r2));
+                        } else {
+                            const double f = __ldg(gs + j) * (-expm1(-r2 * inv2s2) / r2);
+                            su += -ddy * f;
+                            sv += ddx * f;
+                        }
                     }
                 }
             }
@@ -451,12 +457,17 @@ __global__ void __launch_bounds__(P2P_THREADS) k_p2p_f64(
                 const double wy = w.x * zy + w.y * zx + ck.y;
                 w = make_double2(wx, wy);
             }
-            fu = d.cfar64 * w.y;
-            fv = d.cfar64 * w.x;
+            if (lap) {
+                fu = w.x;  // the potential is Re of the local expansion
+            } else {
+                fu = d.cfar64 * w.y;
+                fv = d.cfar64 * w.x;
+            }
         }
         if (has && grp == 0) {
             const int64_t q = int64_t(perm[ti]) - d.poff;
-            const double uo = su * d.cnear64 + fu, vo = sv * d.cnear64 + fv;
+            const double uo = lap ? su + fu : su * d.cnear64 + fu;
+            const double vo = lap ? 0.0 : sv * d.cnear64 + fv;
             if (dtype_f32) {
                 static_cast<float *>(d.u)[q] = float(uo);
                 static_cast<float *>(d.v)[q] = float(vo);
