@@ -250,6 +250,43 @@ def serving_leg(_lib, n_req=48, seed=5):
                       "5 midpoint-RK2 steps, 150 GB budget"}
 
 
+def laplace_leg(_lib, torch, stream, steps=5):
+    """The second kernel (PETFMM_KERNEL_LAPLACE, the 2D logarithmic potential),
+    FP64 path: 2^20 uniform charges, L = 8, p = 17.  Its parity with the
+    oracle is the tests' (tests/test_gpu_laplace.py)."""
+    w = W.laplace_uniform()
+    ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="fp64", dtype="f64",
+                       stream=stream, kernel="laplace")
+    ctx.set_option(_lib.PETFMM_OPT_TIMING, 1)
+    ctx.set_option(_lib.PETFMM_OPT_GRAPH, 1)
+    with torch.cuda.stream(stream):
+        x, y, q = (torch.from_numpy(a).cuda() for a in (w.x, w.y, w.gamma))
+        u, v = torch.empty_like(x), torch.empty_like(x)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        ctx.evaluate(x, y, q, u, v)
+    ctx.sync()
+    ms, stages = [], []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.evaluate(x, y, q, u, v)
+        e1.record(stream)
+        ctx.sync()
+        ms.append(e0.elapsed_time(e1))
+        stages.append(ctx.stage_times())
+    st = ctx.stats()
+    ctx.close()
+    t = statistics.median(ms)
+    stage_ms = {k: statistics.median(s[k] for s in stages) for k in stages[0]}
+    return {"kernel": "laplace (2D log potential), FP64", "n": w.n, "levels": w.L, "order": w.p,
+            "value": w.n / (t * 1e-3), "unit": "particles/s", "ms_per_step": t,
+            "stages_ms": stage_ms, "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"],
+            "p2p_pairs_per_s": st["p2p_pairs"] / (stage_ms["p2p"] * 1e-3),
+            "m2l_fp64_flops": 8.0 * w.p * w.p * st["m2l_pairs"] / (stage_ms["m2l"] * 1e-3),
+            "data": "synthetic: x, y ~ U(0,1), q ~ U(-1,1), seed 1"}
+
+
 def batch_leg(_lib, torch, stream, steps=5):
     """512 independent instances (N log-uniform in [1e3, 2^18], uniform, sigma =
     0.5/sqrt(N), p in {8, 12, 17}) in one batched evaluation; L chosen by the
@@ -290,6 +327,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-laplace", action="store_true")
     ap.add_argument("--workload", default="clustered-16M",
                     choices=["clustered-16M", "clustered-4M", "lattice-1M", "lamb-oseen-765k"],
                     help="clustered-4M (2^22 blobs, L = 9, same blobs per leaf) and lattice-1M "
@@ -489,6 +527,8 @@ def main():
             line["config"]["workload"] = w.name + " (profiling case)"
         if not args.no_batch:
             line["batch"] = batch_leg(_lib, torch, stream)
+        if not args.no_laplace:
+            line["laplace"] = laplace_leg(_lib, torch, stream)
         if not args.no_serve:
             line["serving"] = serving_leg(_lib)
         if not args.no_cpu_baseline:

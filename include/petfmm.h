@@ -281,9 +281,10 @@ enum {
                                   potential u_i = sum_{j != i} g_j log|x_i - x_j|
                                   (coincident pairs excluded; sigma unused), v = 0,
                                   by the same FMM with the series of the complex
-                                  logarithm (p terms, the log counted as one).  The
-                                  Laplace kernel needs PETFMM_FP64 (an evaluation of
-                                  a mixed context returns PETFMM_EINVAL). */
+                                  logarithm (p terms, the log counted as one).  Both
+                                  precisions; the mixed path sums the near field
+                                  directly (PETFMM_OPT_P2P_PAIRS applies to the
+                                  vortex kernel only). */
 };
 enum { PETFMM_KERNEL_VORTEX = 0, PETFMM_KERNEL_LAPLACE = 1 };
 int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);

@@ -69,7 +69,7 @@ struct TaskRange {
 struct Plan {
     std::vector<InstDesc> inst;
     std::vector<Task> tasks;
-    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tile;
+    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tile, m2l_log;
     std::vector<TaskRange> m2m, l2l;  // in launch order
     int64_t N = 0, nleaves = 0, nstart = 0, ncoef = 0, items_cap = 0;
     int nbits = 0, pmax = 1, Lmax = 0, tile_pmax = 1;
@@ -335,11 +335,12 @@ void flatten_tasks(Plan &pl) {
     put(pl.m2l);
     put(pl.m2l_tc);
     put(pl.m2l_tile);
+    put(pl.m2l_log);
     for (TaskRange &r : pl.m2m) put(r);
     for (TaskRange &r : pl.l2l) put(r);
 }
 
-int build_plan(int precision, bool use_tc, int tc_segmax, double near_tol,
+int build_plan(int precision, int kernel, bool use_tc, int tc_segmax, double near_tol,
                const std::vector<Problem> &probs, Plan &pl) {
     pl = Plan();
     const int ni = int(probs.size());
@@ -360,6 +361,7 @@ int build_plan(int precision, bool use_tc, int tc_segmax, double near_tol,
         InstDesc d;
         std::memset(&d, 0, sizeof(d));
         inst_set_domain(d, pb.dom.x0, pb.dom.y0, pb.dom.width, pb.L);
+        d.kernel = kernel;
         d.sigma = pb.sigma;
         d.L = pb.L;
         d.p = pb.p;
@@ -414,6 +416,7 @@ int build_plan(int precision, bool use_tc, int tc_segmax, double near_tol,
                 pl.tc_smem = std::max(pl.tc_smem, m2l_tc_smem_bytes(d.p, m2l_tc_seg(l, tc_segmax)));
             }
             add_task(pl.m2l, i, l, int64_t(1) << (2 * l), M2L_BOXES);
+            if (kernel == KERNEL_LAPLACE) add_task(pl.m2l_log, i, l, int64_t(1) << (2 * l), 256);
         }
         items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
     }
@@ -530,7 +533,7 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     if (!pl.tasks.empty()) k.add(pl.tasks.data(), pl.tasks.size() * sizeof(Task));
     auto range = [&](const TaskRange &r) { k.put(r.first); k.put(r.count); k.put(r.nblocks); };
     for (const TaskRange *r : {&pl.morton, &pl.start, &pl.particles, &pl.leaves_p2m, &pl.leaves_wl,
-                               &pl.m2l, &pl.m2l_tc, &pl.m2l_tile})
+                               &pl.m2l, &pl.m2l_tc, &pl.m2l_tile, &pl.m2l_log})
         range(*r);
     for (const TaskRange &r : pl.m2m) range(r);
     for (const TaskRange &r : pl.l2l) range(r);
@@ -560,10 +563,7 @@ void stage_mark(petfmm_ctx *c, int stage) {
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     Plan &pl = c->plan;
-    // the Laplace kernel has the FP64 path only
-    if (c->kernel == KERNEL_LAPLACE && c->precision != PETFMM_FP64) return PETFMM_EINVAL;
-    PF_TRY(build_plan(c->precision, c->m2l_tc, c->tc_segmax, c->near_tol, probs, pl));
-    for (InstDesc &d : pl.inst) d.kernel = c->kernel;
+    PF_TRY(build_plan(c->precision, c->kernel, c->m2l_tc, c->tc_segmax, c->near_tol, probs, pl));
     PF_TRY(attach_tables(c, pl));
     cudaStream_t st = c->stream;  // the launch sequence's stream (a capture swaps it)
     const bool mixed = c->precision == PETFMM_MIXED;
@@ -585,7 +585,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->hist, size_t(256) * rb * 4, st));
     // pairwise near field (mixed path): at most 4 forward neighbours per leaf,
     // a pair cut into at most ceil(na / 128) pieces, and the leaf's own pairs
-    const bool pairs = mixed && c->p2p_pairs;
+    // (the pairwise near field is the vortex kernel's)
+    const bool pairs = mixed && c->p2p_pairs && c->kernel == KERNEL_VORTEX;
     const int64_t pair_cap =
         pairs ? 5 * std::min<int64_t>(pl.nleaves, N) + 4 * (N / 128) + 1 : 0;
     const int64_t order_cap = std::max<int64_t>(pl.items_cap, pair_cap);
@@ -649,7 +650,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         porder = order;
         porder.cap = pair_cap;
     }
-    const int grid = p2p_grid(mixed, pl.deg, pl.general);
+    const bool lap = c->kernel == KERNEL_LAPLACE;
+    const int grid = p2p_grid(mixed, pl.deg, pl.general, lap ? 1 : 0);
     if (grid <= 0) return PETFMM_EINVAL;
     const int pgrid = pairs ? p2p_pairs_grid(pl.deg, pl.general) : 0;
     if (pairs && pgrid <= 0) return PETFMM_EINVAL;
@@ -767,6 +769,18 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                                 static_cast<const float2 *>(c->me.p),
                                 static_cast<float2 *>(c->le.p), ucount + pl.m2l_tc.nblocks,
                                 c->tc_dense_pct, st, lc));
+    if (pl.m2l_log.count) {
+        if (mixed)
+            PF_CUDA(launch_m2l_logterm<float>(dtask + pl.m2l_log.first, pl.m2l_log.count,
+                                              pl.m2l_log.nblocks, dinst, start,
+                                              static_cast<const float2 *>(c->me.p),
+                                              static_cast<float2 *>(c->le.p), st, lc));
+        else
+            PF_CUDA(launch_m2l_logterm<double>(dtask + pl.m2l_log.first, pl.m2l_log.count,
+                                               pl.m2l_log.nblocks, dinst, start,
+                                               static_cast<const double2 *>(c->me.p),
+                                               static_cast<double2 *>(c->le.p), st, lc));
+    }
     stage_mark(c, PETFMM_STAGE_L2L);
     for (const TaskRange &tr : pl.l2l) {
         if (mixed)
@@ -803,7 +817,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         // field and the sum
         PF_CUDA(launch_p2p_mixed(grid, pl.deg, pl.general, static_cast<const uint4 *>(c->items.p),
                                  ctrl, dinst, start, static_cast<const float4 *>(c->rec.p), pb.own,
-                                 pairs, busy, st, lc));
+                                 pairs, lap ? 1 : 0, busy, st, lc));
         PF_CUDA(launch_p2p_final(dtask + pl.particles.first, pl.particles.count,
                                  pl.particles.nblocks, dinst, start, skeys,
                                  static_cast<const float4 *>(c->rec.p),
@@ -1041,7 +1055,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     int rc = problems_from(n_inst, inst, probs);
     if (rc) return rc;
     Plan pl;
-    rc = build_plan(precision, true, kTcSegDefault, kNearTolDefault, probs, pl);
+    rc = build_plan(precision, KERNEL_VORTEX, true, kTcSegDefault, kNearTolDefault, probs, pl);
     if (rc) return rc;
     int n = 0;
     auto emit = [&](int64_t id, const TaskRange &r) {

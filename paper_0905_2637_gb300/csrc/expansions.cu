@@ -228,7 +228,7 @@ static void host_lap_l2l_table(int p, double *out /* [c][n][m] */) {
     }
 }
 
-static void host_lap_m2l_table(int p, double *out /* [op][k][m] */) {
+void host_lap_m2l_table(int p, double *out /* [op][k][m] */) {
     const int nb = 2 * p;
     std::vector<double> C = binomials(nb);
     auto binom = [&](int n, int k) { return C[size_t(n) * (nb + 1) + k]; };
@@ -290,9 +290,9 @@ cudaError_t build_op_tables(int p, int kernel, OpTables *t) {
     if ((e = up((void **)&t->m2m32, m2m32.data(), m2m32.size() * 4)) != cudaSuccess) return e;
     if ((e = up((void **)&t->l2l32, l2l32.data(), l2l32.size() * 4)) != cudaSuccess) return e;
     if ((e = up((void **)&t->m2l32, m2l32.data(), m2l32.size() * 4)) != cudaSuccess) return e;
-    if (kernel == KERNEL_VORTEX && ((2 * p + 15) & ~15) <= 48) {
+    if (((2 * p + 15) & ~15) <= 48) {
         std::vector<float> img;
-        host_m2l_tc_images(p, img);
+        host_m2l_tc_images(p, kernel, img);
         if ((e = up((void **)&t->m2l_tc, img.data(), img.size() * 4)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -476,8 +476,10 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m_reg(
                 so.y += b.y;
             }
             const uint32_t ix = compact_bits(m), iy = compact_bits(m >> 1);
+            // Laplace kernel: a_k = -(1/k) sum q zeta^k for k >= 1
+            const float s = (d.kernel == KERNEL_LAPLACE && lane) ? -1.0f / float(lane) : 1.0f;
             me[d.eoff + (lvl_off(L) + box_index(L, ix, iy)) * p + lane] =
-                make_float2(se.x + so.x, se.y + so.y);
+                make_float2(s * (se.x + so.x), s * (se.y + so.y));
         }
         __syncwarp();
     }
@@ -667,9 +669,6 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
         }
     }
     uint32_t todo = __ballot_sync(0xffffffffu, mine);
-    // Laplace kernel: b^_0 also gets a~_0 log w_l from every source
-    const bool lap = d.kernel == KERNEL_LAPLACE;
-    const R logw = R(d.logw0 - double(l) * 0.69314718055994530942);
     while (todo) {
         const int64_t box = box0 + (__ffs(todo) - 1);
         todo &= todo - 1;
@@ -690,10 +689,6 @@ __global__ void __launch_bounds__(M2L_WARPS * 32) k_m2l(const Task *__restrict__
             const C2 *T = tab + size_t(en.op) * p * p;
             if (lane < p) {
                 for (int k = 0; k < p; ++k) acc0 = cfma(T[k * p + lane], sa[wid][k], acc0);
-                if (lap && lane == 0) {
-                    acc0.x += logw * sa[wid][0].x;
-                    acc0.y += logw * sa[wid][0].y;
-                }
             }
             if (lane + 32 < p) {
                 for (int k = 0; k < p; ++k) acc1 = cfma(T[k * p + lane + 32], sa[wid][k], acc1);
@@ -717,6 +712,66 @@ cudaError_t launch_m2l(const Task *tasks, int ntasks, int64_t nblocks, const Ins
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
+
+// ----------------------------------------------------------------------------
+// Laplace kernel, the level-dependent constant of M2L: the rescaled
+// operators carry log(-delta); the a~_0 log w_l part is added here, after all
+// M2L kernels of the evaluation: b^_0(t) += log w_l * sum over the occupied
+// interaction-list sources s of a~_0(s).  One thread per target box (task =
+// instance, level; units = 4^l boxes, row-major), occupied targets only.
+// ----------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_m2l_logterm(const Task *__restrict__ tasks, int ntasks,
+                                                     const InstDesc *__restrict__ insts,
+                                                     const uint32_t *__restrict__ start,
+                                                     const typename Cplx<R>::T *__restrict__ me,
+                                                     typename Cplx<R>::T *__restrict__ le) {
+    using C2 = typename Cplx<R>::T;
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t box = (int64_t(blockIdx.x) - t.block0) * 256 + threadIdx.x;
+    if (box >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int p = d.p, l = t.level, nside = 1 << l;
+    const uint32_t *st = start + d.soff;
+    const int ix = int(box & (nside - 1)), iy = int(box >> l);
+    if (!box_count(st, d.L, l, morton_key(uint32_t(ix), uint32_t(iy)))) return;
+    const int c = (ix & 1) | ((iy & 1) << 1);
+    const C2 *lev = me + d.eoff + lvl_off(l) * p;
+    R sr = R(0), si = R(0);
+    for (int e = 0; e < 27; ++e) {
+        const IlEntry en = c_il[c][e];
+        const int sx = ix + en.dx, sy = iy + en.dy;
+        if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
+        if (!box_count(st, d.L, l, morton_key(uint32_t(sx), uint32_t(sy)))) continue;
+        const C2 a0 = lev[box_index(l, uint32_t(sx), uint32_t(sy)) * p];
+        sr += a0.x;
+        si += a0.y;
+    }
+    const R logw = R(d.logw0 - double(l) * 0.69314718055994530942);
+    C2 *dst = le + d.eoff + (lvl_off(l) + box_index(l, uint32_t(ix), uint32_t(iy))) * p;
+    C2 o = *dst;
+    o.x += logw * sr;
+    o.y += logw * si;
+    *dst = o;
+}
+
+template <typename R>
+cudaError_t launch_m2l_logterm(const Task *tasks, int ntasks, int64_t nblocks,
+                               const InstDesc *insts, const uint32_t *start,
+                               const typename Cplx<R>::T *me, typename Cplx<R>::T *le,
+                               cudaStream_t st, uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_m2l_logterm<R><<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, me, le);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
+}
+template cudaError_t launch_m2l_logterm<double>(const Task *, int, int64_t, const InstDesc *,
+                                                const uint32_t *, const double2 *, double2 *,
+                                                cudaStream_t, uint64_t *);
+template cudaError_t launch_m2l_logterm<float>(const Task *, int, int64_t, const InstDesc *,
+                                               const uint32_t *, const float2 *, float2 *,
+                                               cudaStream_t, uint64_t *);
 
 template cudaError_t launch_p2m<double>(const uint2 *, const uint32_t *, int64_t,
                                         const InstDesc *, int, const uint32_t *, const double *,

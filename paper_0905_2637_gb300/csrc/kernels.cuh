@@ -101,7 +101,15 @@ bool m2l_tc_supported(int p, int level, int segmax);
 int64_t m2l_tc_units(int level, int segmax);
 size_t m2l_tc_smem_bytes(int p, int seg);
 int m2l_tc_seg(int level, int segmax);
-void host_m2l_tc_images(int p, std::vector<float> &out);
+void host_m2l_tc_images(int p, int kernel, std::vector<float> &out);
+void host_lap_m2l_table(int p, double *out_re_im /* 40 * p * p * 2, [op][k][m] */);
+// Laplace kernel: the level-dependent constant of M2L, added after every M2L
+// kernel (tasks: instance, level; units: 4^l target boxes).
+template <typename R>
+cudaError_t launch_m2l_logterm(const Task *tasks, int ntasks, int64_t nblocks,
+                               const InstDesc *insts, const uint32_t *start,
+                               const typename Cplx<R>::T *me, typename Cplx<R>::T *le,
+                               cudaStream_t st, uint64_t *launches);
 // ucount[u] = targets holding particles in unit u of the launch (tensor-core
 // or tiled SIMT units; block index = unit).
 cudaError_t launch_tc_unit_count(const Task *tasks, int ntasks, int64_t nunits,
@@ -166,8 +174,8 @@ cudaError_t launch_p2p_f64(int grid, const uint4 *items, uint32_t *ctrl, const I
 // (launch_p2p_final then adds the far field).
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
                              const InstDesc *insts, const uint32_t *start, const float4 *rec,
-                             float2 *own, int pairs, unsigned long long *busy, cudaStream_t st,
-                             uint64_t *launches);
+                             float2 *own, int pairs, int laplace, unsigned long long *busy,
+                             cudaStream_t st, uint64_t *launches);
 // Pairwise near field between neighbouring leaves (mixed path).  Buffers:
 // own[N]: each blob's directly summed part (sorted order; the only one used
 // by the directed mode, part == nullptr there); part: 9 slots of
@@ -206,7 +214,7 @@ cudaError_t launch_p2p_final(const Task *tasks, int ntasks, int64_t nblocks,
                                 const uint32_t *skeys, const float4 *rec, const float2 *le,
                                 const PairBufs &pb, int dtype_f32, cudaStream_t st,
                                 uint64_t *launches);
-int p2p_grid(int precision_mixed, int deg, int general);
+int p2p_grid(int precision_mixed, int deg, int general, int laplace);
 int device_sm_count();
 constexpr int P2P_TPI_F64 = 32;
 constexpr int P2P_TPI_MIXED = 64;

@@ -360,10 +360,13 @@ int64_t m2l_tc_units(int level, int segmax) {
 
 // B images for p: for each of the 40 offsets, hi then lo, each Kpad x Npad
 // floats in the K-major core-matrix layout [k / 4][n][k % 4].
-void host_m2l_tc_images(int p, std::vector<float> &out) {
+void host_m2l_tc_images(int p, int kernel, std::vector<float> &out) {
     const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
     std::vector<double> T(size_t(40) * p * p * 2);
-    host_m2l_table(p, T.data());  // [op][k][m] complex
+    if (kernel == KERNEL_LAPLACE)
+        host_lap_m2l_table(p, T.data());  // [op][k][m] complex
+    else
+        host_m2l_table(p, T.data());
     const size_t slot = size_t(Kpad) * Npad;
     out.assign(size_t(40) * 2 * slot, 0.0f);
     for (int op = 0; op < 40; ++op) {

@@ -297,7 +297,22 @@ __device__ __forceinline__ void pair2(const float4 s, float xa, float ya, float 
 // kernel covers); the near sum goes to own[] in sorted order, the final pass
 // adds the far field.  No L2P here: with few targets per item the lanes of
 // all source groups would repeat it.
-template <int DEG, bool GENERAL, bool PAIRS>
+// Laplace kernel: one source against the lane's two targets, both in the
+// source leaf's frame (leaf units): u += q (log rho + log w), i.e. q log r in
+// global units; coincident pairs add nothing.
+__device__ __forceinline__ void pair2_lap(const float4 s, float xa, float ya, float xb, float yb,
+                                          float logw, float &ua, float &ub) {
+    const float dxa = xa - s.x, dya = ya - s.y;
+    const float dxb = xb - s.x, dyb = yb - s.y;
+    const float r2a = fmaf(dxa, dxa, dya * dya);
+    const float r2b = fmaf(dxb, dxb, dyb * dyb);
+    const float la = r2a > 0.f ? fmaf(0.5f, __logf(r2a), logw) : 0.f;
+    const float lb = r2b > 0.f ? fmaf(0.5f, __logf(r2b), logw) : 0.f;
+    ua = fmaf(s.z, la, ua);
+    ub = fmaf(s.z, lb, ub);
+}
+
+template <int DEG, bool GENERAL, bool PAIRS, bool LAP>
 __device__ __forceinline__ void directed_item(const uint4 item, const InstDesc *__restrict__ insts,
                                               const uint32_t *__restrict__ start,
                                               const float4 *__restrict__ rec,
@@ -321,6 +336,7 @@ __device__ __forceinline__ void directed_item(const uint4 item, const InstDesc *
     float ua = 0.f, va = 0.f, ub = 0.f, vb = 0.f;
     const uint32_t *st = start + d.soff;
     const int nside = 1 << L;
+    const float logw = LAP ? float(d.logw0 - double(L) * 0.69314718055994530942) : 0.f;
     for (int dy = -1; dy <= 1; ++dy) {
         const int sy = iy + dy;
         if (sy < 0 || sy >= nside) continue;
@@ -337,14 +353,22 @@ __device__ __forceinline__ void directed_item(const uint4 item, const InstDesc *
             // the stride-1 loop keeps constant load offsets after unrolling
             if (S == 1) {
 #pragma unroll 4
-                for (uint32_t j = j0; j < j1; ++j)
-                    pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
-                                        va, ub, vb);
+                for (uint32_t j = j0; j < j1; ++j) {
+                    if constexpr (LAP)
+                        pair2_lap(__ldg(rec + j), xa, ya, xb, yb, logw, ua, ub);
+                    else
+                        pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
+                                            va, ub, vb);
+                }
             } else {
 #pragma unroll 4
-                for (uint32_t j = j0 + grp; j < j1; j += S)
-                    pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
-                                        va, ub, vb);
+                for (uint32_t j = j0 + grp; j < j1; j += S) {
+                    if constexpr (LAP)
+                        pair2_lap(__ldg(rec + j), xa, ya, xb, yb, logw, ua, ub);
+                    else
+                        pair2<DEG, GENERAL>(__ldg(rec + j), xa, ya, xb, yb, a, kappa, split, ua,
+                                            va, ub, vb);
+                }
             }
         }
     }
@@ -355,12 +379,12 @@ __device__ __forceinline__ void directed_item(const uint4 item, const InstDesc *
         ub += __shfl_xor_sync(0xffffffffu, ub, int(o));
         vb += __shfl_xor_sync(0xffffffffu, vb, int(o));
     }
-    const float cn = d.cnear;
+    const float cn = LAP ? 1.f : d.cnear;
     if (has_a && grp == 0) own[ta] = make_float2(cn * ua, cn * va);
     if (has_b && grp == 0) own[tb] = make_float2(cn * ub, cn * vb);
 }
 
-template <int DEG, bool GENERAL, bool PAIRS>
+template <int DEG, bool GENERAL, bool PAIRS, bool LAP>
 __global__ void __launch_bounds__(P2P_THREADS, 5) k_p2p_mixed(
     const uint4 *__restrict__ items, uint32_t *ctrl, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const float4 *__restrict__ rec,
@@ -373,7 +397,7 @@ __global__ void __launch_bounds__(P2P_THREADS, 5) k_p2p_mixed(
         if (lane == 0) it = atomicAdd(ctrl + CTRL_QUEUE, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= nitems) break;
-        directed_item<DEG, GENERAL, PAIRS>(items[it], insts, start, rec, own, lane);
+        directed_item<DEG, GENERAL, PAIRS, LAP>(items[it], insts, start, rec, own, lane);
     }
     if (busy && lane == 0) {
         const uint64_t t_end = global_ns();
@@ -1059,7 +1083,9 @@ __global__ void __launch_bounds__(256) k_p2p_final(
             z = make_float2(fmaf(z.x, rr.x, fmaf(-z.y, rr.y, ck.x)),
                             fmaf(z.x, rr.y, fmaf(z.y, rr.x, ck.y)));
         }
-        w = make_float2(d.cfar * z.y, d.cfar * z.x);
+        // vortex: u - i v = cfar w; Laplace: the potential is Re of the LE
+        w = d.kernel == KERNEL_LAPLACE ? make_float2(z.x, 0.f)
+                                       : make_float2(d.cfar * z.y, d.cfar * z.x);
     }
     // then the near-field parts this leaf has, in a fixed order
     const uint32_t fl = pb.part ? pb.lflags[d.loff + m] : LF_DIRECTED;
@@ -1140,11 +1166,13 @@ typedef void (*MixedKernel)(const uint4 *, uint32_t *, const InstDesc *, const u
                             const float4 *, float2 *, unsigned long long *);
 template <int D>
 static MixedKernel pick2(int general, bool pairs) {
-    if (pairs) return general ? k_p2p_mixed<D, true, true> : k_p2p_mixed<D, false, true>;
-    return general ? k_p2p_mixed<D, true, false> : k_p2p_mixed<D, false, false>;
+    if (pairs)
+        return general ? k_p2p_mixed<D, true, true, false> : k_p2p_mixed<D, false, true, false>;
+    return general ? k_p2p_mixed<D, true, false, false> : k_p2p_mixed<D, false, false, false>;
 }
 
-static MixedKernel pick_mixed(int deg, int general, bool pairs = false) {
+static MixedKernel pick_mixed(int deg, int general, bool pairs = false, bool lap = false) {
+    if (lap) return k_p2p_mixed<4, false, false, true>;  // no polynomial, no pairs
     switch (deg) {
         case 4: return pick2<4>(general, pairs);
         case 5: return pick2<5>(general, pairs);
@@ -1171,10 +1199,10 @@ int device_sm_count() {
     return g_sms;
 }
 
-int p2p_grid(int precision_mixed, int deg, int general) {
+int p2p_grid(int precision_mixed, int deg, int general, int laplace) {
     int per_sm = 1;
     if (precision_mixed) {
-        MixedKernel k = pick_mixed(deg, general);
+        MixedKernel k = pick_mixed(deg, general, false, laplace != 0);
         if (!k) return 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, P2P_THREADS, 0);
     } else {
@@ -1186,9 +1214,9 @@ int p2p_grid(int precision_mixed, int deg, int general) {
 
 cudaError_t launch_p2p_mixed(int grid, int deg, int general, const uint4 *items, uint32_t *ctrl,
                              const InstDesc *insts, const uint32_t *start, const float4 *rec,
-                             float2 *own, int pairs, unsigned long long *busy, cudaStream_t st,
-                             uint64_t *launches) {
-    MixedKernel k = pick_mixed(deg, general, pairs != 0);
+                             float2 *own, int pairs, int laplace, unsigned long long *busy,
+                             cudaStream_t st, uint64_t *launches) {
+    MixedKernel k = pick_mixed(deg, general, pairs != 0, laplace != 0);
     if (!k) return cudaErrorInvalidValue;
     k<<<grid, P2P_THREADS, 0, st>>>(items, ctrl, insts, start, rec, own, busy);
     PF_LAUNCHED(1);

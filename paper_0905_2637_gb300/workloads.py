@@ -145,6 +145,18 @@ def batch(n_inst=512, seed=1, dtype="f64", n_min=1_000, n_max=262_144):
     return out
 
 
+def laplace_uniform(n=1 << 20, seed=1, L=8, p=17, dtype="f64", name="laplace-1M"):
+    """The second kernel's workload: n charges q ~ U(-1, 1) uniform on the
+    unit square (the paper's "square domain" points), 16 per leaf at L = 8.
+    sigma is unused by the logarithmic kernel."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.0, 1.0, n)
+    y = rng.uniform(0.0, 1.0, n)
+    q = rng.uniform(-1.0, 1.0, n)
+    x, y, q = _store(dtype, x, y, q)
+    return Workload(name, x, y, q, 1.0, UNIT_DOMAIN, L, p, dtype)
+
+
 def tiny(n, seed, L=3, p=10, sigma=None, dtype="f64", clustered_frac=0.0):
     """Small random cases for property sweeps: uniform points, optionally with a
     fraction packed into one tight clump (ragged, very uneven leaves)."""

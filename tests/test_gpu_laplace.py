@@ -6,7 +6,9 @@ direct sum (pinned in test_oracle_laplace.py).
 Bars: the GPU FMM computes the oracle FMM's sums with rescaled (but
 mathematically identical) coefficients in another order, so rel-L2 <= 1e-12;
 against the direct sum the difference is the FMM's truncation error, which
-decays geometrically in p."""
+decays geometrically in p.  The mixed path (FP32 expansions, 3xTF32 tensor-core
+M2L, FP32 near field with the SFU logarithm) stays within the vortex kernel's
+bar, rel-L2 <= 1e-5 of the FP64 GPU FMM at the same L and p."""
 import numpy as np
 import pytest
 
@@ -117,13 +119,6 @@ def test_laplace_edge_cases(orc):
     ref = orc.laplace_fmm(xs.cpu().numpy(), ys.cpu().numpy(), qs.cpu().numpy(), (0, 0, 1), 3, 8)
     assert np.allclose(u.cpu().numpy(), ref, rtol=1e-13, atol=1e-14)
     ctx.close()
-    # the Laplace kernel has the FP64 path only
-    mx = _lib.Context((0, 0, 1), 3, 8, 0.01, precision="mixed", dtype="f32", kernel="laplace")
-    xf = torch.rand(100, device="cuda")
-    with pytest.raises(_lib.PetfmmError) as e:
-        mx.evaluate(xf, xf.clone(), xf.clone())
-    assert e.value.code == _lib.PETFMM_EINVAL
-    mx.close()
 
 
 def test_vortex_and_laplace_contexts_side_by_side(orc):
@@ -134,3 +129,27 @@ def test_vortex_and_laplace_contexts_side_by_side(orc):
     run_laplace(w)
     u2, v2 = G.run(w, "fp64")
     assert np.array_equal(u1, u2) and np.array_equal(v1, v2)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("case", [
+    dict(n=10_000, seed=1, L=4, p=12, frac=0.0),
+    dict(n=60_000, seed=2, L=6, p=17, frac=0.5),
+    dict(n=300_000, seed=3, L=8, p=17, frac=0.2),   # tensor-core M2L levels
+    dict(n=1000, seed=4, L=2, p=40, frac=0.0),      # no tensor cores at this order
+])
+def test_laplace_mixed_vs_fp64(case, dtype):
+    w = W.tiny(case["n"], case["seed"], L=case["L"], p=case["p"], clustered_frac=case["frac"],
+               dtype=dtype)
+    u64, _ = run_laplace(w)
+    umx, vmx = run_laplace(w, precision="mixed")
+    assert np.all(vmx == 0.0)
+    assert rel(umx, u64) <= 1e-5
+
+
+def test_laplace_mixed_against_oracle_sample(orc):
+    w = W.laplace_uniform(n=1 << 18, seed=7, L=7, p=17, dtype="f32")
+    umx, _ = run_laplace(w, precision="mixed")
+    tg = W.sample_targets(w.n, 400)
+    ref = orc.laplace_fmm(w.x, w.y, w.gamma, w.domain, w.L, w.p, targets=tg)
+    assert rel(umx[tg], ref) <= 1e-5
