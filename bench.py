@@ -251,40 +251,59 @@ def serving_leg(_lib, n_req=48, seed=5):
 
 
 def laplace_leg(_lib, torch, stream, steps=5):
-    """The second kernel (PETFMM_KERNEL_LAPLACE, the 2D logarithmic potential),
-    FP64 path: 2^20 uniform charges, L = 8, p = 17.  Its parity with the
-    oracle is the tests' (tests/test_gpu_laplace.py)."""
-    w = W.laplace_uniform()
-    ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="fp64", dtype="f64",
-                       stream=stream, kernel="laplace")
-    ctx.set_option(_lib.PETFMM_OPT_TIMING, 1)
-    ctx.set_option(_lib.PETFMM_OPT_GRAPH, 1)
+    """The second kernel (PETFMM_KERNEL_LAPLACE, the 2D logarithmic potential):
+    2^20 uniform charges, L = 8, p = 17, mixed path timed, FP64 path timed and
+    used as the accuracy reference (rel-L2 of mixed vs FP64 on the device).
+    Its parity with the oracle is the tests' (tests/test_gpu_laplace.py)."""
+    w = W.laplace_uniform(dtype="f32")
     with torch.cuda.stream(stream):
         x, y, q = (torch.from_numpy(a).cuda() for a in (w.x, w.y, w.gamma))
-        u, v = torch.empty_like(x), torch.empty_like(x)
     torch.cuda.synchronize()
-    for _ in range(3):
-        ctx.evaluate(x, y, q, u, v)
-    ctx.sync()
-    ms, stages = [], []
-    for _ in range(steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.evaluate(x, y, q, u, v)
-        e1.record(stream)
+    res = {}
+    for prec in ("mixed", "fp64"):
+        ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision=prec, dtype="f32",
+                           stream=stream, kernel="laplace")
+        ctx.set_option(_lib.PETFMM_OPT_TIMING, 1)
+        ctx.set_option(_lib.PETFMM_OPT_GRAPH, 1)
+        with torch.cuda.stream(stream):
+            u, v = torch.empty_like(x), torch.empty_like(x)
+        for _ in range(3):
+            ctx.evaluate(x, y, q, u, v)
         ctx.sync()
-        ms.append(e0.elapsed_time(e1))
-        stages.append(ctx.stage_times())
-    st = ctx.stats()
-    ctx.close()
-    t = statistics.median(ms)
-    stage_ms = {k: statistics.median(s[k] for s in stages) for k in stages[0]}
-    return {"kernel": "laplace (2D log potential), FP64", "n": w.n, "levels": w.L, "order": w.p,
-            "value": w.n / (t * 1e-3), "unit": "particles/s", "ms_per_step": t,
-            "stages_ms": stage_ms, "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"],
-            "p2p_pairs_per_s": st["p2p_pairs"] / (stage_ms["p2p"] * 1e-3),
-            "m2l_fp64_flops": 8.0 * w.p * w.p * st["m2l_pairs"] / (stage_ms["m2l"] * 1e-3),
-            "data": "synthetic: x, y ~ U(0,1), q ~ U(-1,1), seed 1"}
+        ms, stages = [], []
+        for _ in range(steps if prec == "mixed" else 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.evaluate(x, y, q, u, v)
+            e1.record(stream)
+            ctx.sync()
+            ms.append(e0.elapsed_time(e1))
+            stages.append(ctx.stage_times())
+        st = ctx.stats()
+        ctx.close()
+        t = statistics.median(ms)
+        stage_ms = {k: statistics.median(s_[k] for s_ in stages) for k in stages[0]}
+        res[prec] = dict(value=w.n / (t * 1e-3), ms_per_step=t, stages_ms=stage_ms,
+                         p2p_pairs=st["p2p_pairs"], m2l_pairs=st["m2l_pairs"], u=u.double())
+    d = res["mixed"]["u"] - res["fp64"]["u"]
+    rel = float(torch.sqrt((d * d).sum() / (res["fp64"]["u"] ** 2).sum()))
+    mx = res["mixed"]
+    # near field: one SFU logarithm per ordered pair (16 per SM per clock)
+    p2p_s = mx["stages_ms"]["p2p"] * 1e-3
+    mufu_peak = SMS * 16 * 2070e6
+    return {"kernel": "laplace (2D log potential)", "n": w.n, "levels": w.L, "order": w.p,
+            "value": mx["value"], "unit": "particles/s", "ms_per_step": mx["ms_per_step"],
+            "dtype": "f32 (mixed: FP32 near field, 3xTF32 M2L)", "rel_l2_vs_fp64": rel,
+            "fp64_gpu": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_step"],
+                         "stages_ms": res["fp64"]["stages_ms"]},
+            "stages_ms": mx["stages_ms"], "p2p_pairs": mx["p2p_pairs"],
+            "m2l_pairs": mx["m2l_pairs"],
+            "p2p_roofline": {"bound": "mufu (lg2)", "achieved": mx["p2p_pairs"] / p2p_s,
+                             "peak": mufu_peak, "unit": "pairs/s",
+                             "frac": mx["p2p_pairs"] / p2p_s / mufu_peak,
+                             "note": "one SFU lg2 per ordered pair; 152 SMs x 16 SFU lanes x "
+                                     "2070 MHz; the stage includes the final pass"},
+            "data": "synthetic: x, y ~ U(0,1), q ~ U(-1,1), seed 1, fp32 storage"}
 
 
 def batch_leg(_lib, torch, stream, steps=5):
