@@ -118,7 +118,7 @@ struct petfmm_ctx {
 
     DevBuf keysA, keysB, valsA, valsB, hist, scratch, start, xs, ys, gs, rec, me, le, cnt, off,
         items, ctrl, plan_dev, busy, ucount, recu, occ, items_u, ikA, ikB, ivA, ivB, ihist, own,
-        part, pitems, pxtra, pxs;
+        part, pitems, pxtra, pxs, ustage;
     DevBuf hx, hy, hg, hu, hv;  // device staging for petfmm_evaluate_host
     std::map<int, OpTables> tables;
 
@@ -547,7 +547,8 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
                             &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
                             &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount,
                             &c->recu, &c->occ, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB,
-                            &c->ihist, &c->own, &c->part, &c->pitems, &c->pxtra, &c->pxs})
+                            &c->ihist, &c->own, &c->part, &c->pitems, &c->pxtra, &c->pxs,
+                            &c->ustage})
         k.put(b->p);
     return k.h;
 }
@@ -560,6 +561,9 @@ void stage_mark(petfmm_ctx *c, int stage) {
     else
         cudaEventRecord(c->ev[stage], c->stream);
 }
+
+// blobs from which the final pass stages FP32 results (2 x 4 B x N > 64 MB)
+constexpr int64_t kUnsortStageMin = int64_t(8) << 20;
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     Plan &pl = c->plan;
@@ -677,6 +681,13 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     uint64_t *lc = &c->launches;
 
     // the launch sequence (the only part of an evaluation a graph replays)
+    // FP32 outputs larger than half the L2: the final pass stages them in
+    // sorted order, then one scatter per component (see k_unsort_f32)
+    float *stage = nullptr;
+    if (mixed && f32 && N >= kUnsortStageMin) {
+        PF_TRY(ensure(c->ustage, size_t(2) * N * sizeof(float), st));
+        stage = static_cast<float *>(c->ustage.p);
+    }
     auto launch_all = [&]() -> int {
     if (c->poison) {
         const size_t es = mixed ? sizeof(float2) : sizeof(double2);
@@ -821,7 +832,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         PF_CUDA(launch_p2p_final(dtask + pl.particles.first, pl.particles.count,
                                  pl.particles.nblocks, dinst, start, skeys,
                                  static_cast<const float4 *>(c->rec.p),
-                                 static_cast<const float2 *>(c->le.p), pb, f32, st, lc));
+                                 static_cast<const float2 *>(c->le.p), pb, f32, perm, stage, N, st,
+                                 lc));
     } else
         PF_CUDA(launch_p2p_f64(grid, static_cast<const uint4 *>(c->items.p), ctrl, dinst, start,
                                static_cast<const double *>(c->xs.p),
@@ -957,7 +969,7 @@ int petfmm_destroy(petfmm_ctx *c) {
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                       &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
-                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->recu, &c->occ, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB, &c->ihist, &c->own, &c->part, &c->pitems, &c->pxtra, &c->pxs, &c->hx, &c->hy,
+                      &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount, &c->recu, &c->occ, &c->items_u, &c->ikA, &c->ikB, &c->ivA, &c->ivB, &c->ihist, &c->own, &c->part, &c->pitems, &c->pxtra, &c->pxs, &c->ustage, &c->hx, &c->hy,
                       &c->hg, &c->hu, &c->hv};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);

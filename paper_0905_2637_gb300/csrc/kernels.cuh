@@ -210,10 +210,13 @@ cudaError_t launch_p2p_pairs(int grid, int deg, int general, const uint4 *pitems
 // Either mode's final pass: far field (L2P) + own + pair slots per blob,
 // written at the caller's index (tasks over blobs).
 cudaError_t launch_p2p_final(const Task *tasks, int ntasks, int64_t nblocks,
-                                const InstDesc *insts, const uint32_t *start,
-                                const uint32_t *skeys, const float4 *rec, const float2 *le,
-                                const PairBufs &pb, int dtype_f32, cudaStream_t st,
-                                uint64_t *launches);
+                             const InstDesc *insts, const uint32_t *start, const uint32_t *skeys,
+                             const float4 *rec, const float2 *le, const PairBufs &pb,
+                             int dtype_f32, const uint32_t *perm, float *stage, int64_t nstage,
+                             cudaStream_t st, uint64_t *launches);
+// (stage != nullptr, FP32 outputs: the pass writes u, v in sorted order to
+// stage[0 .. nstage) and stage[nstage ..), then one launch per component
+// scatters them to the caller's arrays through perm.)
 int p2p_grid(int precision_mixed, int deg, int general, int laplace);
 int device_sm_count();
 constexpr int P2P_TPI_F64 = 32;

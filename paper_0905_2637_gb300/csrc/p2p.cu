@@ -1059,7 +1059,7 @@ __global__ void __launch_bounds__(256) k_p2p_final(
     const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const uint32_t *__restrict__ skeys,
     const float4 *__restrict__ rec, const float2 *__restrict__ le, const PairBufs pb,
-    int dtype_f32) {
+    int dtype_f32, float *__restrict__ stage, int64_t nstage) {
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
     const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
@@ -1124,6 +1124,12 @@ __global__ void __launch_bounds__(256) k_p2p_final(
                 w.y += x.y;
             }
         }
+    }
+    if (stage) {
+        // sorted order; k_unsort writes the caller's arrays
+        stage[r] = w.x;
+        stage[nstage + r] = w.y;
+        return;
     }
     const int64_t q = int64_t(__float_as_uint(rr.w)) - d.poff;
     if (dtype_f32) {
@@ -1266,16 +1272,43 @@ cudaError_t launch_p2p_pairs(int grid, int deg, int general, const uint4 *pitems
     return cudaGetLastError();
 }
 
+// The caller's u (comp 0) or v (comp 1) from the sorted-order stage, FP32
+// outputs.  One component per launch: its scattered 4-byte writes then fit in
+// L2 and leave it as whole sectors, where writing u and v together from the
+// final pass evicts partly written sectors (each one read back and written
+// again).
+__global__ void __launch_bounds__(256) k_unsort_f32(const Task *__restrict__ tasks, int ntasks,
+                                                    const InstDesc *__restrict__ insts,
+                                                    const uint32_t *__restrict__ perm,
+                                                    const float *__restrict__ stage, int comp) {
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
+    if (j >= t.count) return;
+    const InstDesc &d = insts[t.inst];
+    const int64_t r = d.poff + j;
+    float *out = static_cast<float *>(comp ? d.v : d.u);
+    out[int64_t(perm[r]) - d.poff] = stage[r];
+}
+
 cudaError_t launch_p2p_final(const Task *tasks, int ntasks, int64_t nblocks,
-                                const InstDesc *insts, const uint32_t *start,
-                                const uint32_t *skeys, const float4 *rec, const float2 *le,
-                                const PairBufs &pb, int dtype_f32, cudaStream_t st,
-                                uint64_t *launches) {
+                             const InstDesc *insts, const uint32_t *start, const uint32_t *skeys,
+                             const float4 *rec, const float2 *le, const PairBufs &pb,
+                             int dtype_f32, const uint32_t *perm, float *stage, int64_t nstage,
+                             cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
     k_p2p_final<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, skeys, rec, le, pb,
-                                                   dtype_f32);
+                                                   dtype_f32, stage, nstage);
     PF_LAUNCHED(1);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !stage) return e;
+    for (int comp = 0; comp < 2; ++comp) {
+        k_unsort_f32<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm,
+                                                        stage + comp * nstage, comp);
+        PF_LAUNCHED(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_p2p_f64(int grid, const uint4 *items, uint32_t *ctrl, const InstDesc *insts,
