@@ -337,17 +337,40 @@ __device__ __forceinline__ void directed_item(const uint4 item, const InstDesc *
     const uint32_t *st = start + d.soff;
     const int nside = 1 << L;
     const float logw = LAP ? float(d.logw0 - double(L) * 0.69314718055994530942) : 0.f;
-    for (int dy = -1; dy <= 1; ++dy) {
-        const int sy = iy + dy;
-        if (sy < 0 || sy >= nside) continue;
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int sx = ix + dx;
-            if (sx < 0 || sx >= nside) continue;
+    // The pairwise mode's directed items (small leaves, leftover neighbours)
+    // and the Laplace kernel's are mostly short: lanes 0..8 fetch the 9
+    // leaves' source ranges at once (lane q: offset (q % 3 - 1, q / 3 - 1)),
+    // so an item pays one load latency, not nine.  The directed-only vortex
+    // mode (long items) keeps the plain loop, which measured faster there.
+    constexpr bool FETCH9 = PAIRS || LAP;
+    uint32_t lj0 = 0, lj1 = 0;
+    if (FETCH9 && lane < 9) {
+        const int sx = ix + lane % 3 - 1, sy = iy + lane / 3 - 1;
+        if (sx >= 0 && sy >= 0 && sx < nside && sy < nside) {
             const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
-            const uint32_t j0 = st[nm], j1 = st[nm + 1];
+            lj0 = st[nm];
+            lj1 = st[nm + 1];
+        }
+    }
+    const uint32_t nme = PAIRS ? st[m + 1] - st[m] : 0u;
+    for (int q = 0; q < 9; ++q) {
+        const int dx = q % 3 - 1, dy = q / 3 - 1;
+        uint32_t j0, j1;
+        if (FETCH9) {
+            j0 = __shfl_sync(0xffffffffu, lj0, q);
+            j1 = __shfl_sync(0xffffffffu, lj1, q);
+        } else {
+            const int sx = ix + dx, sy = iy + dy;
+            if (sx < 0 || sy < 0 || sx >= nside || sy >= nside) continue;
+            const uint32_t nm = morton_key(uint32_t(sx), uint32_t(sy));
+            j0 = st[nm];
+            j1 = st[nm + 1];
+        }
+        if (j0 == j1) continue;
+        {
             // pairwise mode: the leaves the pair kernel covers (the leaf itself
             // included) are skipped
-            if (PAIRS && pairwise(st[m + 1] - st[m], j1 - j0)) continue;
+            if (PAIRS && pairwise(nme, j1 - j0)) continue;
             const float xa = ra.x - float(dx), ya = ra.y - float(dy);
             const float xb = rb.x - float(dx), yb = rb.y - float(dy);
             // the stride-1 loop keeps constant load offsets after unrolling
