@@ -562,7 +562,8 @@ void stage_mark(petfmm_ctx *c, int stage) {
         cudaEventRecord(c->ev[stage], c->stream);
 }
 
-// blobs from which the final pass stages FP32 results (2 x 4 B x N > 64 MB)
+// blobs of one instance from which the final pass stages FP32 results
+// (2 x 4 B x n > 64 MB)
 constexpr int64_t kUnsortStageMin = int64_t(8) << 20;
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
@@ -684,7 +685,9 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     // FP32 outputs larger than half the L2: the final pass stages them in
     // sorted order, then one scatter per component (see k_unsort_f32)
     float *stage = nullptr;
-    if (mixed && f32 && N >= kUnsortStageMin) {
+    int64_t nmax = 0;  // an instance's scatter stays within its own arrays
+    for (const InstDesc &d : pl.inst) nmax = std::max(nmax, d.n);
+    if (mixed && f32 && nmax >= kUnsortStageMin) {
         PF_TRY(ensure(c->ustage, size_t(2) * N * sizeof(float), st));
         stage = static_cast<float *>(c->ustage.p);
     }
