@@ -69,10 +69,20 @@ struct TaskRange {
 struct Plan {
     std::vector<InstDesc> inst;
     std::vector<Task> tasks;
-    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tile, m2l_log;
+    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_log;
+    // tiled SIMT M2L, one launch per order class (p <= 8, 12, 18, 24): each
+    // launch's kernel is specialised for its class's largest order
+    static constexpr int kTileClasses = 4;
+    TaskRange m2l_tile[kTileClasses];
+    int tile_pmax[kTileClasses] = {};
+    int64_t tile_blocks() const {
+        int64_t b = 0;
+        for (const TaskRange &r : m2l_tile) b += r.nblocks;
+        return b;
+    }
     std::vector<TaskRange> m2m, l2l;  // in launch order
     int64_t N = 0, nleaves = 0, nstart = 0, ncoef = 0, items_cap = 0;
-    int nbits = 0, pmax = 1, Lmax = 0, tile_pmax = 1;
+    int nbits = 0, pmax = 1, Lmax = 0;
     int deg = 0, general = 0;          // mixed P2P variant (max over instances)
     size_t tc_smem = 0;                // dynamic shared memory of the tensor-core M2L
 };
@@ -334,11 +344,14 @@ void flatten_tasks(Plan &pl) {
     put(pl.leaves_wl);
     put(pl.m2l);
     put(pl.m2l_tc);
-    put(pl.m2l_tile);
+    for (TaskRange &r : pl.m2l_tile) put(r);
     put(pl.m2l_log);
     for (TaskRange &r : pl.m2m) put(r);
     for (TaskRange &r : pl.l2l) put(r);
 }
+
+// order class of the tiled M2L launches: p <= 8, 12, 18, 24
+int tile_class(int p) { return p <= 8 ? 0 : p <= 12 ? 1 : p <= 18 ? 2 : 3; }
 
 int build_plan(int precision, int kernel, bool use_tc, int tc_segmax, double near_tol,
                const std::vector<Problem> &probs, Plan &pl) {
@@ -421,17 +434,23 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_segmax, double nea
         items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
     }
     // the other levels of the mixed path: dense units on the tiled SIMT kernel
-    // (their units follow the tensor-core units in the unit-count array)
+    // (their units follow the tensor-core units in the unit-count array, class
+    // by class)
     if (precision == PETFMM_MIXED) {
-        for (int i = 0; i < ni; ++i) {
-            InstDesc &d = pl.inst[i];
-            if (!m2l_tile_supported(d.p)) continue;
-            for (int l = 2; l <= d.L; ++l) {
-                if ((d.tc_levels >> l) & 1u) continue;
-                d.tc_unit0[l] = pl.m2l_tc.nblocks + pl.m2l_tile.nblocks;
-                add_task(pl.m2l_tile, i, l, m2l_tile_units(l), 1);
-                pl.tile_pmax = std::max(pl.tile_pmax, d.p);
+        int64_t base = pl.m2l_tc.nblocks;
+        for (int cls = 0; cls < Plan::kTileClasses; ++cls) {
+            TaskRange &tr = pl.m2l_tile[cls];
+            for (int i = 0; i < ni; ++i) {
+                InstDesc &d = pl.inst[i];
+                if (!m2l_tile_supported(d.p) || tile_class(d.p) != cls) continue;
+                for (int l = 2; l <= d.L; ++l) {
+                    if ((d.tc_levels >> l) & 1u) continue;
+                    d.tc_unit0[l] = base + tr.nblocks;
+                    add_task(tr, i, l, m2l_tile_units(l), 1);
+                    pl.tile_pmax[cls] = std::max(pl.tile_pmax[cls], d.p);
+                }
             }
+            base += tr.nblocks;
         }
     }
     // M2M rounds: round r computes level L_i - 1 - r (>= 2) of every instance.
@@ -533,13 +552,15 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     if (!pl.tasks.empty()) k.add(pl.tasks.data(), pl.tasks.size() * sizeof(Task));
     auto range = [&](const TaskRange &r) { k.put(r.first); k.put(r.count); k.put(r.nblocks); };
     for (const TaskRange *r : {&pl.morton, &pl.start, &pl.particles, &pl.leaves_p2m, &pl.leaves_wl,
-                               &pl.m2l, &pl.m2l_tc, &pl.m2l_tile, &pl.m2l_log})
+                               &pl.m2l, &pl.m2l_tc, &pl.m2l_log})
         range(*r);
+    for (const TaskRange &r : pl.m2l_tile) range(r);
+    for (int cls = 0; cls < Plan::kTileClasses; ++cls) k.put(pl.tile_pmax[cls]);
     for (const TaskRange &r : pl.m2m) range(r);
     for (const TaskRange &r : pl.l2l) range(r);
     k.put(pl.m2m.size()); k.put(pl.l2l.size());
     k.put(pl.N); k.put(pl.nleaves); k.put(pl.nstart); k.put(pl.ncoef); k.put(pl.items_cap);
-    k.put(pl.nbits); k.put(pl.pmax); k.put(pl.tile_pmax); k.put(pl.deg); k.put(pl.general);
+    k.put(pl.nbits); k.put(pl.pmax); k.put(pl.deg); k.put(pl.general);
     k.put(pl.tc_smem); k.put(grid);
     k.put(c->precision); k.put(c->dtype); k.put(c->timing); k.put(c->p2p_mode); k.put(c->poison);
     k.put(c->tc_dense_pct); k.put(c->spin_limit); k.put(c->p2p_pairs); k.put(c->kernel);
@@ -615,7 +636,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->occ, size_t(pl.nleaves) * sizeof(uint2), st));
     PF_TRY(ensure(c->off, size_t(pl.nleaves) * 4, st));
     PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
-    PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks + pl.m2l_tile.nblocks) * sizeof(uint32_t),
+    PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks + pl.tile_blocks()) * sizeof(uint32_t),
                   st));
     if (mixed) PF_TRY(ensure(c->own, size_t(N) * sizeof(float2), st));
     if (pairs) {
@@ -747,15 +768,18 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     }
     stage_mark(c, PETFMM_STAGE_M2L);
     uint32_t *ucount = nullptr;
-    if (pl.m2l_tc.count || pl.m2l_tile.count) {
+    if (pl.m2l_tc.count || pl.tile_blocks()) {
         ucount = static_cast<uint32_t *>(c->ucount.p);
         if (pl.m2l_tc.count)
             PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc.first, pl.m2l_tc.count,
                                          pl.m2l_tc.nblocks, dinst, start, ucount, st, lc));
-        if (pl.m2l_tile.count)
-            PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tile.first, pl.m2l_tile.count,
-                                         pl.m2l_tile.nblocks, dinst, start,
-                                         ucount + pl.m2l_tc.nblocks, st, lc));
+        int64_t base = pl.m2l_tc.nblocks;
+        for (const TaskRange &tr : pl.m2l_tile) {
+            if (tr.count)
+                PF_CUDA(launch_tc_unit_count(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
+                                             ucount + base, st, lc));
+            base += tr.nblocks;
+        }
     }
     if (pl.m2l.count) {
         if (mixed)
@@ -777,12 +801,18 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                               pl.tc_smem, spin, reinterpret_cast<int *>(ctrl + CTRL_STATUS), st,
                               lc));
     }
-    if (pl.m2l_tile.count)
-        PF_CUDA(launch_m2l_tile(dtask + pl.m2l_tile.first, pl.m2l_tile.count, pl.m2l_tile.nblocks,
-                                pl.tile_pmax, dinst, start,
-                                static_cast<const float2 *>(c->me.p),
-                                static_cast<float2 *>(c->le.p), ucount + pl.m2l_tc.nblocks,
-                                c->tc_dense_pct, st, lc));
+    {
+        int64_t base = pl.m2l_tc.nblocks;
+        for (int cls = 0; cls < Plan::kTileClasses; ++cls) {
+            const TaskRange &tr = pl.m2l_tile[cls];
+            if (tr.count)
+                PF_CUDA(launch_m2l_tile(dtask + tr.first, tr.count, tr.nblocks, pl.tile_pmax[cls],
+                                        dinst, start, static_cast<const float2 *>(c->me.p),
+                                        static_cast<float2 *>(c->le.p), ucount + base,
+                                        c->tc_dense_pct, st, lc));
+            base += tr.nblocks;
+        }
+    }
     if (pl.m2l_log.count) {
         if (mixed)
             PF_CUDA(launch_m2l_logterm<float>(dtask + pl.m2l_log.first, pl.m2l_log.count,
@@ -1090,7 +1120,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     emit(4, pl.leaves_wl);
     emit(5, pl.m2l);
     emit(6, pl.m2l_tc);
-    emit(7, pl.m2l_tile);
+    for (int cls = 0; cls < Plan::kTileClasses; ++cls) emit(70 + cls, pl.m2l_tile[cls]);
     for (size_t r = 0; r < pl.m2m.size(); ++r) emit(100 + int64_t(r), pl.m2m[r]);
     for (size_t r = 0; r < pl.l2l.size(); ++r) emit(200 + int64_t(r), pl.l2l[r]);
     return n;

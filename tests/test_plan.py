@@ -17,7 +17,7 @@ def lib():
     return _lib
 
 
-UNITS_PER_BLOCK = {0: 256, 1: 256, 2: 256, 3: 256, 4: 256, 5: 32, 6: 1, 7: 1}
+UNITS_PER_BLOCK = {0: 256, 1: 256, 2: 256, 3: 256, 4: 256, 5: 32, 6: 1, 70: 1, 71: 1, 72: 1, 73: 1}
 
 
 def _instances(seed, k):
@@ -71,10 +71,14 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
         # the other levels of the mixed path (p <= 24) get the tiled SIMT
         # launch, one CTA per (class, 128 target boxes: a 128-cell segment of
         # a parent row, or several whole rows where rows are shorter)
-        tile = sorted(int(r[2]) for r in ranges.get(7, []) if r[1] == i)
+        # (one launch per order class, p <= 8, 12, 18, 24: ids 70 .. 73)
+        cls = 70 + (0 if p <= 8 else 1 if p <= 12 else 2 if p <= 18 else 3)
+        tile_rows = [r for rid in range(70, 74) for r in ranges.get(rid, []) if r[1] == i]
+        assert all(r[0] == cls for r in tile_rows)
+        tile = sorted(int(r[2]) for r in tile_rows)
         assert tile == ([l for l in range(2, L + 1) if l not in tc]
                         if precision == 1 and p <= 24 else [])
-        for r in ranges.get(7, []):
+        for r in tile_rows:
             if r[1] == i:
                 w = 2 ** (int(r[2]) - 1)
                 seg = min(w, 128)
