@@ -61,8 +61,11 @@ __device__ __forceinline__ float leaf_coord(TIn xin, float x0h, float x0l, float
 // of order u^2 (u = 2^-24: one rounding each of xf, x0f, scalef, the
 // difference and the product); the margin m = 8 u scale (|x| + |x0|) also
 // covers the roundings of s32 -/+ m.  If both ends of [s32 - m, s32 + m] fall
-// in the same bin and inside (0.5, nb - 0.5), the FP64 value is in that bin
-// too, and strictly inside the domain (no clamping, no out-of-domain report).
+// in the same bin and inside (0, nb (1 - 2^-20)), the FP64 value s is in that
+// bin too (no clamping) and the point is inside the domain: s > 0 means
+// fl(x - x0) > 0, i.e. x > x0; s < nb (1 - 2^-20) bounds x - x0 below
+// W (1 - 2^-21), so x <= fl(x0 + W) whenever |x0 + W| <= 2^32 W -- and a
+// domain farther from the origin has m > nb, so the test fails there.
 // Otherwise (near a bin edge or the domain boundary, NaN, Inf) returns false
 // and the caller takes the FP64 path.  The result is therefore bit-identical.
 __device__ __forceinline__ bool bin_coord_fast(float xf, float x0f, float scalef, uint32_t nb,
@@ -70,7 +73,7 @@ __device__ __forceinline__ bool bin_coord_fast(float xf, float x0f, float scalef
     const float s = __fmul_rn(__fsub_rn(xf, x0f), scalef);
     const float m = __fmul_rn(__fmul_rn(__fadd_rn(fabsf(xf), fabsf(x0f)), scalef), 0x1p-21f);
     const float lo = __fsub_rn(s, m), hi = __fadd_rn(s, m);
-    if (!(lo > 0.5f && hi < float(nb) - 0.5f)) return false;
+    if (!(lo > 0.0f && hi < float(nb) * (1.0f - 0x1p-20f))) return false;
     const float f = floorf(lo);
     if (f != floorf(hi)) return false;
     *bin = uint32_t(f);

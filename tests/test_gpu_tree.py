@@ -102,15 +102,16 @@ def test_outside_particle_reports_edomain_then_recovers():
     ctx.close()
 
 
+@pytest.mark.parametrize("L", [10, 3])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("dom", [(0.1234567891, -0.3718281828, 0.7071067811865476),
-                                 (1.0e5 + 0.3, -2.5e4, 3.0)])
-def test_binning_near_bin_edges(orc, dtype, dom):
+                                 (1.0e5 + 0.3, -2.5e4, 3.0), (-2.0, 1.0, 4.0)])
+def test_binning_near_bin_edges(orc, dtype, dom, L):
     # The kernel bins in FP32 where that provably gives the FP64 bin and falls
     # back to FP64 otherwise: points on and a few ulps around every bin edge
-    # of one row, in an awkward domain (x0 and the scale not representable in
-    # FP32; the second one so far from the origin that FP32 never decides)
-    L = 10
+    # of one row -- the domain's own edges included -- in awkward domains (x0
+    # and the scale not representable in FP32; one so far from the origin that
+    # FP32 never decides; one straddling it), on a deep and a shallow tree
     nb = 1 << L
     x0, y0, wd = dom
     ft = np.float32 if dtype == "f32" else np.float64
