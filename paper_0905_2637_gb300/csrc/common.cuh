@@ -66,6 +66,7 @@ struct InstDesc {
     uint32_t tc_levels;                 // bit l: level l's dense units run on the tensor
                                         // cores (else, if tc_unit0[l] >= 0, on the
                                         // tiled SIMT kernel)
+    uint32_t tc2_levels;                // bit l: ... on the tensor cores in 8 x 16 blocks
     // mixed-precision P2P constants (leaf units)
     float kappa;            // w^2 / (2 sigma^2): q = kappa * rho^2
     float cnear;            // w / (4 pi sigma^2)
@@ -234,6 +235,21 @@ __host__ __device__ __forceinline__ int64_t tc_unit_of(int l, int segmax, int c,
     return (int64_t(c) * W + Py) * nseg + Px / s;
 }
 
+// Block units of the tensor-core M2L (levels whose parent rows are too short
+// for row units): 8 x 16 parent cells (x, y) of one target class, 128 targets;
+// units are numbered (c (W / 16) + Py / 16) (W / 8) + Px / 8.
+constexpr int TC2_BX = 8, TC2_BY = 16;
+
+__host__ __device__ __forceinline__ void tc2_unit_decode(int l, int64_t unit, int *c, int *Py0,
+                                                         int *Px0) {
+    const int W = 1 << (l - 1);
+    const int nbx = W / TC2_BX, nby = W / TC2_BY;
+    *c = int(unit / (int64_t(nbx) * nby));
+    const int64_t rem = unit - int64_t(*c) * nbx * nby;
+    *Py0 = int(rem / nbx) * TC2_BY;
+    *Px0 = int(rem - (rem / nbx) * nbx) * TC2_BX;
+}
+
 // Units of the tiled SIMT M2L: a segment of M2L_TILE_SEG parent cells of one
 // parent row, or, where rows are shorter, R whole rows of together at most
 // M2L_TILE_ROWS_BOXES target boxes (half a full unit: a shallow level has few
@@ -275,6 +291,10 @@ __host__ __device__ __forceinline__ int64_t unit_of(const InstDesc &d, int l, in
         return tc_unit_of(l, d.tc_segmax, c, Py, Px);
     }
     const int W = 1 << (l - 1);
+    if ((d.tc2_levels >> l) & 1u) {
+        *nbox = TC2_BX * TC2_BY;
+        return (int64_t(c) * (W / TC2_BY) + Py / TC2_BY) * (W / TC2_BX) + Px / TC2_BX;
+    }
     int R, s;
     tile_geom(l, &R, &s);
     *nbox = R * s;

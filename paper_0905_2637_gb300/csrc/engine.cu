@@ -69,7 +69,7 @@ struct TaskRange {
 struct Plan {
     std::vector<InstDesc> inst;
     std::vector<Task> tasks;
-    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_log;
+    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tc2, m2l_log;
     // tiled SIMT M2L, one launch per order class (p <= 8, 12, 18, 24): each
     // launch's kernel is specialised for its class's largest order
     static constexpr int kTileClasses = 4;
@@ -85,6 +85,7 @@ struct Plan {
     int nbits = 0, pmax = 1, Lmax = 0;
     int deg = 0, general = 0;          // mixed P2P variant (max over instances)
     size_t tc_smem = 0;                // dynamic shared memory of the tensor-core M2L
+    int tc2_pmax = 0;                  // largest order among the block units
 };
 
 struct Problem {
@@ -116,6 +117,7 @@ struct petfmm_ctx {
     int p2p_mode = 0;  // 0: work items heaviest first (Eq. 14 weights), 1: Morton order
     bool p2p_pairs = true;  // mixed path: neighbouring leaves pairwise (PETFMM_OPT_P2P_PAIRS)
     int kernel = KERNEL_VORTEX;  // PETFMM_OPT_KERNEL
+    int tc_blocks = 0;           // PETFMM_OPT_TC_BLOCKS: 0 automatic, 1 always, 2 never
     bool poison = false;
     bool m2l_tc = true;
     // measured on GB300 (clustered 16M and lattice 1M blobs): 128-cell units
@@ -344,6 +346,7 @@ void flatten_tasks(Plan &pl) {
     put(pl.leaves_wl);
     put(pl.m2l);
     put(pl.m2l_tc);
+    put(pl.m2l_tc2);
     for (TaskRange &r : pl.m2l_tile) put(r);
     put(pl.m2l_log);
     for (TaskRange &r : pl.m2m) put(r);
@@ -351,9 +354,14 @@ void flatten_tasks(Plan &pl) {
 }
 
 // order class of the tiled M2L launches: p <= 8, 12, 18, 24
+// Fewest block units for which the tensor-core block launch beats the tiled
+// SIMT kernel (measured: a batch of 512 trees has 13,040; one tree of 2^20
+// blobs, 168).
+constexpr int64_t kTc2MinUnits = 2048;
+
 int tile_class(int p) { return p <= 8 ? 0 : p <= 12 ? 1 : p <= 18 ? 2 : 3; }
 
-int build_plan(int precision, int kernel, bool use_tc, int tc_segmax, double near_tol,
+int build_plan(int precision, int kernel, bool use_tc, int tc_blocks, int tc_segmax, double near_tol,
                const std::vector<Problem> &probs, Plan &pl) {
     pl = Plan();
     const int ni = int(probs.size());
@@ -413,6 +421,7 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_segmax, double nea
         for (int l = 0; l <= MAX_L; ++l) d.tc_unit0[l] = -1;
         d.tc_segmax = tc_segmax;
         d.tc_levels = 0;
+        d.tc2_levels = 0;
         add_task(pl.morton, i, d.L, d.n, 256);
         add_task(pl.start, i, d.L, nleaf + 1, 256);
         add_task(pl.particles, i, d.L, d.n, 256);
@@ -433,18 +442,39 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_segmax, double nea
         }
         items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
     }
-    // the other levels of the mixed path: dense units on the tiled SIMT kernel
-    // (their units follow the tensor-core units in the unit-count array, class
-    // by class)
+    // the other levels of the mixed path: dense units on the tensor cores in
+    // 8 x 16 blocks where rows hold 16 to 64 parent cells, on the tiled SIMT
+    // kernel below that (their units follow the row units in the unit-count
+    // array: blocks, then the tile classes one by one)
     if (precision == PETFMM_MIXED) {
         int64_t base = pl.m2l_tc.nblocks;
+        // blocks only where there are many of them (a batch): a single tree's
+        // levels 5 to 7 keep more CTAs in flight on the tiled SIMT kernel
+        int64_t blocks = 0;
+        for (int i = 0; i < ni; ++i)
+            for (int l = 2; l <= pl.inst[i].L; ++l)
+                if (!((pl.inst[i].tc_levels >> l) & 1u) && m2l_tc2_supported(pl.inst[i].p, l))
+                    blocks += m2l_tc2_units(l);
+        if (use_tc && (tc_blocks == 1 || (tc_blocks == 0 && blocks >= kTc2MinUnits))) {
+            for (int i = 0; i < ni; ++i) {
+                InstDesc &d = pl.inst[i];
+                for (int l = 2; l <= d.L; ++l) {
+                    if (((d.tc_levels >> l) & 1u) || !m2l_tc2_supported(d.p, l)) continue;
+                    d.tc_unit0[l] = base + pl.m2l_tc2.nblocks;
+                    d.tc2_levels |= 1u << l;
+                    add_task(pl.m2l_tc2, i, l, m2l_tc2_units(l), 1);
+                    pl.tc2_pmax = std::max(pl.tc2_pmax, d.p);
+                }
+            }
+        }
+        base += pl.m2l_tc2.nblocks;
         for (int cls = 0; cls < Plan::kTileClasses; ++cls) {
             TaskRange &tr = pl.m2l_tile[cls];
             for (int i = 0; i < ni; ++i) {
                 InstDesc &d = pl.inst[i];
                 if (!m2l_tile_supported(d.p) || tile_class(d.p) != cls) continue;
                 for (int l = 2; l <= d.L; ++l) {
-                    if ((d.tc_levels >> l) & 1u) continue;
+                    if (((d.tc_levels | d.tc2_levels) >> l) & 1u) continue;
                     d.tc_unit0[l] = base + tr.nblocks;
                     add_task(tr, i, l, m2l_tile_units(l), 1);
                     pl.tile_pmax[cls] = std::max(pl.tile_pmax[cls], d.p);
@@ -552,7 +582,7 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     if (!pl.tasks.empty()) k.add(pl.tasks.data(), pl.tasks.size() * sizeof(Task));
     auto range = [&](const TaskRange &r) { k.put(r.first); k.put(r.count); k.put(r.nblocks); };
     for (const TaskRange *r : {&pl.morton, &pl.start, &pl.particles, &pl.leaves_p2m, &pl.leaves_wl,
-                               &pl.m2l, &pl.m2l_tc, &pl.m2l_log})
+                               &pl.m2l, &pl.m2l_tc, &pl.m2l_tc2, &pl.m2l_log})
         range(*r);
     for (const TaskRange &r : pl.m2l_tile) range(r);
     for (int cls = 0; cls < Plan::kTileClasses; ++cls) k.put(pl.tile_pmax[cls]);
@@ -561,9 +591,10 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     k.put(pl.m2m.size()); k.put(pl.l2l.size());
     k.put(pl.N); k.put(pl.nleaves); k.put(pl.nstart); k.put(pl.ncoef); k.put(pl.items_cap);
     k.put(pl.nbits); k.put(pl.pmax); k.put(pl.deg); k.put(pl.general);
-    k.put(pl.tc_smem); k.put(grid);
+    k.put(pl.tc_smem); k.put(pl.tc2_pmax); k.put(grid);
     k.put(c->precision); k.put(c->dtype); k.put(c->timing); k.put(c->p2p_mode); k.put(c->poison);
     k.put(c->tc_dense_pct); k.put(c->spin_limit); k.put(c->p2p_pairs); k.put(c->kernel);
+    k.put(c->tc_blocks);
     for (const DevBuf *b : {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                             &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
                             &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount,
@@ -589,7 +620,8 @@ constexpr int64_t kUnsortStageMin = int64_t(8) << 20;
 
 int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     Plan &pl = c->plan;
-    PF_TRY(build_plan(c->precision, c->kernel, c->m2l_tc, c->tc_segmax, c->near_tol, probs, pl));
+    PF_TRY(build_plan(c->precision, c->kernel, c->m2l_tc, c->tc_blocks, c->tc_segmax, c->near_tol,
+                      probs, pl));
     PF_TRY(attach_tables(c, pl));
     cudaStream_t st = c->stream;  // the launch sequence's stream (a capture swaps it)
     const bool mixed = c->precision == PETFMM_MIXED;
@@ -636,7 +668,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->occ, size_t(pl.nleaves) * sizeof(uint2), st));
     PF_TRY(ensure(c->off, size_t(pl.nleaves) * 4, st));
     PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
-    PF_TRY(ensure(c->ucount, size_t(pl.m2l_tc.nblocks + pl.tile_blocks()) * sizeof(uint32_t),
+    PF_TRY(ensure(c->ucount,
+                  size_t(pl.m2l_tc.nblocks + pl.m2l_tc2.nblocks + pl.tile_blocks()) * sizeof(uint32_t),
                   st));
     if (mixed) PF_TRY(ensure(c->own, size_t(N) * sizeof(float2), st));
     if (pairs) {
@@ -768,12 +801,16 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     }
     stage_mark(c, PETFMM_STAGE_M2L);
     uint32_t *ucount = nullptr;
-    if (pl.m2l_tc.count || pl.tile_blocks()) {
+    if (pl.m2l_tc.count || pl.m2l_tc2.count || pl.tile_blocks()) {
         ucount = static_cast<uint32_t *>(c->ucount.p);
         if (pl.m2l_tc.count)
             PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc.first, pl.m2l_tc.count,
                                          pl.m2l_tc.nblocks, dinst, start, ucount, st, lc));
-        int64_t base = pl.m2l_tc.nblocks;
+        if (pl.m2l_tc2.count)
+            PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc2.first, pl.m2l_tc2.count,
+                                         pl.m2l_tc2.nblocks, dinst, start,
+                                         ucount + pl.m2l_tc.nblocks, st, lc));
+        int64_t base = pl.m2l_tc.nblocks + pl.m2l_tc2.nblocks;
         for (const TaskRange &tr : pl.m2l_tile) {
             if (tr.count)
                 PF_CUDA(launch_tc_unit_count(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
@@ -801,8 +838,16 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                               pl.tc_smem, spin, reinterpret_cast<int *>(ctrl + CTRL_STATUS), st,
                               lc));
     }
+    if (pl.m2l_tc2.count) {
+        const long long spin = c->spin_limit > 0 ? c->spin_limit : c->spin_limit < 0 ? 0 : (1LL << 26);
+        PF_CUDA(launch_m2l_tc2(dtask + pl.m2l_tc2.first, pl.m2l_tc2.count, pl.m2l_tc2.nblocks,
+                               dinst, start, static_cast<const float2 *>(c->me.p),
+                               static_cast<float2 *>(c->le.p), ucount + pl.m2l_tc.nblocks,
+                               c->tc_dense_pct, pl.tc2_pmax, spin,
+                               reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
+    }
     {
-        int64_t base = pl.m2l_tc.nblocks;
+        int64_t base = pl.m2l_tc.nblocks + pl.m2l_tc2.nblocks;
         for (int cls = 0; cls < Plan::kTileClasses; ++cls) {
             const TaskRange &tr = pl.m2l_tile[cls];
             if (tr.count)
@@ -1100,7 +1145,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     int rc = problems_from(n_inst, inst, probs);
     if (rc) return rc;
     Plan pl;
-    rc = build_plan(precision, KERNEL_VORTEX, true, kTcSegDefault, kNearTolDefault, probs, pl);
+    rc = build_plan(precision, KERNEL_VORTEX, true, 0, kTcSegDefault, kNearTolDefault, probs, pl);
     if (rc) return rc;
     int n = 0;
     auto emit = [&](int64_t id, const TaskRange &r) {
@@ -1120,6 +1165,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     emit(4, pl.leaves_wl);
     emit(5, pl.m2l);
     emit(6, pl.m2l_tc);
+    emit(7, pl.m2l_tc2);
     for (int cls = 0; cls < Plan::kTileClasses; ++cls) emit(70 + cls, pl.m2l_tile[cls]);
     for (size_t r = 0; r < pl.m2m.size(); ++r) emit(100 + int64_t(r), pl.m2m[r]);
     for (size_t r = 0; r < pl.l2l.size(); ++r) emit(200 + int64_t(r), pl.l2l[r]);
@@ -1166,6 +1212,10 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
             return PETFMM_OK;
         case PETFMM_OPT_GRAPH: c->use_graph = value != 0; return PETFMM_OK;
         case PETFMM_OPT_P2P_PAIRS: c->p2p_pairs = value != 0; return PETFMM_OK;
+        case PETFMM_OPT_TC_BLOCKS:
+            if (value < 0 || value > 2) return PETFMM_EINVAL;
+            c->tc_blocks = int(value);
+            return PETFMM_OK;
         case PETFMM_OPT_KERNEL:
             if (value != PETFMM_KERNEL_VORTEX && value != PETFMM_KERNEL_LAPLACE)
                 return PETFMM_EINVAL;

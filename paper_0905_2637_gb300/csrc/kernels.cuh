@@ -98,6 +98,15 @@ cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const Ins
 // Tensor-core M2L (mixed path) for levels with at least 128 parent cells per
 // row and p <= 24: one CTA per (target class, parent row, segment) unit.
 bool m2l_tc_supported(int p, int level, int segmax);
+// block units (8 x 16 parent cells) for 16 <= W < 128 parent cells per side
+bool m2l_tc2_supported(int p, int level);
+int64_t m2l_tc2_units(int level);
+size_t m2l_tc2_smem_bytes(int p);
+// pmax: the largest order among the launch's units (sizes shared memory)
+cudaError_t launch_m2l_tc2(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                           const uint32_t *start, const float2 *me, float2 *le,
+                           const uint32_t *ucount, int dense_pct, int pmax, long long spin_limit,
+                           int *status, cudaStream_t st, uint64_t *launches);
 int64_t m2l_tc_units(int level, int segmax);
 size_t m2l_tc_smem_bytes(int p, int seg);
 int m2l_tc_seg(int level, int segmax);

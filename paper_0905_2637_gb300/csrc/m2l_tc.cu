@@ -76,10 +76,15 @@ __global__ void __launch_bounds__(256) k_tc_unit_count(const Task *__restrict__ 
     const InstDesc &d = insts[t.inst];
     const int l = t.level;
     int c, Py0, R = 1, Px0, SEG;
-    if ((d.tc_levels >> l) & 1u)
+    if ((d.tc_levels >> l) & 1u) {
         tc_unit_decode(l, d.tc_segmax, u - t.block0, &c, &Py0, &Px0, &SEG);
-    else
+    } else if ((d.tc2_levels >> l) & 1u) {
+        tc2_unit_decode(l, u - t.block0, &c, &Py0, &Px0);
+        R = TC2_BY;
+        SEG = TC2_BX;
+    } else {
         tile_unit_decode(l, u - t.block0, &c, &Py0, &R, &Px0, &SEG);
+    }
     const uint32_t *st = start + d.soff;
     uint32_t cnt = 0;
     for (int i = lane; i < R * SEG; i += 32) {
@@ -336,6 +341,283 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols));
+}
+
+// ----------------------------------------------------------------------------
+// Block units: the levels whose parent rows are too short for the row units
+// above (16 <= W <= 64 parent cells per side).  One CTA per (target class c,
+// block of 8 x 16 parent cells); the block's 128 targets are the MMA's M
+// rows, target row y (8 cells) being core-matrix group y.  For each source
+// class c' the CTA stages, once, the expansions of the block's cells plus a
+// one-cell halo (10 x 18 cells, empty and out-of-domain boxes as zeros) in
+// the K-major layout with a staged row of 10 cells as the group stride (SBO);
+// the nine parent offsets (dx, dy) of the class read the same staged data
+// from a start dy staged rows and dx cells away.  Operators, 3xTF32 split and
+// accumulation as in the row units; one accumulator (128 lanes x Npad
+// columns) per CTA.
+//
+// The strips (c', dy) of the unit run in a fixed order: the operator images
+// of the strip's (up to three) dx shifts arrive by bulk asynchronous copies
+// (one thread, completion counted in bytes on an mbarrier), the MMAs follow,
+// and the buffers are reused once they have completed.  Two CTAs share an
+// SM (about 104 KB of shared memory each at p = 17), so one CTA's copies and
+// operand splits overlap the other's MMAs.  (A one-CTA-per-SM variant that
+// double-buffered operands and issued the next strip's copies under the
+// current MMAs measured slower: with N = 2p padded to 48, the MMAs are too
+// short to hide one CTA's waits.)
+// ----------------------------------------------------------------------------
+constexpr int TC2_HX = TC2_BX + 2, TC2_HY = TC2_BY + 2;
+constexpr int TC2_HALO = TC2_HX * TC2_HY;  // staged cells per source class
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
+    const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
+    const uint32_t *__restrict__ start, const float2 *__restrict__ me, float2 *__restrict__ le,
+    const uint32_t *__restrict__ ucount, int dense_pct, long long spin_limit, int *status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[1], bbar[1];
+    __shared__ uint32_t tslot;
+    __shared__ uint32_t sany;
+    __shared__ uint8_t hocc[4][TC2_HALO];  // occupied halo cells, per source class
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int ti = find_task(tasks, ntasks, blockIdx.x);
+    const Task t = tasks[ti];
+    const InstDesc &d = insts[t.inst];
+    const int l = t.level, L = d.L, p = d.p;
+    const int W = 1 << (l - 1);
+    int c, Py0, Px0;
+    tc2_unit_decode(l, int64_t(blockIdx.x) - t.block0, &c, &Py0, &Px0);
+    // sparse units are left to the SIMT kernel (same test there)
+    if (!tc_unit_dense(ucount[blockIdx.x], TC2_BX * TC2_BY, dense_pct)) return;
+    const int cx = c & 1, cy = c >> 1;
+    const uint32_t *st = start + d.soff;
+
+    const int K2 = 2 * p;
+    const int Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
+    const int KG = Kpad / 4;
+    const size_t aplane = size_t(KG) * TC2_HALO * 4;  // floats of one A image (hi or lo)
+    const int bslot = Kpad * Npad;                     // floats of one B image
+    float *A0 = reinterpret_cast<float *>(smem);       // hi, then lo
+    float *B0 = A0 + size_t(2) * aplane;               // 6 images: hi and lo of 3 shifts
+    auto a_hi = [&](int) { return A0; };
+    auto b_img = [&](int, int slot) { return B0 + size_t(slot) * bslot; };
+    // zero the K padding of every staged cell once (never overwritten)
+    for (int i = tid; i < TC2_HALO * (Kpad - K2); i += TC_THREADS) {
+        const int r = i / (Kpad - K2), k = K2 + i % (Kpad - K2);
+        const size_t o = (size_t(k >> 2) * TC2_HALO + r) * 4 + (k & 3);
+        A0[o] = 0.f;
+        A0[aplane + o] = 0.f;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bbar[0])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        sany = 0;
+    }
+    const uint32_t ncols = Npad <= 32 ? 32u : 64u;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tslot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // occupancy of the halo cells of all four source classes (one round)
+    for (int i = tid; i < 4 * TC2_HALO; i += TC_THREADS) {
+        const int cs = i / TC2_HALO, q = i - cs * TC2_HALO;
+        const int hy = q / TC2_HX, hx = q - hy * TC2_HX;
+        const int Px = Px0 - 1 + hx, Py = Py0 - 1 + hy;
+        bool o = false;
+        if (Px >= 0 && Px < W && Py >= 0 && Py < W)
+            o = box_count(st, L, l, morton_key(uint32_t(2 * Px + (cs & 1)),
+                                               uint32_t(2 * Py + (cs >> 1)))) != 0;
+        hocc[cs][q] = o;
+        if (o) atomicOr(&sany, 1u << cs);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = tslot;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(Npad >> 3) << 17) |
+                           (uint32_t(128 >> 4) << 24);
+    const uint32_t LBO_A = uint32_t(TC2_HALO) * 16, SBO_A = uint32_t(TC2_HX) * 16;
+    const uint32_t LBO_B = uint32_t(Npad) * 16, SBO_B = 128;
+    const int64_t quarter = int64_t(1) << (2 * (l - 1));
+    const float2 *lev = me + d.eoff + lvl_off(l) * p;
+    const float *bimg = static_cast<const float *>(d.t_m2l_tc);
+
+    // the strips: (source class, dy) with an occupied source cell and at
+    // least one operator, in a fixed order; the same list in every thread
+    const uint32_t cs_any = sany;
+    int nstrip = 0;
+    uint8_t scs[12], sdy[12];
+    for (int cs = 0; cs < 4; ++cs) {
+        if (!((cs_any >> cs) & 1u)) continue;
+        for (int dyp = -1; dyp <= 1; ++dyp) {
+            int ops[3];
+            if (tc_strip_ops(c, cs, dyp, ops)) {
+                scs[nstrip] = uint8_t(cs);
+                sdy[nstrip] = uint8_t(dyp + 1);
+                ++nstrip;
+            }
+        }
+    }
+    // element e of a staged class is coefficient k of cell q, e = q p + k,
+    // with q = e * inv_p >> 20 (exact for e < 2^14, p <= 24)
+    const uint32_t inv_p = ((1u << 20) + uint32_t(p) - 1) / uint32_t(p);
+    // (eight loads in flight per thread before the first is used)
+    constexpr int SB = 8;
+    auto split = [&](int cs, int s) {
+        float *hi = a_hi(s), *lo = hi + aplane;
+        const int total = TC2_HALO * p;
+        for (int e0 = tid; e0 < total; e0 += SB * TC_THREADS) {
+            float2 v[SB];
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+                const int e = e0 + u * TC_THREADS;
+                v[u] = make_float2(0.f, 0.f);
+                if (e < total) {
+                    const int q = int((uint32_t(e) * inv_p) >> 20), k = e - q * p;
+                    if (hocc[cs][q]) {
+                        const int hy = q / TC2_HX, hx = q - hy * TC2_HX;
+                        v[u] = __ldg(lev + (int64_t(cs) * quarter + int64_t(Py0 - 1 + hy) * W +
+                                            (Px0 - 1 + hx)) * p + k);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+                const int e = e0 + u * TC_THREADS;
+                if (e >= total) break;
+                const int q = int((uint32_t(e) * inv_p) >> 20), k = e - q * p;
+                const float hr = tf32_hi(v[u].x), him = tf32_hi(v[u].y);
+                const size_t o_re = (size_t(k >> 2) * TC2_HALO + q) * 4 + (k & 3);
+                const size_t o_im = (size_t((k + p) >> 2) * TC2_HALO + q) * 4 + ((k + p) & 3);
+                hi[o_re] = hr;
+                lo[o_re] = v[u].x - hr;
+                hi[o_im] = him;
+                lo[o_im] = v[u].y - him;
+            }
+        }
+    };
+    // Each strip: operator images by bulk copy (thread 0), MMAs (thread 0),
+    // then every thread waits for the MMAs before the buffers are reused; a
+    // new source class is split after its predecessor's last strip is done.
+    // Two CTAs share an SM, so one's copies and splits overlap the other's
+    // MMAs.
+    int issued = -1;
+    bool ok = true;
+    uint32_t phase = 0;
+    const uint32_t bar = smem_addr(&mbar[0]), bb = smem_addr(&bbar[0]);
+    for (int j = 0; j < nstrip && ok; ++j) {
+        if (j == 0 || scs[j] != scs[j - 1]) {
+            split(scs[j], 0);
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+        }
+        int ops[3];
+        const uint32_t mask3 = tc_strip_ops(c, scs[j], int(sdy[j]) - 1, ops);
+        bool w = true;
+        if (tid == 0) {
+            const uint32_t bytes = uint32_t(2 * bslot * 4);
+            mbar_arrive_expect_tx(bb, uint32_t(__popc(mask3)) * bytes);
+            for (int s3 = 0; s3 < 3; ++s3)
+                if (mask3 & (1u << s3))
+                    bulk_g2s(smem_addr(b_img(0, 2 * s3)), bimg + size_t(ops[s3]) * 2 * bslot, bytes,
+                             bb);
+            w = mbar_wait(bb, phase, spin_limit);
+            if (!w) mbar_wait(bb, phase, 1LL << 26);  // the copies must land before exit
+            if (w) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t ahi = smem_addr(a_hi(0)), alo = ahi + uint32_t(aplane * 4);
+                const uint64_t sa = (2 * LBO_A) >> 4, sb = (2 * LBO_B) >> 4;
+                uint32_t acc = issued >= 0 ? 1u : 0u;  // the unit's first product overwrites
+                for (int s3 = 0; s3 < 3; ++s3) {
+                    if (!(mask3 & (1u << s3))) continue;
+                    const uint32_t bhi = smem_addr(b_img(0, 2 * s3));
+                    const uint32_t blo = smem_addr(b_img(0, 2 * s3 + 1));
+                    const uint64_t dbh = mma_desc(bhi, LBO_B, SBO_B), dbl = mma_desc(blo, LBO_B, SBO_B);
+                    // target (x, y) reads staged cell (x + 1 + dx, y + 1 + dy), dx = s3 - 1
+                    const uint32_t cell0 = uint32_t(int(sdy[j]) * TC2_HX + s3) * 16;
+                    const uint64_t dah = mma_desc(ahi + cell0, LBO_A, SBO_A);
+                    const uint64_t dal = mma_desc(alo + cell0, LBO_A, SBO_A);
+                    for (int ks = 0; ks < Kpad / 8; ++ks) {
+                        mma_tf32(tbase, dah + ks * sa, dbh + ks * sb, idesc, acc);
+                        mma_tf32(tbase, dah + ks * sa, dbl + ks * sb, idesc, 1u);
+                        mma_tf32(tbase, dal + ks * sa, dbh + ks * sb, idesc, 1u);
+                        acc = 1u;
+                    }
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        bar));
+                issued = j;
+                w = mbar_wait(bar, phase, spin_limit);
+                if (!w) mbar_wait(bar, phase, 1LL << 26);  // no TMEM freed under MMAs
+            }
+        }
+        phase ^= 1u;
+        ok = __syncthreads_and(w);
+        if (!ok && tid == 0) set_status(status, ST_ETIMEOUT);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __shared__ int s_issued;
+    if (tid == 0) s_issued = issued;
+    __syncthreads();
+    if (ok && tid < 128) {
+        // thread tid = TMEM lane = M row = target (tid % 8, tid / 8)
+        const int Px = Px0 + (tid & 7), Py = Py0 + (tid >> 3);
+        float v[TC_MAX_NPAD];
+        if (s_issued >= 0) {
+            const uint32_t taddr = tbase + (uint32_t(warp * 32) << 16);
+            for (int c0 = 0; c0 < Npad; c0 += 16) tmem_ld16(taddr + uint32_t(c0), v + c0);
+        } else {
+#pragma unroll
+            for (int i = 0; i < TC_MAX_NPAD; ++i) v[i] = 0.f;
+        }
+        if (box_count(st, L, l, morton_key(uint32_t(2 * Px + cx), uint32_t(2 * Py + cy)))) {
+            float2 *dst = le + d.eoff + (lvl_off(l) + int64_t(c) * quarter + int64_t(Py) * W + Px) * p;
+            for (int m = 0; m < p; ++m) dst[m] = make_float2(v[m], v[p + m]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols));
+}
+
+size_t m2l_tc2_smem_bytes(int p) {
+    const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
+    // hi and lo of one staged class, six B images
+    return size_t(2) * (Kpad / 4) * TC2_HALO * 16 + size_t(6) * Kpad * Npad * 4;
+}
+
+bool m2l_tc2_supported(int p, int level) {
+    const int Npad = (2 * p + 15) & ~15;
+    const int W = 1 << (level - 1);
+    return W >= TC2_BY && W < 128 && Npad <= TC_MAX_NPAD &&
+           m2l_tc2_smem_bytes(p) <= size_t(220) * 1024;
+}
+
+int64_t m2l_tc2_units(int level) {
+    const int64_t W = int64_t(1) << (level - 1);
+    return 4 * (W / TC2_BX) * (W / TC2_BY);
+}
+
+cudaError_t launch_m2l_tc2(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+                           const uint32_t *start, const float2 *me, float2 *le,
+                           const uint32_t *ucount, int dense_pct, int pmax, long long spin_limit,
+                           int *status, cudaStream_t st, uint64_t *launches) {
+    if (nblocks <= 0) return cudaSuccess;
+    const size_t smem_bytes = m2l_tc2_smem_bytes(pmax);
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem_bytes));
+    if (e != cudaSuccess) return e;
+    k_m2l_tc2<<<unsigned(nblocks), TC_THREADS, smem_bytes, st>>>(tasks, ntasks, insts, start, me,
+                                                                 le, ucount, dense_pct, spin_limit,
+                                                                 status);
+    PF_LAUNCHED(1);
+    return cudaGetLastError();
 }
 
 size_t m2l_tc_smem_bytes(int p, int seg) {

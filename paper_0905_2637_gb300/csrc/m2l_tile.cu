@@ -15,9 +15,12 @@
 // the same staged rows one row earlier or later.  Thread t holds target boxes
 // t mod 64 and t mod 64 + 64 and one half of the p output coefficients, so a
 // step of the k loop is two shared loads of source coefficients, one
-// broadcast load of an operator entry per output coefficient and eight FFMA
-// per (box, coefficient): all 32 lanes of every warp work, and every
-// operator entry read serves two boxes.
+// broadcast load of an operator entry per output coefficient and, per (box,
+// coefficient), one complex multiply-add as two packed FP32x2 FMAs:
+//     (re, im) += (t.x, t.x) (a.x, a.y) + (-t.y, t.y) (a.y, a.x)
+// with the operator entry staged as (t.x, t.x, -t.y, t.y), so one 16-byte
+// load gives both packed multipliers.  All 32 lanes of every warp work, and
+// every operator entry read serves two boxes.
 //
 //     LE_c[P] = sum over strips and dx of T_delta ME_c'[P + (dx, dy)]
 //
@@ -31,7 +34,7 @@ namespace petfmm {
 
 constexpr int MT_THREADS = 128;
 constexpr int MT_BOXES = M2L_TILE_SEG;  // target boxes per unit
-constexpr int MT_MAX_ROWS = 160;        // staged rows: R (SEG + 2) <= 144
+constexpr int MT_MAX_ROWS = 136;        // staged rows: R (SEG + 2) <= 130
 constexpr int MT_MAX_P = 24;
 
 // shared-memory row stride of the staged strip: odd, so that the 8-byte reads
@@ -62,9 +65,9 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
     const int SP = mt_stride(p);
     const int Rs = SEG + 2;          // staged rows per parent row
     const int nrows = R * Rs;
-    float2 *strip = mt_smem;                      // nrows x SP
-    float2 *tsm = mt_smem + size_t(nrows) * SP;   // 3 operators, [k][m]
     const int psq = p * p;
+    float4 *tsm = reinterpret_cast<float4 *>(mt_smem);   // 3 operators, [k][m], packed
+    float2 *strip = mt_smem + size_t(6) * psq;             // nrows x SP
 
     // this thread: boxes b0, b1 of the unit, coefficients m0 .. m0 + mc - 1;
     // box b is cell b % SEG of row b / SEG, staged at row (b / SEG) Rs + b % SEG + 1
@@ -136,32 +139,45 @@ __global__ void __launch_bounds__(MT_THREADS) k_m2l_tile(
             for (int s3 = 0; s3 < 3; ++s3) {
                 if (!(mask3 & (1u << s3))) continue;
                 const float2 *T = tab + size_t(ops[s3]) * psq;
-                for (int i = tid; i < psq; i += MT_THREADS) tsm[s3 * psq + i] = __ldg(T + i);
+                for (int i = tid; i < psq; i += MT_THREADS) {
+                    const float2 tk = __ldg(T + i);
+                    tsm[s3 * psq + i] = make_float4(tk.x, tk.x, -tk.y, tk.y);
+                }
             }
             __syncthreads();
             for (int s3 = 0; s3 < 3; ++s3) {
                 if (!(mask3 & (1u << s3))) continue;
-                const float2 *T = tsm + s3 * psq + m0;
+                const float4 *T = tsm + s3 * psq + m0;
                 const float2 *a0p = strip + (s0 + s3 - 1) * SP;
                 const float2 *a1p = strip + (s1 + s3 - 1) * SP;
                 if (act1) {
                     for (int k = 0; k < p; ++k) {
                         const float2 a0 = a0p[k], a1 = a1p[k];
+                        const float2 a0s = make_float2(a0.y, a0.x), a1s = make_float2(a1.y, a1.x);
 #pragma unroll
                         for (int i = 0; i < PH; ++i) {
                             if (i < mc) {
-                                const float2 tk = T[k * p + i];
-                                acc0[i] = cfma(tk, a0, acc0[i]);
-                                acc1[i] = cfma(tk, a1, acc1[i]);
+                                const float4 tk = T[k * p + i];
+                                const float2 tl = make_float2(tk.x, tk.y), th = make_float2(tk.z, tk.w);
+                                acc0[i] = __ffma2_rn(tl, a0, acc0[i]);
+                                acc1[i] = __ffma2_rn(tl, a1, acc1[i]);
+                                acc0[i] = __ffma2_rn(th, a0s, acc0[i]);
+                                acc1[i] = __ffma2_rn(th, a1s, acc1[i]);
                             }
                         }
                     }
                 } else if (act0) {
                     for (int k = 0; k < p; ++k) {
                         const float2 a0 = a0p[k];
+                        const float2 a0s = make_float2(a0.y, a0.x);
 #pragma unroll
-                        for (int i = 0; i < PH; ++i)
-                            if (i < mc) acc0[i] = cfma(T[k * p + i], a0, acc0[i]);
+                        for (int i = 0; i < PH; ++i) {
+                            if (i < mc) {
+                                const float4 tk = T[k * p + i];
+                                acc0[i] = __ffma2_rn(make_float2(tk.x, tk.y), a0, acc0[i]);
+                                acc0[i] = __ffma2_rn(make_float2(tk.z, tk.w), a0s, acc0[i]);
+                            }
+                        }
                     }
                 }
             }
@@ -189,7 +205,7 @@ int64_t m2l_tile_units(int level) { return tile_units(level); }
 size_t m2l_tile_smem_bytes(int p, int level) {
     int R, seg;
     tile_geom(level, &R, &seg);
-    return (size_t(R) * (seg + 2) * mt_stride(p) + size_t(3) * p * p) * sizeof(float2);
+    return (size_t(R) * (seg + 2) * mt_stride(p) + size_t(6) * p * p) * sizeof(float2);
 }
 
 cudaError_t launch_m2l_tile(const Task *tasks, int ntasks, int64_t nblocks, int pmax,
@@ -197,7 +213,7 @@ cudaError_t launch_m2l_tile(const Task *tasks, int ntasks, int64_t nblocks, int 
                             float2 *le, const uint32_t *ucount, int dense_pct, cudaStream_t st,
                             uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    const size_t smem = (size_t(MT_MAX_ROWS) * mt_stride(pmax) + size_t(3) * pmax * pmax) *
+    const size_t smem = (size_t(MT_MAX_ROWS) * mt_stride(pmax) + size_t(6) * pmax * pmax) *
                         sizeof(float2);
     const int ph = (pmax + 1) / 2;
     void (*k)(const Task *, int, const InstDesc *, const uint32_t *, const float2 *, float2 *,

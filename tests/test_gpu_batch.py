@@ -23,16 +23,18 @@ def _batch(ctx, ws, levels):
     return [(u.cpu().numpy(), v.cpu().numpy()) for u, v in outs]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_equals_alone_bitwise(orc, precision):
+@pytest.mark.parametrize("precision,blocks", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
+def test_batch_equals_alone_bitwise(orc, precision, blocks):
+    # (blocks = 1: tensor-core blocks at levels 5 to 7 in the batch and alone)
     _lib = G.lib()
     ws = W.batch(n_inst=24, seed=4, n_min=200, n_max=40_000)
     levels = [_lib.petfmm_choose_levels(w.n, w.p, w.sigma, w.domain) for w in ws]
     ctx = _lib.Context((0, 0, 1), 2, 8, 0.01, precision=precision, dtype="f64")
+    ctx.set_option(_lib.PETFMM_OPT_TC_BLOCKS, blocks)
     res = _batch(ctx, ws, [0] * len(ws))  # automatic L inside the library
     ctx.close()
     for w, L, (u, v) in zip(ws, levels, res):
-        ua, va = G.run(w, precision, L=L)
+        ua, va = G.run(w, precision, L=L, options={_lib.PETFMM_OPT_TC_BLOCKS: blocks})
         assert np.array_equal(u, ua) and np.array_equal(v, va)
     # spot-check a few instances against the oracle
     for i in (0, 7, 23):

@@ -20,13 +20,14 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-12
 
 
-def run_laplace(w, L=None, p=None, domain=None, keep=None, precision="fp64"):
+def run_laplace(w, L=None, p=None, domain=None, keep=None, precision="fp64", blocks=0):
     _lib = G.lib()
     L = w.L if L is None else L
     p = w.p if p is None else p
     ctx = _lib.Context(domain or w.domain, L, p, w.sigma, precision=precision, dtype=w.dtype,
                        kernel="laplace")
     ctx.set_option(_lib.PETFMM_OPT_POISON, 1)
+    ctx.set_option(_lib.PETFMM_OPT_TC_BLOCKS, blocks)
     x, y, g = G.to_dev((w.x, w.y, w.gamma))
     u, v = ctx.evaluate(x, y, g)
     assert ctx.sync() == 0
@@ -136,13 +137,14 @@ def test_vortex_and_laplace_contexts_side_by_side(orc):
     dict(n=10_000, seed=1, L=4, p=12, frac=0.0),
     dict(n=60_000, seed=2, L=6, p=17, frac=0.5),
     dict(n=300_000, seed=3, L=8, p=17, frac=0.2),   # tensor-core M2L levels
+    dict(n=300_000, seed=3, L=8, p=17, frac=0.2, blocks=1),   # ... and blocks at 5 to 7
     dict(n=1000, seed=4, L=2, p=40, frac=0.0),      # no tensor cores at this order
 ])
 def test_laplace_mixed_vs_fp64(case, dtype):
     w = W.tiny(case["n"], case["seed"], L=case["L"], p=case["p"], clustered_frac=case["frac"],
                dtype=dtype)
     u64, _ = run_laplace(w)
-    umx, vmx = run_laplace(w, precision="mixed")
+    umx, vmx = run_laplace(w, precision="mixed", blocks=case.get("blocks", 0))
     assert np.all(vmx == 0.0)
     assert rel(umx, u64) <= 1e-5
 

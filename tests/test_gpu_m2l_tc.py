@@ -1,6 +1,8 @@
-"""The tensor-core M2L (tcgen05, 3xTF32, mixed path, levels >= 8) against
-the FP32 SIMT M2L and the FP64 FMM, for each padded operand shape, plus the
-bounded-wait timeout report."""
+"""The tensor-core M2L (tcgen05, 3xTF32, mixed path: row units at levels
+>= 8, 8 x 16 blocks of parent cells at levels 5 to 7 -- forced here with
+PETFMM_OPT_TC_BLOCKS = 1, a single tree leaves them to the tiled SIMT kernel
+by default) against the FP32 SIMT M2L and the FP64 FMM, for each padded
+operand shape, plus the bounded-wait timeout report."""
 import numpy as np
 import pytest
 
@@ -10,10 +12,11 @@ from paper_0905_2637_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, tc, L=None, p=None, dense_pct=None):
+def _run(w, tc, L=None, p=None, dense_pct=None, blocks=0):
     _lib = G.lib()
     ctx = _lib.Context(w.domain, L or w.L, p or w.p, w.sigma, precision="mixed", dtype=w.dtype)
     ctx.set_option(_lib.PETFMM_OPT_M2L_TC, 1 if tc else 0)
+    ctx.set_option(_lib.PETFMM_OPT_TC_BLOCKS, blocks)
     if dense_pct is not None:
         ctx.set_option(_lib.PETFMM_OPT_TC_DENSE, dense_pct)
     ctx.set_option(_lib.PETFMM_OPT_POISON, 1)
@@ -25,11 +28,12 @@ def _run(w, tc, L=None, p=None, dense_pct=None):
     return out
 
 
+@pytest.mark.parametrize("blocks", [0, 1])
 @pytest.mark.parametrize("p", [8, 12, 17, 24])   # Kpad/Npad = 16/16, 24/32, 40/48, 48/48
 @pytest.mark.parametrize("L,n,frac", [(8, 300_000, 0.0), (9, 400_000, 0.6)])
-def test_tensor_core_m2l_matches_simt_and_fp64(L, n, frac, p):
+def test_tensor_core_m2l_matches_simt_and_fp64(L, n, frac, p, blocks):
     w = W.tiny(n, 31 + L + p, L=L, p=p, clustered_frac=frac)
-    u_tc, v_tc = _run(w, tc=True)
+    u_tc, v_tc = _run(w, tc=True, blocks=blocks)
     u_si, v_si = _run(w, tc=False)
     u64, v64 = G.run(w, "fp64")
     assert G.rel_l2(u_tc, v_tc, u64, v64) <= 1e-5
@@ -39,10 +43,11 @@ def test_tensor_core_m2l_matches_simt_and_fp64(L, n, frac, p):
 
 @pytest.mark.parametrize("dense_pct", [0, 10, 50, 100])
 def test_dense_sparse_split_covers_every_box(dense_pct):
-    # whichever units the tensor cores take, the two kernels together must
-    # translate every target exactly once (poisoned buffers would show NaN)
+    # whichever units the tensor cores take (row units and blocks), the
+    # kernels together must translate every target exactly once (poisoned
+    # buffers would show NaN)
     w = W.tiny(300_000, 91, L=9, p=17, clustered_frac=0.7)
-    u_mx, v_mx = _run(w, tc=True, dense_pct=dense_pct)
+    u_mx, v_mx = _run(w, tc=True, dense_pct=dense_pct, blocks=1)
     u_si, v_si = _run(w, tc=False)
     assert np.all(np.isfinite(u_mx)) and np.all(np.isfinite(v_mx))
     assert G.rel_l2(u_mx, v_mx, u_si, v_si) <= 1e-5

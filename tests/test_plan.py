@@ -17,7 +17,8 @@ def lib():
     return _lib
 
 
-UNITS_PER_BLOCK = {0: 256, 1: 256, 2: 256, 3: 256, 4: 256, 5: 32, 6: 1, 70: 1, 71: 1, 72: 1, 73: 1}
+UNITS_PER_BLOCK = {0: 256, 1: 256, 2: 256, 3: 256, 4: 256, 5: 32, 6: 1, 7: 1, 70: 1, 71: 1, 72: 1,
+                   73: 1}
 
 
 def _instances(seed, k):
@@ -31,9 +32,13 @@ def _instances(seed, k):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("seed,k", [(1, 1), (2, 7), (3, 64)])
+@pytest.mark.parametrize("seed,k", [(1, 1), (2, 7), (3, 64), (4, 200)])
 def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
     insts = _instances(seed, k)
+    # tensor-core blocks at levels 5 to 7 only when the plan has >= 2048 of them
+    blocks = sum(4 * (2 ** (l - 1) // 8) * (2 ** (l - 1) // 16)
+                 for it in insts if it["order"] <= 24 for l in range(5, min(it["levels"], 7) + 1))
+    use_blocks = precision == 1 and blocks >= 2048
     plan = lib.petfmm_debug_plan(precision, insts)
     ranges = {}
     for row in plan:
@@ -68,6 +73,14 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
             if r[1] == i:
                 w = 2 ** (int(r[2]) - 1)
                 assert r[3] == 4 * w * (w // min(w, 128))
+        # levels with 16 to 64 parent cells per row (mixed path, p <= 24) get
+        # the tensor-core launch in blocks, one CTA per (class, 8 x 16 cells)
+        tc2 = sorted(int(r[2]) for r in ranges.get(7, []) if r[1] == i)
+        assert tc2 == ([l for l in range(5, min(L, 7) + 1)] if use_blocks and p <= 24 else [])
+        for r in ranges.get(7, []):
+            if r[1] == i:
+                w = 2 ** (int(r[2]) - 1)
+                assert r[3] == 4 * (w // 8) * (w // 16)
         # the other levels of the mixed path (p <= 24) get the tiled SIMT
         # launch, one CTA per (class, 128 target boxes: a 128-cell segment of
         # a parent row, or several whole rows where rows are shorter)
@@ -76,7 +89,7 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
         tile_rows = [r for rid in range(70, 74) for r in ranges.get(rid, []) if r[1] == i]
         assert all(r[0] == cls for r in tile_rows)
         tile = sorted(int(r[2]) for r in tile_rows)
-        assert tile == ([l for l in range(2, L + 1) if l not in tc]
+        assert tile == ([l for l in range(2, L + 1) if l not in tc and l not in tc2]
                         if precision == 1 and p <= 24 else [])
         for r in tile_rows:
             if r[1] == i:
