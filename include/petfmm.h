@@ -250,8 +250,8 @@ enum {
                                   evaluation (testing: a read of a never-written
                                   coefficient then shows up as NaN in u, v) */
     PETFMM_OPT_M2L_TC = 5,     /* mixed path: 1 (default) M2L of levels >= 8 on the tensor
-                                  cores (3xTF32; see PETFMM_OPT_TC_BLOCKS for levels 5
-                                  to 7), 0 all levels on the FP32 SIMT kernels */
+                                  cores (3xTF32; see PETFMM_OPT_TC_BLOCKS), 0 all levels
+                                  on the FP32 SIMT kernels */
     PETFMM_OPT_TC_DENSE = 6,   /* percent (0..100, default 25) of a tensor-core unit's
                                   targets that must hold particles for the unit to run
                                   on the tensor cores; sparser units use the SIMT kernel */
@@ -278,13 +278,15 @@ enum {
                                   deterministic; they differ by FP32 rounding of the
                                   sums.  Extra device memory in mode 1: 88 bytes per
                                   blob and 28 per leaf. */
-    PETFMM_OPT_TC_BLOCKS = 13, /* mixed path, with PETFMM_OPT_M2L_TC = 1: M2L of levels
-                                  5 to 7 (16 to 64 parent cells per row) on the tensor
-                                  cores in blocks of 8 x 16 parent cells.  0 (default):
-                                  when an evaluation has at least 2048 such blocks (a
-                                  batch; a single tree runs those levels faster on the
-                                  tiled SIMT kernel); 1: always; 2: never.  Results
-                                  differ by FP32 rounding only. */
+    PETFMM_OPT_TC_BLOCKS = 13, /* mixed path, with PETFMM_OPT_M2L_TC = 1: the shape of
+                                  the tensor-core M2L.  0 (default): blocks of 8 x 16
+                                  parent cells (all four child classes) at levels >= 8,
+                                  and at levels 5 to 7 when the evaluation has at least
+                                  512 blocks (a batch; a single tree runs those levels
+                                  faster on the tiled SIMT kernel); 1: blocks at every
+                                  level >= 5; 2: row units (one child class, a segment
+                                  of a parent row) at levels >= 8 and no blocks.
+                                  Results differ by FP32 rounding only. */
     PETFMM_OPT_KERNEL = 12     /* the sum the context evaluates (the kernel parameter of
                                   the paper's Evaluator, Sec. 6.1):
                                   PETFMM_KERNEL_VORTEX (default) the blob velocity of

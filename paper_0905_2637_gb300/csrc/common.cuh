@@ -60,6 +60,7 @@ struct InstDesc {
     void *u, *v;
     const void *t_m2m, *t_l2l, *t_m2l;  // operator tables for this p (path's real type)
     const void *t_m2l_tc;               // tensor-core M2L operator images (mixed path)
+    const void *t_m2l_tcb;              // ... side by side for the block units
     int64_t tc_unit0[MAX_L + 1];        // per level: first unit of this (instance, level)
                                         // in the tensor-core M2L launch, or -1
     int tc_segmax;                      // widest tensor-core unit (parent cells)
@@ -67,6 +68,7 @@ struct InstDesc {
                                         // cores (else, if tc_unit0[l] >= 0, on the
                                         // tiled SIMT kernel)
     uint32_t tc2_levels;                // bit l: ... on the tensor cores in 8 x 16 blocks
+                                        // (all four classes per block)
     // mixed-precision P2P constants (leaf units)
     float kappa;            // w^2 / (2 sigma^2): q = kappa * rho^2
     float cnear;            // w / (4 pi sigma^2)
@@ -235,19 +237,15 @@ __host__ __device__ __forceinline__ int64_t tc_unit_of(int l, int segmax, int c,
     return (int64_t(c) * W + Py) * nseg + Px / s;
 }
 
-// Block units of the tensor-core M2L (levels whose parent rows are too short
-// for row units): 8 x 16 parent cells (x, y) of one target class, 128 targets;
-// units are numbered (c (W / 16) + Py / 16) (W / 8) + Px / 8.
+// Block units of the tensor-core M2L: 8 x 16 parent cells (x, y), all four
+// target classes (512 targets); units are numbered (Py / 16) (W / 8) + Px / 8.
 constexpr int TC2_BX = 8, TC2_BY = 16;
 
-__host__ __device__ __forceinline__ void tc2_unit_decode(int l, int64_t unit, int *c, int *Py0,
-                                                         int *Px0) {
+__host__ __device__ __forceinline__ void tcb_unit_decode(int l, int64_t unit, int *Py0, int *Px0) {
     const int W = 1 << (l - 1);
-    const int nbx = W / TC2_BX, nby = W / TC2_BY;
-    *c = int(unit / (int64_t(nbx) * nby));
-    const int64_t rem = unit - int64_t(*c) * nbx * nby;
-    *Py0 = int(rem / nbx) * TC2_BY;
-    *Px0 = int(rem - (rem / nbx) * nbx) * TC2_BX;
+    const int nbx = W / TC2_BX;
+    *Py0 = int(unit / nbx) * TC2_BY;
+    *Px0 = int(unit - (unit / nbx) * nbx) * TC2_BX;
 }
 
 // Units of the tiled SIMT M2L: a segment of M2L_TILE_SEG parent cells of one
@@ -292,8 +290,9 @@ __host__ __device__ __forceinline__ int64_t unit_of(const InstDesc &d, int l, in
     }
     const int W = 1 << (l - 1);
     if ((d.tc2_levels >> l) & 1u) {
-        *nbox = TC2_BX * TC2_BY;
-        return (int64_t(c) * (W / TC2_BY) + Py / TC2_BY) * (W / TC2_BX) + Px / TC2_BX;
+        (void)c;
+        *nbox = 4 * TC2_BX * TC2_BY;
+        return int64_t(Py / TC2_BY) * (W / TC2_BX) + Px / TC2_BX;
     }
     int R, s;
     tile_geom(l, &R, &s);

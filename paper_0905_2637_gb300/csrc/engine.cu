@@ -354,10 +354,10 @@ void flatten_tasks(Plan &pl) {
 }
 
 // order class of the tiled M2L launches: p <= 8, 12, 18, 24
-// Fewest block units for which the tensor-core block launch beats the tiled
-// SIMT kernel (measured: a batch of 512 trees has 13,040; one tree of 2^20
-// blobs, 168).
-constexpr int64_t kTc2MinUnits = 2048;
+// Fewest block units (all levels >= 5) for which levels 5 to 7 run faster as
+// blocks than on the tiled SIMT kernel (a batch of 512 trees has 3,260; one
+// tree of 2^20 blobs at L = 8, 170).
+constexpr int64_t kTc2MinUnits = 512;
 
 int tile_class(int p) { return p <= 8 ? 0 : p <= 12 ? 1 : p <= 18 ? 2 : 3; }
 
@@ -431,7 +431,9 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_blocks, int tc_seg
             // levels the tensor cores can take get both launches: the tensor
             // cores translate the dense units, the SIMT kernel the boxes of the
             // sparse ones (a data-dependent split made on the device)
-            if (precision == PETFMM_MIXED && use_tc && m2l_tc_supported(d.p, l, tc_segmax)) {
+            // (row units: only when blocks are switched off, PETFMM_OPT_TC_BLOCKS = 2)
+            if (precision == PETFMM_MIXED && use_tc && tc_blocks == 2 &&
+                m2l_tc_supported(d.p, l, tc_segmax)) {
                 d.tc_unit0[l] = pl.m2l_tc.nblocks;  // one unit per block
                 d.tc_levels |= 1u << l;
                 add_task(pl.m2l_tc, i, l, m2l_tc_units(l, tc_segmax), 1);
@@ -443,26 +445,29 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_blocks, int tc_seg
         items_cap += d.n / tpi + std::min<int64_t>(d.n, nleaf) + 1;
     }
     // the other levels of the mixed path: dense units on the tensor cores in
-    // 8 x 16 blocks where rows hold 16 to 64 parent cells, on the tiled SIMT
-    // kernel below that (their units follow the row units in the unit-count
-    // array: blocks, then the tile classes one by one)
+    // blocks of 8 x 16 parent cells (levels >= 8; levels 5 to 7 too when the
+    // plan has many blocks), the rest on the tiled SIMT kernel (their units
+    // follow the row units in the unit-count array: blocks, then the tile
+    // classes one by one)
     if (precision == PETFMM_MIXED) {
         int64_t base = pl.m2l_tc.nblocks;
-        // blocks only where there are many of them (a batch): a single tree's
-        // levels 5 to 7 keep more CTAs in flight on the tiled SIMT kernel
+        // levels 5 to 7 of a single tree keep more CTAs in flight on the tiled
+        // SIMT kernel; a batch fills the GPU with blocks
         int64_t blocks = 0;
         for (int i = 0; i < ni; ++i)
             for (int l = 2; l <= pl.inst[i].L; ++l)
-                if (!((pl.inst[i].tc_levels >> l) & 1u) && m2l_tc2_supported(pl.inst[i].p, l))
-                    blocks += m2l_tc2_units(l);
-        if (use_tc && (tc_blocks == 1 || (tc_blocks == 0 && blocks >= kTc2MinUnits))) {
+                if (!((pl.inst[i].tc_levels >> l) & 1u) && m2l_tcb_supported(pl.inst[i].p, l))
+                    blocks += m2l_tcb_units(l);
+        const bool shallow = tc_blocks == 1 || (tc_blocks == 0 && blocks >= kTc2MinUnits);
+        if (use_tc && tc_blocks != 2) {
             for (int i = 0; i < ni; ++i) {
                 InstDesc &d = pl.inst[i];
                 for (int l = 2; l <= d.L; ++l) {
-                    if (((d.tc_levels >> l) & 1u) || !m2l_tc2_supported(d.p, l)) continue;
+                    if (((d.tc_levels >> l) & 1u) || !m2l_tcb_supported(d.p, l)) continue;
+                    if (l < 8 && !shallow) continue;
                     d.tc_unit0[l] = base + pl.m2l_tc2.nblocks;
                     d.tc2_levels |= 1u << l;
-                    add_task(pl.m2l_tc2, i, l, m2l_tc2_units(l), 1);
+                    add_task(pl.m2l_tc2, i, l, m2l_tcb_units(l), 1);
                     pl.tc2_pmax = std::max(pl.tc2_pmax, d.p);
                 }
             }
@@ -518,6 +523,7 @@ int attach_tables(petfmm_ctx *c, Plan &pl) {
         } else {
             d.t_m2m = t->m2m32; d.t_l2l = t->l2l32; d.t_m2l = t->m2l32;
             d.t_m2l_tc = t->m2l_tc;
+            d.t_m2l_tcb = t->m2l_tcb;
         }
     }
     return PETFMM_OK;
@@ -840,7 +846,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     }
     if (pl.m2l_tc2.count) {
         const long long spin = c->spin_limit > 0 ? c->spin_limit : c->spin_limit < 0 ? 0 : (1LL << 26);
-        PF_CUDA(launch_m2l_tc2(dtask + pl.m2l_tc2.first, pl.m2l_tc2.count, pl.m2l_tc2.nblocks,
+        PF_CUDA(launch_m2l_tcb(dtask + pl.m2l_tc2.first, pl.m2l_tc2.count, pl.m2l_tc2.nblocks,
                                dinst, start, static_cast<const float2 *>(c->me.p),
                                static_cast<float2 *>(c->le.p), ucount + pl.m2l_tc.nblocks,
                                c->tc_dense_pct, pl.tc2_pmax, spin,

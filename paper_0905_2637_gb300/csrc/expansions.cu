@@ -294,6 +294,8 @@ cudaError_t build_op_tables(int p, int kernel, OpTables *t) {
         std::vector<float> img;
         host_m2l_tc_images(p, kernel, img);
         if ((e = up((void **)&t->m2l_tc, img.data(), img.size() * 4)) != cudaSuccess) return e;
+        host_m2l_tcb_images(p, kernel, img);
+        if ((e = up((void **)&t->m2l_tcb, img.data(), img.size() * 4)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -302,6 +304,7 @@ void free_op_tables(OpTables *t) {
     cudaFree(t->m2m64); cudaFree(t->l2l64); cudaFree(t->m2l64);
     cudaFree(t->m2m32); cudaFree(t->l2l32); cudaFree(t->m2l32);
     cudaFree(t->m2l_tc);
+    cudaFree(t->m2l_tcb);
     *t = OpTables();
 }
 

@@ -55,6 +55,7 @@ struct OpTables {
     double2 *m2m64 = nullptr, *l2l64 = nullptr, *m2l64 = nullptr;
     float2 *m2m32 = nullptr, *l2l32 = nullptr, *m2l32 = nullptr;
     float *m2l_tc = nullptr;  // hi/lo B images for the tensor-core M2L (p <= 24)
+    float *m2l_tcb = nullptr; // ... the four target classes side by side (block units)
 };
 cudaError_t build_op_tables(int p, int kernel, OpTables *out);
 void free_op_tables(OpTables *t);
@@ -98,12 +99,13 @@ cudaError_t launch_l2l(const Task *tasks, int ntasks, int64_t nblocks, const Ins
 // Tensor-core M2L (mixed path) for levels with at least 128 parent cells per
 // row and p <= 24: one CTA per (target class, parent row, segment) unit.
 bool m2l_tc_supported(int p, int level, int segmax);
-// block units (8 x 16 parent cells) for 16 <= W < 128 parent cells per side
-bool m2l_tc2_supported(int p, int level);
-int64_t m2l_tc2_units(int level);
-size_t m2l_tc2_smem_bytes(int p);
+// block units (8 x 16 parent cells, all four target classes), levels >= 5
+bool m2l_tcb_supported(int p, int level);
+int64_t m2l_tcb_units(int level);
+size_t m2l_tcb_smem_bytes(int p);
+void host_m2l_tcb_images(int p, int kernel, std::vector<float> &out);
 // pmax: the largest order among the launch's units (sizes shared memory)
-cudaError_t launch_m2l_tc2(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+cudaError_t launch_m2l_tcb(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                            const uint32_t *start, const float2 *me, float2 *le,
                            const uint32_t *ucount, int dense_pct, int pmax, long long spin_limit,
                            int *status, cudaStream_t st, uint64_t *launches);

@@ -79,9 +79,20 @@ __global__ void __launch_bounds__(256) k_tc_unit_count(const Task *__restrict__ 
     if ((d.tc_levels >> l) & 1u) {
         tc_unit_decode(l, d.tc_segmax, u - t.block0, &c, &Py0, &Px0, &SEG);
     } else if ((d.tc2_levels >> l) & 1u) {
-        tc2_unit_decode(l, u - t.block0, &c, &Py0, &Px0);
-        R = TC2_BY;
-        SEG = TC2_BX;
+        // a block: 8 x 16 parent cells, all four classes (i = c 128 + cell)
+        tcb_unit_decode(l, u - t.block0, &Py0, &Px0);
+        const uint32_t *st = start + d.soff;
+        uint32_t cnt = 0;
+        for (int i = lane; i < 4 * TC2_BX * TC2_BY; i += 32) {
+            const int cc = i >> 7, q = i & 127;
+            const uint32_t ix = uint32_t(2 * (Px0 + (q & 7)) + (cc & 1));
+            const uint32_t iy = uint32_t(2 * (Py0 + (q >> 3)) + (cc >> 1));
+            cnt += box_count(st, d.L, l, morton_key(ix, iy)) != 0;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        if (lane == 0) ucount[u] = cnt;
+        return;
     } else {
         tile_unit_decode(l, u - t.block0, &c, &Py0, &R, &Px0, &SEG);
     }
@@ -344,40 +355,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
 }
 
 // ----------------------------------------------------------------------------
-// Block units: the levels whose parent rows are too short for the row units
-// above (16 <= W <= 64 parent cells per side).  One CTA per (target class c,
-// block of 8 x 16 parent cells); the block's 128 targets are the MMA's M
-// rows, target row y (8 cells) being core-matrix group y.  For each source
-// class c' the CTA stages, once, the expansions of the block's cells plus a
-// one-cell halo (10 x 18 cells, empty and out-of-domain boxes as zeros) in
-// the K-major layout with a staged row of 10 cells as the group stride (SBO);
-// the nine parent offsets (dx, dy) of the class read the same staged data
-// from a start dy staged rows and dx cells away.  Operators, 3xTF32 split and
-// accumulation as in the row units; one accumulator (128 lanes x Npad
-// columns) per CTA.
+// Block units: one CTA per block of 8 x 16 parent cells (x, y), all four
+// target classes.  The block's 128 parent cells are the MMA's M rows (cell
+// row y = core-matrix group y) and the four classes sit side by side in N:
+// columns c Npad .. c Npad + 2p - 1 hold class c's coefficients.  The source
+// cells of a target class c at parent P are P + (dx, dy) in source class c'
+// for every class c (only the operator depends on c), so for each source
+// class c' the CTA stages, once, the block's cells plus a one-cell halo
+// (10 x 18 cells, empty and out-of-domain boxes as zeros) in the K-major
+// layout with a staged row of 10 cells as the group stride (SBO), and each of
+// the nine parent offsets (dx, dy) is one 128 x 4Npad x 2p product whose A
+// starts dy staged rows and dx cells away and whose B is the four classes'
+// operators T_delta, delta = (2 dx + c'x - cx, 2 dy + c'y - cy), side by side
+// (zero for a class whose delta is within one box).  Wide N amortises each A
+// read from shared memory over four operators.
 //
-// The strips (c', dy) of the unit run in a fixed order: the operator images
-// of the strip's (up to three) dx shifts arrive by bulk asynchronous copies
-// (one thread, completion counted in bytes on an mbarrier), the MMAs follow,
-// and the buffers are reused once they have completed.  Two CTAs share an
-// SM (about 104 KB of shared memory each at p = 17), so one CTA's copies and
-// operand splits overlap the other's MMAs.  (A one-CTA-per-SM variant that
-// double-buffered operands and issued the next strip's copies under the
-// current MMAs measured slower: with N = 2p padded to 48, the MMAs are too
-// short to hide one CTA's waits.)
+// Pipeline (one CTA per SM).  The offsets run in a fixed order, source class
+// by source class.  Offset g's B (hi and lo, one bulk asynchronous copy)
+// lands in buffer g mod 2 on mbarrier bbar[g mod 2]; its MMAs complete on
+// mbar[g mod 2].  Thread 0 issues copies and MMAs and alone waits on the
+// barriers, always in offset order, so no barrier runs a phase ahead of its
+// waiter: offset g + 1's copy is issued, once offset g - 1's MMAs (the last
+// reader of that buffer) are done, before offset g's MMAs, and lands while
+// they run.  A new source class is split into A once every MMA so far is done.
 // ----------------------------------------------------------------------------
-constexpr int TC2_HX = TC2_BX + 2, TC2_HY = TC2_BY + 2;
-constexpr int TC2_HALO = TC2_HX * TC2_HY;  // staged cells per source class
+constexpr int TCB_HX = TC2_BX + 2, TCB_HY = TC2_BY + 2;
+constexpr int TCB_HALO = TCB_HX * TCB_HY;  // staged cells per source class
+constexpr int TCB_M = TC2_BX * TC2_BY;     // parent cells per block
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
+// delta's operator for target class c, source class cs and parent offset
+// (dx, dy), or -1 if delta is within one box
+__host__ __device__ __forceinline__ int tcb_op(int c, int cs, int dx, int dy) {
+    const int ddx = 2 * dx + (cs & 1) - (c & 1), ddy = 2 * dy + (cs >> 1) - (c >> 1);
+    const int ax = ddx < 0 ? -ddx : ddx, ay = ddy < 0 ? -ddy : ddy;
+    return (ax > ay ? ax : ay) >= 2 ? m2l_op_index(ddx, ddy) : -1;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
     const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const float2 *__restrict__ me, float2 *__restrict__ le,
     const uint32_t *__restrict__ ucount, int dense_pct, long long spin_limit, int *status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[1], bbar[1];
+    __shared__ __align__(8) uint64_t mbar[2], bbar[2];
     __shared__ uint32_t tslot;
     __shared__ uint32_t sany;
-    __shared__ uint8_t hocc[4][TC2_HALO];  // occupied halo cells, per source class
+    __shared__ int s_issued;
+    __shared__ uint8_t hocc[4][TCB_HALO];  // occupied halo cells, per source class
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int ti = find_task(tasks, ntasks, blockIdx.x);
@@ -385,36 +408,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
     const InstDesc &d = insts[t.inst];
     const int l = t.level, L = d.L, p = d.p;
     const int W = 1 << (l - 1);
-    int c, Py0, Px0;
-    tc2_unit_decode(l, int64_t(blockIdx.x) - t.block0, &c, &Py0, &Px0);
+    int Py0, Px0;
+    tcb_unit_decode(l, int64_t(blockIdx.x) - t.block0, &Py0, &Px0);
     // sparse units are left to the SIMT kernel (same test there)
-    if (!tc_unit_dense(ucount[blockIdx.x], TC2_BX * TC2_BY, dense_pct)) return;
-    const int cx = c & 1, cy = c >> 1;
+    if (!tc_unit_dense(ucount[blockIdx.x], 4 * TCB_M, dense_pct)) return;
     const uint32_t *st = start + d.soff;
 
     const int K2 = 2 * p;
-    const int Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
+    const int Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15, NC = 4 * Npad;
     const int KG = Kpad / 4;
-    const size_t aplane = size_t(KG) * TC2_HALO * 4;  // floats of one A image (hi or lo)
-    const int bslot = Kpad * Npad;                     // floats of one B image
-    float *A0 = reinterpret_cast<float *>(smem);       // hi, then lo
-    float *B0 = A0 + size_t(2) * aplane;               // 6 images: hi and lo of 3 shifts
-    auto a_hi = [&](int) { return A0; };
-    auto b_img = [&](int, int slot) { return B0 + size_t(slot) * bslot; };
+    const size_t aplane = size_t(KG) * TCB_HALO * 4;  // floats of A hi (or lo)
+    const size_t bplane = size_t(Kpad) * NC;          // floats of one offset's B hi (or lo)
+    float *A = reinterpret_cast<float *>(smem);       // hi, then lo
+    float *B = A + 2 * aplane;                        // 2 buffers of (hi, lo)
     // zero the K padding of every staged cell once (never overwritten)
-    for (int i = tid; i < TC2_HALO * (Kpad - K2); i += TC_THREADS) {
+    for (int i = tid; i < TCB_HALO * (Kpad - K2); i += TC_THREADS) {
         const int r = i / (Kpad - K2), k = K2 + i % (Kpad - K2);
-        const size_t o = (size_t(k >> 2) * TC2_HALO + r) * 4 + (k & 3);
-        A0[o] = 0.f;
-        A0[aplane + o] = 0.f;
+        const size_t o = (size_t(k >> 2) * TCB_HALO + r) * 4 + (k & 3);
+        A[o] = 0.f;
+        A[aplane + o] = 0.f;
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bbar[0])));
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bbar[b])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         sany = 0;
     }
-    const uint32_t ncols = Npad <= 32 ? 32u : 64u;
+    uint32_t ncols = 32;
+    while (ncols < uint32_t(NC)) ncols <<= 1;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr(&tslot)),
@@ -422,9 +445,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // occupancy of the halo cells of all four source classes (one round)
-    for (int i = tid; i < 4 * TC2_HALO; i += TC_THREADS) {
-        const int cs = i / TC2_HALO, q = i - cs * TC2_HALO;
-        const int hy = q / TC2_HX, hx = q - hy * TC2_HX;
+    for (int i = tid; i < 4 * TCB_HALO; i += TC_THREADS) {
+        const int cs = i / TCB_HALO, q = i - cs * TCB_HALO;
+        const int hy = q / TCB_HX, hx = q - hy * TCB_HX;
         const int Px = Px0 - 1 + hx, Py = Py0 - 1 + hy;
         bool o = false;
         if (Px >= 0 && Px < W && Py >= 0 && Py < W)
@@ -437,38 +460,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = tslot;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(Npad >> 3) << 17) |
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NC >> 3) << 17) |
                            (uint32_t(128 >> 4) << 24);
-    const uint32_t LBO_A = uint32_t(TC2_HALO) * 16, SBO_A = uint32_t(TC2_HX) * 16;
-    const uint32_t LBO_B = uint32_t(Npad) * 16, SBO_B = 128;
+    const uint32_t LBO_A = uint32_t(TCB_HALO) * 16, SBO_A = uint32_t(TCB_HX) * 16;
+    const uint32_t LBO_B = uint32_t(NC) * 16, SBO_B = 128;
     const int64_t quarter = int64_t(1) << (2 * (l - 1));
     const float2 *lev = me + d.eoff + lvl_off(l) * p;
-    const float *bimg = static_cast<const float *>(d.t_m2l_tc);
+    const float *bimg = static_cast<const float *>(d.t_m2l_tcb);
 
-    // the strips: (source class, dy) with an occupied source cell and at
-    // least one operator, in a fixed order; the same list in every thread
+    // the offsets (source class, dy, dx) of occupied source classes with an
+    // operator for some target class, as g = cs 9 + (dy + 1) 3 + dx + 1, in a
+    // fixed order; the same list in every thread
     const uint32_t cs_any = sany;
-    int nstrip = 0;
-    uint8_t scs[12], sdy[12];
+    int ng = 0;
+    uint8_t gl[36];
     for (int cs = 0; cs < 4; ++cs) {
         if (!((cs_any >> cs) & 1u)) continue;
-        for (int dyp = -1; dyp <= 1; ++dyp) {
-            int ops[3];
-            if (tc_strip_ops(c, cs, dyp, ops)) {
-                scs[nstrip] = uint8_t(cs);
-                sdy[nstrip] = uint8_t(dyp + 1);
-                ++nstrip;
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                bool any = false;
+                for (int c = 0; c < 4; ++c) any |= tcb_op(c, cs, dx, dy) >= 0;
+                if (any) gl[ng++] = uint8_t(cs * 9 + (dy + 1) * 3 + dx + 1);
             }
-        }
     }
     // element e of a staged class is coefficient k of cell q, e = q p + k,
-    // with q = e * inv_p >> 20 (exact for e < 2^14, p <= 24)
+    // with q = e * inv_p >> 20 (exact for e < 2^14, p <= 24); eight loads in
+    // flight per thread before the first is used
     const uint32_t inv_p = ((1u << 20) + uint32_t(p) - 1) / uint32_t(p);
-    // (eight loads in flight per thread before the first is used)
     constexpr int SB = 8;
-    auto split = [&](int cs, int s) {
-        float *hi = a_hi(s), *lo = hi + aplane;
-        const int total = TC2_HALO * p;
+    auto split = [&](int cs) {
+        float *hi = A, *lo = A + aplane;
+        const int total = TCB_HALO * p;
         for (int e0 = tid; e0 < total; e0 += SB * TC_THREADS) {
             float2 v[SB];
 #pragma unroll
@@ -478,7 +500,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
                 if (e < total) {
                     const int q = int((uint32_t(e) * inv_p) >> 20), k = e - q * p;
                     if (hocc[cs][q]) {
-                        const int hy = q / TC2_HX, hx = q - hy * TC2_HX;
+                        const int hy = q / TCB_HX, hx = q - hy * TCB_HX;
                         v[u] = __ldg(lev + (int64_t(cs) * quarter + int64_t(Py0 - 1 + hy) * W +
                                             (Px0 - 1 + hx)) * p + k);
                     }
@@ -490,8 +512,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
                 if (e >= total) break;
                 const int q = int((uint32_t(e) * inv_p) >> 20), k = e - q * p;
                 const float hr = tf32_hi(v[u].x), him = tf32_hi(v[u].y);
-                const size_t o_re = (size_t(k >> 2) * TC2_HALO + q) * 4 + (k & 3);
-                const size_t o_im = (size_t((k + p) >> 2) * TC2_HALO + q) * 4 + ((k + p) & 3);
+                const size_t o_re = (size_t(k >> 2) * TCB_HALO + q) * 4 + (k & 3);
+                const size_t o_im = (size_t((k + p) >> 2) * TCB_HALO + q) * 4 + ((k + p) & 3);
                 hi[o_re] = hr;
                 lo[o_re] = v[u].x - hr;
                 hi[o_im] = him;
@@ -499,85 +521,118 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
             }
         }
     };
-    // Each strip: operator images by bulk copy (thread 0), MMAs (thread 0),
-    // then every thread waits for the MMAs before the buffers are reused; a
-    // new source class is split after its predecessor's last strip is done.
-    // Two CTAs share an SM, so one's copies and splits overlap the other's
-    // MMAs.
-    int issued = -1;
-    bool ok = true;
-    uint32_t phase = 0;
-    const uint32_t bar = smem_addr(&mbar[0]), bb = smem_addr(&bbar[0]);
-    for (int j = 0; j < nstrip && ok; ++j) {
-        if (j == 0 || scs[j] != scs[j - 1]) {
-            split(scs[j], 0);
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
+    // thread 0's state: offsets whose MMAs are known complete, whose B copy
+    // was issued and has landed, MMAs issued, and whether every wait so far
+    // ended in time
+    int done = -1, copied = -1, landed = -1, issued = -1;
+    bool ok0 = true;
+    auto wait_mma = [&](int k) {  // thread 0 only, in offset order
+        for (int kk = done + 1; kk <= k && ok0; ++kk) {
+            ok0 = mbar_wait(smem_addr(&mbar[kk & 1]), uint32_t(kk >> 1) & 1u, spin_limit);
+            if (ok0) done = kk;
         }
-        int ops[3];
-        const uint32_t mask3 = tc_strip_ops(c, scs[j], int(sdy[j]) - 1, ops);
-        bool w = true;
-        if (tid == 0) {
-            const uint32_t bytes = uint32_t(2 * bslot * 4);
-            mbar_arrive_expect_tx(bb, uint32_t(__popc(mask3)) * bytes);
-            for (int s3 = 0; s3 < 3; ++s3)
-                if (mask3 & (1u << s3))
-                    bulk_g2s(smem_addr(b_img(0, 2 * s3)), bimg + size_t(ops[s3]) * 2 * bslot, bytes,
-                             bb);
-            w = mbar_wait(bb, phase, spin_limit);
-            if (!w) mbar_wait(bb, phase, 1LL << 26);  // the copies must land before exit
-            if (w) {
+    };
+    const uint32_t bbytes = uint32_t(2 * bplane * 4);  // hi and lo, contiguous
+    auto copy_b = [&](int k) {  // thread 0 only
+        const uint32_t bb = smem_addr(&bbar[k & 1]);
+        mbar_arrive_expect_tx(bb, bbytes);
+        bulk_g2s(smem_addr(B + size_t(k & 1) * 2 * bplane), bimg + size_t(gl[k]) * 2 * bplane,
+                 bbytes, bb);
+        copied = k;
+    };
+    bool ok = true;
+    if (ng > 0) {
+        split(gl[0] / 9);
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+    }
+    for (int g = 0; g < ng && ok; ++g) {
+        if (tid == 0 && ok0) {
+            if (g == 0) copy_b(0);
+            // offset g + 1's B goes to buffer (g + 1) & 1, last read by
+            // offset g - 1; it lands while offset g multiplies
+            if (g + 1 < ng) {
+                wait_mma(g - 1);
+                if (ok0) copy_b(g + 1);
+            }
+            if (ok0) {
+                ok0 = mbar_wait(smem_addr(&bbar[g & 1]), uint32_t(g >> 1) & 1u, spin_limit);
+                if (ok0) landed = g;
+            }
+            if (ok0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t ahi = smem_addr(a_hi(0)), alo = ahi + uint32_t(aplane * 4);
+                const int dy = (gl[g] % 9) / 3 - 1, dx = gl[g] % 3 - 1;
+                const uint32_t ahi = smem_addr(A), alo = ahi + uint32_t(aplane * 4);
+                const uint32_t bhi = smem_addr(B + size_t(g & 1) * 2 * bplane);
+                const uint32_t blo = bhi + uint32_t(bplane * 4);
                 const uint64_t sa = (2 * LBO_A) >> 4, sb = (2 * LBO_B) >> 4;
+                const uint64_t dbh = mma_desc(bhi, LBO_B, SBO_B), dbl = mma_desc(blo, LBO_B, SBO_B);
+                // target cell (x, y) reads staged cell (x + 1 + dx, y + 1 + dy)
+                const uint32_t cell0 = uint32_t((1 + dy) * TCB_HX + 1 + dx) * 16;
+                const uint64_t dah = mma_desc(ahi + cell0, LBO_A, SBO_A);
+                const uint64_t dal = mma_desc(alo + cell0, LBO_A, SBO_A);
                 uint32_t acc = issued >= 0 ? 1u : 0u;  // the unit's first product overwrites
-                for (int s3 = 0; s3 < 3; ++s3) {
-                    if (!(mask3 & (1u << s3))) continue;
-                    const uint32_t bhi = smem_addr(b_img(0, 2 * s3));
-                    const uint32_t blo = smem_addr(b_img(0, 2 * s3 + 1));
-                    const uint64_t dbh = mma_desc(bhi, LBO_B, SBO_B), dbl = mma_desc(blo, LBO_B, SBO_B);
-                    // target (x, y) reads staged cell (x + 1 + dx, y + 1 + dy), dx = s3 - 1
-                    const uint32_t cell0 = uint32_t(int(sdy[j]) * TC2_HX + s3) * 16;
-                    const uint64_t dah = mma_desc(ahi + cell0, LBO_A, SBO_A);
-                    const uint64_t dal = mma_desc(alo + cell0, LBO_A, SBO_A);
-                    for (int ks = 0; ks < Kpad / 8; ++ks) {
-                        mma_tf32(tbase, dah + ks * sa, dbh + ks * sb, idesc, acc);
-                        mma_tf32(tbase, dah + ks * sa, dbl + ks * sb, idesc, 1u);
-                        mma_tf32(tbase, dal + ks * sa, dbh + ks * sb, idesc, 1u);
-                        acc = 1u;
-                    }
+                for (int ks = 0; ks < Kpad / 8; ++ks) {
+                    mma_tf32(tbase, dah + ks * sa, dbh + ks * sb, idesc, acc);
+                    mma_tf32(tbase, dah + ks * sa, dbl + ks * sb, idesc, 1u);
+                    mma_tf32(tbase, dal + ks * sa, dbh + ks * sb, idesc, 1u);
+                    acc = 1u;
                 }
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        bar));
-                issued = j;
-                w = mbar_wait(bar, phase, spin_limit);
-                if (!w) mbar_wait(bar, phase, 1LL << 26);  // no TMEM freed under MMAs
+                        smem_addr(&mbar[g & 1])));
+                issued = g;
             }
         }
-        phase ^= 1u;
-        ok = __syncthreads_and(w);
-        if (!ok && tid == 0) set_status(status, ST_ETIMEOUT);
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        // a new source class: split it into A once every MMA so far is done
+        if (g + 1 < ng && gl[g + 1] / 9 != gl[g] / 9) {
+            if (tid == 0 && ok0) wait_mma(g);
+            ok = __syncthreads_and(tid != 0 || ok0);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            split(gl[g + 1] / 9);
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+        }
     }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __shared__ int s_issued;
+    if (tid == 0 && ok0) wait_mma(issued);
+    ok = __syncthreads_and(tid != 0 || ok0) && ok;
+    if (!ok) {
+        if (tid == 0) {
+            set_status(status, ST_ETIMEOUT);
+            // let the copies and MMAs in flight finish before the shared
+            // memory and TMEM go (bounded, in order)
+            for (int kk = landed + 1; kk <= copied; ++kk)
+                mbar_wait(smem_addr(&bbar[kk & 1]), uint32_t(kk >> 1) & 1u, 1LL << 26);
+            for (int kk = done + 1; kk <= issued; ++kk)
+                mbar_wait(smem_addr(&mbar[kk & 1]), uint32_t(kk >> 1) & 1u, 1LL << 26);
+        }
+        __syncthreads();
+    }
     if (tid == 0) s_issued = issued;
     __syncthreads();
-    if (ok && tid < 128) {
-        // thread tid = TMEM lane = M row = target (tid % 8, tid / 8)
-        const int Px = Px0 + (tid & 7), Py = Py0 + (tid >> 3);
-        float v[TC_MAX_NPAD];
-        if (s_issued >= 0) {
-            const uint32_t taddr = tbase + (uint32_t(warp * 32) << 16);
-            for (int c0 = 0; c0 < Npad; c0 += 16) tmem_ld16(taddr + uint32_t(c0), v + c0);
-        } else {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        // warp w reads TMEM lanes 32 (w mod 4) .. (M rows = cells (m mod 8,
+        // m / 8)); warps 0-3 take target classes 0 and 1, warps 4-7 classes 2, 3
+        const int m = (warp & 3) * 32 + (tid & 31);
+        const int Px = Px0 + (m & 7), Py = Py0 + (m >> 3);
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = (warp >> 2) * 2 + cc;
+            float v[TC_MAX_NPAD];
+            if (s_issued >= 0) {
+                const uint32_t taddr = tbase + (uint32_t((warp & 3) * 32) << 16) + uint32_t(c * Npad);
+                for (int c0 = 0; c0 < Npad; c0 += 16) tmem_ld16(taddr + uint32_t(c0), v + c0);
+            } else {
 #pragma unroll
-            for (int i = 0; i < TC_MAX_NPAD; ++i) v[i] = 0.f;
-        }
-        if (box_count(st, L, l, morton_key(uint32_t(2 * Px + cx), uint32_t(2 * Py + cy)))) {
-            float2 *dst = le + d.eoff + (lvl_off(l) + int64_t(c) * quarter + int64_t(Py) * W + Px) * p;
-            for (int m = 0; m < p; ++m) dst[m] = make_float2(v[m], v[p + m]);
+                for (int i = 0; i < TC_MAX_NPAD; ++i) v[i] = 0.f;
+            }
+            const uint32_t ix = uint32_t(2 * Px + (c & 1)), iy = uint32_t(2 * Py + (c >> 1));
+            if (box_count(st, L, l, morton_key(ix, iy))) {
+                float2 *dst =
+                    le + d.eoff + (lvl_off(l) + int64_t(c) * quarter + int64_t(Py) * W + Px) * p;
+                for (int k = 0; k < p; ++k) dst[k] = make_float2(v[k], v[p + k]);
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -586,34 +641,63 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc2(
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols));
 }
 
-size_t m2l_tc2_smem_bytes(int p) {
+size_t m2l_tcb_smem_bytes(int p) {
     const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
-    // hi and lo of one staged class, six B images
-    return size_t(2) * (Kpad / 4) * TC2_HALO * 16 + size_t(6) * Kpad * Npad * 4;
+    // A hi and lo of one staged class; two buffers of one offset's B hi and lo
+    return size_t(2) * (Kpad / 4) * TCB_HALO * 16 + size_t(4) * Kpad * (4 * Npad) * 4;
 }
 
-bool m2l_tc2_supported(int p, int level) {
+bool m2l_tcb_supported(int p, int level) {
     const int Npad = (2 * p + 15) & ~15;
-    const int W = 1 << (level - 1);
-    return W >= TC2_BY && W < 128 && Npad <= TC_MAX_NPAD &&
-           m2l_tc2_smem_bytes(p) <= size_t(220) * 1024;
+    return level >= 5 && level <= 15 && Npad <= TC_MAX_NPAD &&
+           m2l_tcb_smem_bytes(p) <= size_t(220) * 1024;
 }
 
-int64_t m2l_tc2_units(int level) {
+int64_t m2l_tcb_units(int level) {
     const int64_t W = int64_t(1) << (level - 1);
-    return 4 * (W / TC2_BX) * (W / TC2_BY);
+    return (W / TC2_BX) * (W / TC2_BY);
 }
 
-cudaError_t launch_m2l_tc2(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
+// B images of the block units for p: for each (source class c', dy, dx), as
+// g = c' 9 + (dy + 1) 3 + dx + 1, hi then lo, each Kpad x 4Npad floats in the
+// K-major core-matrix layout [k / 4][n][k % 4], n = c Npad + (column of the
+// row-unit image of class c's operator, zero if none).
+void host_m2l_tcb_images(int p, int kernel, std::vector<float> &out) {
+    const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15, NC = 4 * Npad;
+    std::vector<float> ops;
+    host_m2l_tc_images(p, kernel, ops);
+    const size_t oslot = size_t(Kpad) * Npad, bslot = size_t(Kpad) * NC;
+    out.assign(size_t(36) * 2 * bslot, 0.0f);
+    for (int cs = 0; cs < 4; ++cs)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int g = cs * 9 + (dy + 1) * 3 + dx + 1;
+                for (int c = 0; c < 4; ++c) {
+                    const int op = tcb_op(c, cs, dx, dy);
+                    if (op < 0) continue;
+                    for (int hl = 0; hl < 2; ++hl) {
+                        const float *src = ops.data() + (size_t(op) * 2 + hl) * oslot;
+                        float *dst = out.data() + (size_t(g) * 2 + hl) * bslot;
+                        for (int kg = 0; kg < Kpad / 4; ++kg)
+                            for (int n = 0; n < Npad; ++n)
+                                for (int r = 0; r < 4; ++r)
+                                    dst[(size_t(kg) * NC + c * Npad + n) * 4 + r] =
+                                        src[(size_t(kg) * Npad + n) * 4 + r];
+                    }
+                }
+            }
+}
+
+cudaError_t launch_m2l_tcb(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                            const uint32_t *start, const float2 *me, float2 *le,
                            const uint32_t *ucount, int dense_pct, int pmax, long long spin_limit,
                            int *status, cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    const size_t smem_bytes = m2l_tc2_smem_bytes(pmax);
-    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem_bytes = m2l_tcb_smem_bytes(pmax);
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_tcb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem_bytes));
     if (e != cudaSuccess) return e;
-    k_m2l_tc2<<<unsigned(nblocks), TC_THREADS, smem_bytes, st>>>(tasks, ntasks, insts, start, me,
+    k_m2l_tcb<<<unsigned(nblocks), TC_THREADS, smem_bytes, st>>>(tasks, ntasks, insts, start, me,
                                                                  le, ucount, dense_pct, spin_limit,
                                                                  status);
     PF_LAUNCHED(1);

@@ -137,7 +137,8 @@ def test_vortex_and_laplace_contexts_side_by_side(orc):
     dict(n=10_000, seed=1, L=4, p=12, frac=0.0),
     dict(n=60_000, seed=2, L=6, p=17, frac=0.5),
     dict(n=300_000, seed=3, L=8, p=17, frac=0.2),   # tensor-core M2L levels
-    dict(n=300_000, seed=3, L=8, p=17, frac=0.2, blocks=1),   # ... and blocks at 5 to 7
+    dict(n=300_000, seed=3, L=8, p=17, frac=0.2, blocks=1),   # ... blocks from level 5
+    dict(n=300_000, seed=3, L=8, p=17, frac=0.2, blocks=2),   # ... row units
     dict(n=1000, seed=4, L=2, p=40, frac=0.0),      # no tensor cores at this order
 ])
 def test_laplace_mixed_vs_fp64(case, dtype):

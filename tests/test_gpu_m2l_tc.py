@@ -1,8 +1,9 @@
-"""The tensor-core M2L (tcgen05, 3xTF32, mixed path: row units at levels
->= 8, 8 x 16 blocks of parent cells at levels 5 to 7 -- forced here with
-PETFMM_OPT_TC_BLOCKS = 1, a single tree leaves them to the tiled SIMT kernel
-by default) against the FP32 SIMT M2L and the FP64 FMM, for each padded
-operand shape, plus the bounded-wait timeout report."""
+"""The tensor-core M2L (tcgen05, 3xTF32, mixed path) in each of its shapes --
+blocks of 8 x 16 parent cells with the four child classes side by side at
+levels >= 8 (default), blocks at every level >= 5 (PETFMM_OPT_TC_BLOCKS = 1),
+row units of one class at levels >= 8 (= 2) -- against the FP32 SIMT M2L and
+the FP64 FMM, for each padded operand shape, plus the bounded-wait timeout
+report."""
 import numpy as np
 import pytest
 
@@ -28,7 +29,7 @@ def _run(w, tc, L=None, p=None, dense_pct=None, blocks=0):
     return out
 
 
-@pytest.mark.parametrize("blocks", [0, 1])
+@pytest.mark.parametrize("blocks", [0, 1, 2])
 @pytest.mark.parametrize("p", [8, 12, 17, 24])   # Kpad/Npad = 16/16, 24/32, 40/48, 48/48
 @pytest.mark.parametrize("L,n,frac", [(8, 300_000, 0.0), (9, 400_000, 0.6)])
 def test_tensor_core_m2l_matches_simt_and_fp64(L, n, frac, p, blocks):
@@ -41,13 +42,14 @@ def test_tensor_core_m2l_matches_simt_and_fp64(L, n, frac, p, blocks):
     assert np.all(np.isfinite(u_tc)) and np.all(np.isfinite(v_tc))
 
 
+@pytest.mark.parametrize("blocks", [1, 2])
 @pytest.mark.parametrize("dense_pct", [0, 10, 50, 100])
-def test_dense_sparse_split_covers_every_box(dense_pct):
+def test_dense_sparse_split_covers_every_box(dense_pct, blocks):
     # whichever units the tensor cores take (row units and blocks), the
     # kernels together must translate every target exactly once (poisoned
     # buffers would show NaN)
     w = W.tiny(300_000, 91, L=9, p=17, clustered_frac=0.7)
-    u_mx, v_mx = _run(w, tc=True, dense_pct=dense_pct, blocks=1)
+    u_mx, v_mx = _run(w, tc=True, dense_pct=dense_pct, blocks=blocks)
     u_si, v_si = _run(w, tc=False)
     assert np.all(np.isfinite(u_mx)) and np.all(np.isfinite(v_mx))
     assert G.rel_l2(u_mx, v_mx, u_si, v_si) <= 1e-5
@@ -64,10 +66,12 @@ def test_tensor_core_m2l_far_field_alone(orc):
     assert G.rel_l2(u_tc[tg], v_tc[tg], ur, vr) <= 1e-5
 
 
-def test_bounded_wait_reports_timeout_and_context_recovers():
+@pytest.mark.parametrize("blocks", [0, 2])
+def test_bounded_wait_reports_timeout_and_context_recovers(blocks):
     _lib = G.lib()
     w = W.tiny(200_000, 5, L=8, p=17)
     ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype="f64")
+    ctx.set_option(_lib.PETFMM_OPT_TC_BLOCKS, blocks)
     x, y, g = G.to_dev((w.x, w.y, w.gamma))
     ctx.set_option(_lib.PETFMM_OPT_SPIN_LIMIT, -1)  # first waits get no iterations
     ctx.evaluate(x, y, g)
@@ -79,5 +83,5 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
     assert ctx.sync() == 0
     u, v = u.cpu().numpy(), v.cpu().numpy()
     ctx.close()
-    uf, vf = _run(w, tc=True)
+    uf, vf = _run(w, tc=True, blocks=blocks)
     assert np.array_equal(u, uf) and np.array_equal(v, vf)

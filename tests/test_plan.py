@@ -35,10 +35,11 @@ def _instances(seed, k):
 @pytest.mark.parametrize("seed,k", [(1, 1), (2, 7), (3, 64), (4, 200)])
 def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
     insts = _instances(seed, k)
-    # tensor-core blocks at levels 5 to 7 only when the plan has >= 2048 of them
-    blocks = sum(4 * (2 ** (l - 1) // 8) * (2 ** (l - 1) // 16)
-                 for it in insts if it["order"] <= 24 for l in range(5, min(it["levels"], 7) + 1))
-    use_blocks = precision == 1 and blocks >= 2048
+    # tensor-core blocks at levels 5 to 7 only when the plan has >= 512 of them
+    # (counted over all levels >= 5)
+    blocks = sum((2 ** (l - 1) // 8) * (2 ** (l - 1) // 16)
+                 for it in insts if it["order"] <= 24 for l in range(5, it["levels"] + 1))
+    use_blocks = precision == 1 and blocks >= 512
     plan = lib.petfmm_debug_plan(precision, insts)
     ranges = {}
     for row in plan:
@@ -65,22 +66,19 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
         simt = sorted(int(r[2]) for r in ranges.get(5, []) if r[1] == i)
         tc = sorted(int(r[2]) for r in ranges.get(6, []) if r[1] == i)
         # every level has a SIMT launch; the levels with >= 128 parent cells per
-        # row (mixed path, p <= 24) also get the tensor-core launch, one CTA per
-        # (class, parent row, 128-cell segment), which takes the dense units
+        # row (mixed path, p <= 24) also get the tensor-core launch in blocks,
+        # one CTA per 8 x 16 parent cells (all four classes), which takes the
+        # dense units; levels 5 to 7 too when the plan has >= 512 blocks.  (The
+        # row units, launch 6, run only with PETFMM_OPT_TC_BLOCKS = 2.)
         assert simt == list(range(2, L + 1))
-        assert tc == ([l for l in range(8, L + 1)] if precision == 1 and p <= 24 else [])
-        for r in ranges.get(6, []):
-            if r[1] == i:
-                w = 2 ** (int(r[2]) - 1)
-                assert r[3] == 4 * w * (w // min(w, 128))
-        # levels with 16 to 64 parent cells per row (mixed path, p <= 24) get
-        # the tensor-core launch in blocks, one CTA per (class, 8 x 16 cells)
+        assert tc == []
         tc2 = sorted(int(r[2]) for r in ranges.get(7, []) if r[1] == i)
-        assert tc2 == ([l for l in range(5, min(L, 7) + 1)] if use_blocks and p <= 24 else [])
+        assert tc2 == ([l for l in range(5 if use_blocks else 8, L + 1)]
+                       if precision == 1 and p <= 24 else [])
         for r in ranges.get(7, []):
             if r[1] == i:
                 w = 2 ** (int(r[2]) - 1)
-                assert r[3] == 4 * (w // 8) * (w // 16)
+                assert r[3] == (w // 8) * (w // 16)
         # the other levels of the mixed path (p <= 24) get the tiled SIMT
         # launch, one CTA per (class, 128 target boxes: a 128-cell segment of
         # a parent row, or several whole rows where rows are shorter)
