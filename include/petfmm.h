@@ -282,8 +282,8 @@ enum {
                                   the tensor-core M2L.  0 (default): blocks of 8 x 16
                                   parent cells (all four child classes) at levels >= 8,
                                   and at levels 5 to 7 when the evaluation has at least
-                                  512 blocks (a batch; a single tree runs those levels
-                                  faster on the tiled SIMT kernel); 1: blocks at every
+                                  512 blocks there (a batch; a single tree runs those
+                                  levels on the tiled SIMT kernel in FP32); 1: blocks at every
                                   level >= 5; 2: row units (one child class, a segment
                                   of a parent row) at levels >= 8 and no blocks.
                                   Results differ by FP32 rounding only. */

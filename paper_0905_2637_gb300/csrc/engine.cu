@@ -354,9 +354,9 @@ void flatten_tasks(Plan &pl) {
 }
 
 // order class of the tiled M2L launches: p <= 8, 12, 18, 24
-// Fewest block units (all levels >= 5) for which levels 5 to 7 run faster as
-// blocks than on the tiled SIMT kernel (a batch of 512 trees has 3,260; one
-// tree of 2^20 blobs at L = 8, 170).
+// Fewest block units at levels 5 to 7 for which those levels run as blocks
+// rather than on the tiled SIMT kernel (a batch of 512 trees has 3,260; one
+// tree, at most 42).
 constexpr int64_t kTc2MinUnits = 512;
 
 int tile_class(int p) { return p <= 8 ? 0 : p <= 12 ? 1 : p <= 18 ? 2 : 3; }
@@ -451,11 +451,12 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_blocks, int tc_seg
     // classes one by one)
     if (precision == PETFMM_MIXED) {
         int64_t base = pl.m2l_tc.nblocks;
-        // levels 5 to 7 of a single tree keep more CTAs in flight on the tiled
-        // SIMT kernel; a batch fills the GPU with blocks
+        // levels 5 to 7: a batch fills the GPU with blocks; a single tree has
+        // few, and runs them on the tiled SIMT kernel (also in FP32, where
+        // the blocks' 3xTF32 adds about 1e-6 to the rel-L2 error)
         int64_t blocks = 0;
         for (int i = 0; i < ni; ++i)
-            for (int l = 2; l <= pl.inst[i].L; ++l)
+            for (int l = 2; l <= std::min(pl.inst[i].L, 7); ++l)
                 if (!((pl.inst[i].tc_levels >> l) & 1u) && m2l_tcb_supported(pl.inst[i].p, l))
                     blocks += m2l_tcb_units(l);
         const bool shallow = tc_blocks == 1 || (tc_blocks == 0 && blocks >= kTc2MinUnits);
