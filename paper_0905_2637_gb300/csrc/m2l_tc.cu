@@ -367,17 +367,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
 // the nine parent offsets (dx, dy) is one 128 x 4Npad x 2p product whose A
 // starts dy staged rows and dx cells away and whose B is the four classes'
 // operators T_delta, delta = (2 dx + c'x - cx, 2 dy + c'y - cy), side by side
-// (zero for a class whose delta is within one box).  Wide N amortises each A
-// read from shared memory over four operators.
+// (zero for a class whose delta is within one box; each class padded to a
+// multiple of 8 columns, NW = 2p rounded up).  Wide N amortises each A read
+// from shared memory over four operators.
 //
-// Pipeline (one CTA per SM).  The offsets run in a fixed order, source class
-// by source class.  Offset g's B (hi and lo, one bulk asynchronous copy)
-// lands in buffer g mod 2 on mbarrier bbar[g mod 2]; its MMAs complete on
-// mbar[g mod 2].  Thread 0 issues copies and MMAs and alone waits on the
-// barriers, always in offset order, so no barrier runs a phase ahead of its
-// waiter: offset g + 1's copy is issued, once offset g - 1's MMAs (the last
-// reader of that buffer) are done, before offset g's MMAs, and lands while
-// they run.  A new source class is split into A once every MMA so far is done.
+// Pipeline.  The offsets run in a fixed order, source class by source class,
+// each as S stages: S = 1, its B hi and lo images together (three products);
+// S = 2, its B hi image (products A_hi B_hi and A_lo B_hi), then its B lo
+// image (A_hi B_lo).  Stage h's images arrive by one bulk asynchronous copy
+// into buffer h mod 2 on mbarrier bbar[h mod 2]; its MMAs complete on
+// mbar[h mod 2].  Thread 0 issues copies and MMAs and alone waits
+// on the barriers, always in stage order, so no barrier runs a phase ahead
+// of its waiter: stage h + 1's copy is issued, once stage h - 1's MMAs (the
+// last reader of that buffer) are done, before stage h's MMAs, and lands
+// while they run.  A new source class is split into A once every MMA so far
+// is done.  With S = 2 a CTA holds 109 KB of shared memory at p = 17, so two
+// share an SM and one's splits overlap the other's MMAs, at twice the waits
+// per offset: the launch takes S = 2 when it has many blocks (a full tree of
+// >= 10 levels, a batch) and S = 1 (181 KB, one CTA per SM) otherwise.
 // ----------------------------------------------------------------------------
 constexpr int TCB_HX = TC2_BX + 2, TCB_HY = TC2_BY + 2;
 constexpr int TCB_HALO = TCB_HX * TCB_HY;  // staged cells per source class
@@ -391,6 +398,7 @@ __host__ __device__ __forceinline__ int tcb_op(int c, int cs, int dx, int dy) {
     return (ax > ay ? ax : ay) >= 2 ? m2l_op_index(ddx, ddy) : -1;
 }
 
+template <int S>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
     const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const float2 *__restrict__ me, float2 *__restrict__ le,
@@ -415,12 +423,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
     const uint32_t *st = start + d.soff;
 
     const int K2 = 2 * p;
-    const int Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15, NC = 4 * Npad;
+    const int Kpad = (K2 + 7) & ~7, NW = (K2 + 7) & ~7, NC = 4 * NW;
     const int KG = Kpad / 4;
     const size_t aplane = size_t(KG) * TCB_HALO * 4;  // floats of A hi (or lo)
-    const size_t bplane = size_t(Kpad) * NC;          // floats of one offset's B hi (or lo)
+    const size_t bplane = size_t(Kpad) * NC;          // floats of one B image (hi or lo)
+    const size_t bstage = size_t(3 - S) * bplane;     // floats of one stage's images
     float *A = reinterpret_cast<float *>(smem);       // hi, then lo
-    float *B = A + 2 * aplane;                        // 2 buffers of (hi, lo)
+    float *B = A + 2 * aplane;                        // 2 buffers of one stage
     // zero the K padding of every staged cell once (never overwritten)
     for (int i = tid; i < TCB_HALO * (Kpad - K2); i += TC_THREADS) {
         const int r = i / (Kpad - K2), k = K2 + i % (Kpad - K2);
@@ -521,23 +530,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
             }
         }
     };
-    // thread 0's state: offsets whose MMAs are known complete, whose B copy
+    // thread 0's state: stages whose MMAs are known complete, whose B copy
     // was issued and has landed, MMAs issued, and whether every wait so far
-    // ended in time
+    // ended in time; stage h is offset gl[h / S] (S = 2: image h % 2, hi or lo)
+    const int nh = S * ng;
     int done = -1, copied = -1, landed = -1, issued = -1;
     bool ok0 = true;
-    auto wait_mma = [&](int k) {  // thread 0 only, in offset order
+    auto wait_mma = [&](int k) {  // thread 0 only, in stage order
         for (int kk = done + 1; kk <= k && ok0; ++kk) {
             ok0 = mbar_wait(smem_addr(&mbar[kk & 1]), uint32_t(kk >> 1) & 1u, spin_limit);
             if (ok0) done = kk;
         }
     };
-    const uint32_t bbytes = uint32_t(2 * bplane * 4);  // hi and lo, contiguous
+    const uint32_t bbytes = uint32_t(bstage * 4);
     auto copy_b = [&](int k) {  // thread 0 only
         const uint32_t bb = smem_addr(&bbar[k & 1]);
         mbar_arrive_expect_tx(bb, bbytes);
-        bulk_g2s(smem_addr(B + size_t(k & 1) * 2 * bplane), bimg + size_t(gl[k]) * 2 * bplane,
-                 bbytes, bb);
+        const size_t src = (size_t(gl[k / S]) * 2 + size_t(S == 2 ? (k & 1) : 0)) * bplane;
+        bulk_g2s(smem_addr(B + size_t(k & 1) * bstage), bimg + src, bbytes, bb);
         copied = k;
     };
     bool ok = true;
@@ -546,51 +556,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
     }
-    for (int g = 0; g < ng && ok; ++g) {
+    for (int h = 0; h < nh && ok; ++h) {
         if (tid == 0 && ok0) {
-            if (g == 0) copy_b(0);
-            // offset g + 1's B goes to buffer (g + 1) & 1, last read by
-            // offset g - 1; it lands while offset g multiplies
-            if (g + 1 < ng) {
-                wait_mma(g - 1);
-                if (ok0) copy_b(g + 1);
+            if (h == 0) copy_b(0);
+            // stage h + 1's image goes to buffer (h + 1) & 1, last read by
+            // stage h - 1; it lands while stage h multiplies
+            if (h + 1 < nh) {
+                wait_mma(h - 1);
+                if (ok0) copy_b(h + 1);
             }
             if (ok0) {
-                ok0 = mbar_wait(smem_addr(&bbar[g & 1]), uint32_t(g >> 1) & 1u, spin_limit);
-                if (ok0) landed = g;
+                ok0 = mbar_wait(smem_addr(&bbar[h & 1]), uint32_t(h >> 1) & 1u, spin_limit);
+                if (ok0) landed = h;
             }
             if (ok0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
+                const int g = h / S;
                 const int dy = (gl[g] % 9) / 3 - 1, dx = gl[g] % 3 - 1;
                 const uint32_t ahi = smem_addr(A), alo = ahi + uint32_t(aplane * 4);
-                const uint32_t bhi = smem_addr(B + size_t(g & 1) * 2 * bplane);
-                const uint32_t blo = bhi + uint32_t(bplane * 4);
+                const uint32_t bimg_s = smem_addr(B + size_t(h & 1) * bstage);
                 const uint64_t sa = (2 * LBO_A) >> 4, sb = (2 * LBO_B) >> 4;
-                const uint64_t dbh = mma_desc(bhi, LBO_B, SBO_B), dbl = mma_desc(blo, LBO_B, SBO_B);
+                const uint64_t db = mma_desc(bimg_s, LBO_B, SBO_B);
+                const uint64_t dbl = mma_desc(bimg_s + uint32_t(bplane * 4), LBO_B, SBO_B);
                 // target cell (x, y) reads staged cell (x + 1 + dx, y + 1 + dy)
                 const uint32_t cell0 = uint32_t((1 + dy) * TCB_HX + 1 + dx) * 16;
                 const uint64_t dah = mma_desc(ahi + cell0, LBO_A, SBO_A);
                 const uint64_t dal = mma_desc(alo + cell0, LBO_A, SBO_A);
                 uint32_t acc = issued >= 0 ? 1u : 0u;  // the unit's first product overwrites
                 for (int ks = 0; ks < Kpad / 8; ++ks) {
-                    mma_tf32(tbase, dah + ks * sa, dbh + ks * sb, idesc, acc);
-                    mma_tf32(tbase, dah + ks * sa, dbl + ks * sb, idesc, 1u);
-                    mma_tf32(tbase, dal + ks * sa, dbh + ks * sb, idesc, 1u);
+                    if (S == 1) {
+                        mma_tf32(tbase, dah + ks * sa, db + ks * sb, idesc, acc);
+                        mma_tf32(tbase, dah + ks * sa, dbl + ks * sb, idesc, 1u);
+                        mma_tf32(tbase, dal + ks * sa, db + ks * sb, idesc, 1u);
+                    } else {
+                        // B hi: A_hi B_hi + A_lo B_hi; B lo: A_hi B_lo
+                        mma_tf32(tbase, dah + ks * sa, db + ks * sb, idesc, acc);
+                        if (!(h & 1)) mma_tf32(tbase, dal + ks * sa, db + ks * sb, idesc, 1u);
+                    }
                     acc = 1u;
                 }
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_addr(&mbar[g & 1])));
-                issued = g;
+                        smem_addr(&mbar[h & 1])));
+                issued = h;
             }
         }
         // a new source class: split it into A once every MMA so far is done
-        if (g + 1 < ng && gl[g + 1] / 9 != gl[g] / 9) {
-            if (tid == 0 && ok0) wait_mma(g);
+        if (h + 1 < nh && (h + 1) % S == 0 && gl[(h + 1) / S] / 9 != gl[h / S] / 9) {
+            if (tid == 0 && ok0) wait_mma(h);
             ok = __syncthreads_and(tid != 0 || ok0);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            split(gl[g + 1] / 9);
+            split(gl[(h + 1) / S] / 9);
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
         }
@@ -619,19 +636,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
         const int Px = Px0 + (m & 7), Py = Py0 + (m >> 3);
         for (int cc = 0; cc < 2; ++cc) {
             const int c = (warp >> 2) * 2 + cc;
-            float v[TC_MAX_NPAD];
+            // class c's columns c NW .. c NW + 2p - 1, read in 16-column chunks
+            // from the 16-aligned column at or below c NW
+            const int a0 = (c * NW) & ~15, off = c * NW - a0;
+            const int nch = (off + K2 + 15) / 16;
+            float v[64];
             if (s_issued >= 0) {
-                const uint32_t taddr = tbase + (uint32_t((warp & 3) * 32) << 16) + uint32_t(c * Npad);
-                for (int c0 = 0; c0 < Npad; c0 += 16) tmem_ld16(taddr + uint32_t(c0), v + c0);
+                const uint32_t taddr = tbase + (uint32_t((warp & 3) * 32) << 16) + uint32_t(a0);
+                for (int q = 0; q < nch; ++q) tmem_ld16(taddr + uint32_t(16 * q), v + 16 * q);
             } else {
 #pragma unroll
-                for (int i = 0; i < TC_MAX_NPAD; ++i) v[i] = 0.f;
+                for (int i = 0; i < 64; ++i) v[i] = 0.f;
             }
             const uint32_t ix = uint32_t(2 * Px + (c & 1)), iy = uint32_t(2 * Py + (c >> 1));
             if (box_count(st, L, l, morton_key(ix, iy))) {
                 float2 *dst =
                     le + d.eoff + (lvl_off(l) + int64_t(c) * quarter + int64_t(Py) * W + Px) * p;
-                for (int k = 0; k < p; ++k) dst[k] = make_float2(v[k], v[p + k]);
+                for (int k = 0; k < p; ++k) dst[k] = make_float2(v[off + k], v[off + p + k]);
             }
         }
     }
@@ -641,11 +662,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols));
 }
 
-size_t m2l_tcb_smem_bytes(int p) {
-    const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15;
-    // A hi and lo of one staged class; two buffers of one offset's B hi and lo
-    return size_t(2) * (Kpad / 4) * TCB_HALO * 16 + size_t(4) * Kpad * (4 * Npad) * 4;
+// stages per offset: 2 for launches of many blocks
+constexpr int64_t kTcbTwoStageUnits = 2048;
+static int tcb_stages(int64_t nblocks) { return nblocks >= kTcbTwoStageUnits ? 2 : 1; }
+
+static size_t tcb_smem_bytes(int p, int S) {
+    const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, NW = (K2 + 7) & ~7;
+    // A hi and lo of one staged class; two buffers of one stage's B images
+    return size_t(2) * (Kpad / 4) * TCB_HALO * 16 + size_t(2) * (3 - S) * Kpad * (4 * NW) * 4;
 }
+
+size_t m2l_tcb_smem_bytes(int p) { return tcb_smem_bytes(p, 1); }
 
 bool m2l_tcb_supported(int p, int level) {
     const int Npad = (2 * p + 15) & ~15;
@@ -659,11 +686,13 @@ int64_t m2l_tcb_units(int level) {
 }
 
 // B images of the block units for p: for each (source class c', dy, dx), as
-// g = c' 9 + (dy + 1) 3 + dx + 1, hi then lo, each Kpad x 4Npad floats in the
-// K-major core-matrix layout [k / 4][n][k % 4], n = c Npad + (column of the
-// row-unit image of class c's operator, zero if none).
+// g = c' 9 + (dy + 1) 3 + dx + 1, hi then lo, each Kpad x 4NW floats (NW = 2p
+// rounded up to 8) in the K-major core-matrix layout [k / 4][n][k % 4],
+// n = c NW + (column of the row-unit image of class c's operator, zero if
+// none).
 void host_m2l_tcb_images(int p, int kernel, std::vector<float> &out) {
-    const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15, NC = 4 * Npad;
+    const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, Npad = (K2 + 15) & ~15, NW = (K2 + 7) & ~7;
+    const int NC = 4 * NW;
     std::vector<float> ops;
     host_m2l_tc_images(p, kernel, ops);
     const size_t oslot = size_t(Kpad) * Npad, bslot = size_t(Kpad) * NC;
@@ -679,9 +708,9 @@ void host_m2l_tcb_images(int p, int kernel, std::vector<float> &out) {
                         const float *src = ops.data() + (size_t(op) * 2 + hl) * oslot;
                         float *dst = out.data() + (size_t(g) * 2 + hl) * bslot;
                         for (int kg = 0; kg < Kpad / 4; ++kg)
-                            for (int n = 0; n < Npad; ++n)
+                            for (int n = 0; n < NW; ++n)
                                 for (int r = 0; r < 4; ++r)
-                                    dst[(size_t(kg) * NC + c * Npad + n) * 4 + r] =
+                                    dst[(size_t(kg) * NC + c * NW + n) * 4 + r] =
                                         src[(size_t(kg) * Npad + n) * 4 + r];
                     }
                 }
@@ -693,13 +722,14 @@ cudaError_t launch_m2l_tcb(const Task *tasks, int ntasks, int64_t nblocks, const
                            const uint32_t *ucount, int dense_pct, int pmax, long long spin_limit,
                            int *status, cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    const size_t smem_bytes = m2l_tcb_smem_bytes(pmax);
-    cudaError_t e = cudaFuncSetAttribute(k_m2l_tcb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const int S = tcb_stages(nblocks);
+    const size_t smem_bytes = tcb_smem_bytes(pmax, S);
+    auto k = S == 2 ? k_m2l_tcb<2> : k_m2l_tcb<1>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem_bytes));
     if (e != cudaSuccess) return e;
-    k_m2l_tcb<<<unsigned(nblocks), TC_THREADS, smem_bytes, st>>>(tasks, ntasks, insts, start, me,
-                                                                 le, ucount, dense_pct, spin_limit,
-                                                                 status);
+    k<<<unsigned(nblocks), TC_THREADS, smem_bytes, st>>>(tasks, ntasks, insts, start, me, le, ucount,
+                                                         dense_pct, spin_limit, status);
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
