@@ -252,9 +252,10 @@ enum {
     PETFMM_OPT_M2L_TC = 5,     /* mixed path: 1 (default) M2L of levels >= 8 on the tensor
                                   cores (3xTF32; see PETFMM_OPT_TC_BLOCKS), 0 all levels
                                   on the FP32 SIMT kernels */
-    PETFMM_OPT_TC_DENSE = 6,   /* percent (0..100, default 25) of a tensor-core unit's
-                                  targets that must hold particles for the unit to run
-                                  on the tensor cores; sparser units use the SIMT kernel */
+    PETFMM_OPT_TC_DENSE = 6,   /* percent (0..100, default 1) of a tensor-core (or
+                                  tiled) unit's targets that must hold particles for the
+                                  unit to run there; sparser units use the per-box SIMT
+                                  kernel */
     PETFMM_OPT_TC_SEG = 8,     /* widest tensor-core M2L unit in parent cells: 128
                                   (default), 256 or 512 */
     PETFMM_OPT_NEAR_TOL = 9,   /* mixed path: relative tolerance of the polynomial that

@@ -122,7 +122,7 @@ struct petfmm_ctx {
     bool m2l_tc = true;
     // measured on GB300 (clustered 16M and lattice 1M blobs): 128-cell units
     // with a 25% occupancy threshold gave the fastest M2L on both
-    int tc_dense_pct = 25;
+    int tc_dense_pct = 1;
     int tc_segmax = kTcSegDefault;
     double near_tol = kNearTolDefault;
     int64_t spin_limit = 0;
