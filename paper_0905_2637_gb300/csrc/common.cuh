@@ -67,7 +67,7 @@ struct InstDesc {
     uint32_t tc_levels;                 // bit l: level l's dense units run on the tensor
                                         // cores (else, if tc_unit0[l] >= 0, on the
                                         // tiled SIMT kernel)
-    uint32_t tc2_levels;                // bit l: ... on the tensor cores in 8 x 16 blocks
+    uint32_t tcb_levels;                // bit l: ... on the tensor cores in 8 x 16 blocks
                                         // (all four classes per block)
     // mixed-precision P2P constants (leaf units)
     float kappa;            // w^2 / (2 sigma^2): q = kappa * rho^2
@@ -239,13 +239,13 @@ __host__ __device__ __forceinline__ int64_t tc_unit_of(int l, int segmax, int c,
 
 // Block units of the tensor-core M2L: 8 x 16 parent cells (x, y), all four
 // target classes (512 targets); units are numbered (Py / 16) (W / 8) + Px / 8.
-constexpr int TC2_BX = 8, TC2_BY = 16;
+constexpr int TCB_BX = 8, TCB_BY = 16;
 
 __host__ __device__ __forceinline__ void tcb_unit_decode(int l, int64_t unit, int *Py0, int *Px0) {
     const int W = 1 << (l - 1);
-    const int nbx = W / TC2_BX;
-    *Py0 = int(unit / nbx) * TC2_BY;
-    *Px0 = int(unit - (unit / nbx) * nbx) * TC2_BX;
+    const int nbx = W / TCB_BX;
+    *Py0 = int(unit / nbx) * TCB_BY;
+    *Px0 = int(unit - (unit / nbx) * nbx) * TCB_BX;
 }
 
 // Units of the tiled SIMT M2L: a segment of M2L_TILE_SEG parent cells of one
@@ -289,10 +289,10 @@ __host__ __device__ __forceinline__ int64_t unit_of(const InstDesc &d, int l, in
         return tc_unit_of(l, d.tc_segmax, c, Py, Px);
     }
     const int W = 1 << (l - 1);
-    if ((d.tc2_levels >> l) & 1u) {
+    if ((d.tcb_levels >> l) & 1u) {
         (void)c;
-        *nbox = 4 * TC2_BX * TC2_BY;
-        return int64_t(Py / TC2_BY) * (W / TC2_BX) + Px / TC2_BX;
+        *nbox = 4 * TCB_BX * TCB_BY;
+        return int64_t(Py / TCB_BY) * (W / TCB_BX) + Px / TCB_BX;
     }
     int R, s;
     tile_geom(l, &R, &s);

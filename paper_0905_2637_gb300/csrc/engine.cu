@@ -69,7 +69,7 @@ struct TaskRange {
 struct Plan {
     std::vector<InstDesc> inst;
     std::vector<Task> tasks;
-    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tc2, m2l_log;
+    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tcb, m2l_log;
     // tiled SIMT M2L, one launch per order class (p <= 8, 12, 18, 24): each
     // launch's kernel is specialised for its class's largest order
     static constexpr int kTileClasses = 4;
@@ -85,7 +85,7 @@ struct Plan {
     int nbits = 0, pmax = 1, Lmax = 0;
     int deg = 0, general = 0;          // mixed P2P variant (max over instances)
     size_t tc_smem = 0;                // dynamic shared memory of the tensor-core M2L
-    int tc2_pmax = 0;                  // largest order among the block units
+    int tcb_pmax = 0;                  // largest order among the block units
 };
 
 struct Problem {
@@ -346,7 +346,7 @@ void flatten_tasks(Plan &pl) {
     put(pl.leaves_wl);
     put(pl.m2l);
     put(pl.m2l_tc);
-    put(pl.m2l_tc2);
+    put(pl.m2l_tcb);
     for (TaskRange &r : pl.m2l_tile) put(r);
     put(pl.m2l_log);
     for (TaskRange &r : pl.m2m) put(r);
@@ -357,7 +357,7 @@ void flatten_tasks(Plan &pl) {
 // Fewest block units at levels 5 to 7 for which those levels run as blocks
 // rather than on the tiled SIMT kernel (a batch of 512 trees has 3,260; one
 // tree, at most 42).
-constexpr int64_t kTc2MinUnits = 512;
+constexpr int64_t kTcbShallowMinUnits = 512;
 
 int tile_class(int p) { return p <= 8 ? 0 : p <= 12 ? 1 : p <= 18 ? 2 : 3; }
 
@@ -421,7 +421,7 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_blocks, int tc_seg
         for (int l = 0; l <= MAX_L; ++l) d.tc_unit0[l] = -1;
         d.tc_segmax = tc_segmax;
         d.tc_levels = 0;
-        d.tc2_levels = 0;
+        d.tcb_levels = 0;
         add_task(pl.morton, i, d.L, d.n, 256);
         add_task(pl.start, i, d.L, nleaf + 1, 256);
         add_task(pl.particles, i, d.L, d.n, 256);
@@ -459,28 +459,28 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_blocks, int tc_seg
             for (int l = 2; l <= std::min(pl.inst[i].L, 7); ++l)
                 if (!((pl.inst[i].tc_levels >> l) & 1u) && m2l_tcb_supported(pl.inst[i].p, l))
                     blocks += m2l_tcb_units(l);
-        const bool shallow = tc_blocks == 1 || (tc_blocks == 0 && blocks >= kTc2MinUnits);
+        const bool shallow = tc_blocks == 1 || (tc_blocks == 0 && blocks >= kTcbShallowMinUnits);
         if (use_tc && tc_blocks != 2) {
             for (int i = 0; i < ni; ++i) {
                 InstDesc &d = pl.inst[i];
                 for (int l = 2; l <= d.L; ++l) {
                     if (((d.tc_levels >> l) & 1u) || !m2l_tcb_supported(d.p, l)) continue;
                     if (l < 8 && !shallow) continue;
-                    d.tc_unit0[l] = base + pl.m2l_tc2.nblocks;
-                    d.tc2_levels |= 1u << l;
-                    add_task(pl.m2l_tc2, i, l, m2l_tcb_units(l), 1);
-                    pl.tc2_pmax = std::max(pl.tc2_pmax, d.p);
+                    d.tc_unit0[l] = base + pl.m2l_tcb.nblocks;
+                    d.tcb_levels |= 1u << l;
+                    add_task(pl.m2l_tcb, i, l, m2l_tcb_units(l), 1);
+                    pl.tcb_pmax = std::max(pl.tcb_pmax, d.p);
                 }
             }
         }
-        base += pl.m2l_tc2.nblocks;
+        base += pl.m2l_tcb.nblocks;
         for (int cls = 0; cls < Plan::kTileClasses; ++cls) {
             TaskRange &tr = pl.m2l_tile[cls];
             for (int i = 0; i < ni; ++i) {
                 InstDesc &d = pl.inst[i];
                 if (!m2l_tile_supported(d.p) || tile_class(d.p) != cls) continue;
                 for (int l = 2; l <= d.L; ++l) {
-                    if (((d.tc_levels | d.tc2_levels) >> l) & 1u) continue;
+                    if (((d.tc_levels | d.tcb_levels) >> l) & 1u) continue;
                     d.tc_unit0[l] = base + tr.nblocks;
                     add_task(tr, i, l, m2l_tile_units(l), 1);
                     pl.tile_pmax[cls] = std::max(pl.tile_pmax[cls], d.p);
@@ -589,7 +589,7 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     if (!pl.tasks.empty()) k.add(pl.tasks.data(), pl.tasks.size() * sizeof(Task));
     auto range = [&](const TaskRange &r) { k.put(r.first); k.put(r.count); k.put(r.nblocks); };
     for (const TaskRange *r : {&pl.morton, &pl.start, &pl.particles, &pl.leaves_p2m, &pl.leaves_wl,
-                               &pl.m2l, &pl.m2l_tc, &pl.m2l_tc2, &pl.m2l_log})
+                               &pl.m2l, &pl.m2l_tc, &pl.m2l_tcb, &pl.m2l_log})
         range(*r);
     for (const TaskRange &r : pl.m2l_tile) range(r);
     for (int cls = 0; cls < Plan::kTileClasses; ++cls) k.put(pl.tile_pmax[cls]);
@@ -598,7 +598,7 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     k.put(pl.m2m.size()); k.put(pl.l2l.size());
     k.put(pl.N); k.put(pl.nleaves); k.put(pl.nstart); k.put(pl.ncoef); k.put(pl.items_cap);
     k.put(pl.nbits); k.put(pl.pmax); k.put(pl.deg); k.put(pl.general);
-    k.put(pl.tc_smem); k.put(pl.tc2_pmax); k.put(grid);
+    k.put(pl.tc_smem); k.put(pl.tcb_pmax); k.put(grid);
     k.put(c->precision); k.put(c->dtype); k.put(c->timing); k.put(c->p2p_mode); k.put(c->poison);
     k.put(c->tc_dense_pct); k.put(c->spin_limit); k.put(c->p2p_pairs); k.put(c->kernel);
     k.put(c->tc_blocks);
@@ -676,7 +676,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->off, size_t(pl.nleaves) * 4, st));
     PF_TRY(ensure(c->items, size_t(pl.items_cap) * sizeof(uint4), st));
     PF_TRY(ensure(c->ucount,
-                  size_t(pl.m2l_tc.nblocks + pl.m2l_tc2.nblocks + pl.tile_blocks()) * sizeof(uint32_t),
+                  size_t(pl.m2l_tc.nblocks + pl.m2l_tcb.nblocks + pl.tile_blocks()) * sizeof(uint32_t),
                   st));
     if (mixed) PF_TRY(ensure(c->own, size_t(N) * sizeof(float2), st));
     if (pairs) {
@@ -808,16 +808,16 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     }
     stage_mark(c, PETFMM_STAGE_M2L);
     uint32_t *ucount = nullptr;
-    if (pl.m2l_tc.count || pl.m2l_tc2.count || pl.tile_blocks()) {
+    if (pl.m2l_tc.count || pl.m2l_tcb.count || pl.tile_blocks()) {
         ucount = static_cast<uint32_t *>(c->ucount.p);
         if (pl.m2l_tc.count)
             PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc.first, pl.m2l_tc.count,
                                          pl.m2l_tc.nblocks, dinst, start, ucount, st, lc));
-        if (pl.m2l_tc2.count)
-            PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc2.first, pl.m2l_tc2.count,
-                                         pl.m2l_tc2.nblocks, dinst, start,
+        if (pl.m2l_tcb.count)
+            PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tcb.first, pl.m2l_tcb.count,
+                                         pl.m2l_tcb.nblocks, dinst, start,
                                          ucount + pl.m2l_tc.nblocks, st, lc));
-        int64_t base = pl.m2l_tc.nblocks + pl.m2l_tc2.nblocks;
+        int64_t base = pl.m2l_tc.nblocks + pl.m2l_tcb.nblocks;
         for (const TaskRange &tr : pl.m2l_tile) {
             if (tr.count)
                 PF_CUDA(launch_tc_unit_count(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
@@ -845,16 +845,16 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                               pl.tc_smem, spin, reinterpret_cast<int *>(ctrl + CTRL_STATUS), st,
                               lc));
     }
-    if (pl.m2l_tc2.count) {
+    if (pl.m2l_tcb.count) {
         const long long spin = c->spin_limit > 0 ? c->spin_limit : c->spin_limit < 0 ? 0 : (1LL << 26);
-        PF_CUDA(launch_m2l_tcb(dtask + pl.m2l_tc2.first, pl.m2l_tc2.count, pl.m2l_tc2.nblocks,
+        PF_CUDA(launch_m2l_tcb(dtask + pl.m2l_tcb.first, pl.m2l_tcb.count, pl.m2l_tcb.nblocks,
                                dinst, start, static_cast<const float2 *>(c->me.p),
                                static_cast<float2 *>(c->le.p), ucount + pl.m2l_tc.nblocks,
-                               c->tc_dense_pct, pl.tc2_pmax, spin,
+                               c->tc_dense_pct, pl.tcb_pmax, spin,
                                reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
     }
     {
-        int64_t base = pl.m2l_tc.nblocks + pl.m2l_tc2.nblocks;
+        int64_t base = pl.m2l_tc.nblocks + pl.m2l_tcb.nblocks;
         for (int cls = 0; cls < Plan::kTileClasses; ++cls) {
             const TaskRange &tr = pl.m2l_tile[cls];
             if (tr.count)
@@ -1172,7 +1172,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
     emit(4, pl.leaves_wl);
     emit(5, pl.m2l);
     emit(6, pl.m2l_tc);
-    emit(7, pl.m2l_tc2);
+    emit(7, pl.m2l_tcb);
     for (int cls = 0; cls < Plan::kTileClasses; ++cls) emit(70 + cls, pl.m2l_tile[cls]);
     for (size_t r = 0; r < pl.m2m.size(); ++r) emit(100 + int64_t(r), pl.m2m[r]);
     for (size_t r = 0; r < pl.l2l.size(); ++r) emit(200 + int64_t(r), pl.l2l[r]);

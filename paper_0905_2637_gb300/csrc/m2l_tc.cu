@@ -13,8 +13,11 @@
 // (real parts then imaginary parts) and N = 2p output coefficients, with
 // B_delta = [[Tr^T, Ti^T], [-Ti^T, Tr^T]].
 //
-// Unit of work (one CTA): a segment of up to 512 parent cells of one parent
-// row, for one target class.  For each of the 12 (c', dy) source strips the
+// Two unit shapes.  Blocks (k_m2l_tcb, the default; below): 8 x 16 parent
+// cells with the four target classes side by side in N.  Row units
+// (k_m2l_tc, PETFMM_OPT_TC_BLOCKS = 2), described here: a segment of up to
+// 512 parent cells of one parent row, for one target class.  For each of the
+// 12 (c', dy) source strips the
 // CTA stages the strip's source expansions once in shared memory, K-major
 // without swizzle (core matrices of 8 rows x 16 bytes; rows 16 B apart inside
 // a k-group, so a row offset is a 16-byte shift of the descriptor start), and
@@ -78,12 +81,12 @@ __global__ void __launch_bounds__(256) k_tc_unit_count(const Task *__restrict__ 
     int c, Py0, R = 1, Px0, SEG;
     if ((d.tc_levels >> l) & 1u) {
         tc_unit_decode(l, d.tc_segmax, u - t.block0, &c, &Py0, &Px0, &SEG);
-    } else if ((d.tc2_levels >> l) & 1u) {
+    } else if ((d.tcb_levels >> l) & 1u) {
         // a block: 8 x 16 parent cells, all four classes (i = c 128 + cell)
         tcb_unit_decode(l, u - t.block0, &Py0, &Px0);
         const uint32_t *st = start + d.soff;
         uint32_t cnt = 0;
-        for (int i = lane; i < 4 * TC2_BX * TC2_BY; i += 32) {
+        for (int i = lane; i < 4 * TCB_BX * TCB_BY; i += 32) {
             const int cc = i >> 7, q = i & 127;
             const uint32_t ix = uint32_t(2 * (Px0 + (q & 7)) + (cc & 1));
             const uint32_t iy = uint32_t(2 * (Py0 + (q >> 3)) + (cc >> 1));
@@ -386,9 +389,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(
 // per offset: the launch takes S = 2 when it has many blocks (a full tree of
 // >= 10 levels, a batch) and S = 1 (181 KB, one CTA per SM) otherwise.
 // ----------------------------------------------------------------------------
-constexpr int TCB_HX = TC2_BX + 2, TCB_HY = TC2_BY + 2;
+constexpr int TCB_HX = TCB_BX + 2, TCB_HY = TCB_BY + 2;
 constexpr int TCB_HALO = TCB_HX * TCB_HY;  // staged cells per source class
-constexpr int TCB_M = TC2_BX * TC2_BY;     // parent cells per block
+constexpr int TCB_M = TCB_BX * TCB_BY;     // parent cells per block
 
 // delta's operator for target class c, source class cs and parent offset
 // (dx, dy), or -1 if delta is within one box
@@ -682,7 +685,7 @@ bool m2l_tcb_supported(int p, int level) {
 
 int64_t m2l_tcb_units(int level) {
     const int64_t W = int64_t(1) << (level - 1);
-    return (W / TC2_BX) * (W / TC2_BY);
+    return (W / TCB_BX) * (W / TCB_BY);
 }
 
 // B images of the block units for p: for each (source class c', dy, dx), as

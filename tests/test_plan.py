@@ -72,8 +72,8 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
         # row units, launch 6, run only with PETFMM_OPT_TC_BLOCKS = 2.)
         assert simt == list(range(2, L + 1))
         assert tc == []
-        tc2 = sorted(int(r[2]) for r in ranges.get(7, []) if r[1] == i)
-        assert tc2 == ([l for l in range(5 if use_blocks else 8, L + 1)]
+        tcb = sorted(int(r[2]) for r in ranges.get(7, []) if r[1] == i)
+        assert tcb == ([l for l in range(5 if use_blocks else 8, L + 1)]
                        if precision == 1 and p <= 24 else [])
         for r in ranges.get(7, []):
             if r[1] == i:
@@ -87,7 +87,7 @@ def test_plan_ranges_are_contiguous_and_complete(lib, precision, seed, k):
         tile_rows = [r for rid in range(70, 74) for r in ranges.get(rid, []) if r[1] == i]
         assert all(r[0] == cls for r in tile_rows)
         tile = sorted(int(r[2]) for r in tile_rows)
-        assert tile == ([l for l in range(2, L + 1) if l not in tc and l not in tc2]
+        assert tile == ([l for l in range(2, L + 1) if l not in tc and l not in tcb]
                         if precision == 1 and p <= 24 else [])
         for r in tile_rows:
             if r[1] == i:
