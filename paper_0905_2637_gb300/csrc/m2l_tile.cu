@@ -36,6 +36,8 @@ constexpr int MT_THREADS = 128;
 constexpr int MT_BOXES = M2L_TILE_SEG;  // target boxes per unit
 constexpr int MT_MAX_ROWS = 136;        // staged rows: R (SEG + 2) <= 130
 constexpr int MT_MAX_P = 24;
+// thread t takes boxes t mod 64 and t mod 64 + 64 of a unit
+static_assert(MT_BOXES <= 128 && MT_THREADS == 128, "two boxes per thread pair of half-units");
 
 // shared-memory row stride of the staged strip: odd, so that the 8-byte reads
 // of 16 consecutive boxes by a half-warp hit distinct banks
