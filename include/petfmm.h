@@ -225,6 +225,27 @@ int petfmm_debug_expansions(petfmm_ctx *ctx, int level, int which, double *out);
  * returns the count, or PETFMM_EINVAL. */
 int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out);
 
+/* Operator images of the tensor-core M2L (Sec. 2.2's M2L with the rescaled
+ * coefficients: c^_m = sum_k T_delta[k][m] a~_k), as the host builds them
+ * for order p (1..24) and kernel (PETFMM_KERNEL_VORTEX / _LAPLACE); host
+ * only, no GPU needed.  Each image is the real 2p x 2p matrix
+ * B = [[Re T, Im T], [-Im T, Re T]] (rows k: real parts of a~ then imaginary
+ * parts; columns n: real parts of c^ then imaginary parts) split for 3xTF32
+ * into hi (low 13 mantissa bits cleared) and lo = B - hi, padded with zeros
+ * to Kpad = 2p rounded up to 8 rows, stored K-major as [k / 4][n][k % 4].
+ *   blocks = 0: for each of the 40 offsets delta of [-3, 3]^2 \ [-1, 1]^2 in
+ *     row order (increasing dy, then dx), hi then lo, Npad = 2p rounded up to
+ *     16 columns.
+ *   blocks = 1: for each (source class c', dy, dx), as
+ *     g = c' 9 + (dy + 1) 3 + dx + 1, hi then lo, 4 NW columns (NW = 2p
+ *     rounded up to 8): target class c's operator for delta = (2 dx + c'x -
+ *     cx, 2 dy + c'y - cy) in columns c NW .., zeros where delta is within one
+ *     box.
+ * Returns the number of floats; copies them to out when cap is at least
+ * that (out may be NULL with cap 0 to ask for the size); PETFMM_EINVAL for
+ * bad arguments. */
+int petfmm_debug_m2l_images(int order, int kernel, int blocks, float *out, int64_t cap);
+
 /* Launch plan of a batch, built on the host without touching the device
  * (pointers in inst are not dereferenced).  Each task is written as five
  * int64 {range, instance, level, units, first block}; range 0 binning,

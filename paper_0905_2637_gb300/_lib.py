@@ -114,6 +114,7 @@ def load():
             "petfmm_debug_tree": (I, [P, P, P, P]),
             "petfmm_debug_expansions": (I, [P, I, I, P]),
             "petfmm_debug_interaction_list": (I, [I, I, I, P]),
+            "petfmm_debug_m2l_images": (I, [I, I, I, P, ctypes.c_int64]),
             "petfmm_debug_plan": (I, [I, I, ctypes.POINTER(Instance), P, I]),
             "petfmm_set_option": (I, [P, I, I64]),
             "petfmm_stage_times": (I, [P, P, I]),
@@ -167,6 +168,16 @@ def petfmm_choose_levels(n, order, sigma, domain):
     dom = Domain(*map(float, domain))
     return _ck(load().petfmm_choose_levels(int(n), int(order), float(sigma), ctypes.byref(dom)),
                "petfmm_choose_levels")
+
+
+def petfmm_debug_m2l_images(order, kernel=0, blocks=0):
+    """The tensor-core M2L operator images (float32 array; layout in petfmm.h)."""
+    n = _ck(load().petfmm_debug_m2l_images(int(order), int(kernel), int(blocks), None, 0),
+            "petfmm_debug_m2l_images")
+    out = np.zeros(n, np.float32)
+    _ck(load().petfmm_debug_m2l_images(int(order), int(kernel), int(blocks), out.ctypes.data, n),
+        "petfmm_debug_m2l_images")
+    return out
 
 
 def petfmm_debug_interaction_list(level, ix, iy):

@@ -1368,4 +1368,16 @@ int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out) {
     return n < 0 ? PETFMM_EINVAL : n;
 }
 
+int petfmm_debug_m2l_images(int order, int kernel, int blocks, float *out, int64_t cap) {
+    if (order < 1 || order > 24 || (kernel != KERNEL_VORTEX && kernel != KERNEL_LAPLACE) ||
+        blocks < 0 || blocks > 1 || cap < 0 || (cap > 0 && !out))
+        return PETFMM_EINVAL;
+    std::vector<float> img;
+    if (blocks) host_m2l_tcb_images(order, kernel, img);
+    else host_m2l_tc_images(order, kernel, img);
+    const int64_t n = int64_t(img.size());
+    if (out && cap >= n) std::memcpy(out, img.data(), size_t(n) * sizeof(float));
+    return int(n);
+}
+
 }  // extern "C"
