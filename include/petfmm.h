@@ -225,6 +225,22 @@ int petfmm_debug_expansions(petfmm_ctx *ctx, int level, int which, double *out);
  * returns the count, or PETFMM_EINVAL. */
 int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out);
 
+/* The FP64 translation operators of Sec. 2.2 for order p (1..40) and kernel,
+ * in the rescaled coefficients (box width r: ME a~_k = a_k / r^k; LE
+ * r^(m+1) b_m for the vortex kernel, r^m b_m for the Laplace kernel), as the
+ * host builds them for both precisions; host only, no GPU needed.  Complex
+ * entries as (re, im) pairs:
+ *   which = 0  M2M [c][l][k]: parent a~'_l += M[c][l][k] a~_k of child class c
+ *              (c = (ix & 1) | (iy & 1) << 1; the child's centre is
+ *              ((c & 1) - 1/2, (c >> 1) - 1/2) child widths from the parent's);
+ *   which = 1  L2L [c][n][m]: child c^'_n += L[c][n][m] c^_m of the parent;
+ *   which = 2  M2L [o][k][m]: target c^_m += T[o][k][m] a~_k for the source
+ *              at offset delta_o (box widths), o as in petfmm_debug_m2l_images.
+ * (For the Laplace kernel the M2L constant a_0 log r is added separately.)
+ * Returns the number of doubles; copies them to out when cap is at least
+ * that; PETFMM_EINVAL for bad arguments. */
+int petfmm_debug_op_table(int order, int kernel, int which, double *out, int64_t cap);
+
 /* Operator images of the tensor-core M2L (Sec. 2.2's M2L with the rescaled
  * coefficients: c^_m = sum_k T_delta[k][m] a~_k), as the host builds them
  * for order p (1..24) and kernel (PETFMM_KERNEL_VORTEX / _LAPLACE); host

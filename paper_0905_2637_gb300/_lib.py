@@ -115,6 +115,7 @@ def load():
             "petfmm_debug_expansions": (I, [P, I, I, P]),
             "petfmm_debug_interaction_list": (I, [I, I, I, P]),
             "petfmm_debug_m2l_images": (I, [I, I, I, P, ctypes.c_int64]),
+            "petfmm_debug_op_table": (I, [I, I, I, P, ctypes.c_int64]),
             "petfmm_debug_plan": (I, [I, I, ctypes.POINTER(Instance), P, I]),
             "petfmm_set_option": (I, [P, I, I64]),
             "petfmm_stage_times": (I, [P, P, I]),
@@ -168,6 +169,17 @@ def petfmm_choose_levels(n, order, sigma, domain):
     dom = Domain(*map(float, domain))
     return _ck(load().petfmm_choose_levels(int(n), int(order), float(sigma), ctypes.byref(dom)),
                "petfmm_choose_levels")
+
+
+def petfmm_debug_op_table(order, kernel=0, which=0):
+    """FP64 M2M (which 0), L2L (1) or M2L (2) operators as a complex array
+    [4 or 40][p][p] (layout in petfmm.h)."""
+    n = _ck(load().petfmm_debug_op_table(int(order), int(kernel), int(which), None, 0),
+            "petfmm_debug_op_table")
+    out = np.zeros(n, np.float64)
+    _ck(load().petfmm_debug_op_table(int(order), int(kernel), int(which), out.ctypes.data, n),
+        "petfmm_debug_op_table")
+    return out.view(np.complex128).reshape(-1, int(order), int(order))
 
 
 def petfmm_debug_m2l_images(order, kernel=0, blocks=0):

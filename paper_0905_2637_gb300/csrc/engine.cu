@@ -1368,6 +1368,17 @@ int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out) {
     return n < 0 ? PETFMM_EINVAL : n;
 }
 
+int petfmm_debug_op_table(int order, int kernel, int which, double *out, int64_t cap) {
+    if (order < 1 || order > MAX_P || (kernel != KERNEL_VORTEX && kernel != KERNEL_LAPLACE) ||
+        which < 0 || which > 2 || cap < 0 || (cap > 0 && !out))
+        return PETFMM_EINVAL;
+    std::vector<double> t;
+    host_op_table(order, kernel, which, t);
+    const int64_t n = int64_t(t.size());
+    if (out && cap >= n) std::memcpy(out, t.data(), size_t(n) * sizeof(double));
+    return int(n);
+}
+
 int petfmm_debug_m2l_images(int order, int kernel, int blocks, float *out, int64_t cap) {
     if (order < 1 || order > 24 || (kernel != KERNEL_VORTEX && kernel != KERNEL_LAPLACE) ||
         blocks < 0 || blocks > 1 || cap < 0 || (cap > 0 && !out))

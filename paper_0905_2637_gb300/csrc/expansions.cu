@@ -262,6 +262,14 @@ void host_lap_m2l_table(int p, double *out /* [op][k][m] */) {
         }
 }
 
+void host_op_table(int p, int kernel, int which, std::vector<double> &out) {
+    const bool lap = kernel == KERNEL_LAPLACE;
+    out.assign(size_t(which == 2 ? 40 : 4) * p * p * 2, 0.0);
+    if (which == 0) (lap ? host_lap_m2m_table : host_m2m_table)(p, out.data());
+    else if (which == 1) (lap ? host_lap_l2l_table : host_l2l_table)(p, out.data());
+    else (lap ? host_lap_m2l_table : host_m2l_table)(p, out.data());
+}
+
 cudaError_t build_op_tables(int p, int kernel, OpTables *t) {
     cudaError_t e = upload_il();
     if (e != cudaSuccess) return e;

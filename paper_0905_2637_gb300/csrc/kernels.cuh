@@ -58,6 +58,9 @@ struct OpTables {
     float *m2l_tcb = nullptr; // ... the four target classes side by side (block units)
 };
 cudaError_t build_op_tables(int p, int kernel, OpTables *out);
+// The FP64 table behind them: which = 0 M2M [c][l][k], 1 L2L [c][n][m],
+// 2 M2L [op][k][m], complex as (re, im) pairs.
+void host_op_table(int p, int kernel, int which, std::vector<double> &out);
 void free_op_tables(OpTables *t);
 void host_m2l_table(int p, double *out_re_im /* 40 * p * p * 2, [op][k][m] */);
 // Interaction list exactly as the kernels enumerate it; returns the count.

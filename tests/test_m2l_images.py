@@ -1,10 +1,12 @@
-"""The tensor-core M2L's operator images, built on the host (no GPU): hi + lo
-of every image reproduces the oracle's M2L operator (Sec. 2.2, with the
-rescaled coefficients at box width 1) for each of the 40 offsets, for both
-kernels; hi holds TF32 values (low 13 mantissa bits zero), lo the remainder,
-and the padding is zero.  The block images put each target class's operator
-in its own column block, bit for bit the per-offset image, and zeros where
-the class's offset is within one box."""
+"""The host-built translation operators (no GPU).  The FP64 M2M, L2L and M2L
+tables (Sec. 2.2, rescaled coefficients) that both precisions use equal the
+oracle's translations applied to unit coefficients, for both kernels and
+p = 1 .. 40.  The tensor-core M2L's images: hi + lo of every image
+reproduces the oracle's M2L operator for each of the 40 offsets; hi holds
+TF32 values (low 13 mantissa bits zero), lo the remainder, and the padding
+is zero.  The block images put each target class's operator in its own
+column block, bit for bit the per-offset image, and zeros where the class's
+offset is within one box."""
 import numpy as np
 import pytest
 
@@ -112,3 +114,42 @@ def test_bad_arguments(lib):
     for args in ((0, 0, 0), (25, 0, 0), (8, 2, 0), (8, 0, 2)):
         with pytest.raises(lib.PetfmmError):
             lib.petfmm_debug_m2l_images(*args)
+
+
+# ---- the FP64 operator tables behind both precisions ----------------------
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("p", [1, 4, 12, 17, 30, 40])
+def test_m2m_l2l_m2l_tables_match_the_oracle(lib, orc, p, kernel):
+    """Rescaled coefficients at child width 1 (parent width 2): M2M maps a
+    child's a~_k to its parent's a~'_l = a'_l / 2^l; L2L maps the parent's
+    scaled LE (unscaled b_m = 2^-(m+1) c^_m, Laplace 2^-m) to the child's;
+    M2L maps a~_k at offset delta to c^_m at box width 1."""
+    m2m = orc.lap_m2m if kernel else orc.m2m
+    m2l = orc.lap_m2l if kernel else orc.m2l
+    M = lib.petfmm_debug_op_table(p, kernel, 0)
+    L = lib.petfmm_debug_op_table(p, kernel, 1)
+    T = lib.petfmm_debug_op_table(p, kernel, 2)
+    assert M.shape == L.shape == (4, p, p) and T.shape == (40, p, p)
+    scale_le = 2.0 ** -(np.arange(p) + (0 if kernel else 1))
+    for c in range(4):
+        e = complex((c & 1) - 0.5, (c >> 1) - 0.5)
+        for k in range(p):
+            unit = np.zeros(p, complex)
+            unit[k] = 1.0
+            ref = m2m(unit, e, 0.0) / 2.0 ** np.arange(p)
+            assert np.allclose(M[c, :, k], ref, rtol=1e-12, atol=1e-300), ("M2M", c, k)
+            ref = orc.l2l(unit * scale_le, 0.0, e)
+            assert np.allclose(L[c, :, k], ref, rtol=1e-12, atol=1e-300), ("L2L", c, k)
+    for o, delta in enumerate(OFFSETS):
+        for k in range(p):
+            unit = np.zeros(p, complex)
+            unit[k] = 1.0
+            ref = m2l(unit, complex(*delta), 0.0)
+            assert np.allclose(T[o, k], ref, rtol=1e-12, atol=1e-300), ("M2L", delta, k)
+
+
+def test_op_table_bad_arguments(lib):
+    for args in ((0, 0, 0), (41, 0, 0), (8, 2, 0), (8, 0, 3)):
+        with pytest.raises(lib.PetfmmError):
+            lib.petfmm_debug_op_table(*args)
