@@ -225,6 +225,17 @@ int petfmm_debug_expansions(petfmm_ctx *ctx, int level, int which, double *out);
  * returns the count, or PETFMM_EINVAL. */
 int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out);
 
+/* The mixed path's near-field factor of Eq. 8, g(q) = (1 - e^-q) / q with
+ * q = kappa rho^2 (rho in leaf widths, kappa = w^2 / (2 sigma^2)), as the
+ * host fits it for blob size sigma, leaf width w and relative tolerance tol
+ * (PETFMM_OPT_NEAR_TOL x 1e-9); host only, no GPU needed.  out[0] = degree,
+ * out[1] = 1 if near pairs reach beyond the polynomial (the kernels then use
+ * (1 - e^-q) / q there), out[2] = kappa and out[3] = the largest rho^2 the
+ * polynomial covers, both as the kernels hold them (FP32), out[4 + k] = the
+ * FP32 coefficient of rho^(2k), k = 0..14 (zero above the degree).  Returns
+ * PETFMM_OK or PETFMM_EINVAL. */
+int petfmm_debug_near_fit(double sigma, double wleaf, double tol, double *out);
+
 /* The FP64 translation operators of Sec. 2.2 for order p (1..40) and kernel,
  * in the rescaled coefficients (box width r: ME a~_k = a_k / r^k; LE
  * r^(m+1) b_m for the vortex kernel, r^m b_m for the Laplace kernel), as the

@@ -116,6 +116,7 @@ def load():
             "petfmm_debug_interaction_list": (I, [I, I, I, P]),
             "petfmm_debug_m2l_images": (I, [I, I, I, P, ctypes.c_int64]),
             "petfmm_debug_op_table": (I, [I, I, I, P, ctypes.c_int64]),
+            "petfmm_debug_near_fit": (I, [ctypes.c_double, ctypes.c_double, ctypes.c_double, P]),
             "petfmm_debug_plan": (I, [I, I, ctypes.POINTER(Instance), P, I]),
             "petfmm_set_option": (I, [P, I, I64]),
             "petfmm_stage_times": (I, [P, P, I]),
@@ -169,6 +170,15 @@ def petfmm_choose_levels(n, order, sigma, domain):
     dom = Domain(*map(float, domain))
     return _ck(load().petfmm_choose_levels(int(n), int(order), float(sigma), ctypes.byref(dom)),
                "petfmm_choose_levels")
+
+
+def petfmm_debug_near_fit(sigma, wleaf, tol):
+    """The near-field polynomial fit: dict(deg, general, kappa, split_rho2, coef)."""
+    out = np.zeros(4 + 15, np.float64)
+    _ck(load().petfmm_debug_near_fit(float(sigma), float(wleaf), float(tol), out.ctypes.data),
+        "petfmm_debug_near_fit")
+    return dict(deg=int(out[0]), general=int(out[1]), kappa=float(out[2]),
+                split_rho2=float(out[3]), coef=out[4:].copy())
 
 
 def petfmm_debug_op_table(order, kernel=0, which=0):

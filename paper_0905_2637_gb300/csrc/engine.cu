@@ -1368,6 +1368,20 @@ int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out) {
     return n < 0 ? PETFMM_EINVAL : n;
 }
 
+int petfmm_debug_near_fit(double sigma, double wleaf, double tol, double *out) {
+    if (!(sigma > 0.0) || !(wleaf > 0.0) || !(tol > 0.0) || !out) return PETFMM_EINVAL;
+    InstDesc d{};
+    d.sigma = sigma;
+    d.wleaf = wleaf;
+    fill_p2p_constants(d, tol);
+    out[0] = d.deg;
+    out[1] = d.general;
+    out[2] = d.kappa;
+    out[3] = d.qsplit_rho2;
+    for (int k = 0; k <= POLY_MAX; ++k) out[4 + k] = d.poly[k];
+    return PETFMM_OK;
+}
+
 int petfmm_debug_op_table(int order, int kernel, int which, double *out, int64_t cap) {
     if (order < 1 || order > MAX_P || (kernel != KERNEL_VORTEX && kernel != KERNEL_LAPLACE) ||
         which < 0 || which > 2 || cap < 0 || (cap > 0 && !out))
