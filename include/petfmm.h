@@ -228,7 +228,8 @@ int petfmm_debug_interaction_list(int level, int ix, int iy, int32_t *out);
 /* The mixed path's near-field factor of Eq. 8, g(q) = (1 - e^-q) / q with
  * q = kappa rho^2 (rho in leaf widths, kappa = w^2 / (2 sigma^2)), as the
  * host fits it for blob size sigma, leaf width w and relative tolerance tol
- * (PETFMM_OPT_NEAR_TOL x 1e-9); host only, no GPU needed.  out[0] = degree,
+ * (the relative tolerance itself, e.g. 2.5e-6: the value that
+ * PETFMM_OPT_NEAR_TOL sets, times 1e-9); host only, no GPU needed.  out[0] = degree,
  * out[1] = 1 if near pairs reach beyond the polynomial (the kernels then use
  * (1 - e^-q) / q there), out[2] = kappa and out[3] = the largest rho^2 the
  * polynomial covers, both as the kernels hold them (FP32), out[4 + k] = the
@@ -275,7 +276,8 @@ int petfmm_debug_m2l_images(int order, int kernel, int blocks, float *out, int64
 
 /* Launch plan of a batch, built on the host without touching the device
  * (pointers in inst are not dereferenced).  Each task is written as five
- * int64 {range, instance, level, units, first block}; range 0 binning,
+ * int64 {range, instance, level, units, first block}; range 0 the scatter of
+ * staged FP32 outputs to the caller's order (1024 blobs per block),
  * 1 leaf starts, 2 gather, 3 P2M, 4 P2P work list, 5 M2L (SIMT, units =
  * target boxes), 6 M2L on the tensor cores (units = CTAs), 7 tiled SIMT M2L
  * (units = CTAs), 100 + r the r-th M2M launch, 200 + r the r-th L2L launch,
@@ -353,12 +355,14 @@ int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
 
 /* Stages reported by petfmm_stage_times (milliseconds, last evaluation).
  * PAIRS: the pairwise near-field kernel (mixed path, PETFMM_OPT_P2P_PAIRS = 1;
- * about zero otherwise); P2P: the directed near field and the final pass
- * (far field, sums, output). */
+ * about zero otherwise); P2P: the directed near field (and, on the FP64 path,
+ * L2P and the output in the same kernel); FINAL: the mixed path's final pass
+ * (L2P, the sum of the near-field parts, the output in the caller's order;
+ * about zero on the FP64 path). */
 enum {
     PETFMM_STAGE_MORTON = 0, PETFMM_STAGE_SORT, PETFMM_STAGE_GATHER, PETFMM_STAGE_P2M,
     PETFMM_STAGE_M2M, PETFMM_STAGE_M2L, PETFMM_STAGE_L2L, PETFMM_STAGE_WORKLIST,
-    PETFMM_STAGE_PAIRS, PETFMM_STAGE_P2P, PETFMM_STAGE_COUNT
+    PETFMM_STAGE_PAIRS, PETFMM_STAGE_P2P, PETFMM_STAGE_FINAL, PETFMM_STAGE_COUNT
 };
 int petfmm_stage_times(petfmm_ctx *ctx, float *ms, int cap);
 
@@ -375,6 +379,8 @@ typedef struct {
     int64_t p2p_sym_pairs;     /* pairwise mode: unordered blob pairs the pair kernel
                                   evaluated (each serves two of the ordered p2p_pairs) */
     float pairs_load_balance;  /* pairwise mode: min / max CTA busy time of the pair kernel */
+    int64_t occupied_leaves;   /* leaves holding at least one particle in the last
+                                  evaluation (all instances) */
 } petfmm_stats;
 /* Counters; p2p_pairs, m2l_pairs, p2p_items and the load balances need
  * PETFMM_OPT_TIMING and a petfmm_sync() after the evaluation. */
@@ -400,13 +406,20 @@ int petfmm_get_stats(petfmm_ctx *ctx, petfmm_stats *out);
  *   perm         device array: perm[r] = input index of sorted rank r.
  *   start        device array of 4^L + 1 leaf starts.
  * Runs on cuda_stream (a cudaStream_t, NULL for the legacy default stream)
- * and waits for it before returning; returns PETFMM_OK, PETFMM_EDOMAIN (a
- * particle outside the domain; outputs unspecified), PETFMM_EINVAL or
- * PETFMM_ECUDA.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call uses the same array, so calls
- * that overlap on the GPU (other streams or host threads) race with each
- * other; serialise them.
+ * and waits for it before returning (so it cannot be called while that
+ * stream is capturing).  Returns PETFMM_OK, PETFMM_EDOMAIN (a particle
+ * outside the domain or NaN; outputs unspecified; the next call is
+ * unaffected), PETFMM_EINVAL, PETFMM_ENOMEM (n above the maximum, or the
+ * device had no room for the static array when it was created) or
+ * PETFMM_ECUDA.  The first call in a CUDA context (for the primary context:
+ * the first call on a device) looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Lookups are cached per context ID, so a context
+ * made after cudaDeviceReset gets a fresh lookup.  The array is created when
+ * the library's device code is loaded onto the device (the first lookup,
+ * under lazy module loading).  Every call uses the same array, so calls that
+ * overlap on the GPU (other streams or host threads) race with each other;
+ * serialise them.  n = 0 writes start[] as all zeros.
  */
 #define PETFMM_NOALLOC_MAX_N 1048576
 int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dtype, int64_t n, const void *x,

@@ -26,7 +26,9 @@ PETFMM_OPT_TIMING, PETFMM_OPT_SPIN_LIMIT, PETFMM_OPT_P2P_MODE, PETFMM_OPT_POISON
 PETFMM_OPT_M2L_TC, PETFMM_OPT_TC_DENSE, PETFMM_OPT_TC_SEG, PETFMM_OPT_NEAR_TOL = 5, 6, 8, 9
 PETFMM_OPT_GRAPH, PETFMM_OPT_P2P_PAIRS, PETFMM_OPT_KERNEL, PETFMM_OPT_TC_BLOCKS = 10, 11, 12, 13
 PETFMM_KERNEL_VORTEX, PETFMM_KERNEL_LAPLACE = 0, 1
-STAGES = ("morton", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "worklist", "pairs", "p2p")
+PETFMM_NOALLOC_MAX_N = 1048576
+STAGES = ("morton", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "worklist", "pairs", "p2p",
+          "final")
 
 
 class Domain(ctypes.Structure):
@@ -58,7 +60,8 @@ class Stats(ctypes.Structure):
                 ("p2p_pairs", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64),
                 ("p2p_items", ctypes.c_int64), ("p2p_load_balance", ctypes.c_float),
                 ("p2p_pair_items", ctypes.c_int64), ("p2p_split_entries", ctypes.c_int64),
-                ("p2p_sym_pairs", ctypes.c_int64), ("pairs_load_balance", ctypes.c_float)]
+                ("p2p_sym_pairs", ctypes.c_int64), ("pairs_load_balance", ctypes.c_float),
+                ("occupied_leaves", ctypes.c_int64)]
 
 
 class PetfmmError(RuntimeError):
@@ -124,6 +127,7 @@ def load():
             "petfmm_strerror": (ctypes.c_char_p, [I]),
             "petfmm_version": (I, []),
             "petfmm_measure_peaks": (I, [ctypes.POINTER(Peaks)]),
+            "petfmm_tree_noalloc": (I, [ctypes.POINTER(Domain), I, I, I64, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -2,7 +2,7 @@
 //
 // One evaluation (Sec. 2.2, Fig. 2) is this sequence of launches on the
 // context's stream, every one of them covering all instances of the batch:
-//   morton -> radix sort (ceil(bits / 8) passes) -> leaf starts -> gather
+//   binning -> radix sort (ceil(bits / 8) passes) -> leaf starts -> gather
 //   -> P2M -> M2M (one launch per level, bottom-up) -> M2L (all levels in one
 //   launch) -> L2L (one launch per level, top-down) -> P2P work list
 //   -> P2P + L2P.
@@ -69,7 +69,7 @@ struct TaskRange {
 struct Plan {
     std::vector<InstDesc> inst;
     std::vector<Task> tasks;
-    TaskRange morton, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tcb, m2l_log;
+    TaskRange outscatter, start, particles, leaves_p2m, leaves_wl, m2l, m2l_tc, m2l_tcb, m2l_log;
     // tiled SIMT M2L, one launch per order class (p <= 8, 12, 18, 24): each
     // launch's kernel is specialised for its class's largest order
     static constexpr int kTileClasses = 4;
@@ -339,7 +339,7 @@ void flatten_tasks(Plan &pl) {
         r.first = int(pl.tasks.size());
         pl.tasks.insert(pl.tasks.end(), r.list.begin(), r.list.end());
     };
-    put(pl.morton);
+    put(pl.outscatter);
     put(pl.start);
     put(pl.particles);
     put(pl.leaves_p2m);
@@ -422,7 +422,7 @@ int build_plan(int precision, int kernel, bool use_tc, int tc_blocks, int tc_seg
         d.tc_segmax = tc_segmax;
         d.tc_levels = 0;
         d.tcb_levels = 0;
-        add_task(pl.morton, i, d.L, d.n, 256);
+        add_task(pl.outscatter, i, d.L, d.n, 1024);  // output scatter: 4 blobs per thread
         add_task(pl.start, i, d.L, nleaf + 1, 256);
         add_task(pl.particles, i, d.L, d.n, 256);
         add_task(pl.leaves_p2m, i, d.L, nleaf, 256);
@@ -588,7 +588,7 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     KeyHash k;
     if (!pl.tasks.empty()) k.add(pl.tasks.data(), pl.tasks.size() * sizeof(Task));
     auto range = [&](const TaskRange &r) { k.put(r.first); k.put(r.count); k.put(r.nblocks); };
-    for (const TaskRange *r : {&pl.morton, &pl.start, &pl.particles, &pl.leaves_p2m, &pl.leaves_wl,
+    for (const TaskRange *r : {&pl.outscatter, &pl.start, &pl.particles, &pl.leaves_p2m, &pl.leaves_wl,
                                &pl.m2l, &pl.m2l_tc, &pl.m2l_tcb, &pl.m2l_log})
         range(*r);
     for (const TaskRange &r : pl.m2l_tile) range(r);
@@ -762,9 +762,11 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_CUDA(cudaMemsetAsync(ctrl + 1, 0, (CTRL_WORDS - 1) * 4, st));
 
     stage_mark(c, PETFMM_STAGE_MORTON);
-    PF_CUDA(launch_morton(dtask + pl.morton.first, pl.morton.count, pl.morton.nblocks, dinst, f32, kA,
-                          mixed ? static_cast<float4 *>(c->recu.p) : nullptr,
-                          reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
+    float4 *recu = mixed ? static_cast<float4 *>(c->recu.p) : nullptr;
+    const float4 *srec = mixed ? static_cast<const float4 *>(c->rec.p) : nullptr;  // sorted
+    PF_CUDA(launch_morton(dtask + pl.particles.first, pl.particles.count, pl.particles.nblocks,
+                          dinst, f32, kA, recu, reinterpret_cast<int *>(ctrl + CTRL_STATUS), st,
+                          lc));
     stage_mark(c, PETFMM_STAGE_SORT);
     bool in_first = true;
     PF_CUDA(radix_sort(kA, vA, kB, vB, N, pl.nbits, static_cast<uint32_t *>(c->hist.p), scratch,
@@ -776,8 +778,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                               start, st, lc));
     stage_mark(c, PETFMM_STAGE_GATHER);
     if (mixed)
-        PF_CUDA(launch_gather_mixed(static_cast<const float4 *>(c->recu.p), perm,
-                                    static_cast<float4 *>(c->rec.p), N, st, lc));
+        PF_CUDA(launch_gather_mixed(recu, perm, static_cast<float4 *>(c->rec.p), N, st, lc));
     else
         PF_CUDA(launch_gather_f64(dtask + pl.particles.first, pl.particles.count,
                                   pl.particles.nblocks, dinst, f32, perm,
@@ -789,7 +790,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                             dinst, start, occ, ctrl, st, lc));
     if (mixed)
         PF_CUDA(launch_p2m<float>(occ, ctrl, pl.nleaves, dinst, pl.pmax, start, nullptr, nullptr,
-                                  nullptr, static_cast<const float4 *>(c->rec.p),
+                                  nullptr, srec,
                                   static_cast<float2 *>(c->me.p), st, lc));
     else
         PF_CUDA(launch_p2m<double>(occ, ctrl, pl.nleaves, dinst, pl.pmax, start,
@@ -905,26 +906,28 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     // pairwise mode: the neighbouring leaves pairwise
     if (pairs)
         PF_CUDA(launch_p2p_pairs(pgrid, pl.deg, pl.general, static_cast<const uint4 *>(c->pitems.p),
-                                 ctrl, dinst, start, static_cast<const float4 *>(c->rec.p), pb,
+                                 ctrl, dinst, start, srec, pb,
                                  pbusy, st, lc));
     stage_mark(c, PETFMM_STAGE_P2P);
     if (mixed) {
         // near sums of the own leaf and the directed neighbours, then far
         // field and the sum
         PF_CUDA(launch_p2p_mixed(grid, pl.deg, pl.general, static_cast<const uint4 *>(c->items.p),
-                                 ctrl, dinst, start, static_cast<const float4 *>(c->rec.p), pb.own,
+                                 ctrl, dinst, start, srec, pb.own,
                                  pairs, lap ? 1 : 0, busy, st, lc));
+        stage_mark(c, PETFMM_STAGE_FINAL);
         PF_CUDA(launch_p2p_final(dtask + pl.particles.first, pl.particles.count,
-                                 pl.particles.nblocks, dinst, start, skeys,
-                                 static_cast<const float4 *>(c->rec.p),
-                                 static_cast<const float2 *>(c->le.p), pb, f32, perm, stage, N, st,
-                                 lc));
+                                 pl.particles.nblocks, dinst, start, skeys, srec,
+                                 static_cast<const float2 *>(c->le.p), pb, f32, perm, stage, N,
+                                 dtask + pl.outscatter.first, pl.outscatter.count,
+                                 pl.outscatter.nblocks, ctrl, N, st, lc));
     } else
         PF_CUDA(launch_p2p_f64(grid, static_cast<const uint4 *>(c->items.p), ctrl, dinst, start,
                                static_cast<const double *>(c->xs.p),
                                static_cast<const double *>(c->ys.p),
                                static_cast<const double *>(c->gs.p), perm,
                                static_cast<const double2 *>(c->le.p), f32, busy, st, lc));
+    if (!mixed) stage_mark(c, PETFMM_STAGE_FINAL);
     stage_mark(c, PETFMM_STAGE_COUNT);
     return PETFMM_OK;
     };
@@ -1165,7 +1168,7 @@ int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, in
             ++n;
         }
     };
-    emit(0, pl.morton);
+    emit(0, pl.outscatter);
     emit(1, pl.start);
     emit(2, pl.particles);
     emit(3, pl.leaves_p2m);
@@ -1262,6 +1265,7 @@ int petfmm_get_stats(petfmm_ctx *c, petfmm_stats *out) {
         uint32_t w[CTRL_WORDS];
         if (cudaMemcpy(w, c->ctrl.p, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return PETFMM_ECUDA;
         out->p2p_items = w[CTRL_NITEMS];
+        out->occupied_leaves = w[CTRL_NOCC];
         unsigned long long pairs;
         std::memcpy(&pairs, w + CTRL_PAIRS_LO, sizeof(pairs));
         out->p2p_pairs = int64_t(pairs);

@@ -457,17 +457,28 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m_reg(
         float2 acc[PM];
 #pragma unroll
         for (int k = 0; k < PM; ++k) acc[k] = make_float2(0.f, 0.f);
-        for (uint32_t c0 = s0; c0 < s1; c0 += 32) {
-            const uint32_t j = c0 + lane;
-            const float4 r = j < s1 ? rec[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 w = make_float2(r.z, 0.f);
-            const float2 z = make_float2(r.x, r.y);
+        // two blobs per lane per step (two independent power chains), and the
+        // next step's two records requested before this step's arithmetic:
+        // up to four 16-byte loads in flight per lane
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 na = s0 + lane < s1 ? rec[s0 + lane] : z4;
+        float4 nb = s0 + 32 + lane < s1 ? rec[s0 + 32 + lane] : z4;
+        for (uint32_t c0 = s0; c0 < s1; c0 += 64) {
+            const float4 ra = na, rb = nb;
+            const uint32_t jn = c0 + 64 + lane;
+            na = jn < s1 ? rec[jn] : z4;
+            nb = jn + 32 < s1 ? rec[jn + 32] : z4;
+            float2 wa = make_float2(ra.z, 0.f), wb = make_float2(rb.z, 0.f);
+            const float2 za = make_float2(ra.x, ra.y), zb = make_float2(rb.x, rb.y);
 #pragma unroll
             for (int k = 0; k < PM; ++k) {
                 if (k < p) {
-                    acc[k].x += w.x;
-                    acc[k].y += w.y;
-                    w = cmul(w, z);
+                    acc[k].x += wa.x;
+                    acc[k].y += wa.y;
+                    acc[k].x += wb.x;
+                    acc[k].y += wb.y;
+                    wa = cmul(wa, za);
+                    wb = cmul(wb, zb);
                 }
             }
         }

@@ -227,10 +227,13 @@ cudaError_t launch_p2p_final(const Task *tasks, int ntasks, int64_t nblocks,
                              const InstDesc *insts, const uint32_t *start, const uint32_t *skeys,
                              const float4 *rec, const float2 *le, const PairBufs &pb,
                              int dtype_f32, const uint32_t *perm, float *stage, int64_t nstage,
-                             cudaStream_t st, uint64_t *launches);
+                             const Task *utasks, int nutasks, int64_t unblocks,
+                             const uint32_t *ctrl, int64_t ntotal, cudaStream_t st,
+                             uint64_t *launches);
 // (stage != nullptr, FP32 outputs: the pass writes u, v in sorted order to
 // stage[0 .. nstage) and stage[nstage ..), then one launch per component
-// scatters them to the caller's arrays through perm.)
+// scatters them to the caller's arrays through perm; utasks: the blobs of
+// every instance, 1024 per block.)
 int p2p_grid(int precision_mixed, int deg, int general, int laplace);
 int device_sm_count();
 constexpr int P2P_TPI_F64 = 32;

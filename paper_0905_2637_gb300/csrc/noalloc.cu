@@ -15,9 +15,17 @@
 // call's contents, calls that overlap on the GPU (different streams, or
 // different host threads) race on it, and each call clears the words that
 // must start at zero.  Host code cannot use the array's name as a device
-// address; its address is fetched once per device with
-// cudaGetSymbolAddress, with that device current, during the first call on
-// that device, so that first call should come before any stream capture.
+// address; its address is fetched with cudaGetSymbolAddress, with the device
+// current, during the first call in each CUDA context (for the usual primary
+// context: once per device), so that first call should come before any
+// stream capture.  The cache is keyed by the context's unique ID, so a
+// context made after cudaDeviceReset (or a non-primary context) gets its own
+// lookup instead of a stale address.  The array itself is created when this
+// file's device code is loaded onto the device: at the first lookup under
+// lazy module loading (the CUDA default), else when the context is created;
+// if the device has no room for it then, the call returns PETFMM_ENOMEM.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -41,25 +49,77 @@ constexpr int64_t kScratchBytes = 4 * (4 * kMaxN + kHistWords + kScanWords + 16)
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
-void *g_addr[64] = {};  // per device: device address of g_noalloc_scratch
+
+// Driver entry points for the current context and its unique ID, fetched
+// through the runtime (no link-time dependency on the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+struct AddrEntry {
+    unsigned long long ctx_id = 0;  // 0: unused slot
+    void *addr = nullptr;
+};
+AddrEntry g_addr[64];  // per CUDA context: device address of g_noalloc_scratch
+int g_next = 0;        // slot to overwrite when all 64 are taken
+
+int map_lookup_error(cudaError_t e) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? PETFMM_ENOMEM : PETFMM_ECUDA;
+}
 
 int scratch_address(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return PETFMM_ECUDA;
-    }
-    if (dev < 0 || dev >= 64) return PETFMM_ECUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaError_t e = cudaSuccess;
+    if (!g_ctx_current || !g_ctx_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                             &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
             cudaGetLastError();
             return PETFMM_ECUDA;
         }
-        g_addr[dev] = p;
+        g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
     }
-    *out = g_addr[dev];
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS) return PETFMM_ECUDA;
+    if (!ctx) {
+        // no context on this thread yet: the runtime's first call makes the
+        // current device's primary context current
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return map_lookup_error(e);
+        if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return PETFMM_ECUDA;
+    }
+    unsigned long long id = 0;
+    if (g_ctx_id(ctx, &id) != CUDA_SUCCESS || id == 0) return PETFMM_ECUDA;
+    for (const AddrEntry &a : g_addr)
+        if (a.ctx_id == id) {
+            *out = a.addr;
+            return PETFMM_OK;
+        }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return map_lookup_error(e);
+    if (!p) return PETFMM_ECUDA;
+    AddrEntry *slot = nullptr;
+    for (AddrEntry &a : g_addr)
+        if (a.ctx_id == 0) {
+            slot = &a;
+            break;
+        }
+    if (!slot) {
+        slot = &g_addr[g_next];
+        g_next = (g_next + 1) % 64;
+    }
+    slot->ctx_id = id;
+    slot->addr = p;
+    *out = p;
     return PETFMM_OK;
 }
 

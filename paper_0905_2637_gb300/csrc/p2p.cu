@@ -1078,11 +1078,16 @@ __global__ void __launch_bounds__(P2P_THREADS, 3) k_p2p_pairs(
 // summed near part, plus (pairwise mode, pb.part != nullptr) the slots of its
 // pairwise neighbours, a split pair's scratch runs after its slot in piece
 // order; a fixed order throughout, written at the caller's index.
-__global__ void __launch_bounds__(256) k_p2p_final(
+// blobs per occupied leaf from which the final pass requests every pair
+// slot of a blob up front (see k_p2p_final)
+constexpr int64_t kEagerBlobsPerLeaf = 48;
+
+__global__ void __launch_bounds__(256, 4) k_p2p_final(
     const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const uint32_t *__restrict__ skeys,
     const float4 *__restrict__ rec, const float2 *__restrict__ le, const PairBufs pb,
-    int dtype_f32, float *__restrict__ stage, int64_t nstage) {
+    int dtype_f32, float *__restrict__ stage, int64_t nstage, const uint32_t *__restrict__ ctrl,
+    int64_t ntotal) {
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
     const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
@@ -1091,6 +1096,22 @@ __global__ void __launch_bounds__(256) k_p2p_final(
     const int64_t r = d.poff + j;
     const uint32_t *st = start + d.soff;
     const int nside = 1 << d.L;
+    // Where the occupied leaves hold many blobs on average (pair slots
+    // nearly everywhere), this blob's near-field parts are requested at once,
+    // with its key and record, instead of after its leaf's flags: one latency
+    // instead of three on the way to the sum.  The flags still decide which
+    // of them are added, in the same order.
+    const bool eager = pb.part && int64_t(ntotal) >= kEagerBlobsPerLeaf * int64_t(ctrl[CTRL_NOCC]);
+    float2 e_own = make_float2(0.f, 0.f), e_self = e_own, e_fwd[4], e_bwd[4];
+    if (eager) {
+        e_own = pb.own[r];
+        e_self = pb.part[8 * pb.nslot + r];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            e_fwd[k] = pb.part[int64_t(k) * pb.nslot + r];
+            e_bwd[k] = pb.part[int64_t(4 + k) * pb.nslot + r];
+        }
+    }
     const uint32_t m = skeys[r] & ((d.L >= 16) ? 0xffffffffu : ((1u << (2 * d.L)) - 1u));
     const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
     const float4 rr = rec[r];
@@ -1113,23 +1134,24 @@ __global__ void __launch_bounds__(256) k_p2p_final(
     // then the near-field parts this leaf has, in a fixed order
     const uint32_t fl = pb.part ? pb.lflags[d.loff + m] : LF_DIRECTED;
     if (fl & LF_DIRECTED) {
-        const float2 o = pb.own[r];
+        const float2 o = eager ? e_own : pb.own[r];
         w.x += o.x;
         w.y += o.y;
     }
     if (fl & LF_SELF) {
-        const float2 sp = pb.part[8 * pb.nslot + r];
+        const float2 sp = eager ? e_self : pb.part[8 * pb.nslot + r];
         w.x += sp.x;
         w.y += sp.y;
     }
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (fl & (LF_FWD << k)) {
-            const float2 p = pb.part[int64_t(k) * pb.nslot + r];
+            const float2 p = eager ? e_fwd[k] : pb.part[int64_t(k) * pb.nslot + r];
             w.x += p.x;
             w.y += p.y;
         }
         if (!(fl & (LF_BWD << k))) continue;
-        const float2 p = pb.part[int64_t(4 + k) * pb.nslot + r];
+        const float2 p = eager ? e_bwd[k] : pb.part[int64_t(4 + k) * pb.nslot + r];
         w.x += p.x;
         w.y += p.y;
         if (fl & (LF_SPLIT << k)) {
@@ -1304,30 +1326,44 @@ __global__ void __launch_bounds__(256) k_unsort_f32(const Task *__restrict__ tas
                                                     const InstDesc *__restrict__ insts,
                                                     const uint32_t *__restrict__ perm,
                                                     const float *__restrict__ stage, int comp) {
+    // four consecutive sorted ranks per thread (tasks of 1024 per block):
+    // four independent scattered stores after two 16-byte loads
     const int ti = find_task(tasks, ntasks, blockIdx.x);
     const Task t = tasks[ti];
-    const int64_t j = (int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x;
-    if (j >= t.count) return;
+    const int64_t j0 = ((int64_t(blockIdx.x) - t.block0) * blockDim.x + threadIdx.x) * 4;
+    if (j0 >= t.count) return;
     const InstDesc &d = insts[t.inst];
-    const int64_t r = d.poff + j;
+    const int64_t r0 = d.poff + j0;
     float *out = static_cast<float *>(comp ? d.v : d.u);
-    out[int64_t(perm[r]) - d.poff] = stage[r];
+    if (j0 + 4 <= t.count && (r0 & 3) == 0) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(perm + r0);
+        const float4 w = *reinterpret_cast<const float4 *>(stage + r0);
+        out[int64_t(q.x) - d.poff] = w.x;
+        out[int64_t(q.y) - d.poff] = w.y;
+        out[int64_t(q.z) - d.poff] = w.z;
+        out[int64_t(q.w) - d.poff] = w.w;
+    } else {
+        for (int e = 0; e < 4; ++e)
+            if (j0 + e < t.count) out[int64_t(perm[r0 + e]) - d.poff] = stage[r0 + e];
+    }
 }
 
 cudaError_t launch_p2p_final(const Task *tasks, int ntasks, int64_t nblocks,
                              const InstDesc *insts, const uint32_t *start, const uint32_t *skeys,
                              const float4 *rec, const float2 *le, const PairBufs &pb,
                              int dtype_f32, const uint32_t *perm, float *stage, int64_t nstage,
-                             cudaStream_t st, uint64_t *launches) {
+                             const Task *utasks, int nutasks, int64_t unblocks,
+                             const uint32_t *ctrl, int64_t ntotal, cudaStream_t st,
+                             uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
     k_p2p_final<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, start, skeys, rec, le, pb,
-                                                   dtype_f32, stage, nstage);
+                                                   dtype_f32, stage, nstage, ctrl, ntotal);
     PF_LAUNCHED(1);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !stage) return e;
+    if (e != cudaSuccess || !stage || unblocks <= 0) return e;
     for (int comp = 0; comp < 2; ++comp) {
-        k_unsort_f32<<<unsigned(nblocks), 256, 0, st>>>(tasks, ntasks, insts, perm,
-                                                        stage + comp * nstage, comp);
+        k_unsort_f32<<<unsigned(unblocks), 256, 0, st>>>(utasks, nutasks, insts, perm,
+                                                         stage + comp * nstage, comp);
         PF_LAUNCHED(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

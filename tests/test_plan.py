@@ -17,7 +17,7 @@ def lib():
     return _lib
 
 
-UNITS_PER_BLOCK = {0: 256, 1: 256, 2: 256, 3: 256, 4: 256, 5: 32, 6: 1, 7: 1, 70: 1, 71: 1, 72: 1,
+UNITS_PER_BLOCK = {0: 1024, 1: 256, 2: 256, 3: 256, 4: 256, 5: 32, 6: 1, 7: 1, 70: 1, 71: 1, 72: 1,
                    73: 1}
 
 
