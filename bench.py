@@ -249,14 +249,17 @@ def cpu_baseline():
                       f"p={w.p}, same recipe and blobs per leaf; {dt:.1f} s wall"}
 
 
-def serving_leg(_lib, n_req=48, seed=5):
+def serving_leg(_lib, n_req=2000, seed=5, pool=96):
     """Poisson arrivals (mean 200/s) of requests of 5 midpoint-RK2 steps
     (10 evaluations) each, N log-uniform in [4e3, 4e6], Gaussian-patch
     lattice or clustered layout, p in {8, 17}, mixed precision, admitted under
-    a 150 GB HBM budget.  Returns latency percentiles and throughput."""
+    a 150 GB HBM budget.  The request bodies come from a seeded pool of
+    `pool` systems (each request draws one), so the host holds the pool
+    rather than n_req systems.  Returns latency percentiles, throughput and
+    the queue over time."""
     rng = np.random.default_rng(seed)
-    reqs = []
-    for i in range(n_req):
+    bodies = []
+    for i in range(pool):
         n = int(np.exp(rng.uniform(np.log(4e3), np.log(4e6))))
         p = int(rng.choice([8, 17]))
         if rng.uniform() < 0.5:
@@ -269,40 +272,80 @@ def serving_leg(_lib, n_req=48, seed=5):
         x, y, g = w.as_f64()
         # the configured tree depth: about 16 blobs per leaf, as at the
         # lattice and clustered configurations
-        levels = int(min(12, max(2, round(np.log(max(n, 16) / 16.0) / np.log(4.0)))))
-        reqs.append((x, y, g, w.sigma, p, dt, levels))
+        levels = int(min(12, max(2, round(np.log(max(x.size, 16) / 16.0) / np.log(4.0)))))
+        bodies.append((x, y, g, w.sigma, p, dt, levels))
+    pick = rng.integers(0, pool, n_req)
     gaps = rng.exponential(1.0 / 200.0, n_req)
-    srv = _lib.Server(150 * (1 << 30), max_slots=64, max_queue=4096)
+    srv = _lib.Server(150 * (1 << 30), max_slots=64, max_queue=n_req)
     t0 = time.perf_counter()
-    tickets = []
-    due = 0.0
-    for (x, y, g, s, p, dt, levels), gap in zip(reqs, gaps):
+    tickets, done, pending = [], {}, []
+    due, last_drain = 0.0, 0.0
+
+    def drain():
+        # oldest first: stop at the first unfinished one (rounds run requests
+        # in admission order, so later ones are rarely done before it)
+        keep = []
+        for t in pending:
+            r = srv.poll(t, positions=False) if not keep else None
+            if r is not None:
+                done[t] = r
+            else:
+                keep.append(t)
+        pending[:] = keep
+
+    for k, gap in zip(pick, gaps):
         due += gap
         now = time.perf_counter() - t0
         if due > now:
-            time.sleep(due - now)
-        tickets.append(srv.submit(x, y, g, s, p, dt, 5, levels=levels, precision="mixed"))
-    done = {}
-    while len(done) < len(tickets):
-        for t in tickets:
-            if t not in done:
-                r = srv.poll(t)
-                if r is not None:
-                    done[t] = r
-        time.sleep(0.0005)
+            if now - last_drain > 0.05:  # results are released as they finish
+                drain()
+                last_drain = time.perf_counter() - t0
+            now = time.perf_counter() - t0
+            if due > now:
+                time.sleep(due - now)
+        x, y, g, sg, p, dt, levels = bodies[int(k)]
+        t = srv.submit(x, y, g, sg, p, dt, 5, levels=levels, precision="mixed")
+        tickets.append(t)
+        pending.append(t)
+    while pending:
+        drain()
+        if pending:
+            # the first unfinished one: wait for it, then sweep the rest
+            r = None
+            while r is None:
+                r = srv.poll(pending[0], positions=False)
+                if r is None:
+                    time.sleep(0.002)
+            done[pending.pop(0)] = r
     makespan = time.perf_counter() - t0
+    st = srv.stats()
+    tt, tq, ta = srv.trace()
     srv.close()
     lat = np.array([done[t]["latency_ms"] for t in tickets])
+    qms = np.array([done[t]["queue_ms"] for t in tickets])
+    shared = np.array([done[t]["max_shared"] for t in tickets])
     ok = sum(done[t]["status"] == 0 for t in tickets)
-    evals = sum(r[0].size for r in reqs) * 10
+    evals = sum(bodies[int(k)][0].size for k in pick) * 10
+    # the queue over time: one sample per second of the run (the round in
+    # progress at that moment)
+    series = []
+    for sec in range(int(np.ceil(makespan))):
+        i = int(np.searchsorted(tt, 1e3 * sec, side="right")) - 1
+        if i >= 0:
+            series.append([sec, int(tq[i]), int(ta[i])])
     return {"requests": n_req, "ok": int(ok), "arrival_rate_per_s": 200.0,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "makespan_s": makespan,
+            "mean_ms": float(lat.mean()), "queue_p50_ms": float(np.percentile(qms, 50)),
+            "queue_p99_ms": float(np.percentile(qms, 99)), "makespan_s": makespan,
             "particles_per_s": evals / makespan,
             "offered_particle_evals_per_s": evals / max(float(np.sum(gaps)), 1e-9),
-            "layout": "Gaussian-patch lattice or 8-cluster, N log-uniform [4e3, 4e6], p in {8, 17}, "
-                      "L = round(log4(N / 16)), "
-                      "5 midpoint-RK2 steps, 150 GB budget"}
+            "rounds": int(st["rounds"]), "max_resident": int(st["max_active"]),
+            "mean_resident": float(st["mean_active"]), "gpu_busy_frac": st["busy_ms"] / st["up_ms"],
+            "requests_batched_with_others": int((shared >= 2).sum()),
+            "queue_series": {"columns": ["second", "queued", "resident"], "rows": series},
+            "layout": f"pool of {pool} seeded systems (Gaussian-patch lattice or 8-cluster, N "
+                      "log-uniform [4e3, 4e6], p in {8, 17}), each request one of them; "
+                      "L = round(log4(N / 16)), 5 midpoint-RK2 steps, 150 GB budget, 64 slots"}
 
 
 def laplace_leg(_lib, torch, stream, steps=5):
@@ -361,10 +404,15 @@ def laplace_leg(_lib, torch, stream, steps=5):
             "data": "synthetic: x, y ~ U(0,1), q ~ U(-1,1), seed 1, fp32 storage"}
 
 
-def batch_leg(_lib, torch, stream, steps=5):
+def batch_leg(_lib, torch, stream, steps=5, n_err=64):
     """512 independent instances (N log-uniform in [1e3, 2^18], uniform, sigma =
-    0.5/sqrt(N), p in {8, 12, 17}) in one batched evaluation; L chosen by the
-    work model."""
+    0.5/sqrt(N), p in {8, 12, 17}) in one batched evaluation.  The autotuner
+    (petfmm_tune_batch, seeded by the work model) picks L per (p, N-bucket)
+    class and the M2L shape first (untimed); then the batch is timed.  The
+    per-instance error is the mixed batch against the FP64 GPU FMM at the same
+    L (itself within 1e-12 of the oracle FMM in the tests), on a seeded subset
+    of n_err instances."""
+    from paper_0905_2637_gb300 import tuning
     ws = W.batch(n_inst=512, seed=1, dtype="f32")
     ctx = _lib.Context((0, 0, 1), 2, 8, 0.01, precision="mixed", dtype="f32", stream=stream)
     ctx.set_option(_lib.PETFMM_OPT_GRAPH, 1)  # one graph launch per batch after the first
@@ -375,6 +423,11 @@ def batch_leg(_lib, torch, stream, steps=5):
             insts.append(dict(domain=w.domain, levels=0, order=w.p, sigma=w.sigma, x=x, y=y, gamma=g,
                               u=torch.empty_like(x), v=torch.empty_like(x)))
     torch.cuda.synchronize()
+    t_tune = time.perf_counter()
+    rules, rep = ctx.tune_batch(insts, reps=3)
+    t_tune = time.perf_counter() - t_tune
+    model = {tuning.class_key(w.p, w.n): _lib.petfmm_choose_levels(w.n, w.p, w.sigma, w.domain)
+             for w in ws if w.n > 0}
     for _ in range(2):
         ctx.evaluate_batch(insts)
     ctx.sync()
@@ -386,9 +439,44 @@ def batch_leg(_lib, torch, stream, steps=5):
     ctx.sync()
     t = e0.elapsed_time(e1) / 1e3 / steps
     ctx.close()
+    # per-instance error: FP64 GPU FMM of a seeded subset at the tuned L
+    rng = np.random.default_rng(7)
+    sub = sorted(int(i) for i in rng.choice(512, n_err, replace=False))
+    ctx64 = _lib.Context((0, 0, 1), 2, 8, 0.01, precision="fp64", dtype="f32", stream=stream)
+    ref = []
+    with torch.cuda.stream(stream):
+        for i in sub:
+            it = dict(insts[i])
+            it["levels"] = _lib.petfmm_rule_levels(rules, ws[i].n, ws[i].p, ws[i].sigma, ws[i].domain)
+            it["u"], it["v"] = torch.empty_like(it["x"]), torch.empty_like(it["x"])
+            ref.append(it)
+    ctx64.evaluate_batch(ref)
+    ctx64.sync()
+    ctx64.close()
+    errs = []
+    for i, r in zip(sub, ref):
+        du = insts[i]["u"].double() - r["u"].double()
+        dv = insts[i]["v"].double() - r["v"].double()
+        den = float((r["u"].double() ** 2 + r["v"].double() ** 2).sum())
+        errs.append(float(torch.sqrt((du * du + dv * dv).sum() / den)) if den > 0 else 0.0)
     n = sum(w.n for w in ws)
+    summ = tuning.summarize(rules, model)
     return {"instances": 512, "particles": n, "ms_per_batch": 1e3 * t, "instances_per_s": 512 / t,
-            "particles_per_s": n / t}
+            "particles_per_s": n / t,
+            "tuning": {"classes": summ["classes"], "changed_vs_model": summ["changed_vs_model"],
+                       "levels_used": summ["levels"], "tc_blocks": rep["tc_blocks"],
+                       "tc_dense_pct": rep["tc_dense_pct"], "ms_model": rep["ms_model"],
+                       "ms_tuned": rep["ms_tuned"], "evaluations": rep["evaluations"],
+                       "tune_s": t_tune,
+                       "note": "petfmm_tune_batch: per (p, floor(log2 N)) class L_model-1..+1 "
+                               "timed as a sub-batch, then TC_BLOCKS x TC_DENSE on the whole "
+                               "batch; medians of 3 CUDA-event timings"},
+            "per_instance_rel_l2_vs_fp64": {
+                "instances": n_err, "max": max(errs), "median": float(np.median(errs)),
+                "p90": float(np.percentile(errs, 90)), "bar": GATE_REL_L2,
+                "pass": bool(max(errs) <= GATE_REL_L2),
+                "note": "mixed batch vs FP64 GPU FMM batch at the same tuned L, every target "
+                        "of a seeded subset of instances"}}
 
 
 def main():

@@ -124,9 +124,10 @@ int petfmm_destroy(petfmm_ctx *ctx);
  * Batched evaluation: many independent FMM problems of uneven size in one
  * pass of batched kernels (every stage launches once for all instances, or
  * once per tree level).
- *   levels <= 0 asks the library to choose L from the work model of Sec. 5.2
- *   (Eq. 14), under the kernel-substitution guard exp(-r_L^2 / 2 sigma^2) <=
- *   1e-8 for the leaf width r_L.
+ *   levels <= 0 asks the library to choose L: a level rule installed in the
+ *   context (petfmm_set_level_rules, petfmm_tune_batch) if one matches, else
+ *   the work model of Sec. 5.2 (Eq. 14), always under the kernel-substitution
+ *   guard exp(-r_L^2 / 2 sigma^2) <= 1e-8 for the leaf width r_L.
  * The context supplies precision, storage type, stream and workspace; its own
  * domain, L, p, sigma are not used.  Arrays are device pointers; the call is
  * asynchronous like petfmm_evaluate().  Each instance's result is bit-for-bit
@@ -154,6 +155,76 @@ int petfmm_evaluate_batch(petfmm_ctx *ctx, int n_inst, const petfmm_instance *in
  * Returns L >= 1, or PETFMM_EINVAL.
  */
 int petfmm_choose_levels(int64_t n, int order, double sigma, const petfmm_domain *dom);
+
+/* ---------------------------------------------------------------------- */
+/* Autotuning of batches (tree depth and M2L shape, seeded by Sec. 5.2).   */
+/* ---------------------------------------------------------------------- */
+/*
+ * A level rule: instances of this order whose particle count n has
+ * floor(log2 n) == log2n get `levels` as their automatic tree depth (levels
+ * <= 0 in petfmm_evaluate_batch) instead of the work model's.  With a
+ * uniform quadtree the depth also fixes the leaf size (n / 4^L on average),
+ * so this is the leaf-size choice too.  ms: the time the tuner measured for
+ * the rule's sub-batch (informational).
+ */
+typedef struct {
+    int32_t order, log2n, levels;
+    float ms;
+} petfmm_level_rule;
+
+/*
+ * petfmm_rule_levels -- the automatic L of one problem (n particles, order,
+ * sigma, domain) under the given rules: the matching rule's L if there is
+ * one and it satisfies the kernel-substitution guard of
+ * petfmm_choose_levels, else petfmm_choose_levels.  Host only; rules may be
+ * NULL when nrules = 0.  Returns L >= 1 or PETFMM_EINVAL.
+ */
+int petfmm_rule_levels(const petfmm_level_rule *rules, int nrules, int64_t n, int order,
+                       double sigma, const petfmm_domain *dom);
+
+/*
+ * petfmm_set_level_rules -- install (copy) rules in the context: its
+ * automatic L (petfmm_evaluate_batch with levels <= 0) follows
+ * petfmm_rule_levels from then on.  nrules = 0 clears them.  Host only.
+ * Returns PETFMM_OK or PETFMM_EINVAL (a rule with order outside 1..40,
+ * log2n outside 0..62 or levels outside 1..15).
+ */
+int petfmm_set_level_rules(petfmm_ctx *ctx, const petfmm_level_rule *rules, int nrules);
+
+typedef struct {
+    int tc_blocks;      /* the PETFMM_OPT_TC_BLOCKS it chose (set on the context) */
+    int tc_dense_pct;   /* the PETFMM_OPT_TC_DENSE it chose (set on the context) */
+    int nrules;         /* rules written to out_rules (one per (order, log2n) class) */
+    int changed;        /* rules whose L differs from the work model's */
+    int evaluations;    /* evaluations run while tuning (warm-up ones included) */
+    float ms_model;     /* the whole batch, work-model L, the context's options on entry */
+    float ms_tuned;     /* the whole batch, tuned L and options */
+} petfmm_tune_report;
+
+/*
+ * petfmm_tune_batch -- the autotuner for petfmm_evaluate_batch.  Seeded by
+ * the work model of Sec. 5.2 (Eq. 13/14, petfmm_choose_levels), it times on
+ * the GPU, with CUDA events on the context's stream, the median of `reps`
+ * evaluations (after one warm-up) of:
+ *   1. per class of instances (same order, same floor(log2 n)), the class
+ *      as a sub-batch (with an empty instance at the batch's deepest level,
+ *      so the launch sequence is the whole batch's) at L_model, L_model - 1
+ *      and L_model + 1 (those the guard allows), keeping the fastest L as
+ *      the class's rule -- another L than the model's only if it is at least
+ *      2% faster;
+ *   2. the whole batch under those rules with the context's options on
+ *      entry and then every PETFMM_OPT_TC_BLOCKS in {0, 1, 2} with
+ *      PETFMM_OPT_TC_DENSE in {1, 5}, keeping the fastest pair if it beats
+ *      the entry options by 2%.
+ * It installs the rules (petfmm_set_level_rules) and the two options in the
+ * context, writes up to cap rules to out_rules (may be NULL with cap 0) and
+ * fills *report.  The instances' levels fields are ignored; their u, v
+ * receive the results of the tuning evaluations (the last one is the tuned
+ * batch).  Synchronous.  Returns PETFMM_OK, PETFMM_EINVAL, PETFMM_ENOMEM,
+ * PETFMM_ECUDA, or the first failing evaluation's status.
+ */
+int petfmm_tune_batch(petfmm_ctx *ctx, int n_inst, const petfmm_instance *inst, int reps,
+                      petfmm_level_rule *out_rules, int cap, petfmm_tune_report *report);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: a thread-safe request loop with continuous batching.           */
@@ -184,6 +255,10 @@ typedef struct {
     int64_t n;
     double *x, *y;         /* host arrays owned by the server: final positions
                               (valid until petfmm_serve_release or destroy) */
+    int32_t rounds;        /* scheduler rounds the request took part in */
+    int32_t max_shared;    /* most requests resident in one of those rounds
+                              (itself included): > 1 means its evaluations
+                              ran batched with other requests' */
 } petfmm_result;
 
 /* hbm_budget_bytes: device memory the server may hold for admitted requests;
@@ -199,12 +274,39 @@ int petfmm_serve_poll(petfmm_server *s, uint64_t ticket, petfmm_result *out);
 int petfmm_serve_release(petfmm_server *s, uint64_t ticket);
 /* Stop the scheduler thread (finishing admitted work) and free everything. */
 int petfmm_serve_destroy(petfmm_server *s);
+/* Server counters since creation (a snapshot). */
+typedef struct {
+    uint64_t rounds;      /* scheduler rounds run (one batched evaluation each) */
+    uint64_t submitted, admitted, completed;
+    int32_t queued;       /* requests waiting now */
+    int32_t max_active;   /* most requests resident in one round */
+    double mean_active;   /* mean requests resident per round */
+    double busy_ms;       /* time spent in rounds */
+    double up_ms;         /* time since petfmm_serve_create */
+} petfmm_serve_counters;
+int petfmm_serve_stats(petfmm_server *s, petfmm_serve_counters *out);
+/* Per-round trace: for the first min(cap, count) rounds since creation, the
+ * round's start time (ms since creation) and the requests queued and
+ * resident at that moment.  Returns the number of rounds recorded, or
+ * PETFMM_EINVAL.  Host only. */
+int petfmm_serve_trace(petfmm_server *s, double *t_ms, int32_t *queued, int32_t *active, int cap);
 /* Per-request device-memory estimate used for admission (Table 1 adapted). */
 size_t petfmm_serve_estimate_bytes(int64_t n, int levels, int order, int precision);
 
 /* ---------------------------------------------------------------------- */
 /* Inspection (the verification dump of Sec. 6.2) and instrumentation.    */
 /* ---------------------------------------------------------------------- */
+
+/* Bounds checks (the library built with -DPETFMM_CHECKS, libpetfmm_checked.so:
+ * every index read from device data -- permutation, leaf ranges, work items,
+ * the caller index of a blob, split-pair scratch bases -- is checked before
+ * use; a bad one is skipped and its check's source line recorded, never a
+ * trap).  Writes the first failing line of tree.cu, expansions.cu and p2p.cu
+ * (0: none) to lines[0..2] and clears them; call after petfmm_sync().
+ * Returns 3 in the checked build, 0 in the regular one (lines all 0), or
+ * PETFMM_EINVAL for a NULL pointer.  Section 6.2's verification support;
+ * the paper has no counterpart of the checks themselves. */
+int petfmm_debug_checks(uint32_t *lines);
 
 /* Tree of the last petfmm_evaluate (after petfmm_sync): host arrays
  * keys[n] (Morton key of each particle, input order), perm[n] (input index

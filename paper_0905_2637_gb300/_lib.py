@@ -15,7 +15,9 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpetfmm.so")
+# PETFMM_CHECKED=1 loads the bounds-checked build (libpetfmm_checked.so)
+LIB_PATH = os.path.join(HERE, "libpetfmm_checked.so" if os.environ.get("PETFMM_CHECKED") == "1"
+                        else "libpetfmm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "petfmm.h")
 
 PETFMM_OK, PETFMM_EINVAL, PETFMM_ENOMEM, PETFMM_EDOMAIN = 0, -1, -2, -3
@@ -52,7 +54,16 @@ class Request(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("latency_ms", ctypes.c_double),
                 ("queue_ms", ctypes.c_double), ("n", ctypes.c_int64),
-                ("x", ctypes.POINTER(ctypes.c_double)), ("y", ctypes.POINTER(ctypes.c_double))]
+                ("x", ctypes.POINTER(ctypes.c_double)), ("y", ctypes.POINTER(ctypes.c_double)),
+                ("rounds", ctypes.c_int32), ("max_shared", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint64), ("submitted", ctypes.c_uint64),
+                ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("queued", ctypes.c_int32), ("max_active", ctypes.c_int32),
+                ("mean_active", ctypes.c_double), ("busy_ms", ctypes.c_double),
+                ("up_ms", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -62,6 +73,18 @@ class Stats(ctypes.Structure):
                 ("p2p_pair_items", ctypes.c_int64), ("p2p_split_entries", ctypes.c_int64),
                 ("p2p_sym_pairs", ctypes.c_int64), ("pairs_load_balance", ctypes.c_float),
                 ("occupied_leaves", ctypes.c_int64)]
+
+
+class LevelRule(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("log2n", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("tc_blocks", ctypes.c_int), ("tc_dense_pct", ctypes.c_int),
+                ("nrules", ctypes.c_int), ("changed", ctypes.c_int),
+                ("evaluations", ctypes.c_int), ("ms_model", ctypes.c_float),
+                ("ms_tuned", ctypes.c_float)]
 
 
 class PetfmmError(RuntimeError):
@@ -114,6 +137,8 @@ def load():
             "petfmm_serve_release": (I, [P, ctypes.c_uint64]),
             "petfmm_serve_destroy": (I, [P]),
             "petfmm_serve_estimate_bytes": (SZ, [I64, I, I, I]),
+            "petfmm_serve_stats": (I, [P, ctypes.POINTER(ServeStats)]),
+            "petfmm_serve_trace": (I, [P, P, P, P, I]),
             "petfmm_debug_tree": (I, [P, P, P, P]),
             "petfmm_debug_expansions": (I, [P, I, I, P]),
             "petfmm_debug_interaction_list": (I, [I, I, I, P]),
@@ -128,6 +153,12 @@ def load():
             "petfmm_version": (I, []),
             "petfmm_measure_peaks": (I, [ctypes.POINTER(Peaks)]),
             "petfmm_tree_noalloc": (I, [ctypes.POINTER(Domain), I, I, I64, P, P, P, P, P, P]),
+            "petfmm_debug_checks": (I, [P]),
+            "petfmm_rule_levels": (I, [ctypes.POINTER(LevelRule), I, I64, I, D,
+                                       ctypes.POINTER(Domain)]),
+            "petfmm_set_level_rules": (I, [P, ctypes.POINTER(LevelRule), I]),
+            "petfmm_tune_batch": (I, [P, I, ctypes.POINTER(Instance), I,
+                                      ctypes.POINTER(LevelRule), I, ctypes.POINTER(TuneReport)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -174,6 +205,22 @@ def petfmm_choose_levels(n, order, sigma, domain):
     dom = Domain(*map(float, domain))
     return _ck(load().petfmm_choose_levels(int(n), int(order), float(sigma), ctypes.byref(dom)),
                "petfmm_choose_levels")
+
+
+def _rules_array(rules):
+    arr = (LevelRule * max(1, len(rules)))()
+    for i, r in enumerate(rules):
+        arr[i] = LevelRule(int(r["order"]), int(r["log2n"]), int(r["levels"]),
+                           float(r.get("ms", 0.0)))
+    return arr
+
+
+def petfmm_rule_levels(rules, n, order, sigma, domain):
+    """Automatic L of one problem under level rules (list of dicts with order,
+    log2n, levels); host only."""
+    dom = Domain(*map(float, domain))
+    return _ck(load().petfmm_rule_levels(_rules_array(rules), len(rules), int(n), int(order),
+                                         float(sigma), ctypes.byref(dom)), "petfmm_rule_levels")
 
 
 def petfmm_debug_near_fit(sigma, wleaf, tol):
@@ -359,16 +406,37 @@ class Context:
             "petfmm_debug_expansions")
         return out.view(np.complex128).reshape(1 << (2 * level), self.order)
 
-    def evaluate_batch(self, instances):
-        """instances: list of dicts with domain, levels (<= 0: automatic), order,
-        sigma, x, y, gamma, u, v (CUDA tensors of the context's dtype)."""
+    def _instances(self, instances):
         arr = (Instance * max(1, len(instances)))()
         for i, it in enumerate(instances):
             n = it["x"].numel()
             ptrs = [_dev_ptr(it[k], self.torch_dtype, n, k) for k in ("x", "y", "gamma", "u", "v")]
             arr[i] = Instance(Domain(*map(float, it["domain"])), int(it.get("levels", 0)),
                               int(it["order"]), float(it["sigma"]), n, *ptrs)
-        _ck(load().petfmm_evaluate_batch(self.handle, len(instances), arr), "petfmm_evaluate_batch")
+        return arr
+
+    def evaluate_batch(self, instances):
+        """instances: list of dicts with domain, levels (<= 0: automatic), order,
+        sigma, x, y, gamma, u, v (CUDA tensors of the context's dtype)."""
+        _ck(load().petfmm_evaluate_batch(self.handle, len(instances), self._instances(instances)),
+            "petfmm_evaluate_batch")
+
+    def set_level_rules(self, rules):
+        """Install level rules (list of dicts with order, log2n, levels)."""
+        _ck(load().petfmm_set_level_rules(self.handle, _rules_array(rules), len(rules)),
+            "petfmm_set_level_rules")
+
+    def tune_batch(self, instances, reps=3):
+        """Run the autotuner on a batch (petfmm_tune_batch); returns (rules,
+        report) as a list of dicts and a dict.  The context keeps the result."""
+        cap = 4 * max(1, len(instances))
+        out = (LevelRule * cap)()
+        rep = TuneReport()
+        _ck(load().petfmm_tune_batch(self.handle, len(instances), self._instances(instances),
+                                     int(reps), out, cap, ctypes.byref(rep)), "petfmm_tune_batch")
+        rules = [dict(order=out[i].order, log2n=out[i].log2n, levels=out[i].levels, ms=out[i].ms)
+                 for i in range(rep.nrules)]
+        return rules, {f: getattr(rep, f) for f, _ in TuneReport._fields_}
 
 
 class Server:
@@ -390,19 +458,36 @@ class Server:
             "petfmm_serve_submit")
         return int(t.value)
 
-    def poll(self, ticket):
-        """None while running; else dict(status, latency_ms, queue_ms, x, y)."""
+    def poll(self, ticket, positions=True):
+        """None while running; else dict(status, latency_ms, queue_ms, rounds,
+        max_shared and, with positions, x, y); the result is then released."""
         r = Result()
         rc = load().petfmm_serve_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(r))
         if rc == PETFMM_ENOTREADY:
             return None
         _ck(rc, "petfmm_serve_poll")
-        out = {"status": r.status, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms}
-        if r.status == PETFMM_OK and r.n > 0:
+        out = {"status": r.status, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms,
+               "rounds": r.rounds, "max_shared": r.max_shared}
+        if positions and r.status == PETFMM_OK and r.n > 0:
             out["x"] = np.ctypeslib.as_array(r.x, shape=(r.n,)).copy()
             out["y"] = np.ctypeslib.as_array(r.y, shape=(r.n,)).copy()
         load().petfmm_serve_release(self.handle, ctypes.c_uint64(ticket))
         return out
+
+    def stats(self):
+        st = ServeStats()
+        _ck(load().petfmm_serve_stats(self.handle, ctypes.byref(st)), "petfmm_serve_stats")
+        return {f: getattr(st, f) for f, _ in ServeStats._fields_}
+
+    def trace(self):
+        """Per round: (start ms since creation, queued, resident) arrays."""
+        n = _ck(load().petfmm_serve_trace(self.handle, None, None, None, 0), "petfmm_serve_trace")
+        t = np.zeros(max(n, 1), np.float64)
+        q = np.zeros(max(n, 1), np.int32)
+        a = np.zeros(max(n, 1), np.int32)
+        n = _ck(load().petfmm_serve_trace(self.handle, t.ctypes.data, q.ctypes.data, a.ctypes.data,
+                                          n), "petfmm_serve_trace")
+        return t[:n], q[:n], a[:n]
 
     def close(self):
         if self.handle is not None:

@@ -3,6 +3,11 @@
 Translation units compile in parallel; the link uses the static CUDA runtime
 so the library does not depend on which ``libcudart`` the caller loaded.
 A stamp of the sources and flags skips the build when nothing changed.
+
+``build(checked=True)`` makes the bounds-checked variant
+``libpetfmm_checked.so`` (``-DPETFMM_CHECKS``: indices read from device data
+are checked before use and a failure is reported by petfmm_debug_checks, never
+trapped) from the same sources, in its own object folder.
 """
 from __future__ import annotations
 
@@ -18,6 +23,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpetfmm.so")
+LIB_CHECKED = os.path.join(HERE, "libpetfmm_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include")] + ARCH
@@ -47,19 +53,21 @@ def _stamp(sources, extra) -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    extra = list(extra_flags or [])
+def build(force: bool = False, verbose: bool = False, extra_flags=None, checked: bool = False) -> str:
+    extra = list(extra_flags or []) + (["-DPETFMM_CHECKS"] if checked else [])
+    lib = LIB_CHECKED if checked else LIB
+    objdir = os.path.join(BUILD, "checked") if checked else BUILD
     srcs = _sources()
     stamp = _stamp(srcs, extra)
-    stamp_file = os.path.join(BUILD, "stamp")
-    if (not force and os.path.exists(LIB) and os.path.exists(stamp_file)
+    stamp_file = os.path.join(objdir, "stamp")
+    if (not force and os.path.exists(lib) and os.path.exists(stamp_file)
             and open(stamp_file).read() == stamp):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + NVCC_FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -71,17 +79,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     workers = min(len(srcs), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None,
+                checked="--checked" in sys.argv))

@@ -182,6 +182,37 @@ __device__ __forceinline__ void set_status(int *status, int code) {
     atomicCAS(status, 0, code);
 }
 
+// Bounds-checked build (compiled with -DPETFMM_CHECKS; the library build
+// makes it as libpetfmm_checked.so).  PF_IN(i, n) is true when 0 <= i < n;
+// otherwise it records the source line of the check in this file's device
+// word pf_check_line (the first failure wins) and is false, and the caller
+// skips the access (reads a zero, writes nothing).  It never traps, so a bad
+// index leaves the context usable and is reported by petfmm_debug_checks().
+// In the regular build PF_IN is the constant true and costs nothing.
+#ifdef PETFMM_CHECKS
+static __device__ unsigned int pf_check_line = 0;
+__device__ __forceinline__ bool pf_in_range(int64_t i, int64_t n, unsigned line) {
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&pf_check_line, 0u, line);
+    return false;
+}
+#define PF_IN(i, n) ::petfmm::pf_in_range(int64_t(i), int64_t(n), __LINE__)
+// host: read and clear this file's word (0: no failure)
+#define PF_DEFINE_CHECK_READER(name)                                            \
+    unsigned pf_checks_##name() {                                               \
+        unsigned v = 0, z = 0;                                                  \
+        if (cudaMemcpyFromSymbol(&v, pf_check_line, sizeof(v)) != cudaSuccess) \
+            cudaGetLastError();                                                 \
+        if (cudaMemcpyToSymbol(pf_check_line, &z, sizeof(z)) != cudaSuccess)   \
+            cudaGetLastError();                                                 \
+        return v;                                                               \
+    }
+#else
+#define PF_IN(i, n) true
+#define PF_DEFINE_CHECK_READER(name) \
+    unsigned pf_checks_##name() { return 0; }
+#endif
+
 template <typename R> struct Cplx;
 template <> struct Cplx<double> { using T = double2; };
 template <> struct Cplx<float> { using T = float2; };

@@ -153,6 +153,8 @@ struct petfmm_ctx {
     uint64_t gkey = 0, glaunches = 0;
     cudaEvent_t ev[PETFMM_STAGE_COUNT + 1] = {};
     bool ev_recorded = false;
+    // level rules of the automatic L (petfmm_set_level_rules / petfmm_tune_batch)
+    std::vector<petfmm_level_rule> rules;
 };
 
 namespace {
@@ -1123,13 +1125,17 @@ int petfmm_sync(petfmm_ctx *c) {
     return status;
 }
 
-static int problems_from(int n_inst, const petfmm_instance *inst, std::vector<Problem> &probs) {
+static int problems_from(int n_inst, const petfmm_instance *inst, std::vector<Problem> &probs,
+                         const std::vector<petfmm_level_rule> *rules = nullptr) {
     probs.resize(static_cast<size_t>(n_inst));
     for (int i = 0; i < n_inst; ++i) {
         const petfmm_instance &s = inst[i];
         int L = s.levels;
         if (L <= 0) {
-            L = petfmm_choose_levels(s.n, s.order, s.sigma, &s.domain);
+            L = rules && !rules->empty()
+                    ? petfmm_rule_levels(rules->data(), int(rules->size()), s.n, s.order, s.sigma,
+                                         &s.domain)
+                    : petfmm_choose_levels(s.n, s.order, s.sigma, &s.domain);
             if (L < 0) return L;
         }
         int rc = check_problem(&s.domain, L, s.order, s.sigma);
@@ -1143,9 +1149,208 @@ static int problems_from(int n_inst, const petfmm_instance *inst, std::vector<Pr
 int petfmm_evaluate_batch(petfmm_ctx *c, int n_inst, const petfmm_instance *inst) {
     if (!c || n_inst < 0 || (n_inst > 0 && !inst)) return PETFMM_EINVAL;
     std::vector<Problem> probs;
-    int rc = problems_from(n_inst, inst, probs);
+    int rc = problems_from(n_inst, inst, probs, &c->rules);
     if (rc) return rc;
     return run(c, probs);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner (petfmm_tune_batch): the work model seeds L, the GPU decides.
+// ---------------------------------------------------------------------------
+namespace {
+
+int floor_log2(int64_t n) {
+    int e = 0;
+    while (n > 1) {
+        n >>= 1;
+        ++e;
+    }
+    return e;
+}
+
+// fraction by which a candidate must beat the work model's choice (or the
+// entry options) to replace it
+constexpr float kTuneMargin = 0.02f;
+
+// Median of `reps` timed evaluations of the problems (after one warm-up,
+// which also captures the graph of a new launch shape), CUDA events on the
+// context's stream.
+int time_batch(petfmm_ctx *c, const std::vector<Problem> &probs, int reps, float *ms, int *nevals) {
+    int rc = run(c, probs);
+    if (rc) return rc;
+    ++*nevals;
+    if ((rc = petfmm_sync(c))) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return PETFMM_ECUDA;
+    }
+    std::vector<float> t;
+    for (int r = 0; r < reps && rc == PETFMM_OK; ++r) {
+        cudaEventRecord(e0, c->stream);
+        rc = run(c, probs);
+        cudaEventRecord(e1, c->stream);
+        if (rc) break;
+        ++*nevals;
+        if ((rc = petfmm_sync(c))) break;
+        float x = 0.f;
+        if (cudaEventElapsedTime(&x, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            rc = PETFMM_ECUDA;
+            break;
+        }
+        t.push_back(x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    std::sort(t.begin(), t.end());
+    *ms = t.empty() ? 0.f : t[t.size() / 2];
+    return PETFMM_OK;
+}
+
+}  // namespace
+
+int petfmm_rule_levels(const petfmm_level_rule *rules, int nrules, int64_t n, int order,
+                       double sigma, const petfmm_domain *dom) {
+    const int Lm = petfmm_choose_levels(n, order, sigma, dom);
+    if (Lm < 0 || nrules <= 0 || !rules) return Lm;
+    const int e = floor_log2(n);
+    const double rmin = sigma * std::sqrt(2.0 * std::log(1e8));
+    for (int i = 0; i < nrules; ++i) {
+        const petfmm_level_rule &r = rules[i];
+        if (r.order != order || r.log2n != e) continue;
+        if (r.levels < 1 || r.levels > MAX_L) return Lm;
+        // the kernel-substitution guard of petfmm_choose_levels
+        if (dom->width / std::ldexp(1.0, r.levels) < rmin) return Lm;
+        return r.levels;
+    }
+    return Lm;
+}
+
+int petfmm_set_level_rules(petfmm_ctx *c, const petfmm_level_rule *rules, int nrules) {
+    if (!c || nrules < 0 || (nrules > 0 && !rules)) return PETFMM_EINVAL;
+    for (int i = 0; i < nrules; ++i)
+        if (rules[i].order < 1 || rules[i].order > MAX_P || rules[i].log2n < 0 ||
+            rules[i].log2n > 62 || rules[i].levels < 1 || rules[i].levels > MAX_L)
+            return PETFMM_EINVAL;
+    c->rules.assign(rules, rules + nrules);
+    return PETFMM_OK;
+}
+
+int petfmm_tune_batch(petfmm_ctx *c, int n_inst, const petfmm_instance *inst, int reps,
+                      petfmm_level_rule *out_rules, int cap, petfmm_tune_report *report) {
+    if (!c || n_inst < 0 || (n_inst > 0 && !inst) || reps < 1 || cap < 0 ||
+        (cap > 0 && !out_rules) || !report)
+        return PETFMM_EINVAL;
+    std::memset(report, 0, sizeof(*report));
+    report->tc_blocks = c->tc_blocks;
+    report->tc_dense_pct = c->tc_dense_pct;
+    if (n_inst == 0) return PETFMM_OK;
+    // whole batch at the work model's L, options as on entry
+    const std::vector<petfmm_level_rule> none;
+    std::vector<Problem> probs;
+    int rc = problems_from(n_inst, inst, probs, &none);
+    if (rc) return rc;
+    int nev = 0;
+    rc = time_batch(c, probs, reps, &report->ms_model, &nev);
+    if (rc) return rc;
+    // 1. per class (order, floor(log2 n)): the class alone at L_model - 1,
+    //    L_model, L_model + 1
+    std::map<std::pair<int, int>, std::vector<int>> classes;
+    for (int i = 0; i < n_inst; ++i)
+        if (inst[i].n > 0) classes[{inst[i].order, floor_log2(inst[i].n)}].push_back(i);
+    // Each class is timed with an empty anchor instance at the batch's
+    // deepest level, so that every candidate runs the launch sequence of the
+    // whole batch (one M2M/L2L launch per level, ...): the comparison then
+    // sees the class's work, not the launches a shallower tree would drop
+    // when alone but not inside the batch.
+    int Ldeep = 1;
+    for (const Problem &q : probs) Ldeep = std::max(Ldeep, q.L);
+    std::vector<petfmm_level_rule> rules;
+    for (const auto &kv : classes) {
+        const std::vector<int> &members = kv.second;
+        std::vector<petfmm_instance> sub;
+        for (int i : members) sub.push_back(inst[i]);
+        petfmm_instance anchor{};
+        anchor.domain = petfmm_domain{0.0, 0.0, 1.0};
+        anchor.levels = Ldeep;
+        anchor.order = kv.first.first;
+        anchor.sigma = 1.0;
+        anchor.n = 0;
+        sub.push_back(anchor);
+        const petfmm_instance &f = sub.front();
+        const int Lm = petfmm_choose_levels(f.n, f.order, f.sigma, &f.domain);
+        if (Lm < 0) return Lm;
+        petfmm_level_rule best{kv.first.first, kv.first.second, Lm, -1.f};
+        float model_ms = -1.f;
+        for (int L : {Lm, Lm - 1, Lm + 1}) {
+            if (L < 1 || L > MAX_L) continue;
+            const petfmm_level_rule cand{kv.first.first, kv.first.second, L, 0.f};
+            const std::vector<petfmm_level_rule> one{cand};
+            std::vector<Problem> sp;
+            if ((rc = problems_from(int(sub.size()), sub.data(), sp, &one))) return rc;
+            bool applies = false;  // the guard may send every member back to the model
+            for (size_t q = 0; q + 1 < sp.size(); ++q) applies |= sp[q].L == L;
+            if (!applies) continue;
+            float ms = 0.f;
+            if ((rc = time_batch(c, sp, reps, &ms, &nev))) return rc;
+            if (L == Lm) model_ms = ms;
+            // another depth must beat the model's by kTuneMargin (timing noise
+            // is not a reason to leave the model)
+            const bool better = L == Lm ? best.ms < 0.f || ms < best.ms
+                                        : ms < best.ms && (model_ms < 0.f ||
+                                                           ms < (1.f - kTuneMargin) * model_ms);
+            if (best.ms < 0.f || better) {
+                best.levels = L;
+                best.ms = ms;
+            }
+        }
+        if (best.levels != Lm) report->changed++;
+        rules.push_back(best);
+    }
+    // 2. the M2L shape for the whole batch under those rules (the entry
+    //    options first; another pair must beat them by kTuneMargin)
+    if ((rc = problems_from(n_inst, inst, probs, &rules))) return rc;
+    const int blocks0 = c->tc_blocks, dense0 = c->tc_dense_pct;
+    float best_ms = -1.f, entry_ms = -1.f;
+    int best_blocks = blocks0, best_dense = dense0;
+    std::vector<std::pair<int, int>> shapes{{blocks0, dense0}};
+    for (int blocks = 0; blocks <= 2; ++blocks)
+        for (int dense : {1, 5})
+            if (!(blocks == blocks0 && dense == dense0)) shapes.push_back({blocks, dense});
+    for (const auto &sh : shapes) {
+        c->tc_blocks = sh.first;
+        c->tc_dense_pct = sh.second;
+        float ms = 0.f;
+        rc = time_batch(c, probs, reps, &ms, &nev);
+        if (rc) {
+            c->tc_blocks = blocks0;
+            c->tc_dense_pct = dense0;
+            return rc;
+        }
+        if (entry_ms < 0.f) entry_ms = ms;
+        if (best_ms < 0.f || (ms < best_ms && ms < (1.f - kTuneMargin) * entry_ms)) {
+            best_ms = ms;
+            best_blocks = sh.first;
+            best_dense = sh.second;
+        }
+    }
+    c->tc_blocks = best_blocks;
+    c->tc_dense_pct = best_dense;
+    c->rules = rules;
+    // the tuned batch once more, so the caller's u, v hold its result
+    if ((rc = run(c, probs))) return rc;
+    ++nev;
+    if ((rc = petfmm_sync(c))) return rc;
+    report->tc_blocks = best_blocks;
+    report->tc_dense_pct = best_dense;
+    report->nrules = int(rules.size());
+    report->evaluations = nev;
+    report->ms_tuned = best_ms;
+    for (int i = 0; i < std::min(cap, int(rules.size())); ++i) out_rules[i] = rules[i];
+    return PETFMM_OK;
 }
 
 int petfmm_debug_plan(int precision, int n_inst, const petfmm_instance *inst, int64_t *out, int cap) {
@@ -1304,6 +1509,18 @@ int petfmm_get_stats(petfmm_ctx *c, petfmm_stats *out) {
         if (pairs) out->pairs_load_balance = lb(size_t(c->p2p_grid), size_t(c->pairs_grid));
     }
     return PETFMM_OK;
+}
+
+int petfmm_debug_checks(uint32_t *lines) {
+    if (!lines) return PETFMM_EINVAL;
+    lines[0] = pf_checks_tree();
+    lines[1] = pf_checks_expansions();
+    lines[2] = pf_checks_p2p();
+#ifdef PETFMM_CHECKS
+    return 3;
+#else
+    return 0;
+#endif
 }
 
 int petfmm_debug_tree(petfmm_ctx *c, uint32_t *keys, uint32_t *perm, uint32_t *start) {

@@ -379,7 +379,10 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m(
         const InstDesc &d = insts[e.x];
         const int p = d.p, L = d.L;
         const uint32_t m = e.y;
-        const uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+        uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+        if (!(PF_IN(m, int64_t(1) << (2 * L)) && PF_IN(int64_t(s0) - d.poff, d.n + 1) &&
+              PF_IN(int64_t(s1) - d.poff, d.n + 1)) || s1 < s0)
+            s1 = s0;  // checked build: a leaf range outside the instance is skipped
         const uint32_t ix = compact_bits(m), iy = compact_bits(m >> 1);
         const double cx = d.x0 + (double(ix) + 0.5) * d.wleaf;
         const double cy = d.y0 + (double(iy) + 0.5) * d.wleaf;
@@ -453,7 +456,10 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m_reg(
         const InstDesc &d = insts[e.x];
         const int p = d.p, L = d.L;
         const uint32_t m = e.y;
-        const uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+        uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
+        if (!(PF_IN(m, int64_t(1) << (2 * L)) && PF_IN(int64_t(s0) - d.poff, d.n + 1) &&
+              PF_IN(int64_t(s1) - d.poff, d.n + 1)) || s1 < s0)
+            s1 = s0;  // checked build: a leaf range outside the instance is skipped
         float2 acc[PM];
 #pragma unroll
         for (int k = 0; k < PM; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -817,5 +823,7 @@ template cudaError_t launch_m2l<double>(const Task *, int, int64_t, const InstDe
 template cudaError_t launch_m2l<float>(const Task *, int, int64_t, const InstDesc *,
                                        const uint32_t *, const float2 *, float2 *,
                                        const uint32_t *, int, cudaStream_t, uint64_t *);
+
+PF_DEFINE_CHECK_READER(expansions)
 
 }  // namespace petfmm

@@ -9,6 +9,12 @@ namespace petfmm {
 // Every launcher returns cudaGetLastError() after the launch and adds the
 // number of kernels it launched to *launches.
 
+// Bounds-checked build: the first failing PF_IN check's source line in each
+// file (0: none), read and cleared (always 0 in the regular build).
+unsigned pf_checks_tree();
+unsigned pf_checks_expansions();
+unsigned pf_checks_p2p();
+
 // ---- tree.cu ---------------------------------------------------------------
 // Sec. 2.1 binning + z-order key of every particle (composite key for batches);
 // if recu != nullptr also its mixed-path record (see launch_gather_mixed) in

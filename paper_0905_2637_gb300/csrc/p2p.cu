@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) k_item_permute(const uint4 *__restrict__ 
                                                       uint4 *__restrict__ out, int64_t cap,
                                                       const uint32_t *count) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r < cap && r < int64_t(*count)) out[r] = in[perm[r]];
+    if (r < cap && r < int64_t(*count) && PF_IN(perm[r], cap)) out[r] = in[perm[r]];
 }
 
 // heaviest items first: one stable 8-bit radix pass over the work classes in
@@ -324,6 +324,10 @@ __device__ __forceinline__ void directed_item(const uint4 item, const InstDesc *
     for (int k = 0; k <= DEG; ++k) a[k] = d.poly[k];
     const float kappa = d.kappa, split = d.qsplit_rho2;
     const uint32_t m = item.y;
+    // checked build: the item's leaf and target range lie inside the instance
+    if (!(PF_IN(m, int64_t(1) << (2 * L)) && PF_IN(int64_t(item.z) - d.poff, d.n + 1) &&
+          PF_IN(int64_t(item.z) + item.w - d.poff, d.n + 1)))
+        return;
     const int ix = int(compact_bits(m)), iy = int(compact_bits(m >> 1));
     // lane = (source group grp, target slot k); targets k and k + W
     const int lw = p2p_group_log2(item.w, 2);
@@ -1004,7 +1008,7 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
                                           const uint32_t *__restrict__ start,
                                           const float4 *__restrict__ rec,
                                           float2 *__restrict__ part, int64_t nslot,
-                                          float2 *__restrict__ xs, int lane) {
+                                          float2 *__restrict__ xs, int64_t xcap, int lane) {
     const InstDesc &d = insts[item.x];
     float a[DEG + 1];
 #pragma unroll
@@ -1016,6 +1020,10 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
     const uint32_t piece = item.z >> 4;
     const uint32_t *st = start + d.soff;
     const uint32_t a0 = st[m], na = st[m + 1] - a0;
+    // checked build: the leaf and its range lie inside the instance
+    if (!(PF_IN(m, int64_t(1) << (2 * d.L)) && PF_IN(int64_t(a0) - d.poff, d.n + 1) &&
+          PF_IN(int64_t(a0) + na - d.poff, d.n + 1) && PF_IN(int64_t(a0) + na, nslot + 1)))
+        return;
     if (dir == 4) {
         self_leaf<DEG, GENERAL>(rec, a0, na, a, kappa, split, cn, part + 8 * nslot + a0, lane);
         return;
@@ -1024,6 +1032,9 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
     const int ox = c_fwd[dir][0], oy = c_fwd[dir][1];
     const uint32_t mb = morton_key(uint32_t(ix + ox), uint32_t(iy + oy));
     const uint32_t b0 = st[mb], nb = st[mb + 1] - b0;
+    if (!(PF_IN(mb, int64_t(1) << (2 * d.L)) && PF_IN(int64_t(b0) - d.poff, d.n + 1) &&
+          PF_IN(int64_t(b0) + nb - d.poff, d.n + 1)))
+        return;
     float2 *fwd = part + int64_t(dir) * nslot + a0;      // A's particles, from B
     float2 *bwd = part + int64_t(4 + dir) * nslot + b0;  // B's particles, from A
     if (swap) {
@@ -1037,7 +1048,10 @@ __device__ __forceinline__ void pair_item(const uint4 item, const InstDesc *__re
         pair_pieces(na, nb, &pc);
         abeg = piece * pc;
         aend = min(na, abeg + pc);
-        if (piece) bwd = xs + item.w + int64_t(piece - 1) * nb;
+        if (piece) {
+            if (!PF_IN(int64_t(item.w) + int64_t(piece) * nb - 1, xcap)) return;
+            bwd = xs + item.w + int64_t(piece - 1) * nb;
+        }
     } else if (piece) {
         return;
     }
@@ -1064,7 +1078,8 @@ __global__ void __launch_bounds__(P2P_THREADS, 3) k_p2p_pairs(
         if (lane == 0) it = atomicAdd(ctrl + CTRL_QUEUE2, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= npairs) break;
-        pair_item<DEG, GENERAL>(pitems[it], insts, start, rec, pb.part, pb.nslot, pb.xs, lane);
+        pair_item<DEG, GENERAL>(pitems[it], insts, start, rec, pb.part, pb.nslot, pb.xs, pb.xcap,
+                                lane);
     }
     if (busy && lane == 0) {
         const size_t gw = size_t(blockIdx.x) * (P2P_THREADS / 32) + (threadIdx.x >> 5);
@@ -1177,6 +1192,7 @@ __global__ void __launch_bounds__(256, 4) k_p2p_final(
         return;
     }
     const int64_t q = int64_t(__float_as_uint(rr.w)) - d.poff;
+    if (!PF_IN(q, d.n)) return;  // checked build: the caller's index of the blob
     if (dtype_f32) {
         static_cast<float *>(d.u)[q] = w.x;
         static_cast<float *>(d.v)[q] = w.y;
@@ -1338,13 +1354,14 @@ __global__ void __launch_bounds__(256) k_unsort_f32(const Task *__restrict__ tas
     if (j0 + 4 <= t.count && (r0 & 3) == 0) {
         const uint4 q = *reinterpret_cast<const uint4 *>(perm + r0);
         const float4 w = *reinterpret_cast<const float4 *>(stage + r0);
-        out[int64_t(q.x) - d.poff] = w.x;
-        out[int64_t(q.y) - d.poff] = w.y;
-        out[int64_t(q.z) - d.poff] = w.z;
-        out[int64_t(q.w) - d.poff] = w.w;
+        if (PF_IN(int64_t(q.x) - d.poff, d.n)) out[int64_t(q.x) - d.poff] = w.x;
+        if (PF_IN(int64_t(q.y) - d.poff, d.n)) out[int64_t(q.y) - d.poff] = w.y;
+        if (PF_IN(int64_t(q.z) - d.poff, d.n)) out[int64_t(q.z) - d.poff] = w.z;
+        if (PF_IN(int64_t(q.w) - d.poff, d.n)) out[int64_t(q.w) - d.poff] = w.w;
     } else {
         for (int e = 0; e < 4; ++e)
-            if (j0 + e < t.count) out[int64_t(perm[r0 + e]) - d.poff] = stage[r0 + e];
+            if (j0 + e < t.count && PF_IN(int64_t(perm[r0 + e]) - d.poff, d.n))
+                out[int64_t(perm[r0 + e]) - d.poff] = stage[r0 + e];
     }
 }
 
@@ -1380,5 +1397,7 @@ cudaError_t launch_p2p_f64(int grid, const uint4 *items, uint32_t *ctrl, const I
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
+
+PF_DEFINE_CHECK_READER(p2p)
 
 }  // namespace petfmm

@@ -113,6 +113,13 @@ struct Req {
     petfmm_domain dom{};
     int evals_done = 0;
     size_t bytes = 0;
+    int rounds = 0;      // rounds this request took part in
+    int max_shared = 0;  // most requests resident in one of those rounds (itself included)
+};
+
+struct TraceSample {
+    double t_ms;  // since the server was created
+    int32_t queued, active;
 };
 
 }  // namespace
@@ -134,6 +141,13 @@ struct petfmm_server {
     petfmm_ctx *ctx64 = nullptr, *ctxmx = nullptr;
     double *dbox = nullptr, *hbox = nullptr;
     int box_cap = 0;
+    cudaMemPool_t pool = nullptr;  // request state (see free_state)
+    // counters (under mu)
+    Clock::time_point t_create;
+    uint64_t rounds = 0, submitted = 0, admitted = 0, completed = 0;
+    int max_active = 0;
+    double sum_active = 0.0, busy_ms = 0.0;
+    std::vector<TraceSample> trace;  // one sample per round (its start)
 };
 
 namespace {
@@ -148,10 +162,14 @@ size_t estimate(int64_t n, int L, int p, int precision) {
            size_t((n / 32 + leaves) * 16.0) + (1u << 20);
 }
 
-void free_state(Req *r) {
+// Request state comes from the server's own stream-ordered memory pool:
+// allocating and freeing it does not synchronise the device (cudaMalloc and
+// cudaFree would wait for the round in flight), and freed blocks stay in the
+// pool for the next admissions.
+void free_state(petfmm_server *s, Req *r) {
     double *bufs[] = {r->x, r->y, r->g, r->u, r->v, r->xn, r->yn};
     for (double *b : bufs)
-        if (b) cudaFree(b);
+        if (b) cudaFreeAsync(b, s->stream);
     r->x = r->y = r->g = r->u = r->v = r->xn = r->yn = nullptr;
 }
 
@@ -176,9 +194,10 @@ int admit(petfmm_server *s, Req *r) {
     const size_t bytes = size_t(n > 0 ? n : 1) * sizeof(double);
     double **bufs[] = {&r->x, &r->y, &r->g, &r->u, &r->v, &r->xn, &r->yn};
     for (double **b : bufs) {
-        if (cudaMalloc(b, bytes) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(b), bytes, s->pool, s->stream) !=
+            cudaSuccess) {
             cudaGetLastError();
-            free_state(r);
+            free_state(s, r);
             return PETFMM_ENOMEM;
         }
     }
@@ -186,12 +205,12 @@ int admit(petfmm_server *s, Req *r) {
         if (cudaMemcpyAsync(r->x, r->hx.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
             cudaMemcpyAsync(r->y, r->hy.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
             cudaMemcpyAsync(r->g, r->hg.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
-            free_state(r);
+            free_state(s, r);
             return PETFMM_ECUDA;
         }
         // host copies stay valid until the stream is synchronised below
         if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
-            free_state(r);
+            free_state(s, r);
             return PETFMM_ECUDA;
         }
         double bx0 = r->hx[0], by0 = r->hy[0], bx1 = bx0, by1 = by0;
@@ -206,7 +225,7 @@ int admit(petfmm_server *s, Req *r) {
     r->levels = r->spec.levels > 0 ? r->spec.levels
                                    : petfmm_choose_levels(n, r->spec.order, r->spec.sigma, &r->dom);
     if (r->levels < 1) {
-        free_state(r);
+        free_state(s, r);
         return PETFMM_EINVAL;
     }
     return PETFMM_OK;
@@ -219,10 +238,11 @@ void finish(petfmm_server *s, Req *r, int status) {
             cudaMemcpy(r->hy.data(), r->y, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
             status = PETFMM_ECUDA;
     }
-    free_state(r);
+    free_state(s, r);
     r->hg.clear();
     r->hg.shrink_to_fit();
     std::lock_guard<std::mutex> lk(s->mu);
+    s->completed++;
     r->status = status;
     r->t_done = Clock::now();
     r->done = true;
@@ -231,6 +251,19 @@ void finish(petfmm_server *s, Req *r, int status) {
 
 // One round: one evaluation for every resident request, then its RK2 stage.
 void run_round(petfmm_server *s, std::vector<Req *> &act) {
+    const Clock::time_point t0 = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->rounds++;
+        s->max_active = std::max(s->max_active, int(act.size()));
+        s->sum_active += double(act.size());
+        s->trace.push_back(TraceSample{std::chrono::duration<double, std::milli>(t0 - s->t_create).count(),
+                                       int32_t(s->queue.size()), int32_t(act.size())});
+        for (Req *r : act) {
+            r->rounds++;
+            r->max_shared = std::max(r->max_shared, int(act.size()));
+        }
+    }
     std::vector<petfmm_instance> in64, inmx;
     std::vector<Req *> r64, rmx;
     for (Req *r : act) {
@@ -301,6 +334,8 @@ void run_round(petfmm_server *s, std::vector<Req *> &act) {
         keep.push_back(r);
     }
     act.swap(keep);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
 }
 
 void worker_main(petfmm_server *s) {
@@ -325,6 +360,7 @@ void worker_main(petfmm_server *s) {
                 Req *r = s->queue.front();
                 s->queue.pop_front();
                 s->used += r->bytes;
+                s->admitted++;
                 newly.push_back(r);
             }
         }
@@ -362,6 +398,7 @@ int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, p
     if (!out || max_slots < 1 || max_queue < 1 || hbm_budget_bytes == 0) return PETFMM_EINVAL;
     *out = nullptr;
     petfmm_server *s = new (std::nothrow) petfmm_server();
+    if (s) s->t_create = Clock::now();
     if (!s) return PETFMM_ENOMEM;
     s->budget = hbm_budget_bytes;
     s->max_slots = max_slots;
@@ -372,12 +409,28 @@ int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, p
         delete s;
         return PETFMM_ECUDA;
     }
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = s->device;
+        uint64_t keep = UINT64_MAX;  // hold freed blocks for reuse
+        if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
+            cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaGetLastError();
+            if (s->pool) cudaMemPoolDestroy(s->pool);
+            cudaStreamDestroy(s->stream);
+            delete s;
+            return PETFMM_ECUDA;
+        }
+    }
     const petfmm_domain unit{0.0, 0.0, 1.0};
     int rc = petfmm_create(&unit, 2, 8, 0.01, PETFMM_FP64, PETFMM_F64, s->stream, &s->ctx64);
     if (rc == PETFMM_OK)
         rc = petfmm_create(&unit, 2, 8, 0.01, PETFMM_MIXED, PETFMM_F64, s->stream, &s->ctxmx);
     if (rc != PETFMM_OK) {
         if (s->ctx64) petfmm_destroy(s->ctx64);
+        cudaMemPoolDestroy(s->pool);
         cudaStreamDestroy(s->stream);
         delete s;
         return rc;
@@ -424,6 +477,7 @@ int petfmm_serve_submit(petfmm_server *s, const petfmm_request *req, uint64_t *t
             return PETFMM_EBUSY;
         }
         r->ticket = s->next_ticket++;
+        s->submitted++;
         s->queue.push_back(r);
         s->all[r->ticket] = r;
         *ticket = r->ticket;
@@ -443,6 +497,8 @@ int petfmm_serve_poll(petfmm_server *s, uint64_t ticket, petfmm_result *out) {
     out->latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
     const auto adm = r->t_admit.time_since_epoch().count() ? r->t_admit : r->t_done;
     out->queue_ms = std::chrono::duration<double, std::milli>(adm - r->t_submit).count();
+    out->rounds = r->rounds;
+    out->max_shared = r->max_shared;
     out->n = r->status == PETFMM_OK ? r->spec.n : 0;
     out->x = r->status == PETFMM_OK ? r->hx.data() : nullptr;
     out->y = r->status == PETFMM_OK ? r->hy.data() : nullptr;
@@ -460,6 +516,33 @@ int petfmm_serve_release(petfmm_server *s, uint64_t ticket) {
     return PETFMM_OK;
 }
 
+int petfmm_serve_stats(petfmm_server *s, petfmm_serve_counters *out) {
+    if (!s || !out) return PETFMM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->rounds = s->rounds;
+    out->submitted = s->submitted;
+    out->admitted = s->admitted;
+    out->completed = s->completed;
+    out->queued = int32_t(s->queue.size());
+    out->max_active = s->max_active;
+    out->mean_active = s->rounds ? s->sum_active / double(s->rounds) : 0.0;
+    out->busy_ms = s->busy_ms;
+    out->up_ms = std::chrono::duration<double, std::milli>(Clock::now() - s->t_create).count();
+    return PETFMM_OK;
+}
+
+int petfmm_serve_trace(petfmm_server *s, double *t_ms, int32_t *queued, int32_t *active, int cap) {
+    if (!s || cap < 0 || (cap > 0 && (!t_ms || !queued || !active))) return PETFMM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int n = int(std::min<size_t>(s->trace.size(), size_t(INT32_MAX)));
+    for (int i = 0; i < std::min(n, cap); ++i) {
+        t_ms[i] = s->trace[size_t(i)].t_ms;
+        queued[i] = s->trace[size_t(i)].queued;
+        active[i] = s->trace[size_t(i)].active;
+    }
+    return n;
+}
+
 int petfmm_serve_destroy(petfmm_server *s) {
     if (!s) return PETFMM_EINVAL;
     {
@@ -469,9 +552,11 @@ int petfmm_serve_destroy(petfmm_server *s) {
     s->cv.notify_all();
     if (s->worker.joinable()) s->worker.join();
     for (auto &kv : s->all) {
-        free_state(kv.second);
+        free_state(s, kv.second);
         delete kv.second;
     }
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     if (s->ctx64) petfmm_destroy(s->ctx64);
     if (s->ctxmx) petfmm_destroy(s->ctxmx);
     if (s->dbox) cudaFree(s->dbox);

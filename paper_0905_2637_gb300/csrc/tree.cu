@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
         const uint32_t k = skey[q];
         const uint32_t dg = (k >> shift) & mask;
         const uint32_t pos = gbase[dg] + (uint32_t(q) - lstart[dg]);
+        if (!PF_IN(pos, n)) continue;
         kout[pos] = k;
         vout[pos] = sval[q];
     }
@@ -463,6 +464,7 @@ __global__ void __launch_bounds__(256) k_gather_f64(const Task *__restrict__ tas
     const InstDesc &d = insts[t.inst];
     const int64_t r = d.poff + j;
     const int64_t q = int64_t(perm[r]) - d.poff;
+    if (!PF_IN(q, d.n)) return;
     xs[r] = double(static_cast<const TIn *>(d.x)[q]);
     ys[r] = double(static_cast<const TIn *>(d.y)[q]);
     gs[r] = double(static_cast<const TIn *>(d.g)[q]);
@@ -475,7 +477,10 @@ __global__ void __launch_bounds__(256) k_gather_mixed(const float4 *__restrict__
                                                       const uint32_t *__restrict__ perm,
                                                       float4 *__restrict__ rec, int64_t n) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (r < n) rec[r] = recu[perm[r]];
+    if (r < n) {
+        const uint32_t q = perm[r];
+        rec[r] = PF_IN(q, n) ? recu[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 }
 
 cudaError_t launch_gather_f64(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
@@ -497,5 +502,7 @@ cudaError_t launch_gather_mixed(const float4 *recu, const uint32_t *perm, float4
     PF_LAUNCHED(1);
     return cudaGetLastError();
 }
+
+PF_DEFINE_CHECK_READER(tree)
 
 }  // namespace petfmm

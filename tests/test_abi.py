@@ -105,3 +105,19 @@ def test_missing_library_fails_loudly(monkeypatch, lib):
     monkeypatch.setattr(mod, "LIB_PATH", "/nonexistent/libpetfmm.so")
     with pytest.raises(ImportError):
         mod.load()
+
+
+def test_checked_build_exists_and_reports_itself(lib):
+    """The bounds-checked variant is built beside the library; its
+    petfmm_debug_checks answers 3 (files checked), the regular one 0."""
+    import ctypes
+    import os
+    from paper_0905_2637_gb300 import build as b
+    assert os.path.exists(b.LIB_CHECKED)
+    lines = (ctypes.c_uint32 * 3)()
+    assert lib.load().petfmm_debug_checks(lines) == 0 and list(lines) == [0, 0, 0]
+    chk = ctypes.CDLL(b.LIB_CHECKED)
+    chk.petfmm_debug_checks.restype = ctypes.c_int
+    chk.petfmm_debug_checks.argtypes = [ctypes.c_void_p]
+    assert chk.petfmm_debug_checks(lines) == 3
+    assert chk.petfmm_debug_checks(None) == lib.PETFMM_EINVAL

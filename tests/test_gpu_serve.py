@@ -45,15 +45,20 @@ def test_result_same_alone_and_in_mix():
         srv.close()
     srv = _lib.Server(8 << 30, max_slots=8)
     tickets = []
-    for r in reqs:
+    for r in reqs:  # back to back: the later ones arrive while the first is on the GPU
         tickets.append(srv.submit(**r))
-        time.sleep(0.01)  # arrivals while others are on the GPU
     mixed = _wait(srv, tickets)
+    st = srv.stats()
     srv.close()
     for a, m in zip(alone, mixed):
         assert a["status"] == 0 and m["status"] == 0
         assert np.array_equal(a["x"], m["x"]) and np.array_equal(a["y"], m["y"])
         assert m["latency_ms"] >= m["queue_ms"] >= 0.0
+        assert a["max_shared"] == 1 and a["rounds"] == 2 * 3
+    # the mix really overlapped: requests shared rounds (batched evaluations)
+    assert max(m["max_shared"] for m in mixed) >= 2
+    assert sum(m["max_shared"] >= 2 for m in mixed) >= 2
+    assert st["max_active"] >= 2 and st["completed"] == st["submitted"] == len(reqs)
 
 
 def test_served_rk2_matches_oracle_stepper(orc):
