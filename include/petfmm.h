@@ -227,6 +227,59 @@ int petfmm_tune_batch(petfmm_ctx *ctx, int n_inst, const petfmm_instance *inst, 
                       petfmm_level_rule *out_rules, int cap, petfmm_tune_report *report);
 
 /* ---------------------------------------------------------------------- */
+/* Sharding one evaluation over several GPUs: the tree cut of Sec. 4 with  */
+/* the work and communication model of Sec. 5.1-5.2 (host only).           */
+/* ---------------------------------------------------------------------- */
+/*
+ * The quadtree of depth L is cut at level k (0 <= k <= L) into a root tree
+ * and 4^k subtrees, one per level-k box (Morton index s); leaf_counts[m] is
+ * the number of particles in leaf m (Morton order, 4^L entries).
+ *
+ * petfmm_shard_weights -- work[s] of every subtree: Eq. 13 for each of its
+ *   (4^(L-k) - 1) / 3 non-leaf boxes plus Eq. 14 for each of its leaves with
+ *   that leaf's particle count (the reading of Eq. 15), with n_c = 4,
+ *   n_IL = 27, n_nd = 9.
+ * petfmm_shard_comm -- expansion terms exchanged (both directions) between
+ *   two lateral neighbour subtrees (Eq. 11: sum over n = k+1..L of
+ *   alpha 2^(n-k) 4) and two diagonal neighbour subtrees (alpha 8 (L - k):
+ *   the corner boxes, four per level each way, as the interaction lists give
+ *   them; Eq. 12's printed form is garbled).  alpha: terms per box, e.g. p
+ *   complex numbers.
+ * petfmm_shard_partition -- assign the subtrees to nranks ranks
+ *   (1 <= nranks <= 4^k) as contiguous runs of their z-order, with the
+ *   largest run work as small as a contiguous split allows; owner[s] = rank.
+ *   ranks[r] summarises rank r: work, particles, subtrees, its Morton range
+ *   [first_subtree, last_subtree) and comm = the model's expansion terms
+ *   (alpha = 1) over the edges it cuts.
+ * petfmm_shard_halo -- what rank `rank` must receive from other ranks: the
+ *   leaves (Morton, level L) adjacent to its leaves that other ranks own (their
+ *   particles, for the near field), and the boxes (level, Morton) at levels
+ *   k+1..L in the interaction lists of its boxes that other ranks own (their
+ *   multipole expansions).  The level-k expansions of all subtrees are
+ *   all-gathered and the root tree evaluated by every rank, so they are not
+ *   listed.  Writes at most leaf_cap leaves and box_cap (level, box) pairs
+ *   and sets *nleaves, *nboxes to the full counts (call with caps 0 first to
+ *   size the arrays).
+ * All return PETFMM_OK or PETFMM_EINVAL.
+ */
+typedef struct {
+    double work;            /* Eq. 13-15 work of its subtrees */
+    double comm;            /* model expansion terms over its cut edges (alpha = 1) */
+    int64_t particles;
+    int32_t subtrees;
+    int32_t first_subtree;  /* its z-order run of level-k boxes: [first, last) */
+    int32_t last_subtree;
+} petfmm_shard_rank;
+
+int petfmm_shard_weights(int L, int k, int order, const uint32_t *leaf_counts, double *work);
+int petfmm_shard_comm(int L, int k, double alpha, double *lateral, double *diagonal);
+int petfmm_shard_partition(int L, int k, int order, const uint32_t *leaf_counts, int nranks,
+                           int32_t *owner, petfmm_shard_rank *ranks);
+int petfmm_shard_halo(int L, int k, const int32_t *owner, int rank, int32_t *leaves,
+                      int64_t leaf_cap, int32_t *boxes, int64_t box_cap, int64_t *nleaves,
+                      int64_t *nboxes);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: a thread-safe request loop with continuous batching.           */
 /* ---------------------------------------------------------------------- */
 typedef struct petfmm_server petfmm_server;
