@@ -606,14 +606,15 @@ __global__ void __launch_bounds__(256) k_pair_count(const Task *__restrict__ tas
 // items (inst, leaf A, direction d, 0) and their work class (targets x
 // sources, log2 in quarter steps, stored as 127 - class: heaviest first)
 // Estimated time of nt targets against ns sources in the pair kernel: the
-// target chunks it cuts (256/128/64/32, see pair_leaves) weighted by their
-// measured time per source step (8 packed, 4 packed, 2 and 1 targets per
-// lane: 10.3, 5.6, 3.4 and 2.5 relative units), times the source steps (32
-// per chunk of 32, 16 for a last chunk of at most 16).
+// target chunks it cuts (320/256/128/64/32, see pair_leaves) weighted by
+// their measured time per source step (10 and 8 packed, 4 packed, 2 and 1
+// targets per lane: 12.1, 10.3, 5.6, 3.4 and 2.5 relative units), times the
+// source steps (32 per chunk of 32, 16 for a last chunk of at most 16).
 __device__ __forceinline__ uint32_t pair_cost(uint32_t nt, uint32_t ns) {
     uint32_t c = 0;
     for (uint32_t r = nt; r > 0;) {
-        if (r >= 192) { c += 103; r = r > 256 ? r - 256 : 0; }
+        if (r >= 257) { c += 121; r = r > 320 ? r - 320 : 0; }
+        else if (r >= 192) { c += 103; r = r > 256 ? r - 256 : 0; }
         else if (r >= 96) { c += 56; r = r > 128 ? r - 128 : 0; }
         else if (r >= 33) { c += 34; r = r > 64 ? r - 64 : 0; }
         else { c += 25; r = r > 32 ? r - 32 : 0; }
@@ -764,22 +765,26 @@ __device__ __forceinline__ void source_pass(const float (&tx)[TPL], const float 
 // packed FP32x2 instructions (polynomial near-field factor only): the same
 // products per pair as source_pass, each packed instruction doing two of
 // them, so half the issue slots.  The reaction sums of a step run in the two
-// halves of a pair and are added before the source moves on.
+// halves of a pair and are added before the source moves on.  Signs are
+// folded out of the loop: the source travels as (-x, -y), the targets keep
+// U = -u and the reaction BV = -bv (round-to-nearest is symmetric in sign,
+// so the sums are bit for bit the negated ones), which saves the negated
+// copies of the strengths and one broadcast per step.
 template <int DEG, int H, int W>
 __device__ __forceinline__ void source_pass_x2(const float2 (&tx)[H], const float2 (&ty)[H],
-                                               const float2 (&tg)[H], const float2 (&ntg)[H],
-                                               float2 (&u)[H], float2 (&v)[H],
-                                               const float2 (&a2)[DEG + 1], float xs, float ys,
-                                               float gs, float &bu, float &bv, int lane) {
+                                               const float2 (&tg)[H], float2 (&U)[H],
+                                               float2 (&v)[H], const float2 (&a2)[DEG + 1],
+                                               float nxs, float nys, float gs, float &bu,
+                                               float &BV, int lane) {
     const int next = (lane & ~(W - 1)) | ((lane + 1) & (W - 1));
     bu = 0.f;
-    bv = 0.f;
+    BV = 0.f;
 #pragma unroll 2
     for (int k = 0; k < W; ++k) {
         // with K = (-dy, dx) g: u_a += g_s K, reaction u_b -= g_a K
-        const float2 nx = make_float2(-xs, -xs), ny = make_float2(-ys, -ys);
-        const float2 g2 = make_float2(gs, gs), ng2 = make_float2(-gs, -gs);
-        float2 bu2 = make_float2(bu, 0.f), bv2 = make_float2(bv, 0.f);
+        const float2 nx = make_float2(nxs, nxs), ny = make_float2(nys, nys);
+        const float2 g2 = make_float2(gs, gs);
+        float2 bu2 = make_float2(bu, 0.f), bv2 = make_float2(BV, 0.f);
 #pragma unroll
         for (int h = 0; h < H; ++h) {
             const float2 dx = __fadd2_rn(tx[h], nx), dy = __fadd2_rn(ty[h], ny);
@@ -788,22 +793,22 @@ __device__ __forceinline__ void source_pass_x2(const float2 (&tx)[H], const floa
 #pragma unroll
             for (int q = DEG - 1; q >= 0; --q) g = __ffma2_rn(g, r2, a2[q]);
             const float2 py = __fmul2_rn(dy, g), px = __fmul2_rn(dx, g);
-            u[h] = __ffma2_rn(ng2, py, u[h]);
+            U[h] = __ffma2_rn(g2, py, U[h]);
             v[h] = __ffma2_rn(g2, px, v[h]);
             bu2 = __ffma2_rn(tg[h], py, bu2);
-            bv2 = __ffma2_rn(ntg[h], px, bv2);
+            bv2 = __ffma2_rn(tg[h], px, bv2);
         }
         bu = bu2.x + bu2.y;
-        bv = bv2.x + bv2.y;
-        xs = __shfl_sync(0xffffffffu, xs, next);
-        ys = __shfl_sync(0xffffffffu, ys, next);
+        BV = bv2.x + bv2.y;
+        nxs = __shfl_sync(0xffffffffu, nxs, next);
+        nys = __shfl_sync(0xffffffffu, nys, next);
         gs = __shfl_sync(0xffffffffu, gs, next);
         bu = __shfl_sync(0xffffffffu, bu, next);
-        bv = __shfl_sync(0xffffffffu, bv, next);
+        BV = __shfl_sync(0xffffffffu, BV, next);
     }
     if (W < 32) {
         bu += __shfl_xor_sync(0xffffffffu, bu, 16);
-        bv += __shfl_xor_sync(0xffffffffu, bv, 16);
+        BV += __shfl_xor_sync(0xffffffffu, BV, 16);
     }
 }
 
@@ -875,14 +880,15 @@ __device__ __noinline__ void pair_chunk(const float4 *__restrict__ rec, uint32_t
 }
 
 // The same chunk with 2 H targets per lane held as H pairs (targets lane +
-// 64 h and lane + 64 h + 32), evaluated by source_pass_x2.
+// 64 h and lane + 64 h + 32), evaluated by source_pass_x2 (which keeps -u
+// and the reaction's -v; the signs are restored on the way out).
 template <int DEG, int H>
 __device__ __noinline__ void pair_chunk_x2(const float4 *__restrict__ rec, uint32_t a0,
                                            uint32_t ac, uint32_t aend, uint32_t b0, uint32_t nb,
                                            int ox, int oy, const float (&a)[DEG + 1], float cn,
                                            float2 *fwd, float2 *bwd, bool bwd_add, bool fwd_add,
                                            int lane) {
-    float2 tx[H], ty[H], tg[H], ntg[H], u[H], v[H];
+    float2 tx[H], ty[H], tg[H], U[H], v[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) {
         const uint32_t i0 = ac + lane + 64 * h, i1 = i0 + 32;
@@ -891,38 +897,37 @@ __device__ __noinline__ void pair_chunk_x2(const float4 *__restrict__ rec, uint3
         tx[h] = make_float2(r0.x, r1.x);
         ty[h] = make_float2(r0.y, r1.y);
         tg[h] = make_float2(r0.z, r1.z);
-        ntg[h] = make_float2(-r0.z, -r1.z);
-        u[h] = v[h] = make_float2(0.f, 0.f);
+        U[h] = v[h] = make_float2(0.f, 0.f);
     }
     float2 a2[DEG + 1];
 #pragma unroll
     for (int k = 0; k <= DEG; ++k) a2[k] = make_float2(a[k], a[k]);
     for (uint32_t bc = 0; bc < nb; bc += 32) {
         const SourceSlot ss = source_slot(rec, b0, bc, nb, ox, oy, lane);
-        float bu, bv;
+        float bu, BV;
         if (ss.half)
-            source_pass_x2<DEG, H, 16>(tx, ty, tg, ntg, u, v, a2, ss.xs, ss.ys, ss.gs, bu, bv,
-                                       lane);
+            source_pass_x2<DEG, H, 16>(tx, ty, tg, U, v, a2, -ss.xs, -ss.ys, ss.gs, bu, BV, lane);
         else
-            source_pass_x2<DEG, H, 32>(tx, ty, tg, ntg, u, v, a2, ss.xs, ss.ys, ss.gs, bu, bv,
-                                       lane);
+            source_pass_x2<DEG, H, 32>(tx, ty, tg, U, v, a2, -ss.xs, -ss.ys, ss.gs, bu, BV, lane);
         if (ss.hs && (!ss.half || lane < 16))
-            put2(bwd + ss.sb, make_float2(cn * bu, cn * bv), bwd_add);
+            put2(bwd + ss.sb, make_float2(cn * bu, -(cn * BV)), bwd_add);
     }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
         const uint32_t i0 = ac + lane + 64 * h, i1 = i0 + 32;
-        if (i0 < aend) put2(fwd + i0, make_float2(cn * u[h].x, cn * v[h].x), fwd_add);
-        if (i1 < aend) put2(fwd + i1, make_float2(cn * u[h].y, cn * v[h].y), fwd_add);
+        if (i0 < aend) put2(fwd + i0, make_float2(-(cn * U[h].x), cn * v[h].x), fwd_add);
+        if (i1 < aend) put2(fwd + i1, make_float2(-(cn * U[h].y), cn * v[h].y), fwd_add);
     }
 }
 
 // The pairs of blobs abeg .. aend - 1 of leaf A (from a0) with the nb blobs
-// of leaf B (from b0): A in chunks of 256, 128, 64 or 32 targets.  Leaf
+// of leaf B (from b0): A in chunks of 320, 256, 128, 64 or 32 targets.  Leaf
 // pairs take the largest chunk that the remaining targets fill to at least
-// three quarters (less padding than one fixed size; more targets per lane,
-// fewer shuffles per pair); a range of whole 32-blob chunks (exact) is cut
-// without padding.  The first chunk writes bwd (unless bwd_add), later ones
+// three quarters (for 320: more than 256, where one 320-chunk is faster
+// than 256 + a tail chunk); more targets per lane amortise the shuffles of
+// a step over more pairs (measured in isolation on GB300: 10 targets per
+// lane 0.776 of the FP32 peak, 8 per lane 0.727).  A range of whole 32-blob
+// chunks (exact) is cut without padding.  The first chunk writes bwd (unless bwd_add), later ones
 // add to it; fwd_add: the chunks add to fwd.
 template <int DEG, bool GENERAL>
 __device__ __forceinline__ void pair_leaves(const float4 *__restrict__ rec, uint32_t a0,
@@ -931,10 +936,15 @@ __device__ __forceinline__ void pair_leaves(const float4 *__restrict__ rec, uint
                                             float kappa, float split, float cn, float2 *fwd,
                                             float2 *bwd, bool bwd_add, bool fwd_add, bool exact,
                                             int lane) {
-    const uint32_t t8 = exact ? 256 : 192, t4 = exact ? 128 : 96, t2 = exact ? 64 : 33;
+    const uint32_t t10 = exact ? 320 : 257, t8 = exact ? 256 : 192, t4 = exact ? 128 : 96,
+                   t2 = exact ? 64 : 33;
     for (uint32_t ac = abeg; ac < aend; bwd_add = true) {
         const uint32_t rem = aend - ac;
-        if (!GENERAL && rem >= t8) {
+        if (!GENERAL && rem >= t10) {
+            pair_chunk_x2<DEG, 5>(rec, a0, ac, aend, b0, nb, ox, oy, a, cn, fwd, bwd, bwd_add,
+                                  fwd_add, lane);
+            ac += 320;
+        } else if (!GENERAL && rem >= t8) {
             pair_chunk_x2<DEG, 4>(rec, a0, ac, aend, b0, nb, ox, oy, a, cn, fwd, bwd, bwd_add,
                                   fwd_add, lane);
             ac += 256;
