@@ -341,6 +341,8 @@ def serving_leg(_lib, n_req=2000, seed=5, pool=96):
             "offered_particle_evals_per_s": evals / max(float(np.sum(gaps)), 1e-9),
             "rounds": int(st["rounds"]), "max_resident": int(st["max_active"]),
             "mean_resident": float(st["mean_active"]), "gpu_busy_frac": st["busy_ms"] / st["up_ms"],
+            "scheduler_ms": {k: round(st[k], 1) for k in ("admit_ms", "launch_ms", "wait_ms",
+                                                          "post_ms", "up_ms")},
             "requests_batched_with_others": int((shared >= 2).sum()),
             "queue_series": {"columns": ["second", "queued", "resident"], "rows": series},
             "layout": f"pool of {pool} seeded systems (Gaussian-patch lattice or 8-cluster, N "

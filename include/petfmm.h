@@ -318,8 +318,10 @@ typedef struct {
  * max_slots: most requests resident at once; max_queue: most waiting. */
 int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue,
                         petfmm_server **out);
-/* Queue a request; PETFMM_EBUSY if the queue is full, PETFMM_EINVAL, or
- * PETFMM_ENOMEM if the request alone exceeds the budget. */
+/* Queue a request; PETFMM_EBUSY if the queue is full, PETFMM_EINVAL,
+ * PETFMM_EDOMAIN if a position is not finite, or PETFMM_ENOMEM if the
+ * request alone exceeds the budget.  The host arrays are copied and the
+ * initial domain fitted here, in the caller's thread. */
 int petfmm_serve_submit(petfmm_server *s, const petfmm_request *req, uint64_t *ticket);
 /* PETFMM_ENOTREADY until the request is done; then fills *out. */
 int petfmm_serve_poll(petfmm_server *s, uint64_t ticket, petfmm_result *out);
@@ -336,6 +338,10 @@ typedef struct {
     double mean_active;   /* mean requests resident per round */
     double busy_ms;       /* time spent in rounds */
     double up_ms;         /* time since petfmm_serve_create */
+    /* scheduler-thread time by phase: admitting requests (device state,
+     * copies in), launching rounds, waiting for the GPU, and the work after
+     * a round (statuses, refitted domains, finished requests copied out) */
+    double admit_ms, launch_ms, wait_ms, post_ms;
 } petfmm_serve_counters;
 int petfmm_serve_stats(petfmm_server *s, petfmm_serve_counters *out);
 /* Per-round trace: for the first min(cap, count) rounds since creation, the

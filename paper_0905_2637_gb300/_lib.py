@@ -63,7 +63,9 @@ class ServeStats(ctypes.Structure):
                 ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("queued", ctypes.c_int32), ("max_active", ctypes.c_int32),
                 ("mean_active", ctypes.c_double), ("busy_ms", ctypes.c_double),
-                ("up_ms", ctypes.c_double)]
+                ("up_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                ("launch_ms", ctypes.c_double), ("wait_ms", ctypes.c_double),
+                ("post_ms", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

@@ -142,11 +142,20 @@ struct petfmm_server {
     double *dbox = nullptr, *hbox = nullptr;
     int box_cap = 0;
     cudaMemPool_t pool = nullptr;  // request state (see free_state)
+    // admissions run on their own stream while a round computes; the next
+    // round waits for their copies through ev_copy
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_copy = nullptr;
+    bool copies_pending = false;
     // counters (under mu)
     Clock::time_point t_create;
     uint64_t rounds = 0, submitted = 0, admitted = 0, completed = 0;
     int max_active = 0;
     double sum_active = 0.0, busy_ms = 0.0;
+    // host time of the worker by phase: admissions (allocation, copies to
+    // the device, domain), launching a round, waiting for it, and the work
+    // after it (statuses, domains, completions with their copies back)
+    double admit_ms = 0.0, launch_ms = 0.0, wait_ms = 0.0, post_ms = 0.0;
     std::vector<TraceSample> trace;  // one sample per round (its start)
 };
 
@@ -189,12 +198,16 @@ bool inside(const petfmm_domain &d, const double *b) {
     return b[0] >= d.x0 && b[1] >= d.y0 && b[2] <= d.x0 + d.width && b[3] <= d.y0 + d.width;
 }
 
+// Device state of an admitted request, from the server's pool, and its
+// initial positions and strengths copied in on the admission stream (the
+// host arrays live in the request until it finishes; the next round waits
+// for the copies).  The domain was fitted at submit time.
 int admit(petfmm_server *s, Req *r) {
     const int64_t n = r->spec.n;
     const size_t bytes = size_t(n > 0 ? n : 1) * sizeof(double);
     double **bufs[] = {&r->x, &r->y, &r->g, &r->u, &r->v, &r->xn, &r->yn};
     for (double **b : bufs) {
-        if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(b), bytes, s->pool, s->stream) !=
+        if (cudaMallocFromPoolAsync(reinterpret_cast<void **>(b), bytes, s->pool, s->cstream) !=
             cudaSuccess) {
             cudaGetLastError();
             free_state(s, r);
@@ -202,26 +215,16 @@ int admit(petfmm_server *s, Req *r) {
         }
     }
     if (n > 0) {
-        if (cudaMemcpyAsync(r->x, r->hx.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-            cudaMemcpyAsync(r->y, r->hy.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-            cudaMemcpyAsync(r->g, r->hg.data(), bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+        if (cudaMemcpyAsync(r->x, r->hx.data(), bytes, cudaMemcpyHostToDevice, s->cstream) != cudaSuccess ||
+            cudaMemcpyAsync(r->y, r->hy.data(), bytes, cudaMemcpyHostToDevice, s->cstream) != cudaSuccess ||
+            cudaMemcpyAsync(r->g, r->hg.data(), bytes, cudaMemcpyHostToDevice, s->cstream) != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamSynchronize(s->cstream);  // no copy in flight into what is freed
             free_state(s, r);
             return PETFMM_ECUDA;
         }
-        // host copies stay valid until the stream is synchronised below
-        if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
-            free_state(s, r);
-            return PETFMM_ECUDA;
-        }
-        double bx0 = r->hx[0], by0 = r->hy[0], bx1 = bx0, by1 = by0;
-        for (int64_t i = 1; i < n; ++i) {
-            bx0 = std::min(bx0, r->hx[i]); bx1 = std::max(bx1, r->hx[i]);
-            by0 = std::min(by0, r->hy[i]); by1 = std::max(by1, r->hy[i]);
-        }
-        r->dom = fit_domain(bx0, by0, bx1, by1);
-    } else {
-        r->dom = petfmm_domain{0.0, 0.0, 1.0};
     }
+    s->copies_pending = true;
     r->levels = r->spec.levels > 0 ? r->spec.levels
                                    : petfmm_choose_levels(n, r->spec.order, r->spec.sigma, &r->dom);
     if (r->levels < 1) {
@@ -250,8 +253,22 @@ void finish(petfmm_server *s, Req *r, int status) {
 }
 
 // One round: one evaluation for every resident request, then its RK2 stage.
-void run_round(petfmm_server *s, std::vector<Req *> &act) {
+// launch_round enqueues it (the scheduler then admits new requests while the
+// GPU computes); complete_round waits for it and handles its results.
+struct Round {
+    Clock::time_point t0, t1;
+    int rc64 = 0, rcmx = 0;
+    bool any64 = false, anymx = false;
+};
+
+void launch_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
     const Clock::time_point t0 = Clock::now();
+    rd.t0 = t0;
+    if (s->copies_pending) {  // the copies of the requests admitted last time
+        cudaEventRecord(s->ev_copy, s->cstream);
+        cudaStreamWaitEvent(s->stream, s->ev_copy, 0);
+        s->copies_pending = false;
+    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->rounds++;
@@ -277,8 +294,10 @@ void run_round(petfmm_server *s, std::vector<Req *> &act) {
         if (r->spec.precision == PETFMM_FP64) { in64.push_back(it); r64.push_back(r); }
         else { inmx.push_back(it); rmx.push_back(r); }
     }
-    int rc64 = in64.empty() ? 0 : petfmm_evaluate_batch(s->ctx64, int(in64.size()), in64.data());
-    int rcmx = inmx.empty() ? 0 : petfmm_evaluate_batch(s->ctxmx, int(inmx.size()), inmx.data());
+    rd.any64 = !in64.empty();
+    rd.anymx = !inmx.empty();
+    rd.rc64 = in64.empty() ? 0 : petfmm_evaluate_batch(s->ctx64, int(in64.size()), in64.data());
+    rd.rcmx = inmx.empty() ? 0 : petfmm_evaluate_batch(s->ctxmx, int(inmx.size()), inmx.data());
     if ((int)act.size() > s->box_cap) {
         cudaFree(s->dbox);
         cudaFreeHost(s->hbox);
@@ -301,9 +320,16 @@ void run_round(petfmm_server *s, std::vector<Req *> &act) {
     if (!act.empty())
         k_bbox_final<<<unsigned(act.size()), 32, 0, s->stream>>>(dpart, s->dbox);
     cudaMemcpyAsync(s->hbox, s->dbox, act.size() * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    int st64 = in64.empty() ? 0 : petfmm_sync(s->ctx64);
-    int stmx = inmx.empty() ? 0 : petfmm_sync(s->ctxmx);
+    rd.t1 = Clock::now();
+}
+
+void complete_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
+    const int rc64 = rd.rc64, rcmx = rd.rcmx;
+    const Clock::time_point t0 = rd.t0, t1 = Clock::now();
+    int st64 = rd.any64 ? petfmm_sync(s->ctx64) : 0;
+    int stmx = rd.anymx ? petfmm_sync(s->ctxmx) : 0;
     cudaError_t e = cudaStreamSynchronize(s->stream);
+    const Clock::time_point t2 = Clock::now();
     // A finished request belongs to the caller from the moment finish() marks
     // it done (a poll may release it at once), so it is dropped from the
     // active list here and never touched again.
@@ -334,8 +360,12 @@ void run_round(petfmm_server *s, std::vector<Req *> &act) {
         keep.push_back(r);
     }
     act.swap(keep);
+    const Clock::time_point t3 = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
-    s->busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    s->busy_ms += std::chrono::duration<double, std::milli>(t3 - t0).count();
+    s->launch_ms += std::chrono::duration<double, std::milli>(rd.t1 - t0).count();
+    s->wait_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
+    s->post_ms += std::chrono::duration<double, std::milli>(t3 - t2).count();
 }
 
 void worker_main(petfmm_server *s) {
@@ -364,6 +394,13 @@ void worker_main(petfmm_server *s) {
                 newly.push_back(r);
             }
         }
+        // the resident requests' round goes to the GPU first; the new ones are
+        // admitted (device state, copies on the admission stream) while it
+        // computes, and join the next round
+        Round rd;
+        if (!act.empty()) launch_round(s, act, rd);
+        const Clock::time_point ta = Clock::now();
+        std::vector<Req *> joined;
         for (Req *r : newly) {
             int rc = admit(s, r);
             r->t_admit = Clock::now();
@@ -379,9 +416,14 @@ void worker_main(petfmm_server *s) {
                 finish(s, r, PETFMM_OK);
                 continue;
             }
-            act.push_back(r);
+            joined.push_back(r);
         }
-        if (!act.empty()) run_round(s, act);
+        if (!newly.empty()) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->admit_ms += std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
+        }
+        if (!act.empty()) complete_round(s, act, rd);
+        act.insert(act.end(), joined.begin(), joined.end());
     }
 }
 
@@ -404,8 +446,13 @@ int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, p
     s->max_slots = max_slots;
     s->max_queue = max_queue;
     if (cudaGetDevice(&s->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_copy, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (s->ev_copy) cudaEventDestroy(s->ev_copy);
+        if (s->cstream) cudaStreamDestroy(s->cstream);
+        if (s->stream) cudaStreamDestroy(s->stream);
         delete s;
         return PETFMM_ECUDA;
     }
@@ -419,6 +466,8 @@ int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, p
             cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
             cudaGetLastError();
             if (s->pool) cudaMemPoolDestroy(s->pool);
+            cudaEventDestroy(s->ev_copy);
+            cudaStreamDestroy(s->cstream);
             cudaStreamDestroy(s->stream);
             delete s;
             return PETFMM_ECUDA;
@@ -431,6 +480,8 @@ int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, p
     if (rc != PETFMM_OK) {
         if (s->ctx64) petfmm_destroy(s->ctx64);
         cudaMemPoolDestroy(s->pool);
+        cudaEventDestroy(s->ev_copy);
+        cudaStreamDestroy(s->cstream);
         cudaStreamDestroy(s->stream);
         delete s;
         return rc;
@@ -458,6 +509,24 @@ int petfmm_serve_submit(petfmm_server *s, const petfmm_request *req, uint64_t *t
     } catch (...) {
         delete r;
         return PETFMM_ENOMEM;
+    }
+    // the initial domain, here in the caller's thread rather than in the
+    // scheduler's: a square 1.25 times the bounding box
+    if (q.n > 0) {
+        double bx0 = r->hx[0], by0 = r->hy[0], bx1 = bx0, by1 = by0;
+        for (int64_t i = 1; i < q.n; ++i) {
+            bx0 = std::min(bx0, r->hx[size_t(i)]);
+            bx1 = std::max(bx1, r->hx[size_t(i)]);
+            by0 = std::min(by0, r->hy[size_t(i)]);
+            by1 = std::max(by1, r->hy[size_t(i)]);
+        }
+        if (!(std::isfinite(bx0) && std::isfinite(bx1) && std::isfinite(by0) && std::isfinite(by1))) {
+            delete r;
+            return PETFMM_EDOMAIN;
+        }
+        r->dom = fit_domain(bx0, by0, bx1, by1);
+    } else {
+        r->dom = petfmm_domain{0.0, 0.0, 1.0};
     }
     // admission estimate with the level the request will use (worst case 10)
     int L = q.levels > 0 ? q.levels : 10;
@@ -527,6 +596,10 @@ int petfmm_serve_stats(petfmm_server *s, petfmm_serve_counters *out) {
     out->max_active = s->max_active;
     out->mean_active = s->rounds ? s->sum_active / double(s->rounds) : 0.0;
     out->busy_ms = s->busy_ms;
+    out->admit_ms = s->admit_ms;
+    out->launch_ms = s->launch_ms;
+    out->wait_ms = s->wait_ms;
+    out->post_ms = s->post_ms;
     out->up_ms = std::chrono::duration<double, std::milli>(Clock::now() - s->t_create).count();
     return PETFMM_OK;
 }
@@ -555,8 +628,11 @@ int petfmm_serve_destroy(petfmm_server *s) {
         free_state(s, kv.second);
         delete kv.second;
     }
+    if (s->cstream) cudaStreamSynchronize(s->cstream);
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->pool) cudaMemPoolDestroy(s->pool);
+    if (s->ev_copy) cudaEventDestroy(s->ev_copy);
+    if (s->cstream) cudaStreamDestroy(s->cstream);
     if (s->ctx64) petfmm_destroy(s->ctx64);
     if (s->ctxmx) petfmm_destroy(s->ctxmx);
     if (s->dbox) cudaFree(s->dbox);
