@@ -499,6 +499,15 @@ enum {
                                   level >= 5; 2: row units (one child class, a segment
                                   of a parent row) at levels >= 8 and no blocks.
                                   Results differ by FP32 rounding only. */
+    PETFMM_OPT_TC_PIPE = 14,   /* mixed path, block tensor-core M2L: 1: one staging buffer
+                                  for the source expansions (a source class is split after
+                                  every MMA so far is done; two stages per offset, two CTAs
+                                  per SM, in launches of >= 2048 blocks); 2: two staging
+                                  buffers, the next class split while the current one
+                                  multiplies (one stage per offset, one CTA per SM; p <= 20);
+                                  0 (default): 2 in launches under 2048 blocks where it
+                                  fits, else 1.  The two differ by FP32 rounding when the
+                                  stages per offset differ. */
     PETFMM_OPT_KERNEL = 12     /* the sum the context evaluates (the kernel parameter of
                                   the paper's Evaluator, Sec. 6.1):
                                   PETFMM_KERNEL_VORTEX (default) the blob velocity of

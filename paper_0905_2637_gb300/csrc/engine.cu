@@ -118,6 +118,7 @@ struct petfmm_ctx {
     bool p2p_pairs = true;  // mixed path: neighbouring leaves pairwise (PETFMM_OPT_P2P_PAIRS)
     int kernel = KERNEL_VORTEX;  // PETFMM_OPT_KERNEL
     int tc_blocks = 0;           // PETFMM_OPT_TC_BLOCKS: 0 automatic, 1 always, 2 never
+    int tc_pipe = 0;             // PETFMM_OPT_TC_PIPE: 0 automatic, 1 single A, 2 double A
     bool poison = false;
     bool m2l_tc = true;
     // measured on GB300 (clustered 16M and lattice 1M blobs): 128-cell units
@@ -603,7 +604,7 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     k.put(pl.tc_smem); k.put(pl.tcb_pmax); k.put(grid);
     k.put(c->precision); k.put(c->dtype); k.put(c->timing); k.put(c->p2p_mode); k.put(c->poison);
     k.put(c->tc_dense_pct); k.put(c->spin_limit); k.put(c->p2p_pairs); k.put(c->kernel);
-    k.put(c->tc_blocks);
+    k.put(c->tc_blocks); k.put(c->tc_pipe);
     for (const DevBuf *b : {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                             &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
                             &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount,
@@ -853,7 +854,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         PF_CUDA(launch_m2l_tcb(dtask + pl.m2l_tcb.first, pl.m2l_tcb.count, pl.m2l_tcb.nblocks,
                                dinst, start, static_cast<const float2 *>(c->me.p),
                                static_cast<float2 *>(c->le.p), ucount + pl.m2l_tc.nblocks,
-                               c->tc_dense_pct, pl.tcb_pmax, spin,
+                               c->tc_dense_pct, pl.tcb_pmax, spin, c->tc_pipe,
                                reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
     }
     {
@@ -1430,6 +1431,10 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
         case PETFMM_OPT_TC_BLOCKS:
             if (value < 0 || value > 2) return PETFMM_EINVAL;
             c->tc_blocks = int(value);
+            return PETFMM_OK;
+        case PETFMM_OPT_TC_PIPE:
+            if (value < 0 || value > 2) return PETFMM_EINVAL;
+            c->tc_pipe = int(value);
             return PETFMM_OK;
         case PETFMM_OPT_KERNEL:
             if (value != PETFMM_KERNEL_VORTEX && value != PETFMM_KERNEL_LAPLACE)

@@ -117,7 +117,7 @@ void host_m2l_tcb_images(int p, int kernel, std::vector<float> &out);
 cudaError_t launch_m2l_tcb(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                            const uint32_t *start, const float2 *me, float2 *le,
                            const uint32_t *ucount, int dense_pct, int pmax, long long spin_limit,
-                           int *status, cudaStream_t st, uint64_t *launches);
+                           int pipe, int *status, cudaStream_t st, uint64_t *launches);
 int64_t m2l_tc_units(int level, int segmax);
 size_t m2l_tc_smem_bytes(int p, int seg);
 int m2l_tc_seg(int level, int segmax);

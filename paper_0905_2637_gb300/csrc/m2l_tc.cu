@@ -401,7 +401,7 @@ __host__ __device__ __forceinline__ int tcb_op(int c, int cs, int dx, int dy) {
     return (ax > ay ? ax : ay) >= 2 ? m2l_op_index(ddx, ddy) : -1;
 }
 
-template <int S>
+template <int S, bool DA>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
     const Task *__restrict__ tasks, int ntasks, const InstDesc *__restrict__ insts,
     const uint32_t *__restrict__ start, const float2 *__restrict__ me, float2 *__restrict__ le,
@@ -431,14 +431,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
     const size_t aplane = size_t(KG) * TCB_HALO * 4;  // floats of A hi (or lo)
     const size_t bplane = size_t(Kpad) * NC;          // floats of one B image (hi or lo)
     const size_t bstage = size_t(3 - S) * bplane;     // floats of one stage's images
-    float *A = reinterpret_cast<float *>(smem);       // hi, then lo
-    float *B = A + 2 * aplane;                        // 2 buffers of one stage
+    // DA: two A buffers (a source class is split into one while the other's
+    // MMAs run); each holds hi, then lo
+    constexpr int NA = DA ? 2 : 1;
+    float *A = reinterpret_cast<float *>(smem);       // hi, then lo (then the second buffer)
+    float *B = A + NA * 2 * aplane;                   // 2 buffers of one stage
     // zero the K padding of every staged cell once (never overwritten)
     for (int i = tid; i < TCB_HALO * (Kpad - K2); i += TC_THREADS) {
         const int r = i / (Kpad - K2), k = K2 + i % (Kpad - K2);
         const size_t o = (size_t(k >> 2) * TCB_HALO + r) * 4 + (k & 3);
-        A[o] = 0.f;
-        A[aplane + o] = 0.f;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            A[a * 2 * aplane + o] = 0.f;
+            A[a * 2 * aplane + aplane + o] = 0.f;
+        }
     }
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
@@ -500,14 +506,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
     // flight per thread before the first is used
     const uint32_t inv_p = ((1u << 20) + uint32_t(p) - 1) / uint32_t(p);
     constexpr int SB = 8;
-    auto split = [&](int cs) {
-        float *hi = A, *lo = A + aplane;
+    auto split = [&](int cs, int buf, int t0, int nt) {
+        float *hi = A + size_t(buf) * 2 * aplane, *lo = hi + aplane;
         const int total = TCB_HALO * p;
-        for (int e0 = tid; e0 < total; e0 += SB * TC_THREADS) {
+        for (int e0 = t0; e0 < total; e0 += SB * nt) {
             float2 v[SB];
 #pragma unroll
             for (int u = 0; u < SB; ++u) {
-                const int e = e0 + u * TC_THREADS;
+                const int e = e0 + u * nt;
                 v[u] = make_float2(0.f, 0.f);
                 if (e < total) {
                     const int q = int((uint32_t(e) * inv_p) >> 20), k = e - q * p;
@@ -520,7 +526,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
             }
 #pragma unroll
             for (int u = 0; u < SB; ++u) {
-                const int e = e0 + u * TC_THREADS;
+                const int e = e0 + u * nt;
                 if (e >= total) break;
                 const int q = int((uint32_t(e) * inv_p) >> 20), k = e - q * p;
                 const float hr = tf32_hi(v[u].x), him = tf32_hi(v[u].y);
@@ -555,62 +561,94 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
     };
     bool ok = true;
     if (ng > 0) {
-        split(gl[0] / 9);
+        split(gl[0] / 9, 0, tid, TC_THREADS);
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
     }
-    for (int h = 0; h < nh && ok; ++h) {
-        if (tid == 0 && ok0) {
-            if (h == 0) copy_b(0);
-            // stage h + 1's image goes to buffer (h + 1) & 1, last read by
-            // stage h - 1; it lands while stage h multiplies
-            if (h + 1 < nh) {
-                wait_mma(h - 1);
-                if (ok0) copy_b(h + 1);
-            }
-            if (ok0) {
-                ok0 = mbar_wait(smem_addr(&bbar[h & 1]), uint32_t(h >> 1) & 1u, spin_limit);
-                if (ok0) landed = h;
-            }
-            if (ok0) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const int g = h / S;
-                const int dy = (gl[g] % 9) / 3 - 1, dx = gl[g] % 3 - 1;
-                const uint32_t ahi = smem_addr(A), alo = ahi + uint32_t(aplane * 4);
-                const uint32_t bimg_s = smem_addr(B + size_t(h & 1) * bstage);
-                const uint64_t sa = (2 * LBO_A) >> 4, sb = (2 * LBO_B) >> 4;
-                const uint64_t db = mma_desc(bimg_s, LBO_B, SBO_B);
-                const uint64_t dbl = mma_desc(bimg_s + uint32_t(bplane * 4), LBO_B, SBO_B);
-                // target cell (x, y) reads staged cell (x + 1 + dx, y + 1 + dy)
-                const uint32_t cell0 = uint32_t((1 + dy) * TCB_HX + 1 + dx) * 16;
-                const uint64_t dah = mma_desc(ahi + cell0, LBO_A, SBO_A);
-                const uint64_t dal = mma_desc(alo + cell0, LBO_A, SBO_A);
-                uint32_t acc = issued >= 0 ? 1u : 0u;  // the unit's first product overwrites
-                for (int ks = 0; ks < Kpad / 8; ++ks) {
-                    if (S == 1) {
-                        mma_tf32(tbase, dah + ks * sa, db + ks * sb, idesc, acc);
-                        mma_tf32(tbase, dah + ks * sa, dbl + ks * sb, idesc, 1u);
-                        mma_tf32(tbase, dal + ks * sa, db + ks * sb, idesc, 1u);
-                    } else {
-                        // B hi: A_hi B_hi + A_lo B_hi; B lo: A_hi B_lo
-                        mma_tf32(tbase, dah + ks * sa, db + ks * sb, idesc, acc);
-                        if (!(h & 1)) mma_tf32(tbase, dal + ks * sa, db + ks * sb, idesc, 1u);
-                    }
-                    acc = 1u;
-                }
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_addr(&mbar[h & 1])));
-                issued = h;
-            }
+    // Thread 0: stage h, its MMAs reading A buffer abuf.  They are issued
+    // as soon as stage h's images have landed, queued behind stage h - 1's
+    // (so the tensor core does not drain between stages); then, once stage
+    // h - 1 is done, stage h + 1's images go to the buffer it read, to land
+    // while stage h multiplies.
+    auto issue_stage = [&](int h, int abuf) {
+        if (h == 0) copy_b(0);
+        if (h + 1 < nh && ok0) {
+            wait_mma(h - 1);
+            if (ok0) copy_b(h + 1);
         }
+        if (ok0) {
+            ok0 = mbar_wait(smem_addr(&bbar[h & 1]), uint32_t(h >> 1) & 1u, spin_limit);
+            if (ok0) landed = h;
+        }
+        if (ok0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int g = h / S;
+            const int dy = (gl[g] % 9) / 3 - 1, dx = gl[g] % 3 - 1;
+            const uint32_t ahi = smem_addr(A + size_t(abuf) * 2 * aplane),
+                           alo = ahi + uint32_t(aplane * 4);
+            const uint32_t bimg_s = smem_addr(B + size_t(h & 1) * bstage);
+            const uint64_t sa = (2 * LBO_A) >> 4, sb = (2 * LBO_B) >> 4;
+            const uint64_t db = mma_desc(bimg_s, LBO_B, SBO_B);
+            const uint64_t dbl = mma_desc(bimg_s + uint32_t(bplane * 4), LBO_B, SBO_B);
+            const uint32_t cell0 = uint32_t((1 + dy) * TCB_HX + 1 + dx) * 16;
+            const uint64_t dah = mma_desc(ahi + cell0, LBO_A, SBO_A);
+            const uint64_t dal = mma_desc(alo + cell0, LBO_A, SBO_A);
+            uint32_t acc = issued >= 0 ? 1u : 0u;
+            for (int ks = 0; ks < Kpad / 8; ++ks) {
+                if (S == 1) {
+                    mma_tf32(tbase, dah + ks * sa, db + ks * sb, idesc, acc);
+                    mma_tf32(tbase, dah + ks * sa, dbl + ks * sb, idesc, 1u);
+                    mma_tf32(tbase, dal + ks * sa, db + ks * sb, idesc, 1u);
+                } else {
+                    mma_tf32(tbase, dah + ks * sa, db + ks * sb, idesc, acc);
+                    if (!(h & 1)) mma_tf32(tbase, dal + ks * sa, db + ks * sb, idesc, 1u);
+                }
+                acc = 1u;
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&mbar[h & 1])));
+            issued = h;
+        }
+    };
+    if constexpr (DA) {
+        // One source class at a time: thread 0 issues the class's stages from
+        // A buffer cur while warps 1-7 split the next class into the other
+        // buffer.  That buffer's last readers are the previous class's MMAs:
+        // thread 0 first queues this class's first stage behind them, then
+        // waits for them, and only then lets the splitters in.
+        int cur = 0;
+        for (int h0 = 0; h0 < nh && ok;) {
+            int h1 = h0 + S;
+            while (h1 < nh && gl[h1 / S] / 9 == gl[h0 / S] / 9) h1 += S;
+            if (tid == 0 && ok0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                issue_stage(h0, cur);
+                if (ok0) wait_mma(h0 - 1);
+            }
+            ok = __syncthreads_and(tid != 0 || ok0);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0) {
+                for (int h = h0 + 1; h < h1 && ok0; ++h) issue_stage(h, cur);
+            } else if (warp > 0 && h1 < nh) {
+                split(gl[h1 / S] / 9, cur ^ 1, tid - 32, TC_THREADS - 32);
+                asm volatile("fence.proxy.async.shared::cta;");
+            }
+            ok = __syncthreads_and(tid != 0 || ok0);
+            cur ^= 1;
+            h0 = h1;
+        }
+    }
+    for (int h = 0; h < (DA ? 0 : nh) && ok; ++h) {
+        if (tid == 0 && ok0) issue_stage(h, 0);
         // a new source class: split it into A once every MMA so far is done
         if (h + 1 < nh && (h + 1) % S == 0 && gl[(h + 1) / S] / 9 != gl[h / S] / 9) {
             if (tid == 0 && ok0) wait_mma(h);
             ok = __syncthreads_and(tid != 0 || ok0);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            split(gl[(h + 1) / S] / 9);
+            split(gl[(h + 1) / S] / 9, 0, tid, TC_THREADS);
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
         }
@@ -669,11 +707,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tcb(
 constexpr int64_t kTcbTwoStageUnits = 2048;
 static int tcb_stages(int64_t nblocks) { return nblocks >= kTcbTwoStageUnits ? 2 : 1; }
 
-static size_t tcb_smem_bytes(int p, int S) {
+static size_t tcb_smem_bytes(int p, int S, bool da = false) {
     const int K2 = 2 * p, Kpad = (K2 + 7) & ~7, NW = (K2 + 7) & ~7;
-    // A hi and lo of one staged class; two buffers of one stage's B images
-    return size_t(2) * (Kpad / 4) * TCB_HALO * 16 + size_t(2) * (3 - S) * Kpad * (4 * NW) * 4;
+    // A hi and lo of one staged class (two with da); two buffers of one
+    // stage's B images
+    return size_t(da ? 4 : 2) * (Kpad / 4) * TCB_HALO * 16 +
+           size_t(2) * (3 - S) * Kpad * (4 * NW) * 4;
 }
+
+// Most dynamic shared memory a block unit may take (plus the static part).
+constexpr size_t kTcbSmemMax = size_t(220) * 1024;
 
 size_t m2l_tcb_smem_bytes(int p) { return tcb_smem_bytes(p, 1); }
 
@@ -723,11 +766,22 @@ void host_m2l_tcb_images(int p, int kernel, std::vector<float> &out) {
 cudaError_t launch_m2l_tcb(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
                            const uint32_t *start, const float2 *me, float2 *le,
                            const uint32_t *ucount, int dense_pct, int pmax, long long spin_limit,
-                           int *status, cudaStream_t st, uint64_t *launches) {
+                           int pipe, int *status, cudaStream_t st, uint64_t *launches) {
     if (nblocks <= 0) return cudaSuccess;
-    const int S = tcb_stages(nblocks);
-    const size_t smem_bytes = tcb_smem_bytes(pmax, S);
-    auto k = S == 2 ? k_m2l_tcb<2> : k_m2l_tcb<1>;
+    // pipe 2: double-buffered A, one stage per offset (if it fits); 1: the
+    // single A, stages by launch size; 0: automatic
+    // (measured on GB300, M2L stage: two CTAs per SM with two stages per
+    // offset beat one CTA with the double buffer in launches of >= 2048
+    // blocks -- Lamb-Oseen 1.05 against 1.16 ms, clustered-16M 0.36 against
+    // 0.38 ms -- while in smaller launches, one CTA per SM either way, the
+    // double buffer gains: lattice-1M 0.188 -> 0.184 ms)
+    const bool da_fits = tcb_smem_bytes(pmax, 1, true) <= kTcbSmemMax;
+    const bool da = pipe == 2   ? da_fits
+                    : pipe == 1 ? false
+                                : da_fits && tcb_stages(nblocks) == 1;
+    const int S = da ? 1 : tcb_stages(nblocks);
+    const size_t smem_bytes = tcb_smem_bytes(pmax, S, da);
+    auto k = da ? k_m2l_tcb<1, true> : S == 2 ? k_m2l_tcb<2, false> : k_m2l_tcb<1, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem_bytes));
     if (e != cudaSuccess) return e;

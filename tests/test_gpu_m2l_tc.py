@@ -13,11 +13,12 @@ from paper_0905_2637_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, tc, L=None, p=None, dense_pct=None, blocks=0):
+def _run(w, tc, L=None, p=None, dense_pct=None, blocks=0, pipe=0):
     _lib = G.lib()
     ctx = _lib.Context(w.domain, L or w.L, p or w.p, w.sigma, precision="mixed", dtype=w.dtype)
     ctx.set_option(_lib.PETFMM_OPT_M2L_TC, 1 if tc else 0)
     ctx.set_option(_lib.PETFMM_OPT_TC_BLOCKS, blocks)
+    ctx.set_option(_lib.PETFMM_OPT_TC_PIPE, pipe)
     if dense_pct is not None:
         ctx.set_option(_lib.PETFMM_OPT_TC_DENSE, dense_pct)
     ctx.set_option(_lib.PETFMM_OPT_POISON, 1)
@@ -40,6 +41,20 @@ def test_tensor_core_m2l_matches_simt_and_fp64(L, n, frac, p, blocks):
     assert G.rel_l2(u_tc, v_tc, u64, v64) <= 1e-5
     assert G.rel_l2(u_tc, v_tc, u_si, v_si) <= 1e-5
     assert np.all(np.isfinite(u_tc)) and np.all(np.isfinite(v_tc))
+
+
+@pytest.mark.parametrize("p", [8, 12, 17])
+def test_block_pipelines_agree(p):
+    """One staging buffer (two stages per offset when the launch is large) and
+    two staging buffers (one stage per offset): the same products in another
+    order, so FP32 rounding apart; both against the FP64 FMM."""
+    w = W.tiny(400_000, 77 + p, L=9, p=p, clustered_frac=0.5)
+    u1, v1 = _run(w, tc=True, blocks=1, pipe=1)
+    u2, v2 = _run(w, tc=True, blocks=1, pipe=2)
+    u64, v64 = G.run(w, "fp64")
+    for u, v in ((u1, v1), (u2, v2)):
+        assert np.all(np.isfinite(u)) and G.rel_l2(u, v, u64, v64) <= 1e-5
+    assert G.rel_l2(u2, v2, u1, v1) <= 2e-6
 
 
 @pytest.mark.parametrize("blocks", [1, 2])
