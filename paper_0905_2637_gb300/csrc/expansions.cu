@@ -463,13 +463,31 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m_reg(
         float2 acc[PM];
 #pragma unroll
         for (int k = 0; k < PM; ++k) acc[k] = make_float2(0.f, 0.f);
-        // two blobs per lane per step (two independent power chains), and the
-        // next step's two records requested before this step's arithmetic:
-        // up to four 16-byte loads in flight per lane
+        // Leaves of more than 32 blobs: two blobs per lane per step (two
+        // independent power chains), and the next step's two records
+        // requested before this step's arithmetic: up to four 16-byte loads
+        // in flight per lane.  Smaller leaves take one step of one blob per
+        // lane (a second chain would only add padding).
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 na = s0 + lane < s1 ? rec[s0 + lane] : z4;
-        float4 nb = s0 + 32 + lane < s1 ? rec[s0 + 32 + lane] : z4;
-        for (uint32_t c0 = s0; c0 < s1; c0 += 64) {
+        if (s1 - s0 <= 32) {
+            const float4 r = s0 + lane < s1 ? rec[s0 + lane] : z4;
+            float2 w = make_float2(r.z, 0.f);
+            const float2 z = make_float2(r.x, r.y);
+#pragma unroll
+            for (int k = 0; k < PM; ++k) {
+                if (k < p) {
+                    acc[k].x += w.x;
+                    acc[k].y += w.y;
+                    w = cmul(w, z);
+                }
+            }
+        }
+        float4 na = z4, nb = z4;
+        if (s1 - s0 > 32) {
+            na = rec[s0 + lane];
+            nb = s0 + 32 + lane < s1 ? rec[s0 + 32 + lane] : z4;
+        }
+        for (uint32_t c0 = s0; s1 - s0 > 32 && c0 < s1; c0 += 64) {
             const float4 ra = na, rb = nb;
             const uint32_t jn = c0 + 64 + lane;
             na = jn < s1 ? rec[jn] : z4;
