@@ -437,6 +437,9 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m(
     }
 }
 
+// Leaves of at most this many blobs are summed by one lane each (k_p2m_reg).
+constexpr uint32_t P2M_LANE_MAX = 16;
+
 // Mixed path, p <= PM: each lane keeps the running sums of its particles'
 // gamma zeta^k in registers over all chunks of the leaf, and the warp adds
 // the 32 lanes' sums once per leaf (transposed through shared memory, lane k
@@ -450,16 +453,69 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m_reg(
     __shared__ float2 buf[P2M_WARPS][32 * SP];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t nocc = ctrl[CTRL_NOCC];
-    const uint32_t nwarps = gridDim.x * P2M_WARPS;
-    for (uint32_t i = blockIdx.x * P2M_WARPS + wid; i < nocc; i += nwarps) {
+    const uint32_t gw = blockIdx.x * P2M_WARPS + wid, nwarps = gridDim.x * P2M_WARPS;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // leaf range of occupied-leaf entry i (empty in the checked build when
+    // it lies outside its instance)
+    auto range = [&](uint32_t i, const InstDesc *&dp, uint32_t &m, uint32_t &s0, uint32_t &s1) {
         const uint2 e = occ[i];
-        const InstDesc &d = insts[e.x];
+        dp = insts + e.x;
+        m = e.y;
+        s0 = start[dp->soff + m];
+        s1 = start[dp->soff + m + 1];
+        if (!(PF_IN(m, int64_t(1) << (2 * dp->L)) && PF_IN(int64_t(s0) - dp->poff, dp->n + 1) &&
+              PF_IN(int64_t(s1) - dp->poff, dp->n + 1)) || s1 < s0)
+            s1 = s0;
+    };
+    // 1. Leaves of at most P2M_LANE_MAX blobs, one per lane, 32 entries per
+    //    warp at a time: the lane sums its few blobs' series by itself and
+    //    writes the p coefficients (a warp and a 32-row reduction per leaf
+    //    of one or a few blobs would be mostly idle).
+    for (uint32_t base = gw * 32; base < nocc; base += nwarps * 32) {
+        const uint32_t i = base + lane;
+        if (i >= nocc) continue;
+        const InstDesc *dp;
+        uint32_t m, s0, s1;
+        range(i, dp, m, s0, s1);
+        if (s1 - s0 > P2M_LANE_MAX) continue;
+        const InstDesc &d = *dp;
+        const int p = d.p;
+        float2 acc[PM];
+#pragma unroll
+        for (int k = 0; k < PM; ++k) acc[k] = make_float2(0.f, 0.f);
+        for (uint32_t j = s0; j < s1; ++j) {
+            const float4 r = rec[j];
+            float2 w = make_float2(r.z, 0.f);
+            const float2 z = make_float2(r.x, r.y);
+#pragma unroll
+            for (int k = 0; k < PM; ++k) {
+                if (k < p) {
+                    acc[k].x += w.x;
+                    acc[k].y += w.y;
+                    w = cmul(w, z);
+                }
+            }
+        }
+        const uint32_t ix = compact_bits(m), iy = compact_bits(m >> 1);
+        float2 *dst = me + d.eoff + (lvl_off(d.L) + box_index(d.L, ix, iy)) * p;
+        const bool lap = d.kernel == KERNEL_LAPLACE;
+#pragma unroll
+        for (int k = 0; k < PM; ++k) {
+            if (k < p) {
+                // Laplace kernel: a_k = -(1/k) sum q zeta^k for k >= 1
+                const float sc = (lap && k) ? -1.0f / float(k) : 1.0f;
+                dst[k] = make_float2(sc * acc[k].x, sc * acc[k].y);
+            }
+        }
+    }
+    // 2. Larger leaves, one per warp (striding over the entries)
+    for (uint32_t i = gw; i < nocc; i += nwarps) {
+        const InstDesc *dp;
+        uint32_t m, s0, s1;
+        range(i, dp, m, s0, s1);
+        if (s1 - s0 <= P2M_LANE_MAX) continue;
+        const InstDesc &d = *dp;
         const int p = d.p, L = d.L;
-        const uint32_t m = e.y;
-        uint32_t s0 = start[d.soff + m], s1 = start[d.soff + m + 1];
-        if (!(PF_IN(m, int64_t(1) << (2 * L)) && PF_IN(int64_t(s0) - d.poff, d.n + 1) &&
-              PF_IN(int64_t(s1) - d.poff, d.n + 1)) || s1 < s0)
-            s1 = s0;  // checked build: a leaf range outside the instance is skipped
         float2 acc[PM];
 #pragma unroll
         for (int k = 0; k < PM; ++k) acc[k] = make_float2(0.f, 0.f);
@@ -468,7 +524,6 @@ __global__ void __launch_bounds__(P2M_WARPS * 32) k_p2m_reg(
         // requested before this step's arithmetic: up to four 16-byte loads
         // in flight per lane.  Smaller leaves take one step of one blob per
         // lane (a second chain would only add padding).
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (s1 - s0 <= 32) {
             const float4 r = s0 + lane < s1 ? rec[s0 + lane] : z4;
             float2 w = make_float2(r.z, 0.f);
