@@ -27,7 +27,7 @@ PETFMM_F64, PETFMM_F32 = 0, 1
 PETFMM_OPT_TIMING, PETFMM_OPT_SPIN_LIMIT, PETFMM_OPT_P2P_MODE, PETFMM_OPT_POISON = 1, 2, 3, 4
 PETFMM_OPT_M2L_TC, PETFMM_OPT_TC_DENSE, PETFMM_OPT_TC_SEG, PETFMM_OPT_NEAR_TOL = 5, 6, 8, 9
 PETFMM_OPT_GRAPH, PETFMM_OPT_P2P_PAIRS, PETFMM_OPT_KERNEL, PETFMM_OPT_TC_BLOCKS = 10, 11, 12, 13
-PETFMM_OPT_TC_PIPE = 14
+PETFMM_OPT_TC_PIPE, PETFMM_OPT_OVERLAP = 14, 15
 PETFMM_KERNEL_VORTEX, PETFMM_KERNEL_LAPLACE = 0, 1
 PETFMM_NOALLOC_MAX_N = 1048576
 STAGES = ("morton", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "worklist", "pairs", "p2p",

@@ -152,7 +152,13 @@ struct petfmm_ctx {
     cudaStream_t cap_stream = nullptr;  // captures run here (the legacy stream cannot)
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey = 0, glaunches = 0;
-    cudaEvent_t ev[PETFMM_STAGE_COUNT + 1] = {};
+    // stage events: ev[s] starts stage s, ev[COUNT] ends the evaluation and
+    // ev[COUNT + 1] ends the L2L stage (its stream may be aux)
+    cudaEvent_t ev[PETFMM_STAGE_COUNT + 2] = {};
+    // the expansion chain's stream on the mixed path, and its fork / join
+    bool overlap = true;  // PETFMM_OPT_OVERLAP
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool ev_recorded = false;
     // level rules of the automatic L (petfmm_set_level_rules / petfmm_tune_batch)
     std::vector<petfmm_level_rule> rules;
@@ -604,7 +610,7 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     k.put(pl.tc_smem); k.put(pl.tcb_pmax); k.put(grid);
     k.put(c->precision); k.put(c->dtype); k.put(c->timing); k.put(c->p2p_mode); k.put(c->poison);
     k.put(c->tc_dense_pct); k.put(c->spin_limit); k.put(c->p2p_pairs); k.put(c->kernel);
-    k.put(c->tc_blocks); k.put(c->tc_pipe);
+    k.put(c->tc_blocks); k.put(c->tc_pipe); k.put(c->overlap);
     for (const DevBuf *b : {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->hist, &c->scratch,
                             &c->start, &c->xs, &c->ys, &c->gs, &c->rec, &c->me, &c->le, &c->cnt,
                             &c->off, &c->items, &c->ctrl, &c->plan_dev, &c->busy, &c->ucount,
@@ -615,14 +621,16 @@ uint64_t graph_key(const petfmm_ctx *c, const Plan &pl, int grid) {
     return k.h;
 }
 
-void stage_mark(petfmm_ctx *c, int stage) {
+void stage_mark_on(petfmm_ctx *c, int stage, cudaStream_t s) {
     if (!c->timing) return;
     // inside a capture the record must become an event node of the graph
     if (c->capturing)
-        cudaEventRecordWithFlags(c->ev[stage], c->stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(c->ev[stage], s, cudaEventRecordExternal);
     else
-        cudaEventRecord(c->ev[stage], c->stream);
+        cudaEventRecord(c->ev[stage], s);
 }
+
+void stage_mark(petfmm_ctx *c, int stage) { stage_mark_on(c, stage, c->stream); }
 
 // blobs of one instance from which the final pass stages FP32 results
 // (2 x 4 B x n > 64 MB)
@@ -787,45 +795,56 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                                   pl.particles.nblocks, dinst, f32, perm,
                                   static_cast<double *>(c->xs.p), static_cast<double *>(c->ys.p),
                                   static_cast<double *>(c->gs.p), st, lc));
-    stage_mark(c, PETFMM_STAGE_P2M);
+    // The expansion chain (P2M, M2M, M2L, L2L) runs on a second stream on
+    // the mixed path: the near field (work lists, pair and directed kernels)
+    // needs only the sorted blobs and the leaf starts, so the two overlap,
+    // and the final pass joins them (PETFMM_OPT_OVERLAP).
+    cudaStream_t xs = st;
+    const bool fork = mixed && c->overlap;
+    if (fork) {
+        PF_CUDA(cudaEventRecord(c->ev_fork, st));
+        PF_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+        xs = c->aux;
+    }
+    stage_mark_on(c, PETFMM_STAGE_P2M, xs);
     uint2 *occ = static_cast<uint2 *>(c->occ.p);
     PF_CUDA(launch_occ_list(dtask + pl.leaves_p2m.first, pl.leaves_p2m.count, pl.leaves_p2m.nblocks,
-                            dinst, start, occ, ctrl, st, lc));
+                            dinst, start, occ, ctrl, xs, lc));
     if (mixed)
         PF_CUDA(launch_p2m<float>(occ, ctrl, pl.nleaves, dinst, pl.pmax, start, nullptr, nullptr,
                                   nullptr, srec,
-                                  static_cast<float2 *>(c->me.p), st, lc));
+                                  static_cast<float2 *>(c->me.p), xs, lc));
     else
         PF_CUDA(launch_p2m<double>(occ, ctrl, pl.nleaves, dinst, pl.pmax, start,
                                    static_cast<const double *>(c->xs.p),
                                    static_cast<const double *>(c->ys.p),
                                    static_cast<const double *>(c->gs.p), nullptr,
-                                   static_cast<double2 *>(c->me.p), st, lc));
-    stage_mark(c, PETFMM_STAGE_M2M);
+                                   static_cast<double2 *>(c->me.p), xs, lc));
+    stage_mark_on(c, PETFMM_STAGE_M2M, xs);
     for (const TaskRange &tr : pl.m2m) {
         if (mixed)
             PF_CUDA(launch_m2m<float>(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
-                                      static_cast<float2 *>(c->me.p), st, lc));
+                                      static_cast<float2 *>(c->me.p), xs, lc));
         else
             PF_CUDA(launch_m2m<double>(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
-                                       static_cast<double2 *>(c->me.p), st, lc));
+                                       static_cast<double2 *>(c->me.p), xs, lc));
     }
-    stage_mark(c, PETFMM_STAGE_M2L);
+    stage_mark_on(c, PETFMM_STAGE_M2L, xs);
     uint32_t *ucount = nullptr;
     if (pl.m2l_tc.count || pl.m2l_tcb.count || pl.tile_blocks()) {
         ucount = static_cast<uint32_t *>(c->ucount.p);
         if (pl.m2l_tc.count)
             PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tc.first, pl.m2l_tc.count,
-                                         pl.m2l_tc.nblocks, dinst, start, ucount, st, lc));
+                                         pl.m2l_tc.nblocks, dinst, start, ucount, xs, lc));
         if (pl.m2l_tcb.count)
             PF_CUDA(launch_tc_unit_count(dtask + pl.m2l_tcb.first, pl.m2l_tcb.count,
                                          pl.m2l_tcb.nblocks, dinst, start,
-                                         ucount + pl.m2l_tc.nblocks, st, lc));
+                                         ucount + pl.m2l_tc.nblocks, xs, lc));
         int64_t base = pl.m2l_tc.nblocks + pl.m2l_tcb.nblocks;
         for (const TaskRange &tr : pl.m2l_tile) {
             if (tr.count)
                 PF_CUDA(launch_tc_unit_count(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
-                                             ucount + base, st, lc));
+                                             ucount + base, xs, lc));
             base += tr.nblocks;
         }
     }
@@ -834,11 +853,11 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
             PF_CUDA(launch_m2l<float>(dtask + pl.m2l.first, pl.m2l.count, pl.m2l.nblocks, dinst,
                                       start, static_cast<const float2 *>(c->me.p),
                                       static_cast<float2 *>(c->le.p), ucount, c->tc_dense_pct,
-                                      st, lc));
+                                      xs, lc));
         else
             PF_CUDA(launch_m2l<double>(dtask + pl.m2l.first, pl.m2l.count, pl.m2l.nblocks, dinst,
                                        start, static_cast<const double2 *>(c->me.p),
-                                       static_cast<double2 *>(c->le.p), nullptr, 0, st, lc));
+                                       static_cast<double2 *>(c->le.p), nullptr, 0, xs, lc));
     }
     if (pl.m2l_tc.count) {
         // spin_limit < 0: zero-iteration budget (tests the timeout report)
@@ -846,7 +865,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         PF_CUDA(launch_m2l_tc(dtask + pl.m2l_tc.first, pl.m2l_tc.count, pl.m2l_tc.nblocks, dinst,
                               start, static_cast<const float2 *>(c->me.p),
                               static_cast<float2 *>(c->le.p), ucount, c->tc_dense_pct,
-                              pl.tc_smem, spin, reinterpret_cast<int *>(ctrl + CTRL_STATUS), st,
+                              pl.tc_smem, spin, reinterpret_cast<int *>(ctrl + CTRL_STATUS), xs,
                               lc));
     }
     if (pl.m2l_tcb.count) {
@@ -855,7 +874,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                                dinst, start, static_cast<const float2 *>(c->me.p),
                                static_cast<float2 *>(c->le.p), ucount + pl.m2l_tc.nblocks,
                                c->tc_dense_pct, pl.tcb_pmax, spin, c->tc_pipe,
-                               reinterpret_cast<int *>(ctrl + CTRL_STATUS), st, lc));
+                               reinterpret_cast<int *>(ctrl + CTRL_STATUS), xs, lc));
     }
     {
         int64_t base = pl.m2l_tc.nblocks + pl.m2l_tcb.nblocks;
@@ -865,7 +884,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                 PF_CUDA(launch_m2l_tile(dtask + tr.first, tr.count, tr.nblocks, pl.tile_pmax[cls],
                                         dinst, start, static_cast<const float2 *>(c->me.p),
                                         static_cast<float2 *>(c->le.p), ucount + base,
-                                        c->tc_dense_pct, st, lc));
+                                        c->tc_dense_pct, xs, lc));
             base += tr.nblocks;
         }
     }
@@ -874,22 +893,24 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
             PF_CUDA(launch_m2l_logterm<float>(dtask + pl.m2l_log.first, pl.m2l_log.count,
                                               pl.m2l_log.nblocks, dinst, start,
                                               static_cast<const float2 *>(c->me.p),
-                                              static_cast<float2 *>(c->le.p), st, lc));
+                                              static_cast<float2 *>(c->le.p), xs, lc));
         else
             PF_CUDA(launch_m2l_logterm<double>(dtask + pl.m2l_log.first, pl.m2l_log.count,
                                                pl.m2l_log.nblocks, dinst, start,
                                                static_cast<const double2 *>(c->me.p),
-                                               static_cast<double2 *>(c->le.p), st, lc));
+                                               static_cast<double2 *>(c->le.p), xs, lc));
     }
-    stage_mark(c, PETFMM_STAGE_L2L);
+    stage_mark_on(c, PETFMM_STAGE_L2L, xs);
     for (const TaskRange &tr : pl.l2l) {
         if (mixed)
             PF_CUDA(launch_l2l<float>(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
-                                      static_cast<float2 *>(c->le.p), st, lc));
+                                      static_cast<float2 *>(c->le.p), xs, lc));
         else
             PF_CUDA(launch_l2l<double>(dtask + tr.first, tr.count, tr.nblocks, dinst, start,
-                                       static_cast<double2 *>(c->le.p), st, lc));
+                                       static_cast<double2 *>(c->le.p), xs, lc));
     }
+    stage_mark_on(c, PETFMM_STAGE_COUNT + 1, xs);  // end of the L2L stage
+    if (fork) PF_CUDA(cudaEventRecord(c->ev_join, xs));
     stage_mark(c, PETFMM_STAGE_WORKLIST);
     const int tpi = mixed ? P2P_TPI_MIXED : P2P_TPI_F64;
     PF_CUDA(launch_p2p_worklist(dtask + pl.leaves_wl.first, pl.leaves_wl.count, pl.leaves_wl.nblocks,
@@ -918,6 +939,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         PF_CUDA(launch_p2p_mixed(grid, pl.deg, pl.general, static_cast<const uint4 *>(c->items.p),
                                  ctrl, dinst, start, srec, pb.own,
                                  pairs, lap ? 1 : 0, busy, st, lc));
+        if (fork) PF_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
         stage_mark(c, PETFMM_STAGE_FINAL);
         PF_CUDA(launch_p2p_final(dtask + pl.particles.first, pl.particles.count,
                                  pl.particles.nblocks, dinst, start, skeys, srec,
@@ -1046,6 +1068,13 @@ int petfmm_create(const petfmm_domain *dom, int levels, int order, double sigma,
             return PETFMM_ECUDA;
         }
     }
+    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        petfmm_destroy(c);
+        return PETFMM_ECUDA;
+    }
     int err = PETFMM_OK;
     if (!get_tables(c, order, KERNEL_VORTEX, &err)) {
         petfmm_destroy(c);
@@ -1069,6 +1098,12 @@ int petfmm_destroy(petfmm_ctx *c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->upload_done) cudaEventDestroy(c->upload_done);
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        cudaStreamDestroy(c->aux);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     cudaGetLastError();
@@ -1436,6 +1471,7 @@ int petfmm_set_option(petfmm_ctx *c, int option, int64_t value) {
             if (value < 0 || value > 2) return PETFMM_EINVAL;
             c->tc_pipe = int(value);
             return PETFMM_OK;
+        case PETFMM_OPT_OVERLAP: c->overlap = value != 0; return PETFMM_OK;
         case PETFMM_OPT_KERNEL:
             if (value != PETFMM_KERNEL_VORTEX && value != PETFMM_KERNEL_LAPLACE)
                 return PETFMM_EINVAL;
@@ -1456,7 +1492,8 @@ int petfmm_stage_times(petfmm_ctx *c, float *ms, int cap) {
     const int n = std::min(cap, int(PETFMM_STAGE_COUNT));
     for (int s = 0; s < n; ++s) {
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, c->ev[s], c->ev[s + 1]) != cudaSuccess) {
+        const cudaEvent_t end = s == PETFMM_STAGE_L2L ? c->ev[PETFMM_STAGE_COUNT + 1] : c->ev[s + 1];
+        if (cudaEventElapsedTime(&t, c->ev[s], end) != cudaSuccess) {
             cudaGetLastError();
             return PETFMM_ECUDA;
         }

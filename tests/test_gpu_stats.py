@@ -140,3 +140,29 @@ def test_graph_replay_matches_plain_launches():
     assert ctx.stats()["kernel_launches"] > 0
     ctx.close()
     torch.cuda.synchronize()
+
+
+def test_overlap_streams_match_one_stream():
+    # PETFMM_OPT_OVERLAP: the expansion chain on the context's second stream,
+    # beside the near field, plain and captured in a graph, gives bitwise the
+    # velocities of one stream; the stage times stay readable.
+    _lib = G.lib()
+    torch = G.torch_cuda()
+    w = W.tiny(60_000, 41, L=6, p=12, clustered_frac=0.5, dtype="f32")
+    x, y, g = G.to_dev((w.x, w.y, w.gamma))
+    outs = []
+    for overlap, graph in ((0, 0), (1, 0), (1, 1), (0, 1)):
+        ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision="mixed", dtype="f32")
+        ctx.set_option(_lib.PETFMM_OPT_OVERLAP, overlap)
+        ctx.set_option(_lib.PETFMM_OPT_GRAPH, graph)
+        ctx.set_option(_lib.PETFMM_OPT_TIMING, 1)
+        for _ in range(2):
+            u, v = ctx.evaluate(x, y, g)
+            assert ctx.sync() == 0
+        st = ctx.stage_times()
+        assert st["m2l"] > 0 and st["pairs"] > 0 and all(t >= 0 for t in st.values())
+        outs.append((u.cpu().numpy(), v.cpu().numpy()))
+        ctx.close()
+    for u, v in outs[1:]:
+        assert np.array_equal(u, outs[0][0]) and np.array_equal(v, outs[0][1])
+    torch.cuda.synchronize()
