@@ -657,8 +657,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     PF_TRY(ensure(c->keysB, N * 4, st));
     PF_TRY(ensure(c->valsA, N * 4, st));
     PF_TRY(ensure(c->valsB, N * 4, st));
-    const int64_t rb = radix_blocks(N);
-    PF_TRY(ensure(c->hist, size_t(256) * rb * 4, st));
+    PF_TRY(ensure(c->hist, size_t(radix_scratch_words(N)) * 4, st));
     // pairwise near field (mixed path): at most 4 forward neighbours per leaf,
     // a pair cut into at most ceil(na / 128) pieces, and the leaf's own pairs
     // (the pairwise near field is the vortex kernel's)
@@ -666,8 +665,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     const int64_t pair_cap =
         pairs ? 5 * std::min<int64_t>(pl.nleaves, N) + 4 * (N / 128) + 1 : 0;
     const int64_t order_cap = std::max<int64_t>(pl.items_cap, pair_cap);
-    const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(256 * rb, pl.nleaves),
-                                             256 * radix_blocks(order_cap));
+    const int64_t scan_n = pl.nleaves;
     PF_TRY(ensure(c->scratch, size_t(scan_scratch_words(scan_n)) * 4, st));
     PF_TRY(ensure(c->start, size_t(pl.nstart) * 4, st));
     if (mixed) {
@@ -716,7 +714,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         PF_TRY(ensure(c->ikB, cap * 4, st));
         PF_TRY(ensure(c->ivA, cap * 4, st));
         PF_TRY(ensure(c->ivB, cap * 4, st));
-        PF_TRY(ensure(c->ihist, size_t(256) * radix_blocks(order_cap) * 4, st));
+        PF_TRY(ensure(c->ihist, size_t(radix_scratch_words(order_cap)) * 4, st));
         order.cap = pl.items_cap;
         order.items_unsorted = static_cast<uint4 *>(c->items_u.p);
         order.kA = static_cast<uint32_t *>(c->ikA.p);
@@ -780,8 +778,8 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                           lc));
     stage_mark(c, PETFMM_STAGE_SORT);
     bool in_first = true;
-    PF_CUDA(radix_sort(kA, vA, kB, vB, N, pl.nbits, static_cast<uint32_t *>(c->hist.p), scratch,
-                       &in_first, st, lc));
+    PF_CUDA(radix_sort(kA, vA, kB, vB, N, pl.nbits, static_cast<uint32_t *>(c->hist.p), &in_first,
+                       st, lc));
     c->sorted_in_first = in_first;
     const uint32_t *skeys = in_first ? kA : kB;
     const uint32_t *perm = in_first ? vA : vB;

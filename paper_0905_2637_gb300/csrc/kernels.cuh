@@ -30,15 +30,18 @@ int64_t scan_scratch_words(int64_t n);
 cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *scratch,
                            uint32_t *total, cudaStream_t st, uint64_t *launches);
 
-// Stable LSD radix sort of (key, value) over the low nbits bits; the initial
-// values are the element indices.  Result ends up in (k0, v0) or (k1, v1):
-// *result_in_first tells which.  hist must hold 256 * radix_blocks(n) words.
-// n_live (device, optional): sort only the first min(n, *n_live) elements
-// (the grid stays sized for n; tiles past the live ones return at once).
+// Stable LSD radix sort of (key, value) over the low nbits bits (8-bit
+// digits, at most 4 passes, n < 2^32); the initial values are the element
+// indices.  Result ends up in (k0, v0) or (k1, v1): *result_in_first tells
+// which.  scratch: radix_scratch_words(n) words (per-tile digit counts and
+// their scan).  n_live (device, optional): sort only the
+// first min(n, *n_live) elements (the grid stays sized for n; tiles past the
+// live ones return at once).
 int64_t radix_blocks(int64_t n);
+int64_t radix_scratch_words(int64_t n);
 cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n,
-                       int nbits, uint32_t *hist, uint32_t *scan_scratch, bool *result_in_first,
-                       cudaStream_t st, uint64_t *launches, const uint32_t *n_live = nullptr);
+                       int nbits, uint32_t *scratch, bool *result_in_first, cudaStream_t st,
+                       uint64_t *launches, const uint32_t *n_live = nullptr);
 
 // start[soff + b] = first sorted rank of leaf b (b = 0..4^L).
 cudaError_t launch_leaf_start(const Task *tasks, int ntasks, int64_t nblocks, const InstDesc *insts,
@@ -175,7 +178,7 @@ enum { CTRL_STATUS = 0, CTRL_NITEMS = 1, CTRL_QUEUE = 2, CTRL_PAIRS_LO = 4, CTRL
 struct P2POrder {
     int64_t cap;
     uint4 *items_unsorted;
-    uint32_t *kA, *kB, *vA, *vB, *hist;  // hist: 256 * radix_blocks(cap) words
+    uint32_t *kA, *kB, *vA, *vB, *hist;  // hist: radix_scratch_words(cap) words
 };
 // pairs_mode: only the leaves with directed work (leaves under 32 blobs, or
 // with a neighbour the pair kernel does not cover) get items.

@@ -39,13 +39,14 @@ namespace {
 
 constexpr int64_t kMaxN = PETFMM_NOALLOC_MAX_N;
 constexpr int64_t kRsBlocks = (kMaxN + 4095) / 4096;     // radix tiles of 4096 keys
-constexpr int64_t kHistWords = 256 * kRsBlocks;
-constexpr int64_t kScanWords = 1024;                     // >= scan scratch for kHistWords
+// radix scratch: per-tile digit counts and the partial sums of their scan
+// (fewer than 1024 words)
+constexpr int64_t kSortWords = 256 * kRsBlocks + 1024;
 constexpr int64_t kDescBytes = 4096;                     // InstDesc + Tasks
-constexpr int64_t kScratchBytes = 4 * (4 * kMaxN + kHistWords + kScanWords + 16) + kDescBytes;
+constexpr int64_t kScratchBytes = 4 * (4 * kMaxN + kSortWords + 16) + kDescBytes;
 
-// The scratch: keys A, keys B, values A, values B (uint32 each), radix
-// histograms, scan partial sums, a status word, then the launch descriptors.
+// The scratch: keys A, keys B, values A, values B (uint32 each), the radix
+// sort's scratch, a status word, then the launch descriptors.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
@@ -133,9 +134,7 @@ extern "C" int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dty
     if (dtype != PETFMM_F64 && dtype != PETFMM_F32) return PETFMM_EINVAL;
     if (n > 0 && (!x || !y)) return PETFMM_EINVAL;
     if (n > kMaxN) return PETFMM_ENOMEM;  // the fixed scratch holds at most kMaxN particles
-    if (radix_blocks(n) > kRsBlocks || scan_scratch_words(256 * radix_blocks(n)) > kScanWords)
-        return PETFMM_ENOMEM;
-    static_assert(kScanWords >= 64, "scan scratch");
+    if (radix_blocks(n) > kRsBlocks || radix_scratch_words(n) > kSortWords) return PETFMM_ENOMEM;
     void *base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;
@@ -145,9 +144,8 @@ extern "C" int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dty
     uint32_t *kB = kA + kMaxN;
     uint32_t *vA = kB + kMaxN;
     uint32_t *vB = vA + kMaxN;
-    uint32_t *hist = vB + kMaxN;
-    uint32_t *scan = hist + kHistWords;
-    int *status = reinterpret_cast<int *>(scan + kScanWords);
+    uint32_t *sortw = vB + kMaxN;
+    int *status = reinterpret_cast<int *>(sortw + kSortWords);
     unsigned char *descs = reinterpret_cast<unsigned char *>(status + 16);
 
     // launch descriptors of this call: one instance, one task per stage
@@ -176,7 +174,7 @@ extern "C" int petfmm_tree_noalloc(const petfmm_domain *dom, int levels, int dty
                           &launches);
         if (e == cudaSuccess && keys) e = cudaMemcpyAsync(keys, kA, size_t(n) * 4, cudaMemcpyDeviceToDevice, st);
         bool in_first = true;
-        if (e == cudaSuccess) e = radix_sort(kA, vA, kB, vB, n, 2 * levels, hist, scan, &in_first, st, &launches);
+        if (e == cudaSuccess) e = radix_sort(kA, vA, kB, vB, n, 2 * levels, sortw, &in_first, st, &launches);
         const uint32_t *sk = in_first ? kA : kB;
         const uint32_t *sv = in_first ? vA : vB;
         if (e == cudaSuccess) e = cudaMemcpyAsync(perm, sv, size_t(n) * 4, cudaMemcpyDeviceToDevice, st);

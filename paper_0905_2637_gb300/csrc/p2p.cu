@@ -220,7 +220,7 @@ static cudaError_t order_items(const P2POrder *order, uint4 *items, const uint32
     const unsigned g = unsigned((cap + 255) / 256);
     bool in_first = true;
     cudaError_t e = radix_sort(order->kA, order->vA, order->kB, order->vB, cap, 8, order->hist,
-                               scan_scratch, &in_first, st, launches, count);
+                               &in_first, st, launches, count);
     if (e != cudaSuccess) return e;
     k_item_permute<<<g, 256, 0, st>>>(order->items_unsorted, in_first ? order->vA : order->vB,
                                       items, cap, count);

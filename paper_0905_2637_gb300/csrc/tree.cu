@@ -3,9 +3,9 @@
 // ranges, and the gather of the particles into sorted order.
 //
 // All of it is bandwidth-bound.  Per particle the algorithmic traffic is one
-// read of x, y and one key write (binning), then per radix pass one read of
-// (key, value) for the histogram, one more read and one write for the
-// scatter, and finally a gather of x, y, gamma into sorted order.
+// read of x, y and one key write (binning), one read of the key for the digit
+// counts of all passes, then per radix pass one read and one write of
+// (key, value), and finally a gather of x, y, gamma into sorted order.
 #include <cstdio>
 
 #include "kernels.cuh"
@@ -234,14 +234,18 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_
 }
 
 // ----------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits, reduce-then-scan.  A block owns a tile
-// of RS_TILE consecutive elements; warp w owns the consecutive chunk
-// [w * RS_WCHUNK, (w + 1) * RS_WCHUNK) of the tile and reads it in rounds of
-// 32 (lane order), so (warp, round, lane) is the input order.  The scatter
-// ranks every element within its warp (digit_peers per round), turns the ranks
-// into positions of the tile sorted by digit, sorts the tile in shared memory
-// and writes each digit's run to its place in the output: consecutive
-// threads write consecutive addresses.
+// Stable LSD radix sort, 8-bit digits, reduce-then-scan.  Per pass:
+// k_radix_counts counts the digits of each tile of RS_TILE consecutive
+// elements in digit-major order, count[digit * tiles + tile]; an exclusive
+// scan of that gives every (digit, tile) its first output position; then
+// k_radix_scatter moves the tile.
+//
+// Within a tile, warp w owns the consecutive chunk [w * RS_WCHUNK, (w + 1) *
+// RS_WCHUNK) and reads it in rounds of 32 (lane order), so (warp, round, lane)
+// is the input order.  The ranks within the warp (digit_peers per round)
+// become positions in the tile sorted by digit; the tile is sorted in shared
+// memory and each digit's run written to its place in the output, consecutive
+// threads to consecutive addresses.
 // ----------------------------------------------------------------------------
 // Lanes of the warp holding the same digit as this lane (bit d of the
 // 9-bit value 0..256, 256 = no element): 9 ballots, which run on the ALU
@@ -257,13 +261,21 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t dg) {
     return peers;
 }
 
-constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
+constexpr int RS_THREADS = 512;
+constexpr int RS_ITEMS = 8;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_WCHUNK = RS_ITEMS * 32;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+static_assert(RS_WCHUNK <= 256 && RS_ITEMS % 4 == 0 && RS_TILE < 65536,
+              "ranks packed as 8-bit fields, warp offsets as 16-bit");
+constexpr int RC_THREADS = 256;
 
 int64_t radix_blocks(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
+
+int64_t radix_scratch_words(int64_t n) {
+    const int64_t c = 256 * radix_blocks(n);
+    return c + scan_scratch_words(c);
+}
 
 // n_live (device, may be null): only the first *n_live of the n elements
 // take part; tiles past them count nothing and move nothing.
@@ -273,91 +285,134 @@ __device__ __forceinline__ int64_t live_count(int64_t n, const uint32_t *n_live)
     return m < n ? m : n;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const uint32_t *__restrict__ keys,
-                                                           int64_t n, const uint32_t *n_live,
-                                                           int shift, uint32_t mask,
-                                                           uint32_t *__restrict__ hist,
-                                                           int64_t nblocks) {
-    __shared__ uint32_t cnt[256];
-    const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
-    n = live_count(n, n_live);
-    if (tile >= n) {
-        hist[int64_t(threadIdx.x) * nblocks + blockIdx.x] = 0;
-        return;
+// Exclusive sums of (a, b) over the block's NT threads.
+template <int NT>
+__device__ __forceinline__ void block_exclusive_sum2(uint32_t a, uint32_t b, uint32_t *ea,
+                                                     uint32_t *eb, uint2 *ws) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t na = __shfl_up_sync(0xffffffffu, ia, o);
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += na;
+            ib += nb;
+        }
     }
-    cnt[threadIdx.x] = 0;
+    if (lane == 31) ws[warp] = make_uint2(ia, ib);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-#pragma unroll 4
-    for (int k = 0; k < RS_ITEMS; ++k) {
-        const int64_t i = tile + int64_t(k) * RS_THREADS + threadIdx.x;
-        const uint32_t dg = i < n ? (keys[i] >> shift) & mask : 0x100u;
-        // one shared atomic per distinct digit of the warp (clustered keys
-        // share few digits)
-        const uint32_t peers = digit_peers(dg);
-        if (dg < 0x100u && (peers & ((1u << lane) - 1u)) == 0)
-            atomicAdd(&cnt[dg], uint32_t(__popc(peers)));
+    if (warp == 0) {
+        uint2 s = lane < NT / 32 ? ws[lane] : make_uint2(0u, 0u);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t nx = __shfl_up_sync(0xffffffffu, s.x, o);
+            const uint32_t ny = __shfl_up_sync(0xffffffffu, s.y, o);
+            if (lane >= o) {
+                s.x += nx;
+                s.y += ny;
+            }
+        }
+        if (lane < NT / 32) ws[lane] = s;
     }
     __syncthreads();
-    hist[int64_t(threadIdx.x) * nblocks + blockIdx.x] = cnt[threadIdx.x];
+    const uint2 before = warp ? ws[warp - 1] : make_uint2(0u, 0u);
+    *ea = before.x + ia - a;
+    *eb = before.y + ib - b;
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
+// count[d * nblocks + tile]: elements of the tile whose digit
+// (key >> shift) & mask is d (tiles past the live elements count zero).
+__global__ void __launch_bounds__(RC_THREADS) k_radix_counts(const uint32_t *__restrict__ keys,
+                                                             int64_t n, const uint32_t *n_live,
+                                                             int shift, uint32_t mask,
+                                                             uint32_t *__restrict__ count,
+                                                             int64_t nblocks) {
+    __shared__ uint32_t h[256];
+    const int tid = threadIdx.x;
+    h[tid] = 0;
+    __syncthreads();
+    n = live_count(n, n_live);
+    const int64_t t0 = int64_t(blockIdx.x) * RS_TILE;
+    uint32_t k[RS_TILE / RC_THREADS];
+#pragma unroll
+    for (int u = 0; u < RS_TILE / RC_THREADS; ++u) {
+        const int64_t i = t0 + u * RC_THREADS + tid;
+        k[u] = i < n ? keys[i] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < RS_TILE / RC_THREADS; ++u)
+        if (t0 + u * RC_THREADS + tid < n) atomicAdd(&h[(k[u] >> shift) & mask], 1u);
+    __syncthreads();
+    count[int64_t(tid) * nblocks + blockIdx.x] = h[tid];
+}
+
+// One pass: digit (key >> shift) & mask; offs: the scanned counts (first
+// output position of each digit of each tile).
+template <bool FIRST>
+__global__ void __launch_bounds__(RS_THREADS, 3) k_radix_scatter(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, const uint32_t *n_live, int shift, uint32_t mask,
     const uint32_t *__restrict__ offs, int64_t nblocks) {
-    __shared__ uint32_t wcnt[RS_WARPS][256];  // per-warp digit counts, then warp offsets
+    __shared__ uint16_t wcnt[RS_WARPS][256];  // per-warp digit counts, then warp offsets
     __shared__ uint32_t lstart[256];          // start of each digit's run in the sorted tile
     __shared__ uint32_t gbase[256];           // its start in the output
     __shared__ uint32_t skey[RS_TILE], sval[RS_TILE];
+    __shared__ uint2 wsum[RS_WARPS];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    const int64_t tile = int64_t(blockIdx.x) * RS_TILE;
     n = live_count(n, n_live);
-    if (tile >= n) return;
-    const int64_t tile_n = n - tile < RS_TILE ? n - tile : RS_TILE;
-#pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) wcnt[w][tid] = 0;
-    gbase[tid] = offs[int64_t(tid) * nblocks + blockIdx.x];
+    const int64_t t0 = int64_t(blockIdx.x) * RS_TILE;
+    if (t0 >= n) return;
+    const int64_t tile_n = n - t0 < RS_TILE ? n - t0 : RS_TILE;
+    for (int i = tid; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    if (tid < 256) gbase[tid] = offs[int64_t(tid) * nblocks + blockIdx.x];
     __syncthreads();
     // 1. rank within the warp, in input order
-    uint32_t key[RS_ITEMS], val[RS_ITEMS], rk[RS_ITEMS];
-    const int64_t wbase = tile + int64_t(warp) * RS_WCHUNK;
+    // rk: ranks within the warp (< RS_WCHUNK = 256), four 8-bit fields a word
+    uint32_t key[RS_ITEMS], val[RS_ITEMS], rk[RS_ITEMS / 4] = {};
+    const int64_t wbase = t0 + int64_t(warp) * RS_WCHUNK;
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         const int64_t i = wbase + r * 32 + lane;
         const bool valid = i < n;
         key[r] = valid ? kin[i] : 0u;
-        val[r] = valid ? (vin ? vin[i] : uint32_t(i)) : 0u;
+        val[r] = valid ? (FIRST ? uint32_t(i) : vin[i]) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const bool valid = wbase + r * 32 + lane < n;
         const uint32_t dg = valid ? (key[r] >> shift) & mask : 0x100u;
         const uint32_t peers = digit_peers(dg);
         const uint32_t below = peers & lt_mask;
-        rk[r] = valid ? wcnt[warp][dg & 0xffu] + __popc(below) : 0u;
+        if (valid) rk[r >> 2] |= (wcnt[warp][dg] + __popc(below)) << (8 * (r & 3));
         __syncwarp();
-        if (valid && below == 0) wcnt[warp][dg] += __popc(peers);
+        if (valid && below == 0) wcnt[warp][dg] = uint16_t(wcnt[warp][dg] + __popc(peers));
         __syncwarp();
     }
     __syncthreads();
-    // 2. per digit (thread tid = digit): offsets of the warps, then the runs
-    {
-        uint32_t s = 0;
+    // 2. per digit (thread tid < 256 = digit): the warps' offsets, then the
+    //    runs' starts in the sorted tile
+    uint32_t cnt = 0;
+    if (tid < 256) {
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
             const uint32_t c = wcnt[w][tid];
-            wcnt[w][tid] = s;
-            s += c;
+            wcnt[w][tid] = uint16_t(cnt);
+            cnt += c;
         }
-        uint32_t total;
-        lstart[tid] = block_exclusive_sum(s, &total);
     }
+    uint32_t ls, unused;
+    block_exclusive_sum2<RS_THREADS>(cnt, 0u, &ls, &unused, wsum);
+    if (tid < 256) lstart[tid] = ls;
     __syncthreads();
     // 3. sort the tile in shared memory
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
-        const int64_t i = wbase + r * 32 + lane;
-        if (i < n) {
+        if (wbase + r * 32 + lane < n) {
             const uint32_t dg = (key[r] >> shift) & mask;
-            const uint32_t pos = lstart[dg] + wcnt[warp][dg] + rk[r];
+            const uint32_t pos = lstart[dg] + wcnt[warp][dg] + ((rk[r >> 2] >> (8 * (r & 3))) & 0xffu);
             skey[pos] = key[r];
             sval[pos] = val[r];
         }
@@ -375,28 +430,31 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(
 }
 
 cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, int64_t n,
-                       int nbits, uint32_t *hist, uint32_t *scan_scratch, bool *result_in_first,
-                       cudaStream_t st, uint64_t *launches, const uint32_t *n_live) {
+                       int nbits, uint32_t *scratch, bool *result_in_first, cudaStream_t st,
+                       uint64_t *launches, const uint32_t *n_live) {
     *result_in_first = true;
     if (n <= 0) return cudaSuccess;
+    const int passes = (nbits + 7) / 8;
+    if (passes <= 0 || passes > 4 || n > int64_t(0xffffffffu)) return cudaErrorInvalidValue;
     const int64_t nb = radix_blocks(n);
+    uint32_t *count = scratch;
+    uint32_t *scan = scratch + 256 * nb;
     uint32_t *kin = k0, *vin = nullptr, *kout = k1, *vout = v1;
     bool in_first = true;
-    const int passes = (nbits + 7) / 8;
-    if (passes == 0) {
-        // nothing to sort: values are the identity
-        return cudaErrorInvalidValue;
-    }
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
         const int bits = nbits - shift < 8 ? nbits - shift : 8;
         const uint32_t mask = (1u << bits) - 1u;
-        k_radix_hist<<<unsigned(nb), RS_THREADS, 0, st>>>(kin, n, n_live, shift, mask, hist, nb);
+        k_radix_counts<<<unsigned(nb), RC_THREADS, 0, st>>>(kin, n, n_live, shift, mask, count, nb);
         PF_LAUNCHED(1);
-        cudaError_t e = exclusive_scan(hist, hist, 256 * nb, scan_scratch, nullptr, st, launches);
+        cudaError_t e = exclusive_scan(count, count, 256 * nb, scan, nullptr, st, launches);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<unsigned(nb), RS_THREADS, 0, st>>>(kin, vin, kout, vout, n, n_live, shift,
-                                                               mask, hist, nb);
+        if (pass == 0)
+            k_radix_scatter<true><<<unsigned(nb), RS_THREADS, 0, st>>>(
+                kin, vin, kout, vout, n, n_live, shift, mask, count, nb);
+        else
+            k_radix_scatter<false><<<unsigned(nb), RS_THREADS, 0, st>>>(
+                kin, vin, kout, vout, n, n_live, shift, mask, count, nb);
         PF_LAUNCHED(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -9,9 +9,11 @@ from paper_0905_2637_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _tree(w, precision="mixed"):
+def _tree(w, precision="mixed", opts=()):
     _lib = G.lib()
     ctx = _lib.Context(w.domain, w.L, w.p, w.sigma, precision=precision, dtype=w.dtype)
+    for k, v in opts:
+        ctx.set_option(getattr(_lib, k), v)
     x, y, g = G.to_dev((w.x, w.y, w.gamma))
     ctx.evaluate(x, y, g)
     assert ctx.sync() == 0
@@ -20,11 +22,11 @@ def _tree(w, precision="mixed"):
     return keys, perm, start
 
 
-def _check(orc, w, precision="mixed"):
+def _check(orc, w, precision="mixed", opts=()):
     xd, yd, _ = w.as_f64()
     _, _, key = orc.bin(xd, yd, w.domain, w.L)
     perm, start = orc.sort(key, w.L)
-    k2, p2, s2 = _tree(w, precision)
+    k2, p2, s2 = _tree(w, precision, opts)
     assert np.array_equal(k2, key)
     assert np.array_equal(p2, perm)
     assert np.array_equal(s2, start)
