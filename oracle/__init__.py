@@ -21,6 +21,12 @@ Every function cites the passage of the PetFMM paper it follows:
                       logarithmic potential sum_{j != i} q_j log|x_i - x_j|,
                       directly and by the FMM of Sec. 2.2 with the series of
                       the complex logarithm.
+* ``direct3d`` / ``fmm3d`` (and ``bin3d``, ``sort3d``, ``interaction_list3d``,
+  the operators ``p2m3d`` ... ``l2p3d``) -- the three-dimensional extension
+                      the paper names first (Sec. 8): the Laplace potential
+                      and field of point charges, directly and by the FMM on
+                      a uniform octree with solid-harmonic series
+                      (``oracle3d.c``).
 """
 from __future__ import annotations
 
@@ -33,6 +39,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC3 = os.path.join(_HERE, "oracle3d.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -43,11 +50,12 @@ ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_EDOMAIN = 0, -1, -2, -3
 def build(force: bool = False) -> str:
     """Compile ``oracle.c`` into ``liboracle.so`` (gcc, -O2, no FMA contraction)."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(_SRC3))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+           "-fopenmp", "-fPIC", "-shared", _SRC, _SRC3, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -94,6 +102,31 @@ def _load():
         lib.orc_laplace_fmm.restype = i32
         lib.orc_max_threads.argtypes = []
         lib.orc_max_threads.restype = i32
+        # three dimensions (oracle3d.c)
+        lib.o3_harmonics.argtypes = [f64, f64, f64, i32, P, P]
+        lib.o3_harmonics.restype = i32
+        lib.o3_direct.argtypes = [i64, P, P, P, P, i64, P, P, P, P, P]
+        lib.o3_direct.restype = i32
+        lib.o3_morton.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, i32]
+        lib.o3_morton.restype = ctypes.c_uint32
+        lib.o3_bin.argtypes = [i64, P, P, P, f64, f64, f64, f64, i32, P]
+        lib.o3_bin.restype = i32
+        lib.o3_sort.argtypes = [i64, P, i32, P, P]
+        lib.o3_sort.restype = i32
+        lib.o3_interaction_list.argtypes = [i32, i32, i32, i32, P]
+        lib.o3_interaction_list.restype = i32
+        lib.o3_p2m.argtypes = [i64, P, P, P, P, P, i32, P]
+        lib.o3_p2m.restype = None
+        for name in ("o3_m2m", "o3_m2l", "o3_l2l"):
+            fn = getattr(lib, name)
+            fn.argtypes = [i32, P, P, P, P]
+            fn.restype = None
+        lib.o3_l2p.argtypes = [i32, P, P, f64, f64, f64, P]
+        lib.o3_l2p.restype = None
+        lib.o3_me_eval.argtypes = [i32, P, P, f64, f64, f64]
+        lib.o3_me_eval.restype = f64
+        lib.o3_fmm.argtypes = [i64, P, P, P, P, f64, f64, f64, f64, i32, i32, P, P, P, P]
+        lib.o3_fmm.restype = i32
         _lib = lib
         return lib
 
@@ -336,3 +369,144 @@ def lap_me_eval(a, zc, z):
     lib.orc_lap_me_eval(len(a), _ptr(a), complex(zc).real, complex(zc).imag, complex(z).real,
                         complex(z).imag, _ptr(w))
     return complex(w[0], w[1])
+
+
+# ---------------------------------------------------------------------------
+# Three dimensions (oracle3d.c): the 3D Laplace potential and field of point
+# charges, directly and by the FMM on a uniform octree -- the extension the
+# paper names first in its conclusions (Sec. 8), with the solid-harmonic
+# series written out in oracle3d.c.  Expansions are arrays of p * (2p - 1)
+# complex coefficients, index n (2p - 1) + m + p - 1 for degree n < p and
+# order -n <= m <= n (entries with |m| > n unused).
+# ---------------------------------------------------------------------------
+def idx3(p, n, m):
+    """Index of coefficient (n, m) in a 3D expansion of p terms."""
+    return n * (2 * p - 1) + m + p - 1
+
+
+def _cplx(a, size):
+    out = np.zeros(size, dtype=np.complex128) if a is None else np.ascontiguousarray(
+        a, dtype=np.complex128).copy()
+    assert out.size == size
+    return out
+
+
+def harmonics3d(v, P, irregular=True):
+    """Regular R_n^m(v) and irregular I_n^m(v) solid harmonics, n < P, as
+    (P, 2P - 1) complex arrays indexed [n, m + P - 1]."""
+    lib = _load()
+    R = np.zeros(P * (2 * P - 1), np.complex128)
+    Iv = np.zeros(P * (2 * P - 1), np.complex128) if irregular else None
+    _check(lib.o3_harmonics(float(v[0]), float(v[1]), float(v[2]), P, R.ctypes.data,
+                            _ptr(Iv)), "harmonics3d")
+    return R.reshape(P, 2 * P - 1), (None if Iv is None else Iv.reshape(P, 2 * P - 1))
+
+
+def direct3d(x, y, z, q, targets=None):
+    """D3: potential sum_{j != i} q_j / r_ij and field -grad of it at each
+    target (all particles if targets is None)."""
+    lib = _load()
+    x, y, z, q = _f64(x), _f64(y), _f64(z), _f64(q)
+    t = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = x.size if t is None else t.size
+    phi, ex, ey, ez = (np.zeros(nt) for _ in range(4))
+    _check(lib.o3_direct(x.size, x.ctypes.data, y.ctypes.data, z.ctypes.data, q.ctypes.data, nt,
+                         _ptr(t), phi.ctypes.data, ex.ctypes.data, ey.ctypes.data,
+                         ez.ctypes.data), "direct3d")
+    return phi, ex, ey, ez
+
+
+def morton3d(ix, iy, iz, L):
+    return int(_load().o3_morton(ix, iy, iz, L))
+
+
+def bin3d(x, y, z, domain, L):
+    """Morton keys of the leaves (domain = (x0, y0, z0, W))."""
+    lib = _load()
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    key = np.zeros(x.size, np.uint32)
+    _check(lib.o3_bin(x.size, x.ctypes.data, y.ctypes.data, z.ctypes.data, float(domain[0]),
+                      float(domain[1]), float(domain[2]), float(domain[3]), L, key.ctypes.data),
+           "bin3d")
+    return key
+
+
+def sort3d(key, L):
+    """(perm, start): stable order by key, and the 8^L + 1 leaf starts."""
+    lib = _load()
+    key = np.ascontiguousarray(key, dtype=np.uint32)
+    perm = np.zeros(key.size, np.uint32)
+    start = np.zeros((1 << (3 * L)) + 1, np.uint32)
+    _check(lib.o3_sort(key.size, key.ctypes.data, L, perm.ctypes.data, start.ctypes.data),
+           "sort3d")
+    return perm, start
+
+
+def interaction_list3d(l, ix, iy, iz):
+    """(k, 3) array of the source boxes, ascending Morton order."""
+    out = np.zeros(3 * 189, np.int32)
+    k = _load().o3_interaction_list(l, ix, iy, iz, out.ctypes.data)
+    return out[:3 * k].reshape(k, 3)
+
+
+def p2m3d(x, y, z, q, c, p):
+    lib = _load()
+    x, y, z, q = _f64(x), _f64(y), _f64(z), _f64(q)
+    M = np.zeros(p * (2 * p - 1), np.complex128)
+    lib.o3_p2m(x.size, x.ctypes.data, y.ctypes.data, z.ctypes.data, q.ctypes.data,
+               _f64(c).ctypes.data, p, M.ctypes.data)
+    return M
+
+
+def m2m3d(M, c, cp, p):
+    """Shift a multipole expansion from centre c to centre cp."""
+    out = _cplx(None, p * (2 * p - 1))
+    M = _cplx(M, out.size)
+    _load().o3_m2m(p, M.ctypes.data, _f64(c).ctypes.data, _f64(cp).ctypes.data, out.ctypes.data)
+    return out
+
+
+def m2l3d(M, cs, ct, p):
+    """Local expansion about ct of the multipole expansion M about cs."""
+    out = _cplx(None, p * (2 * p - 1))
+    M = _cplx(M, out.size)
+    _load().o3_m2l(p, M.ctypes.data, _f64(cs).ctypes.data, _f64(ct).ctypes.data, out.ctypes.data)
+    return out
+
+
+def l2l3d(Lc, c, cc, p):
+    """Shift a local expansion from centre c to centre cc."""
+    out = _cplx(None, p * (2 * p - 1))
+    Lc = _cplx(Lc, out.size)
+    _load().o3_l2l(p, Lc.ctypes.data, _f64(c).ctypes.data, _f64(cc).ctypes.data, out.ctypes.data)
+    return out
+
+
+def l2p3d(Lc, c, pt, p):
+    """(phi, ex, ey, ez) of a local expansion about c at point pt."""
+    out = np.zeros(4)
+    Lc = _cplx(Lc, p * (2 * p - 1))
+    _load().o3_l2p(p, Lc.ctypes.data, _f64(c).ctypes.data, float(pt[0]), float(pt[1]),
+                   float(pt[2]), out.ctypes.data)
+    return tuple(out)
+
+
+def me_eval3d(M, c, pt, p):
+    """Potential of a multipole expansion about c at point pt."""
+    M = _cplx(M, p * (2 * p - 1))
+    return float(_load().o3_me_eval(p, M.ctypes.data, _f64(c).ctypes.data, float(pt[0]),
+                                    float(pt[1]), float(pt[2])))
+
+
+def fmm3d(x, y, z, q, domain, L, p):
+    """F3: (phi, ex, ey, ez) of every particle by the FMM on the uniform
+    octree of depth L (1..6) with p terms; domain = (x0, y0, z0, W)."""
+    lib = _load()
+    x, y, z, q = _f64(x), _f64(y), _f64(z), _f64(q)
+    n = x.size
+    phi, ex, ey, ez = (np.zeros(n) for _ in range(4))
+    _check(lib.o3_fmm(n, x.ctypes.data, y.ctypes.data, z.ctypes.data, q.ctypes.data,
+                      float(domain[0]), float(domain[1]), float(domain[2]), float(domain[3]), L,
+                      p, phi.ctypes.data, ex.ctypes.data, ey.ctypes.data, ez.ctypes.data),
+           "fmm3d")
+    return phi, ex, ey, ez
