@@ -627,6 +627,70 @@ int petfmm_measure_peaks(petfmm_peaks *out);
 const char *petfmm_strerror(int code);
 int petfmm_version(void);
 
+/* ------------------------------------------------------------------------
+ * Three dimensions: the Laplace potential and field of point charges by the
+ * FMM on a uniform octree -- the extension the paper names first (Sec. 8:
+ * tree, work model and partition unchanged; a new kernel with its 3D series
+ * and translation operators).  For every particle i
+ *     phi_i = sum_{j != i} q_j / |x_i - x_j|,
+ *     E_i   = -grad phi_i = sum_{j != i} q_j (x_i - x_j) / |x_i - x_j|^3,
+ * self and coincident pairs contributing 0.  Series: solid harmonics of the
+ * 1/r kernel with p terms (degrees 0..p-1, p (p + 1) / 2 complex
+ * coefficients per box), rescaled by the box width; near domain = the leaf
+ * and its up to 26 neighbours; interaction list = the children of the
+ * parent's neighbours that are not neighbours of the box (at most 189),
+ * levels >= 2.  Binning and z-order as in 2D with three interleaved
+ * coordinates (bit b of ix, iy, iz to bits 3b, 3b + 1, 3b + 2).
+ * ------------------------------------------------------------------------ */
+typedef struct petfmm3d_ctx petfmm3d_ctx;
+typedef struct {
+    double x0, y0, z0, width; /* closed cube [x0, x0 + W] x [y0, y0 + W] x [z0, z0 + W] */
+} petfmm_domain3d;
+#define PETFMM3D_MAX_L 8
+#define PETFMM3D_MAX_P 16
+
+/* levels 1..PETFMM3D_MAX_L (8^L leaves), order p 1..PETFMM3D_MAX_P;
+ * precision PETFMM_FP64 (every step in FP64) or PETFMM_MIXED (expansions,
+ * translations, near field and L2P in FP32 on leaf-relative coordinates;
+ * binning in FP64); dtype PETFMM_F64 or PETFMM_F32 storage of x, y, z, q and
+ * of the outputs; cuda_stream: the cudaStream_t every launch goes to (NULL:
+ * the legacy default stream).  Uploads the operator tables (synchronous).
+ * Returns PETFMM_OK, PETFMM_EINVAL, PETFMM_ENOMEM or PETFMM_ECUDA. */
+int petfmm3d_create(const petfmm_domain3d *dom, int levels, int order, int precision, int dtype,
+                    void *cuda_stream, petfmm3d_ctx **out);
+/* One evaluation of n particles, asynchronous on the context's stream.
+ * x, y, z, q: device arrays of n values (dtype of the context), read only;
+ * phi, ex, ey, ez: device arrays of n values, written in the caller's order.
+ * The caller owns all eight and keeps them valid until petfmm3d_sync returns.
+ * A particle outside the closed cube (or NaN) is reported as PETFMM_EDOMAIN
+ * by petfmm3d_sync (outputs unspecified).  Grows the context's buffers when n
+ * or the tree needs it (cudaMalloc; PETFMM_ENOMEM if that fails).  Returns
+ * PETFMM_OK, PETFMM_EINVAL (n < 0 or above 2^30, a null array), PETFMM_ENOMEM
+ * or PETFMM_ECUDA. */
+int petfmm3d_evaluate(petfmm3d_ctx *ctx, int64_t n, const void *x, const void *y, const void *z,
+                      const void *q, void *phi, void *ex, void *ey, void *ez);
+/* Waits for the stream; returns the device status of the last evaluation
+ * (PETFMM_OK or PETFMM_EDOMAIN) or PETFMM_ECUDA. */
+int petfmm3d_sync(petfmm3d_ctx *ctx);
+enum { PETFMM3D_OPT_TIMING = 1 /* 1: record CUDA events per stage */ };
+int petfmm3d_set_option(petfmm3d_ctx *ctx, int option, int64_t value);
+enum {
+    PETFMM3D_STAGE_BIN = 0, PETFMM3D_STAGE_SORT, PETFMM3D_STAGE_GATHER, PETFMM3D_STAGE_P2M,
+    PETFMM3D_STAGE_M2M, PETFMM3D_STAGE_M2L, PETFMM3D_STAGE_L2L, PETFMM3D_STAGE_NEAR,
+    PETFMM3D_STAGE_COUNT
+};
+/* milliseconds per stage of the last evaluation (SORT includes the leaf
+ * starts; NEAR is the near field with L2P and the output); returns the
+ * number written, PETFMM_ENOTREADY without a timed evaluation. */
+int petfmm3d_stage_times(petfmm3d_ctx *ctx, float *ms, int cap);
+/* Host copies of the last evaluation's sorted keys and permutation (n each;
+ * perm[r] = input index of sorted rank r) and its 8^L + 1 leaf starts. */
+int petfmm3d_debug_tree(petfmm3d_ctx *ctx, int64_t n, uint32_t *skeys, uint32_t *perm,
+                        uint32_t *start);
+/* kernels this context has launched */
+uint64_t petfmm3d_launches(const petfmm3d_ctx *ctx);
+int petfmm3d_destroy(petfmm3d_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -111,7 +111,7 @@ def header_symbols():
     """Names of the functions the public header declares."""
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(petfmm_[a-z_0-9]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(petfmm(?:3d)?_[a-z_0-9]+)\s*\(", text)))
 
 
 def load():

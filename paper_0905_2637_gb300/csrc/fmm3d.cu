@@ -1,0 +1,1018 @@
+// fmm3d.cu -- the three-dimensional extension and its C ABI (petfmm3d_* in
+// include/petfmm.h).  The paper names 3D as its first extension (Sec. 8):
+// tree, work model and partition carry over, and the new part is a kernel
+// with the 3D series and translation operators.  This file evaluates the
+// Laplace potential and field of point charges,
+//     phi_i = sum_{j != i} q_j / |x_i - x_j|,    E_i = -grad phi_i,
+// by the FMM on a uniform octree: binning with three-coordinate z-order keys
+// (Sec. 2.1, Sec. 5.1), the radix sort and gather of the 2D path, then P2M,
+// M2M, M2L over the interaction list (at most 189 boxes), L2L, and a final
+// per-leaf pass that sums the near field over the leaf and its up to 26
+// neighbours and adds L2P (the steps of Sec. 2.2).
+//
+// Series (the paper gives none for 3D): solid harmonics of the 1/r kernel,
+//   R_n^m(v) = r^n P_n^m(z/r) e^{i m phi} / (n + m)!,
+//   I_n^m(v) = (n - m)! P_n^m(z/r) e^{i m phi} / r^(n+1),
+// P_n^m without the Condon-Shortley phase and X_n^-m = (-1)^m conj(X_n^m),
+// from the Legendre recurrences in Cartesian form (rec_r / rec_i below).
+// They obey 1/|x - y| = sum conj(R_n^m(y)) I_n^m(x), R(a + b) = sum
+// R_k^l(a) R_{n-k}^{m-l}(b) and I_n^m(a + b) = sum (-1)^k conj(R_k^l(b))
+// I_{n+k}^{m+l}(a), so that with M_n^m = sum q conj(R_n^m(y - c)) and
+// phi = sum L_n^m conj(R_n^m(x - c)) the translations are plain sums:
+//   M2M  M'_n^m = sum conj(R_k^l(c - c')) M_{n-k}^{m-l}
+//   M2L  L_k^l  = (-1)^k sum M_n^m I_{n+k}^{m+l}(c_t - c_s)
+//   L2L  L'_j^s = sum L_{j+k}^{s+l} conj(R_k^l(c' - c)).
+// Expansions are rescaled by the box width w (M~ = M / w^n, L~ = L w^(n+1)):
+// every operator is then level independent -- M2L one table of
+// I_j^s(delta) per integer offset delta between same-level boxes, M2M and
+// L2L one table of R_k^l(e) per child octant e = (+-1/4, +-1/4, +-1/4), with
+// the level change a power of two -- and FP32 stays in range for p <= 16.
+// Only m >= 0 is stored (p (p + 1) / 2 complex per box, index n (n + 1) / 2
+// + m); m < 0 follows from the symmetry of a real potential.
+//
+// HBM layout: uint32 key / value ping-pong pairs of the radix sort (3L-bit
+// keys), 8^L + 1 leaf starts, the sorted particles (FP64 path: SoA x, y, z, q
+// in double; mixed path: float4 (xi, eta, zeta, q), the position relative to
+// the leaf centre in leaf widths), ME and LE of every level (8^l boxes in
+// Morton order, level l at box offset (8^l - 1) / 7), the operator tables.
+// Every sum runs in a fixed order: results are bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/petfmm.h"
+#include "kernels.cuh"
+
+using namespace petfmm;
+
+namespace {
+
+constexpr int P3_MAX = PETFMM3D_MAX_P;           // terms
+constexpr int L3_MAX = PETFMM3D_MAX_L;           // levels (3L <= 30 key bits)
+constexpr int NC3_MAX = P3_MAX * (P3_MAX + 1) / 2;  // stored coefficients
+constexpr int OUT3 = (NC3_MAX + 31) / 32;          // per lane, one warp per box
+constexpr int NSLOT3 = 343;                        // offsets in [-3, 3]^3
+constexpr int W3 = 8;                              // warps per block
+
+template <typename T> struct C3;
+template <> struct C3<float> { using V = float2; };
+template <> struct C3<double> { using V = double2; };
+
+template <typename V, typename T>
+__host__ __device__ __forceinline__ V mk(T a, T b) { V v; v.x = a; v.y = b; return v; }
+
+// a sorted particle of the FP64 path: x, y, z, q (32 bytes, one load)
+struct __align__(32) Dbl4 {
+    double x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ int nc3(int p) { return p * (p + 1) / 2; }
+// I_j^s, j < 2p - 1, s >= 0
+__host__ __device__ __forceinline__ int nci3(int p) { return (2 * p - 1) * (2 * p) / 2; }
+__host__ __device__ __forceinline__ int64_t lvl_off3(int l) {
+    return ((int64_t(1) << (3 * l)) - 1) / 7;
+}
+
+// 3D z-order: bit b of ix, iy, iz to bits 3b, 3b + 1, 3b + 2 (10 bits each)
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
+    v &= 0x09249249u;
+    v = (v ^ (v >> 2)) & 0x030c30c3u;
+    v = (v ^ (v >> 4)) & 0x0300f00fu;
+    v = (v ^ (v >> 8)) & 0x030000ffu;
+    v = (v ^ (v >> 16)) & 0x000003ffu;
+    return v;
+}
+__host__ __device__ __forceinline__ uint32_t morton3(uint32_t ix, uint32_t iy, uint32_t iz) {
+    return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+}
+
+// particles in box b of level l (from the leaf starts)
+__device__ __forceinline__ uint32_t box_count3(const uint32_t *start, int L, int l, uint32_t b) {
+    const int sh = 3 * (L - l);
+    return start[(uint64_t(b) + 1) << sh] - start[uint64_t(b) << sh];
+}
+
+// coefficient (n, m) of a stored series; m < 0 by X_n^-m = (-1)^m conj(X_n^m)
+template <typename V>
+__device__ __forceinline__ V coef3(const V *a, int n, int m) {
+    if (m >= 0) return a[n * (n + 1) / 2 + m];
+    const V v = a[n * (n + 1) / 2 - m];
+    return (m & 1) ? mk<V>(-v.x, v.y) : mk<V>(v.x, -v.y);
+}
+
+template <typename V> __device__ __forceinline__ void cmac(V &acc, V a, V b) {  // acc += a b
+    acc.x += a.x * b.x - a.y * b.y;
+    acc.y += a.x * b.y + a.y * b.x;
+}
+template <typename V> __device__ __forceinline__ void cmac_conj(V &acc, V a, V b) {  // acc += conj(a) b
+    acc.x += a.x * b.x + a.y * b.y;
+    acc.y += a.x * b.y - a.y * b.x;
+}
+
+// ---------------------------------------------------------------------------
+// Binning (Sec. 2.1 in 3D): t = x - x0; s = t 2^L / W; floor, clamped; FP64
+// with round-to-nearest intrinsics (no contraction).  recu (mixed path): the
+// record (xi, eta, zeta, q) in input order.
+// ---------------------------------------------------------------------------
+struct Dom3 {
+    double x0, y0, z0, width, scale;  // scale = 2^L / width
+};
+
+__device__ __forceinline__ uint32_t bin3(double v, double v0, double scale, uint32_t nb) {
+    const double f = floor(__dmul_rn(__dsub_rn(v, v0), scale));
+    if (!(f >= 0.0)) return 0u;
+    if (f > double(nb - 1)) return nb - 1;
+    return uint32_t(f);
+}
+
+template <typename TIn>
+__global__ void __launch_bounds__(256) k3_bin(int64_t n, const TIn *__restrict__ x,
+                                              const TIn *__restrict__ y, const TIn *__restrict__ z,
+                                              const TIn *__restrict__ q, Dom3 d, int L,
+                                              uint32_t *__restrict__ keys,
+                                              float4 *__restrict__ recu, int *status) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double X = double(x[j]), Y = double(y[j]), Z = double(z[j]);
+    const double x1 = __dadd_rn(d.x0, d.width), y1 = __dadd_rn(d.y0, d.width),
+                 z1 = __dadd_rn(d.z0, d.width);
+    if (!(X >= d.x0 && X <= x1 && Y >= d.y0 && Y <= y1 && Z >= d.z0 && Z <= z1))
+        set_status(status, ST_EDOMAIN);
+    const uint32_t nb = 1u << L;
+    const uint32_t ix = bin3(X, d.x0, d.scale, nb), iy = bin3(Y, d.y0, d.scale, nb),
+                   iz = bin3(Z, d.z0, d.scale, nb);
+    keys[j] = morton3(ix, iy, iz);
+    if (recu) {
+        float4 r;
+        r.x = float(__dsub_rn(__dmul_rn(__dsub_rn(X, d.x0), d.scale), double(ix) + 0.5));
+        r.y = float(__dsub_rn(__dmul_rn(__dsub_rn(Y, d.y0), d.scale), double(iy) + 0.5));
+        r.z = float(__dsub_rn(__dmul_rn(__dsub_rn(Z, d.z0), d.scale), double(iz) + 0.5));
+        r.w = float(q[j]);
+        recu[j] = r;
+    }
+}
+
+// start[b] = first sorted rank with key >= b, b = 0..8^L
+__global__ void __launch_bounds__(256) k3_leaf_start(const uint32_t *__restrict__ skeys, int64_t n,
+                                                     int64_t nleaf, uint32_t *__restrict__ start) {
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b > nleaf) return;
+    int64_t lo = 0, hi = n;
+    if (b == nleaf) {
+        lo = n;
+    } else {
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (int64_t(skeys[mid]) < b) lo = mid + 1; else hi = mid;
+        }
+    }
+    start[b] = uint32_t(lo);
+}
+
+template <typename TIn>
+__global__ void __launch_bounds__(256) k3_gather_f64(int64_t n, const uint32_t *__restrict__ perm,
+                                                     const TIn *__restrict__ x,
+                                                     const TIn *__restrict__ y,
+                                                     const TIn *__restrict__ z,
+                                                     const TIn *__restrict__ q,
+                                                     Dbl4 *__restrict__ out) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t i = perm[r];
+    if (!PF_IN(i, n)) return;
+    out[r] = Dbl4{double(x[i]), double(y[i]), double(z[i]), double(q[i])};
+}
+
+// A particle of the leaf as (position relative to the leaf centre in leaf
+// widths, charge).
+template <typename T> struct Part3 { T x, y, z, q; };
+__device__ __forceinline__ Part3<float> leaf_part(const float4 *rec, int64_t j, double, double,
+                                                  double, double) {
+    const float4 r = rec[j];
+    return {r.x, r.y, r.z, r.w};
+}
+__device__ __forceinline__ Part3<double> leaf_part(const Dbl4 *xs, int64_t j, double cx,
+                                                   double cy, double cz, double inv_w) {
+    const Dbl4 r = xs[j];
+    return {(r.x - cx) * inv_w, (r.y - cy) * inv_w, (r.z - cz) * inv_w, r.w};
+}
+
+// ---------------------------------------------------------------------------
+// P2M (leaves): M~_n^m = sum_j q_j conj(R_n^m(xi_j)).  A warp per leaf; lane
+// m < p owns column m: R_m^m = (xi + i eta)^m / (2^m m!), then the recurrence
+// in n, for every particle of the leaf in order.
+// ---------------------------------------------------------------------------
+template <typename T, typename P>
+__global__ void __launch_bounds__(W3 * 32) k3_p2m(int L, int p, Dom3 d, const uint32_t *__restrict__ start,
+                                                  const P *__restrict__ part,
+                                                  typename C3<T>::V *__restrict__ me) {
+    using V = typename C3<T>::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = int64_t(blockIdx.x) * W3 + (threadIdx.x >> 5);
+    if (b >= (int64_t(1) << (3 * L))) return;
+    const uint32_t s0 = start[b], s1 = start[b + 1];
+    if (s0 == s1) return;
+    const int m = lane;
+    const double w = d.width / double(1u << L);
+    const double cx = d.x0 + (double(compact3(uint32_t(b))) + 0.5) * w;
+    const double cy = d.y0 + (double(compact3(uint32_t(b) >> 1)) + 0.5) * w;
+    const double cz = d.z0 + (double(compact3(uint32_t(b) >> 2)) + 0.5) * w;
+    V acc[P3_MAX];
+#pragma unroll
+    for (int n = 0; n < P3_MAX; ++n) acc[n] = mk<V>(T(0), T(0));
+    if (m < p) {
+        for (uint32_t j = s0; j < s1; ++j) {
+            const Part3<T> a = leaf_part(part, j, cx, cy, cz, 1.0 / w);
+            const T r2 = a.x * a.x + a.y * a.y + a.z * a.z;
+            V rmm = mk<V>(a.q, T(0));  // q R_0^0, then q R_m^m
+            for (int t = 1; t <= m; ++t) {
+                const T s = T(1) / T(2 * t);
+                rmm = mk<V>((rmm.x * a.x - rmm.y * a.y) * s, (rmm.x * a.y + rmm.y * a.x) * s);
+            }
+            V r1 = rmm, r2v = mk<V>(T(0), T(0));
+#pragma unroll
+            for (int n = 0; n < P3_MAX; ++n) {
+                if (n < m || n >= p) continue;
+                V rn = r1;
+                if (n > m) {
+                    const T inv = T(1) / T(n * n - m * m);
+                    const T c1 = T(2 * n - 1) * a.z;
+                    rn = mk<V>((c1 * r1.x - r2 * r2v.x) * inv, (c1 * r1.y - r2 * r2v.y) * inv);
+                    r2v = r1;
+                    r1 = rn;
+                }
+                acc[n].x += rn.x;  // q conj(R) summed: conj taken at the end
+                acc[n].y += rn.y;
+            }
+        }
+        V *dst = me + (lvl_off3(L) + b) * nc3(p);
+#pragma unroll
+        for (int n = 0; n < P3_MAX; ++n)
+            if (n >= m && n < p) dst[n * (n + 1) / 2 + m] = mk<V>(acc[n].x, -acc[n].y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2M (parent level l from level l + 1): M~'_n^m = sum_children sum_{k,l}
+// conj(R_k^l(e_c)) 2^-(n-k) M~_{n-k}^{m-l}.  A warp per parent box, lanes over
+// output coefficients, children in octant order.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(W3 * 32) k3_m2m(int l, int L, int p, const uint32_t *__restrict__ start,
+                                                  const typename C3<T>::V *__restrict__ rtab,
+                                                  typename C3<T>::V *__restrict__ me) {
+    using V = typename C3<T>::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = int64_t(blockIdx.x) * W3 + (threadIdx.x >> 5);
+    if (b >= (int64_t(1) << (3 * l))) return;
+    if (box_count3(start, L, l, uint32_t(b)) == 0) return;
+    const int nc = nc3(p);
+    V acc[OUT3];
+    int on[OUT3], om[OUT3];
+#pragma unroll
+    for (int u = 0; u < OUT3; ++u) {
+        acc[u] = mk<V>(T(0), T(0));
+        const int j = lane + 32 * u;
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= j) ++n;
+        on[u] = n;
+        om[u] = j - n * (n + 1) / 2;
+    }
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t cb = uint32_t(b) * 8u + uint32_t(c);
+        if (box_count3(start, L, l + 1, cb) == 0) continue;
+        const V *mc = me + (lvl_off3(l + 1) + cb) * nc;
+        const V *rt = rtab + c * nc;
+#pragma unroll
+        for (int u = 0; u < OUT3; ++u) {
+            if (lane + 32 * u >= nc) continue;
+            const int n = on[u], m = om[u];
+            V s = mk<V>(T(0), T(0));
+            for (int k = 0; k <= n; ++k) {
+                V sk = mk<V>(T(0), T(0));
+                for (int ll = -k; ll <= k; ++ll) {
+                    const int mm = m - ll;
+                    if (mm < -(n - k) || mm > n - k) continue;
+                    cmac_conj(sk, coef3(rt, k, ll), coef3(mc, n - k, mm));
+                }
+                const T sc = T(ldexp(1.0, -(n - k)));
+                s.x += sk.x * sc;
+                s.y += sk.y * sc;
+            }
+            acc[u].x += s.x;
+            acc[u].y += s.y;
+        }
+    }
+    V *dst = me + (lvl_off3(l) + b) * nc;
+#pragma unroll
+    for (int u = 0; u < OUT3; ++u)
+        if (lane + 32 * u < nc) dst[lane + 32 * u] = acc[u];
+}
+
+// ---------------------------------------------------------------------------
+// M2L (level l >= 2): L~_k^l = (-1)^k sum_{n,m} M~_n^m I_{n+k}^{m+l}(delta),
+// delta = target - source in box widths, over the interaction list: the
+// children of the parent's neighbours that are not neighbours of the box,
+// in a fixed order.  A warp per target box; the source's expansion is staged
+// in shared memory for the warp, lanes over output coefficients.  The result
+// is written (the L2L that follows adds the parent's part).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(W3 * 32) k3_m2l(int l, int L, int p, const uint32_t *__restrict__ start,
+                                                  const typename C3<T>::V *__restrict__ itab,
+                                                  const typename C3<T>::V *__restrict__ me,
+                                                  typename C3<T>::V *__restrict__ le) {
+    using V = typename C3<T>::V;
+    __shared__ V sme[W3][NC3_MAX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t b = int64_t(blockIdx.x) * W3 + wid;
+    if (b >= (int64_t(1) << (3 * l))) return;
+    if (box_count3(start, L, l, uint32_t(b)) == 0) return;
+    const int nc = nc3(p), nci = nci3(p);
+    const int ix = int(compact3(uint32_t(b))), iy = int(compact3(uint32_t(b) >> 1)),
+              iz = int(compact3(uint32_t(b) >> 2));
+    const int pside = 1 << (l - 1);
+    V acc[OUT3];
+    int on[OUT3], om[OUT3];
+#pragma unroll
+    for (int u = 0; u < OUT3; ++u) {
+        acc[u] = mk<V>(T(0), T(0));
+        const int j = lane + 32 * u;
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= j) ++n;
+        on[u] = n;
+        om[u] = j - n * (n + 1) / 2;
+    }
+    const V *lev = me + lvl_off3(l) * nc;
+    for (int qz = (iz >> 1) - 1; qz <= (iz >> 1) + 1; ++qz)
+        for (int qy = (iy >> 1) - 1; qy <= (iy >> 1) + 1; ++qy)
+            for (int qx = (ix >> 1) - 1; qx <= (ix >> 1) + 1; ++qx) {
+                if (qx < 0 || qy < 0 || qz < 0 || qx >= pside || qy >= pside || qz >= pside)
+                    continue;
+                for (int c = 0; c < 8; ++c) {
+                    const int sx = 2 * qx + (c & 1), sy = 2 * qy + ((c >> 1) & 1),
+                              sz = 2 * qz + (c >> 2);
+                    const int dx = ix - sx, dy = iy - sy, dz = iz - sz;
+                    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) continue;
+                    const uint32_t sb = morton3(uint32_t(sx), uint32_t(sy), uint32_t(sz));
+                    if (box_count3(start, L, l, sb) == 0) continue;
+                    __syncwarp();
+                    for (int i = lane; i < nc; i += 32) sme[wid][i] = lev[int64_t(sb) * nc + i];
+                    __syncwarp();
+                    const V *tab = itab + ((dx + 3) + 7 * (dy + 3) + 49 * (dz + 3)) * nci;
+#pragma unroll
+                    for (int u = 0; u < OUT3; ++u) {
+                        if (lane + 32 * u >= nc) continue;
+                        const int k = on[u], lo = om[u];
+                        V s = mk<V>(T(0), T(0));
+                        for (int n = 0; n < p; ++n)
+                            for (int m = -n; m <= n; ++m)
+                                cmac(s, coef3(sme[wid], n, m), coef3(tab, n + k, m + lo));
+                        if (k & 1) {
+                            acc[u].x -= s.x;
+                            acc[u].y -= s.y;
+                        } else {
+                            acc[u].x += s.x;
+                            acc[u].y += s.y;
+                        }
+                    }
+                }
+            }
+    V *dst = le + (lvl_off3(l) + b) * nc;
+#pragma unroll
+    for (int u = 0; u < OUT3; ++u)
+        if (lane + 32 * u < nc) dst[lane + 32 * u] = acc[u];
+}
+
+// ---------------------------------------------------------------------------
+// L2L (child level l >= 3): L~'_j^s += 2^-(j+1) sum_{k,l} L~_{j+k}^{s+l}(parent)
+// conj(R_k^l(e_c)).  A warp per child box.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(W3 * 32) k3_l2l(int l, int L, int p, const uint32_t *__restrict__ start,
+                                                  const typename C3<T>::V *__restrict__ rtab,
+                                                  typename C3<T>::V *__restrict__ le) {
+    using V = typename C3<T>::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t cb = int64_t(blockIdx.x) * W3 + (threadIdx.x >> 5);
+    if (cb >= (int64_t(1) << (3 * l))) return;
+    if (box_count3(start, L, l, uint32_t(cb)) == 0) return;
+    const int nc = nc3(p);
+    const V *lp = le + (lvl_off3(l - 1) + (cb >> 3)) * nc;
+    const V *rt = rtab + int(cb & 7) * nc;
+    V *dst = le + (lvl_off3(l) + cb) * nc;
+    for (int j0 = lane; j0 < nc; j0 += 32) {
+        int j = 0;
+        while ((j + 1) * (j + 2) / 2 <= j0) ++j;
+        const int s = j0 - j * (j + 1) / 2;
+        V acc = mk<V>(T(0), T(0));
+        for (int k = 0; j + k < p; ++k)
+            for (int ll = -k; ll <= k; ++ll) {
+                const int ss = s + ll;
+                if (ss < -(j + k) || ss > j + k) continue;
+                cmac_conj(acc, coef3(rt, k, ll), coef3(lp, j + k, ss));
+            }
+        const T sc = T(ldexp(1.0, -(j + 1)));
+        V o = dst[j0];
+        o.x += acc.x * sc;
+        o.y += acc.y * sc;
+        dst[j0] = o;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2P in leaf units: phi = sum L~_n^m conj(R_n^m(xi)) and g = grad_xi of it,
+// column by column (m >= 0, weight 2 for m > 0: the m and -m terms of a real
+// potential are conjugate), with
+//   d/dz:  sum conj(R_n^m) L_{n+1}^m
+//   d/dx:  sum conj(R_n^m) (L_{n+1}^{m+1} - L_{n+1}^{m-1}) / 2
+//   d/dy:  sum conj(R_n^m) (-i / 2) (L_{n+1}^{m+1} + L_{n+1}^{m-1})
+// (from d/dz R_n^m = R_{n-1}^m, (d/dx -+ i d/dy) R_n^m = +-R_{n-1}^{m-+1}).
+// ---------------------------------------------------------------------------
+template <typename T, typename V>
+__device__ __forceinline__ void l2p3(const V *lc, int p, T x, T y, T z, T &phi, T &gx, T &gy,
+                                     T &gz) {
+    const T r2 = x * x + y * y + z * z;
+    V rmm = mk<V>(T(1), T(0));
+    for (int mu = 0; mu < p; ++mu) {
+        if (mu > 0) {
+            const T s = T(1) / T(2 * mu);
+            rmm = mk<V>((rmm.x * x - rmm.y * y) * s, (rmm.x * y + rmm.y * x) * s);
+        }
+        const T wgt = mu == 0 ? T(1) : T(2);
+        V r1 = rmm, r2v = mk<V>(T(0), T(0));
+        for (int n = mu; n < p; ++n) {
+            V rn = r1;
+            if (n > mu) {
+                const T inv = T(1) / T(n * n - mu * mu);
+                const T c1 = T(2 * n - 1) * z;
+                rn = mk<V>((c1 * r1.x - r2 * r2v.x) * inv, (c1 * r1.y - r2 * r2v.y) * inv);
+                r2v = r1;
+                r1 = rn;
+            }
+            const V a = lc[n * (n + 1) / 2 + mu];
+            phi += wgt * (a.x * rn.x + a.y * rn.y);  // Re(a conj(rn))
+            if (n + 1 < p) {
+                const int o = (n + 1) * (n + 2) / 2;
+                const V lz = lc[o + mu], lpv = lc[o + mu + 1];
+                V lm;
+                if (mu >= 1) {
+                    lm = lc[o + mu - 1];
+                } else {
+                    const V l1 = lc[o + 1];
+                    lm = mk<V>(-l1.x, l1.y);  // L^-1 = -conj(L^1)
+                }
+                // Re(conj(rn) A) = rn.x A.x + rn.y A.y
+                const T axr = (lpv.x - lm.x) * T(0.5), axi = (lpv.y - lm.y) * T(0.5);
+                const T ayr = (lpv.y + lm.y) * T(0.5), ayi = -(lpv.x + lm.x) * T(0.5);
+                gx += wgt * (rn.x * axr + rn.y * axi);
+                gy += wgt * (rn.x * ayr + rn.y * ayi);
+                gz += wgt * (rn.x * lz.x + rn.y * lz.y);
+            }
+        }
+    }
+}
+
+template <typename TOut>
+__device__ __forceinline__ void store3(void *o, int64_t i, double v) {
+    static_cast<TOut *>(o)[i] = TOut(v);
+}
+
+// ---------------------------------------------------------------------------
+// Near field + L2P, mixed path: a warp per leaf, a lane per target (32 at a
+// time); sources of the leaf and its neighbours in a fixed order (dz, dy, dx,
+// then sorted rank), read once per warp (all lanes the same address) in FP32
+// leaf units: d = xi_t - (xi_s + offset), 1/|d| from rsqrt, self and
+// coincident pairs (|d| = 0) skipped.  Output in the caller's order.
+// ---------------------------------------------------------------------------
+template <typename TOut>
+__global__ void __launch_bounds__(W3 * 32) k3_near_mixed(int L, int p, double w,
+                                                         const uint32_t *__restrict__ start,
+                                                         const float4 *__restrict__ rec,
+                                                         const float2 *__restrict__ le,
+                                                         const uint32_t *__restrict__ perm,
+                                                         int64_t n, void *phi, void *ex, void *ey,
+                                                         void *ez) {
+    __shared__ float2 sle[W3][NC3_MAX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t b = int64_t(blockIdx.x) * W3 + wid;
+    if (b >= (int64_t(1) << (3 * L))) return;
+    const uint32_t s0 = start[b], s1 = start[b + 1];
+    if (s0 == s1) return;
+    const int nc = nc3(p);
+    const bool far = L >= 2;
+    if (far)
+        for (int i = lane; i < nc; i += 32) sle[wid][i] = le[(lvl_off3(L) + b) * nc + i];
+    __syncwarp();
+    const int ix = int(compact3(uint32_t(b))), iy = int(compact3(uint32_t(b) >> 1)),
+              iz = int(compact3(uint32_t(b) >> 2));
+    const int side = 1 << L;
+    const float inv_w = float(1.0 / w), inv_w2 = float(1.0 / (w * w));
+    for (uint32_t t0 = s0; t0 < s1; t0 += 32) {
+        const uint32_t i = t0 + uint32_t(lane);
+        const bool valid = i < s1;
+        const float4 tg = valid ? rec[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int nx = ix + dx, ny = iy + dy, nz = iz + dz;
+                    if (nx < 0 || ny < 0 || nz < 0 || nx >= side || ny >= side || nz >= side)
+                        continue;
+                    const uint32_t nb = morton3(uint32_t(nx), uint32_t(ny), uint32_t(nz));
+                    const uint32_t a = start[nb], e = start[nb + 1];
+                    const float ox = tg.x - float(dx), oy = tg.y - float(dy), oz = tg.z - float(dz);
+                    for (uint32_t j = a; j < e; ++j) {
+                        const float4 s = rec[j];
+                        const float ddx = ox - s.x, ddy = oy - s.y, ddz = oz - s.z;
+                        const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                        const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        const float qr = s.w * ri;
+                        const float qr3 = qr * ri * ri;
+                        f += qr;
+                        gx = fmaf(qr3, ddx, gx);
+                        gy = fmaf(qr3, ddy, gy);
+                        gz = fmaf(qr3, ddz, gz);
+                    }
+                }
+        float ff = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+        if (far) l2p3<float, float2>(sle[wid], p, tg.x, tg.y, tg.z, ff, fx, fy, fz);
+        if (valid) {
+            const int64_t o = perm[i];
+            if (!PF_IN(o, n)) continue;
+            store3<TOut>(phi, o, double((f + ff) * inv_w));
+            store3<TOut>(ex, o, double((gx - fx) * inv_w2));
+            store3<TOut>(ey, o, double((gy - fy) * inv_w2));
+            store3<TOut>(ez, o, double((gz - fz) * inv_w2));
+        }
+    }
+}
+
+// The FP64 path: global coordinates, 1/r by division and sqrt.
+template <typename TOut>
+__global__ void __launch_bounds__(W3 * 32) k3_near_f64(int L, int p, Dom3 d,
+                                                       const uint32_t *__restrict__ start,
+                                                       const Dbl4 *__restrict__ xs,
+                                                       const double2 *__restrict__ le,
+                                                       const uint32_t *__restrict__ perm,
+                                                       int64_t n, void *phi, void *ex, void *ey,
+                                                       void *ez) {
+    __shared__ double2 sle[W3][NC3_MAX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t b = int64_t(blockIdx.x) * W3 + wid;
+    if (b >= (int64_t(1) << (3 * L))) return;
+    const uint32_t s0 = start[b], s1 = start[b + 1];
+    if (s0 == s1) return;
+    const int nc = nc3(p);
+    const bool far = L >= 2;
+    if (far)
+        for (int i = lane; i < nc; i += 32) sle[wid][i] = le[(lvl_off3(L) + b) * nc + i];
+    __syncwarp();
+    const int ix = int(compact3(uint32_t(b))), iy = int(compact3(uint32_t(b) >> 1)),
+              iz = int(compact3(uint32_t(b) >> 2));
+    const int side = 1 << L;
+    const double w = d.width / double(side);
+    const double cx = d.x0 + (ix + 0.5) * w, cy = d.y0 + (iy + 0.5) * w,
+                 cz = d.z0 + (iz + 0.5) * w;
+    for (uint32_t t0 = s0; t0 < s1; t0 += 32) {
+        const uint32_t i = t0 + uint32_t(lane);
+        const bool valid = i < s1;
+        const Dbl4 tg = valid ? xs[i] : Dbl4{cx, cy, cz, 0.0};
+        double f = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int nx = ix + dx, ny = iy + dy, nz = iz + dz;
+                    if (nx < 0 || ny < 0 || nz < 0 || nx >= side || ny >= side || nz >= side)
+                        continue;
+                    const uint32_t nb = morton3(uint32_t(nx), uint32_t(ny), uint32_t(nz));
+                    const uint32_t a = start[nb], e = start[nb + 1];
+                    for (uint32_t j = a; j < e; ++j) {
+                        const Dbl4 s = xs[j];
+                        const double ddx = tg.x - s.x, ddy = tg.y - s.y, ddz = tg.z - s.z;
+                        const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        if (r2 == 0.0) continue;
+                        const double ri = 1.0 / sqrt(r2);
+                        const double qr = s.w * ri;
+                        const double qr3 = qr * ri * ri;
+                        f += qr;
+                        gx += qr3 * ddx;
+                        gy += qr3 * ddy;
+                        gz += qr3 * ddz;
+                    }
+                }
+        double ff = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
+        if (far)
+            l2p3<double, double2>(sle[wid], p, (tg.x - cx) / w, (tg.y - cy) / w, (tg.z - cz) / w,
+                                  ff, fx, fy, fz);
+        if (valid) {
+            const int64_t o = perm[i];
+            if (!PF_IN(o, n)) continue;
+            store3<TOut>(phi, o, f + ff / w);
+            store3<TOut>(ex, o, gx - fx / (w * w));
+            store3<TOut>(ey, o, gy - fy / (w * w));
+            store3<TOut>(ez, o, gz - fz / (w * w));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host: operator tables in FP64 from the same recurrences.
+// ---------------------------------------------------------------------------
+using cd = std::complex<double>;
+
+// R_n^m(v), n < P, m >= 0: out[n (n + 1) / 2 + m]
+void host_rec_r(double x, double y, double z, int P, cd *out) {
+    const double r2 = x * x + y * y + z * z;
+    cd rmm(1.0, 0.0);
+    for (int m = 0; m < P; ++m) {
+        if (m > 0) rmm *= cd(x, y) / double(2 * m);
+        cd r1 = rmm, r0(0.0, 0.0);
+        for (int n = m; n < P; ++n) {
+            cd rn = r1;
+            if (n > m) {
+                rn = (double(2 * n - 1) * z * r1 - r2 * r0) / double(n * n - m * m);
+                r0 = r1;
+                r1 = rn;
+            }
+            out[n * (n + 1) / 2 + m] = rn;
+        }
+    }
+}
+
+// I_n^m(v), n < P, m >= 0
+void host_rec_i(double x, double y, double z, int P, cd *out) {
+    const double r2 = x * x + y * y + z * z;
+    cd imm(1.0 / std::sqrt(r2), 0.0);
+    for (int m = 0; m < P; ++m) {
+        if (m > 0) imm *= double(2 * m - 1) * cd(x, y) / r2;
+        cd i1 = imm, i0(0.0, 0.0);
+        for (int n = m; n < P; ++n) {
+            cd in = i1;
+            if (n > m) {
+                in = (double(2 * n - 1) * z * i1 - double((n - 1) * (n - 1) - m * m) * i0) / r2;
+                i0 = i1;
+                i1 = in;
+            }
+            out[n * (n + 1) / 2 + m] = in;
+        }
+    }
+}
+
+struct DevBuf3 {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+int ensure3(DevBuf3 &b, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return PETFMM_OK;
+    if (b.p) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return PETFMM_ECUDA;
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return PETFMM_ENOMEM;
+    }
+    b.cap = bytes;
+    return PETFMM_OK;
+}
+
+}  // namespace
+
+struct petfmm3d_ctx {
+    petfmm_domain3d dom{};
+    int L = 0, p = 0, precision = 0, dtype = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf3 keysA, keysB, valsA, valsB, sortw, start, recu, rec, xs, me, le, status;
+    DevBuf3 rtab32, itab32, rtab64, itab64;
+    bool timing = false, ev_recorded = false;
+    cudaEvent_t ev[PETFMM3D_STAGE_COUNT + 1] = {};
+    uint64_t launches = 0, evaluations = 0;
+    int64_t last_n = 0;
+    bool sorted_in_first = true;
+};
+
+namespace {
+
+#define P3_TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+#define P3_CUDA(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { cudaGetLastError(); \
+    return e_ == cudaErrorMemoryAllocation ? PETFMM_ENOMEM : PETFMM_ECUDA; } } while (0)
+
+int upload_tables(petfmm3d_ctx *c) {
+    const int p = c->p, nc = nc3(p), nci = nci3(p);
+    std::vector<cd> rt(size_t(8) * nc), it(size_t(NSLOT3) * nci, cd(0.0, 0.0));
+    for (int o = 0; o < 8; ++o)
+        host_rec_r((o & 1) ? 0.25 : -0.25, (o & 2) ? 0.25 : -0.25, (o & 4) ? 0.25 : -0.25, p,
+                   rt.data() + size_t(o) * nc);
+    for (int dz = -3; dz <= 3; ++dz)
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -3; dx <= 3; ++dx) {
+                if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) < 2) continue;
+                host_rec_i(dx, dy, dz, 2 * p - 1,
+                           it.data() + size_t((dx + 3) + 7 * (dy + 3) + 49 * (dz + 3)) * nci);
+            }
+    std::vector<double2> r64(rt.size()), i64(it.size());
+    std::vector<float2> r32(rt.size()), i32(it.size());
+    for (size_t i = 0; i < rt.size(); ++i) {
+        r64[i] = make_double2(rt[i].real(), rt[i].imag());
+        r32[i] = make_float2(float(rt[i].real()), float(rt[i].imag()));
+    }
+    for (size_t i = 0; i < it.size(); ++i) {
+        i64[i] = make_double2(it[i].real(), it[i].imag());
+        i32[i] = make_float2(float(it[i].real()), float(it[i].imag()));
+    }
+    P3_TRY(ensure3(c->rtab64, r64.size() * sizeof(double2), c->stream));
+    P3_TRY(ensure3(c->itab64, i64.size() * sizeof(double2), c->stream));
+    P3_TRY(ensure3(c->rtab32, r32.size() * sizeof(float2), c->stream));
+    P3_TRY(ensure3(c->itab32, i32.size() * sizeof(float2), c->stream));
+    P3_CUDA(cudaMemcpy(c->rtab64.p, r64.data(), r64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    P3_CUDA(cudaMemcpy(c->itab64.p, i64.data(), i64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    P3_CUDA(cudaMemcpy(c->rtab32.p, r32.data(), r32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    P3_CUDA(cudaMemcpy(c->itab32.p, i32.data(), i32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    return PETFMM_OK;
+}
+
+void mark3(petfmm3d_ctx *c, int s) {
+    if (c->timing) cudaEventRecord(c->ev[s], c->stream);
+}
+
+unsigned grid_w(int64_t warps) { return unsigned((warps + W3 - 1) / W3); }
+
+template <typename T>
+int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
+    using V = typename C3<T>::V;
+    const int L = c->L, p = c->p;
+    cudaStream_t st = c->stream;
+    V *me = static_cast<V *>(c->me.p), *le = static_cast<V *>(c->le.p);
+    const bool f32 = sizeof(T) == 4;
+    const V *rtab = static_cast<const V *>(f32 ? c->rtab32.p : c->rtab64.p);
+    const V *itab = static_cast<const V *>(f32 ? c->itab32.p : c->itab64.p);
+    const Dom3 d{c->dom.x0, c->dom.y0, c->dom.z0, c->dom.width, std::ldexp(1.0, L) / c->dom.width};
+    mark3(c, PETFMM3D_STAGE_P2M);
+    if constexpr (sizeof(T) == 4)
+        k3_p2m<T, float4><<<grid_w(int64_t(1) << (3 * L)), W3 * 32, 0, st>>>(
+            L, p, d, start, static_cast<const float4 *>(c->rec.p), me);
+    else
+        k3_p2m<T, Dbl4><<<grid_w(int64_t(1) << (3 * L)), W3 * 32, 0, st>>>(
+            L, p, d, start, static_cast<const Dbl4 *>(c->xs.p), me);
+    P3_CUDA(cudaGetLastError());
+    c->launches++;
+    mark3(c, PETFMM3D_STAGE_M2M);
+    for (int l = L - 1; l >= 2; --l) {
+        k3_m2m<T><<<grid_w(int64_t(1) << (3 * l)), W3 * 32, 0, st>>>(l, L, p, start, rtab, me);
+        P3_CUDA(cudaGetLastError());
+        c->launches++;
+    }
+    mark3(c, PETFMM3D_STAGE_M2L);
+    for (int l = 2; l <= L; ++l) {
+        k3_m2l<T><<<grid_w(int64_t(1) << (3 * l)), W3 * 32, 0, st>>>(l, L, p, start, itab, me, le);
+        P3_CUDA(cudaGetLastError());
+        c->launches++;
+    }
+    mark3(c, PETFMM3D_STAGE_L2L);
+    for (int l = 3; l <= L; ++l) {
+        k3_l2l<T><<<grid_w(int64_t(1) << (3 * l)), W3 * 32, 0, st>>>(l, L, p, start, rtab, le);
+        P3_CUDA(cudaGetLastError());
+        c->launches++;
+    }
+    return PETFMM_OK;
+}
+
+int evaluate3(petfmm3d_ctx *c, int64_t n, const void *x, const void *y, const void *z,
+              const void *q, void *phi, void *ex, void *ey, void *ez) {
+    cudaStream_t st = c->stream;
+    const int L = c->L, p = c->p;
+    const bool mixed = c->precision == PETFMM_MIXED, f32 = c->dtype == PETFMM_F32;
+    P3_TRY(ensure3(c->status, 16, st));
+    P3_CUDA(cudaMemsetAsync(c->status.p, 0, sizeof(int), st));
+    c->last_n = n;
+    c->ev_recorded = false;
+    if (n == 0) return PETFMM_OK;
+    const int64_t nleaf = int64_t(1) << (3 * L);
+    const int64_t nbox = lvl_off3(L + 1);
+    const size_t es = mixed ? sizeof(float2) : sizeof(double2);
+    P3_TRY(ensure3(c->keysA, size_t(n) * 4, st));
+    P3_TRY(ensure3(c->keysB, size_t(n) * 4, st));
+    P3_TRY(ensure3(c->valsA, size_t(n) * 4, st));
+    P3_TRY(ensure3(c->valsB, size_t(n) * 4, st));
+    P3_TRY(ensure3(c->sortw, size_t(radix_scratch_words(n)) * 4, st));
+    P3_TRY(ensure3(c->start, size_t(nleaf + 1) * 4, st));
+    P3_TRY(ensure3(c->me, size_t(nbox) * nc3(p) * es, st));
+    P3_TRY(ensure3(c->le, size_t(nbox) * nc3(p) * es, st));
+    if (mixed) {
+        P3_TRY(ensure3(c->recu, size_t(n) * sizeof(float4), st));
+        P3_TRY(ensure3(c->rec, size_t(n) * sizeof(float4), st));
+    } else {
+        P3_TRY(ensure3(c->xs, size_t(n) * sizeof(Dbl4), st));
+    }
+    uint32_t *kA = static_cast<uint32_t *>(c->keysA.p), *kB = static_cast<uint32_t *>(c->keysB.p);
+    uint32_t *vA = static_cast<uint32_t *>(c->valsA.p), *vB = static_cast<uint32_t *>(c->valsB.p);
+    uint32_t *start = static_cast<uint32_t *>(c->start.p);
+    int *status = static_cast<int *>(c->status.p);
+    const Dom3 d{c->dom.x0, c->dom.y0, c->dom.z0, c->dom.width, std::ldexp(1.0, L) / c->dom.width};
+    const unsigned gp = unsigned((n + 255) / 256);
+    float4 *recu = mixed ? static_cast<float4 *>(c->recu.p) : nullptr;
+
+    mark3(c, PETFMM3D_STAGE_BIN);
+    if (f32)
+        k3_bin<float><<<gp, 256, 0, st>>>(n, static_cast<const float *>(x), static_cast<const float *>(y),
+                                          static_cast<const float *>(z), static_cast<const float *>(q),
+                                          d, L, kA, recu, status);
+    else
+        k3_bin<double><<<gp, 256, 0, st>>>(n, static_cast<const double *>(x), static_cast<const double *>(y),
+                                           static_cast<const double *>(z), static_cast<const double *>(q),
+                                           d, L, kA, recu, status);
+    P3_CUDA(cudaGetLastError());
+    c->launches++;
+    mark3(c, PETFMM3D_STAGE_SORT);
+    bool in_first = true;
+    P3_CUDA(radix_sort(kA, vA, kB, vB, n, 3 * L, static_cast<uint32_t *>(c->sortw.p), &in_first, st,
+                       &c->launches));
+    c->sorted_in_first = in_first;
+    const uint32_t *skeys = in_first ? kA : kB;
+    const uint32_t *perm = in_first ? vA : vB;
+    k3_leaf_start<<<unsigned((nleaf + 1 + 255) / 256), 256, 0, st>>>(skeys, n, nleaf, start);
+    P3_CUDA(cudaGetLastError());
+    c->launches++;
+    mark3(c, PETFMM3D_STAGE_GATHER);
+    if (mixed) {
+        P3_CUDA(launch_gather_mixed(recu, perm, static_cast<float4 *>(c->rec.p), n, st, &c->launches));
+    } else {
+        Dbl4 *xs = static_cast<Dbl4 *>(c->xs.p);
+        if (f32)
+            k3_gather_f64<float><<<gp, 256, 0, st>>>(n, perm, static_cast<const float *>(x),
+                                                     static_cast<const float *>(y),
+                                                     static_cast<const float *>(z),
+                                                     static_cast<const float *>(q), xs);
+        else
+            k3_gather_f64<double><<<gp, 256, 0, st>>>(n, perm, static_cast<const double *>(x),
+                                                      static_cast<const double *>(y),
+                                                      static_cast<const double *>(z),
+                                                      static_cast<const double *>(q), xs);
+        P3_CUDA(cudaGetLastError());
+        c->launches++;
+    }
+    if (L >= 2) {
+        if (mixed)
+            P3_TRY(expansions3<float>(c, start));
+        else
+            P3_TRY(expansions3<double>(c, start));
+    } else {
+        for (int s = PETFMM3D_STAGE_P2M; s <= PETFMM3D_STAGE_L2L; ++s) mark3(c, s);
+    }
+    mark3(c, PETFMM3D_STAGE_NEAR);
+    const unsigned gl = grid_w(nleaf);
+    const double w = c->dom.width / double(int64_t(1) << L);
+    if (mixed) {
+        const float4 *rec = static_cast<const float4 *>(c->rec.p);
+        const float2 *le = static_cast<const float2 *>(c->le.p);
+        if (f32)
+            k3_near_mixed<float><<<gl, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, n, phi, ex, ey, ez);
+        else
+            k3_near_mixed<double><<<gl, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, n, phi, ex, ey, ez);
+    } else {
+        const Dbl4 *xs = static_cast<const Dbl4 *>(c->xs.p);
+        const double2 *le = static_cast<const double2 *>(c->le.p);
+        if (f32)
+            k3_near_f64<float><<<gl, W3 * 32, 0, st>>>(L, p, d, start, xs, le, perm, n, phi, ex, ey, ez);
+        else
+            k3_near_f64<double><<<gl, W3 * 32, 0, st>>>(L, p, d, start, xs, le, perm, n, phi, ex, ey, ez);
+    }
+    P3_CUDA(cudaGetLastError());
+    c->launches++;
+    mark3(c, PETFMM3D_STAGE_COUNT);
+    c->ev_recorded = c->timing;
+    return PETFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int petfmm3d_create(const petfmm_domain3d *dom, int levels, int order, int precision, int dtype,
+                    void *cuda_stream, petfmm3d_ctx **out) {
+    if (!out) return PETFMM_EINVAL;
+    *out = nullptr;
+    if (!dom || !(dom->width > 0.0) || !std::isfinite(dom->width) || !std::isfinite(dom->x0) ||
+        !std::isfinite(dom->y0) || !std::isfinite(dom->z0))
+        return PETFMM_EINVAL;
+    if (levels < 1 || levels > L3_MAX || order < 1 || order > P3_MAX) return PETFMM_EINVAL;
+    if (precision != PETFMM_FP64 && precision != PETFMM_MIXED) return PETFMM_EINVAL;
+    if (dtype != PETFMM_F64 && dtype != PETFMM_F32) return PETFMM_EINVAL;
+    petfmm3d_ctx *c = new (std::nothrow) petfmm3d_ctx;
+    if (!c) return PETFMM_ENOMEM;
+    c->dom = *dom;
+    c->L = levels;
+    c->p = order;
+    c->precision = precision;
+    c->dtype = dtype;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    int rc = upload_tables(c);
+    for (int i = 0; !rc && i <= PETFMM3D_STAGE_COUNT; ++i)
+        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) rc = PETFMM_ECUDA;
+    if (rc) {
+        cudaGetLastError();
+        petfmm3d_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return PETFMM_OK;
+}
+
+int petfmm3d_evaluate(petfmm3d_ctx *c, int64_t n, const void *x, const void *y, const void *z,
+                      const void *q, void *phi, void *ex, void *ey, void *ez) {
+    if (!c || n < 0 || n > int64_t(0xffffffffu) / 4) return PETFMM_EINVAL;
+    if (n > 0 && (!x || !y || !z || !q || !phi || !ex || !ey || !ez)) return PETFMM_EINVAL;
+    const int rc = evaluate3(c, n, x, y, z, q, phi, ex, ey, ez);
+    if (!rc) c->evaluations++;
+    return rc;
+}
+
+int petfmm3d_sync(petfmm3d_ctx *c) {
+    if (!c) return PETFMM_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PETFMM_ECUDA;
+    }
+    if (!c->status.p) return PETFMM_OK;
+    int s = 0;
+    if (cudaMemcpy(&s, c->status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return PETFMM_ECUDA;
+    }
+    return s;
+}
+
+int petfmm3d_set_option(petfmm3d_ctx *c, int option, int64_t value) {
+    if (!c) return PETFMM_EINVAL;
+    switch (option) {
+        case PETFMM3D_OPT_TIMING: c->timing = value != 0; return PETFMM_OK;
+        default: return PETFMM_EINVAL;
+    }
+}
+
+int petfmm3d_stage_times(petfmm3d_ctx *c, float *ms, int cap) {
+    if (!c || !ms || cap < 0) return PETFMM_EINVAL;
+    if (!c->ev_recorded) return PETFMM_ENOTREADY;
+    const int k = std::min(cap, int(PETFMM3D_STAGE_COUNT));
+    for (int s = 0; s < k; ++s) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->ev[s], c->ev[s + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return PETFMM_ECUDA;
+        }
+        ms[s] = t;
+    }
+    return k;
+}
+
+int petfmm3d_debug_tree(petfmm3d_ctx *c, int64_t n, uint32_t *skeys, uint32_t *perm,
+                        uint32_t *start) {
+    if (!c || n != c->last_n || n <= 0 || !skeys || !perm || !start) return PETFMM_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PETFMM_ECUDA;
+    const void *k = c->sorted_in_first ? c->keysA.p : c->keysB.p;
+    const void *v = c->sorted_in_first ? c->valsA.p : c->valsB.p;
+    const size_t nleaf = size_t(1) << (3 * c->L);
+    if (cudaMemcpy(skeys, k, size_t(n) * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(perm, v, size_t(n) * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(start, c->start.p, (nleaf + 1) * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return PETFMM_ECUDA;
+    }
+    return PETFMM_OK;
+}
+
+uint64_t petfmm3d_launches(const petfmm3d_ctx *c) { return c ? c->launches : 0; }
+
+int petfmm3d_destroy(petfmm3d_ctx *c) {
+    if (!c) return PETFMM_EINVAL;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    DevBuf3 *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->sortw, &c->start,
+                       &c->recu,  &c->rec,   &c->xs,    &c->me,    &c->le,    &c->status,
+                       &c->rtab32, &c->itab32, &c->rtab64, &c->itab64};
+    for (DevBuf3 *b : bufs)
+        if (b->p) cudaFree(b->p);
+    for (int i = 0; i <= PETFMM3D_STAGE_COUNT; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    cudaGetLastError();
+    delete c;
+    return PETFMM_OK;
+}
+
+}  // extern "C"

@@ -180,3 +180,63 @@ def sample_targets(n, count, seed=7):
     rng = np.random.default_rng(seed)
     count = min(count, n)
     return np.sort(rng.choice(n, count, replace=False)).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Three dimensions (the octree extension): point charges in the unit cube.
+# ---------------------------------------------------------------------------
+UNIT_CUBE = (0.0, 0.0, 0.0, 1.0)
+
+
+@dataclasses.dataclass
+class Workload3D:
+    name: str
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    q: np.ndarray
+    domain: tuple
+    L: int
+    p: int
+    dtype: str
+
+    @property
+    def n(self) -> int:
+        return int(self.x.size)
+
+    def as_f64(self):
+        return tuple(a.astype(np.float64) for a in (self.x, self.y, self.z, self.q))
+
+
+def uniform3d(n=1 << 21, seed=1, L=5, p=8, dtype="f32", name="uniform3d-2M"):
+    """x, y, z ~ U(0, 1), q ~ U(-1, 1) / n: 64 charges per leaf at L = 5."""
+    rng = np.random.default_rng(seed)
+    x, y, z = rng.uniform(0.0, 1.0, (3, n))
+    q = rng.uniform(-1.0, 1.0, n) / n
+    return Workload3D(name, *_store(dtype, x, y, z, q), UNIT_CUBE, L, p, dtype)
+
+
+def clustered3d(n=1 << 21, seed=1, L=6, p=8, dtype="f32", k=8, std=0.04, name="clustered3d-2M"):
+    """A mixture of k isotropic Gaussians (centres U(0.2, 0.8)^3, equal
+    weights), clipped to the cube; q ~ N(0, 1) / n."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.2, 0.8, (k, 3))
+    comp = rng.integers(0, k, n)
+    pts = np.clip(centres[comp] + std * rng.standard_normal((n, 3)), 0.0, 1.0)
+    q = rng.standard_normal(n) / n
+    return Workload3D(name, *_store(dtype, pts[:, 0], pts[:, 1], pts[:, 2], q), UNIT_CUBE, L, p,
+                      dtype)
+
+
+def tiny3d(n, seed, L=3, p=8, dtype="f64", clustered_frac=0.0):
+    """Small 3D inputs for the parity tests: uniform charges, a fraction of
+    them in one tight cluster (hot leaves next to empty ones)."""
+    rng = np.random.default_rng(seed)
+    x, y, z = rng.uniform(0.0, 1.0, (3, n))
+    k = int(n * clustered_frac)
+    if k:
+        c = rng.uniform(0.2, 0.8, 3)
+        pts = np.clip(c + 0.02 * rng.standard_normal((k, 3)), 0.0, 1.0)
+        x[:k], y[:k], z[:k] = pts.T
+    q = rng.uniform(-1.0, 1.0, n)
+    return Workload3D(f"tiny3d-{n}", *_store(dtype, x, y, z, q), UNIT_CUBE, L, p, dtype)

@@ -121,3 +121,21 @@ def test_checked_build_exists_and_reports_itself(lib):
     chk.petfmm_debug_checks.argtypes = [ctypes.c_void_p]
     assert chk.petfmm_debug_checks(lines) == 3
     assert chk.petfmm_debug_checks(None) == lib.PETFMM_EINVAL
+
+
+@pytest.mark.parametrize("args", [
+    ((0.0, 0.0, 0.0, 1.0), 0, 8),       # L < 1
+    ((0.0, 0.0, 0.0, 1.0), 9, 8),       # L > 8
+    ((0.0, 0.0, 0.0, 1.0), 3, 0),       # p < 1
+    ((0.0, 0.0, 0.0, 1.0), 3, 17),      # p > 16
+    ((0.0, 0.0, 0.0, 0.0), 3, 8),       # W <= 0
+    ((0.0, float("inf"), 0.0, 1.0), 3, 8),
+])
+def test_create3d_rejects_bad_arguments_before_touching_cuda(lib, args):
+    from paper_0905_2637_gb300 import fmm3d
+    with pytest.raises(lib.PetfmmError) as e:
+        fmm3d.petfmm3d_create(*args, lib.PETFMM_MIXED, lib.PETFMM_F32)
+    assert e.value.code == lib.PETFMM_EINVAL
+    for prec, dt in ((2, 0), (0, 2)):
+        with pytest.raises(lib.PetfmmError):
+            fmm3d.petfmm3d_create((0, 0, 0, 1), 3, 8, prec, dt)
