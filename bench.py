@@ -252,7 +252,17 @@ def cpu_baseline():
     oracle.direct(wl.x, wl.y, wl.gamma, wl.sigma, targets=tg)
     dt1 = time.perf_counter() - t1
     pairs = tg.size * (wl.n - 1)
+    # the 3D extension: the oracle's octree FMM on 2^15 charges of the
+    # uniform3d recipe at L = 3 (64 charges per leaf, as uniform3d-2M at L = 5)
+    w3 = W.uniform3d(n=1 << 15, L=3, dtype="f64", name="uniform3d-32k")
+    t2 = time.perf_counter()
+    oracle.fmm3d(*w3.as_f64(), w3.domain, w3.L, w3.p)
+    dt2 = time.perf_counter() - t2
     return {"value": w.n / dt, "unit": "particles/s", "cores": threads, "kind": "oracle",
+            "fmm3d": {"value": w3.n / dt2, "unit": "particles/s", "cores": threads,
+                      "sample": f"oracle 3D octree FMM (FP64, OpenMP {threads} threads) on "
+                                f"{w3.name}: N={w3.n}, L={w3.L}, p={w3.p}, 64 charges per leaf "
+                                f"like uniform3d-2M; {dt2:.1f} s wall"},
             "sample": f"oracle FMM (FP64, OpenMP {threads} threads) on {w.name}: N={w.n}, L={w.L}, "
                       f"p={w.p}, same recipe and blobs per leaf; {dt:.1f} s wall",
             "o1_direct": {"value": pairs / dt1, "unit": "pair interactions/s", "cores": threads,
@@ -417,6 +427,97 @@ def laplace_leg(_lib, torch, stream, steps=5):
             "data": "synthetic: x, y ~ U(0,1), q ~ U(-1,1), seed 1, fp32 storage"}
 
 
+def _il_pairs3(L):
+    """(target, source) pairs of the interaction lists of a full octree of
+    depth L: per level, |IL(t)| = |children of the parent's neighbours| -
+    |neighbours of t|, both products over the three axes, so their sums over
+    all boxes factor per axis."""
+    total = 0
+    for l in range(2, L + 1):
+        n, npar = 1 << l, 1 << (l - 1)
+        a = sum(2 * sum(1 for q in (i // 2 - 1, i // 2, i // 2 + 1) if 0 <= q < npar)
+                for i in range(n))
+        b = sum(sum(1 for j in (i - 1, i, i + 1) if 0 <= j < n) for i in range(n))
+        total += a ** 3 - b ** 3
+    return total
+
+
+def threed_leg(torch, stream, steps=5):
+    """The 3D extension (Laplace potential and field of point charges on an
+    octree, fmm3d.cu): 2^21 uniform charges in the unit cube, L = 5, p = 8;
+    the mixed path timed (CUDA events on the launching stream), the FP64
+    path timed and used as the accuracy reference.  Parity with the 3D
+    oracle is the tests' (tests/test_gpu_fmm3d.py)."""
+    from paper_0905_2637_gb300 import fmm3d
+    w = W.uniform3d()
+    with torch.cuda.stream(stream):
+        args = [torch.from_numpy(a).cuda() for a in (w.x, w.y, w.z, w.q)]
+    torch.cuda.synchronize()
+    res = {}
+    for prec in ("mixed", "fp64"):
+        ctx = fmm3d.Context3D(w.domain, w.L, w.p, precision=prec, dtype="f32", stream=stream)
+        ctx.set_option(fmm3d.PETFMM3D_OPT_TIMING, 1)
+        for _ in range(3 if prec == "mixed" else 1):
+            out = ctx.evaluate(*args)
+        ctx.sync()
+        l0 = ctx.launches()
+        ms, stages = [], []
+        for _ in range(steps if prec == "mixed" else 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = ctx.evaluate(*args)
+            e1.record(stream)
+            ctx.sync()
+            ms.append(e0.elapsed_time(e1))
+            stages.append(ctx.stage_times())
+        launches = (ctx.launches() - l0) // len(ms)
+        ctx.close()
+        t = statistics.median(ms)
+        res[prec] = dict(value=w.n / (t * 1e-3), ms_per_step=t, launches=launches,
+                         stages_ms={k: statistics.median(s_[k] for s_ in stages) for k in stages[0]},
+                         out=[o.double() for o in out])
+    mx, fp = res["mixed"], res["fp64"]
+    rel_phi = float(torch.sqrt(((mx["out"][0] - fp["out"][0]) ** 2).sum() / (fp["out"][0] ** 2).sum()))
+    num = sum(((a - b) ** 2).sum() for a, b in zip(mx["out"][1:], fp["out"][1:]))
+    rel_e = float(torch.sqrt(num / sum((b ** 2).sum() for b in fp["out"][1:])))
+    # algorithmic work: M2L as the real p^2 x p^2 map (2 p^4 flops per pair),
+    # near field 13 FP32 operations per ordered pair (3 differences, |d|^2 in
+    # 3, q/r, q/r^3 in 2, 4 accumulations; plus one rsqrt)
+    m2l_pairs = _il_pairs3(w.L)
+    m2l_flops = 2 * w.p ** 4 * m2l_pairs
+    side = 1 << w.L
+    ix, iy, iz = (np.minimum((a.astype(np.float64) * side).astype(np.int64), side - 1)
+                  for a in (w.x, w.y, w.z))
+    cnt = np.zeros((side + 2,) * 3, np.int64)
+    np.add.at(cnt, (ix + 1, iy + 1, iz + 1), 1)
+    nbr = sum(np.roll(np.roll(np.roll(cnt, dx, 0), dy, 1), dz, 2)
+              for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1))
+    near_pairs = int((cnt * nbr).sum() - w.n)
+    fp32_ops = SMS * FP32_LANES * 2070e6  # one FP32 operation per lane per clock
+    m2l_s = mx["stages_ms"]["m2l"] * 1e-3
+    near_s = mx["stages_ms"]["near"] * 1e-3
+    return {"kernel": "3D Laplace potential and field (octree, solid harmonics)",
+            "workload": w.name, "n": w.n, "levels": w.L, "order": w.p,
+            "value": mx["value"], "unit": "particles/s", "ms_per_step": mx["ms_per_step"],
+            "dtype": "f32 (mixed: FP32 expansions, SIMT GEMM M2L, FP32 near field)",
+            "rel_l2_vs_fp64": {"phi": rel_phi, "field": rel_e},
+            "fp64_gpu": {"value": fp["value"], "ms_per_step": fp["ms_per_step"],
+                         "stages_ms": fp["stages_ms"]},
+            "stages_ms": mx["stages_ms"], "gpu_launches": mx["launches"],
+            "m2l_pairs": m2l_pairs, "near_pairs": near_pairs,
+            "m2l_roofline": {"bound": "fp32", "achieved": m2l_flops / m2l_s, "peak": 2 * fp32_ops,
+                             "unit": "FLOP/s", "frac": m2l_flops / m2l_s / (2 * fp32_ops),
+                             "note": "2 p^4 flops per (target, source) pair, the real p^2 x p^2 "
+                                     "operator; 152 SMs x 128 lanes x 2 x 2070 MHz counts an "
+                                     "FMA as 2"},
+            "near_roofline": {"bound": "fp32", "achieved": 13 * near_pairs / near_s,
+                              "peak": fp32_ops, "unit": "ops/s",
+                              "frac": 13 * near_pairs / near_s / fp32_ops,
+                              "note": "13 FP32 operations per ordered pair against 152 x 128 x "
+                                      "2070 MHz; the stage includes L2P and the output"},
+            "data": "synthetic: x, y, z ~ U(0,1), q ~ U(-1,1)/N, seed 1, fp32 storage"}
+
+
 def batch_leg(_lib, torch, stream, steps=5, n_err=64):
     """512 independent instances (N log-uniform in [1e3, 2^18], uniform, sigma =
     0.5/sqrt(N), p in {8, 12, 17}) in one batched evaluation.  The autotuner
@@ -507,6 +608,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-laplace", action="store_true")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D extension leg")
     ap.add_argument("--workload", default="clustered-16M",
                     choices=["clustered-16M", "clustered-4M", "lattice-1M", "lamb-oseen-765k"],
                     help="clustered-4M (2^22 blobs, L = 9, same blobs per leaf) and lattice-1M "
@@ -724,6 +826,8 @@ def main():
             line["batch"] = batch_leg(_lib, torch, stream)
         if not args.no_laplace:
             line["laplace"] = laplace_leg(_lib, torch, stream)
+        if not args.no_3d:
+            line["threed"] = threed_leg(torch, stream)
         if not args.no_serve:
             line["serving"] = serving_leg(_lib)
         if not args.no_cpu_baseline:

@@ -396,6 +396,167 @@ __global__ void __launch_bounds__(W3 * 32) k3_m2l(int l, int L, int p, const uin
 }
 
 // ---------------------------------------------------------------------------
+// M2L of the mixed path as GEMMs.  The coefficients of a real potential with
+// degrees < p are p^2 real numbers: Re of every stored (n, m), then Im of
+// those with m > 0 (Im of m = 0 is zero).  In that basis each offset's
+// translation is a fixed real p^2 x p^2 matrix A_delta (built on the host in
+// FP64 from the M2L sum, rounded to FP32; stored transposed, k-major, padded
+// to NRP = p^2 rounded up to 32); rmap[r] = (coefficient, part) of real index
+// r, part 0 = Re, 1 = Im, 2 = Re of an m = 0 coefficient (its Im is zero).  A block takes 64 consecutive parent cells
+// (Morton order) of level l - 1 and one target child class c: 64 target rows.
+// For each (source class cs, parent offset d) of the interaction list of
+// class c (delta = c - cs - 2d, |delta|_inf >= 2), the 64 source rows (parent
+// P + d, class cs; zero when outside the domain or empty) are staged k-major
+// in shared memory and multiplied by A_delta in K chunks of 32: every thread
+// owns 4 rows x NRP / 8 columns, reading its 4 rows with one 16-byte load and
+// its columns with 16-byte loads (conflict-free: a warp spans 4 row groups x
+// 8 column groups).  Sums in a fixed order; the result is written, the L2L
+// that follows adds the parent's part.
+// ---------------------------------------------------------------------------
+constexpr int MG_ROWS = 64, MG_THREADS = 128, MG_XS = MG_ROWS + 4;
+
+__host__ __device__ constexpr int mg_nrp(int p) { return (p * p + 31) / 32 * 32; }
+// K chunk of A staged at once: all of it up to 64 rows, else 64 or 32 rows,
+// whichever divides NRP (so no chunk reads past its operator)
+__host__ __device__ constexpr int mg_kt(int p) {
+    return mg_nrp(p) <= 64 ? mg_nrp(p) : (mg_nrp(p) % 64 == 0 ? 64 : 32);
+}
+
+template <int P>
+__global__ void __launch_bounds__(MG_THREADS) k3_m2l_gemm(int l, int L, const uint32_t *__restrict__ start,
+                                                        const float *__restrict__ atab,
+                                                        const short2 *__restrict__ rmap,
+                                                        const float2 *__restrict__ me,
+                                                        float2 *__restrict__ le) {
+    constexpr int NC = P * (P + 1) / 2, NR = P * P, NRP = mg_nrp(P), CG = NRP / 8;
+    constexpr int KT = mg_kt(P);
+    static_assert(NRP % KT == 0 && KT % 4 == 0 && CG % 4 == 0, "chunking");
+    constexpr int NLOAD = (MG_ROWS * NC + MG_THREADS - 1) / MG_THREADS;
+    extern __shared__ __align__(16) float mg_smem[];
+    float *xs = mg_smem;                 // [NRP][MG_XS]: X^T, k-major
+    float *as = xs + NRP * MG_XS;        // [KT][NRP]: a K chunk of A^T
+    __shared__ int srow[MG_ROWS];
+    __shared__ short imr[NC];            // real index of Im of coefficient j (m > 0), else -1
+    const int tid = threadIdx.x, rg = tid >> 3, g = tid & 7;
+    const int c = int(blockIdx.x & 7);
+    const int64_t np = int64_t(1) << (3 * (l - 1));  // parent cells of level l - 1
+    const int64_t p0 = int64_t(blockIdx.x >> 3) * MG_ROWS;
+    const int pside = 1 << (l - 1);
+    for (int i = tid; i < (NRP - NR) * MG_XS; i += MG_THREADS) xs[NR * MG_XS + i] = 0.f;
+    for (int j = tid; j < NC; j += MG_THREADS) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= j) ++n;
+        // the m > 0 coefficients before j, in order: j - n - 1
+        imr[j] = short(j == n * (n + 1) / 2 ? -1 : NC + j - n - 1);
+    }
+    float acc[4][CG];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CG; ++j) acc[i][j] = 0.f;
+    const float2 *lev = me + lvl_off3(l) * NC;
+    for (int cs = 0; cs < 8; ++cs)
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    // delta = target - source, in box widths
+                    const int ex = (c & 1) - (cs & 1) - 2 * dx;
+                    const int ey = ((c >> 1) & 1) - ((cs >> 1) & 1) - 2 * dy;
+                    const int ez = (c >> 2) - (cs >> 2) - 2 * dz;
+                    if (ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1 && ez >= -1 && ez <= 1)
+                        continue;  // near field
+                    // source rows (the barrier also ends the previous offset's reads)
+                    bool have = false;
+                    if (tid < MG_ROWS) {
+                        int sb = -1;
+                        const int64_t pc = p0 + tid;
+                        if (pc < np) {
+                            const int qx = int(compact3(uint32_t(pc))) + dx,
+                                      qy = int(compact3(uint32_t(pc) >> 1)) + dy,
+                                      qz = int(compact3(uint32_t(pc) >> 2)) + dz;
+                            if (qx >= 0 && qy >= 0 && qz >= 0 && qx < pside && qy < pside &&
+                                qz < pside) {
+                                const uint32_t b = morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz)) *
+                                                       8u + uint32_t(cs);
+                                if (box_count3(start, L, l, b)) sb = int(b);
+                            }
+                        }
+                        srow[tid] = sb;
+                        have = sb >= 0;
+                    }
+                    if (!__syncthreads_or(have)) continue;
+                    {
+                        // every load of the rows in flight at once, then the
+                        // k-major scatter (Re to row j, Im to row imr[j])
+                        float2 v[NLOAD];
+#pragma unroll
+                        for (int u = 0; u < NLOAD; ++u) {
+                            const int i = tid + u * MG_THREADS;
+                            v[u] = make_float2(0.f, 0.f);
+                            if (i < MG_ROWS * NC) {
+                                const int sb = srow[i / NC];
+                                if (sb >= 0) v[u] = lev[int64_t(sb) * NC + i % NC];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < NLOAD; ++u) {
+                            const int i = tid + u * MG_THREADS;
+                            if (i < MG_ROWS * NC) {
+                                const int row = i / NC, j = i % NC;
+                                xs[j * MG_XS + row] = v[u].x;
+                                if (imr[j] >= 0) xs[imr[j] * MG_XS + row] = v[u].y;
+                            }
+                        }
+                    }
+                    const float *at = atab + size_t((ex + 3) + 7 * (ey + 3) + 49 * (ez + 3)) * NRP * NRP;
+                    for (int k0 = 0; k0 < NRP; k0 += KT) {
+                        __syncthreads();
+#pragma unroll
+                        for (int u = 0; u < (KT * NRP / 4 + MG_THREADS - 1) / MG_THREADS; ++u) {
+                            const int i = tid + u * MG_THREADS;
+                            if (i < KT * NRP / 4)
+                                reinterpret_cast<float4 *>(as)[i] =
+                                    __ldg(reinterpret_cast<const float4 *>(at + size_t(k0) * NRP) + i);
+                        }
+                        __syncthreads();
+#pragma unroll 4
+                        for (int kk = 0; kk < KT; ++kk) {
+                            const float4 x4 = *reinterpret_cast<const float4 *>(
+                                xs + (k0 + kk) * MG_XS + 4 * rg);
+                            const float *ar = as + kk * NRP + g * CG;
+#pragma unroll
+                            for (int j4 = 0; j4 < CG; j4 += 4) {
+                                const float4 a4 = *reinterpret_cast<const float4 *>(ar + j4);
+                                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                                for (int t = 0; t < 4; ++t) {
+                                    acc[0][j4 + t] = fmaf(x4.x, av[t], acc[0][j4 + t]);
+                                    acc[1][j4 + t] = fmaf(x4.y, av[t], acc[1][j4 + t]);
+                                    acc[2][j4 + t] = fmaf(x4.z, av[t], acc[2][j4 + t]);
+                                    acc[3][j4 + t] = fmaf(x4.w, av[t], acc[3][j4 + t]);
+                                }
+                            }
+                        }
+                    }
+                }
+    float *lef = reinterpret_cast<float *>(le + lvl_off3(l) * NC);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t pc = p0 + 4 * rg + i;
+        if (pc >= np) continue;
+        const int64_t box = pc * 8 + c;
+#pragma unroll
+        for (int j = 0; j < CG; ++j) {
+            const int r = g * CG + j;
+            if (r >= NR) continue;
+            const short2 mp = rmap[r];
+            lef[(box * NC + mp.x) * 2 + (mp.y == 1)] = acc[i][j];
+            if (mp.y == 2) lef[(box * NC + mp.x) * 2 + 1] = 0.f;  // Im of m = 0
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // L2L (child level l >= 3): L~'_j^s += 2^-(j+1) sum_{k,l} L~_{j+k}^{s+l}(parent)
 // conj(R_k^l(e_c)).  A warp per child box.
 // ---------------------------------------------------------------------------
@@ -700,7 +861,7 @@ struct petfmm3d_ctx {
     int L = 0, p = 0, precision = 0, dtype = 0;
     cudaStream_t stream = nullptr;
     DevBuf3 keysA, keysB, valsA, valsB, sortw, start, recu, rec, xs, me, le, status;
-    DevBuf3 rtab32, itab32, rtab64, itab64;
+    DevBuf3 rtab32, itab32, rtab64, itab64, atab32, rmap;
     bool timing = false, ev_recorded = false;
     cudaEvent_t ev[PETFMM3D_STAGE_COUNT + 1] = {};
     uint64_t launches = 0, evaluations = 0;
@@ -727,6 +888,59 @@ int upload_tables(petfmm3d_ctx *c) {
                 host_rec_i(dx, dy, dz, 2 * p - 1,
                            it.data() + size_t((dx + 3) + 7 * (dy + 3) + 49 * (dz + 3)) * nci);
             }
+    // the mixed path's M2L matrices: real index r < nc is Re of coefficient
+    // r, r >= nc Im of the coefficients with m > 0 in order
+    const int nr = p * p, nrp = mg_nrp(p);
+    std::vector<short2> rm(static_cast<size_t>(nr));
+    std::vector<int> imidx(size_t(nc), -1);
+    for (int n = 0, r = nc; n < p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            const int j = n * (n + 1) / 2 + m;
+            rm[size_t(j)] = make_short2(short(j), short(m == 0 ? 2 : 0));
+            if (m > 0) {
+                imidx[size_t(j)] = r;
+                rm[size_t(r++)] = make_short2(short(j), 1);
+            }
+        }
+    std::vector<float> at(size_t(NSLOT3) * nrp * nrp, 0.f);
+    auto ival = [&](const cd *iv, int j, int sg) {  // I_j^sg from the stored s >= 0
+        if (sg >= 0) return iv[j * (j + 1) / 2 + sg];
+        const cd v = std::conj(iv[j * (j + 1) / 2 - sg]);
+        return (sg & 1) ? -v : v;
+    };
+    for (int slot = 0; slot < NSLOT3; ++slot) {
+        const cd *iv = it.data() + size_t(slot) * nci;
+        const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+        if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) < 2) continue;
+        float *a = at.data() + size_t(slot) * nrp * nrp;  // a[k_in * nrp + r_out]
+        for (int k = 0; k < p; ++k)
+            for (int lo = 0; lo <= k; ++lo) {
+                const int jo = k * (k + 1) / 2 + lo;
+                for (int n = 0; n < p; ++n)
+                    for (int m = 0; m <= n; ++m) {
+                        const int ji = n * (n + 1) / 2 + m;
+                        const double sk = (k & 1) ? -1.0 : 1.0;
+                        const cd al = sk * ival(iv, n + k, m + lo);
+                        const cd be = m > 0 ? sk * ((m & 1) ? -1.0 : 1.0) * ival(iv, n + k, lo - m)
+                                            : cd(0.0, 0.0);
+                        // input a (real part): L += (al + be) a; input b (imaginary
+                        // part): L += i (al - be) b
+                        const cd vr = al + be, vi = cd(0.0, 1.0) * (al - be);
+                        a[size_t(ji) * nrp + jo] = float(vr.real());
+                        if (lo > 0) a[size_t(ji) * nrp + imidx[size_t(jo)]] = float(vr.imag());
+                        if (m > 0) {
+                            a[size_t(imidx[size_t(ji)]) * nrp + jo] = float(vi.real());
+                            if (lo > 0)
+                                a[size_t(imidx[size_t(ji)]) * nrp + imidx[size_t(jo)]] =
+                                    float(vi.imag());
+                        }
+                    }
+            }
+    }
+    P3_TRY(ensure3(c->atab32, at.size() * sizeof(float), c->stream));
+    P3_TRY(ensure3(c->rmap, rm.size() * sizeof(short2), c->stream));
+    P3_CUDA(cudaMemcpy(c->atab32.p, at.data(), at.size() * sizeof(float), cudaMemcpyHostToDevice));
+    P3_CUDA(cudaMemcpy(c->rmap.p, rm.data(), rm.size() * sizeof(short2), cudaMemcpyHostToDevice));
     std::vector<double2> r64(rt.size()), i64(it.size());
     std::vector<float2> r32(rt.size()), i32(it.size());
     for (size_t i = 0; i < rt.size(); ++i) {
@@ -753,6 +967,35 @@ void mark3(petfmm3d_ctx *c, int s) {
 }
 
 unsigned grid_w(int64_t warps) { return unsigned((warps + W3 - 1) / W3); }
+
+template <int P>
+cudaError_t m2l_gemm_p(int l, int L, const uint32_t *start, const float *atab, const short2 *rmap,
+                       const float2 *me, float2 *le, cudaStream_t st) {
+    const size_t smem = size_t(mg_nrp(P) * MG_XS + mg_kt(P) * mg_nrp(P)) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k3_m2l_gemm<P>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t np = int64_t(1) << (3 * (l - 1));
+    const unsigned grid = unsigned((np + MG_ROWS - 1) / MG_ROWS * 8);
+    k3_m2l_gemm<P><<<grid, MG_THREADS, smem, st>>>(l, L, start, atab, rmap, me, le);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_gemm(int p, int l, int L, const uint32_t *start, const float *atab,
+                            const short2 *rmap, const float2 *me, float2 *le, cudaStream_t st) {
+    switch (p) {
+#define MG_CASE(P) case P: return m2l_gemm_p<P>(l, L, start, atab, rmap, me, le, st);
+        MG_CASE(1) MG_CASE(2) MG_CASE(3) MG_CASE(4) MG_CASE(5) MG_CASE(6) MG_CASE(7) MG_CASE(8)
+        MG_CASE(9) MG_CASE(10) MG_CASE(11) MG_CASE(12) MG_CASE(13) MG_CASE(14) MG_CASE(15)
+        MG_CASE(16)
+#undef MG_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 template <typename T>
 int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
@@ -781,7 +1024,13 @@ int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
     }
     mark3(c, PETFMM3D_STAGE_M2L);
     for (int l = 2; l <= L; ++l) {
-        k3_m2l<T><<<grid_w(int64_t(1) << (3 * l)), W3 * 32, 0, st>>>(l, L, p, start, itab, me, le);
+        if constexpr (sizeof(T) == 4) {
+            P3_CUDA(launch_m2l_gemm(p, l, L, start, static_cast<const float *>(c->atab32.p),
+                                    static_cast<const short2 *>(c->rmap.p), me, le, st));
+        } else {
+            k3_m2l<T><<<grid_w(int64_t(1) << (3 * l)), W3 * 32, 0, st>>>(l, L, p, start, itab,
+                                                                          me, le);
+        }
         P3_CUDA(cudaGetLastError());
         c->launches++;
     }
@@ -1005,7 +1254,7 @@ int petfmm3d_destroy(petfmm3d_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     DevBuf3 *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->sortw, &c->start,
                        &c->recu,  &c->rec,   &c->xs,    &c->me,    &c->le,    &c->status,
-                       &c->rtab32, &c->itab32, &c->rtab64, &c->itab64};
+                       &c->rtab32, &c->itab32, &c->rtab64, &c->itab64, &c->atab32, &c->rmap};
     for (DevBuf3 *b : bufs)
         if (b->p) cudaFree(b->p);
     for (int i = 0; i <= PETFMM3D_STAGE_COUNT; ++i)

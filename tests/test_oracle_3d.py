@@ -254,3 +254,16 @@ def test_fmm_converges_geometrically_to_the_direct_sum():
     got = O.fmm3d(x, y, z, q, (0, 0, 0, 1), 3, 12)
     for e in got[1:]:
         assert abs(np.sum(q * e)) < 1e-5 * np.sum(np.abs(q * e))
+
+
+def test_bench_interaction_pair_count_is_the_enumeration():
+    """The 3D bench leg's algorithmic M2L pair count (a closed form that
+    factors per axis) against the oracle's interaction lists."""
+    import bench
+    for L in (2, 3):
+        tot = 0
+        for l in range(2, L + 1):
+            n = 1 << l
+            for ix, iy, iz in itertools.product(range(n), repeat=3):
+                tot += len(O.interaction_list3d(l, ix, iy, iz))
+        assert bench._il_pairs3(L) == tot
