@@ -556,6 +556,223 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_gemm(int l, int L, const ui
     }
 }
 
+// The same GEMMs with the operands of the next offset in flight: for p <= 8
+// (a whole operator is one K chunk) the operator and the source rows of
+// offset i + 1 are copied with cp.async (16-byte chunks; 8 when a box's
+// coefficients are an odd number of float2; rows of empty or outside boxes
+// zero-filled without a read) into the second operator buffer and a raw row
+// buffer while offset i multiplies; then the raw rows are split into the
+// k-major real layout.  Offsets whose 64 source rows are all empty skip
+// their multiply.
+__device__ __forceinline__ void cp_async_z(void *dst, const void *src, int bytes, bool pred) {
+    const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+    const int n = pred ? bytes : 0;
+    if (bytes == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+template <int P>
+constexpr size_t mgp_smem_bytes() {
+    return size_t(mg_nrp(P) * MG_XS + 2 * mg_nrp(P) * mg_nrp(P)) * sizeof(float) +
+           size_t(MG_ROWS) * (P * (P + 1) / 2) * sizeof(float2);
+}
+
+// blocks of level l in an all-levels M2L launch: ceil(8^(l-1) / 64) x 8
+__host__ __device__ __forceinline__ int64_t mg_blocks(int l) {
+    return ((int64_t(1) << (3 * (l - 1))) + MG_ROWS - 1) / MG_ROWS * 8;
+}
+
+template <int P>
+__global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t *__restrict__ start,
+                                                        const float *__restrict__ atab,
+                                                        const float2 *__restrict__ me,
+                                                        float2 *__restrict__ le) {
+    // this block's level: levels 2..L one after another in the grid
+    int l = 2;
+    int64_t bid = blockIdx.x;
+    while (l < L && bid >= mg_blocks(l)) bid -= mg_blocks(l++);
+    constexpr int NC = P * (P + 1) / 2, NR = P * P, NRP = mg_nrp(P), CG = NRP / 8;
+    static_assert(NRP <= 64, "one K chunk per operator");
+    constexpr int CB = (NC % 2 == 0) ? 16 : 8;          // copy chunk bytes of a row
+    constexpr int RCH = NC * 8 / CB;                     // chunks per row
+    extern __shared__ __align__(16) float mg_smem[];
+    float *xs = mg_smem;                                 // [NRP][MG_XS]
+    float *as0 = xs + NRP * MG_XS;                       // 2 x [NRP][NRP]
+    float2 *raw = reinterpret_cast<float2 *>(as0 + 2 * NRP * NRP);  // [64][NC]
+    __shared__ int srow[2][MG_ROWS];
+    __shared__ short imr[NC];
+    __shared__ unsigned char offs[216];                  // the class's offsets (cs, d)
+    __shared__ int noff;
+    // occupied boxes of the 6 x 6 x 6 parent cells around the block's 4 x 4 x
+    // 4 (64 Morton-consecutive parents), 8 classes each: one bit per class
+    __shared__ unsigned char hocc[216];
+    const int tid = threadIdx.x, rg = tid >> 3, g = tid & 7;
+    const int c = int(bid & 7);
+    const int64_t np = int64_t(1) << (3 * (l - 1));
+    const int64_t p0 = (bid >> 3) * MG_ROWS;
+    const int pside = 1 << (l - 1);
+    const int hx0 = int(compact3(uint32_t(p0))) - 1, hy0 = int(compact3(uint32_t(p0) >> 1)) - 1,
+              hz0 = int(compact3(uint32_t(p0) >> 2)) - 1;
+    for (int h = tid; h < 216; h += MG_THREADS) {
+        const int qx = hx0 + h % 6, qy = hy0 + (h / 6) % 6, qz = hz0 + h / 36;
+        unsigned bits = 0;
+        if (qx >= 0 && qy >= 0 && qz >= 0 && qx < pside && qy < pside && qz < pside) {
+            const uint32_t pb = morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz));
+            for (int cs = 0; cs < 8; ++cs)
+                if (box_count3(start, L, l, pb * 8u + uint32_t(cs))) bits |= 1u << cs;
+        }
+        hocc[h] = (unsigned char)bits;
+    }
+    for (int i = tid; i < (NRP - NR) * MG_XS; i += MG_THREADS) xs[NR * MG_XS + i] = 0.f;
+    for (int j = tid; j < NC; j += MG_THREADS) {
+        int n = 0;
+        while ((n + 1) * (n + 2) / 2 <= j) ++n;
+        imr[j] = short(j == n * (n + 1) / 2 ? -1 : NC + j - n - 1);
+    }
+    if (tid == 0) {
+        int k = 0;
+        for (int o = 0; o < 216; ++o) {
+            const int cs = o / 27, d = o % 27;
+            const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+            const int ex = (c & 1) - (cs & 1) - 2 * dx, ey = ((c >> 1) & 1) - ((cs >> 1) & 1) - 2 * dy,
+                      ez = (c >> 2) - (cs >> 2) - 2 * dz;
+            if (ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1 && ez >= -1 && ez <= 1) continue;
+            offs[k++] = (unsigned char)o;
+        }
+        noff = k;
+    }
+    __syncthreads();
+    const float2 *lev = me + lvl_off3(l) * NC;
+    // source box of target row `row` for offset entry o (-1: none), from the
+    // halo occupancy (no global load)
+    auto source = [&](int o, int row) {
+        const int cs = o / 27, d = o % 27;
+        const int64_t pc = p0 + row;
+        if (pc >= np) return -1;
+        const int qx = int(compact3(uint32_t(pc))) + d % 3 - 1,
+                  qy = int(compact3(uint32_t(pc) >> 1)) + (d / 3) % 3 - 1,
+                  qz = int(compact3(uint32_t(pc) >> 2)) + d / 9 - 1;
+        if (qx < 0 || qy < 0 || qz < 0 || qx >= pside || qy >= pside || qz >= pside) return -1;
+        if (!((hocc[(qx - hx0) + 6 * (qy - hy0) + 36 * (qz - hz0)] >> cs) & 1u)) return -1;
+        return int(morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz)) * 8u + uint32_t(cs));
+    };
+    auto slot_of = [&](int o) {
+        const int cs = o / 27, d = o % 27;
+        const int ex = (c & 1) - (cs & 1) - 2 * (d % 3 - 1),
+                  ey = ((c >> 1) & 1) - ((cs >> 1) & 1) - 2 * ((d / 3) % 3 - 1),
+                  ez = (c >> 2) - (cs >> 2) - 2 * (d / 9 - 1);
+        return (ex + 3) + 7 * (ey + 3) + 49 * (ez + 3);
+    };
+    auto issue = [&](int i) {  // copies of offset i (srow[i & 1] ready)
+        const int o = offs[i];
+        const float *at = atab + size_t(slot_of(o)) * NRP * NRP;
+        float *asb = as0 + (i & 1) * NRP * NRP;
+        for (int q = tid; q < NRP * NRP / 4; q += MG_THREADS)
+            cp_async_z(asb + 4 * q, at + 4 * q, 16, true);
+        for (int q = tid; q < MG_ROWS * RCH; q += MG_THREADS) {
+            const int row = q / RCH, ch = q - row * RCH;
+            const int sb = srow[i & 1][row];
+            const char *src = reinterpret_cast<const char *>(sb >= 0 ? lev + int64_t(sb) * NC : lev);
+            cp_async_z(reinterpret_cast<char *>(raw + row * NC) + ch * CB, src + ch * CB, CB, sb >= 0);
+        }
+        cp_async_commit();
+    };
+    float acc[4][CG];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CG; ++j) acc[i][j] = 0.f;
+    const int nof = noff;
+    bool have = false;
+    if (tid < MG_ROWS) {
+        srow[0][tid] = source(offs[0], tid);
+        have = srow[0][tid] >= 0;
+    }
+    bool cur_any = __syncthreads_or(have);
+    issue(0);
+    for (int i = 0; i < nof; ++i) {
+        cp_async_wait_all();
+        __syncthreads();
+        // split the raw rows of offset i into the k-major real layout, and
+        // find the source rows of offset i + 1
+        for (int q = tid; q < MG_ROWS * NC; q += MG_THREADS) {
+            const int row = q % MG_ROWS, j = q / MG_ROWS;
+            const float2 v = raw[row * NC + j];
+            xs[j * MG_XS + row] = v.x;
+            if (imr[j] >= 0) xs[imr[j] * MG_XS + row] = v.y;
+        }
+        have = false;
+        if (tid < MG_ROWS && i + 1 < nof) {
+            srow[(i + 1) & 1][tid] = source(offs[i + 1], tid);
+            have = srow[(i + 1) & 1][tid] >= 0;
+        }
+        const bool next_any = __syncthreads_or(have);
+        if (i + 1 < nof) issue(i + 1);
+        if (cur_any) {
+            const float *asb = as0 + (i & 1) * NRP * NRP;
+#pragma unroll 4
+            for (int k = 0; k < NRP; ++k) {
+                const float4 x4 = *reinterpret_cast<const float4 *>(xs + k * MG_XS + 4 * rg);
+                const float *ar = asb + k * NRP + g * CG;
+#pragma unroll
+                for (int j4 = 0; j4 < CG; j4 += 4) {
+                    const float4 a4 = *reinterpret_cast<const float4 *>(ar + j4);
+                    const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        acc[0][j4 + t] = fmaf(x4.x, av[t], acc[0][j4 + t]);
+                        acc[1][j4 + t] = fmaf(x4.y, av[t], acc[1][j4 + t]);
+                        acc[2][j4 + t] = fmaf(x4.z, av[t], acc[2][j4 + t]);
+                        acc[3][j4 + t] = fmaf(x4.w, av[t], acc[3][j4 + t]);
+                    }
+                }
+            }
+        }
+        cur_any = next_any;
+    }
+    cp_async_wait_all();
+    float *lef = reinterpret_cast<float *>(le + lvl_off3(l) * NC);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t pc = p0 + 4 * rg + i;
+        if (pc >= np) continue;
+        const int64_t box = pc * 8 + c;
+#pragma unroll
+        for (int j = 0; j < CG; ++j) {
+            const int r = g * CG + j;
+            if (r >= NR) continue;
+            // real index r: Re of coefficient r (r < NC), else Im of the
+            // (r - NC)-th coefficient with m > 0
+            if (r < NC) {
+                lef[(box * NC + r) * 2] = acc[i][j];
+                int n = 0;
+                while ((n + 1) * (n + 2) / 2 <= r) ++n;
+                if (r == n * (n + 1) / 2) lef[(box * NC + r) * 2 + 1] = 0.f;
+            }
+        }
+    }
+    // Im parts: thread columns r >= NC map back through imr (search)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t pc = p0 + 4 * rg + i;
+        if (pc >= np) continue;
+        const int64_t box = pc * 8 + c;
+#pragma unroll
+        for (int j = 0; j < CG; ++j) {
+            const int r = g * CG + j;
+            if (r < NC || r >= NR) continue;
+            for (int jj = 0; jj < NC; ++jj)
+                if (imr[jj] == r) lef[(box * NC + jj) * 2 + 1] = acc[i][j];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // L2L (child level l >= 3): L~'_j^s += 2^-(j+1) sum_{k,l} L~_{j+k}^{s+l}(parent)
 // conj(R_k^l(e_c)).  A warp per child box.
@@ -971,6 +1188,22 @@ unsigned grid_w(int64_t warps) { return unsigned((warps + W3 - 1) / W3); }
 template <int P>
 cudaError_t m2l_gemm_p(int l, int L, const uint32_t *start, const float *atab, const short2 *rmap,
                        const float2 *me, float2 *le, cudaStream_t st) {
+    if constexpr (mg_nrp(P) <= 64) {
+        constexpr size_t smem = mgp_smem_bytes<P>();
+        static bool pattr = false;
+        if (!pattr) {
+            cudaError_t e = cudaFuncSetAttribute(k3_m2l_pipe<P>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(smem));
+            if (e != cudaSuccess) return e;
+            pattr = true;
+        }
+        if (l != L) return cudaSuccess;  // one launch covers levels 2..L
+        int64_t grid = 0;
+        for (int k = 2; k <= L; ++k) grid += mg_blocks(k);
+        k3_m2l_pipe<P><<<unsigned(grid), MG_THREADS, smem, st>>>(L, start, atab, me, le);
+        return cudaGetLastError();
+    }
     const size_t smem = size_t(mg_nrp(P) * MG_XS + mg_kt(P) * mg_nrp(P)) * sizeof(float);
     static bool attr = false;
     if (!attr) {
@@ -1023,7 +1256,10 @@ int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
         c->launches++;
     }
     mark3(c, PETFMM3D_STAGE_M2L);
-    for (int l = 2; l <= L; ++l) {
+    // mixed path with p <= 8: one launch for all levels (launch_m2l_gemm
+    // launches at l = L)
+    const bool one = sizeof(T) == 4 && mg_nrp(p) <= 64;
+    for (int l = one ? L : 2; l <= L; ++l) {
         if constexpr (sizeof(T) == 4) {
             P3_CUDA(launch_m2l_gemm(p, l, L, start, static_cast<const float *>(c->atab32.p),
                                     static_cast<const short2 *>(c->rmap.p), me, le, st));
