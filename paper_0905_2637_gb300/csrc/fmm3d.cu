@@ -414,6 +414,9 @@ __global__ void __launch_bounds__(W3 * 32) k3_m2l(int l, int L, int p, const uin
 // that follows adds the parent's part.
 // ---------------------------------------------------------------------------
 constexpr int MG_ROWS = 64, MG_THREADS = 128, MG_XS = MG_ROWS + 4;
+#ifndef MG_PIPE_ROWS
+#define MG_PIPE_ROWS 128  // target rows per block of the pipelined M2L (64 or 128)
+#endif
 
 __host__ __device__ constexpr int mg_nrp(int p) { return (p * p + 31) / 32 * 32; }
 // K chunk of A staged at once: all of it up to 64 rows, else 64 or 32 rows,
@@ -577,18 +580,21 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <int P>
+template <int P, int R>
 constexpr size_t mgp_smem_bytes() {
-    return size_t(mg_nrp(P) * MG_XS + 2 * mg_nrp(P) * mg_nrp(P)) * sizeof(float) +
-           size_t(MG_ROWS) * (P * (P + 1) / 2) * sizeof(float2);
+    return size_t(mg_nrp(P) * (R + 4) + 2 * mg_nrp(P) * mg_nrp(P)) * sizeof(float) +
+           size_t(R) * (P * (P + 1) / 2) * sizeof(float2);
 }
 
-// blocks of level l in an all-levels M2L launch: ceil(8^(l-1) / 64) x 8
-__host__ __device__ __forceinline__ int64_t mg_blocks(int l) {
-    return ((int64_t(1) << (3 * (l - 1))) + MG_ROWS - 1) / MG_ROWS * 8;
+// blocks of level l in an all-levels M2L launch of R-row blocks:
+// ceil(8^(l-1) / R) x 8
+__host__ __device__ __forceinline__ int64_t mg_blocks(int l, int R) {
+    return ((int64_t(1) << (3 * (l - 1))) + R - 1) / R * 8;
 }
 
-template <int P>
+// R target rows per block (R Morton-consecutive parent cells: 4 x 4 x 4 for
+// 64, 8 x 4 x 4 for 128), R / 16 rows per thread.
+template <int P, int R>
 __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t *__restrict__ start,
                                                         const float *__restrict__ atab,
                                                         const float2 *__restrict__ me,
@@ -596,31 +602,36 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
     // this block's level: levels 2..L one after another in the grid
     int l = 2;
     int64_t bid = blockIdx.x;
-    while (l < L && bid >= mg_blocks(l)) bid -= mg_blocks(l++);
+    while (l < L && bid >= mg_blocks(l, R)) bid -= mg_blocks(l++, R);
     constexpr int NC = P * (P + 1) / 2, NR = P * P, NRP = mg_nrp(P), CG = NRP / 8;
     static_assert(NRP <= 64, "one K chunk per operator");
+    constexpr int XS = R + 4, RT = R / 16;
+    constexpr int BITS = R == 128 ? 7 : 6;              // Morton bits of the block's parents
+    constexpr int NX = 1 << ((BITS + 2) / 3), NY = 1 << ((BITS + 1) / 3), NZ = 1 << (BITS / 3);
+    constexpr int HX = NX + 2, HY = NY + 2, HZ = NZ + 2;
+    static_assert(R == 64 || R == 128, "rows per block");
     constexpr int CB = (NC % 2 == 0) ? 16 : 8;          // copy chunk bytes of a row
     constexpr int RCH = NC * 8 / CB;                     // chunks per row
     extern __shared__ __align__(16) float mg_smem[];
-    float *xs = mg_smem;                                 // [NRP][MG_XS]
-    float *as0 = xs + NRP * MG_XS;                       // 2 x [NRP][NRP]
-    float2 *raw = reinterpret_cast<float2 *>(as0 + 2 * NRP * NRP);  // [64][NC]
-    __shared__ int srow[2][MG_ROWS];
+    float *xs = mg_smem;                                 // [NRP][XS]
+    float *as0 = xs + NRP * XS;                          // 2 x [NRP][NRP]
+    float2 *raw = reinterpret_cast<float2 *>(as0 + 2 * NRP * NRP);  // [R][NC]
+    __shared__ int srow[2][R];
     __shared__ short imr[NC];
     __shared__ unsigned char offs[216];                  // the class's offsets (cs, d)
     __shared__ int noff;
-    // occupied boxes of the 6 x 6 x 6 parent cells around the block's 4 x 4 x
-    // 4 (64 Morton-consecutive parents), 8 classes each: one bit per class
-    __shared__ unsigned char hocc[216];
+    // occupied boxes of the parent cells around the block's (one cell of
+    // halo), 8 classes each: one bit per class
+    __shared__ unsigned char hocc[HX * HY * HZ];
     const int tid = threadIdx.x, rg = tid >> 3, g = tid & 7;
     const int c = int(bid & 7);
     const int64_t np = int64_t(1) << (3 * (l - 1));
-    const int64_t p0 = (bid >> 3) * MG_ROWS;
+    const int64_t p0 = (bid >> 3) * R;
     const int pside = 1 << (l - 1);
     const int hx0 = int(compact3(uint32_t(p0))) - 1, hy0 = int(compact3(uint32_t(p0) >> 1)) - 1,
               hz0 = int(compact3(uint32_t(p0) >> 2)) - 1;
-    for (int h = tid; h < 216; h += MG_THREADS) {
-        const int qx = hx0 + h % 6, qy = hy0 + (h / 6) % 6, qz = hz0 + h / 36;
+    for (int h = tid; h < HX * HY * HZ; h += MG_THREADS) {
+        const int qx = hx0 + h % HX, qy = hy0 + (h / HX) % HY, qz = hz0 + h / (HX * HY);
         unsigned bits = 0;
         if (qx >= 0 && qy >= 0 && qz >= 0 && qx < pside && qy < pside && qz < pside) {
             const uint32_t pb = morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz));
@@ -629,7 +640,7 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
         }
         hocc[h] = (unsigned char)bits;
     }
-    for (int i = tid; i < (NRP - NR) * MG_XS; i += MG_THREADS) xs[NR * MG_XS + i] = 0.f;
+    for (int i = tid; i < (NRP - NR) * XS; i += MG_THREADS) xs[NR * XS + i] = 0.f;
     for (int j = tid; j < NC; j += MG_THREADS) {
         int n = 0;
         while ((n + 1) * (n + 2) / 2 <= j) ++n;
@@ -659,7 +670,7 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
                   qy = int(compact3(uint32_t(pc) >> 1)) + (d / 3) % 3 - 1,
                   qz = int(compact3(uint32_t(pc) >> 2)) + d / 9 - 1;
         if (qx < 0 || qy < 0 || qz < 0 || qx >= pside || qy >= pside || qz >= pside) return -1;
-        if (!((hocc[(qx - hx0) + 6 * (qy - hy0) + 36 * (qz - hz0)] >> cs) & 1u)) return -1;
+        if (!((hocc[(qx - hx0) + HX * ((qy - hy0) + HY * (qz - hz0))] >> cs) & 1u)) return -1;
         return int(morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz)) * 8u + uint32_t(cs));
     };
     auto slot_of = [&](int o) {
@@ -675,7 +686,7 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
         float *asb = as0 + (i & 1) * NRP * NRP;
         for (int q = tid; q < NRP * NRP / 4; q += MG_THREADS)
             cp_async_z(asb + 4 * q, at + 4 * q, 16, true);
-        for (int q = tid; q < MG_ROWS * RCH; q += MG_THREADS) {
+        for (int q = tid; q < R * RCH; q += MG_THREADS) {
             const int row = q / RCH, ch = q - row * RCH;
             const int sb = srow[i & 1][row];
             const char *src = reinterpret_cast<const char *>(sb >= 0 ? lev + int64_t(sb) * NC : lev);
@@ -683,14 +694,14 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
         }
         cp_async_commit();
     };
-    float acc[4][CG];
+    float acc[RT][CG];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int j = 0; j < CG; ++j) acc[i][j] = 0.f;
     const int nof = noff;
     bool have = false;
-    if (tid < MG_ROWS) {
+    if (tid < R) {
         srow[0][tid] = source(offs[0], tid);
         have = srow[0][tid] >= 0;
     }
@@ -701,14 +712,14 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
         __syncthreads();
         // split the raw rows of offset i into the k-major real layout, and
         // find the source rows of offset i + 1
-        for (int q = tid; q < MG_ROWS * NC; q += MG_THREADS) {
-            const int row = q % MG_ROWS, j = q / MG_ROWS;
+        for (int q = tid; q < R * NC; q += MG_THREADS) {
+            const int row = q % R, j = q / R;
             const float2 v = raw[row * NC + j];
-            xs[j * MG_XS + row] = v.x;
-            if (imr[j] >= 0) xs[imr[j] * MG_XS + row] = v.y;
+            xs[j * XS + row] = v.x;
+            if (imr[j] >= 0) xs[imr[j] * XS + row] = v.y;
         }
         have = false;
-        if (tid < MG_ROWS && i + 1 < nof) {
+        if (tid < R && i + 1 < nof) {
             srow[(i + 1) & 1][tid] = source(offs[i + 1], tid);
             have = srow[(i + 1) & 1][tid] >= 0;
         }
@@ -718,19 +729,25 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
             const float *asb = as0 + (i & 1) * NRP * NRP;
 #pragma unroll 4
             for (int k = 0; k < NRP; ++k) {
-                const float4 x4 = *reinterpret_cast<const float4 *>(xs + k * MG_XS + 4 * rg);
+                float xv[RT];
+#pragma unroll
+                for (int i4 = 0; i4 < RT; i4 += 4) {
+                    const float4 x4 = *reinterpret_cast<const float4 *>(xs + k * XS + RT * rg + i4);
+                    xv[i4] = x4.x;
+                    xv[i4 + 1] = x4.y;
+                    xv[i4 + 2] = x4.z;
+                    xv[i4 + 3] = x4.w;
+                }
                 const float *ar = asb + k * NRP + g * CG;
 #pragma unroll
                 for (int j4 = 0; j4 < CG; j4 += 4) {
                     const float4 a4 = *reinterpret_cast<const float4 *>(ar + j4);
                     const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        acc[0][j4 + t] = fmaf(x4.x, av[t], acc[0][j4 + t]);
-                        acc[1][j4 + t] = fmaf(x4.y, av[t], acc[1][j4 + t]);
-                        acc[2][j4 + t] = fmaf(x4.z, av[t], acc[2][j4 + t]);
-                        acc[3][j4 + t] = fmaf(x4.w, av[t], acc[3][j4 + t]);
-                    }
+                    for (int t = 0; t < 4; ++t)
+#pragma unroll
+                        for (int i = 0; i < RT; ++i)
+                            acc[i][j4 + t] = fmaf(xv[i], av[t], acc[i][j4 + t]);
                 }
             }
         }
@@ -739,8 +756,8 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
     cp_async_wait_all();
     float *lef = reinterpret_cast<float *>(le + lvl_off3(l) * NC);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t pc = p0 + 4 * rg + i;
+    for (int i = 0; i < RT; ++i) {
+        const int64_t pc = p0 + RT * rg + i;
         if (pc >= np) continue;
         const int64_t box = pc * 8 + c;
 #pragma unroll
@@ -759,8 +776,8 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
     }
     // Im parts: thread columns r >= NC map back through imr (search)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t pc = p0 + 4 * rg + i;
+    for (int i = 0; i < RT; ++i) {
+        const int64_t pc = p0 + RT * rg + i;
         if (pc >= np) continue;
         const int64_t box = pc * 8 + c;
 #pragma unroll
@@ -1189,10 +1206,11 @@ template <int P>
 cudaError_t m2l_gemm_p(int l, int L, const uint32_t *start, const float *atab, const short2 *rmap,
                        const float2 *me, float2 *le, cudaStream_t st) {
     if constexpr (mg_nrp(P) <= 64) {
-        constexpr size_t smem = mgp_smem_bytes<P>();
+        constexpr int R = MG_PIPE_ROWS;
+        constexpr size_t smem = mgp_smem_bytes<P, R>();
         static bool pattr = false;
         if (!pattr) {
-            cudaError_t e = cudaFuncSetAttribute(k3_m2l_pipe<P>,
+            cudaError_t e = cudaFuncSetAttribute(k3_m2l_pipe<P, R>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  int(smem));
             if (e != cudaSuccess) return e;
@@ -1200,8 +1218,8 @@ cudaError_t m2l_gemm_p(int l, int L, const uint32_t *start, const float *atab, c
         }
         if (l != L) return cudaSuccess;  // one launch covers levels 2..L
         int64_t grid = 0;
-        for (int k = 2; k <= L; ++k) grid += mg_blocks(k);
-        k3_m2l_pipe<P><<<unsigned(grid), MG_THREADS, smem, st>>>(L, start, atab, me, le);
+        for (int k = 2; k <= L; ++k) grid += mg_blocks(k, R);
+        k3_m2l_pipe<P, R><<<unsigned(grid), MG_THREADS, smem, st>>>(L, start, atab, me, le);
         return cudaGetLastError();
     }
     const size_t smem = size_t(mg_nrp(P) * MG_XS + mg_kt(P) * mg_nrp(P)) * sizeof(float);
