@@ -56,6 +56,9 @@ constexpr int NC3_MAX = P3_MAX * (P3_MAX + 1) / 2;  // stored coefficients
 constexpr int OUT3 = (NC3_MAX + 31) / 32;          // per lane, one warp per box
 constexpr int NSLOT3 = 343;                        // offsets in [-3, 3]^3
 constexpr int W3 = 8;                              // warps per block
+// targets per lane of the mixed near-field kernel (2 measured no faster at
+// 64 charges per leaf, and slower with the sources fetched four at a time)
+constexpr int NEAR_TPL = 1;
 
 template <typename T> struct C3;
 template <> struct C3<float> { using V = float2; };
@@ -885,20 +888,20 @@ __device__ __forceinline__ void store3(void *o, int64_t i, double v) {
 }
 
 // ---------------------------------------------------------------------------
-// Near field + L2P, mixed path: a warp per leaf, a lane per target (32 at a
-// time); sources of the leaf and its neighbours in a fixed order (dz, dy, dx,
-// then sorted rank), read once per warp (all lanes the same address) in FP32
-// leaf units: d = xi_t - (xi_s + offset), 1/|d| from rsqrt, self and
-// coincident pairs (|d| = 0) skipped.  Output in the caller's order.
-// ---------------------------------------------------------------------------
-template <typename TOut>
-__global__ void __launch_bounds__(W3 * 32) k3_near_mixed(int L, int p, double w,
-                                                         const uint32_t *__restrict__ start,
-                                                         const float4 *__restrict__ rec,
-                                                         const float2 *__restrict__ le,
-                                                         const uint32_t *__restrict__ perm,
-                                                         int64_t n, void *phi, void *ex, void *ey,
-                                                         void *ez) {
+// Near field + L2P, mixed path: a warp per leaf, TPL targets per lane (32 TPL
+// at a time); sources of the leaf and its neighbours in a fixed order (dz,
+// dy, dx, then sorted rank), read once per warp (all lanes the same address)
+// in FP32 leaf units: d = xi_t - (xi_s + offset), 1/|d| from
+// rsqrt, self and coincident pairs (|d| = 0) skipped.  Output in the
+// caller's order.
+template <typename TOut, int TPL>
+__global__ void __launch_bounds__(W3 * 32, 4 / TPL) k3_near_mixed(int L, int p, double w,
+                                                                const uint32_t *__restrict__ start,
+                                                                const float4 *__restrict__ rec,
+                                                                const float2 *__restrict__ le,
+                                                                const uint32_t *__restrict__ perm,
+                                                                int64_t n, void *phi, void *ex,
+                                                                void *ey, void *ez) {
     __shared__ float2 sle[W3][NC3_MAX];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t b = int64_t(blockIdx.x) * W3 + wid;
@@ -914,11 +917,15 @@ __global__ void __launch_bounds__(W3 * 32) k3_near_mixed(int L, int p, double w,
               iz = int(compact3(uint32_t(b) >> 2));
     const int side = 1 << L;
     const float inv_w = float(1.0 / w), inv_w2 = float(1.0 / (w * w));
-    for (uint32_t t0 = s0; t0 < s1; t0 += 32) {
-        const uint32_t i = t0 + uint32_t(lane);
-        const bool valid = i < s1;
-        const float4 tg = valid ? rec[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    for (uint32_t t0 = s0; t0 < s1; t0 += 32 * TPL) {
+        float4 tg[TPL];
+        float f[TPL], gx[TPL], gy[TPL], gz[TPL];
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            const uint32_t i = t0 + uint32_t(lane + 32 * u);
+            tg[u] = i < s1 ? rec[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            f[u] = gx[u] = gy[u] = gz[u] = 0.f;
+        }
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
@@ -927,29 +934,44 @@ __global__ void __launch_bounds__(W3 * 32) k3_near_mixed(int L, int p, double w,
                         continue;
                     const uint32_t nb = morton3(uint32_t(nx), uint32_t(ny), uint32_t(nz));
                     const uint32_t a = start[nb], e = start[nb + 1];
-                    const float ox = tg.x - float(dx), oy = tg.y - float(dy), oz = tg.z - float(dz);
-                    for (uint32_t j = a; j < e; ++j) {
-                        const float4 s = rec[j];
-                        const float ddx = ox - s.x, ddy = oy - s.y, ddz = oz - s.z;
-                        const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                        const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                        const float qr = s.w * ri;
-                        const float qr3 = qr * ri * ri;
-                        f += qr;
-                        gx = fmaf(qr3, ddx, gx);
-                        gy = fmaf(qr3, ddy, gy);
-                        gz = fmaf(qr3, ddz, gz);
+                    float ox[TPL], oy[TPL], oz[TPL];
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) {
+                        ox[u] = tg[u].x - float(dx);
+                        oy[u] = tg[u].y - float(dy);
+                        oz[u] = tg[u].z - float(dz);
                     }
+                    auto pair = [&](const float4 sr) {
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) {
+                            const float ddx = ox[u] - sr.x, ddy = oy[u] - sr.y, ddz = oz[u] - sr.z;
+                            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                            const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                            const float qr = sr.w * ri;
+                            const float qr3 = qr * ri * ri;
+                            f[u] += qr;
+                            gx[u] = fmaf(qr3, ddx, gx[u]);
+                            gy[u] = fmaf(qr3, ddy, gy[u]);
+                            gz[u] = fmaf(qr3, ddz, gz[u]);
+                        }
+                    };
+                    for (uint32_t j = a; j < e; ++j) pair(rec[j]);
                 }
-        float ff = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-        if (far) l2p3<float, float2>(sle[wid], p, tg.x, tg.y, tg.z, ff, fx, fy, fz);
-        if (valid) {
-            const int64_t o = perm[i];
-            if (!PF_IN(o, n)) continue;
-            store3<TOut>(phi, o, double((f + ff) * inv_w));
-            store3<TOut>(ex, o, double((gx - fx) * inv_w2));
-            store3<TOut>(ey, o, double((gy - fy) * inv_w2));
-            store3<TOut>(ez, o, double((gz - fz) * inv_w2));
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            if (t0 + 32 * u >= s1) break;  // warp-uniform
+            const uint32_t i = t0 + uint32_t(lane + 32 * u);
+            float ff = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+            if (far) l2p3<float, float2>(sle[wid], p, tg[u].x, tg[u].y, tg[u].z, ff, fx, fy, fz);
+            if (i < s1) {
+                const int64_t o = perm[i];
+                if (PF_IN(o, n)) {
+                    store3<TOut>(phi, o, double((f[u] + ff) * inv_w));
+                    store3<TOut>(ex, o, double((gx[u] - fx) * inv_w2));
+                    store3<TOut>(ey, o, double((gy[u] - fy) * inv_w2));
+                    store3<TOut>(ez, o, double((gz[u] - fz) * inv_w2));
+                }
+            }
         }
     }
 }
@@ -1386,9 +1408,9 @@ int evaluate3(petfmm3d_ctx *c, int64_t n, const void *x, const void *y, const vo
         const float4 *rec = static_cast<const float4 *>(c->rec.p);
         const float2 *le = static_cast<const float2 *>(c->le.p);
         if (f32)
-            k3_near_mixed<float><<<gl, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, n, phi, ex, ey, ez);
+            k3_near_mixed<float, NEAR_TPL><<<gl, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, n, phi, ex, ey, ez);
         else
-            k3_near_mixed<double><<<gl, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, n, phi, ex, ey, ez);
+            k3_near_mixed<double, NEAR_TPL><<<gl, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, n, phi, ex, ey, ez);
     } else {
         const Dbl4 *xs = static_cast<const Dbl4 *>(c->xs.p);
         const double2 *le = static_cast<const double2 *>(c->le.p);
