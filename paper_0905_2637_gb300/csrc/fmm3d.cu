@@ -212,9 +212,10 @@ __device__ __forceinline__ Part3<double> leaf_part(const Dbl4 *xs, int64_t j, do
 }
 
 // ---------------------------------------------------------------------------
-// P2M (leaves): M~_n^m = sum_j q_j conj(R_n^m(xi_j)).  A warp per leaf; lane
-// m < p owns column m: R_m^m = (xi + i eta)^m / (2^m m!), then the recurrence
-// in n, for every particle of the leaf in order.
+// P2M (leaves): M~_n^m = sum_j q_j conj(R_n^m(xi_j)).  A warp per leaf split
+// into 32 / p lane groups; lane m of a group owns column m: R_m^m = (xi + i
+// eta)^m / (2^m m!), then the recurrence in n, for every G-th particle of the
+// leaf; the groups' sums are added in group order.
 // ---------------------------------------------------------------------------
 template <typename T, typename P>
 __global__ void __launch_bounds__(W3 * 32) k3_p2m(int L, int p, Dom3 d, const uint32_t *__restrict__ start,
@@ -226,7 +227,9 @@ __global__ void __launch_bounds__(W3 * 32) k3_p2m(int L, int p, Dom3 d, const ui
     if (b >= (int64_t(1) << (3 * L))) return;
     const uint32_t s0 = start[b], s1 = start[b + 1];
     if (s0 == s1) return;
-    const int m = lane;
+    // G = 32 / p lane groups, group g summing particles g, g + G, ...; lane
+    // m of a group owns column m
+    const int G = 32 / p, g = lane / p, m = lane - g * p;
     const double w = d.width / double(1u << L);
     const double cx = d.x0 + (double(compact3(uint32_t(b))) + 0.5) * w;
     const double cy = d.y0 + (double(compact3(uint32_t(b) >> 1)) + 0.5) * w;
@@ -234,8 +237,8 @@ __global__ void __launch_bounds__(W3 * 32) k3_p2m(int L, int p, Dom3 d, const ui
     V acc[P3_MAX];
 #pragma unroll
     for (int n = 0; n < P3_MAX; ++n) acc[n] = mk<V>(T(0), T(0));
-    if (m < p) {
-        for (uint32_t j = s0; j < s1; ++j) {
+    if (g < G) {
+        for (uint32_t j = s0 + uint32_t(g); j < s1; j += uint32_t(G)) {
             const Part3<T> a = leaf_part(part, j, cx, cy, cz, 1.0 / w);
             const T r2 = a.x * a.x + a.y * a.y + a.z * a.z;
             V rmm = mk<V>(a.q, T(0));  // q R_0^0, then q R_m^m
@@ -259,6 +262,22 @@ __global__ void __launch_bounds__(W3 * 32) k3_p2m(int L, int p, Dom3 d, const ui
                 acc[n].y += rn.y;
             }
         }
+    }
+    // the groups' partial sums added into group 0 in group order (every lane
+    // takes part in the shuffles)
+#pragma unroll
+    for (int n = 0; n < P3_MAX; ++n) {
+        for (int gg = 1; gg < G; ++gg) {
+            const int src = m + gg * p;
+            const T ox = __shfl_sync(0xffffffffu, acc[n].x, src);
+            const T oy = __shfl_sync(0xffffffffu, acc[n].y, src);
+            if (g == 0) {
+                acc[n].x += ox;
+                acc[n].y += oy;
+            }
+        }
+    }
+    if (g == 0) {
         V *dst = me + (lvl_off3(L) + b) * nc3(p);
 #pragma unroll
         for (int n = 0; n < P3_MAX; ++n)
