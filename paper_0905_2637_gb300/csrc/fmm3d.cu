@@ -662,6 +662,20 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
         }
         hocc[h] = (unsigned char)bits;
     }
+    __syncthreads();
+    // a block whose target boxes (class c of its own parent cells) are all
+    // empty writes nothing: an empty box's local expansion is never read
+    {
+        bool mine = false;
+        for (int r = tid; r < R; r += MG_THREADS) {
+            const int64_t pc = p0 + r;
+            if (pc >= np) continue;
+            const int qx = int(compact3(uint32_t(pc))), qy = int(compact3(uint32_t(pc) >> 1)),
+                      qz = int(compact3(uint32_t(pc) >> 2));
+            mine |= (hocc[(qx - hx0) + HX * ((qy - hy0) + HY * (qz - hz0))] >> c) & 1u;
+        }
+        if (!__syncthreads_or(mine)) return;
+    }
     for (int i = tid; i < (NRP - NR) * XS; i += MG_THREADS) xs[NR * XS + i] = 0.f;
     for (int j = tid; j < NC; j += MG_THREADS) {
         int n = 0;
@@ -907,8 +921,30 @@ __device__ __forceinline__ void store3(void *o, int64_t i, double v) {
 }
 
 // ---------------------------------------------------------------------------
-// Near field + L2P, mixed path: a warp per leaf, TPL targets per lane (32 TPL
-// at a time); sources of the leaf and its neighbours in a fixed order (dz,
+// The near field's work items: leaf b with n_b particles gives ceil(n_b / 32)
+// items (b, first sorted rank of the chunk), in leaf order (a hot leaf's
+// chunks go to consecutive warps, so they spread over the SMs).
+__global__ void __launch_bounds__(256) k3_near_count(const uint32_t *__restrict__ start,
+                                                     int64_t nleaf, uint32_t *__restrict__ cnt) {
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    cnt[b] = (start[b + 1] - start[b] + 31u) / 32u;
+}
+__global__ void __launch_bounds__(256) k3_near_emit(const uint32_t *__restrict__ start,
+                                                    int64_t nleaf, const uint32_t *__restrict__ off,
+                                                    const uint32_t *__restrict__ nitems,
+                                                    int64_t cap, uint2 *__restrict__ items) {
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    const uint32_t s0 = start[b], k = (start[b + 1] - s0 + 31u) / 32u;
+    for (uint32_t c = 0; c < k; ++c) {
+        const int64_t o = int64_t(off[b]) + c;
+        if (o < cap && o < int64_t(*nitems)) items[o] = make_uint2(uint32_t(b), s0 + 32u * c);
+    }
+}
+
+// Near field + L2P, mixed path: a warp per work item (32 TPL targets of one
+// leaf), TPL targets per lane; sources of the leaf and its neighbours in a fixed order (dz,
 // dy, dx, then sorted rank), read once per warp (all lanes the same address)
 // in FP32 leaf units: d = xi_t - (xi_s + offset), 1/|d| from
 // rsqrt, self and coincident pairs (|d| = 0) skipped.  Output in the
@@ -919,14 +955,20 @@ __global__ void __launch_bounds__(W3 * 32, 4 / TPL) k3_near_mixed(int L, int p, 
                                                                 const float4 *__restrict__ rec,
                                                                 const float2 *__restrict__ le,
                                                                 const uint32_t *__restrict__ perm,
+                                                                const uint2 *__restrict__ items,
+                                                                const uint32_t *__restrict__ nitems,
                                                                 int64_t n, void *phi, void *ex,
                                                                 void *ey, void *ez) {
     __shared__ float2 sle[W3][NC3_MAX];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t b = int64_t(blockIdx.x) * W3 + wid;
-    if (b >= (int64_t(1) << (3 * L))) return;
-    const uint32_t s0 = start[b], s1 = start[b + 1];
-    if (s0 == s1) return;
+    const int64_t it = int64_t(blockIdx.x) * W3 + wid;
+    if (it >= int64_t(*nitems)) return;
+    // one item: up to 32 TPL targets of leaf b starting at sorted rank s0
+    const uint2 item = items[it];
+    const int64_t b = item.x;
+    if (!PF_IN(b, int64_t(1) << (3 * L))) return;
+    const uint32_t s0 = item.y;
+    const uint32_t s1 = min(start[b + 1], s0 + uint32_t(32 * TPL));
     const int nc = nc3(p);
     const bool far = L >= 2;
     if (far)
@@ -936,7 +978,8 @@ __global__ void __launch_bounds__(W3 * 32, 4 / TPL) k3_near_mixed(int L, int p, 
               iz = int(compact3(uint32_t(b) >> 2));
     const int side = 1 << L;
     const float inv_w = float(1.0 / w), inv_w2 = float(1.0 / (w * w));
-    for (uint32_t t0 = s0; t0 < s1; t0 += 32 * TPL) {
+    {
+        const uint32_t t0 = s0;
         float4 tg[TPL];
         float f[TPL], gx[TPL], gy[TPL], gz[TPL];
 #pragma unroll
@@ -1136,6 +1179,7 @@ struct petfmm3d_ctx {
     int L = 0, p = 0, precision = 0, dtype = 0;
     cudaStream_t stream = nullptr;
     DevBuf3 keysA, keysB, valsA, valsB, sortw, start, recu, rec, xs, me, le, status;
+    DevBuf3 ncnt, noff, nscan, nitems;  // the mixed near field's work items
     DevBuf3 rtab32, itab32, rtab64, itab64, atab32, rmap;
     bool timing = false, ev_recorded = false;
     cudaEvent_t ev[PETFMM3D_STAGE_COUNT + 1] = {};
@@ -1424,12 +1468,32 @@ int evaluate3(petfmm3d_ctx *c, int64_t n, const void *x, const void *y, const vo
     const unsigned gl = grid_w(nleaf);
     const double w = c->dom.width / double(int64_t(1) << L);
     if (mixed) {
+        // work items: ceil(n_b / 32) per leaf, at most min(8^L, n) + n / 32
+        const int64_t cap = std::min<int64_t>(nleaf, n) + n / 32 + 1;
+        P3_TRY(ensure3(c->ncnt, size_t(nleaf) * 4, st));
+        P3_TRY(ensure3(c->noff, size_t(nleaf) * 4 + 16, st));
+        P3_TRY(ensure3(c->nscan, size_t(scan_scratch_words(nleaf)) * 4, st));
+        P3_TRY(ensure3(c->nitems, size_t(cap) * sizeof(uint2), st));
+        uint32_t *cnt = static_cast<uint32_t *>(c->ncnt.p), *off = static_cast<uint32_t *>(c->noff.p);
+        uint32_t *nit = off + nleaf;  // the item count, after the offsets
+        uint2 *items = static_cast<uint2 *>(c->nitems.p);
+        const unsigned gb = unsigned((nleaf + 255) / 256);
+        k3_near_count<<<gb, 256, 0, st>>>(start, nleaf, cnt);
+        P3_CUDA(cudaGetLastError());
+        P3_CUDA(exclusive_scan(cnt, off, nleaf, static_cast<uint32_t *>(c->nscan.p), nit, st,
+                               &c->launches));
+        k3_near_emit<<<gb, 256, 0, st>>>(start, nleaf, off, nit, cap, items);
+        P3_CUDA(cudaGetLastError());
+        c->launches += 2;
         const float4 *rec = static_cast<const float4 *>(c->rec.p);
         const float2 *le = static_cast<const float2 *>(c->le.p);
+        const unsigned gi = grid_w(cap);
         if (f32)
-            k3_near_mixed<float, NEAR_TPL><<<gl, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, n, phi, ex, ey, ez);
+            k3_near_mixed<float, NEAR_TPL><<<gi, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm,
+                                                                   items, nit, n, phi, ex, ey, ez);
         else
-            k3_near_mixed<double, NEAR_TPL><<<gl, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, n, phi, ex, ey, ez);
+            k3_near_mixed<double, NEAR_TPL><<<gi, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm,
+                                                                    items, nit, n, phi, ex, ey, ez);
     } else {
         const Dbl4 *xs = static_cast<const Dbl4 *>(c->xs.p);
         const double2 *le = static_cast<const double2 *>(c->le.p);
@@ -1547,7 +1611,8 @@ uint64_t petfmm3d_launches(const petfmm3d_ctx *c) { return c ? c->launches : 0; 
 int petfmm3d_destroy(petfmm3d_ctx *c) {
     if (!c) return PETFMM_EINVAL;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DevBuf3 *bufs[] = {&c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->sortw, &c->start,
+    DevBuf3 *bufs[] = {&c->ncnt, &c->noff, &c->nscan, &c->nitems,
+                       &c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->sortw, &c->start,
                        &c->recu,  &c->rec,   &c->xs,    &c->me,    &c->le,    &c->status,
                        &c->rtab32, &c->itab32, &c->rtab64, &c->itab64, &c->atab32, &c->rmap};
     for (DevBuf3 *b : bufs)
