@@ -689,6 +689,14 @@ int petfmm3d_debug_tree(petfmm3d_ctx *ctx, int64_t n, uint32_t *skeys, uint32_t 
                         uint32_t *start);
 /* kernels this context has launched */
 uint64_t petfmm3d_launches(const petfmm3d_ctx *ctx);
+/* Host only (no device work): the mixed path's M2L operator for the offset
+ * (dx, dy, dz) between same-level boxes (target minus source, in box widths;
+ * |each| <= 3, max >= 2) and order p, in the real basis of a real
+ * potential's coefficients (real index r < p (p + 1) / 2: Re of coefficient
+ * n (n + 1) / 2 + m; then Im of the coefficients with m > 0, in order), for
+ * expansions scaled by the box width.  out[k * p^2 + r] = d(output r) /
+ * d(input k), FP64 (the library rounds it to FP32); cap >= p^4 doubles. */
+int petfmm3d_debug_m2l_operator(int order, int dx, int dy, int dz, double *out, int64_t cap);
 int petfmm3d_destroy(petfmm3d_ctx *ctx);
 
 #ifdef __cplusplus

@@ -1149,6 +1149,48 @@ void host_rec_i(double x, double y, double z, int P, cd *out) {
     }
 }
 
+// The mixed path's M2L operator for one offset delta in the real basis of a
+// real potential's degree-< p coefficients (real index r < p (p + 1) / 2: Re
+// of coefficient r = n (n + 1) / 2 + m; r >= p (p + 1) / 2: Im of the
+// coefficients with m > 0, in order), from the M2L sum written per stored
+// (n, m >= 0) input: L~_k^l gets alpha M~_n^m + beta conj(M~_n^m) with
+// alpha = (-1)^k I_{n+k}^{m+l}(delta) and, for m > 0, beta =
+// (-1)^(k+m) I_{n+k}^{l-m}(delta) (the -m term).  iv: I_j^s(delta), j < 2p - 1,
+// s >= 0; a[k_in * p^2 + r_out] = d(output r_out) / d(input k_in), FP64.
+void host_m2l_real(int p, const cd *iv, double *a) {
+    const int nc = p * (p + 1) / 2, nr = p * p;
+    std::vector<int> imidx(size_t(nc), -1);
+    for (int n = 0, r = nc; n < p; ++n)
+        for (int m = 1; m <= n; ++m) imidx[size_t(n * (n + 1) / 2 + m)] = r++;
+    auto ival = [&](int j, int sg) {  // I_j^sg from the stored s >= 0
+        if (sg >= 0) return iv[j * (j + 1) / 2 + sg];
+        const cd v = std::conj(iv[j * (j + 1) / 2 - sg]);
+        return (sg & 1) ? -v : v;
+    };
+    std::fill(a, a + size_t(nr) * nr, 0.0);
+    for (int k = 0; k < p; ++k)
+        for (int lo = 0; lo <= k; ++lo) {
+            const int jo = k * (k + 1) / 2 + lo;
+            for (int n = 0; n < p; ++n)
+                for (int m = 0; m <= n; ++m) {
+                    const int ji = n * (n + 1) / 2 + m;
+                    const double sk = (k & 1) ? -1.0 : 1.0;
+                    const cd al = sk * ival(n + k, m + lo);
+                    const cd be =
+                        m > 0 ? sk * ((m & 1) ? -1.0 : 1.0) * ival(n + k, lo - m) : cd(0.0, 0.0);
+                    // input a (real part): L += (al + be) a; input b (imaginary
+                    // part): L += i (al - be) b
+                    const cd vr = al + be, vi = cd(0.0, 1.0) * (al - be);
+                    a[size_t(ji) * nr + jo] = vr.real();
+                    if (lo > 0) a[size_t(ji) * nr + imidx[size_t(jo)]] = vr.imag();
+                    if (m > 0) {
+                        a[size_t(imidx[size_t(ji)]) * nr + jo] = vi.real();
+                        if (lo > 0) a[size_t(imidx[size_t(ji)]) * nr + imidx[size_t(jo)]] = vi.imag();
+                    }
+                }
+        }
+}
+
 struct DevBuf3 {
     void *p = nullptr;
     size_t cap = 0;
@@ -1222,39 +1264,14 @@ int upload_tables(petfmm3d_ctx *c) {
             }
         }
     std::vector<float> at(size_t(NSLOT3) * nrp * nrp, 0.f);
-    auto ival = [&](const cd *iv, int j, int sg) {  // I_j^sg from the stored s >= 0
-        if (sg >= 0) return iv[j * (j + 1) / 2 + sg];
-        const cd v = std::conj(iv[j * (j + 1) / 2 - sg]);
-        return (sg & 1) ? -v : v;
-    };
+    std::vector<double> a64(size_t(nr) * nr);
     for (int slot = 0; slot < NSLOT3; ++slot) {
-        const cd *iv = it.data() + size_t(slot) * nci;
         const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
         if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) < 2) continue;
-        float *a = at.data() + size_t(slot) * nrp * nrp;  // a[k_in * nrp + r_out]
-        for (int k = 0; k < p; ++k)
-            for (int lo = 0; lo <= k; ++lo) {
-                const int jo = k * (k + 1) / 2 + lo;
-                for (int n = 0; n < p; ++n)
-                    for (int m = 0; m <= n; ++m) {
-                        const int ji = n * (n + 1) / 2 + m;
-                        const double sk = (k & 1) ? -1.0 : 1.0;
-                        const cd al = sk * ival(iv, n + k, m + lo);
-                        const cd be = m > 0 ? sk * ((m & 1) ? -1.0 : 1.0) * ival(iv, n + k, lo - m)
-                                            : cd(0.0, 0.0);
-                        // input a (real part): L += (al + be) a; input b (imaginary
-                        // part): L += i (al - be) b
-                        const cd vr = al + be, vi = cd(0.0, 1.0) * (al - be);
-                        a[size_t(ji) * nrp + jo] = float(vr.real());
-                        if (lo > 0) a[size_t(ji) * nrp + imidx[size_t(jo)]] = float(vr.imag());
-                        if (m > 0) {
-                            a[size_t(imidx[size_t(ji)]) * nrp + jo] = float(vi.real());
-                            if (lo > 0)
-                                a[size_t(imidx[size_t(ji)]) * nrp + imidx[size_t(jo)]] =
-                                    float(vi.imag());
-                        }
-                    }
-            }
+        host_m2l_real(p, it.data() + size_t(slot) * nci, a64.data());
+        float *ap = at.data() + size_t(slot) * nrp * nrp;  // ap[k_in * nrp + r_out]
+        for (int k = 0; k < nr; ++k)
+            for (int r = 0; r < nr; ++r) ap[size_t(k) * nrp + r] = float(a64[size_t(k) * nr + r]);
     }
     P3_TRY(ensure3(c->atab32, at.size() * sizeof(float), c->stream));
     P3_TRY(ensure3(c->rmap, rm.size() * sizeof(short2), c->stream));
@@ -1607,6 +1624,19 @@ int petfmm3d_debug_tree(petfmm3d_ctx *c, int64_t n, uint32_t *skeys, uint32_t *p
 }
 
 uint64_t petfmm3d_launches(const petfmm3d_ctx *c) { return c ? c->launches : 0; }
+
+int petfmm3d_debug_m2l_operator(int order, int dx, int dy, int dz, double *out, int64_t cap) {
+    if (order < 1 || order > P3_MAX || !out) return PETFMM_EINVAL;
+    if (std::abs(dx) > 3 || std::abs(dy) > 3 || std::abs(dz) > 3 ||
+        std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) < 2)
+        return PETFMM_EINVAL;
+    const int64_t nr = int64_t(order) * order;
+    if (cap < nr * nr) return PETFMM_EINVAL;
+    std::vector<cd> iv(size_t(nci3(order)));
+    host_rec_i(dx, dy, dz, 2 * order - 1, iv.data());
+    host_m2l_real(order, iv.data(), out);
+    return PETFMM_OK;
+}
 
 int petfmm3d_destroy(petfmm3d_ctx *c) {
     if (!c) return PETFMM_EINVAL;

@@ -38,6 +38,7 @@ def lib3():
                 ("petfmm3d_stage_times", I, [P, P, I]),
                 ("petfmm3d_debug_tree", I, [P, I64, P, P, P]),
                 ("petfmm3d_launches", ctypes.c_uint64, [P]),
+                ("petfmm3d_debug_m2l_operator", I, [I, I, I, I, P, I64]),
                 ("petfmm3d_destroy", I, [P])):
             fn = getattr(lib, name)
             fn.restype = res
@@ -52,6 +53,16 @@ def petfmm3d_create(domain, levels, order, precision, dtype, cuda_stream=None):
     _lib._ck(lib3().petfmm3d_create(ctypes.byref(dom), int(levels), int(order), int(precision),
                                     int(dtype), cuda_stream, ctypes.byref(h)), "petfmm3d_create")
     return h
+
+
+def m2l_operator(order, dx, dy, dz):
+    """The mixed path's real M2L operator for offset (dx, dy, dz), as the
+    library builds it on the host (FP64): a[k, r] = d(output r) / d(input k)."""
+    nr = order * order
+    out = np.zeros(nr * nr, np.float64)
+    _lib._ck(lib3().petfmm3d_debug_m2l_operator(order, dx, dy, dz, out.ctypes.data, out.size),
+             "petfmm3d_debug_m2l_operator")
+    return out.reshape(nr, nr)
 
 
 class Context3D:
