@@ -126,8 +126,14 @@ template <typename V> __device__ __forceinline__ void cmac_conj(V &acc, V a, V b
 // ---------------------------------------------------------------------------
 // Binning (Sec. 2.1 in 3D): t = x - x0; s = t 2^L / W; floor, clamped; FP64
 // with round-to-nearest intrinsics (no contraction).  recu (mixed path): the
-// record (xi, eta, zeta, q) in input order.
+// record (xi, eta, zeta, q) in input order, each coordinate rounded to FP32
+// and held below 0.5 - 2^-24.  The cap moves a point by at most one FP32
+// rounding and keeps two particles of adjacent leaves apart by at least
+// 2^-24 leaf widths along the axis they differ in, so |d| = 0 in the near
+// field can only come from the target's own leaf.
 // ---------------------------------------------------------------------------
+constexpr float REC_MAX = 0.5f - 0x1p-24f;
+
 struct Dom3 {
     double x0, y0, z0, width, scale;  // scale = 2^L / width
 };
@@ -158,9 +164,12 @@ __global__ void __launch_bounds__(256) k3_bin(int64_t n, const TIn *__restrict__
     keys[j] = morton3(ix, iy, iz);
     if (recu) {
         float4 r;
-        r.x = float(__dsub_rn(__dmul_rn(__dsub_rn(X, d.x0), d.scale), double(ix) + 0.5));
-        r.y = float(__dsub_rn(__dmul_rn(__dsub_rn(Y, d.y0), d.scale), double(iy) + 0.5));
-        r.z = float(__dsub_rn(__dmul_rn(__dsub_rn(Z, d.z0), d.scale), double(iz) + 0.5));
+        r.x = fminf(float(__dsub_rn(__dmul_rn(__dsub_rn(X, d.x0), d.scale), double(ix) + 0.5)),
+                    REC_MAX);
+        r.y = fminf(float(__dsub_rn(__dmul_rn(__dsub_rn(Y, d.y0), d.scale), double(iy) + 0.5)),
+                    REC_MAX);
+        r.z = fminf(float(__dsub_rn(__dmul_rn(__dsub_rn(Z, d.z0), d.scale), double(iz) + 0.5)),
+                    REC_MAX);
         r.w = float(q[j]);
         recu[j] = r;
     }
@@ -947,8 +956,8 @@ __global__ void __launch_bounds__(256) k3_near_emit(const uint32_t *__restrict__
 // leaf), TPL targets per lane; sources of the leaf and its neighbours in a fixed order (dz,
 // dy, dx, then sorted rank), read once per warp (all lanes the same address)
 // in FP32 leaf units: d = xi_t - (xi_s + offset), 1/|d| from
-// rsqrt, self and coincident pairs (|d| = 0) skipped.  Output in the
-// caller's order.
+// rsqrt, self and coincident pairs (|d| = 0, own leaf only: the records are
+// capped below 0.5 - 2^-24) skipped.  Output in the caller's order.
 template <typename TOut, int TPL>
 __global__ void __launch_bounds__(W3 * 32, 4 / TPL) k3_near_mixed(int L, int p, double w,
                                                                 const uint32_t *__restrict__ start,
@@ -1003,12 +1012,16 @@ __global__ void __launch_bounds__(W3 * 32, 4 / TPL) k3_near_mixed(int L, int p, 
                         oy[u] = tg[u].y - float(dy);
                         oz[u] = tg[u].z - float(dz);
                     }
-                    auto pair = [&](const float4 sr) {
+                    // |d| = 0 only within the target's own leaf (self, and
+                    // coincident particles, which bin to the same leaf); the
+                    // record cap keeps it from pairs across a leaf face
+                    auto pair = [&](const float4 sr, bool guard) {
 #pragma unroll
                         for (int u = 0; u < TPL; ++u) {
                             const float ddx = ox[u] - sr.x, ddy = oy[u] - sr.y, ddz = oz[u] - sr.z;
                             const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                            const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                            float ri = rsqrtf(r2);
+                            if (guard) ri = r2 > 0.f ? ri : 0.f;
                             const float qr = sr.w * ri;
                             const float qr3 = qr * ri * ri;
                             f[u] += qr;
@@ -1017,7 +1030,10 @@ __global__ void __launch_bounds__(W3 * 32, 4 / TPL) k3_near_mixed(int L, int p, 
                             gz[u] = fmaf(qr3, ddz, gz[u]);
                         }
                     };
-                    for (uint32_t j = a; j < e; ++j) pair(rec[j]);
+                    if (dx == 0 && dy == 0 && dz == 0)
+                        for (uint32_t j = a; j < e; ++j) pair(rec[j], true);
+                    else
+                        for (uint32_t j = a; j < e; ++j) pair(rec[j], false);
                 }
 #pragma unroll
         for (int u = 0; u < TPL; ++u) {

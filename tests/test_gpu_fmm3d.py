@@ -116,6 +116,23 @@ def test_bitwise_reproducible_and_coincident_particles(orc):
     assert _field_rel(a, ref) <= 1e-5
 
 
+def test_pair_across_a_leaf_face_closer_than_fp32():
+    # Two FP64 particles 1e-13 apart on either side of the face x = 1/2
+    # (leaves 3 and 4 at L = 3): their FP32 leaf coordinates are +-1/2, so
+    # without the record cap the mixed near field would meet |d| = 0 between
+    # two leaves and give inf.  The mixed path stays finite; every other
+    # particle keeps its FP32 budget against the FP64 path.
+    w = W.tiny3d(3000, 17, L=3, p=8, dtype="f64")
+    w.x[0], w.y[0], w.z[0] = 0.5 - 1e-13, 0.3, 0.7
+    w.x[1], w.y[1], w.z[1] = 0.5, 0.3, 0.7
+    rc, mixed = _run(w, "mixed")
+    assert rc == 0 and all(np.all(np.isfinite(a)) for a in mixed)
+    rc, fp64 = _run(w, "fp64")
+    assert rc == 0 and all(np.all(np.isfinite(a)) for a in fp64)
+    rest = [a[2:] for a in mixed], [a[2:] for a in fp64]
+    assert _field_rel(*rest) <= 1e-5
+
+
 def test_empty_input_and_outside_particle_then_recovery():
     torch = G.torch_cuda()
     w = W.tiny3d(1000, 14, L=3, p=6, dtype="f32")
