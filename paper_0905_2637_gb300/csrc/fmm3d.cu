@@ -56,9 +56,6 @@ constexpr int NC3_MAX = P3_MAX * (P3_MAX + 1) / 2;  // stored coefficients
 constexpr int OUT3 = (NC3_MAX + 31) / 32;          // per lane, one warp per box
 constexpr int NSLOT3 = 343;                        // offsets in [-3, 3]^3
 constexpr int W3 = 8;                              // warps per block
-// targets per lane of the mixed near-field kernel (2 measured no faster at
-// 64 charges per leaf, and slower with the sources fetched four at a time)
-constexpr int NEAR_TPL = 1;
 
 template <typename T> struct C3;
 template <> struct C3<float> { using V = float2; };
@@ -952,104 +949,118 @@ __global__ void __launch_bounds__(256) k3_near_emit(const uint32_t *__restrict__
     }
 }
 
-// Near field + L2P, mixed path: a warp per work item (32 TPL targets of one
-// leaf), TPL targets per lane; sources of the leaf and its neighbours in a fixed order (dz,
-// dy, dx, then sorted rank), read once per warp (all lanes the same address)
-// in FP32 leaf units: d = xi_t - (xi_s + offset), 1/|d| from
-// rsqrt, self and coincident pairs (|d| = 0, own leaf only: the records are
-// capped below 0.5 - 2^-24) skipped.  Output in the caller's order.
-template <typename TOut, int TPL>
-__global__ void __launch_bounds__(W3 * 32, 4 / TPL) k3_near_mixed(int L, int p, double w,
-                                                                const uint32_t *__restrict__ start,
-                                                                const float4 *__restrict__ rec,
-                                                                const float2 *__restrict__ le,
-                                                                const uint32_t *__restrict__ perm,
-                                                                const uint2 *__restrict__ items,
-                                                                const uint32_t *__restrict__ nitems,
-                                                                int64_t n, void *phi, void *ex,
-                                                                void *ey, void *ez) {
+// 1/sqrt(x) for a normal x > 0: the PTX approximate reciprocal square root
+// with denormal inputs flushed (none reach it: the pairs of two adjacent
+// leaves have |d|^2 >= 2^-48).
+__device__ __forceinline__ float rsqrt_normal(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Near field + L2P, mixed path: a warp per work item (up to 32 targets of
+// one leaf).  An item of k targets gives each target a group of rep lanes,
+// rep the largest power of two with k rep <= 32, lane c of a group taking
+// sources c, c + rep, ... of every range (a leaf's last, partly filled item
+// keeps most lanes busy), the group's partial sums added by shuffles.
+// Sources of the leaf and its neighbours in a fixed order (dz, dy, dx, then
+// sorted rank), each read once per lane group (one address per group) in
+// FP32 leaf units: d = xi_t - (xi_s + offset), 1/|d| from rsqrt, self and
+// coincident pairs (|d| = 0, own leaf only: the records are capped below
+// 0.5 - 2^-24) skipped.  Output in the caller's order.
+template <typename TOut>
+__global__ void __launch_bounds__(W3 * 32, 4) k3_near_mixed(int L, int p, double w,
+                                                            const uint32_t *__restrict__ start,
+                                                            const float4 *__restrict__ rec,
+                                                            const float2 *__restrict__ le,
+                                                            const uint32_t *__restrict__ perm,
+                                                            const uint2 *__restrict__ items,
+                                                            const uint32_t *__restrict__ nitems,
+                                                            int64_t n, void *phi, void *ex,
+                                                            void *ey, void *ez) {
     __shared__ float2 sle[W3][NC3_MAX];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t it = int64_t(blockIdx.x) * W3 + wid;
     if (it >= int64_t(*nitems)) return;
-    // one item: up to 32 TPL targets of leaf b starting at sorted rank s0
+    // one item: the targets s0 .. s1 - 1 of leaf b
     const uint2 item = items[it];
     const int64_t b = item.x;
     if (!PF_IN(b, int64_t(1) << (3 * L))) return;
     const uint32_t s0 = item.y;
-    const uint32_t s1 = min(start[b + 1], s0 + uint32_t(32 * TPL));
+    const uint32_t s1 = min(start[b + 1], s0 + 32u);
+    const int k = int(s1 - s0);  // 1..32 (an item holds at least one target)
+    int lg = 0;
+    while (lg < 5 && (k << (lg + 1)) <= 32) ++lg;
+    const uint32_t rep = 1u << lg, c = uint32_t(lane) & (rep - 1u);
+    const uint32_t i = s0 + uint32_t(lane >> lg);
+    const bool live = i < s1;
     const int nc = nc3(p);
     const bool far = L >= 2;
     if (far)
-        for (int i = lane; i < nc; i += 32) sle[wid][i] = le[(lvl_off3(L) + b) * nc + i];
+        for (int t = lane; t < nc; t += 32) sle[wid][t] = le[(lvl_off3(L) + b) * nc + t];
     __syncwarp();
     const int ix = int(compact3(uint32_t(b))), iy = int(compact3(uint32_t(b) >> 1)),
               iz = int(compact3(uint32_t(b) >> 2));
     const int side = 1 << L;
     const float inv_w = float(1.0 / w), inv_w2 = float(1.0 / (w * w));
-    {
-        const uint32_t t0 = s0;
-        float4 tg[TPL];
-        float f[TPL], gx[TPL], gy[TPL], gz[TPL];
-#pragma unroll
-        for (int u = 0; u < TPL; ++u) {
-            const uint32_t i = t0 + uint32_t(lane + 32 * u);
-            tg[u] = i < s1 ? rec[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            f[u] = gx[u] = gy[u] = gz[u] = 0.f;
-        }
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int nx = ix + dx, ny = iy + dy, nz = iz + dz;
-                    if (nx < 0 || ny < 0 || nz < 0 || nx >= side || ny >= side || nz >= side)
-                        continue;
-                    const uint32_t nb = morton3(uint32_t(nx), uint32_t(ny), uint32_t(nz));
-                    const uint32_t a = start[nb], e = start[nb + 1];
-                    float ox[TPL], oy[TPL], oz[TPL];
-#pragma unroll
-                    for (int u = 0; u < TPL; ++u) {
-                        ox[u] = tg[u].x - float(dx);
-                        oy[u] = tg[u].y - float(dy);
-                        oz[u] = tg[u].z - float(dz);
-                    }
-                    // |d| = 0 only within the target's own leaf (self, and
-                    // coincident particles, which bin to the same leaf); the
-                    // record cap keeps it from pairs across a leaf face
-                    auto pair = [&](const float4 sr, bool guard) {
-#pragma unroll
-                        for (int u = 0; u < TPL; ++u) {
-                            const float ddx = ox[u] - sr.x, ddy = oy[u] - sr.y, ddz = oz[u] - sr.z;
-                            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                            float ri = rsqrtf(r2);
-                            if (guard) ri = r2 > 0.f ? ri : 0.f;
-                            const float qr = sr.w * ri;
-                            const float qr3 = qr * ri * ri;
-                            f[u] += qr;
-                            gx[u] = fmaf(qr3, ddx, gx[u]);
-                            gy[u] = fmaf(qr3, ddy, gy[u]);
-                            gz[u] = fmaf(qr3, ddz, gz[u]);
-                        }
-                    };
-                    if (dx == 0 && dy == 0 && dz == 0)
+    const float4 tg = live ? rec[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int nx = ix + dx, ny = iy + dy, nz = iz + dz;
+                if (nx < 0 || ny < 0 || nz < 0 || nx >= side || ny >= side || nz >= side)
+                    continue;
+                const uint32_t nb = morton3(uint32_t(nx), uint32_t(ny), uint32_t(nz));
+                const uint32_t a = start[nb], e = start[nb + 1];
+                const float ox = tg.x - float(dx), oy = tg.y - float(dy), oz = tg.z - float(dz);
+                // |d| = 0 only within the target's own leaf (self, and
+                // coincident particles, which bin to the same leaf); the
+                // record cap keeps it from pairs across a leaf face
+                auto pair = [&](const float4 sr, bool guard) {
+                    const float ddx = ox - sr.x, ddy = oy - sr.y, ddz = oz - sr.z;
+                    const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                    float ri = guard ? rsqrtf(r2) : rsqrt_normal(r2);
+                    if (guard) ri = r2 > 0.f ? ri : 0.f;
+                    const float qr = sr.w * ri;
+                    const float qr3 = qr * ri * ri;
+                    f += qr;
+                    gx = fmaf(qr3, ddx, gx);
+                    gy = fmaf(qr3, ddy, gy);
+                    gz = fmaf(qr3, ddz, gz);
+                };
+                // full items (rep = 1) on the plain loop: the strided one
+                // measured slower there
+                const bool own = dx == 0 && dy == 0 && dz == 0;
+                if (rep == 1u) {
+                    if (own)
                         for (uint32_t j = a; j < e; ++j) pair(rec[j], true);
                     else
                         for (uint32_t j = a; j < e; ++j) pair(rec[j], false);
-                }
-#pragma unroll
-        for (int u = 0; u < TPL; ++u) {
-            if (t0 + 32 * u >= s1) break;  // warp-uniform
-            const uint32_t i = t0 + uint32_t(lane + 32 * u);
-            float ff = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-            if (far) l2p3<float, float2>(sle[wid], p, tg[u].x, tg[u].y, tg[u].z, ff, fx, fy, fz);
-            if (i < s1) {
-                const int64_t o = perm[i];
-                if (PF_IN(o, n)) {
-                    store3<TOut>(phi, o, double((f[u] + ff) * inv_w));
-                    store3<TOut>(ex, o, double((gx[u] - fx) * inv_w2));
-                    store3<TOut>(ey, o, double((gy[u] - fy) * inv_w2));
-                    store3<TOut>(ez, o, double((gz[u] - fz) * inv_w2));
+                } else {
+                    const float4 *sp = rec + a + c;
+                    const int cnt = a + c < e ? int((e - a - c + rep - 1u) >> lg) : 0;
+                    if (own)
+                        for (int t = 0; t < cnt; ++t) pair(sp[size_t(t) * rep], true);
+                    else
+                        for (int t = 0; t < cnt; ++t) pair(sp[size_t(t) * rep], false);
                 }
             }
+    for (uint32_t o = 1; o < rep; o <<= 1) {
+        f += __shfl_xor_sync(0xffffffffu, f, int(o));
+        gx += __shfl_xor_sync(0xffffffffu, gx, int(o));
+        gy += __shfl_xor_sync(0xffffffffu, gy, int(o));
+        gz += __shfl_xor_sync(0xffffffffu, gz, int(o));
+    }
+    if (c == 0 && live) {
+        float ff = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+        if (far) l2p3<float, float2>(sle[wid], p, tg.x, tg.y, tg.z, ff, fx, fy, fz);
+        const int64_t o = perm[i];
+        if (PF_IN(o, n)) {
+            store3<TOut>(phi, o, double((f + ff) * inv_w));
+            store3<TOut>(ex, o, double((gx - fx) * inv_w2));
+            store3<TOut>(ey, o, double((gy - fy) * inv_w2));
+            store3<TOut>(ez, o, double((gz - fz) * inv_w2));
         }
     }
 }
@@ -1522,11 +1533,11 @@ int evaluate3(petfmm3d_ctx *c, int64_t n, const void *x, const void *y, const vo
         const float2 *le = static_cast<const float2 *>(c->le.p);
         const unsigned gi = grid_w(cap);
         if (f32)
-            k3_near_mixed<float, NEAR_TPL><<<gi, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm,
-                                                                   items, nit, n, phi, ex, ey, ez);
+            k3_near_mixed<float><<<gi, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, items,
+                                                         nit, n, phi, ex, ey, ez);
         else
-            k3_near_mixed<double, NEAR_TPL><<<gi, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm,
-                                                                    items, nit, n, phi, ex, ey, ez);
+            k3_near_mixed<double><<<gi, W3 * 32, 0, st>>>(L, p, w, start, rec, le, perm, items,
+                                                          nit, n, phi, ex, ey, ez);
     } else {
         const Dbl4 *xs = static_cast<const Dbl4 *>(c->xs.p);
         const double2 *le = static_cast<const double2 *>(c->le.p);
