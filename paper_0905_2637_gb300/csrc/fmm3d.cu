@@ -869,6 +869,137 @@ __global__ void __launch_bounds__(W3 * 32) k3_l2l(int l, int L, int p, const uin
 }
 
 // ---------------------------------------------------------------------------
+// M2M and L2L of the mixed path for p <= 8 as real matrix-vector products:
+// each of the eight child octants has a fixed real P^2 x P^2 operator in the
+// real basis of the M2L matrices (the sums of k3_m2m / k3_l2l applied to the
+// basis vectors on the host in FP64), staged in shared memory for a block.
+// ---------------------------------------------------------------------------
+constexpr int TT_MAXP = 8;  // operators of up to 64 x 64 in shared memory
+
+// A warp per parent box of level l: ME = sum over occupied children c of
+// A_c x_c, x_c the child's ME in the real basis; lanes over output rows.
+template <int P>
+__global__ void __launch_bounds__(W3 * 32) k3_m2m_real(int l, int L, const uint32_t *__restrict__ start,
+                                                       const float *__restrict__ op,
+                                                       const short2 *__restrict__ rmap,
+                                                       float2 *__restrict__ me) {
+    constexpr int NC = P * (P + 1) / 2, NR = P * P, RL = (NR + 31) / 32;
+    __shared__ float sA[NR * NR];  // sA[k_in * NR + r_out]
+    __shared__ float sx[W3][NR];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t b = int64_t(blockIdx.x) * W3 + wid;
+    const bool act = b < (int64_t(1) << (3 * l)) && box_count3(start, L, l, uint32_t(b)) != 0;
+    short2 rm[RL];
+    float acc[RL];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        const int r = lane + 32 * i;
+        rm[i] = r < NR ? rmap[r] : make_short2(0, 0);
+        acc[i] = 0.f;
+    }
+    for (int c = 0; c < 8; ++c) {
+        __syncthreads();  // the previous operator is no longer read
+        for (int t = threadIdx.x; t < NR * NR; t += W3 * 32) sA[t] = op[size_t(c) * NR * NR + t];
+        const uint32_t cb = uint32_t(b) * 8u + uint32_t(c);
+        const bool use = act && box_count3(start, L, l + 1, cb) != 0;
+        if (use) {
+            const float2 *mc = me + (lvl_off3(l + 1) + cb) * NC;
+#pragma unroll
+            for (int i = 0; i < RL; ++i) {
+                const int r = lane + 32 * i;
+                if (r < NR) {
+                    const float2 v = mc[rm[i].x];
+                    sx[wid][r] = rm[i].y == 1 ? v.y : v.x;
+                }
+            }
+        }
+        __syncthreads();
+        if (use)
+            for (int k = 0; k < NR; ++k) {
+                const float xk = sx[wid][k];
+#pragma unroll
+                for (int i = 0; i < RL; ++i)
+                    if (lane + 32 * i < NR) acc[i] = fmaf(sA[k * NR + lane + 32 * i], xk, acc[i]);
+            }
+    }
+    if (!act) return;
+    float *dst = reinterpret_cast<float *>(me + (lvl_off3(l) + b) * NC);
+#pragma unroll
+    for (int i = 0; i < RL; ++i)
+        if (lane + 32 * i < NR) {
+            dst[2 * rm[i].x + (rm[i].y == 1 ? 1 : 0)] = acc[i];
+            if (rm[i].y == 2) dst[2 * rm[i].x + 1] = 0.f;  // Im of m = 0
+        }
+}
+
+// L2L: a block per (child octant o, W3 parents of level l - 1), a warp per
+// parent; its child of octant o adds B_o y to the local expansion that M2L
+// wrote, y the parent's LE in the real basis.
+template <int P>
+__global__ void __launch_bounds__(W3 * 32) k3_l2l_real(int l, int L, const uint32_t *__restrict__ start,
+                                                       const float *__restrict__ op,
+                                                       const short2 *__restrict__ rmap,
+                                                       float2 *__restrict__ le) {
+    constexpr int NC = P * (P + 1) / 2, NR = P * P, RL = (NR + 31) / 32;
+    __shared__ float sA[NR * NR];
+    __shared__ float sx[W3][NR];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int o = int(blockIdx.x & 7u);
+    const int64_t pb = int64_t(blockIdx.x >> 3) * W3 + wid;
+    const int64_t cb = pb * 8 + o;
+    const bool act = pb < (int64_t(1) << (3 * (l - 1))) && box_count3(start, L, l, uint32_t(cb)) != 0;
+    for (int t = threadIdx.x; t < NR * NR; t += W3 * 32) sA[t] = op[size_t(o) * NR * NR + t];
+    short2 rm[RL];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        const int r = lane + 32 * i;
+        rm[i] = r < NR ? rmap[r] : make_short2(0, 0);
+        if (act && r < NR) {
+            const float2 v = le[(lvl_off3(l - 1) + pb) * NC + rm[i].x];
+            sx[wid][r] = rm[i].y == 1 ? v.y : v.x;
+        }
+    }
+    __syncthreads();
+    if (!act) return;
+    float acc[RL];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) acc[i] = 0.f;
+    for (int k = 0; k < NR; ++k) {
+        const float xk = sx[wid][k];
+#pragma unroll
+        for (int i = 0; i < RL; ++i)
+            if (lane + 32 * i < NR) acc[i] = fmaf(sA[k * NR + lane + 32 * i], xk, acc[i]);
+    }
+    float *dst = reinterpret_cast<float *>(le + (lvl_off3(l) + cb) * NC);
+#pragma unroll
+    for (int i = 0; i < RL; ++i)
+        if (lane + 32 * i < NR) dst[2 * rm[i].x + (rm[i].y == 1 ? 1 : 0)] += acc[i];
+}
+
+template <int P>
+cudaError_t m2m_l2l_real_p(bool m2m, int l, int L, const uint32_t *start, const float *op,
+                           const short2 *rmap, float2 *ex, cudaStream_t st) {
+    if (m2m)
+        k3_m2m_real<P><<<unsigned(((int64_t(1) << (3 * l)) + W3 - 1) / W3), W3 * 32, 0, st>>>(
+            l, L, start, op, rmap, ex);
+    else
+        k3_l2l_real<P><<<unsigned(8 * (((int64_t(1) << (3 * (l - 1))) + W3 - 1) / W3)), W3 * 32, 0,
+                         st>>>(l, L, start, op, rmap, ex);
+    return cudaGetLastError();
+}
+
+// m2m: level l's parents from level l + 1; else level l's children from l - 1
+cudaError_t launch_m2m_l2l_real(bool m2m, int p, int l, int L, const uint32_t *start,
+                                const float *op, const short2 *rmap, float2 *ex, cudaStream_t st) {
+    switch (p) {
+#define TT_CASE(P) case P: return m2m_l2l_real_p<P>(m2m, l, L, start, op, rmap, ex, st);
+        TT_CASE(1) TT_CASE(2) TT_CASE(3) TT_CASE(4) TT_CASE(5) TT_CASE(6) TT_CASE(7) TT_CASE(8)
+#undef TT_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // L2P in leaf units: phi = sum L~_n^m conj(R_n^m(xi)) and g = grad_xi of it,
 // column by column (m >= 0, weight 2 for m > 0: the m and -m terms of a real
 // potential are conjugate), with
@@ -1218,6 +1349,78 @@ void host_m2l_real(int p, const cd *iv, double *a) {
         }
 }
 
+// Coefficient (n, m) of a stored m >= 0 series, m < 0 by symmetry.
+cd host_coef(const cd *a, int n, int m) {
+    if (m >= 0) return a[n * (n + 1) / 2 + m];
+    const cd v = std::conj(a[n * (n + 1) / 2 - m]);
+    return (m & 1) ? -v : v;
+}
+
+// The M2M sum of k3_m2m for one child (rt: R_k^l of the child's offset):
+// out_n^m = sum_k 2^-(n-k) sum_l conj(R_k^l) M_{n-k}^{m-l}.
+void host_m2m_one(int p, const cd *rt, const cd *mc, cd *out) {
+    for (int n = 0; n < p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            cd s(0.0, 0.0);
+            for (int k = 0; k <= n; ++k) {
+                cd sk(0.0, 0.0);
+                for (int ll = -k; ll <= k; ++ll) {
+                    const int mm = m - ll;
+                    if (mm < -(n - k) || mm > n - k) continue;
+                    sk += std::conj(host_coef(rt, k, ll)) * host_coef(mc, n - k, mm);
+                }
+                s += sk * std::ldexp(1.0, -(n - k));
+            }
+            out[n * (n + 1) / 2 + m] = s;
+        }
+}
+
+// The L2L sum of k3_l2l for one child: out_j^s = 2^-(j+1) sum_{k, l}
+// conj(R_k^l) L_{j+k}^{s+l}.
+void host_l2l_one(int p, const cd *rt, const cd *lp, cd *out) {
+    for (int j = 0; j < p; ++j)
+        for (int s = 0; s <= j; ++s) {
+            cd acc(0.0, 0.0);
+            for (int k = 0; j + k < p; ++k)
+                for (int ll = -k; ll <= k; ++ll) {
+                    const int ss = s + ll;
+                    if (ss < -(j + k) || ss > j + k) continue;
+                    acc += std::conj(host_coef(rt, k, ll)) * host_coef(lp, j + k, ss);
+                }
+            out[j * (j + 1) / 2 + s] = acc * std::ldexp(1.0, -(j + 1));
+        }
+}
+
+// The real p^2 x p^2 matrix of a map of real-potential series (the basis
+// of host_m2l_real), by applying it to each basis vector:
+// a[k_in * p^2 + r_out], FP64.
+template <typename F> void host_real_matrix(int p, F apply, double *a) {
+    const int nc = p * (p + 1) / 2, nr = p * p;
+    // real index -> (coefficient, imaginary part?)
+    std::vector<int> jof(static_cast<size_t>(nr)), imof(static_cast<size_t>(nr), 0);
+    std::vector<int> imidx(size_t(nc), -1);
+    for (int n = 0, r = nc; n < p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            const int j = n * (n + 1) / 2 + m;
+            jof[size_t(j)] = j;
+            if (m > 0) {
+                imidx[size_t(j)] = r;
+                jof[size_t(r)] = j;
+                imof[size_t(r++)] = 1;
+            }
+        }
+    std::vector<cd> in(static_cast<size_t>(nc)), out(static_cast<size_t>(nc));
+    for (int k = 0; k < nr; ++k) {
+        std::fill(in.begin(), in.end(), cd(0.0, 0.0));
+        in[size_t(jof[size_t(k)])] = imof[size_t(k)] ? cd(0.0, 1.0) : cd(1.0, 0.0);
+        apply(in.data(), out.data());
+        for (int j = 0; j < nc; ++j) {
+            a[size_t(k) * nr + j] = out[size_t(j)].real();
+            if (imidx[size_t(j)] >= 0) a[size_t(k) * nr + imidx[size_t(j)]] = out[size_t(j)].imag();
+        }
+    }
+}
+
 struct DevBuf3 {
     void *p = nullptr;
     size_t cap = 0;
@@ -1250,6 +1453,7 @@ struct petfmm3d_ctx {
     DevBuf3 keysA, keysB, valsA, valsB, sortw, start, recu, rec, xs, me, le, status;
     DevBuf3 ncnt, noff, nscan, nitems;  // the mixed near field's work items
     DevBuf3 rtab32, itab32, rtab64, itab64, atab32, rmap;
+    DevBuf3 m2m32, l2l32;  // p <= 8: the real M2M / L2L operators of the 8 octants
     bool timing = false, ev_recorded = false;
     cudaEvent_t ev[PETFMM3D_STAGE_COUNT + 1] = {};
     uint64_t launches = 0, evaluations = 0;
@@ -1322,6 +1526,23 @@ int upload_tables(petfmm3d_ctx *c) {
     P3_CUDA(cudaMemcpy(c->itab64.p, i64.data(), i64.size() * sizeof(double2), cudaMemcpyHostToDevice));
     P3_CUDA(cudaMemcpy(c->rtab32.p, r32.data(), r32.size() * sizeof(float2), cudaMemcpyHostToDevice));
     P3_CUDA(cudaMemcpy(c->itab32.p, i32.data(), i32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    if (p <= TT_MAXP) {
+        // op[(octant * p^2 + k_in) * p^2 + r_out]
+        std::vector<float> mm(size_t(8) * nr * nr), ll(size_t(8) * nr * nr);
+        for (int o = 0; o < 8; ++o) {
+            const cd *ro = rt.data() + size_t(o) * nc;
+            host_real_matrix(p, [&](const cd *in, cd *out) { host_m2m_one(p, ro, in, out); },
+                             a64.data());
+            for (size_t i = 0; i < size_t(nr) * nr; ++i) mm[size_t(o) * nr * nr + i] = float(a64[i]);
+            host_real_matrix(p, [&](const cd *in, cd *out) { host_l2l_one(p, ro, in, out); },
+                             a64.data());
+            for (size_t i = 0; i < size_t(nr) * nr; ++i) ll[size_t(o) * nr * nr + i] = float(a64[i]);
+        }
+        P3_TRY(ensure3(c->m2m32, mm.size() * sizeof(float), c->stream));
+        P3_TRY(ensure3(c->l2l32, ll.size() * sizeof(float), c->stream));
+        P3_CUDA(cudaMemcpy(c->m2m32.p, mm.data(), mm.size() * sizeof(float), cudaMemcpyHostToDevice));
+        P3_CUDA(cudaMemcpy(c->l2l32.p, ll.data(), ll.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     return PETFMM_OK;
 }
 
@@ -1397,7 +1618,17 @@ int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
     P3_CUDA(cudaGetLastError());
     c->launches++;
     mark3(c, PETFMM3D_STAGE_M2M);
+    // mixed path with p <= 8: M2M and L2L as real matrix-vector products
+    const bool real_tt = sizeof(T) == 4 && p <= TT_MAXP;
     for (int l = L - 1; l >= 2; --l) {
+        if constexpr (sizeof(T) == 4) {
+            if (real_tt) {
+                P3_CUDA(launch_m2m_l2l_real(true, p, l, L, start, static_cast<const float *>(c->m2m32.p),
+                                            static_cast<const short2 *>(c->rmap.p), me, st));
+                c->launches++;
+                continue;
+            }
+        }
         k3_m2m<T><<<grid_w(int64_t(1) << (3 * l)), W3 * 32, 0, st>>>(l, L, p, start, rtab, me);
         P3_CUDA(cudaGetLastError());
         c->launches++;
@@ -1419,6 +1650,14 @@ int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
     }
     mark3(c, PETFMM3D_STAGE_L2L);
     for (int l = 3; l <= L; ++l) {
+        if constexpr (sizeof(T) == 4) {
+            if (real_tt) {
+                P3_CUDA(launch_m2m_l2l_real(false, p, l, L, start, static_cast<const float *>(c->l2l32.p),
+                                            static_cast<const short2 *>(c->rmap.p), le, st));
+                c->launches++;
+                continue;
+            }
+        }
         k3_l2l<T><<<grid_w(int64_t(1) << (3 * l)), W3 * 32, 0, st>>>(l, L, p, start, rtab, le);
         P3_CUDA(cudaGetLastError());
         c->launches++;
@@ -1671,7 +1910,8 @@ int petfmm3d_destroy(petfmm3d_ctx *c) {
     DevBuf3 *bufs[] = {&c->ncnt, &c->noff, &c->nscan, &c->nitems,
                        &c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->sortw, &c->start,
                        &c->recu,  &c->rec,   &c->xs,    &c->me,    &c->le,    &c->status,
-                       &c->rtab32, &c->itab32, &c->rtab64, &c->itab64, &c->atab32, &c->rmap};
+                       &c->rtab32, &c->itab32, &c->rtab64, &c->itab64, &c->atab32, &c->rmap,
+                       &c->m2m32, &c->l2l32};
     for (DevBuf3 *b : bufs)
         if (b->p) cudaFree(b->p);
     for (int i = 0; i <= PETFMM3D_STAGE_COUNT; ++i)
