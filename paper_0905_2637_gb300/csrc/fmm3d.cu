@@ -220,8 +220,9 @@ __device__ __forceinline__ Part3<double> leaf_part(const Dbl4 *xs, int64_t j, do
 // ---------------------------------------------------------------------------
 // P2M (leaves): M~_n^m = sum_j q_j conj(R_n^m(xi_j)).  A warp per leaf split
 // into 32 / p lane groups; lane m of a group owns column m: R_m^m = (xi + i
-// eta)^m / (2^m m!), then the recurrence in n, for every G-th particle of the
-// leaf; the groups' sums are added in group order.
+// eta)^m / (2^m m!), then the recurrence in n (its reciprocals computed once
+// per lane), for every G-th particle of the leaf; the groups' sums are added
+// in group order.
 // ---------------------------------------------------------------------------
 template <typename T, typename P>
 __global__ void __launch_bounds__(W3 * 32) k3_p2m(int L, int p, Dom3 d, const uint32_t *__restrict__ start,
@@ -241,26 +242,39 @@ __global__ void __launch_bounds__(W3 * 32) k3_p2m(int L, int p, Dom3 d, const ui
     const double cy = d.y0 + (double(compact3(uint32_t(b) >> 1)) + 0.5) * w;
     const double cz = d.z0 + (double(compact3(uint32_t(b) >> 2)) + 0.5) * w;
     V acc[P3_MAX];
+    // the lane's constants, out of the particle loop: 1 / (2^m m!) and
+    // 1 / (n^2 - m^2) of the recurrence
+    T cm = T(1), inv[P3_MAX];
+    for (int t = 1; t <= m; ++t) cm /= T(2 * t);
 #pragma unroll
-    for (int n = 0; n < P3_MAX; ++n) acc[n] = mk<V>(T(0), T(0));
-    if (g < G) {
-        for (uint32_t j = s0 + uint32_t(g); j < s1; j += uint32_t(G)) {
-            const Part3<T> a = leaf_part(part, j, cx, cy, cz, 1.0 / w);
+    for (int n = 0; n < P3_MAX; ++n) {
+        acc[n] = mk<V>(T(0), T(0));
+        inv[n] = n > m && n < p ? T(1) / T(n * n - m * m) : T(0);
+    }
+    // the leaf's records staged 64 at a time in shared memory by coalesced
+    // loads, so that no particle's load waits in the groups' loops
+    __shared__ P stage[W3][64];
+    const int wid = threadIdx.x >> 5;
+    for (uint32_t c0 = s0; c0 < s1; c0 += 64u) {
+        const uint32_t cn = min(64u, s1 - c0);
+        __syncwarp();
+        for (uint32_t i = uint32_t(lane); i < cn; i += 32u) stage[wid][i] = part[c0 + i];
+        __syncwarp();
+        if (g >= G) continue;
+        for (uint32_t j = uint32_t(g); j < cn; j += uint32_t(G)) {
+            const Part3<T> a = leaf_part(stage[wid], j, cx, cy, cz, 1.0 / w);
             const T r2 = a.x * a.x + a.y * a.y + a.z * a.z;
-            V rmm = mk<V>(a.q, T(0));  // q R_0^0, then q R_m^m
-            for (int t = 1; t <= m; ++t) {
-                const T s = T(1) / T(2 * t);
-                rmm = mk<V>((rmm.x * a.x - rmm.y * a.y) * s, (rmm.x * a.y + rmm.y * a.x) * s);
-            }
-            V r1 = rmm, r2v = mk<V>(T(0), T(0));
+            V zm = mk<V>(T(1), T(0));  // (xi + i eta)^m
+            for (int t = 1; t <= m; ++t) zm = mk<V>(zm.x * a.x - zm.y * a.y, zm.x * a.y + zm.y * a.x);
+            const T qc = a.q * cm;
+            V r1 = mk<V>(zm.x * qc, zm.y * qc), r2v = mk<V>(T(0), T(0));  // q R_m^m
 #pragma unroll
             for (int n = 0; n < P3_MAX; ++n) {
                 if (n < m || n >= p) continue;
                 V rn = r1;
                 if (n > m) {
-                    const T inv = T(1) / T(n * n - m * m);
                     const T c1 = T(2 * n - 1) * a.z;
-                    rn = mk<V>((c1 * r1.x - r2 * r2v.x) * inv, (c1 * r1.y - r2 * r2v.y) * inv);
+                    rn = mk<V>((c1 * r1.x - r2 * r2v.x) * inv[n], (c1 * r1.y - r2 * r2v.y) * inv[n]);
                     r2v = r1;
                     r1 = rn;
                 }
