@@ -697,6 +697,18 @@ uint64_t petfmm3d_launches(const petfmm3d_ctx *ctx);
  * expansions scaled by the box width.  out[k * p^2 + r] = d(output r) /
  * d(input k), FP64 (the library rounds it to FP32); cap >= p^4 doubles. */
 int petfmm3d_debug_m2l_operator(int order, int dx, int dy, int dz, double *out, int64_t cap);
+/* kinds of petfmm3d_debug_shift_operator */
+enum { PETFMM3D_SHIFT_M2M = 0, PETFMM3D_SHIFT_L2L = 1 };
+/* Host only (no device work): the mixed path's M2M (child of the octant to
+ * its parent) or L2L (parent to its child of the octant) operator of order
+ * p <= 16 (the library uses them for p <= 8), in the real basis of
+ * petfmm3d_debug_m2l_operator, for expansions scaled by each box's own
+ * width (the Sec. 8 octree: a child is half its parent's width).  Octant
+ * bit 0/1/2 set: the child lies on the +x/+y/+z side of the parent's
+ * centre.  out[k * p^2 + r] = d(output r) / d(input k), FP64 (the library
+ * rounds it to FP32); cap >= p^4 doubles; PETFMM_EINVAL for a bad kind,
+ * octant, order or cap. */
+int petfmm3d_debug_shift_operator(int order, int kind, int octant, double *out, int64_t cap);
 int petfmm3d_destroy(petfmm3d_ctx *ctx);
 
 #ifdef __cplusplus

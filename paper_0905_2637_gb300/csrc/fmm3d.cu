@@ -1435,6 +1435,18 @@ template <typename F> void host_real_matrix(int p, F apply, double *a) {
     }
 }
 
+// The real M2M (kind 0: child of the octant -> parent) or L2L (kind 1:
+// parent -> child of the octant) operator of order p, FP64.
+void host_shift_real(int p, int kind, int octant, double *a) {
+    std::vector<cd> ro(static_cast<size_t>(p * (p + 1) / 2));
+    host_rec_r((octant & 1) ? 0.25 : -0.25, (octant & 2) ? 0.25 : -0.25,
+               (octant & 4) ? 0.25 : -0.25, p, ro.data());
+    if (kind == 0)
+        host_real_matrix(p, [&](const cd *in, cd *out) { host_m2m_one(p, ro.data(), in, out); }, a);
+    else
+        host_real_matrix(p, [&](const cd *in, cd *out) { host_l2l_one(p, ro.data(), in, out); }, a);
+}
+
 struct DevBuf3 {
     void *p = nullptr;
     size_t cap = 0;
@@ -1544,12 +1556,9 @@ int upload_tables(petfmm3d_ctx *c) {
         // op[(octant * p^2 + k_in) * p^2 + r_out]
         std::vector<float> mm(size_t(8) * nr * nr), ll(size_t(8) * nr * nr);
         for (int o = 0; o < 8; ++o) {
-            const cd *ro = rt.data() + size_t(o) * nc;
-            host_real_matrix(p, [&](const cd *in, cd *out) { host_m2m_one(p, ro, in, out); },
-                             a64.data());
+            host_shift_real(p, 0, o, a64.data());
             for (size_t i = 0; i < size_t(nr) * nr; ++i) mm[size_t(o) * nr * nr + i] = float(a64[i]);
-            host_real_matrix(p, [&](const cd *in, cd *out) { host_l2l_one(p, ro, in, out); },
-                             a64.data());
+            host_shift_real(p, 1, o, a64.data());
             for (size_t i = 0; i < size_t(nr) * nr; ++i) ll[size_t(o) * nr * nr + i] = float(a64[i]);
         }
         P3_TRY(ensure3(c->m2m32, mm.size() * sizeof(float), c->stream));
@@ -1915,6 +1924,16 @@ int petfmm3d_debug_m2l_operator(int order, int dx, int dy, int dz, double *out, 
     std::vector<cd> iv(size_t(nci3(order)));
     host_rec_i(dx, dy, dz, 2 * order - 1, iv.data());
     host_m2l_real(order, iv.data(), out);
+    return PETFMM_OK;
+}
+
+int petfmm3d_debug_shift_operator(int order, int kind, int octant, double *out, int64_t cap) {
+    if (order < 1 || order > P3_MAX || !out) return PETFMM_EINVAL;
+    if ((kind != PETFMM3D_SHIFT_M2M && kind != PETFMM3D_SHIFT_L2L) || octant < 0 || octant > 7)
+        return PETFMM_EINVAL;
+    const int64_t nr = int64_t(order) * order;
+    if (cap < nr * nr) return PETFMM_EINVAL;
+    host_shift_real(order, kind == PETFMM3D_SHIFT_M2M ? 0 : 1, octant, out);
     return PETFMM_OK;
 }
 

@@ -39,6 +39,7 @@ def lib3():
                 ("petfmm3d_debug_tree", I, [P, I64, P, P, P]),
                 ("petfmm3d_launches", ctypes.c_uint64, [P]),
                 ("petfmm3d_debug_m2l_operator", I, [I, I, I, I, P, I64]),
+                ("petfmm3d_debug_shift_operator", I, [I, I, I, P, I64]),
                 ("petfmm3d_destroy", I, [P])):
             fn = getattr(lib, name)
             fn.restype = res
@@ -62,6 +63,21 @@ def m2l_operator(order, dx, dy, dz):
     out = np.zeros(nr * nr, np.float64)
     _lib._ck(lib3().petfmm3d_debug_m2l_operator(order, dx, dy, dz, out.ctypes.data, out.size),
              "petfmm3d_debug_m2l_operator")
+    return out.reshape(nr, nr)
+
+
+PETFMM3D_SHIFT_M2M, PETFMM3D_SHIFT_L2L = 0, 1
+
+
+def shift_operator(order, kind, octant):
+    """The mixed path's real M2M (kind PETFMM3D_SHIFT_M2M: child of the
+    octant to its parent) or L2L (PETFMM3D_SHIFT_L2L: parent to the child)
+    operator, as the library builds it on the host (FP64):
+    a[k, r] = d(output r) / d(input k)."""
+    nr = order * order
+    out = np.zeros(nr * nr, np.float64)
+    _lib._ck(lib3().petfmm3d_debug_shift_operator(order, kind, octant, out.ctypes.data, out.size),
+             "petfmm3d_debug_shift_operator")
     return out.reshape(nr, nr)
 
 

@@ -54,3 +54,50 @@ def test_bad_offsets_are_rejected(f3):
             f3.m2l_operator(8, *d)
     with pytest.raises(_lib.PetfmmError):
         f3.m2l_operator(17, 2, 0, 0)
+
+
+def _real_series(p, n, m, part):
+    """The real-potential series of one basis vector (oracle storage)."""
+    S = np.zeros(p * (2 * p - 1), np.complex128)
+    v = 1.0 if part == 0 else 1j
+    S[O.idx3(p, n, m)] = v
+    if m:
+        S[O.idx3(p, n, -m)] = (-1) ** m * np.conj(v)
+    return S
+
+
+def _read_real(p, S, basis):
+    return np.array([S[O.idx3(p, n, m)].real if pt == 0 else S[O.idx3(p, n, m)].imag
+                     for (n, m), pt in basis])
+
+
+@pytest.mark.parametrize("p", [1, 3, 8, 10])
+@pytest.mark.parametrize("kind", ["m2m", "l2l"])
+def test_shift_operator_columns_are_the_oracle_translation(f3, p, kind):
+    # child width 1, parent width 2 centred at the origin; the scaled series
+    # are M~ = M / w^n and L~ = L w^(n+1) with each box's own width w
+    basis = _basis(p)
+    deg = np.array([n for (n, _), _ in basis], dtype=np.float64)
+    code = f3.PETFMM3D_SHIFT_M2M if kind == "m2m" else f3.PETFMM3D_SHIFT_L2L
+    for octant in range(8):
+        a = f3.shift_operator(p, code, octant)
+        assert a.shape == (p * p, p * p)
+        cc = np.array([0.5 if octant & (1 << ax) else -0.5 for ax in range(3)])
+        for k, ((n, m), part) in enumerate(basis):
+            S = _real_series(p, n, m, part)
+            if kind == "m2m":
+                out = O.m2m3d(S, cc, np.zeros(3), p)
+                col = _read_real(p, out, basis) / 2.0 ** deg
+            else:
+                Sp = S / 2.0 ** (n + 1)       # the parent's unscaled local expansion
+                out = O.l2l3d(Sp, np.zeros(3), cc, p)
+                col = _read_real(p, out, basis)
+            scale = max(1.0, np.max(np.abs(col)))
+            assert np.max(np.abs(a[k] - col)) <= 1e-12 * scale, (octant, k, n, m, part)
+
+
+def test_shift_operator_bad_arguments(f3):
+    from paper_0905_2637_gb300 import _lib
+    for args in ((8, 2, 0), (8, -1, 0), (8, 0, 8), (8, 1, -1), (0, 0, 0), (17, 0, 0)):
+        with pytest.raises(_lib.PetfmmError):
+            f3.shift_operator(*args)
