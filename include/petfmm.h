@@ -508,11 +508,12 @@ enum {
                                   0 (default): 2 in launches under 2048 blocks where it
                                   fits, else 1.  The two differ by FP32 rounding when the
                                   stages per offset differ. */
-    PETFMM_OPT_OVERLAP = 15,   /* mixed path: 1 (default) run the expansion chain (P2M,
-                                  M2M, M2L, L2L) on a second stream of the context,
-                                  overlapping the near field (work lists, pair and
-                                  directed kernels), which needs only the sorted blobs;
-                                  the final pass waits for both.  0: one stream.  Results
+    PETFMM_OPT_OVERLAP = 15,   /* mixed path: 1 (default) run the record gather and the
+                                  expansion chain (P2M, M2M, M2L, L2L) on a second
+                                  stream of the context, overlapping the near field:
+                                  its work lists need only the leaf starts, the pair
+                                  and directed kernels wait for the gather only; the
+                                  final pass waits for both.  0: one stream.  Results
                                   identical. */
     PETFMM_OPT_KERNEL = 12     /* the sum the context evaluates (the kernel parameter of
                                   the paper's Evaluator, Sec. 6.1):
@@ -534,9 +535,10 @@ int petfmm_set_option(petfmm_ctx *ctx, int option, int64_t value);
  * about zero otherwise); P2P: the directed near field (and, on the FP64 path,
  * L2P and the output in the same kernel); FINAL: the mixed path's final pass
  * (L2P, the sum of the near-field parts, the output in the caller's order;
- * about zero on the FP64 path).  With PETFMM_OPT_OVERLAP the stages P2M..L2L
- * run beside WORKLIST..P2P, so the times overlap (their sum exceeds the
- * evaluation's), and P2P also holds any wait for the end of L2L. */
+ * about zero on the FP64 path).  With PETFMM_OPT_OVERLAP the stages
+ * GATHER..L2L run beside WORKLIST..P2P, so the times overlap (their sum
+ * exceeds the evaluation's), WORKLIST also holds any wait for the end of the
+ * gather and P2P any wait for the end of L2L. */
 enum {
     PETFMM_STAGE_MORTON = 0, PETFMM_STAGE_SORT, PETFMM_STAGE_GATHER, PETFMM_STAGE_P2M,
     PETFMM_STAGE_M2M, PETFMM_STAGE_M2L, PETFMM_STAGE_L2L, PETFMM_STAGE_WORKLIST,

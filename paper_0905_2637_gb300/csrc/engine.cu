@@ -158,7 +158,7 @@ struct petfmm_ctx {
     // the expansion chain's stream on the mixed path, and its fork / join
     bool overlap = true;  // PETFMM_OPT_OVERLAP
     cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_gathered = nullptr;
     bool ev_recorded = false;
     // level rules of the automatic L (petfmm_set_level_rules / petfmm_tune_batch)
     std::vector<petfmm_level_rule> rules;
@@ -785,18 +785,11 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
     const uint32_t *perm = in_first ? vA : vB;
     PF_CUDA(launch_leaf_start(dtask + pl.start.first, pl.start.count, pl.start.nblocks, dinst, skeys,
                               start, st, lc));
-    stage_mark(c, PETFMM_STAGE_GATHER);
-    if (mixed)
-        PF_CUDA(launch_gather_mixed(recu, perm, static_cast<float4 *>(c->rec.p), N, st, lc));
-    else
-        PF_CUDA(launch_gather_f64(dtask + pl.particles.first, pl.particles.count,
-                                  pl.particles.nblocks, dinst, f32, perm,
-                                  static_cast<double *>(c->xs.p), static_cast<double *>(c->ys.p),
-                                  static_cast<double *>(c->gs.p), st, lc));
-    // The expansion chain (P2M, M2M, M2L, L2L) runs on a second stream on
-    // the mixed path: the near field (work lists, pair and directed kernels)
-    // needs only the sorted blobs and the leaf starts, so the two overlap,
-    // and the final pass joins them (PETFMM_OPT_OVERLAP).
+    // The record gather and the expansion chain (P2M, M2M, M2L, L2L) run on
+    // a second stream on the mixed path: the near-field work lists need only
+    // the leaf starts and run beside the gather, the pair and directed
+    // kernels wait for the gathered blobs only, and the final pass joins
+    // the two streams (PETFMM_OPT_OVERLAP).
     cudaStream_t xs = st;
     const bool fork = mixed && c->overlap;
     if (fork) {
@@ -804,6 +797,15 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
         PF_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
         xs = c->aux;
     }
+    stage_mark_on(c, PETFMM_STAGE_GATHER, xs);
+    if (mixed)
+        PF_CUDA(launch_gather_mixed(recu, perm, static_cast<float4 *>(c->rec.p), N, xs, lc));
+    else
+        PF_CUDA(launch_gather_f64(dtask + pl.particles.first, pl.particles.count,
+                                  pl.particles.nblocks, dinst, f32, perm,
+                                  static_cast<double *>(c->xs.p), static_cast<double *>(c->ys.p),
+                                  static_cast<double *>(c->gs.p), st, lc));
+    if (fork) PF_CUDA(cudaEventRecord(c->ev_gathered, xs));
     stage_mark_on(c, PETFMM_STAGE_P2M, xs);
     uint2 *occ = static_cast<uint2 *>(c->occ.p);
     PF_CUDA(launch_occ_list(dtask + pl.leaves_p2m.first, pl.leaves_p2m.count, pl.leaves_p2m.nblocks,
@@ -924,6 +926,7 @@ int run(petfmm_ctx *c, const std::vector<Problem> &probs) {
                                      static_cast<uint32_t *>(c->off.p), scratch,
                                      static_cast<uint4 *>(c->pitems.p), ctrl,
                                      c->p2p_mode == 0 ? &porder : nullptr, pb, st, lc));
+    if (fork) PF_CUDA(cudaStreamWaitEvent(st, c->ev_gathered, 0));
     stage_mark(c, PETFMM_STAGE_PAIRS);
     // pairwise mode: the neighbouring leaves pairwise
     if (pairs)
@@ -1068,7 +1071,8 @@ int petfmm_create(const petfmm_domain *dom, int levels, int order, double sigma,
     }
     if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_gathered, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         petfmm_destroy(c);
         return PETFMM_ECUDA;
@@ -1102,6 +1106,7 @@ int petfmm_destroy(petfmm_ctx *c) {
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_gathered) cudaEventDestroy(c->ev_gathered);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     cudaGetLastError();
