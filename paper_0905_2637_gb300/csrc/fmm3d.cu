@@ -122,9 +122,10 @@ template <typename V> __device__ __forceinline__ void cmac_conj(V &acc, V a, V b
 
 // ---------------------------------------------------------------------------
 // Binning (Sec. 2.1 in 3D): t = x - x0; s = t 2^L / W; floor, clamped; FP64
-// with round-to-nearest intrinsics (no contraction).  recu (mixed path): the
-// record (xi, eta, zeta, q) in input order, each coordinate rounded to FP32
-// and held below 0.5 - 2^-24.  The cap moves a point by at most one FP32
+// with round-to-nearest intrinsics (no contraction), through an FP32
+// shortcut with the same result.  recu (mixed path): the record (xi, eta,
+// zeta, q) in input order, each coordinate rounded to FP32 and held below
+// 0.5 - 2^-24.  The cap moves a point by at most one FP32
 // rounding and keeps two particles of adjacent leaves apart by at least
 // 2^-24 leaf widths along the axis they differ in, so |d| = 0 in the near
 // field can only come from the target's own leaf.
@@ -133,6 +134,9 @@ constexpr float REC_MAX = 0.5f - 0x1p-24f;
 
 struct Dom3 {
     double x0, y0, z0, width, scale;  // scale = 2^L / width
+    // float-float copies (x0 = x0h + x0l, ..., scale = sh + sl) for the FP32
+    // binning shortcut and the records
+    float x0h, x0l, y0h, y0l, z0h, z0l, sh, sl;
 };
 
 __device__ __forceinline__ uint32_t bin3(double v, double v0, double scale, uint32_t nb) {
@@ -140,6 +144,51 @@ __device__ __forceinline__ uint32_t bin3(double v, double v0, double scale, uint
     if (!(f >= 0.0)) return 0u;
     if (f > double(nb - 1)) return nb - 1;
     return uint32_t(f);
+}
+
+// FP32 shortcut of bin3 (FP64 arithmetic is slow here), bit-identical: with
+// xf, x0f, scalef the FP32 roundings of v, v0, scale, s32 = fl(fl(xf - x0f)
+// scalef) is within 4 u scale (|v| + |v0|) (u = 2^-24, plus O(u^2)) of the
+// FP64 s, and m = 2^-21 scale (|v| + |v0|) covers that and the roundings of
+// s32 -/+ m.  Both ends of [s32 - m, s32 + m] in one bin inside
+// (0, nb (1 - 2^-20)) put s in that bin, unclamped, and v inside the domain
+// (s > 0: v > v0; s < nb (1 - 2^-20): v <= fl(v0 + W) while |v0 + W| <=
+// 2^32 W, and a domain farther out makes m > nb, failing the test);
+// otherwise (a bin edge, the boundary, NaN, Inf) false: the FP64 path.
+__device__ __forceinline__ bool bin3_fast(float xf, float x0f, float scalef, uint32_t nb,
+                                          uint32_t *bin) {
+    const float sv = __fmul_rn(__fsub_rn(xf, x0f), scalef);
+    const float m = __fmul_rn(__fmul_rn(__fadd_rn(fabsf(xf), fabsf(x0f)), scalef), 0x1p-21f);
+    const float lo = __fsub_rn(sv, m), hi = __fadd_rn(sv, m);
+    if (!(lo > 0.0f && hi < float(nb) * (1.0f - 0x1p-20f))) return false;
+    const float f = floorf(lo);
+    if (f != floorf(hi)) return false;
+    *bin = uint32_t(f);
+    return true;
+}
+
+// The record coordinate (v - v0) scale - (i + 1/2) in float-float
+// arithmetic (two-sum for the difference, FMA for the product's error
+// terms): before its final rounding within about 2^-44 of the exact value,
+// relative to (v - v0) scale.
+__device__ __forceinline__ void ff_split(float v, float *h, float *l) { *h = v; *l = 0.f; }
+__device__ __forceinline__ void ff_split(double v, float *h, float *l) {
+    *h = float(v);
+    *l = float(v - double(*h));
+}
+template <typename TIn>
+__device__ __forceinline__ float rec3_coord(TIn v, float v0h, float v0l, float sh, float sl,
+                                            uint32_t i) {
+    float vh, vl;
+    ff_split(v, &vh, &vl);
+    const float th = __fsub_rn(vh, v0h);
+    const float bv = __fsub_rn(th, vh);
+    float tl = __fadd_rn(__fsub_rn(vh, __fsub_rn(th, bv)), __fsub_rn(-v0h, bv));
+    tl = __fadd_rn(tl, __fsub_rn(vl, v0l));
+    const float ph = __fmul_rn(th, sh);
+    float pe = __fmaf_rn(th, sh, -ph);
+    pe = __fmaf_rn(th, sl, __fmaf_rn(tl, sh, pe));
+    return __fadd_rn(__fsub_rn(ph, __fadd_rn(float(i), 0.5f)), pe);
 }
 
 template <typename TIn>
@@ -150,23 +199,26 @@ __global__ void __launch_bounds__(256) k3_bin(int64_t n, const TIn *__restrict__
                                               float4 *__restrict__ recu, int *status) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    const double X = double(x[j]), Y = double(y[j]), Z = double(z[j]);
-    const double x1 = __dadd_rn(d.x0, d.width), y1 = __dadd_rn(d.y0, d.width),
-                 z1 = __dadd_rn(d.z0, d.width);
-    if (!(X >= d.x0 && X <= x1 && Y >= d.y0 && Y <= y1 && Z >= d.z0 && Z <= z1))
-        set_status(status, ST_EDOMAIN);
+    const TIn xv = x[j], yv = y[j], zv = z[j];
     const uint32_t nb = 1u << L;
-    const uint32_t ix = bin3(X, d.x0, d.scale, nb), iy = bin3(Y, d.y0, d.scale, nb),
-                   iz = bin3(Z, d.z0, d.scale, nb);
+    uint32_t ix, iy, iz;
+    if (!(bin3_fast(float(xv), d.x0h, d.sh, nb, &ix) && bin3_fast(float(yv), d.y0h, d.sh, nb, &iy) &&
+          bin3_fast(float(zv), d.z0h, d.sh, nb, &iz))) {
+        const double X = double(xv), Y = double(yv), Z = double(zv);
+        const double x1 = __dadd_rn(d.x0, d.width), y1 = __dadd_rn(d.y0, d.width),
+                     z1 = __dadd_rn(d.z0, d.width);
+        if (!(X >= d.x0 && X <= x1 && Y >= d.y0 && Y <= y1 && Z >= d.z0 && Z <= z1))
+            set_status(status, ST_EDOMAIN);
+        ix = bin3(X, d.x0, d.scale, nb);
+        iy = bin3(Y, d.y0, d.scale, nb);
+        iz = bin3(Z, d.z0, d.scale, nb);
+    }
     keys[j] = morton3(ix, iy, iz);
     if (recu) {
         float4 r;
-        r.x = fminf(float(__dsub_rn(__dmul_rn(__dsub_rn(X, d.x0), d.scale), double(ix) + 0.5)),
-                    REC_MAX);
-        r.y = fminf(float(__dsub_rn(__dmul_rn(__dsub_rn(Y, d.y0), d.scale), double(iy) + 0.5)),
-                    REC_MAX);
-        r.z = fminf(float(__dsub_rn(__dmul_rn(__dsub_rn(Z, d.z0), d.scale), double(iz) + 0.5)),
-                    REC_MAX);
+        r.x = fminf(rec3_coord(xv, d.x0h, d.x0l, d.sh, d.sl, ix), REC_MAX);
+        r.y = fminf(rec3_coord(yv, d.y0h, d.y0l, d.sh, d.sl, iy), REC_MAX);
+        r.z = fminf(rec3_coord(zv, d.z0h, d.z0l, d.sh, d.sl, iz), REC_MAX);
         r.w = float(q[j]);
         recu[j] = r;
     }
@@ -1569,6 +1621,24 @@ int upload_tables(petfmm3d_ctx *c) {
     return PETFMM_OK;
 }
 
+Dom3 make_dom3(const petfmm_domain3d &dom, int L) {
+    Dom3 d{};
+    d.x0 = dom.x0;
+    d.y0 = dom.y0;
+    d.z0 = dom.z0;
+    d.width = dom.width;
+    d.scale = std::ldexp(1.0, L) / dom.width;
+    d.x0h = float(d.x0);
+    d.x0l = float(d.x0 - double(d.x0h));
+    d.y0h = float(d.y0);
+    d.y0l = float(d.y0 - double(d.y0h));
+    d.z0h = float(d.z0);
+    d.z0l = float(d.z0 - double(d.z0h));
+    d.sh = float(d.scale);
+    d.sl = float(d.scale - double(d.sh));
+    return d;
+}
+
 void mark3(petfmm3d_ctx *c, int s) {
     if (c->timing) cudaEventRecord(c->ev[s], c->stream);
 }
@@ -1630,7 +1700,7 @@ int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
     const bool f32 = sizeof(T) == 4;
     const V *rtab = static_cast<const V *>(f32 ? c->rtab32.p : c->rtab64.p);
     const V *itab = static_cast<const V *>(f32 ? c->itab32.p : c->itab64.p);
-    const Dom3 d{c->dom.x0, c->dom.y0, c->dom.z0, c->dom.width, std::ldexp(1.0, L) / c->dom.width};
+    const Dom3 d = make_dom3(c->dom, L);
     mark3(c, PETFMM3D_STAGE_P2M);
     if constexpr (sizeof(T) == 4)
         k3_p2m<T, float4><<<grid_w(int64_t(1) << (3 * L)), W3 * 32, 0, st>>>(
@@ -1719,7 +1789,7 @@ int evaluate3(petfmm3d_ctx *c, int64_t n, const void *x, const void *y, const vo
     uint32_t *vA = static_cast<uint32_t *>(c->valsA.p), *vB = static_cast<uint32_t *>(c->valsB.p);
     uint32_t *start = static_cast<uint32_t *>(c->start.p);
     int *status = static_cast<int *>(c->status.p);
-    const Dom3 d{c->dom.x0, c->dom.y0, c->dom.z0, c->dom.width, std::ldexp(1.0, L) / c->dom.width};
+    const Dom3 d = make_dom3(c->dom, L);
     const unsigned gp = unsigned((n + 255) / 256);
     float4 *recu = mixed ? static_cast<float4 *>(c->recu.p) : nullptr;
 

@@ -86,6 +86,11 @@ def test_fp64_path_matches_oracle_fmm(orc, case, dtype):
     dict(n=20000, seed=10, L=3, p=8),
     dict(n=30000, seed=11, L=4, p=12, clustered_frac=0.5),
     dict(n=20000, seed=12, L=4, p=16, clustered_frac=0.2),
+    # small orders: real M2M / L2L with partly filled lanes, odd coefficient
+    # counts in the pipelined M2L's row copies (p = 5: 15 complex)
+    dict(n=15000, seed=21, L=3, p=3),
+    dict(n=20000, seed=22, L=4, p=5, clustered_frac=0.4),
+    dict(n=40000, seed=23, L=5, p=7, clustered_frac=0.3),
 ])
 def test_mixed_path_within_fp32_budget_of_fp64(orc, case):
     # FP32 arithmetic (relative rounding 6e-8 per operation) over sums of a
