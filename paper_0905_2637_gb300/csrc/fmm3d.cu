@@ -357,6 +357,117 @@ __global__ void __launch_bounds__(W3 * 32) k3_p2m(int L, int p, Dom3 d, const ui
     }
 }
 
+// P2M of the mixed path for p <= 8: a warp per leaf with a lane per charge
+// (charges j, j + 32, ... of the leaf), each lane computing all p (p + 1) / 2
+// terms q R_n^m column by column with compile-time constants and summing
+// them over its charges; then a reduce-scatter across the warp (three
+// halving exchanges, offsets 16, 8, 4, then a butterfly over offsets 2 and
+// 1) leaves each group of four lanes the full sums of a ninth of the 2 NC
+// values, which one lane of the group writes.
+template <int P>
+__global__ void __launch_bounds__(W3 * 32) k3_p2m_lanes(int L, const uint32_t *__restrict__ start,
+                                                        const float4 *__restrict__ rec,
+                                                        float2 *__restrict__ me) {
+    constexpr int NC = P * (P + 1) / 2, NV = 2 * NC;  // values: Re of all, then Im of all
+    constexpr int NV8 = (NV + 7) / 8, NVP = 8 * NV8;  // padded to eight equal parts
+    const int lane = threadIdx.x & 31;
+    const int64_t b = int64_t(blockIdx.x) * W3 + (threadIdx.x >> 5);
+    if (b >= (int64_t(1) << (3 * L))) return;
+    const uint32_t s0 = start[b], s1 = start[b + 1];
+    if (s0 == s1) return;
+    float v[NVP];
+#pragma unroll
+    for (int k = 0; k < NVP; ++k) v[k] = 0.f;
+    for (uint32_t j = s0 + uint32_t(lane); j < s1; j += 32u) {
+        const float4 a = rec[j];
+        const float r2 = a.x * a.x + a.y * a.y + a.z * a.z;
+        float pr = a.w, pi = 0.f;  // q R_m^m
+#pragma unroll
+        for (int m = 0; m < P; ++m) {
+            if (m > 0) {
+                const float sc = 1.f / float(2 * m);
+                const float tr = (pr * a.x - pi * a.y) * sc, ti = (pr * a.y + pi * a.x) * sc;
+                pr = tr;
+                pi = ti;
+            }
+            float r1r = pr, r1i = pi, r0r = 0.f, r0i = 0.f;
+            v[m * (m + 1) / 2 + m] += r1r;
+            v[NC + m * (m + 1) / 2 + m] += r1i;
+#pragma unroll
+            for (int n = m + 1; n < P; ++n) {
+                const float c1 = float(2 * n - 1) * a.z;
+                const float inv = 1.f / float(n * n - m * m);
+                const float rr = (c1 * r1r - r2 * r0r) * inv, ri = (c1 * r1i - r2 * r0i) * inv;
+                r0r = r1r;
+                r0i = r1i;
+                r1r = rr;
+                r1i = ri;
+                v[n * (n + 1) / 2 + m] += rr;
+                v[NC + n * (n + 1) / 2 + m] += ri;
+            }
+        }
+    }
+    // halving exchanges: at offset o the lane keeps the lower half of its
+    // values if (lane & o) == 0, else the upper half, adding the partner's
+    // copy of the half it keeps
+#pragma unroll
+    for (int k = 0; k < NVP / 2; ++k) {
+        const bool up = lane & 16;
+        const float send = up ? v[k] : v[k + NVP / 2];
+        const float keep = up ? v[k + NVP / 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < NVP / 4; ++k) {
+        const bool up = lane & 8;
+        const float send = up ? v[k] : v[k + NVP / 4];
+        const float keep = up ? v[k + NVP / 4] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int k = 0; k < NV8; ++k) {
+        const bool up = lane & 4;
+        const float send = up ? v[k] : v[k + NV8];
+        const float keep = up ? v[k + NV8] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+#pragma unroll
+    for (int k = 0; k < NV8; ++k) {
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 2);
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1);
+    }
+    // this group's values: index 4 NVP/8 bit4 + 2 NVP/8 bit3 + NVP/8 bit2 + k
+    if ((lane & 3) == 0) {
+        const int base = NV8 * (4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1));
+        float *dst = reinterpret_cast<float *>(me + (lvl_off3(L) + b) * NC);
+#pragma unroll
+        for (int k = 0; k < NV8; ++k) {
+            const int vi = base + k;
+            if (vi < NC)
+                dst[2 * vi] = v[k];
+            else if (vi < NV)
+                dst[2 * (vi - NC) + 1] = -v[k];  // conj
+        }
+    }
+}
+
+template <int P>
+cudaError_t p2m_lanes_p(int L, const uint32_t *start, const float4 *rec, float2 *me, cudaStream_t st) {
+    k3_p2m_lanes<P><<<unsigned(((int64_t(1) << (3 * L)) + W3 - 1) / W3), W3 * 32, 0, st>>>(L, start,
+                                                                                          rec, me);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2m_lanes(int p, int L, const uint32_t *start, const float4 *rec, float2 *me,
+                             cudaStream_t st) {
+    switch (p) {
+#define PL_CASE(P) case P: return p2m_lanes_p<P>(L, start, rec, me, st);
+        PL_CASE(1) PL_CASE(2) PL_CASE(3) PL_CASE(4) PL_CASE(5) PL_CASE(6) PL_CASE(7) PL_CASE(8)
+#undef PL_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // M2M (parent level l from level l + 1): M~'_n^m = sum_children sum_{k,l}
 // conj(R_k^l(e_c)) 2^-(n-k) M~_{n-k}^{m-l}.  A warp per parent box, lanes over
@@ -1702,10 +1813,13 @@ int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
     const V *itab = static_cast<const V *>(f32 ? c->itab32.p : c->itab64.p);
     const Dom3 d = make_dom3(c->dom, L);
     mark3(c, PETFMM3D_STAGE_P2M);
-    if constexpr (sizeof(T) == 4)
-        k3_p2m<T, float4><<<grid_w(int64_t(1) << (3 * L)), W3 * 32, 0, st>>>(
-            L, p, d, start, static_cast<const float4 *>(c->rec.p), me);
-    else
+    if constexpr (sizeof(T) == 4) {
+        if (p <= 8)
+            P3_CUDA(launch_p2m_lanes(p, L, start, static_cast<const float4 *>(c->rec.p), me, st));
+        else
+            k3_p2m<T, float4><<<grid_w(int64_t(1) << (3 * L)), W3 * 32, 0, st>>>(
+                L, p, d, start, static_cast<const float4 *>(c->rec.p), me);
+    } else
         k3_p2m<T, Dbl4><<<grid_w(int64_t(1) << (3 * L)), W3 * 32, 0, st>>>(
             L, p, d, start, static_cast<const Dbl4 *>(c->xs.p), me);
     P3_CUDA(cudaGetLastError());
