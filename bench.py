@@ -252,9 +252,9 @@ def cpu_baseline():
     oracle.direct(wl.x, wl.y, wl.gamma, wl.sigma, targets=tg)
     dt1 = time.perf_counter() - t1
     pairs = tg.size * (wl.n - 1)
-    # the 3D extension: the oracle's octree FMM on 2^15 charges of the
-    # uniform3d recipe at L = 3 (64 charges per leaf, as uniform3d-2M at L = 5)
-    w3 = W.uniform3d(n=1 << 15, L=3, dtype="f64", name="uniform3d-32k")
+    # the 3D extension: the oracle's octree FMM on 2^18 charges of the
+    # uniform3d recipe at L = 4 (64 charges per leaf, as uniform3d-2M at L = 5)
+    w3 = W.uniform3d(n=1 << 18, L=4, dtype="f64", name="uniform3d-262k")
     t2 = time.perf_counter()
     oracle.fmm3d(*w3.as_f64(), w3.domain, w3.L, w3.p)
     dt2 = time.perf_counter() - t2
