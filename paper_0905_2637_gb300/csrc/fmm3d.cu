@@ -1337,21 +1337,24 @@ __global__ void __launch_bounds__(W3 * 32, 4) k3_near_mixed(int L, int p, double
                     gy = fmaf(qr3, ddy, gy);
                     gz = fmaf(qr3, ddz, gz);
                 };
-                // full items (rep = 1) on the plain loop: the strided one
-                // measured slower there
+                // full items (rep = 1) on the plain loop (the strided one
+                // measured slower there), both unrolled eight / two deep
                 const bool own = dx == 0 && dy == 0 && dz == 0;
                 if (rep == 1u) {
                     if (own)
                         for (uint32_t j = a; j < e; ++j) pair(rec[j], true);
-                    else
+                    else {
+#pragma unroll 8
                         for (uint32_t j = a; j < e; ++j) pair(rec[j], false);
+                    }
                 } else {
-                    const float4 *sp = rec + a + c;
-                    const int cnt = a + c < e ? int((e - a - c + rep - 1u) >> lg) : 0;
+                    const float4 *sp = rec + a + c, *se = rec + e;
                     if (own)
-                        for (int t = 0; t < cnt; ++t) pair(sp[size_t(t) * rep], true);
-                    else
-                        for (int t = 0; t < cnt; ++t) pair(sp[size_t(t) * rep], false);
+                        for (; sp < se; sp += rep) pair(*sp, true);
+                    else {
+#pragma unroll 2
+                        for (; sp < se; sp += rep) pair(*sp, false);
+                    }
                 }
             }
     for (uint32_t o = 1; o < rep; o <<= 1) {
