@@ -323,7 +323,11 @@ void launch_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
     rd.t1 = Clock::now();
 }
 
-void complete_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
+// Requests a round finished, with their statuses: the worker completes them
+// (copies back, frees) once the next round is on the GPU.
+using Finished = std::vector<std::pair<Req *, int>>;
+
+void complete_round(petfmm_server *s, std::vector<Req *> &act, Round &rd, Finished &fin) {
     const int rc64 = rd.rc64, rcmx = rd.rcmx;
     const Clock::time_point t0 = rd.t0, t1 = Clock::now();
     int st64 = rd.any64 ? petfmm_sync(s->ctx64) : 0;
@@ -332,7 +336,8 @@ void complete_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
     const Clock::time_point t2 = Clock::now();
     // A finished request belongs to the caller from the moment finish() marks
     // it done (a poll may release it at once), so it is dropped from the
-    // active list here and never touched again.
+    // active list here, handed to the worker through fin, and never touched
+    // by a round again.
     std::vector<Req *> keep;
     keep.reserve(act.size());
     for (size_t i = 0; i < act.size(); ++i) {
@@ -342,19 +347,19 @@ void complete_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
         if (e != cudaSuccess) st = PETFMM_ECUDA;
         r->evals_done++;
         if (st != PETFMM_OK) {
-            finish(s, r, st);
+            fin.emplace_back(r, st);
             continue;
         }
         if (r->spec.n > 0 && !inside(r->dom, s->hbox + 4 * i)) {
             const double *b = s->hbox + 4 * i;
             if (!(std::isfinite(b[0]) && std::isfinite(b[1]) && std::isfinite(b[2]) && std::isfinite(b[3]))) {
-                finish(s, r, PETFMM_EDOMAIN);
+                fin.emplace_back(r, PETFMM_EDOMAIN);
                 continue;
             }
             r->dom = fit_domain(b[0], b[1], b[2], b[3]);
         }
         if (r->evals_done >= 2 * r->spec.n_steps) {
-            finish(s, r, PETFMM_OK);
+            fin.emplace_back(r, PETFMM_OK);
             continue;
         }
         keep.push_back(r);
@@ -371,7 +376,19 @@ void complete_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
 void worker_main(petfmm_server *s) {
     cudaSetDevice(s->device);
     std::vector<Req *> act;
+    // completions of the last round: their copies back to the host (which
+    // block this thread) run while the next round computes
+    Finished fin;
+    auto complete = [&]() {
+        if (fin.empty()) return;
+        const Clock::time_point tf = Clock::now();
+        for (auto &f : fin) finish(s, f.first, f.second);
+        fin.clear();
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->post_ms += std::chrono::duration<double, std::milli>(Clock::now() - tf).count();
+    };
     for (;;) {
+        if (act.empty()) complete();  // no round to overlap them with
         std::vector<Req *> newly;
         {
             std::unique_lock<std::mutex> lk(s->mu);
@@ -399,6 +416,7 @@ void worker_main(petfmm_server *s) {
         // computes, and join the next round
         Round rd;
         if (!act.empty()) launch_round(s, act, rd);
+        complete();
         const Clock::time_point ta = Clock::now();
         std::vector<Req *> joined;
         for (Req *r : newly) {
@@ -422,7 +440,7 @@ void worker_main(petfmm_server *s) {
             std::lock_guard<std::mutex> lk(s->mu);
             s->admit_ms += std::chrono::duration<double, std::milli>(Clock::now() - ta).count();
         }
-        if (!act.empty()) complete_round(s, act, rd);
+        if (!act.empty()) complete_round(s, act, rd, fin);
         act.insert(act.end(), joined.begin(), joined.end());
     }
 }
