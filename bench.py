@@ -361,7 +361,8 @@ def serving_leg(_lib, n_req=2000, seed=5, pool=96):
             "particles_per_s": evals / makespan,
             "offered_particle_evals_per_s": evals / max(float(np.sum(gaps)), 1e-9),
             "rounds": int(st["rounds"]), "max_resident": int(st["max_active"]),
-            "mean_resident": float(st["mean_active"]), "gpu_busy_frac": st["busy_ms"] / st["up_ms"],
+            "mean_resident": float(st["mean_active"]), "gpu_busy_frac": st["gpu_ms"] / st["up_ms"],
+            "worker_busy_frac": st["busy_ms"] / st["up_ms"],
             "scheduler_ms": {k: round(st[k], 1) for k in ("admit_ms", "launch_ms", "wait_ms",
                                                           "post_ms", "up_ms")},
             "requests_batched_with_others": int((shared >= 2).sum()),

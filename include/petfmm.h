@@ -336,12 +336,16 @@ typedef struct {
     int32_t queued;       /* requests waiting now */
     int32_t max_active;   /* most requests resident in one round */
     double mean_active;   /* mean requests resident per round */
-    double busy_ms;       /* time spent in rounds */
+    double busy_ms;       /* scheduler-thread time spent in rounds */
     double up_ms;         /* time since petfmm_serve_create */
     /* scheduler-thread time by phase: admitting requests (device state,
      * copies in), launching rounds, waiting for the GPU, and the work after
      * a round (statuses, refitted domains, finished requests copied out) */
     double admit_ms, launch_ms, wait_ms, post_ms;
+    double gpu_ms;        /* device time of the rounds: CUDA events on the
+                             server's stream around each round's work (from
+                             its start, after the admitted copies, to the
+                             copy of its bounding boxes) */
 } petfmm_serve_counters;
 int petfmm_serve_stats(petfmm_server *s, petfmm_serve_counters *out);
 /* Per-round trace: for the first min(cap, count) rounds since creation, the

@@ -66,7 +66,7 @@ class ServeStats(ctypes.Structure):
                 ("mean_active", ctypes.c_double), ("busy_ms", ctypes.c_double),
                 ("up_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
                 ("launch_ms", ctypes.c_double), ("wait_ms", ctypes.c_double),
-                ("post_ms", ctypes.c_double)]
+                ("post_ms", ctypes.c_double), ("gpu_ms", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

@@ -147,6 +147,9 @@ struct petfmm_server {
     cudaStream_t cstream = nullptr;
     cudaEvent_t ev_copy = nullptr;
     bool copies_pending = false;
+    // timing events around each round's work on the stream (device time)
+    cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;
+    double gpu_ms = 0.0;
     // counters (under mu)
     Clock::time_point t_create;
     uint64_t rounds = 0, submitted = 0, admitted = 0, completed = 0;
@@ -269,6 +272,7 @@ void launch_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
         cudaStreamWaitEvent(s->stream, s->ev_copy, 0);
         s->copies_pending = false;
     }
+    cudaEventRecord(s->ev_r0, s->stream);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->rounds++;
@@ -320,6 +324,7 @@ void launch_round(petfmm_server *s, std::vector<Req *> &act, Round &rd) {
     if (!act.empty())
         k_bbox_final<<<unsigned(act.size()), 32, 0, s->stream>>>(dpart, s->dbox);
     cudaMemcpyAsync(s->hbox, s->dbox, act.size() * 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    cudaEventRecord(s->ev_r1, s->stream);
     rd.t1 = Clock::now();
 }
 
@@ -334,6 +339,11 @@ void complete_round(petfmm_server *s, std::vector<Req *> &act, Round &rd, Finish
     int stmx = rd.anymx ? petfmm_sync(s->ctxmx) : 0;
     cudaError_t e = cudaStreamSynchronize(s->stream);
     const Clock::time_point t2 = Clock::now();
+    float round_ms = 0.f;
+    if (e == cudaSuccess && cudaEventElapsedTime(&round_ms, s->ev_r0, s->ev_r1) != cudaSuccess) {
+        cudaGetLastError();
+        round_ms = 0.f;
+    }
     // A finished request belongs to the caller from the moment finish() marks
     // it done (a poll may release it at once), so it is dropped from the
     // active list here, handed to the worker through fin, and never touched
@@ -368,6 +378,7 @@ void complete_round(petfmm_server *s, std::vector<Req *> &act, Round &rd, Finish
     const Clock::time_point t3 = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     s->busy_ms += std::chrono::duration<double, std::milli>(t3 - t0).count();
+    s->gpu_ms += round_ms;
     s->launch_ms += std::chrono::duration<double, std::milli>(rd.t1 - t0).count();
     s->wait_ms += std::chrono::duration<double, std::milli>(t2 - t1).count();
     s->post_ms += std::chrono::duration<double, std::milli>(t3 - t2).count();
@@ -466,8 +477,11 @@ int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, p
     if (cudaGetDevice(&s->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev_copy, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&s->ev_copy, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&s->ev_r0) != cudaSuccess || cudaEventCreate(&s->ev_r1) != cudaSuccess) {
         cudaGetLastError();
+        if (s->ev_r1) cudaEventDestroy(s->ev_r1);
+        if (s->ev_r0) cudaEventDestroy(s->ev_r0);
         if (s->ev_copy) cudaEventDestroy(s->ev_copy);
         if (s->cstream) cudaStreamDestroy(s->cstream);
         if (s->stream) cudaStreamDestroy(s->stream);
@@ -484,6 +498,8 @@ int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, p
             cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
             cudaGetLastError();
             if (s->pool) cudaMemPoolDestroy(s->pool);
+            cudaEventDestroy(s->ev_r0);
+            cudaEventDestroy(s->ev_r1);
             cudaEventDestroy(s->ev_copy);
             cudaStreamDestroy(s->cstream);
             cudaStreamDestroy(s->stream);
@@ -498,6 +514,8 @@ int petfmm_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, p
     if (rc != PETFMM_OK) {
         if (s->ctx64) petfmm_destroy(s->ctx64);
         cudaMemPoolDestroy(s->pool);
+        cudaEventDestroy(s->ev_r0);
+        cudaEventDestroy(s->ev_r1);
         cudaEventDestroy(s->ev_copy);
         cudaStreamDestroy(s->cstream);
         cudaStreamDestroy(s->stream);
@@ -614,6 +632,7 @@ int petfmm_serve_stats(petfmm_server *s, petfmm_serve_counters *out) {
     out->max_active = s->max_active;
     out->mean_active = s->rounds ? s->sum_active / double(s->rounds) : 0.0;
     out->busy_ms = s->busy_ms;
+    out->gpu_ms = s->gpu_ms;
     out->admit_ms = s->admit_ms;
     out->launch_ms = s->launch_ms;
     out->wait_ms = s->wait_ms;
@@ -650,6 +669,8 @@ int petfmm_serve_destroy(petfmm_server *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->pool) cudaMemPoolDestroy(s->pool);
     if (s->ev_copy) cudaEventDestroy(s->ev_copy);
+    if (s->ev_r0) cudaEventDestroy(s->ev_r0);
+    if (s->ev_r1) cudaEventDestroy(s->ev_r1);
     if (s->cstream) cudaStreamDestroy(s->cstream);
     if (s->ctx64) petfmm_destroy(s->ctx64);
     if (s->ctxmx) petfmm_destroy(s->ctxmx);
