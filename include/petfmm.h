@@ -678,7 +678,12 @@ int petfmm3d_evaluate(petfmm3d_ctx *ctx, int64_t n, const void *x, const void *y
 /* Waits for the stream; returns the device status of the last evaluation
  * (PETFMM_OK or PETFMM_EDOMAIN) or PETFMM_ECUDA. */
 int petfmm3d_sync(petfmm3d_ctx *ctx);
-enum { PETFMM3D_OPT_TIMING = 1 /* 1: record CUDA events per stage */ };
+enum {
+    PETFMM3D_OPT_TIMING = 1, /* 1: record CUDA events per stage */
+    PETFMM3D_OPT_M2L_TC = 2  /* mixed path, p <= 8: 1 run M2L on the tensor cores
+                                (tcgen05, TF32 hi/lo split, FP32 accumulation);
+                                0 (default) the SIMT GEMM kernel */
+};
 int petfmm3d_set_option(petfmm3d_ctx *ctx, int option, int64_t value);
 enum {
     PETFMM3D_STAGE_BIN = 0, PETFMM3D_STAGE_SORT, PETFMM3D_STAGE_GATHER, PETFMM3D_STAGE_P2M,

@@ -45,6 +45,7 @@
 
 #include "../../include/petfmm.h"
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 using namespace petfmm;
 
@@ -780,10 +781,6 @@ __device__ __forceinline__ void cp_async_z(void *dst, const void *src, int bytes
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
 
 template <int P, int R>
 constexpr size_t mgp_smem_bytes() {
@@ -1007,6 +1004,289 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
                 if (imr[jj] == r) lef[(box * NC + jj) * 2 + 1] = acc[i][j];
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// M2L of the mixed path on the 5th-generation tensor cores (p <= 8): the
+// same real GEMMs as k3_m2l_pipe with TF32 inputs split into hi and lo
+// parts, each rounded to TF32 (a_hi = a to nearest, a_lo = a - a_hi to
+// nearest: a - a_hi - a_lo is within about 2^-23 |a|, near an FP32
+// rounding; the products a_hi b_hi + a_lo b_hi + a_hi b_lo leave out
+// a_lo b_lo, about 2^-24) and FP32 accumulation in tensor memory, spread
+// over TC3_SETS accumulator sets that consecutive pairs take in turn and
+// that the epilogue adds in registers: each set's chain of MMA additions is
+// a quarter as long.  (With one set the potential of a 20k-charge test
+// drifted 1.2e-5 from the FP64 path, past the mixed path's 1e-5 budget,
+// whether the split truncated or rounded: the error grows with the length
+// of the accumulation chain, some 4,500 MMA steps per output here.)  A CTA takes the 128
+// Morton-consecutive parent cells of a pipelined-M2L block and two target
+// classes c0, c0 + 1: M = 128 rows (TMEM lanes), 2 x NRP accumulator
+// columns.  For each (source class cs, parent offset d) pair in a fixed
+// order whose operator is not near for one of the two classes and whose
+// sources are not all empty, the 128 source rows (the expansion of box
+// (P + d) 8 + cs in the real basis, zero for an empty or outside box) are
+// split into hi and lo images in shared memory, K-major without swizzle
+// (core matrices of 8 rows x 16 bytes: element (m, k) at
+// ((k / 4) 128 + m) 16 + (k mod 4) 4 bytes), the two classes' operator
+// images (host-built in the same layout, B(n, k) = A_delta[k][n]) are copied
+// beside them, and one thread issues the MMAs and commits them to an
+// mbarrier that the next pair waits on (bounded) before it overwrites the
+// images.  A wait that gives up sets PETFMM_ETIMEOUT and the CTA writes
+// nothing.
+// ---------------------------------------------------------------------------
+constexpr int TC3_THREADS = 128;  // one thread per row (and TMEM lane)
+constexpr int TC3_ROWS = 128;
+constexpr int TC3_SETS = 4;       // accumulator sets
+
+// coefficient index n (n + 1) / 2 + m of the t-th coefficient with m > 0
+template <int P> __host__ __device__ constexpr int tc3_imcoef(int t) {
+    int r = 0;
+    for (int n = 1; n < P; ++n)
+        for (int m = 1; m <= n; ++m) {
+            if (r == t) return n * (n + 1) / 2 + m;
+            ++r;
+        }
+    return 0;
+}
+
+// v rounded to TF32 (nearest, ties away), in FP32 format
+__device__ __forceinline__ float tf32_rna(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+template <int P> constexpr size_t tc3_smem_bytes() {
+    // A hi and lo (128 x NRP each), then two classes' B hi and lo (NRP x NRP)
+    return size_t(2 * TC3_ROWS * mg_nrp(P) + 4 * mg_nrp(P) * mg_nrp(P)) * sizeof(float);
+}
+
+// blocks of level l in the all-levels launch: 128 parent cells x 4 class pairs
+__host__ __device__ __forceinline__ int64_t tc3_blocks(int l) {
+    return ((int64_t(1) << (3 * (l - 1))) + TC3_ROWS - 1) / TC3_ROWS * 4;
+}
+
+template <int P>
+__global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_t *__restrict__ start,
+                                                          const float *__restrict__ bimg,
+                                                          const float2 *__restrict__ me,
+                                                          float2 *__restrict__ le,
+                                                          long long spin_limit, int *status) {
+    constexpr int NC = P * (P + 1) / 2, NR = P * P, NRP = mg_nrp(P), KG = NRP / 4;
+    static_assert(NRP <= 64 && NRP % 16 == 0, "tensor-core M2L orders");
+    constexpr int HX = 10, HY = 6, HZ = 6;  // the block's 8 x 4 x 4 parent cells and one of halo
+    extern __shared__ __align__(1024) float tsm[];
+    float *ahi = tsm, *alo = ahi + TC3_ROWS * NRP;  // [KG][128][4]
+    float *bsm = alo + TC3_ROWS * NRP;              // [class][hi, lo][KG][NRP][4]
+    __shared__ unsigned char hocc[HX * HY * HZ];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    __shared__ uint32_t set_used;  // bit 2 set + class: that accumulator was written
+    int l = 2;
+    int64_t bid = blockIdx.x;
+    while (l < L && bid >= tc3_blocks(l)) bid -= tc3_blocks(l++);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int c0 = 2 * int(bid & 3);
+    const int64_t np = int64_t(1) << (3 * (l - 1));
+    const int64_t p0 = (bid >> 2) * TC3_ROWS;
+    const int pside = 1 << (l - 1);
+    const int hx0 = int(compact3(uint32_t(p0))) - 1, hy0 = int(compact3(uint32_t(p0) >> 1)) - 1,
+              hz0 = int(compact3(uint32_t(p0) >> 2)) - 1;
+    for (int h = tid; h < HX * HY * HZ; h += TC3_THREADS) {
+        const int qx = hx0 + h % HX, qy = hy0 + (h / HX) % HY, qz = hz0 + h / (HX * HY);
+        unsigned bits = 0;
+        if (qx >= 0 && qy >= 0 && qz >= 0 && qx < pside && qy < pside && qz < pside) {
+            const uint32_t pb = morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz));
+            for (int cs = 0; cs < 8; ++cs)
+                if (box_count3(start, L, l, pb * 8u + uint32_t(cs))) bits |= 1u << cs;
+        }
+        hocc[h] = (unsigned char)bits;
+    }
+    __syncthreads();
+    // this thread's row: parent cell p0 + tid, its halo position
+    const int64_t pc = p0 + tid;
+    const bool row_ok = pc < np;
+    const int rx = int(compact3(uint32_t(pc))), ry = int(compact3(uint32_t(pc) >> 1)),
+              rz = int(compact3(uint32_t(pc) >> 2));
+    const unsigned own = row_ok ? hocc[(rx - hx0) + HX * ((ry - hy0) + HY * (rz - hz0))] : 0u;
+    // nothing to do if the block's targets of both classes are empty
+    if (!__syncthreads_or(int((own >> c0) & 3u))) return;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        set_used = 0;
+    }
+    constexpr uint32_t NCOLS = TC3_SETS * 2 * NRP;  // 256 or 512: a power of two
+    static_assert(NCOLS <= 512, "TMEM columns");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tslot)),
+                     "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = tslot;
+    // kind::tf32: D F32 (bit 4), A and B TF32 (bits 7, 10), both K-major,
+    // N / 8 at bit 17, M / 16 at bit 24
+    constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NRP >> 3) << 17) |
+                               (uint32_t(TC3_ROWS >> 4) << 24);
+    constexpr uint32_t LBO_A = TC3_ROWS * 16, SBO_A = 128, LBO_B = NRP * 16, SBO_B = 128;
+    const float2 *lev = me + lvl_off3(l) * NC;
+    int ncommit = 0;  // commits so far (the same count in every thread)
+    bool ok = true;
+    uint32_t used = 0;  // thread 0: bit 2 set + class, accumulators written
+    for (int o = 0; o < 216 && ok; ++o) {
+        const int cs = o / 27, dd = o % 27;
+        const int dx = dd % 3 - 1, dy = (dd / 3) % 3 - 1, dz = dd / 9 - 1;
+        int slot[2];
+        bool far[2];
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = c0 + cc;
+            const int ex = (c & 1) - (cs & 1) - 2 * dx, ey = ((c >> 1) & 1) - ((cs >> 1) & 1) - 2 * dy,
+                      ez = (c >> 2) - (cs >> 2) - 2 * dz;
+            far[cc] = !(ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1 && ez >= -1 && ez <= 1);
+            slot[cc] = (ex + 3) + 7 * (ey + 3) + 49 * (ez + 3);
+        }
+        if (!far[0] && !far[1]) continue;
+        // this row's source box
+        int sb = -1;
+        if (row_ok) {
+            const int qx = rx + dx, qy = ry + dy, qz = rz + dz;
+            if (qx >= 0 && qy >= 0 && qz >= 0 && qx < pside && qy < pside && qz < pside &&
+                ((hocc[(qx - hx0) + HX * ((qy - hy0) + HY * (qz - hz0))] >> cs) & 1u))
+                sb = int(morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz)) * 8u + uint32_t(cs));
+        }
+        if (!__syncthreads_or(int(sb >= 0))) continue;
+        // the previous pair's MMAs still read the images
+        if (ncommit > 0) {
+            if (tid == 0) ok = mbar_wait(smem_addr(&mbar), uint32_t(ncommit - 1) & 1u, spin_limit);
+            ok = __syncthreads_and(int(tid != 0 || ok)) != 0;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        {
+            // A: the row in the real basis (Re of every coefficient, then Im
+            // of those with m > 0, zero padding to NRP), hi and lo
+            float v[NRP];
+#pragma unroll
+            for (int k = 0; k < NRP; ++k) v[k] = 0.f;
+            if (sb >= 0) {
+                const float2 *src = lev + int64_t(sb) * NC;
+                float2 w[NC];
+#pragma unroll
+                for (int j = 0; j < NC; ++j) w[j] = src[j];
+#pragma unroll
+                for (int j = 0; j < NC; ++j) v[j] = w[j].x;
+#pragma unroll
+                for (int t = 0; t < NR - NC; ++t) v[NC + t] = w[tc3_imcoef<P>(t)].y;
+            }
+#pragma unroll
+            for (int g = 0; g < KG; ++g) {
+                float4 h4, l4;
+                h4.x = tf32_rna(v[4 * g]);
+                h4.y = tf32_rna(v[4 * g + 1]);
+                h4.z = tf32_rna(v[4 * g + 2]);
+                h4.w = tf32_rna(v[4 * g + 3]);
+                l4 = make_float4(tf32_rna(v[4 * g] - h4.x), tf32_rna(v[4 * g + 1] - h4.y),
+                                 tf32_rna(v[4 * g + 2] - h4.z), tf32_rna(v[4 * g + 3] - h4.w));
+                reinterpret_cast<float4 *>(ahi)[g * TC3_ROWS + tid] = h4;
+                reinterpret_cast<float4 *>(alo)[g * TC3_ROWS + tid] = l4;
+            }
+        }
+        // B: the two classes' operator images (hi then lo), where far
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            if (!far[cc]) continue;
+            const float4 *src = reinterpret_cast<const float4 *>(bimg + size_t(slot[cc]) * 2 * NRP * NRP);
+            float4 *dst = reinterpret_cast<float4 *>(bsm + size_t(cc) * 2 * NRP * NRP);
+            for (int i = tid; i < NRP * NRP / 2; i += TC3_THREADS) dst[i] = __ldg(src + i);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint64_t dah = mma_desc(smem_addr(ahi), LBO_A, SBO_A);
+            const uint64_t dal = mma_desc(smem_addr(alo), LBO_A, SBO_A);
+            constexpr uint64_t sa = (2 * LBO_A) >> 4, sbk = (2 * LBO_B) >> 4;
+            const int set = ncommit % TC3_SETS;
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                if (!far[cc]) continue;
+                const uint32_t bh = smem_addr(bsm + size_t(cc) * 2 * NRP * NRP);
+                const uint64_t dbh = mma_desc(bh, LBO_B, SBO_B);
+                const uint64_t dbl = mma_desc(bh + uint32_t(NRP * NRP * 4), LBO_B, SBO_B);
+                const uint32_t dt = tbase + uint32_t((2 * set + cc) * NRP);
+                const uint32_t bit = 1u << (2 * set + cc);
+                const bool was = (used & bit) != 0;
+#pragma unroll
+                for (int ks = 0; ks < NRP / 8; ++ks) {
+                    mma_tf32(dt, dah + ks * sa, dbh + ks * sbk, idesc, (was || ks > 0) ? 1u : 0u);
+                    mma_tf32(dt, dal + ks * sa, dbh + ks * sbk, idesc, 1u);
+                    mma_tf32(dt, dah + ks * sa, dbl + ks * sbk, idesc, 1u);
+                }
+                used |= bit;
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_addr(&mbar)));
+        }
+        ++ncommit;
+    }
+    if (tid == 0) {
+        if (ok && ncommit > 0) ok = mbar_wait(smem_addr(&mbar), uint32_t(ncommit - 1) & 1u, spin_limit);
+        set_used = used;
+        if (!ok) {
+            set_status(status, ST_ETIMEOUT);
+            // the MMAs in flight finish before the memory goes (bounded)
+            if (ncommit > 0) mbar_wait(smem_addr(&mbar), uint32_t(ncommit - 1) & 1u, 1LL << 26);
+        }
+    }
+    ok = __syncthreads_and(int(tid != 0 || ok)) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        float *lef = reinterpret_cast<float *>(le + lvl_off3(l) * NC);
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = c0 + cc;
+            // the sum of the class's accumulator sets, in set order
+            float v[NRP];
+#pragma unroll
+            for (int k = 0; k < NRP; ++k) v[k] = 0.f;
+            for (int set = 0; set < TC3_SETS; ++set) {
+                if (!((set_used >> (2 * set + cc)) & 1u)) continue;  // uniform
+                const uint32_t taddr =
+                    tbase + (uint32_t(warp * 32) << 16) + uint32_t((2 * set + cc) * NRP);
+#pragma unroll
+                for (int q = 0; q < NRP / 16; ++q) {
+                    float t16[16];
+                    tmem_ld16(taddr + uint32_t(16 * q), t16);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[16 * q + i] += t16[i];
+                }
+            }
+            if (row_ok && ((own >> c) & 1u)) {
+                float *dst = lef + (pc * 8 + c) * NC * 2;
+#pragma unroll
+                for (int j = 0; j < NC; ++j) dst[2 * j] = v[j];
+                int t = 0;
+#pragma unroll
+                for (int n = 0; n < P; ++n)
+#pragma unroll
+                    for (int m = 0; m <= n; ++m) {
+                        const int j = n * (n + 1) / 2 + m;
+                        dst[2 * j + 1] = m == 0 ? 0.f : v[NC + t];
+                        t += m > 0 ? 1 : 0;
+                    }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS));
 }
 
 // ---------------------------------------------------------------------------
@@ -1529,6 +1809,17 @@ void host_m2l_real(int p, const cd *iv, double *a) {
         }
 }
 
+// v rounded to TF32 (10 mantissa bits; to nearest, ties away from zero)
+float host_tf32_rna(float v) {
+    uint32_t bits;
+    std::memcpy(&bits, &v, 4);
+    if ((bits & 0x7F800000u) != 0x7F800000u) bits += 0x1000u;  // finite: round the magnitude
+    bits &= 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &bits, 4);
+    return r;
+}
+
 // Coefficient (n, m) of a stored m >= 0 series, m < 0 by symmetry.
 cd host_coef(const cd *a, int n, int m) {
     if (m >= 0) return a[n * (n + 1) / 2 + m];
@@ -1646,6 +1937,8 @@ struct petfmm3d_ctx {
     DevBuf3 ncnt, noff, nscan, nitems;  // the mixed near field's work items
     DevBuf3 rtab32, itab32, rtab64, itab64, atab32, rmap;
     DevBuf3 m2m32, l2l32;  // p <= 8: the real M2M / L2L operators of the 8 octants
+    DevBuf3 tcimg;  // p <= 8: TF32 hi / lo images of the M2L operators (tensor-core M2L)
+    bool m2l_tc = false;  // PETFMM3D_OPT_M2L_TC
     bool timing = false, ev_recorded = false;
     cudaEvent_t ev[PETFMM3D_STAGE_COUNT + 1] = {};
     uint64_t launches = 0, evaluations = 0;
@@ -1695,6 +1988,27 @@ int upload_tables(petfmm3d_ctx *c) {
         float *ap = at.data() + size_t(slot) * nrp * nrp;  // ap[k_in * nrp + r_out]
         for (int k = 0; k < nr; ++k)
             for (int r = 0; r < nr; ++r) ap[size_t(k) * nrp + r] = float(a64[size_t(k) * nr + r]);
+    }
+    if (p <= TT_MAXP) {
+        // TF32 hi / lo images of every operator for the tensor-core M2L:
+        // [slot][hi, lo][k / 4][n][k mod 4] = A[k][n] (zero padding)
+        std::vector<float> img(size_t(NSLOT3) * 2 * nrp * nrp, 0.f);
+        for (int slot = 0; slot < NSLOT3; ++slot) {
+            const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+            if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) < 2) continue;
+            host_m2l_real(p, it.data() + size_t(slot) * nci, a64.data());
+            float *hi = img.data() + size_t(slot) * 2 * nrp * nrp, *lo = hi + size_t(nrp) * nrp;
+            for (int k = 0; k < nr; ++k)
+                for (int n = 0; n < nr; ++n) {
+                    const double a = a64[size_t(k) * nr + n];
+                    const float h = host_tf32_rna(float(a));
+                    const size_t o = (size_t(k / 4) * nrp + n) * 4 + size_t(k % 4);
+                    hi[o] = h;
+                    lo[o] = host_tf32_rna(float(a - double(h)));
+                }
+        }
+        P3_TRY(ensure3(c->tcimg, img.size() * sizeof(float), c->stream));
+        P3_CUDA(cudaMemcpy(c->tcimg.p, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
     P3_TRY(ensure3(c->atab32, at.size() * sizeof(float), c->stream));
     P3_TRY(ensure3(c->rmap, rm.size() * sizeof(short2), c->stream));
@@ -1793,6 +2107,40 @@ cudaError_t m2l_gemm_p(int l, int L, const uint32_t *start, const float *atab, c
     return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t m2l_tc_p(int L, const uint32_t *start, const float *bimg, const float2 *me, float2 *le,
+                     int *status, cudaStream_t st) {
+    if constexpr (mg_nrp(P) <= 64 && mg_nrp(P) % 16 == 0) {
+        constexpr size_t smem = tc3_smem_bytes<P>();
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k3_m2l_tc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(smem));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        int64_t grid = 0;
+        for (int k = 2; k <= L; ++k) grid += tc3_blocks(k);
+        k3_m2l_tc<P><<<unsigned(grid), TC3_THREADS, smem, st>>>(L, start, bimg, me, le, 1LL << 26,
+                                                                status);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+// all levels 2..L in one launch, p <= 8
+cudaError_t launch_m2l_tc3(int p, int L, const uint32_t *start, const float *bimg, const float2 *me,
+                           float2 *le, int *status, cudaStream_t st) {
+    switch (p) {
+#define TC3_CASE(P) case P: return m2l_tc_p<P>(L, start, bimg, me, le, status, st);
+        TC3_CASE(1) TC3_CASE(2) TC3_CASE(3) TC3_CASE(4) TC3_CASE(5) TC3_CASE(6) TC3_CASE(7)
+        TC3_CASE(8)
+#undef TC3_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_m2l_gemm(int p, int l, int L, const uint32_t *start, const float *atab,
                             const short2 *rmap, const float2 *me, float2 *le, cudaStream_t st) {
     switch (p) {
@@ -1847,7 +2195,16 @@ int expansions3(petfmm3d_ctx *c, const uint32_t *start) {
     // mixed path with p <= 8: one launch for all levels (launch_m2l_gemm
     // launches at l = L)
     const bool one = sizeof(T) == 4 && mg_nrp(p) <= 64;
-    for (int l = one ? L : 2; l <= L; ++l) {
+    // mixed path, p <= 8, PETFMM3D_OPT_M2L_TC: all levels on the tensor cores
+    const bool tc = sizeof(T) == 4 && c->m2l_tc && p <= TT_MAXP;
+    if constexpr (sizeof(T) == 4) {
+        if (tc) {
+            P3_CUDA(launch_m2l_tc3(p, L, start, static_cast<const float *>(c->tcimg.p), me, le,
+                                   static_cast<int *>(c->status.p), st));
+            c->launches++;
+        }
+    }
+    for (int l = tc ? L + 1 : one ? L : 2; l <= L; ++l) {
         if constexpr (sizeof(T) == 4) {
             P3_CUDA(launch_m2l_gemm(p, l, L, start, static_cast<const float *>(c->atab32.p),
                                     static_cast<const short2 *>(c->rmap.p), me, le, st));
@@ -2064,6 +2421,10 @@ int petfmm3d_set_option(petfmm3d_ctx *c, int option, int64_t value) {
     if (!c) return PETFMM_EINVAL;
     switch (option) {
         case PETFMM3D_OPT_TIMING: c->timing = value != 0; return PETFMM_OK;
+        case PETFMM3D_OPT_M2L_TC:
+            if (value != 0 && value != 1) return PETFMM_EINVAL;
+            c->m2l_tc = value != 0;
+            return PETFMM_OK;
         default: return PETFMM_EINVAL;
     }
 }
@@ -2131,7 +2492,7 @@ int petfmm3d_destroy(petfmm3d_ctx *c) {
                        &c->keysA, &c->keysB, &c->valsA, &c->valsB, &c->sortw, &c->start,
                        &c->recu,  &c->rec,   &c->xs,    &c->me,    &c->le,    &c->status,
                        &c->rtab32, &c->itab32, &c->rtab64, &c->itab64, &c->atab32, &c->rmap,
-                       &c->m2m32, &c->l2l32};
+                       &c->m2m32, &c->l2l32, &c->tcimg};
     for (DevBuf3 *b : bufs)
         if (b->p) cudaFree(b->p);
     for (int i = 0; i <= PETFMM3D_STAGE_COUNT; ++i)

@@ -13,6 +13,7 @@ from . import _lib
 
 STAGES3 = ("bin", "sort", "gather", "p2m", "m2m", "m2l", "l2l", "near")
 PETFMM3D_OPT_TIMING = 1
+PETFMM3D_OPT_M2L_TC = 2
 PETFMM3D_MAX_L, PETFMM3D_MAX_P = 8, 16
 
 

@@ -108,6 +108,32 @@ def test_mixed_path_within_fp32_budget_of_fp64(orc, case):
     assert _field_rel(mixed, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("case", [
+    dict(n=20000, seed=31, L=3, p=8),
+    dict(n=40000, seed=32, L=4, p=8, clustered_frac=0.4),
+    dict(n=15000, seed=33, L=3, p=5),
+    dict(n=30000, seed=34, L=5, p=3, clustered_frac=0.3),
+])
+def test_tensor_core_m2l_within_fp32_budget(orc, case):
+    # PETFMM3D_OPT_M2L_TC: M2L on tcgen05 with TF32 hi/lo operands; the same
+    # 1e-5 budget against the FP64 path, and close to the SIMT GEMM M2L
+    from paper_0905_2637_gb300 import fmm3d
+    w = W.tiny3d(case["n"], case["seed"], L=case["L"], p=case["p"], dtype="f32",
+                 clustered_frac=case.get("clustered_frac", 0.0))
+    ctx = _ctx(w, "mixed")
+    ctx.set_option(fmm3d.PETFMM3D_OPT_M2L_TC, 1)
+    rc, tc = _run(w, "mixed", ctx)
+    ctx.close()
+    assert rc == 0
+    rc, simt = _run(w, "mixed")
+    assert rc == 0
+    rc, fp64 = _run(w, "fp64")
+    assert rc == 0
+    assert _rel(tc[0], fp64[0]) <= 1e-5
+    assert _field_rel(tc, fp64) <= 1e-5
+    assert _field_rel(tc, simt) <= 1e-5
+
+
 def test_bitwise_reproducible_and_coincident_particles(orc):
     w = W.tiny3d(5000, 13, L=3, p=8, dtype="f32")
     w.x[1], w.y[1], w.z[1] = w.x[0], w.y[0], w.z[0]   # a coincident pair contributes 0
