@@ -680,9 +680,10 @@ int petfmm3d_evaluate(petfmm3d_ctx *ctx, int64_t n, const void *x, const void *y
 int petfmm3d_sync(petfmm3d_ctx *ctx);
 enum {
     PETFMM3D_OPT_TIMING = 1, /* 1: record CUDA events per stage */
-    PETFMM3D_OPT_M2L_TC = 2  /* mixed path, p <= 8: 1 run M2L on the tensor cores
-                                (tcgen05, TF32 hi/lo split, FP32 accumulation);
-                                0 (default) the SIMT GEMM kernel */
+    PETFMM3D_OPT_M2L_TC = 2  /* mixed path, p <= 8: 1 (default) run M2L on the
+                                tensor cores (tcgen05, TF32 hi/lo split, FP32
+                                accumulation); 0 the SIMT GEMM kernel.  Results
+                                differ by FP32-level rounding. */
 };
 int petfmm3d_set_option(petfmm3d_ctx *ctx, int option, int64_t value);
 enum {

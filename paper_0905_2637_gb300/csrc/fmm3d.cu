@@ -1034,7 +1034,8 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
 // images.  A wait that gives up sets PETFMM_ETIMEOUT and the CTA writes
 // nothing.
 // ---------------------------------------------------------------------------
-constexpr int TC3_THREADS = 128;  // one thread per row (and TMEM lane)
+constexpr int TC3_STAGERS = 256;  // two threads per row (and per TMEM lane)
+constexpr int TC3_THREADS = TC3_STAGERS + 32;  // and a warp that copies and issues
 constexpr int TC3_ROWS = 128;
 constexpr int TC3_SETS = 4;       // accumulator sets
 
@@ -1057,8 +1058,9 @@ __device__ __forceinline__ float tf32_rna(float v) {
 }
 
 template <int P> constexpr size_t tc3_smem_bytes() {
-    // A hi and lo (128 x NRP each), then two classes' B hi and lo (NRP x NRP)
-    return size_t(2 * TC3_ROWS * mg_nrp(P) + 4 * mg_nrp(P) * mg_nrp(P)) * sizeof(float);
+    // two A buffers of hi and lo (128 x NRP each), then two classes' B hi
+    // and lo (NRP x NRP each)
+    return size_t(4 * TC3_ROWS * mg_nrp(P) + 4 * mg_nrp(P) * mg_nrp(P)) * sizeof(float);
 }
 
 // blocks of level l in the all-levels launch: 128 parent cells x 4 class pairs
@@ -1075,17 +1077,20 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
     constexpr int NC = P * (P + 1) / 2, NR = P * P, NRP = mg_nrp(P), KG = NRP / 4;
     static_assert(NRP <= 64 && NRP % 16 == 0, "tensor-core M2L orders");
     constexpr int HX = 10, HY = 6, HZ = 6;  // the block's 8 x 4 x 4 parent cells and one of halo
+    constexpr int AIMG = TC3_ROWS * NRP;    // floats of one A image (hi or lo)
+    constexpr int BIMG = 2 * NRP * NRP;     // floats of one class's B images (hi, lo)
     extern __shared__ __align__(1024) float tsm[];
-    float *ahi = tsm, *alo = ahi + TC3_ROWS * NRP;  // [KG][128][4]
-    float *bsm = alo + TC3_ROWS * NRP;              // [class][hi, lo][KG][NRP][4]
+    float *abuf = tsm;                      // 2 buffers x [hi, lo][KG][128][4]
+    float *bsm = abuf + 2 * 2 * AIMG;       // [class][hi, lo][KG][NRP][4]
     __shared__ unsigned char hocc[HX * HY * HZ];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2], bbar[2];  // per class: MMAs done, B landed
     __shared__ uint32_t tslot;
     __shared__ uint32_t set_used;  // bit 2 set + class: that accumulator was written
     int l = 2;
     int64_t bid = blockIdx.x;
     while (l < L && bid >= tc3_blocks(l)) bid -= tc3_blocks(l++);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (TC3_ROWS - 1), half = tid / TC3_ROWS;  // two threads per row
     const int c0 = 2 * int(bid & 3);
     const int64_t np = int64_t(1) << (3 * (l - 1));
     const int64_t p0 = (bid >> 2) * TC3_ROWS;
@@ -1103,8 +1108,8 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
         hocc[h] = (unsigned char)bits;
     }
     __syncthreads();
-    // this thread's row: parent cell p0 + tid, its halo position
-    const int64_t pc = p0 + tid;
+    // this thread's row: parent cell p0 + row, its halo position
+    const int64_t pc = p0 + row;
     const bool row_ok = pc < np;
     const int rx = int(compact3(uint32_t(pc))), ry = int(compact3(uint32_t(pc) >> 1)),
               rz = int(compact3(uint32_t(pc) >> 2));
@@ -1112,7 +1117,10 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
     // nothing to do if the block's targets of both classes are empty
     if (!__syncthreads_or(int((own >> c0) & 3u))) return;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bbar[b])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         set_used = 0;
     }
@@ -1134,9 +1142,24 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
                                (uint32_t(TC3_ROWS >> 4) << 24);
     constexpr uint32_t LBO_A = TC3_ROWS * 16, SBO_A = 128, LBO_B = NRP * 16, SBO_B = 128;
     const float2 *lev = me + lvl_off3(l) * NC;
-    int ncommit = 0;  // commits so far (the same count in every thread)
+    // Pipeline (pairs that run, i = 0, 1, ...): threads 0-255 stage A(i)
+    // into buffer i mod 2 while the MMAs of pair i - 1 run; meanwhile thread
+    // ORCH (warp 8) waits for pair i - 1's class-0 MMAs and sends class 0's
+    // images of pair i to their buffer, then the same for class 1; after the
+    // block's barrier it issues pair i's MMAs, class by class, each once its
+    // images have landed, and commits once per class and pair to mbar[cc]
+    // (also for a near class), so that mbar[cc] phase i means "pair i's
+    // MMAs up to class cc done".  The barrier of pair i - 1 came after
+    // ORCH's wait for pair i - 2's class-1 MMAs, the last reader of A
+    // buffer i mod 2.
+    constexpr int ORCH = TC3_STAGERS;
+    int npair = 0;            // pairs run (the same count in every thread)
+    int ncopy[2] = {0, 0};    // ORCH: B copies per class
     bool ok = true;
-    uint32_t used = 0;  // thread 0: bit 2 set + class, accumulators written
+    uint32_t used = 0;        // ORCH: accumulators written
+    auto wait_bar = [&](uint64_t *bar, int phase) {  // ORCH
+        if (ok && phase >= 0) ok = mbar_wait(smem_addr(bar), uint32_t(phase) & 1u, spin_limit);
+    };
     for (int o = 0; o < 216 && ok; ++o) {
         const int cs = o / 27, dd = o % 27;
         const int dx = dd % 3 - 1, dy = (dd / 3) % 3 - 1, dz = dd / 9 - 1;
@@ -1151,40 +1174,57 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
             slot[cc] = (ex + 3) + 7 * (ey + 3) + 49 * (ez + 3);
         }
         if (!far[0] && !far[1]) continue;
-        // this row's source box
         int sb = -1;
-        if (row_ok) {
+        if (row_ok && tid < TC3_STAGERS) {
             const int qx = rx + dx, qy = ry + dy, qz = rz + dz;
             if (qx >= 0 && qy >= 0 && qz >= 0 && qx < pside && qy < pside && qz < pside &&
                 ((hocc[(qx - hx0) + HX * ((qy - hy0) + HY * (qz - hz0))] >> cs) & 1u))
                 sb = int(morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz)) * 8u + uint32_t(cs));
         }
         if (!__syncthreads_or(int(sb >= 0))) continue;
-        // the previous pair's MMAs still read the images
-        if (ncommit > 0) {
-            if (tid == 0) ok = mbar_wait(smem_addr(&mbar), uint32_t(ncommit - 1) & 1u, spin_limit);
-            ok = __syncthreads_and(int(tid != 0 || ok)) != 0;
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-        }
-        {
+        const int i = npair;
+        if (tid == ORCH) {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                wait_bar(&mbar[cc], i - 1);
+                if (ok && far[cc]) {
+                    const uint32_t bb = smem_addr(&bbar[cc]);
+                    mbar_arrive_expect_tx(bb, uint32_t(BIMG * 4));
+                    bulk_g2s(smem_addr(bsm + cc * BIMG), bimg + size_t(slot[cc]) * BIMG,
+                             uint32_t(BIMG * 4), bb);
+                    ++ncopy[cc];
+                }
+            }
+        } else if (tid < TC3_STAGERS) {
             // A: the row in the real basis (Re of every coefficient, then Im
-            // of those with m > 0, zero padding to NRP), hi and lo
+            // of those with m > 0, zero padding to NRP), each half of the
+            // stagers writing half of the K groups
             float v[NRP];
 #pragma unroll
             for (int k = 0; k < NRP; ++k) v[k] = 0.f;
             if (sb >= 0) {
                 const float2 *src = lev + int64_t(sb) * NC;
                 float2 w[NC];
+                if constexpr (NC % 2 == 0) {
 #pragma unroll
-                for (int j = 0; j < NC; ++j) w[j] = src[j];
+                    for (int j = 0; j < NC / 2; ++j) {
+                        const float4 q4 = reinterpret_cast<const float4 *>(src)[j];
+                        w[2 * j] = make_float2(q4.x, q4.y);
+                        w[2 * j + 1] = make_float2(q4.z, q4.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) w[j] = src[j];
+                }
 #pragma unroll
                 for (int j = 0; j < NC; ++j) v[j] = w[j].x;
 #pragma unroll
                 for (int t = 0; t < NR - NC; ++t) v[NC + t] = w[tc3_imcoef<P>(t)].y;
             }
+            float *ahi = abuf + (i & 1) * 2 * AIMG, *alo = ahi + AIMG;
 #pragma unroll
             for (int g = 0; g < KG; ++g) {
+                if ((g < KG / 2) != (half == 0)) continue;
                 float4 h4, l4;
                 h4.x = tf32_rna(v[4 * g]);
                 h4.y = tf32_rna(v[4 * g + 1]);
@@ -1192,95 +1232,101 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
                 h4.w = tf32_rna(v[4 * g + 3]);
                 l4 = make_float4(tf32_rna(v[4 * g] - h4.x), tf32_rna(v[4 * g + 1] - h4.y),
                                  tf32_rna(v[4 * g + 2] - h4.z), tf32_rna(v[4 * g + 3] - h4.w));
-                reinterpret_cast<float4 *>(ahi)[g * TC3_ROWS + tid] = h4;
-                reinterpret_cast<float4 *>(alo)[g * TC3_ROWS + tid] = l4;
+                reinterpret_cast<float4 *>(ahi)[g * TC3_ROWS + row] = h4;
+                reinterpret_cast<float4 *>(alo)[g * TC3_ROWS + row] = l4;
             }
+            asm volatile("fence.proxy.async.shared::cta;");
         }
-        // B: the two classes' operator images (hi then lo), where far
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            if (!far[cc]) continue;
-            const float4 *src = reinterpret_cast<const float4 *>(bimg + size_t(slot[cc]) * 2 * NRP * NRP);
-            float4 *dst = reinterpret_cast<float4 *>(bsm + size_t(cc) * 2 * NRP * NRP);
-            for (int i = tid; i < NRP * NRP / 2; i += TC3_THREADS) dst[i] = __ldg(src + i);
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
-        if (tid == 0) {
+        ok = __syncthreads_and(int(tid != ORCH || ok)) != 0;
+        if (!ok) break;
+        if (tid == ORCH) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint64_t dah = mma_desc(smem_addr(ahi), LBO_A, SBO_A);
-            const uint64_t dal = mma_desc(smem_addr(alo), LBO_A, SBO_A);
+            const uint32_t ah = smem_addr(abuf + (i & 1) * 2 * AIMG);
+            const uint64_t dah = mma_desc(ah, LBO_A, SBO_A);
+            const uint64_t dal = mma_desc(ah + uint32_t(AIMG * 4), LBO_A, SBO_A);
             constexpr uint64_t sa = (2 * LBO_A) >> 4, sbk = (2 * LBO_B) >> 4;
-            const int set = ncommit % TC3_SETS;
+            const int set = i % TC3_SETS;
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-                if (!far[cc]) continue;
-                const uint32_t bh = smem_addr(bsm + size_t(cc) * 2 * NRP * NRP);
-                const uint64_t dbh = mma_desc(bh, LBO_B, SBO_B);
-                const uint64_t dbl = mma_desc(bh + uint32_t(NRP * NRP * 4), LBO_B, SBO_B);
-                const uint32_t dt = tbase + uint32_t((2 * set + cc) * NRP);
-                const uint32_t bit = 1u << (2 * set + cc);
-                const bool was = (used & bit) != 0;
+                if (far[cc] && ok) {
+                    wait_bar(&bbar[cc], ncopy[cc] - 1);
+                    if (ok) {
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint32_t bh = smem_addr(bsm + cc * BIMG);
+                        const uint64_t dbh = mma_desc(bh, LBO_B, SBO_B);
+                        const uint64_t dbl = mma_desc(bh + uint32_t(NRP * NRP * 4), LBO_B, SBO_B);
+                        const uint32_t dt = tbase + uint32_t((2 * set + cc) * NRP);
+                        const uint32_t bit = 1u << (2 * set + cc);
+                        const bool was = (used & bit) != 0;
 #pragma unroll
-                for (int ks = 0; ks < NRP / 8; ++ks) {
-                    mma_tf32(dt, dah + ks * sa, dbh + ks * sbk, idesc, (was || ks > 0) ? 1u : 0u);
-                    mma_tf32(dt, dal + ks * sa, dbh + ks * sbk, idesc, 1u);
-                    mma_tf32(dt, dah + ks * sa, dbl + ks * sbk, idesc, 1u);
+                        for (int ks = 0; ks < NRP / 8; ++ks) {
+                            mma_tf32(dt, dah + ks * sa, dbh + ks * sbk, idesc,
+                                     (was || ks > 0) ? 1u : 0u);
+                            mma_tf32(dt, dal + ks * sa, dbh + ks * sbk, idesc, 1u);
+                            mma_tf32(dt, dah + ks * sa, dbl + ks * sbk, idesc, 1u);
+                        }
+                        used |= bit;
+                    }
                 }
-                used |= bit;
+                // one commit per class per pair (also with no MMA of the class)
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_addr(&mbar[cc])));
             }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_addr(&mbar)));
         }
-        ++ncommit;
+        ++npair;
     }
-    if (tid == 0) {
-        if (ok && ncommit > 0) ok = mbar_wait(smem_addr(&mbar), uint32_t(ncommit - 1) & 1u, spin_limit);
+    if (tid == ORCH) {
+        wait_bar(&mbar[0], npair - 1);
+        wait_bar(&mbar[1], npair - 1);
         set_used = used;
         if (!ok) {
             set_status(status, ST_ETIMEOUT);
-            // the MMAs in flight finish before the memory goes (bounded)
-            if (ncommit > 0) mbar_wait(smem_addr(&mbar), uint32_t(ncommit - 1) & 1u, 1LL << 26);
+            // the copies and MMAs in flight finish before the memory goes
+            // (bounded; commits and copies complete in order)
+            if (ncopy[0] > 0) mbar_wait(smem_addr(&bbar[0]), uint32_t(ncopy[0] - 1) & 1u, 1LL << 26);
+            if (ncopy[1] > 0) mbar_wait(smem_addr(&bbar[1]), uint32_t(ncopy[1] - 1) & 1u, 1LL << 26);
+            if (npair > 0) {
+                mbar_wait(smem_addr(&mbar[0]), uint32_t(npair - 1) & 1u, 1LL << 26);
+                mbar_wait(smem_addr(&mbar[1]), uint32_t(npair - 1) & 1u, 1LL << 26);
+            }
         }
     }
-    ok = __syncthreads_and(int(tid != 0 || ok)) != 0;
+    ok = __syncthreads_and(int(tid != ORCH || ok)) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok) {
+    if (ok && tid < TC3_STAGERS) {
+        // warps 0-3 take class c0 (TMEM lanes 32 w ..), warps 4-7 class c0 + 1
         float *lef = reinterpret_cast<float *>(le + lvl_off3(l) * NC);
+        const int cc = half;
+        const int c = c0 + cc;
+        float v[NRP];
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int c = c0 + cc;
-            // the sum of the class's accumulator sets, in set order
-            float v[NRP];
+        for (int k = 0; k < NRP; ++k) v[k] = 0.f;
+        for (int set = 0; set < TC3_SETS; ++set) {  // the sets in order
+            if (!((set_used >> (2 * set + cc)) & 1u)) continue;  // uniform in the warp
+            const uint32_t taddr =
+                tbase + (uint32_t((warp & 3) * 32) << 16) + uint32_t((2 * set + cc) * NRP);
 #pragma unroll
-            for (int k = 0; k < NRP; ++k) v[k] = 0.f;
-            for (int set = 0; set < TC3_SETS; ++set) {
-                if (!((set_used >> (2 * set + cc)) & 1u)) continue;  // uniform
-                const uint32_t taddr =
-                    tbase + (uint32_t(warp * 32) << 16) + uint32_t((2 * set + cc) * NRP);
+            for (int q = 0; q < NRP / 16; ++q) {
+                float t16[16];
+                tmem_ld16(taddr + uint32_t(16 * q), t16);
 #pragma unroll
-                for (int q = 0; q < NRP / 16; ++q) {
-                    float t16[16];
-                    tmem_ld16(taddr + uint32_t(16 * q), t16);
+                for (int k = 0; k < 16; ++k) v[16 * q + k] += t16[k];
+            }
+        }
+        if (row_ok && ((own >> c) & 1u)) {
+            float *dst = lef + (pc * 8 + c) * NC * 2;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[16 * q + i] += t16[i];
+            for (int j = 0; j < NC; ++j) dst[2 * j] = v[j];
+            int t = 0;
+#pragma unroll
+            for (int n = 0; n < P; ++n)
+#pragma unroll
+                for (int m = 0; m <= n; ++m) {
+                    const int j = n * (n + 1) / 2 + m;
+                    dst[2 * j + 1] = m == 0 ? 0.f : v[NC + t];
+                    t += m > 0 ? 1 : 0;
                 }
-            }
-            if (row_ok && ((own >> c) & 1u)) {
-                float *dst = lef + (pc * 8 + c) * NC * 2;
-#pragma unroll
-                for (int j = 0; j < NC; ++j) dst[2 * j] = v[j];
-                int t = 0;
-#pragma unroll
-                for (int n = 0; n < P; ++n)
-#pragma unroll
-                    for (int m = 0; m <= n; ++m) {
-                        const int j = n * (n + 1) / 2 + m;
-                        dst[2 * j + 1] = m == 0 ? 0.f : v[NC + t];
-                        t += m > 0 ? 1 : 0;
-                    }
-            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1938,7 +1984,7 @@ struct petfmm3d_ctx {
     DevBuf3 rtab32, itab32, rtab64, itab64, atab32, rmap;
     DevBuf3 m2m32, l2l32;  // p <= 8: the real M2M / L2L operators of the 8 octants
     DevBuf3 tcimg;  // p <= 8: TF32 hi / lo images of the M2L operators (tensor-core M2L)
-    bool m2l_tc = false;  // PETFMM3D_OPT_M2L_TC
+    bool m2l_tc = true;  // PETFMM3D_OPT_M2L_TC
     bool timing = false, ev_recorded = false;
     cudaEvent_t ev[PETFMM3D_STAGE_COUNT + 1] = {};
     uint64_t launches = 0, evaluations = 0;

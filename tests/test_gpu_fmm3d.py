@@ -115,8 +115,9 @@ def test_mixed_path_within_fp32_budget_of_fp64(orc, case):
     dict(n=30000, seed=34, L=5, p=3, clustered_frac=0.3),
 ])
 def test_tensor_core_m2l_within_fp32_budget(orc, case):
-    # PETFMM3D_OPT_M2L_TC: M2L on tcgen05 with TF32 hi/lo operands; the same
-    # 1e-5 budget against the FP64 path, and close to the SIMT GEMM M2L
+    # PETFMM3D_OPT_M2L_TC (the default for p <= 8): M2L on tcgen05 with TF32
+    # hi/lo operands; the same 1e-5 budget against the FP64 path, and close
+    # to the SIMT GEMM M2L (option 0)
     from paper_0905_2637_gb300 import fmm3d
     w = W.tiny3d(case["n"], case["seed"], L=case["L"], p=case["p"], dtype="f32",
                  clustered_frac=case.get("clustered_frac", 0.0))
@@ -125,7 +126,10 @@ def test_tensor_core_m2l_within_fp32_budget(orc, case):
     rc, tc = _run(w, "mixed", ctx)
     ctx.close()
     assert rc == 0
-    rc, simt = _run(w, "mixed")
+    ctx = _ctx(w, "mixed")
+    ctx.set_option(fmm3d.PETFMM3D_OPT_M2L_TC, 0)
+    rc, simt = _run(w, "mixed", ctx)
+    ctx.close()
     assert rc == 0
     rc, fp64 = _run(w, "fp64")
     assert rc == 0
