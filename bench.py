@@ -443,7 +443,7 @@ def _il_pairs3(L):
     return total
 
 
-def threed_leg(torch, stream, steps=5):
+def threed_leg(torch, stream, steps=5, tf32_flops=None):
     """The 3D extension (Laplace potential and field of point charges on an
     octree, fmm3d.cu): 2^21 uniform charges in the unit cube, L = 5, p = 8;
     the mixed path timed (CUDA events on the launching stream), the FP64
@@ -500,17 +500,24 @@ def threed_leg(torch, stream, steps=5):
     return {"kernel": "3D Laplace potential and field (octree, solid harmonics)",
             "workload": w.name, "n": w.n, "levels": w.L, "order": w.p,
             "value": mx["value"], "unit": "particles/s", "ms_per_step": mx["ms_per_step"],
-            "dtype": "f32 (mixed: FP32 expansions, SIMT GEMM M2L, FP32 near field)",
+            "dtype": "f32 (mixed: FP32 expansions, tensor-core M2L with TF32 hi/lo operands and "
+                     "FP32 accumulation, FP32 near field)",
             "rel_l2_vs_fp64": {"phi": rel_phi, "field": rel_e},
             "fp64_gpu": {"value": fp["value"], "ms_per_step": fp["ms_per_step"],
                          "stages_ms": fp["stages_ms"]},
             "stages_ms": mx["stages_ms"], "gpu_launches": mx["launches"],
             "m2l_pairs": m2l_pairs, "near_pairs": near_pairs,
-            "m2l_roofline": {"bound": "fp32", "achieved": m2l_flops / m2l_s, "peak": 2 * fp32_ops,
-                             "unit": "FLOP/s", "frac": m2l_flops / m2l_s / (2 * fp32_ops),
+            "m2l_roofline": {"bound": "tensor", "achieved": m2l_flops / m2l_s,
+                             "peak": tf32_flops, "unit": "FLOP/s",
+                             "frac": m2l_flops / m2l_s / tf32_flops if tf32_flops else None,
+                             "frac_of_fp32_fma": m2l_flops / m2l_s / (2 * fp32_ops),
                              "note": "2 p^4 flops per (target, source) pair, the real p^2 x p^2 "
-                                     "operator; 152 SMs x 128 lanes x 2 x 2070 MHz counts an "
-                                     "FMA as 2"},
+                                     "operator (k3_m2l_tc: tcgen05 kind::tf32, three products "
+                                     "per split operand pair, so the tensor pipe executes 3x "
+                                     "these flops); peak = the tcgen05 kind::tf32 "
+                                     "microbenchmark (petfmm_measure_peaks); frac_of_fp32_fma "
+                                     "against 152 SMs x 128 lanes x 2 x 2070 MHz, the SIMT "
+                                     "kernel's bound"},
             "near_roofline": {"bound": "fp32", "achieved": 13 * near_pairs / near_s,
                               "peak": fp32_ops, "unit": "ops/s",
                               "frac": 13 * near_pairs / near_s / fp32_ops,
@@ -828,7 +835,7 @@ def main():
         if not args.no_laplace:
             line["laplace"] = laplace_leg(_lib, torch, stream)
         if not args.no_3d:
-            line["threed"] = threed_leg(torch, stream)
+            line["threed"] = threed_leg(torch, stream, tf32_flops=pipes["tf32_flops"])
         if not args.no_serve:
             line["serving"] = serving_leg(_lib)
         if not args.no_cpu_baseline:
