@@ -1058,9 +1058,9 @@ __device__ __forceinline__ float tf32_rna(float v) {
 }
 
 template <int P> constexpr size_t tc3_smem_bytes() {
-    // two A buffers of hi and lo (128 x NRP each), then two classes' B hi
-    // and lo (NRP x NRP each)
-    return size_t(4 * TC3_ROWS * mg_nrp(P) + 4 * mg_nrp(P) * mg_nrp(P)) * sizeof(float);
+    // one A buffer of hi and lo (128 x NRP each), then four slots of a
+    // class's B hi and lo (NRP x NRP each)
+    return size_t(2 * TC3_ROWS * mg_nrp(P) + 8 * mg_nrp(P) * mg_nrp(P)) * sizeof(float);
 }
 
 // blocks of level l in the all-levels launch: 128 parent cells x 4 class pairs
@@ -1079,24 +1079,30 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
     constexpr int HX = 10, HY = 6, HZ = 6;  // the block's 8 x 4 x 4 parent cells and one of halo
     constexpr int AIMG = TC3_ROWS * NRP;    // floats of one A image (hi or lo)
     constexpr int BIMG = 2 * NRP * NRP;     // floats of one class's B images (hi, lo)
+    constexpr int NSLOT = 4;                // B slots: step s = 2 pair + class uses slot s mod 4
     extern __shared__ __align__(1024) float tsm[];
-    float *abuf = tsm;                      // 2 buffers x [hi, lo][KG][128][4]
-    float *bsm = abuf + 2 * 2 * AIMG;       // [class][hi, lo][KG][NRP][4]
+    float *ahi = tsm, *alo = ahi + AIMG;    // [KG][128][4] each
+    float *bsm = alo + AIMG;                // NSLOT x [hi, lo][KG][NRP][4]
     __shared__ unsigned char hocc[HX * HY * HZ];
-    __shared__ __align__(8) uint64_t mbar[2], bbar[2];  // per class: MMAs done, B landed
+    __shared__ unsigned char plist[216];    // the pairs that run: offset entries o
+    __shared__ uint32_t pmask[7];           // offsets o with an occupied source row
+    __shared__ int npl;
+    __shared__ __align__(8) uint64_t mbar[NSLOT], bbar[NSLOT];  // per slot: MMAs done, B landed
     __shared__ uint32_t tslot;
     __shared__ uint32_t set_used;  // bit 2 set + class: that accumulator was written
     int l = 2;
     int64_t bid = blockIdx.x;
     while (l < L && bid >= tc3_blocks(l)) bid -= tc3_blocks(l++);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & (TC3_ROWS - 1), half = tid / TC3_ROWS;  // two threads per row
+    const int row = tid & (TC3_ROWS - 1), half = (tid / TC3_ROWS) & 1;  // two stagers per row
+    const bool stager = tid < TC3_STAGERS;
     const int c0 = 2 * int(bid & 3);
     const int64_t np = int64_t(1) << (3 * (l - 1));
     const int64_t p0 = (bid >> 2) * TC3_ROWS;
     const int pside = 1 << (l - 1);
     const int hx0 = int(compact3(uint32_t(p0))) - 1, hy0 = int(compact3(uint32_t(p0) >> 1)) - 1,
               hz0 = int(compact3(uint32_t(p0) >> 2)) - 1;
+    if (tid < 7) pmask[tid] = 0;
     for (int h = tid; h < HX * HY * HZ; h += TC3_THREADS) {
         const int qx = hx0 + h % HX, qy = hy0 + (h / HX) % HY, qz = hz0 + h / (HX * HY);
         unsigned bits = 0;
@@ -1116,8 +1122,36 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
     const unsigned own = row_ok ? hocc[(rx - hx0) + HX * ((ry - hy0) + HY * (rz - hz0))] : 0u;
     // nothing to do if the block's targets of both classes are empty
     if (!__syncthreads_or(int((own >> c0) & 3u))) return;
+    // the row's source box for offset entry o (-1: empty or outside)
+    auto source = [&](int o) {
+        if (!row_ok) return -1;
+        const int cs = o / 27, dd = o % 27;
+        const int qx = rx + dd % 3 - 1, qy = ry + (dd / 3) % 3 - 1, qz = rz + dd / 9 - 1;
+        if (qx < 0 || qy < 0 || qz < 0 || qx >= pside || qy >= pside || qz >= pside) return -1;
+        if (!((hocc[(qx - hx0) + HX * ((qy - hy0) + HY * (qz - hz0))] >> cs) & 1u)) return -1;
+        return int(morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz)) * 8u + uint32_t(cs));
+    };
+    // class cc's operator slot for offset entry o, or -1 where it is near
+    auto op_slot = [&](int o, int cc) {
+        const int c = c0 + cc, cs = o / 27, dd = o % 27;
+        const int ex = (c & 1) - (cs & 1) - 2 * (dd % 3 - 1),
+                  ey = ((c >> 1) & 1) - ((cs >> 1) & 1) - 2 * ((dd / 3) % 3 - 1),
+                  ez = (c >> 2) - (cs >> 2) - 2 * (dd / 9 - 1);
+        if (ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1 && ez >= -1 && ez <= 1) return -1;
+        return (ex + 3) + 7 * (ey + 3) + 49 * (ez + 3);
+    };
+    // the pairs that run: an operator for one of the two classes, a source row
+    if (stager && half == 0)
+        for (int o = 0; o < 216; ++o)
+            if (source(o) >= 0) atomicOr(&pmask[o >> 5], 1u << (o & 31));
+    __syncthreads();
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
+        int k = 0;
+        for (int o = 0; o < 216; ++o)
+            if (((pmask[o >> 5] >> (o & 31)) & 1u) && (op_slot(o, 0) >= 0 || op_slot(o, 1) >= 0))
+                plist[k++] = (unsigned char)o;
+        npl = k;
+        for (int b = 0; b < NSLOT; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[b])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bbar[b])));
         }
@@ -1136,92 +1170,84 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = tslot;
+    const int n_pairs = npl;
     // kind::tf32: D F32 (bit 4), A and B TF32 (bits 7, 10), both K-major,
     // N / 8 at bit 17, M / 16 at bit 24
     constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(NRP >> 3) << 17) |
                                (uint32_t(TC3_ROWS >> 4) << 24);
     constexpr uint32_t LBO_A = TC3_ROWS * 16, SBO_A = 128, LBO_B = NRP * 16, SBO_B = 128;
     const float2 *lev = me + lvl_off3(l) * NC;
-    // Pipeline (pairs that run, i = 0, 1, ...): threads 0-255 stage A(i)
-    // into buffer i mod 2 while the MMAs of pair i - 1 run; meanwhile thread
-    // ORCH (warp 8) waits for pair i - 1's class-0 MMAs and sends class 0's
-    // images of pair i to their buffer, then the same for class 1; after the
-    // block's barrier it issues pair i's MMAs, class by class, each once its
-    // images have landed, and commits once per class and pair to mbar[cc]
-    // (also for a near class), so that mbar[cc] phase i means "pair i's
-    // MMAs up to class cc done".  The barrier of pair i - 1 came after
-    // ORCH's wait for pair i - 2's class-1 MMAs, the last reader of A
-    // buffer i mod 2.
+    // Pipeline over the pairs i = 0 .. n_pairs - 1, each two steps s = 2 i +
+    // class: ORCH (warp 8, one thread) copies the operator images of pair
+    // i + 1 into slots (2 i + 2 + class) mod 4 while pair i multiplies; the
+    // stagers hold pair i + 1's source rows in registers, loaded while pair
+    // i multiplies, and write them into the single A buffer once ORCH has
+    // seen pair i's MMAs done (barrier 1), then ORCH issues pair i + 1's
+    // MMAs (barrier 2).  Every step commits once to its slot's mbar (also a
+    // near class with no MMA), so mbar[s mod 4] phase s / 4 is "step s done".
     constexpr int ORCH = TC3_STAGERS;
-    int npair = 0;            // pairs run (the same count in every thread)
-    int ncopy[2] = {0, 0};    // ORCH: B copies per class
     bool ok = true;
     uint32_t used = 0;        // ORCH: accumulators written
-    auto wait_bar = [&](uint64_t *bar, int phase) {  // ORCH
-        if (ok && phase >= 0) ok = mbar_wait(smem_addr(bar), uint32_t(phase) & 1u, spin_limit);
+    int ncopy[NSLOT] = {0, 0, 0, 0};  // ORCH: copies into each slot
+    int committed = 0;                // ORCH: steps committed
+    auto wait_step = [&](int st) {  // ORCH: step st's MMAs done
+        if (ok && st >= 0)
+            ok = mbar_wait(smem_addr(&mbar[st % NSLOT]), uint32_t(st / NSLOT) & 1u, spin_limit);
     };
-    for (int o = 0; o < 216 && ok; ++o) {
-        const int cs = o / 27, dd = o % 27;
-        const int dx = dd % 3 - 1, dy = (dd / 3) % 3 - 1, dz = dd / 9 - 1;
-        int slot[2];
-        bool far[2];
+    auto copy_pair = [&](int i) {  // ORCH: pair i's images into slots (2 i + class) mod 4
+        const int o = plist[i];
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
-            const int c = c0 + cc;
-            const int ex = (c & 1) - (cs & 1) - 2 * dx, ey = ((c >> 1) & 1) - ((cs >> 1) & 1) - 2 * dy,
-                      ez = (c >> 2) - (cs >> 2) - 2 * dz;
-            far[cc] = !(ex >= -1 && ex <= 1 && ey >= -1 && ey <= 1 && ez >= -1 && ez <= 1);
-            slot[cc] = (ex + 3) + 7 * (ey + 3) + 49 * (ez + 3);
+            const int os = op_slot(o, cc);
+            const int sl = (2 * i + cc) % NSLOT;
+            if (os < 0 || !ok) continue;
+            const uint32_t bb = smem_addr(&bbar[sl]);
+            mbar_arrive_expect_tx(bb, uint32_t(BIMG * 4));
+            bulk_g2s(smem_addr(bsm + sl * BIMG), bimg + size_t(os) * BIMG, uint32_t(BIMG * 4), bb);
+            ++ncopy[sl];
         }
-        if (!far[0] && !far[1]) continue;
-        int sb = -1;
-        if (row_ok && tid < TC3_STAGERS) {
-            const int qx = rx + dx, qy = ry + dy, qz = rz + dz;
-            if (qx >= 0 && qy >= 0 && qz >= 0 && qx < pside && qy < pside && qz < pside &&
-                ((hocc[(qx - hx0) + HX * ((qy - hy0) + HY * (qz - hz0))] >> cs) & 1u))
-                sb = int(morton3(uint32_t(qx), uint32_t(qy), uint32_t(qz)) * 8u + uint32_t(cs));
-        }
-        if (!__syncthreads_or(int(sb >= 0))) continue;
-        const int i = npair;
-        if (tid == ORCH) {
+    };
+    // rows of pair 0 in registers; the images of pair 0 on their way
+    float2 w[NC];
+    auto load_row = [&](int i) {
+        const int sb = (stager && i < n_pairs) ? source(plist[i]) : -1;
+        if (sb >= 0) {
+            const float2 *src = lev + int64_t(sb) * NC;
+            if constexpr (NC % 2 == 0) {
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                wait_bar(&mbar[cc], i - 1);
-                if (ok && far[cc]) {
-                    const uint32_t bb = smem_addr(&bbar[cc]);
-                    mbar_arrive_expect_tx(bb, uint32_t(BIMG * 4));
-                    bulk_g2s(smem_addr(bsm + cc * BIMG), bimg + size_t(slot[cc]) * BIMG,
-                             uint32_t(BIMG * 4), bb);
-                    ++ncopy[cc];
+                for (int j = 0; j < NC / 2; ++j) {
+                    const float4 q4 = reinterpret_cast<const float4 *>(src)[j];
+                    w[2 * j] = make_float2(q4.x, q4.y);
+                    w[2 * j + 1] = make_float2(q4.z, q4.w);
                 }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NC; ++j) w[j] = src[j];
             }
-        } else if (tid < TC3_STAGERS) {
+        } else {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) w[j] = make_float2(0.f, 0.f);
+        }
+    };
+    load_row(0);
+    if (tid == ORCH && n_pairs > 0) copy_pair(0);
+    for (int i = 0; i < n_pairs && ok; ++i) {
+        // barrier 1: the A buffer is free (pair i - 1's MMAs done)
+        if (tid == ORCH) wait_step(2 * i - 1);
+        ok = __syncthreads_and(int(tid != ORCH || ok)) != 0;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (stager) {
             // A: the row in the real basis (Re of every coefficient, then Im
-            // of those with m > 0, zero padding to NRP), each half of the
-            // stagers writing half of the K groups
+            // of those with m > 0, zero padding to NRP), each of the two
+            // stagers of a row writing half of the K groups
             float v[NRP];
 #pragma unroll
-            for (int k = 0; k < NRP; ++k) v[k] = 0.f;
-            if (sb >= 0) {
-                const float2 *src = lev + int64_t(sb) * NC;
-                float2 w[NC];
-                if constexpr (NC % 2 == 0) {
+            for (int j = 0; j < NC; ++j) v[j] = w[j].x;
 #pragma unroll
-                    for (int j = 0; j < NC / 2; ++j) {
-                        const float4 q4 = reinterpret_cast<const float4 *>(src)[j];
-                        w[2 * j] = make_float2(q4.x, q4.y);
-                        w[2 * j + 1] = make_float2(q4.z, q4.w);
-                    }
-                } else {
+            for (int t = 0; t < NR - NC; ++t) v[NC + t] = w[tc3_imcoef<P>(t)].y;
 #pragma unroll
-                    for (int j = 0; j < NC; ++j) w[j] = src[j];
-                }
-#pragma unroll
-                for (int j = 0; j < NC; ++j) v[j] = w[j].x;
-#pragma unroll
-                for (int t = 0; t < NR - NC; ++t) v[NC + t] = w[tc3_imcoef<P>(t)].y;
-            }
-            float *ahi = abuf + (i & 1) * 2 * AIMG, *alo = ahi + AIMG;
+            for (int k = NR; k < NRP; ++k) v[k] = 0.f;
 #pragma unroll
             for (int g = 0; g < KG; ++g) {
                 if ((g < KG / 2) != (half == 0)) continue;
@@ -1236,23 +1262,28 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
                 reinterpret_cast<float4 *>(alo)[g * TC3_ROWS + row] = l4;
             }
             asm volatile("fence.proxy.async.shared::cta;");
+        } else if (tid == ORCH && i + 1 < n_pairs) {
+            // pair i + 1's images: its slots last held steps 2 i - 2 and
+            // 2 i - 1, done (waited above)
+            copy_pair(i + 1);
         }
-        ok = __syncthreads_and(int(tid != ORCH || ok)) != 0;
-        if (!ok) break;
-        if (tid == ORCH) {
+        // barrier 2: A(i) written
+        __syncthreads();
+        if (tid == ORCH && ok) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t ah = smem_addr(abuf + (i & 1) * 2 * AIMG);
-            const uint64_t dah = mma_desc(ah, LBO_A, SBO_A);
-            const uint64_t dal = mma_desc(ah + uint32_t(AIMG * 4), LBO_A, SBO_A);
+            const uint64_t dah = mma_desc(smem_addr(ahi), LBO_A, SBO_A);
+            const uint64_t dal = mma_desc(smem_addr(alo), LBO_A, SBO_A);
             constexpr uint64_t sa = (2 * LBO_A) >> 4, sbk = (2 * LBO_B) >> 4;
             const int set = i % TC3_SETS;
+            const int o = plist[i];
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
-                if (far[cc] && ok) {
-                    wait_bar(&bbar[cc], ncopy[cc] - 1);
+                const int sl = (2 * i + cc) % NSLOT;
+                if (op_slot(o, cc) >= 0 && ok) {
+                    ok = mbar_wait(smem_addr(&bbar[sl]), uint32_t(ncopy[sl] - 1) & 1u, spin_limit);
                     if (ok) {
                         asm volatile("tcgen05.fence::after_thread_sync;");
-                        const uint32_t bh = smem_addr(bsm + cc * BIMG);
+                        const uint32_t bh = smem_addr(bsm + sl * BIMG);
                         const uint64_t dbh = mma_desc(bh, LBO_B, SBO_B);
                         const uint64_t dbl = mma_desc(bh + uint32_t(NRP * NRP * 4), LBO_B, SBO_B);
                         const uint32_t dt = tbase + uint32_t((2 * set + cc) * NRP);
@@ -1268,33 +1299,34 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
                         used |= bit;
                     }
                 }
-                // one commit per class per pair (also with no MMA of the class)
+                // one commit per step (also with no MMA)
                 asm volatile(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_addr(&mbar[cc])));
+                        smem_addr(&mbar[sl])));
+                ++committed;
             }
         }
-        ++npair;
+        // the stagers load pair i + 1's rows while pair i multiplies
+        load_row(i + 1);
     }
     if (tid == ORCH) {
-        wait_bar(&mbar[0], npair - 1);
-        wait_bar(&mbar[1], npair - 1);
+        wait_step(2 * n_pairs - 1);
         set_used = used;
         if (!ok) {
             set_status(status, ST_ETIMEOUT);
             // the copies and MMAs in flight finish before the memory goes
-            // (bounded; commits and copies complete in order)
-            if (ncopy[0] > 0) mbar_wait(smem_addr(&bbar[0]), uint32_t(ncopy[0] - 1) & 1u, 1LL << 26);
-            if (ncopy[1] > 0) mbar_wait(smem_addr(&bbar[1]), uint32_t(ncopy[1] - 1) & 1u, 1LL << 26);
-            if (npair > 0) {
-                mbar_wait(smem_addr(&mbar[0]), uint32_t(npair - 1) & 1u, 1LL << 26);
-                mbar_wait(smem_addr(&mbar[1]), uint32_t(npair - 1) & 1u, 1LL << 26);
+            // (bounded)
+            for (int sl = 0; sl < NSLOT; ++sl)
+                if (ncopy[sl] > 0) mbar_wait(smem_addr(&bbar[sl]), uint32_t(ncopy[sl] - 1) & 1u, 1LL << 26);
+            if (committed > 0) {  // the last commit covers every earlier MMA
+                const int st = committed - 1;
+                mbar_wait(smem_addr(&mbar[st % NSLOT]), uint32_t(st / NSLOT) & 1u, 1LL << 26);
             }
         }
     }
     ok = __syncthreads_and(int(tid != ORCH || ok)) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok && tid < TC3_STAGERS) {
+    if (ok && stager) {
         // warps 0-3 take class c0 (TMEM lanes 32 w ..), warps 4-7 class c0 + 1
         float *lef = reinterpret_cast<float *>(le + lvl_off3(l) * NC);
         const int cc = half;
