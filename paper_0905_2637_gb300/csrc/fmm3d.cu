@@ -1057,6 +1057,85 @@ __device__ __forceinline__ float tf32_rna(float v) {
     return __uint_as_float(r);
 }
 
+// The tensor-core M2L's input (K) basis, coefficient by coefficient: Re of
+// coefficient j, then Im of j if its m > 0 (zero padding to NRP), so that
+// each half of K covers about half of a row's coefficients and each of the
+// two threads staging a row loads about half of it.  The output (N) basis
+// stays the one of the M2L matrices (Re of all, then Im of m > 0).
+template <int P> struct Tc3Basis {
+    int j[mg_nrp(P)];     // coefficient, -1 for padding
+    int part[mg_nrp(P)];  // 0 Re, 1 Im
+    __host__ __device__ constexpr Tc3Basis() : j(), part() {
+        int k = 0;
+        for (int n = 0; n < P; ++n)
+            for (int m = 0; m <= n; ++m) {
+                const int jj = n * (n + 1) / 2 + m;
+                j[k] = jj;
+                part[k++] = 0;
+                if (m > 0) {
+                    j[k] = jj;
+                    part[k++] = 1;
+                }
+            }
+        for (; k < mg_nrp(P); ++k) {
+            j[k] = -1;
+            part[k] = 0;
+        }
+    }
+    // the coefficients K half h reads: [lo, hi]
+    __host__ __device__ constexpr int jlo(int h) const {
+        int r = 1 << 30;
+        for (int k = h * (mg_nrp(P) / 2); k < (h + 1) * (mg_nrp(P) / 2); ++k)
+            if (j[k] >= 0 && j[k] < r) r = j[k];
+        return r == (1 << 30) ? 0 : r;
+    }
+    __host__ __device__ constexpr int jhi(int h) const {
+        int r = -1;
+        for (int k = h * (mg_nrp(P) / 2); k < (h + 1) * (mg_nrp(P) / 2); ++k)
+            if (j[k] > r) r = j[k];
+        return r;
+    }
+};
+
+// Coefficients a K half reads, and the most either half reads.
+template <int P> __host__ __device__ constexpr int tc3_half_j0(int h) { return Tc3Basis<P>{}.jlo(h); }
+template <int P> __host__ __device__ constexpr int tc3_half_nw(int h) {
+    return Tc3Basis<P>{}.jhi(h) - Tc3Basis<P>{}.jlo(h) + 1;
+}
+template <int P> __host__ __device__ constexpr int tc3_nw() {
+    return tc3_half_nw<P>(0) > tc3_half_nw<P>(1) ? tc3_half_nw<P>(0) : tc3_half_nw<P>(1);
+}
+
+// One K half H of a row of A in the input basis, hi and lo, into the K-major
+// images, from the coefficients j0(H) .. of the row held in w.
+template <int P, int H>
+__device__ __forceinline__ void tc3_write_half(const float2 (&w)[tc3_nw<P>()], float *ahi, float *alo,
+                                               int row) {
+    constexpr int NRP = mg_nrp(P), KH = NRP / 2;
+    constexpr Tc3Basis<P> bas{};
+    constexpr int J0 = tc3_half_j0<P>(H);
+#pragma unroll
+    for (int g = 0; g < KH / 4; ++g) {
+        float v4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = H * KH + 4 * g + e;
+            const int jj = bas.j[k];
+            v4[e] = jj < 0 ? 0.f : (bas.part[k] ? w[jj - J0].y : w[jj - J0].x);
+        }
+        float4 h4, l4;
+        h4.x = tf32_rna(v4[0]);
+        h4.y = tf32_rna(v4[1]);
+        h4.z = tf32_rna(v4[2]);
+        h4.w = tf32_rna(v4[3]);
+        l4 = make_float4(tf32_rna(v4[0] - h4.x), tf32_rna(v4[1] - h4.y), tf32_rna(v4[2] - h4.z),
+                         tf32_rna(v4[3] - h4.w));
+        const int kg = H * (KH / 4) + g;
+        reinterpret_cast<float4 *>(ahi)[kg * TC3_ROWS + row] = h4;
+        reinterpret_cast<float4 *>(alo)[kg * TC3_ROWS + row] = l4;
+    }
+}
+
 template <int P> constexpr size_t tc3_smem_bytes() {
     // one A buffer of hi and lo (128 x NRP each), then four slots of a
     // class's B hi and lo (NRP x NRP each)
@@ -1208,26 +1287,16 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
         }
     };
     // rows of pair 0 in registers; the images of pair 0 on their way
-    float2 w[NC];
+    // this stager's half of the next pair's row, in registers
+    constexpr int NW = tc3_nw<P>();
+    const int j0 = half ? tc3_half_j0<P>(1) : tc3_half_j0<P>(0);
+    const int nw = half ? tc3_half_nw<P>(1) : tc3_half_nw<P>(0);
+    float2 w[NW];
     auto load_row = [&](int i) {
         const int sb = (stager && i < n_pairs) ? source(plist[i]) : -1;
-        if (sb >= 0) {
-            const float2 *src = lev + int64_t(sb) * NC;
-            if constexpr (NC % 2 == 0) {
+        const float2 *src = lev + int64_t(sb < 0 ? 0 : sb) * NC + j0;
 #pragma unroll
-                for (int j = 0; j < NC / 2; ++j) {
-                    const float4 q4 = reinterpret_cast<const float4 *>(src)[j];
-                    w[2 * j] = make_float2(q4.x, q4.y);
-                    w[2 * j + 1] = make_float2(q4.z, q4.w);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < NC; ++j) w[j] = src[j];
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < NC; ++j) w[j] = make_float2(0.f, 0.f);
-        }
+        for (int t = 0; t < NW; ++t) w[t] = (sb >= 0 && t < nw) ? src[t] : make_float2(0.f, 0.f);
     };
     load_row(0);
     if (tid == ORCH && n_pairs > 0) copy_pair(0);
@@ -1238,29 +1307,12 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (stager) {
-            // A: the row in the real basis (Re of every coefficient, then Im
-            // of those with m > 0, zero padding to NRP), each of the two
-            // stagers of a row writing half of the K groups
-            float v[NRP];
-#pragma unroll
-            for (int j = 0; j < NC; ++j) v[j] = w[j].x;
-#pragma unroll
-            for (int t = 0; t < NR - NC; ++t) v[NC + t] = w[tc3_imcoef<P>(t)].y;
-#pragma unroll
-            for (int k = NR; k < NRP; ++k) v[k] = 0.f;
-#pragma unroll
-            for (int g = 0; g < KG; ++g) {
-                if ((g < KG / 2) != (half == 0)) continue;
-                float4 h4, l4;
-                h4.x = tf32_rna(v[4 * g]);
-                h4.y = tf32_rna(v[4 * g + 1]);
-                h4.z = tf32_rna(v[4 * g + 2]);
-                h4.w = tf32_rna(v[4 * g + 3]);
-                l4 = make_float4(tf32_rna(v[4 * g] - h4.x), tf32_rna(v[4 * g + 1] - h4.y),
-                                 tf32_rna(v[4 * g + 2] - h4.z), tf32_rna(v[4 * g + 3] - h4.w));
-                reinterpret_cast<float4 *>(ahi)[g * TC3_ROWS + row] = h4;
-                reinterpret_cast<float4 *>(alo)[g * TC3_ROWS + row] = l4;
-            }
+            // A: the row in the input basis, each of the two stagers of a row
+            // writing its half of the K groups
+            if (half == 0)
+                tc3_write_half<P, 0>(w, ahi, alo, row);
+            else
+                tc3_write_half<P, 1>(w, ahi, alo, row);
             asm volatile("fence.proxy.async.shared::cta;");
         } else if (tid == ORCH && i + 1 < n_pairs) {
             // pair i + 1's images: its slots last held steps 2 i - 2 and
@@ -2071,19 +2123,32 @@ int upload_tables(petfmm3d_ctx *c) {
         // TF32 hi / lo images of every operator for the tensor-core M2L:
         // [slot][hi, lo][k / 4][n][k mod 4] = A[k][n] (zero padding)
         std::vector<float> img(size_t(NSLOT3) * 2 * nrp * nrp, 0.f);
+        // input-basis position k -> row of the M2L matrix (Re of j: j; Im of
+        // j: NC + its rank among the m > 0 coefficients)
+        std::vector<int> tc3_kin(static_cast<size_t>(nr));
+        for (int n = 0, k = 0, t = 0; n < p; ++n)
+            for (int m = 0; m <= n; ++m) {
+                const int j = n * (n + 1) / 2 + m;
+                tc3_kin[size_t(k++)] = j;
+                if (m > 0) tc3_kin[size_t(k++)] = nc + t++;
+            }
         for (int slot = 0; slot < NSLOT3; ++slot) {
             const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
             if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) < 2) continue;
             host_m2l_real(p, it.data() + size_t(slot) * nci, a64.data());
             float *hi = img.data() + size_t(slot) * 2 * nrp * nrp, *lo = hi + size_t(nrp) * nrp;
-            for (int k = 0; k < nr; ++k)
+            // K in the input basis of the tensor-core M2L (coefficient by
+            // coefficient: Re, then Im if m > 0); N in the M2L matrices' basis
+            for (int k = 0; k < nr; ++k) {
+                const int kin = tc3_kin[size_t(k)];
                 for (int n = 0; n < nr; ++n) {
-                    const double a = a64[size_t(k) * nr + n];
+                    const double a = a64[size_t(kin) * nr + n];
                     const float h = host_tf32_rna(float(a));
                     const size_t o = (size_t(k / 4) * nrp + n) * 4 + size_t(k % 4);
                     hi[o] = h;
                     lo[o] = host_tf32_rna(float(a - double(h)));
                 }
+            }
         }
         P3_TRY(ensure3(c->tcimg, img.size() * sizeof(float), c->stream));
         P3_CUDA(cudaMemcpy(c->tcimg.p, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice));
