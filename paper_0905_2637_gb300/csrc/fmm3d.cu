@@ -1013,9 +1013,9 @@ __global__ void __launch_bounds__(MG_THREADS) k3_m2l_pipe(int L, const uint32_t 
 // nearest: a - a_hi - a_lo is within about 2^-23 |a|, near an FP32
 // rounding; the products a_hi b_hi + a_lo b_hi + a_hi b_lo leave out
 // a_lo b_lo, about 2^-24) and FP32 accumulation in tensor memory, spread
-// over TC3_SETS accumulator sets that consecutive pairs take in turn and
-// that the epilogue adds in registers: each set's chain of MMA additions is
-// a quarter as long.  (With one set the potential of a 20k-charge test
+// over TC3_SETS accumulator sets that consecutive pairs take in turn, read
+// out every TC3_FLUSH pairs and added in registers (round to nearest): a
+// chain of MMA additions into one accumulator spans two pairs, 48 steps.  (With one set the potential of a 20k-charge test
 // drifted 1.2e-5 from the FP64 path, past the mixed path's 1e-5 budget,
 // whether the split truncated or rounded: the error grows with the length
 // of the accumulation chain, some 4,500 MMA steps per output here.)  A CTA takes the 128
@@ -1038,6 +1038,7 @@ constexpr int TC3_STAGERS = 256;  // two threads per row (and per TMEM lane)
 constexpr int TC3_THREADS = TC3_STAGERS + 32;  // and a warp that copies and issues
 constexpr int TC3_ROWS = 128;
 constexpr int TC3_SETS = 4;       // accumulator sets
+constexpr int TC3_FLUSH = 8;      // pairs between read-outs of the sets into registers
 
 // coefficient index n (n + 1) / 2 + m of the t-th coefficient with m > 0
 template <int P> __host__ __device__ constexpr int tc3_imcoef(int t) {
@@ -1298,6 +1299,13 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
 #pragma unroll
         for (int t = 0; t < NW; ++t) w[t] = (sb >= 0 && t < nw) ? src[t] : make_float2(0.f, 0.f);
     };
+    // the stager's class, its row's sums so far (registers, FP32 round to
+    // nearest): every TC3_FLUSH pairs the accumulator sets are read out of
+    // TMEM, added here, and the next pairs start the sets afresh
+    const int my_cc = half;
+    float acc[NRP];
+#pragma unroll
+    for (int k = 0; k < NRP; ++k) acc[k] = 0.f;
     load_row(0);
     if (tid == ORCH && n_pairs > 0) copy_pair(0);
     for (int i = 0; i < n_pairs && ok; ++i) {
@@ -1360,10 +1368,37 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
         }
         // the stagers load pair i + 1's rows while pair i multiplies
         load_row(i + 1);
+        if ((i + 1) % TC3_FLUSH == 0 || i + 1 == n_pairs) {
+            // flush: every MMA so far done, the sets added into registers
+            if (tid == ORCH) {
+                wait_step(2 * i + 1);
+                set_used = used;
+            }
+            ok = __syncthreads_and(int(tid != ORCH || ok)) != 0;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (stager) {
+                const uint32_t su = set_used;
+                for (int set = 0; set < TC3_SETS; ++set) {  // the sets in order
+                    if (!((su >> (2 * set + my_cc)) & 1u)) continue;  // uniform in the warp
+                    const uint32_t taddr = tbase + (uint32_t((warp & 3) * 32) << 16) +
+                                           uint32_t((2 * set + my_cc) * NRP);
+#pragma unroll
+                    for (int q = 0; q < NRP / 16; ++q) {
+                        float t16[16];
+                        tmem_ld16(taddr + uint32_t(16 * q), t16);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) acc[16 * q + k] += t16[k];
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            if (tid == ORCH) used = 0;  // the next MMAs overwrite the sets
+        }
     }
     if (tid == ORCH) {
         wait_step(2 * n_pairs - 1);
-        set_used = used;
         if (!ok) {
             set_status(status, ST_ETIMEOUT);
             // the copies and MMAs in flight finish before the memory goes
@@ -1381,23 +1416,8 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
     if (ok && stager) {
         // warps 0-3 take class c0 (TMEM lanes 32 w ..), warps 4-7 class c0 + 1
         float *lef = reinterpret_cast<float *>(le + lvl_off3(l) * NC);
-        const int cc = half;
-        const int c = c0 + cc;
-        float v[NRP];
-#pragma unroll
-        for (int k = 0; k < NRP; ++k) v[k] = 0.f;
-        for (int set = 0; set < TC3_SETS; ++set) {  // the sets in order
-            if (!((set_used >> (2 * set + cc)) & 1u)) continue;  // uniform in the warp
-            const uint32_t taddr =
-                tbase + (uint32_t((warp & 3) * 32) << 16) + uint32_t((2 * set + cc) * NRP);
-#pragma unroll
-            for (int q = 0; q < NRP / 16; ++q) {
-                float t16[16];
-                tmem_ld16(taddr + uint32_t(16 * q), t16);
-#pragma unroll
-                for (int k = 0; k < 16; ++k) v[16 * q + k] += t16[k];
-            }
-        }
+        const int c = c0 + my_cc;
+        const float *v = acc;
         if (row_ok && ((own >> c) & 1u)) {
             float *dst = lef + (pc * 8 + c) * NC * 2;
 #pragma unroll

@@ -138,6 +138,19 @@ def test_tensor_core_m2l_within_fp32_budget(orc, case):
     assert _field_rel(tc, simt) <= 1e-5
 
 
+def test_tensor_core_m2l_at_the_bench_size():
+    # uniform3d-2M (2^21 charges, L = 5, p = 8): some 200 (source class,
+    # offset) pairs reach each local expansion, the longest sums of the
+    # tensor-core path; the potential is the more sensitive output
+    w = W.uniform3d()
+    rc, tc = _run(w, "mixed")
+    assert rc == 0
+    rc, fp64 = _run(w, "fp64")
+    assert rc == 0
+    assert _rel(tc[0], fp64[0]) <= 1e-5
+    assert _field_rel(tc, fp64) <= 1e-5
+
+
 def test_bitwise_reproducible_and_coincident_particles(orc):
     w = W.tiny3d(5000, 13, L=3, p=8, dtype="f32")
     w.x[1], w.y[1], w.z[1] = w.x[0], w.y[0], w.z[0]   # a coincident pair contributes 0
