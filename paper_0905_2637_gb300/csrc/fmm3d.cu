@@ -1107,14 +1107,19 @@ template <int P> __host__ __device__ constexpr int tc3_nw() {
     return tc3_half_nw<P>(0) > tc3_half_nw<P>(1) ? tc3_half_nw<P>(0) : tc3_half_nw<P>(1);
 }
 
+// Registers for a half row: from coefficient j0 rounded down to even (so
+// that rows with an even coefficient count load 16-byte pieces), one spare.
+template <int P> __host__ __device__ constexpr int tc3_nwr() { return tc3_nw<P>() + 2; }
+
 // One K half H of a row of A in the input basis, hi and lo, into the K-major
-// images, from the coefficients j0(H) .. of the row held in w.
+// images, from the coefficients (j0(H) rounded down to even) .. of the row
+// held in w.
 template <int P, int H>
-__device__ __forceinline__ void tc3_write_half(const float2 (&w)[tc3_nw<P>()], float *ahi, float *alo,
+__device__ __forceinline__ void tc3_write_half(const float2 (&w)[tc3_nwr<P>()], float *ahi, float *alo,
                                                int row) {
     constexpr int NRP = mg_nrp(P), KH = NRP / 2;
     constexpr Tc3Basis<P> bas{};
-    constexpr int J0 = tc3_half_j0<P>(H);
+    constexpr int J0 = tc3_half_j0<P>(H) & ~1;
 #pragma unroll
     for (int g = 0; g < KH / 4; ++g) {
         float v4[4];
@@ -1288,16 +1293,32 @@ __global__ void __launch_bounds__(TC3_THREADS, 1) k3_m2l_tc(int L, const uint32_
         }
     };
     // rows of pair 0 in registers; the images of pair 0 on their way
-    // this stager's half of the next pair's row, in registers
-    constexpr int NW = tc3_nw<P>();
-    const int j0 = half ? tc3_half_j0<P>(1) : tc3_half_j0<P>(0);
-    const int nw = half ? tc3_half_nw<P>(1) : tc3_half_nw<P>(0);
-    float2 w[NW];
+    // this stager's half of the next pair's row, in registers, from its
+    // first coefficient rounded down to even
+    constexpr int NWR = tc3_nwr<P>();
+    const int j0 = (half ? tc3_half_j0<P>(1) : tc3_half_j0<P>(0)) & ~1;
+    const int jend = (half ? tc3_half_j0<P>(1) + tc3_half_nw<P>(1) : tc3_half_j0<P>(0) + tc3_half_nw<P>(0));
+    const int nw = jend - j0;  // coefficients wanted, <= NWR
+    float2 w[NWR];
     auto load_row = [&](int i) {
         const int sb = (stager && i < n_pairs) ? source(plist[i]) : -1;
         const float2 *src = lev + int64_t(sb < 0 ? 0 : sb) * NC + j0;
+        if constexpr (NC % 2 == 0) {
+            // 16-byte pieces: the row starts 16-byte aligned and j0 is even
 #pragma unroll
-        for (int t = 0; t < NW; ++t) w[t] = (sb >= 0 && t < nw) ? src[t] : make_float2(0.f, 0.f);
+            for (int t = 0; t < NWR / 2; ++t) {
+                float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (sb >= 0 && 2 * t < nw && j0 + 2 * t + 1 < NC)
+                    q4 = reinterpret_cast<const float4 *>(src)[t];
+                else if (sb >= 0 && 2 * t < nw)
+                    q4 = make_float4(src[2 * t].x, src[2 * t].y, 0.f, 0.f);
+                w[2 * t] = make_float2(q4.x, q4.y);
+                w[2 * t + 1] = make_float2(q4.z, q4.w);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < NWR; ++t) w[t] = (sb >= 0 && t < nw) ? src[t] : make_float2(0.f, 0.f);
+        }
     };
     // the stager's class, its row's sums so far (registers, FP32 round to
     // nearest): every TC3_FLUSH pairs the accumulator sets are read out of
